@@ -1,0 +1,311 @@
+/*
+ * nif.h -- C ABI of libnif.so, the GB300 (sm_103a) shadow-ray path of the
+ * Neural Intersection Function (Fujieda, Kao & Harada, HPG 2023).
+ *
+ * What the library computes (paper, Eq. 1): the visibility f(p, d) in {0, 1}
+ * of shadow-ray segments, 1 = visible, 0 = occluded.  Two ways are offered:
+ *   - exact: a BVH over the triangles, Moller-Trumbore tests (the comparison,
+ *     Sec. 6.6 "BVH Ray Cast");
+ *   - learned (Sec. 3, Sec. 4.1): for every (ray, object) pair whose segment
+ *     overlaps the object's AABB, the entry/exit points and the direction are
+ *     normalised to [0,1]^3 (Eq. 2), encoded with per-object latent grids
+ *     (Sec. 3.1, Table 1), fed to a small MLP (Sec. 5 "Architecture") whose
+ *     sigmoid output below 0.5 means occluded (Sec. 5).  Pairs are "outer" or
+ *     "inner" by whether the ray starts inside the box (Sec. 3.2).
+ *   - training (Sec. 4.2, Sec. 5 "Training"): L2 loss on sigmoid(z) against
+ *     per-pair BVH labels (Sec. 6.4), back-propagation into the MLP weights and
+ *     the grid latents, Adam.
+ *
+ * Conventions for every call
+ *   - Pointers named d_* are DEVICE pointers owned by the caller; the library
+ *     never allocates, frees or keeps device memory beyond a call.  Host
+ *     descriptors are read during the call only.
+ *   - Every call is asynchronous on `stream` (a cudaStream_t passed as void*;
+ *     NULL = legacy default stream) except nif_check and the *_size helpers,
+ *     which touch no device state or synchronise as documented.
+ *   - Argument errors are detected on the host and returned synchronously as
+ *     NIF_ERR_ARG (null pointer, negative size, unsupported combination ->
+ *     NIF_ERR_UNSUPPORTED, too small a buffer -> NIF_ERR_WORKSPACE) before any
+ *     work is queued; nif_last_error() then describes the error.  A failed
+ *     launch returns NIF_ERR_CUDA.  Errors found on the device (capacity
+ *     overflow, bounded waits that expired, non-finite loss) are recorded in
+ *     the first 16 bytes of the workspace and read by nif_check().
+ *   - n == 0 is valid everywhere and queues nothing.
+ */
+#ifndef NIF_H
+#define NIF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* One shadow-ray segment: origin o, direction d (unit length), valid hits
+ * strictly inside (tmin, tmax).  32 bytes, arrays must be 16-byte aligned. */
+typedef struct nif_ray {
+  float ox, oy, oz, tmin;
+  float dx, dy, dz, tmax;
+} nif_ray;
+
+typedef int32_t nif_status;
+#define NIF_OK 0
+#define NIF_ERR_ARG (-1)
+#define NIF_ERR_CUDA (-2)
+#define NIF_ERR_WORKSPACE (-3)
+#define NIF_ERR_TIMEOUT (-4)
+#define NIF_ERR_NUMERIC (-5)
+#define NIF_ERR_UNSUPPORTED (-6)
+#define NIF_ERR_BOUNDS (-7)
+
+#define NIF_MAX_LEVELS 24
+
+/* element types */
+#define NIF_F32 0
+#define NIF_F16 1
+#define NIF_BF16 2
+#define NIF_E4M3 3
+
+/* hidden-layer activation (Sec. 5 "Architecture": leaky ReLU; ReLU default) */
+#define NIF_ACT_RELU 0
+#define NIF_ACT_LEAKY 1
+
+/* which network answers a pair (Sec. 3: one outer and one inner network shared
+ * by all objects; Sec. 6.3: one network per object) */
+#define NIF_NETS_SINGLE 0 /* net 0 for every pair */
+#define NIF_NETS_CLASS 1  /* net 0 for outer pairs, net 1 for inner pairs */
+#define NIF_NETS_OBJECT 2 /* net = object id */
+
+/*
+ * Model description (host struct, read during a call).
+ *
+ * Grids (Sec. 3.1, Table 1; multi-resolution 3D form): level l has res[l]
+ * cells per axis and (res[l]+1)^3 vertices; it stores min((res[l]+1)^3,
+ * 2^log2_table) vertices: x-fastest dense indexing when all fit, otherwise the
+ * spatial hash (ix*1 ^ iy*2654435761 ^ iz*805459861) mod 2^log2_table (uint32
+ * arithmetic).  Every vertex holds n_features latents.  Per object there are
+ * two grids, position (entry and exit points) then direction, so
+ *   d_grids = [n_objects][2][V][n_features]  in grid_dtype,
+ *   V = sum_l stored vertices of level l        (nif_grid_vertices()).
+ * The network input is x = [entry levels | exit levels | direction levels],
+ * level-major, n_features per level: K = 3 * n_levels * n_features.
+ *
+ * Network (Sec. 5): bias-free, n_hidden layers of `width` units, one output
+ * logit.  d_weights = [n_nets][P] in mlp_dtype with, per net, row-major
+ * W_1 [width][K], W_2..W_H [width][width], w_out [1][width];
+ * P = nif_weight_count().  mlp_dtype NIF_F32 runs on CUDA cores;
+ * NIF_F16/NIF_BF16/NIF_E4M3 run on tcgen05 tensor cores with FP32
+ * accumulation (width 64 or 128, K a multiple of 16 (32 for E4M3)).
+ * NIF_E4M3 also needs d_scales = [n_nets][n_hidden+1][2] FP32 pairs
+ * (activation scale, weight scale) per layer: stored value = real / scale.
+ */
+typedef struct nif_model_desc {
+  int32_t n_levels;
+  int32_t n_features;
+  int32_t log2_table;
+  int32_t res[NIF_MAX_LEVELS];
+  int32_t grid_dtype; /* NIF_F32 or NIF_F16 */
+  int32_t n_objects;
+  const float* d_obj_aabb; /* [n_objects][6]: min xyz, max xyz */
+  const void* d_grids;
+  int32_t n_hidden;
+  int32_t width;
+  int32_t act;
+  float leaky_slope;
+  int32_t mlp_dtype;
+  int32_t net_mode;
+  int32_t n_nets;
+  const void* d_weights;
+  const float* d_scales; /* NIF_E4M3 only, else NULL */
+  int32_t tile_m;        /* tensor-core rows per tile: 0 (=128), 128 or 256 */
+  int32_t ctas_per_sm;   /* 0 = library default */
+} nif_model_desc;
+
+/* Thread-local description of the last error returned on this thread. */
+const char* nif_last_error(void);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int32_t nif_version(void);
+
+/* Stored vertices per grid V, and weights per network P; -1 on a bad desc. */
+int64_t nif_grid_vertices(const nif_model_desc* m);
+int64_t nif_weight_count(const nif_model_desc* m);
+
+/* ------------------------------------------------------------------ BVH --
+ * Exact visibility, the comparison of Sec. 6.6 and the source of training
+ * labels (Sec. 4.2).  Triangles are tested with two-sided Moller-Trumbore
+ * (no epsilon, det == 0 misses, u,v,u+v bounds inclusive, hit iff
+ * tmin < t < tmax), computed in FP32 with IEEE division and no FMA
+ * contraction; node culling is conservative, so any-hit results equal
+ * brute force over all triangles bit for bit.
+ *
+ * bvh_build: d_verts [n_verts][3] FP32, d_tris [n_tris][3] int32 vertex ids,
+ * d_tri_tag [n_tris] int32 or NULL (a per-triangle tag, e.g. object id, used
+ * by bvh_cast_pairs; -1 = untagged).  Output is written into d_bvh
+ * (bvh_build_size(n_tris) bytes); scratch d_ws (bvh_build_workspace_size
+ * bytes) may be reused after the stream reaches the end of the build.
+ * The result is self-contained: it keeps no pointer to the inputs.
+ * An AABB-only hierarchy (a top-level BVH over object boxes, Sec. 4.1) is
+ * built by bvh_build_boxes from d_boxes [n][6] (min xyz, max xyz). */
+size_t bvh_build_size(int64_t n_tris);
+size_t bvh_build_workspace_size(int64_t n_tris);
+nif_status bvh_build(const float* d_verts, int64_t n_verts, const int32_t* d_tris,
+                     int64_t n_tris, const int32_t* d_tri_tag, void* d_bvh, size_t bvh_bytes,
+                     void* d_ws, size_t ws_bytes, void* stream);
+nif_status bvh_build_boxes(const float* d_boxes, int64_t n, void* d_bvh, size_t bvh_bytes,
+                           void* d_ws, size_t ws_bytes, void* stream);
+
+/* Host copy of the build statistics (synchronises the stream): node count,
+ * primitive count, tree depth.  Returns NIF_OK or an error. */
+nif_status bvh_info(const void* d_bvh, int64_t* n_nodes, int64_t* n_prims, int32_t* depth,
+                    void* stream);
+
+/* Any-hit shadow cast (Eq. 1): bit i of d_occluded_bits (uint32 words,
+ * ceil(n/32) of them, bit i%32 of word i/32) is set to 1 when ray i is
+ * occluded, 0 when visible.  The words are overwritten, not OR-ed. */
+nif_status bvh_cast_shadow(const void* d_bvh, const nif_ray* d_rays, int64_t n,
+                           uint32_t* d_occluded_bits, void* stream);
+
+/* Closest-hit cast (primary visibility, Sec. 5 "Primary Visibility
+ * Computation"): d_t[i] = nearest hit t or +inf, d_prim[i] = that triangle's
+ * input index (smallest on a tie) or -1.  Either output may be NULL. */
+nif_status bvh_cast_closest(const void* d_bvh, const nif_ray* d_rays, int64_t n, float* d_t,
+                            int32_t* d_prim, void* stream);
+
+/* Per-pair labels (Sec. 6.4: one sample per (ray, object) pair): d_hit[q] = 1
+ * when a triangle whose tag equals d_obj[q] is hit inside the segment of ray
+ * d_ray_id[q], else 0.  Needs a BVH built with tags. */
+nif_status bvh_cast_pairs(const void* d_bvh, const nif_ray* d_rays, const uint32_t* d_ray_id,
+                          const uint32_t* d_obj, int64_t nq, uint8_t* d_hit, void* stream);
+
+/* Shadow rays from primary hits (Sec. 6.5: rays from the shading points to
+ * a light): ray i*spp+s starts at o_i + t_i d_i of camera ray i and points at
+ * light sample d_light[(i*spp+s)*3 .. +2]
+ * (or at d_light[0..2] for every ray when light_per_ray == 0), with
+ * tmin = `tmin`, tmax = distance to the light.  A camera ray without a hit
+ * (t = +inf) yields an empty segment (tmin = tmax = 0). */
+nif_status nif_shadow_rays(const nif_ray* d_camera, const float* d_t, int64_t n, int32_t spp,
+                           const float* d_light, int32_t light_per_ray, float tmin,
+                           nif_ray* d_out, void* stream);
+
+/* ------------------------------------------------------------ NIF path --
+ * Queries.  A query is a (ray, object) pair: d_ray_id[q] (uint32) and
+ * d_qobj[q] = object id | (1u << 31 when the pair is inner).  Query lists
+ * passed to nif_infer_queries / nif_fwd_train / nif_train_step are grouped
+ * by network: queries of net g occupy [d_group_off[g], d_group_off[g+1]),
+ * d_group_off is device int64 [n_nets + 1]. */
+#define NIF_QUERY_INNER 0x80000000u
+
+/* Workspace for nif_frontend / nif_infer with up to max_rays rays and
+ * max_queries queries, and for nif_train_step with a batch of nq queries.
+ * The first 256 bytes (the device error word) must be zero before first use;
+ * nif_check clears them after reporting an error.  0 on a bad descriptor. */
+size_t nif_workspace_size(const nif_model_desc* m, int64_t max_rays, int64_t max_queries);
+size_t nif_train_workspace_size(const nif_model_desc* m, int64_t nq);
+
+/* Reads and clears the device error word of a workspace (synchronises the
+ * stream).  Returns NIF_OK or the first device error recorded since the last
+ * check; *detail (nullable) receives an error-specific value. */
+nif_status nif_check(void* d_ws, int64_t* detail, void* stream);
+
+/* Step a0/a1 (Sec. 4.1): find every (ray, object) pair whose segment overlaps
+ * the object's AABB (FP32 slab test: an axis with d == 0 passes iff
+ * lo <= o <= hi; overlap iff max(tmin, entry) <= min(tmax, exit)), classify it
+ * inner when entry <= tmin, and write the pairs grouped by network, objects
+ * ascending inside a group (pairs of one object in no fixed order).  d_tlas is a
+ * bvh_build_boxes hierarchy over the object boxes, or NULL to test every box.
+ * Outputs: d_ray_id, d_qobj (capacity max_q), d_group_off [n_nets+1],
+ * *d_count (device int64) = number of queries found.  Found > max_q is a
+ * device error NIF_ERR_WORKSPACE (the lists then hold max_q of them). */
+nif_status nif_frontend(const nif_model_desc* m, const void* d_tlas, const nif_ray* d_rays,
+                        int64_t n, uint32_t* d_ray_id, uint32_t* d_qobj, int64_t max_q,
+                        int64_t* d_group_off, int64_t* d_count, void* d_ws, size_t ws_bytes,
+                        void* stream);
+
+/* Step a2 alone (Sec. 3.1): the network input rows of nq queries, written to
+ * d_features [nq][K] in features_dtype (NIF_F32 or NIF_F16). */
+nif_status nif_encode(const nif_model_desc* m, const nif_ray* d_rays, const uint32_t* d_ray_id,
+                      const uint32_t* d_qobj, int64_t nq, void* d_features,
+                      int32_t features_dtype, void* stream);
+
+/* Steps a1-a4 on a grouped query list: per query the logit z (d_logits[q],
+ * nullable) and, for z < 0 (sigmoid(z) < 0.5, occluded), bit d_ray_id[q] is
+ * OR-ed into d_occluded_bits (nullable; caller initialises it, e.g. to zero
+ * or to a bvh_cast_shadow result for non-NIF geometry).  n_rays bounds the
+ * ray ids. */
+nif_status nif_infer_queries(const nif_model_desc* m, const nif_ray* d_rays, int64_t n_rays,
+                             const uint32_t* d_ray_id, const uint32_t* d_qobj,
+                             const int64_t* d_group_off, int64_t nq_max,
+                             uint32_t* d_occluded_bits, float* d_logits, void* d_ws,
+                             size_t ws_bytes, void* stream);
+
+/* The whole query (a0-a4): nif_frontend into the workspace, then
+ * nif_infer_queries.  d_occluded_bits is OR-ed into as above. */
+nif_status nif_infer(const nif_model_desc* m, const void* d_tlas, const nif_ray* d_rays,
+                     int64_t n, uint32_t* d_occluded_bits, void* d_ws, size_t ws_bytes,
+                     void* stream);
+
+/* ------------------------------------------------------------ training --
+ * Optimiser state (Sec. 5 "Training": Adam, beta1 0.9, beta2 0.999,
+ * eps 1e-15, L2 loss).  FP32 master copies of weights and grids are updated;
+ * the model's d_weights / d_grids (in their own dtypes) are refreshed from
+ * them after every step.  Gradients are accumulated in FP32 and zeroed by the
+ * Adam kernel after use.  loss_scale multiplies dL/dz before back-propagation
+ * and divides the gradients in Adam (1 = off). */
+typedef struct nif_optim_desc {
+  float lr, beta1, beta2, eps, loss_scale;
+  int32_t step; /* number of completed steps; nif_train_step increments it */
+  float* d_w_master; float* d_w_grad; float* d_w_m; float* d_w_v; /* [n_nets*P] */
+  float* d_g_master; float* d_g_grad; float* d_g_m; float* d_g_v; /* [n_obj*2*V*F] */
+} nif_optim_desc;
+
+/* Forward for training (FP32 weights and grids on the CUDA cores): per query
+ * the logit d_z[q] and the saved activations d_saved (nif_saved_size bytes,
+ * FP32, feature-major [K + n_hidden*width][nq]: x then every hidden layer). */
+size_t nif_saved_size(const nif_model_desc* m, int64_t nq);
+nif_status nif_fwd_train(const nif_model_desc* m, const nif_ray* d_rays,
+                         const uint32_t* d_ray_id, const uint32_t* d_qobj,
+                         const int64_t* d_group_off, int64_t nq, float* d_z, void* d_saved,
+                         void* stream);
+
+/* dL/dz of L = (1/B) sum_q (sigmoid(z_q) - y_q)^2, y = d_label[q] (1 visible),
+ * B = nq; times loss_scale.  d_loss (nullable, device FP32) receives L. */
+nif_status nif_loss(const float* d_z, const uint8_t* d_label, int64_t nq, float loss_scale,
+                    float* d_dz, float* d_loss, void* stream);
+
+/* MLP backward: accumulates dL/dW into d_w_grad ([n_nets*P] FP32, +=) and
+ * writes dL/dx into d_dx, FP32 feature-major [K][nq]. */
+nif_status nif_mlp_bwd(const nif_model_desc* m, const uint32_t* d_qobj,
+                       const int64_t* d_group_off, int64_t nq, const void* d_saved,
+                       const float* d_dz, float* d_w_grad, float* d_dx, void* stream);
+
+/* Grid backward: scatters dL/dx (FP32 [K][nq]) through the interpolation
+ * weights into d_g_grad ([n_obj][2][V][F] FP32, +=; FP32 atomics, so the
+ * summation order is not fixed). */
+nif_status nif_grid_bwd(const nif_model_desc* m, const nif_ray* d_rays,
+                        const uint32_t* d_ray_id, const uint32_t* d_qobj, int64_t nq,
+                        const float* d_dx, float* d_g_grad, void* stream);
+
+/* One dense Adam update with bias correction over n entries (every entry,
+ * zero gradients included): master, m, v updated in place, grad zeroed,
+ * d_copy (nullable) refreshed in copy_dtype.  `step` is the 1-based step
+ * number used for bias correction; grads are divided by grad_scale. */
+nif_status nif_adam(float* d_master, float* d_grad, float* d_m, float* d_v, int64_t n,
+                    float lr, float beta1, float beta2, float eps, float grad_scale,
+                    int32_t step, void* d_copy, int32_t copy_dtype, void* stream);
+
+/* A whole step: forward and backward on the FP32 masters (as nif_fwd_train,
+ * nif_loss, nif_mlp_bwd, nif_grid_bwd), then Adam on the weights and the grids
+ * refreshing m->d_weights and m->d_grids in their own dtypes (o->step is
+ * incremented).  d_loss (nullable) receives the batch loss.  Workspace:
+ * nif_train_workspace_size(m, nq) bytes. */
+nif_status nif_train_step(nif_model_desc* m, nif_optim_desc* o, const nif_ray* d_rays,
+                          const uint32_t* d_ray_id, const uint32_t* d_qobj,
+                          const int64_t* d_group_off, const uint8_t* d_label, int64_t nq,
+                          float* d_loss, void* d_ws, size_t ws_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NIF_H */

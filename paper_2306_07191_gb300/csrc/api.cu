@@ -1,0 +1,428 @@
+// C ABI of libnif: argument validation, workspace layout and dispatch to
+// the kernels.  Every entry point validates on the host, queues work on the
+// caller's stream and returns; nothing here allocates device memory.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "nif_kernels.cuh"
+
+namespace nif {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+nif_status fail(nif_status code, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return code;
+}
+
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return kSMs;
+  if (cached[dev] == 0) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = kSMs;
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
+static bool level_layout(const nif_model_desc* m, uint32_t* off, uint32_t* hashed) {
+  if (m->n_levels < 1 || m->n_levels > NIF_MAX_LEVELS) return false;
+  if (m->log2_table < 1 || m->log2_table > 30) return false;
+  uint64_t T = 1ull << m->log2_table;
+  uint64_t o = 0;
+  uint32_t hm = 0;
+  for (int l = 0; l < m->n_levels; ++l) {
+    int R = m->res[l];
+    if (R < 1 || R > (1 << 20)) return false;
+    uint64_t full = (uint64_t)(R + 1) * (R + 1) * (R + 1);
+    uint64_t stored = full > T ? T : full;
+    if (full > T) hm |= 1u << l;
+    if (off) off[l] = (uint32_t)o;
+    o += stored;
+    if (o >= (1ull << 32)) return false;
+  }
+  if (off) off[m->n_levels] = (uint32_t)o;
+  if (hashed) *hashed = hm;
+  return true;
+}
+
+int64_t grid_vertices(const nif_model_desc* m) {
+  uint32_t off[NIF_MAX_LEVELS + 1];
+  if (!m || !level_layout(m, off, nullptr)) return -1;
+  return off[m->n_levels];
+}
+
+int64_t weight_count(const nif_model_desc* m) {
+  if (!m || m->n_hidden < 0 || m->n_hidden > 8 || m->width < 1 || m->n_levels < 1 ||
+      m->n_features < 1)
+    return -1;
+  int64_t K = 3LL * m->n_levels * m->n_features;
+  if (m->n_hidden == 0) return K;
+  return K * m->width + (int64_t)(m->n_hidden - 1) * m->width * m->width + m->width;
+}
+
+nif_status make_params(const nif_model_desc* m, NifParams* p) {
+  NIF_CHECK_ARG(m != nullptr, "null model descriptor");
+  NIF_CHECK_ARG(m->n_features == 1 || m->n_features == 2 || m->n_features == 4 || m->n_features == 8,
+                "n_features must be 1, 2, 4 or 8 (got %d)", m->n_features);
+  std::memset(p, 0, sizeof(*p));
+  NIF_CHECK_ARG(level_layout(m, p->off, &p->hashed),
+                "bad grid levels (n_levels 1..%d, log2_table 1..30, res >= 1, < 2^32 vertices)",
+                NIF_MAX_LEVELS);
+  NIF_CHECK_ARG(m->grid_dtype == NIF_F32 || m->grid_dtype == NIF_F16, "grid_dtype must be F32 or F16");
+  NIF_CHECK_ARG(m->n_objects >= 1, "n_objects must be >= 1");
+  NIF_CHECK_ARG(m->d_obj_aabb && m->d_grids && m->d_weights, "null model pointer");
+  NIF_CHECK_ARG(m->n_hidden >= 0 && m->n_hidden <= 8, "n_hidden must be 0..8");
+  NIF_CHECK_ARG(m->width >= 1 && m->width <= 256, "width must be 1..256");
+  NIF_CHECK_ARG(m->act == NIF_ACT_RELU || m->act == NIF_ACT_LEAKY, "bad activation");
+  NIF_CHECK_ARG(m->mlp_dtype >= NIF_F32 && m->mlp_dtype <= NIF_E4M3, "bad mlp dtype");
+  int want_nets = m->net_mode == NIF_NETS_SINGLE ? 1
+                  : m->net_mode == NIF_NETS_CLASS ? 2
+                  : m->net_mode == NIF_NETS_OBJECT ? m->n_objects : -1;
+  NIF_CHECK_ARG(want_nets > 0, "bad net_mode");
+  NIF_CHECK_ARG(m->n_nets == want_nets, "n_nets %d does not match net_mode (%d)", m->n_nets, want_nets);
+  NIF_CHECK_ARG(m->n_nets <= kMaxGroups, "at most %d networks", kMaxGroups);
+  int n_buckets = (m->net_mode == NIF_NETS_CLASS ? 2 : 1) * m->n_objects;
+  NIF_CHECK_ARG(n_buckets <= 16384, "too many objects for the front end (%d buckets)", n_buckets);
+  p->L = m->n_levels;
+  p->F = m->n_features;
+  p->log2T = m->log2_table;
+  p->K = 3 * p->L * p->F;
+  for (int l = 0; l < p->L; ++l) p->res[l] = m->res[l];
+  p->grid_elems = (int64_t)p->off[p->L] * p->F;
+  p->grid_dtype = m->grid_dtype;
+  p->n_obj = m->n_objects;
+  p->aabb = m->d_obj_aabb;
+  p->grids = m->d_grids;
+  p->n_hidden = m->n_hidden;
+  p->width = m->width;
+  p->act = m->act;
+  p->slope = m->leaky_slope;
+  p->mlp_dtype = m->mlp_dtype;
+  p->net_mode = m->net_mode;
+  p->n_nets = m->n_nets;
+  p->weights = m->d_weights;
+  p->P = weight_count(m);
+  p->scales = m->mlp_dtype == NIF_E4M3 ? m->d_scales : nullptr;
+  return NIF_OK;
+}
+
+int n_groups_of(const NifParams& p) { return p.n_nets; }
+
+size_t frontend_ws_bytes(const NifParams& p) {
+  int n_buckets = (p.net_mode == NIF_NETS_CLASS ? 2 : 1) * p.n_obj;
+  return align_up(2 * align_up(n_buckets, 64) * sizeof(uint32_t), 256);
+}
+
+// Workspace layout of nif_infer / nif_frontend.
+struct InferWs {
+  DevError* err;
+  int64_t* goff;
+  int64_t* count;
+  uint32_t* qray;
+  uint32_t* qobj;
+  size_t bytes;
+};
+
+static InferWs infer_layout(const NifParams& p, void* base, int64_t max_q) {
+  InferWs w{};
+  size_t o = kErrBytes + frontend_ws_bytes(p);
+  char* b = static_cast<char*>(base);
+  w.err = reinterpret_cast<DevError*>(b);
+  w.goff = reinterpret_cast<int64_t*>(b + o);
+  o += align_up((p.n_nets + 1) * sizeof(int64_t), 256);
+  w.count = reinterpret_cast<int64_t*>(b + o);
+  o += 256;
+  w.qray = reinterpret_cast<uint32_t*>(b + o);
+  o += align_up(max_q * sizeof(uint32_t), 256);
+  w.qobj = reinterpret_cast<uint32_t*>(b + o);
+  o += align_up(max_q * sizeof(uint32_t), 256);
+  w.bytes = o;
+  return w;
+}
+
+// Queries a nif_infer workspace can hold: encoded in the error block.
+struct WsHeaderExtra {
+  int64_t max_q;
+};
+
+static int64_t ws_max_q(const NifParams& p, size_t ws_bytes) {
+  InferWs w0 = infer_layout(p, nullptr, 0);
+  if (ws_bytes <= w0.bytes) return 0;
+  return static_cast<int64_t>((ws_bytes - w0.bytes) / 8 / 64 * 64) - 128;
+}
+
+// Training workspace: error block, z, dz, saved activations, dx.
+struct TrainWs {
+  DevError* err;
+  float* z;
+  float* dz;
+  float* saved;
+  float* dx;
+  size_t bytes;
+};
+
+static TrainWs train_layout(const NifParams& p, void* base, int64_t nq) {
+  TrainWs w{};
+  char* b = static_cast<char*>(base);
+  size_t o = kErrBytes;
+  w.err = reinterpret_cast<DevError*>(b);
+  w.z = reinterpret_cast<float*>(b + o);
+  o += align_up(nq * 4, 256);
+  w.dz = reinterpret_cast<float*>(b + o);
+  o += align_up(nq * 4, 256);
+  w.saved = reinterpret_cast<float*>(b + o);
+  o += align_up((size_t)(p.K + p.n_hidden * p.width) * nq * 4, 256);
+  w.dx = reinterpret_cast<float*>(b + o);
+  o += align_up((size_t)p.K * nq * 4, 256);
+  w.bytes = o;
+  return w;
+}
+
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+
+}  // namespace nif
+
+using namespace nif;
+
+extern "C" {
+
+const char* nif_last_error(void) { return g_err; }
+
+int32_t nif_version(void) { return 10000; }
+
+int64_t nif_grid_vertices(const nif_model_desc* m) { return grid_vertices(m); }
+
+int64_t nif_weight_count(const nif_model_desc* m) { return weight_count(m); }
+
+size_t nif_workspace_size(const nif_model_desc* m, int64_t max_rays, int64_t max_queries) {
+  NifParams p;
+  if (make_params(m, &p) != NIF_OK || max_rays < 0 || max_queries < 0) return 0;
+  (void)max_rays;
+  return infer_layout(p, nullptr, max_queries + 256).bytes;
+}
+
+size_t nif_train_workspace_size(const nif_model_desc* m, int64_t nq) {
+  NifParams p;
+  if (make_params(m, &p) != NIF_OK || nq < 0) return 0;
+  return train_layout(p, nullptr, nq).bytes;
+}
+
+nif_status nif_check(void* d_ws, int64_t* detail, void* stream) {
+  NIF_CHECK_ARG(d_ws != nullptr, "nif_check: null workspace");
+  DevError e;
+  cudaStream_t st = as_stream(stream);
+  NIF_CUDA_TRY(cudaMemcpyAsync(&e, d_ws, sizeof(e), cudaMemcpyDeviceToHost, st));
+  NIF_CUDA_TRY(cudaStreamSynchronize(st));
+  if (detail) *detail = e.detail;
+  if (e.code != 0) {
+    NIF_CUDA_TRY(cudaMemsetAsync(d_ws, 0, sizeof(DevError), st));
+    NIF_CUDA_TRY(cudaStreamSynchronize(st));
+    return fail(e.code, "device error %d (detail %lld)", e.code, (long long)e.detail);
+  }
+  return NIF_OK;
+}
+
+nif_status nif_frontend(const nif_model_desc* m, const void* d_tlas, const nif_ray* d_rays, int64_t n,
+                        uint32_t* d_ray_id, uint32_t* d_qobj, int64_t max_q, int64_t* d_group_off,
+                        int64_t* d_count, void* d_ws, size_t ws_bytes, void* stream) {
+  NifParams p;
+  nif_status s = make_params(m, &p);
+  if (s != NIF_OK) return s;
+  NIF_CHECK_ARG(n >= 0 && max_q >= 0, "nif_frontend: negative size");
+  NIF_CHECK_ARG(d_group_off && d_count && d_ws, "nif_frontend: null pointer");
+  NIF_CHECK_ARG(n == 0 || (d_rays && aligned16(d_rays)), "nif_frontend: rays null or not 16-byte aligned");
+  NIF_CHECK_ARG(max_q == 0 || (d_ray_id && d_qobj), "nif_frontend: null query arrays");
+  NIF_CHECK_ARG(n < (int64_t(1) << 32), "nif_frontend: at most 2^32 rays");
+  if (ws_bytes < kErrBytes + frontend_ws_bytes(p))
+    return fail(NIF_ERR_WORKSPACE, "nif_frontend: workspace too small");
+  return launch_frontend(p, d_tlas, d_rays, n, d_ray_id, d_qobj, max_q, d_group_off, d_count, d_ws,
+                         as_stream(stream));
+}
+
+nif_status nif_encode(const nif_model_desc* m, const nif_ray* d_rays, const uint32_t* d_ray_id,
+                      const uint32_t* d_qobj, int64_t nq, void* d_features, int32_t features_dtype,
+                      void* stream) {
+  NifParams p;
+  nif_status s = make_params(m, &p);
+  if (s != NIF_OK) return s;
+  NIF_CHECK_ARG(nq >= 0, "nif_encode: negative nq");
+  NIF_CHECK_ARG(features_dtype == NIF_F32 || features_dtype == NIF_F16, "nif_encode: features dtype");
+  if (nq == 0) return NIF_OK;
+  NIF_CHECK_ARG(d_rays && d_ray_id && d_qobj && d_features, "nif_encode: null pointer");
+  NIF_CHECK_ARG(aligned16(d_rays), "nif_encode: rays not 16-byte aligned");
+  return launch_encode(p, d_rays, d_ray_id, d_qobj, nq, d_features, features_dtype, as_stream(stream));
+}
+
+nif_status nif_infer_queries(const nif_model_desc* m, const nif_ray* d_rays, int64_t n_rays,
+                             const uint32_t* d_ray_id, const uint32_t* d_qobj,
+                             const int64_t* d_group_off, int64_t nq_max, uint32_t* d_occluded_bits,
+                             float* d_logits, void* d_ws, size_t ws_bytes, void* stream) {
+  NifParams p;
+  nif_status s = make_params(m, &p);
+  if (s != NIF_OK) return s;
+  NIF_CHECK_ARG(n_rays >= 0 && nq_max >= 0, "nif_infer_queries: negative size");
+  NIF_CHECK_ARG(d_group_off != nullptr, "nif_infer_queries: null group offsets");
+  if (nq_max == 0) return NIF_OK;
+  NIF_CHECK_ARG(d_rays && d_ray_id && d_qobj, "nif_infer_queries: null pointer");
+  NIF_CHECK_ARG(aligned16(d_rays), "nif_infer_queries: rays not 16-byte aligned");
+  NIF_CHECK_ARG(d_ws == nullptr || ws_bytes >= kErrBytes, "nif_infer_queries: workspace too small");
+  cudaStream_t st = as_stream(stream);
+  if (p.mlp_dtype == NIF_F32)
+    return launch_fwd_f32(p, d_rays, d_ray_id, d_qobj, d_group_off, nq_max, d_occluded_bits,
+                          d_logits, nullptr, 0, st);
+  return launch_fwd_tc(p, d_rays, d_ray_id, d_qobj, d_group_off, nq_max, d_occluded_bits, d_logits,
+                       m->tile_m, m->ctas_per_sm, static_cast<DevError*>(d_ws), st);
+}
+
+nif_status nif_infer(const nif_model_desc* m, const void* d_tlas, const nif_ray* d_rays, int64_t n,
+                     uint32_t* d_occluded_bits, void* d_ws, size_t ws_bytes, void* stream) {
+  NifParams p;
+  nif_status s = make_params(m, &p);
+  if (s != NIF_OK) return s;
+  NIF_CHECK_ARG(n >= 0, "nif_infer: negative n");
+  NIF_CHECK_ARG(d_ws != nullptr, "nif_infer: null workspace");
+  if (n == 0) return NIF_OK;
+  NIF_CHECK_ARG(d_rays && d_occluded_bits, "nif_infer: null pointer");
+  int64_t max_q = ws_max_q(p, ws_bytes);
+  if (max_q <= 0) return fail(NIF_ERR_WORKSPACE, "nif_infer: workspace too small");
+  InferWs w = infer_layout(p, d_ws, max_q);
+  if (w.bytes > ws_bytes) return fail(NIF_ERR_WORKSPACE, "nif_infer: workspace too small");
+  cudaStream_t st = as_stream(stream);
+  s = launch_frontend(p, d_tlas, d_rays, n, w.qray, w.qobj, max_q, w.goff, w.count, d_ws, st);
+  if (s != NIF_OK) return s;
+  if (p.mlp_dtype == NIF_F32)
+    return launch_fwd_f32(p, d_rays, w.qray, w.qobj, w.goff, -1, d_occluded_bits, nullptr, nullptr,
+                          0, st);
+  return launch_fwd_tc(p, d_rays, w.qray, w.qobj, w.goff, -1, d_occluded_bits, nullptr, m->tile_m,
+                       m->ctas_per_sm, w.err, st);
+}
+
+size_t nif_saved_size(const nif_model_desc* m, int64_t nq) {
+  NifParams p;
+  if (make_params(m, &p) != NIF_OK || nq < 0) return 0;
+  return (size_t)(p.K + p.n_hidden * p.width) * nq * sizeof(float);
+}
+
+nif_status nif_fwd_train(const nif_model_desc* m, const nif_ray* d_rays, const uint32_t* d_ray_id,
+                         const uint32_t* d_qobj, const int64_t* d_group_off, int64_t nq, float* d_z,
+                         void* d_saved, void* stream) {
+  NifParams p;
+  nif_status s = make_params(m, &p);
+  if (s != NIF_OK) return s;
+  NIF_CHECK_ARG(p.mlp_dtype == NIF_F32, "nif_fwd_train: training runs on FP32 weights");
+  NIF_CHECK_ARG(nq >= 0, "nif_fwd_train: negative nq");
+  if (nq == 0) return NIF_OK;
+  NIF_CHECK_ARG(d_rays && d_ray_id && d_qobj && d_group_off && d_z && d_saved, "nif_fwd_train: null pointer");
+  return launch_fwd_f32(p, d_rays, d_ray_id, d_qobj, d_group_off, nq, nullptr, d_z,
+                        static_cast<float*>(d_saved), nq, as_stream(stream));
+}
+
+nif_status nif_loss(const float* d_z, const uint8_t* d_label, int64_t nq, float loss_scale, float* d_dz,
+                    float* d_loss, void* stream) {
+  NIF_CHECK_ARG(nq >= 0, "nif_loss: negative nq");
+  NIF_CHECK_ARG(nq == 0 || (d_z && d_label && d_dz), "nif_loss: null pointer");
+  return launch_loss(d_z, d_label, nq, loss_scale, d_dz, d_loss, as_stream(stream));
+}
+
+nif_status nif_mlp_bwd(const nif_model_desc* m, const uint32_t* d_qobj, const int64_t* d_group_off,
+                       int64_t nq, const void* d_saved, const float* d_dz, float* d_w_grad, float* d_dx,
+                       void* stream) {
+  NifParams p;
+  nif_status s = make_params(m, &p);
+  if (s != NIF_OK) return s;
+  (void)d_qobj;
+  NIF_CHECK_ARG(p.mlp_dtype == NIF_F32, "nif_mlp_bwd: training runs on FP32 weights");
+  NIF_CHECK_ARG(nq >= 0, "nif_mlp_bwd: negative nq");
+  if (nq == 0) return NIF_OK;
+  NIF_CHECK_ARG(d_group_off && d_saved && d_dz && d_w_grad && d_dx, "nif_mlp_bwd: null pointer");
+  return launch_bwd_f32(p, d_group_off, nq, static_cast<const float*>(d_saved), d_dz, d_w_grad, d_dx,
+                        as_stream(stream));
+}
+
+nif_status nif_grid_bwd(const nif_model_desc* m, const nif_ray* d_rays, const uint32_t* d_ray_id,
+                        const uint32_t* d_qobj, int64_t nq, const float* d_dx, float* d_g_grad,
+                        void* stream) {
+  NifParams p;
+  nif_status s = make_params(m, &p);
+  if (s != NIF_OK) return s;
+  NIF_CHECK_ARG(nq >= 0, "nif_grid_bwd: negative nq");
+  if (nq == 0) return NIF_OK;
+  NIF_CHECK_ARG(d_rays && d_ray_id && d_qobj && d_dx && d_g_grad, "nif_grid_bwd: null pointer");
+  return launch_grid_bwd(p, d_rays, d_ray_id, d_qobj, nq, d_dx, nq, d_g_grad, as_stream(stream));
+}
+
+nif_status nif_adam(float* d_master, float* d_grad, float* d_m, float* d_v, int64_t n, float lr,
+                    float beta1, float beta2, float eps, float grad_scale, int32_t step, void* d_copy,
+                    int32_t copy_dtype, void* stream) {
+  NIF_CHECK_ARG(n >= 0, "nif_adam: negative n");
+  NIF_CHECK_ARG(step >= 1, "nif_adam: step is 1-based");
+  NIF_CHECK_ARG(grad_scale > 0.f, "nif_adam: grad_scale must be positive");
+  if (n == 0) return NIF_OK;
+  NIF_CHECK_ARG(d_master && d_grad && d_m && d_v, "nif_adam: null pointer");
+  return launch_adam(d_master, d_grad, d_m, d_v, n, lr, beta1, beta2, eps, grad_scale, step, d_copy,
+                     copy_dtype, as_stream(stream));
+}
+
+nif_status nif_train_step(nif_model_desc* m, nif_optim_desc* o, const nif_ray* d_rays,
+                          const uint32_t* d_ray_id, const uint32_t* d_qobj, const int64_t* d_group_off,
+                          const uint8_t* d_label, int64_t nq, float* d_loss, void* d_ws, size_t ws_bytes,
+                          void* stream) {
+  NifParams p;
+  nif_status s = make_params(m, &p);
+  if (s != NIF_OK) return s;
+  NIF_CHECK_ARG(o != nullptr, "nif_train_step: null optimiser");
+  NIF_CHECK_ARG(o->d_w_master && o->d_w_grad && o->d_w_m && o->d_w_v, "nif_train_step: null weight state");
+  NIF_CHECK_ARG(o->d_g_master && o->d_g_grad && o->d_g_m && o->d_g_v, "nif_train_step: null grid state");
+  NIF_CHECK_ARG(nq >= 1, "nif_train_step: empty batch");
+  NIF_CHECK_ARG(d_rays && d_ray_id && d_qobj && d_group_off && d_label && d_ws, "nif_train_step: null pointer");
+  NIF_CHECK_ARG(o->loss_scale > 0.f, "nif_train_step: loss_scale must be positive");
+  TrainWs w = train_layout(p, d_ws, nq);
+  if (w.bytes > ws_bytes) return fail(NIF_ERR_WORKSPACE, "nif_train_step: workspace too small (%zu < %zu)", ws_bytes, w.bytes);
+  // FP32 master view of the model: forward and backward run on the masters.
+  NifParams pm = p;
+  pm.grids = o->d_g_master;
+  pm.grid_dtype = NIF_F32;
+  pm.weights = o->d_w_master;
+  pm.mlp_dtype = NIF_F32;
+  pm.scales = nullptr;
+  cudaStream_t st = as_stream(stream);
+  s = launch_fwd_f32(pm, d_rays, d_ray_id, d_qobj, d_group_off, nq, nullptr, w.z, w.saved, nq, st);
+  if (s != NIF_OK) return s;
+  s = launch_loss(w.z, d_label, nq, o->loss_scale, w.dz, d_loss, st);
+  if (s != NIF_OK) return s;
+  s = launch_bwd_f32(pm, d_group_off, nq, w.saved, w.dz, o->d_w_grad, w.dx, st);
+  if (s != NIF_OK) return s;
+  s = launch_grid_bwd(pm, d_rays, d_ray_id, d_qobj, nq, w.dx, nq, o->d_g_grad, st);
+  if (s != NIF_OK) return s;
+  const int step = o->step + 1;
+  const int64_t nw = (int64_t)p.n_nets * p.P;
+  const int64_t ng = (int64_t)p.n_obj * 2 * p.grid_elems;
+  void* wcopy = m->mlp_dtype == NIF_E4M3 ? nullptr : const_cast<void*>(m->d_weights);
+  s = launch_adam(o->d_w_master, o->d_w_grad, o->d_w_m, o->d_w_v, nw, o->lr, o->beta1, o->beta2, o->eps,
+                  o->loss_scale, step, wcopy == o->d_w_master ? nullptr : wcopy, m->mlp_dtype, st);
+  if (s != NIF_OK) return s;
+  void* gcopy = const_cast<void*>(m->d_grids);
+  s = launch_adam(o->d_g_master, o->d_g_grad, o->d_g_m, o->d_g_v, ng, o->lr, o->beta1, o->beta2, o->eps,
+                  o->loss_scale, step, gcopy == o->d_g_master ? nullptr : gcopy, m->grid_dtype, st);
+  if (s != NIF_OK) return s;
+  o->step = step;
+  return NIF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,63 @@
+// Shared host/device plumbing of libnif: status codes, the thread-local
+// error message, launch checking, the device error word kept at the start of
+// every workspace, and small device helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdarg.h>
+
+#include "../../include/nif.h"
+
+namespace nif {
+
+constexpr int kSMs = 152;  // GB300: 2 dies x 76 SMs (queried at run time too)
+
+// ----------------------------------------------------------------- errors
+void set_error(const char* fmt, ...);
+nif_status fail(nif_status code, const char* fmt, ...);
+
+#define NIF_CHECK_ARG(cond, ...)                     \
+  do {                                               \
+    if (!(cond)) return ::nif::fail(NIF_ERR_ARG, __VA_ARGS__); \
+  } while (0)
+
+#define NIF_CUDA_TRY(expr)                                                                   \
+  do {                                                                                       \
+    cudaError_t e_ = (expr);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return ::nif::fail(NIF_ERR_CUDA, "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_), \
+                         __FILE__, __LINE__);                                                \
+  } while (0)
+
+#define NIF_LAUNCH_CHECK() NIF_CUDA_TRY(cudaGetLastError())
+
+int sm_count();
+
+// Device error word at the head of every workspace (16 bytes):
+//   [0] int32 first error code (0 = none), [1] int32 pad, [2..3] int64 detail.
+struct DevError {
+  int32_t code;
+  int32_t pad;
+  int64_t detail;
+};
+constexpr size_t kErrBytes = 256;  // error word + counters, keeps later data aligned
+
+__device__ __forceinline__ void raise_error(DevError* e, int32_t code, int64_t detail) {
+  if (e && atomicCAS(&e->code, 0, code) == 0) e->detail = detail;
+}
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline size_t align_up(size_t a, size_t b) { return (a + b - 1) / b * b; }
+
+// ------------------------------------------------------------ device misc
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+}  // namespace nif

@@ -1,0 +1,46 @@
+// Host-side launchers of the NIF kernels (defined in nif_simt.cu and
+// nif_tc.cu), called by the C ABI in api.cu.
+#pragma once
+
+#include "nif_params.cuh"
+
+namespace nif {
+
+constexpr int kMaxGroups = 1024;
+
+nif_status launch_frontend(const NifParams& p, const void* tlas, const nif_ray* rays, int64_t n,
+                           uint32_t* out_ray, uint32_t* out_qobj, int64_t max_q, int64_t* goff,
+                           int64_t* count, void* ws, cudaStream_t st);
+size_t frontend_ws_bytes(const NifParams& p);
+
+nif_status launch_encode(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
+                         const uint32_t* qobj, int64_t nq, void* out, int out_dtype,
+                         cudaStream_t st);
+
+// FP32 forward on the CUDA cores.  nq_hint >= 0 bounds the grid when the
+// number of queries is known on the host; saved (nullable) receives
+// [K + H*W][ld_saved] activations for training.
+nif_status launch_fwd_f32(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
+                          const uint32_t* qobj, const int64_t* goff, int64_t nq_hint,
+                          uint32_t* occ, float* logits, float* saved, int64_t ld_saved,
+                          cudaStream_t st);
+
+// Tensor-core forward (FP16 / BF16 / E4M3 operands, FP32 accumulation).
+nif_status launch_fwd_tc(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
+                         const uint32_t* qobj, const int64_t* goff, int64_t nq_hint,
+                         uint32_t* occ, float* logits, int tile_m, int ctas_per_sm,
+                         DevError* err, cudaStream_t st);
+nif_status check_tc_shape(const NifParams& p);
+
+nif_status launch_loss(const float* z, const uint8_t* label, int64_t nq, float scale, float* dz,
+                       float* loss, cudaStream_t st);
+nif_status launch_bwd_f32(const NifParams& p, const int64_t* goff, int64_t nq, const float* saved,
+                          const float* dz, float* wgrad, float* dx, cudaStream_t st);
+nif_status launch_grid_bwd(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
+                           const uint32_t* qobj, int64_t nq, const float* dx, int64_t ld,
+                           float* ggrad, cudaStream_t st);
+nif_status launch_adam(float* th, float* gr, float* m1, float* m2, int64_t n, float lr, float b1,
+                       float b2, float eps, float grad_scale, int step, void* copy, int copy_dtype,
+                       cudaStream_t st);
+
+}  // namespace nif

@@ -1,0 +1,254 @@
+// Device-side view of a nif_model_desc and the per-query parameterisation
+// shared by every NIF kernel: exact FP32 slab test (query selection and the
+// inner/outer class, Sec. 3.2, Sec. 4.1), entry/exit/direction normalisation
+// (Eq. 2, Sec. 3.1) and the multi-resolution grid lookup (Sec. 3.1, Table 1).
+#pragma once
+
+#include "common.cuh"
+
+namespace nif {
+
+constexpr int kMaxK = 3 * NIF_MAX_LEVELS * 8;
+constexpr uint32_t kHashP1 = 1u;
+constexpr uint32_t kHashP2 = 2654435761u;
+constexpr uint32_t kHashP3 = 805459861u;
+
+struct NifParams {
+  int L, F, log2T, K;
+  int res[NIF_MAX_LEVELS];
+  uint32_t off[NIF_MAX_LEVELS + 1];  // first stored vertex of each level
+  uint32_t hashed;                   // bit l set: level l is hashed
+  int64_t grid_elems;                // V * F, elements of one grid
+  int grid_dtype;
+  int n_obj;
+  const float* aabb;
+  const void* grids;
+  int n_hidden, width, act;
+  float slope;
+  int mlp_dtype, net_mode, n_nets;
+  const void* weights;
+  int64_t P;  // weights per network
+  const float* scales;
+};
+
+// Host: validate a descriptor and derive the device view.
+nif_status make_params(const nif_model_desc* m, NifParams* p);
+int64_t grid_vertices(const nif_model_desc* m);
+int64_t weight_count(const nif_model_desc* m);
+
+// Network that answers a query.
+__device__ __forceinline__ int net_of(const NifParams& p, uint32_t qobj) {
+  if (p.net_mode == NIF_NETS_CLASS) return (qobj & NIF_QUERY_INNER) ? 1 : 0;
+  if (p.net_mode == NIF_NETS_OBJECT) return static_cast<int>(qobj & 0x7fffffffu);
+  return 0;
+}
+
+// Exact FP32 slab test of a segment against a box.  Per axis t0 = (lo-o)/d,
+// t1 = (hi-o)/d; an axis with d == 0 passes iff lo <= o <= hi.
+// entry = max_k min(t0,t1), tin = max(tmin, entry), tout = min(tmax, min_k max).
+// No multiply-add occurs, so contraction cannot change the result.
+__device__ __forceinline__ bool exact_slab(const float o[3], const float d[3], float tmin,
+                                           float tmax, const float* box, float& tin, float& tout,
+                                           float& entry) {
+  float en = -INFINITY, ex = INFINITY;
+  bool blocked = false;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float lo = box[k], hi = box[3 + k];
+    if (d[k] == 0.0f) {
+      if (!(lo <= o[k] && o[k] <= hi)) blocked = true;
+    } else {
+      float t0 = __fdiv_rn(lo - o[k], d[k]);
+      float t1 = __fdiv_rn(hi - o[k], d[k]);
+      en = fmaxf(en, fminf(t0, t1));
+      ex = fminf(ex, fmaxf(t0, t1));
+    }
+  }
+  if (blocked) {
+    en = INFINITY;
+    ex = -INFINITY;
+  }
+  entry = en;
+  tin = fmaxf(tmin, en);
+  tout = fminf(tmax, ex);
+  return tin <= tout;
+}
+
+struct QueryPoints {
+  float u[3][3];  // entry, exit, direction, each in [0,1]^3
+};
+
+// Entry and exit points of the clipped segment, normalised to the box, and
+// the direction mapped to (d+1)/2 (Eq. 2 in its 3D form).
+__device__ __forceinline__ void query_points(const nif_ray& r, const float* box, QueryPoints& q) {
+  float o[3] = {r.ox, r.oy, r.oz}, d[3] = {r.dx, r.dy, r.dz};
+  float tin, tout, entry;
+  exact_slab(o, d, r.tmin, r.tmax, box, tin, tout, entry);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float lo = box[k], ext = box[3 + k] - box[k];
+    float a = (o[k] + tin * d[k] - lo) / ext;
+    float b = (o[k] + tout * d[k] - lo) / ext;
+    q.u[0][k] = fminf(fmaxf(a, 0.f), 1.f);
+    q.u[1][k] = fminf(fmaxf(b, 0.f), 1.f);
+    q.u[2][k] = (d[k] + 1.0f) * 0.5f;
+  }
+}
+
+// Cell, fractions and the 8 vertex indices of a point at one level.
+struct Taps {
+  uint32_t idx[8];
+  float w[8];
+};
+
+__device__ __forceinline__ void level_taps(const NifParams& p, int l, const float u[3], Taps& t) {
+  const int R = p.res[l];
+  int i[3];
+  float f[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float s = u[k] * static_cast<float>(R);
+    int c = static_cast<int>(floorf(s));
+    c = c < 0 ? 0 : (c > R - 1 ? R - 1 : c);
+    i[k] = c;
+    f[k] = s - static_cast<float>(c);
+  }
+  const bool hashed = (p.hashed >> l) & 1u;
+  const uint32_t mask = (1u << p.log2T) - 1u;
+  const uint32_t n1 = static_cast<uint32_t>(R + 1);
+  const uint32_t base = p.off[l];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    uint32_t x = i[0] + (c & 1), y = i[1] + ((c >> 1) & 1), z = i[2] + ((c >> 2) & 1);
+    uint32_t v = hashed ? (((x * kHashP1) ^ (y * kHashP2) ^ (z * kHashP3)) & mask)
+                        : (x + n1 * (y + n1 * z));
+    t.idx[c] = base + v;
+    float wx = (c & 1) ? f[0] : 1.f - f[0];
+    float wy = ((c >> 1) & 1) ? f[1] : 1.f - f[1];
+    float wz = ((c >> 2) & 1) ? f[2] : 1.f - f[2];
+    t.w[c] = wx * wy * wz;
+  }
+}
+
+__device__ __forceinline__ const void* grid_ptr(const NifParams& p, uint32_t obj, int which) {
+  size_t esz = p.grid_dtype == NIF_F16 ? 2 : 4;
+  return static_cast<const char*>(p.grids) +
+         (static_cast<int64_t>(obj) * 2 + which) * p.grid_elems * static_cast<int64_t>(esz);
+}
+
+// Interpolated F features of one level.
+template <int F, typename TG>
+__device__ __forceinline__ void gather_level(const TG* table, const Taps& t, float out[F]) {
+#pragma unroll
+  for (int f = 0; f < F; ++f) out[f] = 0.f;
+  if constexpr (F == 2 && sizeof(TG) == 2) {
+    __half2 v[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      v[c] = __ldg(reinterpret_cast<const __half2*>(table) + t.idx[c]);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      float2 fv = __half22float2(v[c]);
+      out[0] += t.w[c] * fv.x;
+      out[1] += t.w[c] * fv.y;
+    }
+  } else if constexpr (F == 2 && sizeof(TG) == 4) {
+    float2 v[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) v[c] = __ldg(reinterpret_cast<const float2*>(table) + t.idx[c]);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      out[0] += t.w[c] * v[c].x;
+      out[1] += t.w[c] * v[c].y;
+    }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+#pragma unroll
+      for (int f = 0; f < F; ++f) {
+        float v;
+        if constexpr (sizeof(TG) == 2)
+          v = __half2float(__ldg(reinterpret_cast<const __half*>(table) + (size_t)t.idx[c] * F + f));
+        else
+          v = __ldg(reinterpret_cast<const float*>(table) + (size_t)t.idx[c] * F + f);
+        out[f] += t.w[c] * v;
+      }
+    }
+  }
+}
+
+// Full network input of one query: calls sink(k, value) for k = 0..K-1 in
+// the order [entry levels | exit levels | direction levels].
+template <int F, typename TG, typename Sink>
+__device__ __forceinline__ void encode_query(const NifParams& p, const nif_ray& r, uint32_t qobj,
+                                             Sink&& sink) {
+  uint32_t obj = qobj & 0x7fffffffu;
+  const float* box = p.aabb + 6 * static_cast<size_t>(obj);
+  float bx[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) bx[k] = __ldg(box + k);
+  QueryPoints q;
+  query_points(r, bx, q);
+  const TG* tpos = static_cast<const TG*>(grid_ptr(p, obj, 0));
+  const TG* tdir = static_cast<const TG*>(grid_ptr(p, obj, 1));
+  for (int j = 0; j < 3; ++j) {
+    const TG* tab = j < 2 ? tpos : tdir;
+    for (int l = 0; l < p.L; ++l) {
+      Taps t;
+      level_taps(p, l, q.u[j], t);
+      float v[F];
+      gather_level<F, TG>(tab, t, v);
+#pragma unroll
+      for (int f = 0; f < F; ++f) sink((j * p.L + l) * F + f, v[f]);
+    }
+  }
+}
+
+__device__ __forceinline__ nif_ray load_nif_ray(const nif_ray* rays, uint32_t i) {
+  const float4* p4 = reinterpret_cast<const float4*>(rays + i);
+  float4 a = __ldg(p4), b = __ldg(p4 + 1);
+  nif_ray r;
+  r.ox = a.x; r.oy = a.y; r.oz = a.z; r.tmin = a.w;
+  r.dx = b.x; r.dy = b.y; r.dz = b.z; r.tmax = b.w;
+  return r;
+}
+
+// ---------------------------------------------------------- tile mapping
+// Block-local table of tile starts per group: tiles of `tile` queries never
+// cross a group boundary.  Returns the total number of tiles.
+__device__ __forceinline__ int64_t build_tile_prefix(const int64_t* goff, int n_groups, int tile, int64_t* s_pre) {
+  // one warp scans; groups are few (<= kMaxGroups)
+  if (threadIdx.x < 32) {
+    int lane = threadIdx.x;
+    int per = (n_groups + 31) / 32;
+    int g0 = lane * per, g1 = min(n_groups, g0 + per);
+    int64_t sum = 0;
+    for (int g = g0; g < g1; ++g) sum += (goff[g + 1] - goff[g] + tile - 1) / tile;
+    int64_t inc = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t v = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += v;
+    }
+    int64_t run = inc - sum;
+    for (int g = g0; g < g1; ++g) {
+      s_pre[g] = run;
+      run += (goff[g + 1] - goff[g] + tile - 1) / tile;
+    }
+    if (lane == 31) s_pre[n_groups] = inc;
+  }
+  __syncthreads();
+  return s_pre[n_groups];
+}
+
+__device__ __forceinline__ int find_group(const int64_t* s_pre, int n_groups, int64_t t) {
+  int lo = 0, hi = n_groups - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (s_pre[mid] <= t) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+
+}  // namespace nif

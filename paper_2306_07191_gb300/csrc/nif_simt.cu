@@ -1,0 +1,588 @@
+// NIF kernels on the CUDA cores:
+//  * the front end (Sec. 4.1: find the (ray, object) pairs whose segment
+//    overlaps an object's AABB, classify them inner/outer, Sec. 3.2, and bin
+//    them by network with block-aggregated atomics, the GPU counterpart of the
+//    paper's "Ray Cast" stage);
+//  * the stand-alone grid encoding (Sec. 3.1);
+//  * the FP32 MLP forward (Sec. 5 "Architecture") with optional saving of
+//    activations for training, the loss (Sec. 5 "Training": L2 on the sigmoid
+//    output), the FP32 MLP backward and the grid-latent scatter;
+//  * dense Adam (Sec. 5 "Training").
+#include <algorithm>
+#include <cmath>
+#include <type_traits>
+
+#include "bvh_layout.cuh"
+#include "nif_params.cuh"
+#include "nif_kernels.cuh"
+
+namespace nif {
+
+constexpr int kMaxHits = 64;
+
+// --------------------------------------------------------------- front end
+__device__ __forceinline__ int bucket_of(const NifParams& p, uint32_t obj, bool inner) {
+  return (p.net_mode == NIF_NETS_CLASS && inner ? p.n_obj : 0) + static_cast<int>(obj);
+}
+
+// Calls emit(obj, inner) for every object whose box the ray's segment overlaps.
+template <bool kTlas, typename Emit>
+__device__ __forceinline__ void for_each_pair(const NifParams& p, const char* tlas,
+                                              const bvh::Header* H, const nif_ray& r, Emit&& emit) {
+  float o[3] = {r.ox, r.oy, r.oz}, d[3] = {r.dx, r.dy, r.dz};
+  auto test = [&](uint32_t obj) {
+    float bx[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) bx[k] = __ldg(p.aabb + 6 * (size_t)obj + k);
+    float tin, tout, entry;
+    if (exact_slab(o, d, r.tmin, r.tmax, bx, tin, tout, entry)) emit(obj, entry <= r.tmin);
+  };
+  if (!kTlas) {
+    for (int k = 0; k < p.n_obj; ++k) test(static_cast<uint32_t>(k));
+    return;
+  }
+  const bvh::Node* nodes = reinterpret_cast<const bvh::Node*>(tlas + H->off_nodes);
+  const float4* prims = reinterpret_cast<const float4*>(tlas + H->off_prims);
+  bvh::RayF rf;
+  rf.o = make_float3(r.ox, r.oy, r.oz);
+  rf.d = make_float3(r.dx, r.dy, r.dz);
+  auto inv = [](float x) { return 1.0f / (fabsf(x) > 1e-30f ? x : copysignf(1e-30f, x)); };
+  rf.id = make_float3(inv(r.dx), inv(r.dy), inv(r.dz));
+  rf.tmin = r.tmin;
+  rf.tmax = r.tmax;
+  int32_t stack[bvh::kStack];
+  int sp = 0;
+  int32_t ref = H->root;
+  if (ref == bvh::kEmptyRoot) return;
+  for (int guard = 0; guard < bvh::kMaxVisits; ++guard) {
+    if (ref >= 0) {
+      const float4* np = reinterpret_cast<const float4*>(nodes + ref);
+      float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
+      int4 dd = __ldg(reinterpret_cast<const int4*>(np + 3));
+      float t0, t1;
+      bool h0 = bvh::cull(a.x, a.y, a.z, a.w, c.x, c.y, rf, rf.tmax, t0);
+      bool h1 = bvh::cull(b.x, b.y, b.z, b.w, c.z, c.w, rf, rf.tmax, t1);
+      if (h0 && h1) {
+        if (sp < bvh::kStack) stack[sp++] = dd.y;
+        ref = dd.x;
+        continue;
+      }
+      if (h0) { ref = dd.x; continue; }
+      if (h1) { ref = dd.y; continue; }
+    } else {
+      int32_t code = ~ref;
+      int32_t first = code >> 3, count = (code & 7) + 1;
+      for (int32_t k = first; k < first + count; ++k)
+        test(static_cast<uint32_t>(__float_as_int(__ldg(prims + 3 * (int64_t)k).w)));
+    }
+    if (sp == 0) break;
+    ref = stack[--sp];
+  }
+}
+
+template <bool kTlas>
+__global__ void __launch_bounds__(256) k_front_count(NifParams p, const char* tlas,
+                                                     const nif_ray* rays, int64_t n, int n_buckets,
+                                                     uint32_t* g_count) {
+  extern __shared__ uint32_t s_cnt[];
+  __shared__ bvh::Header H;
+  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x) s_cnt[b] = 0;
+  if (kTlas && threadIdx.x == 0) H = *reinterpret_cast<const bvh::Header*>(tlas);
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
+    for_each_pair<kTlas>(p, tlas, &H, r, [&](uint32_t obj, bool inner) {
+      atomicAdd(&s_cnt[bucket_of(p, obj, inner)], 1u);
+    });
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x)
+    if (s_cnt[b]) atomicAdd(&g_count[b], s_cnt[b]);
+}
+
+// Single block: exclusive scan of bucket counts into bucket cursors, group
+// offsets and the total; overflow of max_q is recorded as a device error.
+__global__ void __launch_bounds__(1024) k_front_scan(const uint32_t* count, int n_buckets,
+                                                     int buckets_per_group, int n_groups,
+                                                     int64_t max_q, uint32_t* cursor,
+                                                     int64_t* goff, int64_t* total,
+                                                     DevError* err) {
+  __shared__ int64_t s_part[1024];
+  int t = threadIdx.x;
+  int per = (n_buckets + blockDim.x - 1) / blockDim.x;
+  int b0 = t * per, b1 = min(n_buckets, b0 + per);
+  int64_t sum = 0;
+  for (int b = b0; b < b1; ++b) sum += count[b];
+  s_part[t] = sum;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    int64_t v = t >= o ? s_part[t - o] : 0;
+    __syncthreads();
+    s_part[t] += v;
+    __syncthreads();
+  }
+  int64_t run = s_part[t] - sum;
+  for (int b = b0; b < b1; ++b) {
+    int64_t c = run < max_q ? run : max_q;
+    cursor[b] = static_cast<uint32_t>(c);
+    if (b % buckets_per_group == 0) goff[b / buckets_per_group] = c;
+    run += count[b];
+  }
+  if (t == blockDim.x - 1) {
+    int64_t all = s_part[t];
+    goff[n_groups] = all < max_q ? all : max_q;
+    *total = all;
+    if (all > max_q) raise_error(err, NIF_ERR_WORKSPACE, all);
+  }
+}
+
+template <bool kTlas>
+__global__ void __launch_bounds__(256) k_front_scatter(NifParams p, const char* tlas,
+                                                       const nif_ray* rays, int64_t n,
+                                                       int n_buckets, uint32_t* g_cursor,
+                                                       int64_t max_q, uint32_t* out_ray,
+                                                       uint32_t* out_qobj, DevError* err) {
+  extern __shared__ uint32_t s_dyn[];
+  uint32_t* s_cnt = s_dyn;
+  uint32_t* s_base = s_dyn + n_buckets;
+  __shared__ bvh::Header H;
+  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x) s_cnt[b] = 0;
+  if (kTlas && threadIdx.x == 0) H = *reinterpret_cast<const bvh::Header*>(tlas);
+  __syncthreads();
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  uint32_t hits[kMaxHits];
+  uint32_t slot[kMaxHits];
+  int nh = 0;
+  if (i < n) {
+    nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
+    for_each_pair<kTlas>(p, tlas, &H, r, [&](uint32_t obj, bool inner) {
+      if (nh < kMaxHits) {
+        uint32_t b = static_cast<uint32_t>(bucket_of(p, obj, inner));
+        hits[nh] = obj | (inner ? NIF_QUERY_INNER : 0u);
+        slot[nh] = b;
+        ++nh;
+      } else {
+        raise_error(err, NIF_ERR_BOUNDS, i);
+      }
+    });
+  }
+  // local ranks inside the block
+  uint32_t rank[kMaxHits];
+  for (int k = 0; k < nh; ++k) rank[k] = atomicAdd(&s_cnt[slot[k]], 1u);
+  __syncthreads();
+  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x)
+    s_base[b] = s_cnt[b] ? atomicAdd(&g_cursor[b], s_cnt[b]) : 0u;
+  __syncthreads();
+  for (int k = 0; k < nh; ++k) {
+    int64_t pos = static_cast<int64_t>(s_base[slot[k]]) + rank[k];
+    if (pos < max_q) {
+      out_ray[pos] = static_cast<uint32_t>(i);
+      out_qobj[pos] = hits[k];
+    }
+  }
+}
+
+// ------------------------------------------------------------ encode only
+template <int F, typename TG, typename TO>
+__global__ void __launch_bounds__(128) k_encode(NifParams p, const nif_ray* rays,
+                                                const uint32_t* ray_id, const uint32_t* qobj,
+                                                int64_t nq, TO* out) {
+  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  nif_ray r = load_nif_ray(rays, ray_id[q]);
+  TO* row = out + q * p.K;
+  encode_query<F, TG>(p, r, qobj[q], [&](int k, float v) {
+    if constexpr (sizeof(TO) == 2) row[k] = __float2half_rn(v);
+    else row[k] = v;
+  });
+}
+
+// ------------------------------------------------------- FP32 MLP forward
+// One block of kTile threads handles a tile of queries of one network; the
+// activations live in shared memory as [feature][query] (+1 padding).
+constexpr int kTile = 64;
+constexpr int kLd = kTile + 1;
+
+__device__ __forceinline__ float act_fn(const NifParams& p, float a) {
+  return a > 0.f ? a : (p.act == NIF_ACT_LEAKY ? p.slope * a : 0.f);
+}
+
+template <int F, typename TG>
+__global__ void __launch_bounds__(kTile) k_mlp_fwd_f32(NifParams p, const nif_ray* rays,
+                                                       const uint32_t* ray_id,
+                                                       const uint32_t* qobj, const int64_t* goff,
+                                                       uint32_t* occ_bits, float* logits,
+                                                       float* saved, int64_t ld_saved) {
+  extern __shared__ float s_act[];
+  __shared__ int64_t s_pre[kMaxGroups + 1];
+  const int W = p.width, K = p.K, H = p.n_hidden;
+  const int maxf = K > W ? K : W;
+  float* A = s_act;               // [maxf][kLd]
+  float* B = s_act + maxf * kLd;  // [maxf][kLd]
+  int64_t n_tiles = build_tile_prefix(goff, p.n_nets, kTile, s_pre);
+  const float* wall = static_cast<const float*>(p.weights);
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    int g = find_group(s_pre, p.n_nets, t);
+    int64_t q0 = goff[g] + (t - s_pre[g]) * kTile;
+    int64_t qend = goff[g + 1];
+    int64_t q = q0 + threadIdx.x;
+    bool live = q < qend;
+    int tid = threadIdx.x;
+    if (live) {
+      nif_ray r = load_nif_ray(rays, ray_id[q]);
+      encode_query<F, TG>(p, r, qobj[q], [&](int k, float v) { A[k * kLd + tid] = v; });
+      if (saved)
+        for (int k = 0; k < K; ++k) saved[k * ld_saved + q] = A[k * kLd + tid];
+    }
+    __syncthreads();
+    const float* w = wall + static_cast<int64_t>(g) * p.P;
+    int fan_in = K;
+    float* in = A;
+    float* out = B;
+    int soff = K;
+    for (int l = 0; l < H; ++l) {
+      if (live) {
+        for (int j = 0; j < W; ++j) {
+          const float* wr = w + static_cast<int64_t>(j) * fan_in;
+          float acc = 0.f;
+          for (int k = 0; k < fan_in; ++k) acc += __ldg(wr + k) * in[k * kLd + tid];
+          float h = act_fn(p, acc);
+          out[j * kLd + tid] = h;
+          if (saved) saved[(soff + j) * ld_saved + q] = h;
+        }
+      }
+      w += static_cast<int64_t>(W) * fan_in;
+      fan_in = W;
+      soff += W;
+      float* tmp = in;
+      in = out;
+      out = tmp;
+    }
+    if (live) {
+      float z = 0.f;
+      for (int k = 0; k < fan_in; ++k) z += __ldg(w + k) * in[k * kLd + tid];
+      if (logits) logits[q] = z;
+      if (occ_bits && z < 0.f) atomicOr(&occ_bits[ray_id[q] >> 5], 1u << (ray_id[q] & 31));
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------- loss
+__global__ void k_loss(const float* z, const uint8_t* label, int64_t nq, float scale, float* dz,
+                       float* loss) {
+  float part = 0.f;
+  const float invB = 1.0f / static_cast<float>(nq);
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    float s = 1.0f / (1.0f + expf(-z[q]));
+    float y = label[q] ? 1.0f : 0.0f;
+    float e = s - y;
+    part += e * e;
+    dz[q] = scale * 2.0f * invB * e * s * (1.0f - s);
+  }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if (loss && (threadIdx.x & 31) == 0) atomicAdd(loss, part * invB);
+}
+
+// ----------------------------------------------------- FP32 MLP backward
+// Tile of kTile queries of one network: loads the saved activations, walks
+// the layers backwards, accumulates the tile's weight gradient in registers
+// (one output row per thread) and adds it to the global gradient.
+__global__ void __launch_bounds__(kTile) k_mlp_bwd_f32(NifParams p, const int64_t* goff,
+                                                       const float* saved, int64_t ld_saved,
+                                                       const float* dz, float* wgrad, float* dx) {
+  extern __shared__ float s_act[];
+  __shared__ int64_t s_pre[kMaxGroups + 1];
+  const int W = p.width, K = p.K, H = p.n_hidden;
+  const int maxf = K > W ? K : W;
+  float* Hs = s_act;                                   // [K + H*W][kLd]
+  float* DA = s_act + (K + H * W) * kLd;               // [W][kLd]
+  float* DH = DA + W * kLd;                            // [maxf][kLd]
+  int64_t n_tiles = build_tile_prefix(goff, p.n_nets, kTile, s_pre);
+  const float* wall = static_cast<const float*>(p.weights);
+  const int tid = threadIdx.x;
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    int g = find_group(s_pre, p.n_nets, t);
+    int64_t q0 = goff[g] + (t - s_pre[g]) * kTile;
+    int64_t qend = goff[g + 1];
+    int nrow = static_cast<int>(qend - q0 < kTile ? qend - q0 : kTile);
+    const int S = K + H * W;
+    for (int idx = tid; idx < S * kTile; idx += blockDim.x) {
+      int f = idx / kTile, c = idx % kTile;
+      Hs[f * kLd + c] = c < nrow ? saved[f * ld_saved + q0 + c] : 0.f;
+    }
+    float dzq = tid < nrow ? dz[q0 + tid] : 0.f;
+    __syncthreads();
+    // offsets of each layer's weights inside the network's block
+    const float* w = wall + static_cast<int64_t>(g) * p.P;
+    float* gw = wgrad + static_cast<int64_t>(g) * p.P;
+    int64_t woff[NIF_MAX_LEVELS];  // H <= NIF_MAX_LEVELS
+    {
+      int64_t o = 0;
+      int fi = K;
+      for (int l = 0; l < H; ++l) {
+        woff[l] = o;
+        o += static_cast<int64_t>(W) * fi;
+        fi = W;
+      }
+      woff[H] = o;
+    }
+    const int fan_last = H > 0 ? W : K;
+    const float* hl = Hs + (H > 0 ? (K + (H - 1) * W) : 0) * kLd;
+    // output layer: dw_out[j] = sum_q dz_q h_H[j][q]; dh[j][q] = dz_q w_out[j]
+    // (dz staged in row 0 of DA so every thread can read all of them)
+    DA[tid] = dzq;  // row 0 of DA used as scratch for dz
+    __syncthreads();
+    for (int j = tid; j < fan_last; j += blockDim.x) {
+      float acc = 0.f;
+      for (int c = 0; c < nrow; ++c) acc += DA[c] * hl[j * kLd + c];
+      atomicAdd(&gw[woff[H] + j], acc);
+    }
+    __syncthreads();
+    for (int j = 0; j < fan_last; ++j) DH[j * kLd + tid] = dzq * __ldg(w + woff[H] + j);
+    __syncthreads();
+    for (int l = H - 1; l >= 0; --l) {
+      const int fan_in = l == 0 ? K : W;
+      const float* hin = Hs + (l == 0 ? 0 : (K + (l - 1) * W)) * kLd;
+      const float* hout = Hs + (K + l * W) * kLd;
+      // da = dh * act'(a); act'(a) from the sign of the saved activation
+      for (int j = 0; j < W; ++j) {
+        float h = hout[j * kLd + tid];
+        float gdr = h > 0.f ? 1.f : (p.act == NIF_ACT_LEAKY ? p.slope : 0.f);
+        DA[j * kLd + tid] = tid < nrow ? DH[j * kLd + tid] * gdr : 0.f;
+      }
+      __syncthreads();
+      // dW_l[j][k] += sum_q da[j][q] hin[k][q]
+      for (int j = tid; j < W; j += blockDim.x) {
+        for (int k = 0; k < fan_in; ++k) {
+          float acc = 0.f;
+          for (int c = 0; c < nrow; ++c) acc += DA[j * kLd + c] * hin[k * kLd + c];
+          atomicAdd(&gw[woff[l] + static_cast<int64_t>(j) * fan_in + k], acc);
+        }
+      }
+      // dh_prev[k][q] = sum_j da[j][q] W_l[j][k]
+      for (int k = 0; k < fan_in; ++k) {
+        float acc = 0.f;
+        for (int j = 0; j < W; ++j) acc += DA[j * kLd + tid] * __ldg(w + woff[l] + static_cast<int64_t>(j) * fan_in + k);
+        DH[k * kLd + tid] = acc;
+      }
+      __syncthreads();
+    }
+    if (tid < nrow)
+      for (int k = 0; k < K; ++k) dx[k * ld_saved + q0 + tid] = DH[k * kLd + tid];
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------- grid backward
+template <int F, typename TG>
+__global__ void __launch_bounds__(128) k_grid_bwd(NifParams p, const nif_ray* rays,
+                                                  const uint32_t* ray_id, const uint32_t* qobj,
+                                                  int64_t nq, const float* dx, int64_t ld,
+                                                  float* ggrad) {
+  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  nif_ray r = load_nif_ray(rays, ray_id[q]);
+  uint32_t obj = qobj[q] & 0x7fffffffu;
+  float bx[6];
+  for (int k = 0; k < 6; ++k) bx[k] = __ldg(p.aabb + 6 * (size_t)obj + k);
+  QueryPoints pts;
+  query_points(r, bx, pts);
+  for (int j = 0; j < 3; ++j) {
+    float* g = ggrad + (static_cast<int64_t>(obj) * 2 + (j == 2 ? 1 : 0)) * p.grid_elems;
+    for (int l = 0; l < p.L; ++l) {
+      Taps t;
+      level_taps(p, l, pts.u[j], t);
+      float d[F];
+#pragma unroll
+      for (int f = 0; f < F; ++f) d[f] = dx[static_cast<int64_t>((j * p.L + l) * F + f) * ld + q];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        if constexpr (F == 2) {
+          atomicAdd(reinterpret_cast<float2*>(g) + t.idx[c], make_float2(t.w[c] * d[0], t.w[c] * d[1]));
+        } else {
+#pragma unroll
+          for (int f = 0; f < F; ++f) atomicAdd(g + static_cast<int64_t>(t.idx[c]) * F + f, t.w[c] * d[f]);
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------- Adam
+template <typename TC>
+__global__ void __launch_bounds__(256) k_adam(float* __restrict__ th, float* __restrict__ gr,
+                                              float* __restrict__ m1, float* __restrict__ m2,
+                                              int64_t n, float lr, float b1, float b2, float eps,
+                                              float inv_scale, float c1, float c2,
+                                              TC* __restrict__ copy) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float g = gr[i] * inv_scale;
+    float m = b1 * m1[i] + (1.f - b1) * g;
+    float v = b2 * m2[i] + (1.f - b2) * g * g;
+    float mh = m * c1, vh = v * c2;
+    float t = th[i] - lr * mh / (sqrtf(vh) + eps);
+    th[i] = t;
+    m1[i] = m;
+    m2[i] = v;
+    gr[i] = 0.f;
+    if (copy) {
+      if constexpr (sizeof(TC) == 2) {
+        if constexpr (std::is_same<TC, __half>::value) copy[i] = __float2half_rn(t);
+        else copy[i] = __float2bfloat16_rn(t);
+      } else {
+        copy[i] = t;
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------- launchers
+#define NIF_DISPATCH_FG(p, ...)                                               \
+  do {                                                                        \
+    if ((p).grid_dtype == NIF_F16) {                                          \
+      using TG = __half;                                                      \
+      switch ((p).F) {                                                        \
+        case 1: { constexpr int F = 1; __VA_ARGS__; } break;                  \
+        case 2: { constexpr int F = 2; __VA_ARGS__; } break;                  \
+        case 4: { constexpr int F = 4; __VA_ARGS__; } break;                  \
+        default: { constexpr int F = 8; __VA_ARGS__; } break;                 \
+      }                                                                       \
+    } else {                                                                  \
+      using TG = float;                                                       \
+      switch ((p).F) {                                                        \
+        case 1: { constexpr int F = 1; __VA_ARGS__; } break;                  \
+        case 2: { constexpr int F = 2; __VA_ARGS__; } break;                  \
+        case 4: { constexpr int F = 4; __VA_ARGS__; } break;                  \
+        default: { constexpr int F = 8; __VA_ARGS__; } break;                 \
+      }                                                                       \
+    }                                                                         \
+  } while (0)
+
+nif_status launch_frontend(const NifParams& p, const void* tlas, const nif_ray* rays, int64_t n,
+                           uint32_t* out_ray, uint32_t* out_qobj, int64_t max_q, int64_t* goff,
+                           int64_t* count, void* ws, cudaStream_t st) {
+  int n_groups = p.net_mode == NIF_NETS_OBJECT ? p.n_obj : (p.net_mode == NIF_NETS_CLASS ? 2 : 1);
+  int n_buckets = (p.net_mode == NIF_NETS_CLASS ? 2 : 1) * p.n_obj;
+  int per_group = p.net_mode == NIF_NETS_OBJECT ? 1 : p.n_obj;
+  DevError* err = static_cast<DevError*>(ws);
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + kErrBytes);
+  uint32_t* cur = cnt + align_up(n_buckets, 64);
+  NIF_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * n_buckets, st));
+  int blocks = static_cast<int>(std::min<int64_t>(ceil_div(n, 256), sm_count() * 8));
+  if (blocks < 1) blocks = 1;
+  size_t sh1 = sizeof(uint32_t) * n_buckets;
+  const char* tl = static_cast<const char*>(tlas);
+  if (n > 0) {
+    if (tlas) k_front_count<true><<<blocks, 256, sh1, st>>>(p, tl, rays, n, n_buckets, cnt);
+    else k_front_count<false><<<blocks, 256, sh1, st>>>(p, tl, rays, n, n_buckets, cnt);
+    NIF_LAUNCH_CHECK();
+  }
+  k_front_scan<<<1, 1024, 0, st>>>(cnt, n_buckets, per_group, n_groups, max_q, cur, goff, count, err);
+  NIF_LAUNCH_CHECK();
+  if (n > 0) {
+    int sblocks = static_cast<int>(ceil_div(n, 256));
+    size_t sh2 = 2 * sizeof(uint32_t) * n_buckets;
+    if (tlas)
+      k_front_scatter<true><<<sblocks, 256, sh2, st>>>(p, tl, rays, n, n_buckets, cur, max_q, out_ray,
+                                                       out_qobj, err);
+    else
+      k_front_scatter<false><<<sblocks, 256, sh2, st>>>(p, tl, rays, n, n_buckets, cur, max_q,
+                                                        out_ray, out_qobj, err);
+    NIF_LAUNCH_CHECK();
+  }
+  return NIF_OK;
+}
+
+nif_status launch_encode(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
+                         const uint32_t* qobj, int64_t nq, void* out, int out_dtype,
+                         cudaStream_t st) {
+  if (nq == 0) return NIF_OK;
+  int64_t blocks = ceil_div(nq, 128);
+  NIF_DISPATCH_FG(p, {
+    if (out_dtype == NIF_F16)
+      k_encode<F, TG, __half><<<blocks, 128, 0, st>>>(p, rays, ray_id, qobj, nq, (__half*)out);
+    else
+      k_encode<F, TG, float><<<blocks, 128, 0, st>>>(p, rays, ray_id, qobj, nq, (float*)out);
+  });
+  NIF_LAUNCH_CHECK();
+  return NIF_OK;
+}
+
+size_t fwd_f32_smem(const NifParams& p) {
+  int maxf = p.K > p.width ? p.K : p.width;
+  return 2 * sizeof(float) * maxf * kLd;
+}
+
+nif_status launch_fwd_f32(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
+                          const uint32_t* qobj, const int64_t* goff, int64_t nq_hint,
+                          uint32_t* occ, float* logits, float* saved, int64_t ld_saved,
+                          cudaStream_t st) {
+  size_t sh = fwd_f32_smem(p);
+  int blocks = sm_count() * 8;
+  if (nq_hint >= 0) blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(blocks, ceil_div(nq_hint, kTile) + p.n_nets)));
+  NIF_DISPATCH_FG(p, {
+    auto kern = k_mlp_fwd_f32<F, TG>;
+    NIF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    kern<<<blocks, kTile, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, saved, ld_saved);
+  });
+  NIF_LAUNCH_CHECK();
+  return NIF_OK;
+}
+
+nif_status launch_loss(const float* z, const uint8_t* label, int64_t nq, float scale, float* dz,
+                       float* loss, cudaStream_t st) {
+  if (loss) NIF_CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(float), st));
+  if (nq == 0) return NIF_OK;
+  int blocks = static_cast<int>(std::min<int64_t>(ceil_div(nq, 256), sm_count() * 4));
+  k_loss<<<blocks, 256, 0, st>>>(z, label, nq, scale, dz, loss);
+  NIF_LAUNCH_CHECK();
+  return NIF_OK;
+}
+
+nif_status launch_bwd_f32(const NifParams& p, const int64_t* goff, int64_t nq, const float* saved,
+                          const float* dz, float* wgrad, float* dx, cudaStream_t st) {
+  int maxf = p.K > p.width ? p.K : p.width;
+  size_t sh = sizeof(float) * kLd * (p.K + p.n_hidden * p.width + p.width + maxf);
+  if (sh > 220 * 1024) return fail(NIF_ERR_UNSUPPORTED, "mlp backward: network too large for one tile");
+  NIF_CUDA_TRY(cudaFuncSetAttribute(k_mlp_bwd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+  int blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(sm_count() * 2, ceil_div(nq, kTile) + p.n_nets)));
+  k_mlp_bwd_f32<<<blocks, kTile, sh, st>>>(p, goff, saved, nq, dz, wgrad, dx);
+  NIF_LAUNCH_CHECK();
+  return NIF_OK;
+}
+
+nif_status launch_grid_bwd(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
+                           const uint32_t* qobj, int64_t nq, const float* dx, int64_t ld,
+                           float* ggrad, cudaStream_t st) {
+  if (nq == 0) return NIF_OK;
+  int64_t blocks = ceil_div(nq, 128);
+  NIF_DISPATCH_FG(p, { k_grid_bwd<F, TG><<<blocks, 128, 0, st>>>(p, rays, ray_id, qobj, nq, dx, ld, ggrad); });
+  NIF_LAUNCH_CHECK();
+  return NIF_OK;
+}
+
+nif_status launch_adam(float* th, float* gr, float* m1, float* m2, int64_t n, float lr, float b1,
+                       float b2, float eps, float grad_scale, int step, void* copy, int copy_dtype,
+                       cudaStream_t st) {
+  if (n == 0) return NIF_OK;
+  double c1 = 1.0 / (1.0 - std::pow(static_cast<double>(b1), step));
+  double c2 = 1.0 / (1.0 - std::pow(static_cast<double>(b2), step));
+  int blocks = static_cast<int>(std::min<int64_t>(ceil_div(n, 256), sm_count() * 16));
+  float inv = 1.0f / grad_scale;
+  if (copy == nullptr || copy_dtype == NIF_F32)
+    k_adam<float><<<blocks, 256, 0, st>>>(th, gr, m1, m2, n, lr, b1, b2, eps, inv, (float)c1, (float)c2, (float*)copy);
+  else if (copy_dtype == NIF_F16)
+    k_adam<__half><<<blocks, 256, 0, st>>>(th, gr, m1, m2, n, lr, b1, b2, eps, inv, (float)c1, (float)c2, (__half*)copy);
+  else if (copy_dtype == NIF_BF16)
+    k_adam<__nv_bfloat16><<<blocks, 256, 0, st>>>(th, gr, m1, m2, n, lr, b1, b2, eps, inv, (float)c1, (float)c2, (__nv_bfloat16*)copy);
+  else
+    return fail(NIF_ERR_UNSUPPORTED, "adam: unsupported copy dtype %d", copy_dtype);
+  NIF_LAUNCH_CHECK();
+  return NIF_OK;
+}
+
+}  // namespace nif

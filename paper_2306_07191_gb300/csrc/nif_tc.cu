@@ -1,0 +1,478 @@
+// Fused NIF inference on the 5th-generation tensor cores (steps a1-a4).
+//
+// The paper runs the grid lookup and the MLP as separate kernels and keeps
+// each network's weights in shared memory for a thread block (Sec. 4.1,
+// Sec. 5, after Mueller et al.'s fully fused MLPs).  Here one persistent
+// kernel does everything for a tile of 128 queries of one network:
+//   1. every thread computes its query's entry/exit/direction points and
+//      trilinear lookups (Eq. 2, Sec. 3.1) and writes the network input, in
+//      the operand type, straight into the shared-memory A tile;
+//   2. one thread issues tcgen05.mma (M=128, N=width, K=16/32 per
+//      instruction) for layer 1 with the weights resident in shared memory;
+//      the FP32 accumulator lives in tensor memory (TMEM);
+//   3. all eight warps read the accumulator back with tcgen05.ld, apply the
+//      activation (ReLU / leaky ReLU, Sec. 5), convert, and write the next A
+//      tile into the same shared-memory buffer; repeat per hidden layer;
+//   4. the last hidden layer is dotted with the output weights on the CUDA
+//      cores; z < 0 (sigmoid(z) < 0.5) marks the pair occluded (Sec. 5) and the
+//      ray's bit is OR-ed into the occlusion mask.
+// Several CTAs per SM overlap one CTA's gathers with another's MMAs.
+//
+// Shared-memory operands use the canonical K-major layout without swizzle:
+// 8-row x 16-byte core matrices, 128 contiguous bytes each; core matrices
+// adjacent along K are 128 B apart (leading byte offset) and 8-row groups are
+// K*esize*8 B apart (stride byte offset).
+#include <cuda_fp8.h>
+
+#include <algorithm>
+
+#include "nif_params.cuh"
+#include "nif_kernels.cuh"
+
+namespace nif {
+namespace tc {
+
+constexpr int kM = 128;
+constexpr int kThreads = 256;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+// ------------------------------------------------------------ PTX wrappers
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after ~2 s and records NIF_ERR_TIMEOUT.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, DevError* err) {
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) {
+      raise_error(err, NIF_ERR_TIMEOUT, 1);
+      return false;
+    }
+  }
+  return true;
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+template <int kKind>  // 0: kind::f16 (f16/bf16), 1: kind::f8f6f4 (e4m3)
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                    uint32_t accumulate) {
+  if constexpr (kKind == 0) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  }
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+// 32 lanes x 16 columns of FP32 from TMEM (this warp's lane quarter).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: K-major, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>((lbo & 0x3FFFFu) >> 4) << 16;
+  d |= static_cast<uint64_t>((sbo & 0x3FFFFu) >> 4) << 32;
+  d |= static_cast<uint64_t>(1) << 46;  // descriptor version for tcgen05
+  return d;                             // base offset 0, no swizzle
+}
+
+// Instruction descriptor: FP32 accumulator, A and B of format `fmt`
+// (kind::f16: 0 = f16, 1 = bf16; kind::f8f6f4: 0 = e4m3), both K-major.
+__host__ __device__ constexpr uint32_t instr_desc(int m, int n, uint32_t fmt) {
+  return (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
+         (static_cast<uint32_t>(m >> 4) << 24);
+}
+
+// Byte offset of element (row, k) of a K-major tile with kdim columns.
+__device__ __forceinline__ uint32_t tile_off(int row, int k, int kdim, int esz) {
+  const int cb = 16 / esz;  // elements per 16-byte core row
+  return static_cast<uint32_t>(((row >> 3) * (kdim / cb) + k / cb) * 128 + (row & 7) * 16 +
+                               (k % cb) * esz);
+}
+
+template <int DT>
+struct Op;
+template <>
+struct Op<NIF_F16> {
+  using T = __half;
+  static constexpr int esz = 2, kind = 0, fmt = 0;
+  __device__ static T cvt(float v) { return __float2half_rn(v); }
+  __device__ static float load(const void* p, int64_t i) {
+    return __half2float(static_cast<const __half*>(p)[i]);
+  }
+};
+template <>
+struct Op<NIF_BF16> {
+  using T = __nv_bfloat16;
+  static constexpr int esz = 2, kind = 0, fmt = 1;
+  __device__ static T cvt(float v) { return __float2bfloat16_rn(v); }
+  __device__ static float load(const void* p, int64_t i) {
+    return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]);
+  }
+};
+template <>
+struct Op<NIF_E4M3> {
+  using T = __nv_fp8_e4m3;
+  static constexpr int esz = 1, kind = 1, fmt = 0;
+  __device__ static T cvt(float v) { return __nv_fp8_e4m3(v); }
+  __device__ static float load(const void* p, int64_t i) {
+    return static_cast<float>(static_cast<const __nv_fp8_e4m3*>(p)[i]);
+  }
+};
+
+template <int DT>
+__device__ __forceinline__ void store_elem(uint8_t* tile, int row, int k, int kdim, float v) {
+  using O = Op<DT>;
+  typename O::T t = O::cvt(v);
+  *reinterpret_cast<typename O::T*>(tile + tile_off(row, k, kdim, O::esz)) = t;
+}
+
+struct Layout {
+  uint32_t a_off, w_off[8], wout_off, zpart_off, total;
+};
+
+__host__ __device__ inline Layout make_layout(int Kp, int W, int H, int esz) {
+  Layout L{};
+  uint32_t o = 0;
+  L.a_off = o;
+  o += kM * (Kp > W ? Kp : W) * esz;
+  for (int l = 0; l < H; ++l) {
+    o = (o + 127) / 128 * 128;
+    L.w_off[l] = o;
+    o += W * (l == 0 ? Kp : W) * esz;
+  }
+  o = (o + 15) / 16 * 16;
+  L.wout_off = o;
+  o += W * 4;
+  L.zpart_off = o;
+  o += 2 * kM * 4;
+  L.total = o;
+  return L;
+}
+
+template <int F, typename TG, int DT>
+__global__ void __launch_bounds__(kThreads, 2)
+    k_fused(NifParams p, const nif_ray* __restrict__ rays, const uint32_t* __restrict__ ray_id,
+            const uint32_t* __restrict__ qobj, const int64_t* __restrict__ goff,
+            uint32_t* __restrict__ occ, float* __restrict__ logits, DevError* err, int Kp) {
+  using O = Op<DT>;
+  constexpr int esz = O::esz;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+  __shared__ int64_t s_pre[kMaxGroups + 1];
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int W = p.width, H = p.n_hidden, K = p.K;
+  const Layout L = make_layout(Kp, W, H, esz);
+  uint8_t* tileA = smem + L.a_off;
+  float* wout = reinterpret_cast<float*>(smem + L.wout_off);
+  float* zpart = reinterpret_cast<float*>(smem + L.zpart_off);
+  const uint32_t bar = smem_u32(&s_bar);
+  const uint32_t ncols = W <= 32 ? 32 : (W <= 64 ? 64 : (W <= 128 ? 128 : 256));
+
+  if (warp == 0) tmem_alloc(smem_u32(&s_tmem), ncols);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    s_abort = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+
+  const int64_t n_tiles = build_tile_prefix(goff, p.n_nets, kM, s_pre);
+  const uint32_t idesc = instr_desc(kM, W, O::fmt);
+  const int kstep = 32 / esz;  // K per MMA instruction: 16 (16-bit) or 32 (8-bit)
+  uint32_t phase = 0;
+  int cur_g = -1;
+
+  // epilogue ownership: TMEM lane quarter (warp & 3), column half (warp >> 2)
+  const int erow = 32 * (warp & 3) + lane;
+  const int ecol0 = (warp >> 2) * (W / 2);
+  const uint32_t taddr_row = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
+
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int g = find_group(s_pre, p.n_nets, t);
+    const int64_t q0 = goff[g] + (t - s_pre[g]) * kM;
+    const int64_t qend = goff[g + 1];
+    const float* sc = p.scales ? p.scales + static_cast<int64_t>(g) * (H + 1) * 2 : nullptr;
+
+    // ---- weights of network g into shared memory (B operands, K-major)
+    if (g != cur_g) {
+      const int64_t wbase = static_cast<int64_t>(g) * p.P;
+      int64_t off = 0;
+      for (int l = 0; l < H; ++l) {
+        const int fin = l == 0 ? K : W;
+        const int fpad = l == 0 ? Kp : W;
+        uint8_t* wt = smem + L.w_off[l];
+        for (int e = tid; e < W * fpad; e += kThreads) {
+          const int n = e / fpad, k = e % fpad;
+          const float v = k < fin ? O::load(p.weights, wbase + off + static_cast<int64_t>(n) * fin + k) : 0.f;
+          store_elem<DT>(wt, n, k, fpad, v);
+        }
+        off += static_cast<int64_t>(W) * fin;
+      }
+      for (int e = tid; e < W; e += kThreads) {
+        float v = O::load(p.weights, wbase + off + e);
+        wout[e] = sc ? v * sc[2 * H + 1] : v;
+      }
+      cur_g = g;
+    }
+
+    // ---- step a1/a2: encode 128 queries into the A tile (2 threads per query)
+    {
+      const int qi = tid & (kM - 1);
+      const int half = tid >> 7;
+      const int64_t q = q0 + qi;
+      const float s_in = sc ? 1.0f / sc[0] : 1.0f;
+      if (q < qend) {
+        const nif_ray r = load_nif_ray(rays, ray_id[q]);
+        const uint32_t qo = qobj[q];
+        const uint32_t obj = qo & 0x7fffffffu;
+        float bx[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) bx[k] = __ldg(p.aabb + 6 * static_cast<size_t>(obj) + k);
+        QueryPoints pts;
+        query_points(r, bx, pts);
+        const TG* tpos = static_cast<const TG*>(grid_ptr(p, obj, 0));
+        const TG* tdir = static_cast<const TG*>(grid_ptr(p, obj, 1));
+        for (int m = half; m < 3 * p.L; m += 2) {
+          const int j = m / p.L, l = m - j * p.L;
+          Taps tp;
+          level_taps(p, l, pts.u[j], tp);
+          float v[F];
+          gather_level<F, TG>(j < 2 ? tpos : tdir, tp, v);
+          const int k0 = m * F;
+          if constexpr (F == 2 && esz == 2) {
+            typename O::T a = O::cvt(v[0] * s_in), b = O::cvt(v[1] * s_in);
+            uint32_t packed = static_cast<uint32_t>(*reinterpret_cast<uint16_t*>(&a)) |
+                              (static_cast<uint32_t>(*reinterpret_cast<uint16_t*>(&b)) << 16);
+            *reinterpret_cast<uint32_t*>(tileA + tile_off(qi, k0, Kp, esz)) = packed;
+          } else {
+#pragma unroll
+            for (int f = 0; f < F; ++f) store_elem<DT>(tileA, qi, k0 + f, Kp, v[f] * s_in);
+          }
+        }
+        if (half == 0)
+          for (int k = K; k < Kp; ++k) store_elem<DT>(tileA, qi, k, Kp, 0.f);
+      } else {
+        for (int k = half; k < Kp; k += 2) store_elem<DT>(tileA, qi, k, Kp, 0.f);
+      }
+    }
+    fence_proxy_async();
+    __syncthreads();
+
+    // ---- step a3: hidden layers on the tensor cores
+    float zacc = 0.f;
+    for (int l = 0; l < H; ++l) {
+      const int kdim = l == 0 ? Kp : W;
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t a0 = smem_u32(tileA), b0 = smem_u32(smem + L.w_off[l]);
+        const uint32_t sbo = (kdim / (16 / esz)) * 128;
+        for (int kk = 0; kk < kdim / kstep; ++kk) {
+          const uint64_t ad = smem_desc(a0 + kk * 256, 128, sbo);
+          const uint64_t bd = smem_desc(b0 + kk * 256, 128, sbo);
+          mma<O::kind>(tmem, ad, bd, idesc, kk > 0 ? 1u : 0u);
+        }
+        mma_commit(bar);
+      }
+      bool ok = mbar_wait(bar, phase, err);
+      phase ^= 1u;
+      if (!ok) s_abort = 1;
+      tc_fence_after();
+      // epilogue: accumulator -> activation -> next A tile (or output dot)
+      const float scale = sc ? sc[2 * l] * sc[2 * l + 1] : 1.0f;
+      const float next_inv = (sc && l + 1 < H) ? 1.0f / sc[2 * (l + 1)] : 1.0f;
+      for (int c0 = 0; c0 < W / 2; c0 += 16) {
+        float v[16];
+        tmem_ld16(taddr_row + static_cast<uint32_t>(ecol0 + c0), v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          float a = v[i] * scale;
+          v[i] = a > 0.f ? a : (p.act == NIF_ACT_LEAKY ? p.slope * a : 0.f);
+        }
+        if (l + 1 < H) {
+          if constexpr (esz == 2) {
+            uint32_t pk[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              typename O::T a = O::cvt(v[2 * i] * next_inv), b = O::cvt(v[2 * i + 1] * next_inv);
+              pk[i] = static_cast<uint32_t>(*reinterpret_cast<uint16_t*>(&a)) |
+                      (static_cast<uint32_t>(*reinterpret_cast<uint16_t*>(&b)) << 16);
+            }
+            uint4* d0 = reinterpret_cast<uint4*>(tileA + tile_off(erow, ecol0 + c0, W, esz));
+            uint4* d1 = reinterpret_cast<uint4*>(tileA + tile_off(erow, ecol0 + c0 + 8, W, esz));
+            *d0 = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            *d1 = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) store_elem<DT>(tileA, erow, ecol0 + c0 + i, W, v[i] * next_inv);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) zacc += v[i] * wout[ecol0 + c0 + i];
+        }
+      }
+      tc_fence_before();
+      fence_proxy_async();
+      __syncthreads();
+      if (s_abort) break;
+    }
+    if (s_abort) break;
+
+    // ---- step a4: logit and visibility
+    zpart[(warp >> 2) * kM + erow] = zacc;
+    __syncthreads();
+    if (tid < kM) {
+      const int64_t q = q0 + tid;
+      if (q < qend) {
+        const float z = zpart[tid] + zpart[kM + tid];
+        if (logits) logits[q] = z;
+        if (occ && z < 0.f) {
+          const uint32_t rid = ray_id[q];
+          atomicOr(&occ[rid >> 5], 1u << (rid & 31));
+        }
+      }
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
+}  // namespace tc
+
+nif_status check_tc_shape(const NifParams& p) {
+  const int esz = p.mlp_dtype == NIF_E4M3 ? 1 : 2;
+  if (p.n_hidden < 1 || p.n_hidden > 8)
+    return fail(NIF_ERR_UNSUPPORTED, "tensor-core path needs 1..8 hidden layers");
+  if (!(p.width == 32 || p.width == 64 || p.width == 128 || p.width == 256))
+    return fail(NIF_ERR_UNSUPPORTED, "tensor-core path needs width 32, 64, 128 or 256");
+  const int Kp = (p.K + 32 / esz - 1) / (32 / esz) * (32 / esz);
+  tc::Layout L = tc::make_layout(Kp, p.width, p.n_hidden, esz);
+  if (L.total + 2048 > 200 * 1024)
+    return fail(NIF_ERR_UNSUPPORTED, "tensor-core path: %u bytes of shared memory needed", L.total);
+  if (p.mlp_dtype == NIF_E4M3 && p.scales == nullptr)
+    return fail(NIF_ERR_ARG, "E4M3 network needs d_scales");
+  return NIF_OK;
+}
+
+#define NIF_DISPATCH_FG_TC(p, ...)                                            \
+  do {                                                                        \
+    if ((p).grid_dtype == NIF_F16) {                                          \
+      using TG = __half;                                                      \
+      switch ((p).F) {                                                        \
+        case 1: { constexpr int F = 1; __VA_ARGS__; } break;                  \
+        case 2: { constexpr int F = 2; __VA_ARGS__; } break;                  \
+        case 4: { constexpr int F = 4; __VA_ARGS__; } break;                  \
+        default: { constexpr int F = 8; __VA_ARGS__; } break;                 \
+      }                                                                       \
+    } else {                                                                  \
+      using TG = float;                                                       \
+      switch ((p).F) {                                                        \
+        case 1: { constexpr int F = 1; __VA_ARGS__; } break;                  \
+        case 2: { constexpr int F = 2; __VA_ARGS__; } break;                  \
+        case 4: { constexpr int F = 4; __VA_ARGS__; } break;                  \
+        default: { constexpr int F = 8; __VA_ARGS__; } break;                 \
+      }                                                                       \
+    }                                                                         \
+  } while (0)
+
+template <int DT>
+static nif_status launch_dt(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
+                            const uint32_t* qobj, const int64_t* goff, int blocks, uint32_t* occ,
+                            float* logits, DevError* err, cudaStream_t st) {
+  const int esz = DT == NIF_E4M3 ? 1 : 2;
+  const int Kp = (p.K + 32 / esz - 1) / (32 / esz) * (32 / esz);
+  tc::Layout L = tc::make_layout(Kp, p.width, p.n_hidden, esz);
+  size_t sh = L.total + 1024;
+  NIF_DISPATCH_FG_TC(p, {
+    auto kern = tc::k_fused<F, TG, DT>;
+    NIF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    kern<<<blocks, tc::kThreads, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, err, Kp);
+  });
+  NIF_LAUNCH_CHECK();
+  return NIF_OK;
+}
+
+nif_status launch_fwd_tc(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
+                         const uint32_t* qobj, const int64_t* goff, int64_t nq_hint, uint32_t* occ,
+                         float* logits, int tile_m, int ctas_per_sm, DevError* err,
+                         cudaStream_t st) {
+  nif_status s = check_tc_shape(p);
+  if (s != NIF_OK) return s;
+  if (tile_m != 0 && tile_m != 128)
+    return fail(NIF_ERR_UNSUPPORTED, "tensor-core path: tile_m %d (128 supported)", tile_m);
+  int per_sm = ctas_per_sm > 0 ? ctas_per_sm : 2;
+  int blocks = sm_count() * per_sm;
+  if (nq_hint >= 0)
+    blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(blocks, ceil_div(nq_hint, tc::kM) + p.n_nets)));
+  if (p.mlp_dtype == NIF_F16) return launch_dt<NIF_F16>(p, rays, ray_id, qobj, goff, blocks, occ, logits, err, st);
+  if (p.mlp_dtype == NIF_BF16) return launch_dt<NIF_BF16>(p, rays, ray_id, qobj, goff, blocks, occ, logits, err, st);
+  if (p.mlp_dtype == NIF_E4M3) return launch_dt<NIF_E4M3>(p, rays, ray_id, qobj, goff, blocks, occ, logits, err, st);
+  return fail(NIF_ERR_UNSUPPORTED, "tensor-core path: mlp dtype %d", p.mlp_dtype);
+}
+
+}  // namespace nif

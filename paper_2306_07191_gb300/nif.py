@@ -1,0 +1,350 @@
+"""Python-side objects over the libnif C ABI: device buffers come from torch
+(caching allocator, streams), every computation runs in libnif's kernels.
+
+* ``BVH``        -- bvh_build / bvh_cast_shadow / bvh_cast_closest / bvh_cast_pairs
+* ``NifModel``   -- model description, grids and weights; frontend, encode,
+                    infer_queries, infer
+* ``Trainer``    -- FP32 master state and Adam moments; nif_train_step
+* ``NifQueryFn`` -- torch.autograd.Function whose forward is nif_fwd_train and
+                    whose backward is nif_mlp_bwd + nif_grid_bwd
+* ``NifLossFn``  -- torch.autograd.Function around nif_loss
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass, field
+
+import torch
+
+from . import _lib as L
+
+_DT = {L.NIF_F32: torch.float32, L.NIF_F16: torch.float16, L.NIF_BF16: torch.bfloat16,
+       L.NIF_E4M3: torch.float8_e4m3fn}
+
+
+def _ptr(t: torch.Tensor | None):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def bits_to_bool(bits: torch.Tensor, n: int) -> torch.Tensor:
+    """Unpack a uint32 occlusion bitmask (bit i%32 of word i/32) into bool[n]."""
+    w = bits.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+    sh = torch.arange(32, device=bits.device, dtype=torch.int64)
+    return (((w[:, None] >> sh[None, :]) & 1).reshape(-1)[:n]).bool()
+
+
+def empty_bits(n: int, device="cuda") -> torch.Tensor:
+    return torch.zeros((n + 31) // 32, dtype=torch.int32, device=device)
+
+
+class BVH:
+    """Exact shadow-ray visibility over a triangle soup (or object boxes)."""
+
+    def __init__(self, verts: torch.Tensor, tris: torch.Tensor, tags: torch.Tensor | None = None,
+                 boxes: bool = False, stream=None):
+        self.n = int(tris.shape[0])
+        nb = L.lib.bvh_build_size(self.n)
+        nw = L.lib.bvh_build_workspace_size(self.n)
+        dev = verts.device
+        self.buf = torch.empty(nb, dtype=torch.uint8, device=dev)
+        ws = torch.empty(max(nw, 256), dtype=torch.uint8, device=dev)
+        if boxes:
+            L.call("bvh_build_boxes", _ptr(verts), self.n, _ptr(self.buf), nb, _ptr(ws), ws.numel(),
+                   _stream(stream))
+        else:
+            self._inputs = (verts, tris, tags)
+            L.call("bvh_build", _ptr(verts), int(verts.shape[0]), _ptr(tris), self.n, _ptr(tags),
+                   _ptr(self.buf), nb, _ptr(ws), ws.numel(), _stream(stream))
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        del ws
+        self._inputs = None
+
+    @classmethod
+    def from_boxes(cls, boxes: torch.Tensor, stream=None) -> "BVH":
+        return cls(boxes.contiguous(), boxes, boxes=True, stream=stream)
+
+    def info(self):
+        nn, npr, dep = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()
+        L.call("bvh_info", _ptr(self.buf), ctypes.byref(nn), ctypes.byref(npr), ctypes.byref(dep),
+               _stream())
+        return {"nodes": nn.value, "prims": npr.value, "depth": dep.value}
+
+    def cast_shadow(self, rays: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        n = int(rays.shape[0])
+        bits = out if out is not None else empty_bits(n, rays.device)
+        L.call("bvh_cast_shadow", _ptr(self.buf), _ptr(rays), n, _ptr(bits), _stream(stream))
+        return bits
+
+    def cast_closest(self, rays: torch.Tensor, stream=None):
+        n = int(rays.shape[0])
+        t = torch.empty(n, dtype=torch.float32, device=rays.device)
+        prim = torch.empty(n, dtype=torch.int32, device=rays.device)
+        L.call("bvh_cast_closest", _ptr(self.buf), _ptr(rays), n, _ptr(t), _ptr(prim), _stream(stream))
+        return t, prim
+
+    def cast_pairs(self, rays, ray_id, obj, stream=None):
+        nq = int(ray_id.shape[0])
+        hit = torch.empty(nq, dtype=torch.uint8, device=rays.device)
+        L.call("bvh_cast_pairs", _ptr(self.buf), _ptr(rays), _ptr(ray_id), _ptr(obj), nq, _ptr(hit),
+               _stream(stream))
+        return hit
+
+
+def shadow_rays(camera: torch.Tensor, t: torch.Tensor, light: torch.Tensor, spp: int = 1,
+                per_ray: bool = False, tmin: float = 1e-3, stream=None) -> torch.Tensor:
+    n = int(camera.shape[0])
+    out = torch.empty((n * spp, 8), dtype=torch.float32, device=camera.device)
+    L.call("nif_shadow_rays", _ptr(camera), _ptr(t), n, spp, _ptr(light), int(per_ray), tmin,
+           _ptr(out), _stream(stream))
+    return out
+
+
+@dataclass
+class NifConfig:
+    res: list
+    n_features: int = 2
+    log2_table: int = 19
+    grid_dtype: int = L.NIF_F32
+    n_hidden: int = 3
+    width: int = 64
+    act: int = L.NIF_ACT_RELU
+    leaky_slope: float = 0.01
+    mlp_dtype: int = L.NIF_F32
+    net_mode: int = L.NIF_NETS_SINGLE
+    tile_m: int = 0
+    ctas_per_sm: int = 0
+
+    @property
+    def n_levels(self):
+        return len(self.res)
+
+    @property
+    def K(self):
+        return 3 * len(self.res) * self.n_features
+
+
+class NifModel:
+    """A NIF model: per-object grids and per-network weights on the device."""
+
+    def __init__(self, cfg: NifConfig, obj_aabb: torch.Tensor, grids: torch.Tensor,
+                 weights: torch.Tensor, scales: torch.Tensor | None = None):
+        self.cfg = cfg
+        self.obj_aabb = obj_aabb.contiguous()
+        self.grids = grids
+        self.weights = weights
+        self.scales = scales
+        self.n_obj = int(obj_aabb.shape[0])
+        if cfg.net_mode == L.NIF_NETS_CLASS:
+            self.n_nets = 2
+        elif cfg.net_mode == L.NIF_NETS_OBJECT:
+            self.n_nets = self.n_obj
+        else:
+            self.n_nets = 1
+        self._ws = None
+
+    def desc(self) -> L.ModelDesc:
+        c = self.cfg
+        d = L.ModelDesc()
+        d.n_levels = len(c.res)
+        d.n_features = c.n_features
+        d.log2_table = c.log2_table
+        for i, r in enumerate(c.res):
+            d.res[i] = int(r)
+        d.grid_dtype = c.grid_dtype
+        d.n_objects = self.n_obj
+        d.d_obj_aabb = self.obj_aabb.data_ptr()
+        d.d_grids = self.grids.data_ptr()
+        d.n_hidden = c.n_hidden
+        d.width = c.width
+        d.act = c.act
+        d.leaky_slope = c.leaky_slope
+        d.mlp_dtype = c.mlp_dtype
+        d.net_mode = c.net_mode
+        d.n_nets = self.n_nets
+        d.d_weights = self.weights.data_ptr()
+        d.d_scales = self.scales.data_ptr() if self.scales is not None else None
+        d.tile_m = c.tile_m
+        d.ctas_per_sm = c.ctas_per_sm
+        return d
+
+    @staticmethod
+    def grid_vertices(cfg: NifConfig) -> int:
+        d = L.ModelDesc()
+        d.n_levels = len(cfg.res)
+        d.n_features = cfg.n_features
+        d.log2_table = cfg.log2_table
+        for i, r in enumerate(cfg.res):
+            d.res[i] = int(r)
+        v = L.lib.nif_grid_vertices(ctypes.byref(d))
+        if v < 0:
+            raise L.NifError(L.NIF_ERR_ARG, "bad grid configuration")
+        return int(v)
+
+    @staticmethod
+    def weight_count(cfg: NifConfig) -> int:
+        d = L.ModelDesc()
+        d.n_levels = len(cfg.res)
+        d.n_features = cfg.n_features
+        d.n_hidden = cfg.n_hidden
+        d.width = cfg.width
+        return int(L.lib.nif_weight_count(ctypes.byref(d)))
+
+    def workspace(self, max_q: int) -> torch.Tensor:
+        d = self.desc()
+        need = L.lib.nif_workspace_size(ctypes.byref(d), 0, max_q)
+        if need == 0:
+            raise L.NifError(L.NIF_ERR_ARG, L.last_error())
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.zeros(need, dtype=torch.uint8, device=self.obj_aabb.device)
+        return self._ws
+
+    def check(self, ws: torch.Tensor | None = None, stream=None):
+        ws = ws if ws is not None else self._ws
+        det = ctypes.c_int64()
+        L.call("nif_check", _ptr(ws), ctypes.byref(det), _stream(stream))
+
+    def frontend(self, rays: torch.Tensor, tlas: BVH | None = None, max_q: int | None = None,
+                 stream=None):
+        n = int(rays.shape[0])
+        max_q = max_q if max_q is not None else 4 * n + 1024
+        dev = rays.device
+        ray_id = torch.empty(max_q, dtype=torch.int32, device=dev)
+        qobj = torch.empty(max_q, dtype=torch.int32, device=dev)
+        goff = torch.empty(self.n_nets + 1, dtype=torch.int64, device=dev)
+        count = torch.empty(1, dtype=torch.int64, device=dev)
+        ws = self.workspace(0)
+        d = self.desc()
+        L.call("nif_frontend", ctypes.byref(d), _ptr(tlas.buf) if tlas else None, _ptr(rays), n,
+               _ptr(ray_id), _ptr(qobj), max_q, _ptr(goff), _ptr(count), _ptr(ws), ws.numel(),
+               _stream(stream))
+        return ray_id, qobj, goff, count
+
+    def encode(self, rays, ray_id, qobj, nq: int, dtype=L.NIF_F32, stream=None):
+        out = torch.empty((nq, self.cfg.K), dtype=_DT[dtype], device=rays.device)
+        d = self.desc()
+        L.call("nif_encode", ctypes.byref(d), _ptr(rays), _ptr(ray_id), _ptr(qobj), nq, _ptr(out),
+               dtype, _stream(stream))
+        return out
+
+    def infer_queries(self, rays, ray_id, qobj, goff, nq_max: int, bits=None, logits=True,
+                      stream=None):
+        z = torch.empty(max(nq_max, 1), dtype=torch.float32, device=rays.device) if logits else None
+        ws = self.workspace(0)
+        d = self.desc()
+        L.call("nif_infer_queries", ctypes.byref(d), _ptr(rays), int(rays.shape[0]), _ptr(ray_id),
+               _ptr(qobj), _ptr(goff), nq_max, _ptr(bits), _ptr(z), _ptr(ws), ws.numel(),
+               _stream(stream))
+        return z
+
+    def infer(self, rays, bits, tlas: BVH | None = None, max_q: int | None = None, stream=None):
+        n = int(rays.shape[0])
+        ws = self.workspace(max_q if max_q is not None else 4 * n + 1024)
+        d = self.desc()
+        L.call("nif_infer", ctypes.byref(d), _ptr(tlas.buf) if tlas else None, _ptr(rays), n,
+               _ptr(bits), _ptr(ws), ws.numel(), _stream(stream))
+        return bits
+
+
+class Trainer:
+    """Adam state for a NifModel (Sec. 5 'Training'): FP32 masters, FP32
+    gradients and moments; nif_train_step refreshes the model's copies."""
+
+    def __init__(self, model: NifModel, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-15,
+                 loss_scale=1.0, w_master: torch.Tensor | None = None,
+                 g_master: torch.Tensor | None = None):
+        self.model = model
+        dev = model.obj_aabb.device
+        self.w_master = (w_master if w_master is not None else model.weights.float()).clone().contiguous()
+        self.g_master = (g_master if g_master is not None else model.grids.float()).clone().contiguous()
+        self.w_grad = torch.zeros_like(self.w_master)
+        self.w_m = torch.zeros_like(self.w_master)
+        self.w_v = torch.zeros_like(self.w_master)
+        self.g_grad = torch.zeros_like(self.g_master)
+        self.g_m = torch.zeros_like(self.g_master)
+        self.g_v = torch.zeros_like(self.g_master)
+        self.o = L.OptimDesc()
+        self.o.lr, self.o.beta1, self.o.beta2, self.o.eps = lr, beta1, beta2, eps
+        self.o.loss_scale = loss_scale
+        self.o.step = 0
+        for name in ("w_master", "w_grad", "w_m", "w_v", "g_master", "g_grad", "g_m", "g_v"):
+            setattr(self.o, "d_" + name, getattr(self, name).data_ptr())
+        self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        self._ws = None
+
+    def step(self, rays, ray_id, qobj, goff, label, nq: int, stream=None):
+        d = self.model.desc()
+        need = L.lib.nif_train_workspace_size(ctypes.byref(d), nq)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.zeros(need, dtype=torch.uint8, device=rays.device)
+        L.call("nif_train_step", ctypes.byref(d), ctypes.byref(self.o), _ptr(rays), _ptr(ray_id),
+               _ptr(qobj), _ptr(goff), _ptr(label), nq, _ptr(self.loss), _ptr(self._ws),
+               self._ws.numel(), _stream(stream))
+        return self.loss
+
+
+def _f32_view(model: NifModel, grids: torch.Tensor, weights: torch.Tensor) -> NifModel:
+    cfg = NifConfig(**{**model.cfg.__dict__, "grid_dtype": L.NIF_F32, "mlp_dtype": L.NIF_F32})
+    return NifModel(cfg, model.obj_aabb, grids, weights)
+
+
+class NifQueryFn(torch.autograd.Function):
+    """z = NIF(grids, weights; rays, queries): forward by nif_fwd_train, backward
+    by nif_mlp_bwd (weights) and nif_grid_bwd (grid latents), all FP32."""
+
+    @staticmethod
+    def forward(ctx, grids, weights, model, rays, ray_id, qobj, goff, nq):
+        m = _f32_view(model, grids, weights)
+        d = m.desc()
+        z = torch.empty(nq, dtype=torch.float32, device=rays.device)
+        saved = torch.empty(L.lib.nif_saved_size(ctypes.byref(d), nq) // 4, dtype=torch.float32,
+                            device=rays.device)
+        L.call("nif_fwd_train", ctypes.byref(d), _ptr(rays), _ptr(ray_id), _ptr(qobj), _ptr(goff), nq,
+               _ptr(z), _ptr(saved), _stream())
+        ctx.m = m
+        ctx.nq = nq
+        ctx.save_for_backward(rays, ray_id, qobj, goff, saved)
+        return z
+
+    @staticmethod
+    def backward(ctx, gz):
+        rays, ray_id, qobj, goff, saved = ctx.saved_tensors
+        m, nq = ctx.m, ctx.nq
+        d = m.desc()
+        gz = gz.contiguous().float()
+        gw = torch.zeros_like(m.weights)
+        gg = torch.zeros_like(m.grids)
+        dx = torch.empty(m.cfg.K * nq, dtype=torch.float32, device=rays.device)
+        L.call("nif_mlp_bwd", ctypes.byref(d), _ptr(qobj), _ptr(goff), nq, _ptr(saved), _ptr(gz),
+               _ptr(gw), _ptr(dx), _stream())
+        L.call("nif_grid_bwd", ctypes.byref(d), _ptr(rays), _ptr(ray_id), _ptr(qobj), nq, _ptr(dx),
+               _ptr(gg), _stream())
+        return gg, gw, None, None, None, None, None, None
+
+
+class NifLossFn(torch.autograd.Function):
+    """L = mean (sigmoid(z) - y)^2 (Sec. 5 'Training', L2 loss) by nif_loss."""
+
+    @staticmethod
+    def forward(ctx, z, label):
+        nq = int(z.shape[0])
+        dz = torch.empty_like(z)
+        loss = torch.zeros(1, dtype=torch.float32, device=z.device)
+        L.call("nif_loss", _ptr(z), _ptr(label), nq, 1.0, _ptr(dz), _ptr(loss), _stream())
+        ctx.save_for_backward(dz)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, g):
+        (dz,) = ctx.saved_tensors
+        return dz * g, None
+
+
+def adam_(master, grad, m1, m2, step: int, lr: float, beta1=0.9, beta2=0.999, eps=1e-15,
+          grad_scale=1.0, copy: torch.Tensor | None = None, copy_dtype: int = L.NIF_F32, stream=None):
+    L.call("nif_adam", _ptr(master), _ptr(grad), _ptr(m1), _ptr(m2), master.numel(), lr, beta1, beta2,
+           eps, grad_scale, step, _ptr(copy), copy_dtype, _stream(stream))

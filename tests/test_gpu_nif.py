@@ -1,0 +1,198 @@
+"""GPU NIF path (nif_frontend, nif_encode, nif_infer_queries, nif_infer)
+against the FP64 oracle: query sets bit-exact, encodings and logits within
+the stated tolerances (FP32 1e-4 abs, FP16 2e-2 abs, BF16 6e-2 abs)."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from oracle import nif as onif  # noqa: E402
+from paper_2306_07191_gb300 import _lib as L  # noqa: E402
+from paper_2306_07191_gb300 import nif, synth, workloads  # noqa: E402
+from helpers import oracle_model, pairs_key, random_boxes_scene, to_dtype_values  # noqa: E402
+
+DT = {"f32": L.NIF_F32, "f16": L.NIF_F16, "bf16": L.NIF_BF16}
+TORCH_DT = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}
+
+
+def _build(res, F, log2, aabb, grid_vals, mats_list, grid_dt="f32", mlp_dt="f32",
+           net_mode=L.NIF_NETS_SINGLE, act=L.NIF_ACT_RELU):
+    """GPU model and the matching oracle model from the same float32 inputs
+    (rounded to the GPU storage types)."""
+    n_hidden = len(mats_list[0]) - 1
+    width = mats_list[0][0].shape[0]
+    cfg = nif.NifConfig(res=list(res), n_features=F, log2_table=log2, grid_dtype=DT[grid_dt],
+                        n_hidden=n_hidden, width=width, act=act, mlp_dtype=DT[mlp_dt],
+                        net_mode=net_mode)
+    flat = np.concatenate([synth.flatten_mlp(m) for m in mats_list])
+    g = torch.from_numpy(np.ascontiguousarray(grid_vals, np.float32)).to(TORCH_DT[grid_dt]).cuda()
+    w = torch.from_numpy(flat).to(TORCH_DT[mlp_dt]).cuda()
+    model = nif.NifModel(cfg, torch.from_numpy(aabb).cuda(), g, w)
+    K = 3 * len(res) * F
+    nets64 = []
+    for m in mats_list:
+        f = to_dtype_values(synth.flatten_mlp(m), mlp_dt)
+        nets64.append(synth.unflatten_mlp(f, K, width, n_hidden))
+    om = oracle_model(onif, res, F, log2, aabb, to_dtype_values(grid_vals, grid_dt), nets64,
+                      net_mode={L.NIF_NETS_SINGLE: "single", L.NIF_NETS_CLASS: "class",
+                                L.NIF_NETS_OBJECT: "object"}[net_mode],
+                      act="relu" if act == L.NIF_ACT_RELU else "leaky")
+    return model, om
+
+
+def _gpu_queries(model, rays_t, tlas=None):
+    ray_id, qobj, goff, count = model.frontend(rays_t, tlas=tlas)
+    torch.cuda.synchronize()
+    nq = int(count.item())
+    return ray_id, qobj, goff, nq
+
+
+def _query_arrays(ray_id, qobj, nq):
+    r = ray_id[:nq].cpu().numpy().astype(np.int64)
+    q = qobj[:nq].cpu().numpy().view(np.uint32)
+    return r, (q & 0x7FFFFFFF).astype(np.int64), (q >> 31).astype(bool)
+
+
+@pytest.mark.parametrize("use_tlas", [False, True])
+def test_frontend_query_set_bit_exact(use_tlas):
+    rng = np.random.default_rng(21)
+    boxes = random_boxes_scene(rng, n_obj=9)
+    o = rng.uniform(-4, 4, size=(20000, 3))
+    d = synth.unit_vectors(rng, 20000)
+    rays = synth.pack_rays(o, d, 1e-3, np.inf)
+    rays[::4, 7] = rng.uniform(0.5, 3.0, size=len(rays[::4]))
+    rays[::7, 4:7] = [1.0, 0.0, 0.0]
+    for mode, nn in ((L.NIF_NETS_CLASS, 2), (L.NIF_NETS_OBJECT, 9), (L.NIF_NETS_SINGLE, 1)):
+        cfg = nif.NifConfig(res=[2], n_features=1, net_mode=mode)
+        model = nif.NifModel(cfg, torch.from_numpy(boxes).cuda(), torch.zeros(9 * 2 * 27).cuda(),
+                             torch.zeros(nn * nif.NifModel.weight_count(cfg)).cuda())
+        tlas = nif.BVH.from_boxes(torch.from_numpy(boxes).cuda()) if use_tlas else None
+        ray_id, qobj, goff, nq = _gpu_queries(model, torch.from_numpy(rays).cuda(), tlas)
+        r, ob, inn = _query_arrays(ray_id, qobj, nq)
+        rr, oo, ii = onif.queries(rays, boxes)
+        assert nq == len(rr)
+        got = sorted(zip(r.tolist(), ob.tolist(), inn.tolist()))
+        want = sorted(zip(rr.tolist(), oo.tolist(), ii.tolist()))
+        assert got == want
+        # grouping: group g holds exactly the pairs of network g, objects ascending
+        go = goff.cpu().numpy()
+        assert go[0] == 0 and go[-1] == nq and np.all(np.diff(go) >= 0)
+        for g in range(nn):
+            s, e = go[g], go[g + 1]
+            if mode == L.NIF_NETS_CLASS:
+                assert np.all(inn[s:e] == bool(g))
+            if mode == L.NIF_NETS_OBJECT:
+                assert np.all(ob[s:e] == g)
+            assert np.all(np.diff(ob[s:e]) >= 0)
+
+
+def _tiny(grid_scale=1.0, aimed=True, n_rays=4000):
+    w = workloads.tiny_object(n_rays=n_rays, aimed=aimed, grid_scale=grid_scale)
+    return w
+
+
+def test_encode_fp32_matches_oracle():
+    w = _tiny()
+    model, om = _build(w.res, 2, 19, w.aabb, w.grid_values, [w.weights])
+    rays_t = torch.from_numpy(w.rays).cuda()
+    ray_id, qobj, goff, nq = _gpu_queries(model, rays_t)
+    x = model.encode(rays_t, ray_id, qobj, nq).cpu().numpy()
+    r, ob, inn = _query_arrays(ray_id, qobj, nq)
+    xo = onif.encode(om, w.rays, r, ob)
+    assert nq > 3000
+    np.testing.assert_allclose(x, xo, atol=2e-5, rtol=0)
+    x16 = model.encode(rays_t, ray_id, qobj, nq, dtype=L.NIF_F16).float().cpu().numpy()
+    np.testing.assert_allclose(x16, xo, atol=2e-3, rtol=0)
+
+
+@pytest.mark.parametrize("mlp_dt,grid_dt,tol", [("f32", "f32", 1e-4), ("f16", "f32", 2e-2),
+                                                 ("f16", "f16", 2e-2), ("bf16", "f32", 6e-2)])
+def test_logits_match_oracle(mlp_dt, grid_dt, tol):
+    w = _tiny(n_rays=6000)
+    model, om = _build(w.res, 2, 19, w.aabb, w.grid_values, [w.weights], grid_dt=grid_dt, mlp_dt=mlp_dt)
+    rays_t = torch.from_numpy(w.rays).cuda()
+    ray_id, qobj, goff, nq = _gpu_queries(model, rays_t)
+    bits = nif.empty_bits(len(w.rays))
+    z = model.infer_queries(rays_t, ray_id, qobj, goff, nq, bits=bits)
+    model.check()
+    torch.cuda.synchronize()
+    r, ob, inn = _query_arrays(ray_id, qobj, nq)
+    zo = onif.forward(om, w.rays, r, ob, inn)
+    zg = z[:nq].cpu().numpy()
+    err = np.abs(zg - zo)
+    assert nq > 4000 and nq % 128 != 0  # several tiles and a ragged tail
+    assert np.abs(zo).max() > 0.05      # logits are not trivially small
+    assert err.max() <= tol, (err.max(), np.abs(zo).max())
+    occ = nif.bits_to_bool(bits, len(w.rays)).cpu().numpy()
+    want = onif.ray_occlusion(len(w.rays), r, zg)
+    assert np.array_equal(occ, want)
+    # decisions agree with the oracle wherever the oracle logit is not within tol of 0
+    firm = np.abs(zo) > tol
+    assert np.array_equal(zg[firm] < 0, zo[firm] < 0)
+
+
+@pytest.mark.parametrize("mlp_dt,tol", [("f32", 1e-4), ("f16", 2e-2)])
+def test_class_networks_hashed_grids_multi_object(mlp_dt, tol):
+    """Two networks (outer / inner), several objects, hashed fine levels."""
+    rng = np.random.default_rng(31)
+    boxes = random_boxes_scene(rng, n_obj=5)
+    res = [3, 6, 12, 40]
+    log2 = 11
+    sizes, hashed, off = onif.level_layout(res, log2)
+    assert hashed == [False, False, True, True]
+    V = int(off[-1])
+    grid = rng.uniform(-1, 1, size=(5, 2, V * 2)).astype(np.float32)
+    mats = [synth.mlp_init(rng, 24, 64, 2), synth.mlp_init(rng, 24, 64, 2)]
+    model, om = _build(res, 2, log2, boxes, grid, mats, grid_dt="f16", mlp_dt=mlp_dt,
+                       net_mode=L.NIF_NETS_CLASS)
+    o = rng.uniform(-4, 4, size=(6000, 3))
+    rays = synth.pack_rays(o, synth.unit_vectors(rng, 6000), 1e-3, np.inf)
+    rays_t = torch.from_numpy(rays).cuda()
+    ray_id, qobj, goff, nq = _gpu_queries(model, rays_t)
+    z = model.infer_queries(rays_t, ray_id, qobj, goff, nq)
+    model.check()
+    r, ob, inn = _query_arrays(ray_id, qobj, nq)
+    assert inn.any() and (~inn).any()
+    zo = onif.forward(om, rays, r, ob, inn)
+    err = np.abs(z[:nq].cpu().numpy() - zo)
+    assert err.max() <= tol, err.max()
+
+
+@pytest.mark.parametrize("mlp_dt", ["f32", "f16"])
+def test_infer_end_to_end_equals_queries_path(mlp_dt):
+    w = _tiny(n_rays=5000, aimed=False)
+    model, om = _build(w.res, 2, 19, w.aabb, w.grid_values, [w.weights], mlp_dt=mlp_dt)
+    rays_t = torch.from_numpy(w.rays).cuda()
+    bits = nif.empty_bits(len(w.rays))
+    model.infer(rays_t, bits)
+    model.check()
+    occ = nif.bits_to_bool(bits, len(w.rays)).cpu().numpy()
+    rr, oo, ii = onif.queries(w.rays, w.aabb)
+    zo = onif.forward(om, w.rays, rr, oo, ii)
+    want = onif.ray_occlusion(len(w.rays), rr, zo)
+    tol = 1e-4 if mlp_dt == "f32" else 2e-2
+    firm = np.ones(len(w.rays), bool)
+    firm[rr[np.abs(zo) <= tol]] = False
+    assert np.array_equal(occ[firm], want[firm])
+    # no ray without a query is ever occluded
+    noq = np.ones(len(w.rays), bool)
+    noq[rr] = False
+    assert not occ[noq].any()
+
+
+def test_zero_rays_and_zero_queries():
+    w = _tiny(n_rays=64)
+    model, _ = _build(w.res, 2, 19, w.aabb, w.grid_values, [w.weights], mlp_dt="f16")
+    empty = torch.zeros((0, 8), dtype=torch.float32, device="cuda")
+    bits = nif.empty_bits(0)
+    model.infer(empty, bits)
+    # rays that miss the box entirely: no queries, nothing occluded
+    far = synth.pack_rays(np.full((100, 3), 10.0), np.tile([[1.0, 0, 0]], (100, 1)), 0.0, np.inf)
+    bits = nif.empty_bits(100)
+    model.infer(torch.from_numpy(far).cuda(), bits)
+    model.check()
+    assert not nif.bits_to_bool(bits, 100).any()
