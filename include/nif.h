@@ -305,6 +305,14 @@ nif_status nif_train_step(nif_model_desc* m, nif_optim_desc* o, const nif_ray* d
                           const int64_t* d_group_off, const uint8_t* d_label, int64_t nq,
                           float* d_loss, void* d_ws, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------------ inputs --
+ * Seeded uniform fill for large parameter tables such as the grid latents'
+ * U(-1e-4, 1e-4) initialisation (Sec. 5 "Initialization"): d_out[i] =
+ * scale * (2u - 1), u = (SplitMix64(seed + (i+1) * 0x9E3779B97F4A7C15) >> 40)
+ * / 2^24 (Steele, Lea & Flood 2014), the product rounded once in FP32.  A
+ * counter-based generator, so any entry can be reproduced independently. */
+nif_status nif_fill_uniform(float* d_out, int64_t n, uint64_t seed, float scale, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

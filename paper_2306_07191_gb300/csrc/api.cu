@@ -426,3 +426,33 @@ nif_status nif_train_step(nif_model_desc* m, nif_optim_desc* o, const nif_ray* d
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ input fill
+// Seeded uniform values for large parameter tables (an input generator, not
+// part of the method): value(i) = scale * (2u - 1) with u the top 24 bits of
+// SplitMix64 (Steele, Lea & Flood 2014) applied to seed + (i + 1) * golden.
+namespace nif {
+__global__ void k_fill_uniform(float* out, int64_t n, uint64_t seed, float scale) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed + static_cast<uint64_t>(i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    float u = static_cast<float>(z >> 40) * (1.0f / 16777216.0f);
+    float s = 2.0f * u - 1.0f;
+    out[i] = __fmul_rn(s, scale);
+  }
+}
+}  // namespace nif
+
+extern "C" nif_status nif_fill_uniform(float* d_out, int64_t n, uint64_t seed, float scale,
+                                       void* stream) {
+  NIF_CHECK_ARG(n >= 0, "nif_fill_uniform: negative n");
+  if (n == 0) return NIF_OK;
+  NIF_CHECK_ARG(d_out != nullptr, "nif_fill_uniform: null output");
+  int blocks = static_cast<int>(std::min<int64_t>(ceil_div(n, 256), sm_count() * 16));
+  k_fill_uniform<<<blocks, 256, 0, as_stream(stream)>>>(d_out, n, seed, scale);
+  NIF_LAUNCH_CHECK();
+  return NIF_OK;
+}

@@ -344,3 +344,44 @@ def unflatten_mlp(flat: np.ndarray, n_in: int, width: int, n_hidden: int) -> lis
 
 def mlp_param_count(n_in: int, width: int, n_hidden: int) -> int:
     return n_in * width + (n_hidden - 1) * width * width + width if n_hidden > 0 else n_in
+
+
+def splitmix_uniform(index: np.ndarray, seed: int, scale: float) -> np.ndarray:
+    """Counter-based U(-scale, scale) values of table entries `index`:
+    scale * (2u - 1) with u the top 24 bits of SplitMix64 (Steele, Lea & Flood
+    2014) of seed + (i + 1) * 0x9E3779B97F4A7C15, rounded once to float32.
+    The device fill (nif_fill_uniform) draws the same values."""
+    i = np.asarray(index, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed) + (i + np.uint64(1)) * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    u = (z >> np.uint64(40)).astype(np.float32) * np.float32(1.0 / 16777216.0)
+    s = np.float32(2.0) * u - np.float32(1.0)
+    return (s * np.float32(scale)).astype(np.float32)
+
+
+class SplitMixTable:
+    """Read-only view of a table whose entry e is splitmix_uniform(base + e):
+    indexing with an integer array returns float64 values on demand, so a
+    1.5G-entry grid initialisation never has to exist on the host."""
+
+    def __init__(self, base: int, seed: int, scale: float):
+        self.base, self.seed, self.scale = int(base), int(seed), float(scale)
+
+    def __getitem__(self, idx):
+        return splitmix_uniform(np.asarray(idx, dtype=np.int64) + self.base, self.seed,
+                                self.scale).astype(np.float64)
+
+
+class SplitMixGrids:
+    """grids[k, g] -> SplitMixTable of object k's grid g in a [n_obj][2][V*F]
+    table filled by nif_fill_uniform(seed, scale)."""
+
+    def __init__(self, grid_elems: int, seed: int, scale: float):
+        self.n, self.seed, self.scale = int(grid_elems), int(seed), float(scale)
+
+    def __getitem__(self, kg):
+        k, g = kg
+        return SplitMixTable((int(k) * 2 + int(g)) * self.n, self.seed, self.scale)
