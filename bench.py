@@ -155,7 +155,7 @@ def oracle_rays_per_s(n_rays: int, seed: int = 5):
     return n_rays / dt, dt, len(rid)
 
 
-def cpu_baseline(n_rays: int = 20000):
+def cpu_baseline(n_rays: int = 150000):
     """Run the oracle timing in a child process limited to one BLAS thread."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = ("import json,sys; sys.path.insert(0, %r); import bench; "
@@ -176,7 +176,7 @@ def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    n = 4000
+    n = 20000
     times = []
     for s in range(args.warmup + args.steps):
         v, dt, nq = oracle_rays_per_s(n, seed=100 + s)
@@ -213,11 +213,15 @@ def run_ours(args):
     cfg = RoomConfig()
     if args.small:
         cfg = RoomConfig(n_obj=16, width=640, height=360, train_steps=8, batch=65536, train_spp=1)
+    if args.ctas_per_sm:
+        cfg.ctas_per_sm = args.ctas_per_sm
     pipe = RoomPipeline(cfg, log=log)
     train_s = pipe.train()
     dis = pipe.disagreement()
     abl = pipe.ablations()
     log(f"disagreement {dis}  ablations {abl}")
+    pipe.release_training_state()
+    torch.cuda.empty_cache()
     n = pipe.n_rays
     rays = pipe.rays
     model = pipe.model
@@ -283,8 +287,10 @@ def run_ours(args):
         return tot, subs
 
     with ClockSampler(local) as clk:
+        torch.cuda.profiler.start()
         nif_ms, subs = timed(nif_step, args.steps, args.warmup, sub=True)
         bvh_ms, _ = timed(lambda: pipe.bvh.cast_shadow(rays, out=bits), args.steps, args.warmup)
+        torch.cuda.profiler.stop()
     clocks = clk.summary()
     nq = int(count.item())
     model.check(ws)
@@ -358,6 +364,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--small", action="store_true", help="reduced workload for quick checks")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ctas-per-sm", type=int, default=0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -130,6 +130,117 @@ __device__ __forceinline__ void level_taps(const NifParams& p, int l, const floa
   }
 }
 
+// Cell corner (x0, y0, z0) and fractions of a point at level l (the same
+// arithmetic as level_taps, split so that callers can issue the loads of
+// several lookups before computing any weight).
+__device__ __forceinline__ void level_cell(const NifParams& p, int l, float ux, float uy, float uz,
+                                           uint32_t c0[3], float f[3]) {
+  const int R = p.res[l];
+  const float u[3] = {ux, uy, uz};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    float s = u[k] * static_cast<float>(R);
+    int c = static_cast<int>(floorf(s));
+    c = c < 0 ? 0 : (c > R - 1 ? R - 1 : c);
+    c0[k] = static_cast<uint32_t>(c);
+    f[k] = s - static_cast<float>(c);
+  }
+}
+
+__device__ __forceinline__ uint32_t corner_entry(const NifParams& p, int l, const uint32_t c0[3],
+                                                 int c) {
+  const uint32_t x = c0[0] + (c & 1), y = c0[1] + ((c >> 1) & 1), z = c0[2] + ((c >> 2) & 1);
+  const bool hashed = (p.hashed >> l) & 1u;
+  const uint32_t n1 = static_cast<uint32_t>(p.res[l] + 1);
+  const uint32_t v = hashed ? (((x * kHashP1) ^ (y * kHashP2) ^ (z * kHashP3)) & ((1u << p.log2T) - 1u))
+                            : (x + n1 * (y + n1 * z));
+  return p.off[l] + v;
+}
+
+// The 8 stored-entry indices of the cell with lower corner c0 at level l,
+// corner c = cx + 2 cy + 4 cz: dense levels add fixed offsets to one base
+// index, hashed levels combine 2+2+2 partial products with XOR.
+struct LevelInfo {
+  uint32_t off, n1, mask;
+  bool hashed;
+  float R;
+  int Ri;
+};
+
+__device__ __forceinline__ LevelInfo level_info(const NifParams& p, int l) {
+  LevelInfo li;
+  li.Ri = p.res[l];
+  li.R = static_cast<float>(li.Ri);
+  li.off = p.off[l];
+  li.n1 = static_cast<uint32_t>(li.Ri + 1);
+  li.hashed = (p.hashed >> l) & 1u;
+  li.mask = (1u << p.log2T) - 1u;
+  return li;
+}
+
+__device__ __forceinline__ void cell_of(const LevelInfo& li, float ux, float uy, float uz,
+                                        uint32_t c0[3], float f[3]) {
+  const float u[3] = {ux, uy, uz};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float s = u[k] * li.R;
+    int c = static_cast<int>(floorf(s));
+    c = c < 0 ? 0 : (c > li.Ri - 1 ? li.Ri - 1 : c);
+    c0[k] = static_cast<uint32_t>(c);
+    f[k] = s - static_cast<float>(c);
+  }
+}
+
+__device__ __forceinline__ void cell_entries(const LevelInfo& li, const uint32_t c0[3],
+                                             uint32_t idx[8]) {
+  if (li.hashed) {
+    const uint32_t hx0 = c0[0] * kHashP1, hx1 = hx0 + kHashP1;
+    const uint32_t hy0 = c0[1] * kHashP2, hy1 = hy0 + kHashP2;
+    const uint32_t hz0 = c0[2] * kHashP3, hz1 = hz0 + kHashP3;
+    const uint32_t a00 = hx0 ^ hy0, a10 = hx1 ^ hy0, a01 = hx0 ^ hy1, a11 = hx1 ^ hy1;
+    idx[0] = li.off + ((a00 ^ hz0) & li.mask);
+    idx[1] = li.off + ((a10 ^ hz0) & li.mask);
+    idx[2] = li.off + ((a01 ^ hz0) & li.mask);
+    idx[3] = li.off + ((a11 ^ hz0) & li.mask);
+    idx[4] = li.off + ((a00 ^ hz1) & li.mask);
+    idx[5] = li.off + ((a10 ^ hz1) & li.mask);
+    idx[6] = li.off + ((a01 ^ hz1) & li.mask);
+    idx[7] = li.off + ((a11 ^ hz1) & li.mask);
+  } else {
+    const uint32_t n2 = li.n1 * li.n1;
+    const uint32_t b = li.off + c0[0] + li.n1 * (c0[1] + li.n1 * c0[2]);
+    idx[0] = b;
+    idx[1] = b + 1;
+    idx[2] = b + li.n1;
+    idx[3] = b + li.n1 + 1;
+    idx[4] = b + n2;
+    idx[5] = b + n2 + 1;
+    idx[6] = b + n2 + li.n1;
+    idx[7] = b + n2 + li.n1 + 1;
+  }
+}
+
+// The 8 trilinear weights, corner c = cx + 2 cy + 4 cz.
+__device__ __forceinline__ void cell_weights(const float f[3], float w[8]) {
+  const float x0 = 1.f - f[0], y0 = 1.f - f[1], z0 = 1.f - f[2];
+  const float a00 = x0 * y0, a10 = f[0] * y0, a01 = x0 * f[1], a11 = f[0] * f[1];
+  w[0] = a00 * z0;
+  w[1] = a10 * z0;
+  w[2] = a01 * z0;
+  w[3] = a11 * z0;
+  w[4] = a00 * f[2];
+  w[5] = a10 * f[2];
+  w[6] = a01 * f[2];
+  w[7] = a11 * f[2];
+}
+
+__device__ __forceinline__ float corner_weight(const float f[3], int c) {
+  const float wx = (c & 1) ? f[0] : 1.f - f[0];
+  const float wy = ((c >> 1) & 1) ? f[1] : 1.f - f[1];
+  const float wz = ((c >> 2) & 1) ? f[2] : 1.f - f[2];
+  return wx * wy * wz;
+}
+
 __device__ __forceinline__ const void* grid_ptr(const NifParams& p, uint32_t obj, int which) {
   size_t esz = p.grid_dtype == NIF_F16 ? 2 : 4;
   return static_cast<const char*>(p.grids) +

@@ -25,6 +25,7 @@
 #include <cuda_fp8.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "nif_params.cuh"
 #include "nif_kernels.cuh"
@@ -186,19 +187,20 @@ __device__ __forceinline__ void store_elem(uint8_t* tile, int row, int k, int kd
 }
 
 struct Layout {
-  uint32_t a_off, w_off[8], wout_off, zpart_off, total;
+  uint32_t a_off, w0_off, w1_bytes, wl_bytes, wout_off, zpart_off, total;
+  // B operand of hidden layer l (every size below is a multiple of 128 bytes)
+  __host__ __device__ uint32_t w_off(int l) const {
+    return l == 0 ? w0_off : w0_off + w1_bytes + static_cast<uint32_t>(l - 1) * wl_bytes;
+  }
 };
 
 __host__ __device__ inline Layout make_layout(int Kp, int W, int H, int esz) {
   Layout L{};
-  uint32_t o = 0;
-  L.a_off = o;
-  o += kM * (Kp > W ? Kp : W) * esz;
-  for (int l = 0; l < H; ++l) {
-    o = (o + 127) / 128 * 128;
-    L.w_off[l] = o;
-    o += W * (l == 0 ? Kp : W) * esz;
-  }
+  L.a_off = 0;
+  L.w0_off = kM * (Kp > W ? Kp : W) * esz;
+  L.w1_bytes = W * Kp * esz;
+  L.wl_bytes = W * W * esz;
+  uint32_t o = L.w0_off + L.w1_bytes + static_cast<uint32_t>(H > 1 ? H - 1 : 0) * L.wl_bytes;
   o = (o + 15) / 16 * 16;
   L.wout_off = o;
   o += W * 4;
@@ -208,9 +210,9 @@ __host__ __device__ inline Layout make_layout(int Kp, int W, int H, int esz) {
   return L;
 }
 
-template <int F, typename TG, int DT>
-__global__ void __launch_bounds__(kThreads, 2)
-    k_fused(NifParams p, const nif_ray* __restrict__ rays, const uint32_t* __restrict__ ray_id,
+template <int F, typename TG, int DT, int kOcc>
+__global__ void __launch_bounds__(kThreads, kOcc)
+    k_fused(const __grid_constant__ NifParams p, const nif_ray* __restrict__ rays, const uint32_t* __restrict__ ray_id,
             const uint32_t* __restrict__ qobj, const int64_t* __restrict__ goff,
             uint32_t* __restrict__ occ, float* __restrict__ logits, DevError* err, int Kp) {
   using O = Op<DT>;
@@ -265,7 +267,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       for (int l = 0; l < H; ++l) {
         const int fin = l == 0 ? K : W;
         const int fpad = l == 0 ? Kp : W;
-        uint8_t* wt = smem + L.w_off[l];
+        uint8_t* wt = smem + L.w_off(l);
         for (int e = tid; e < W * fpad; e += kThreads) {
           const int n = e / fpad, k = e % fpad;
           const float v = k < fin ? O::load(p.weights, wbase + off + static_cast<int64_t>(n) * fin + k) : 0.f;
@@ -297,19 +299,63 @@ __global__ void __launch_bounds__(kThreads, 2)
         query_points(r, bx, pts);
         const TG* tpos = static_cast<const TG*>(grid_ptr(p, obj, 0));
         const TG* tdir = static_cast<const TG*>(grid_ptr(p, obj, 1));
-        for (int m = half; m < 3 * p.L; m += 2) {
-          const int j = m / p.L, l = m - j * p.L;
-          Taps tp;
-          level_taps(p, l, pts.u[j], tp);
-          float v[F];
-          gather_level<F, TG>(j < 2 ? tpos : tdir, tp, v);
-          const int k0 = m * F;
-          if constexpr (F == 2 && esz == 2) {
-            typename O::T a = O::cvt(v[0] * s_in), b = O::cvt(v[1] * s_in);
-            uint32_t packed = static_cast<uint32_t>(*reinterpret_cast<uint16_t*>(&a)) |
-                              (static_cast<uint32_t>(*reinterpret_cast<uint16_t*>(&b)) << 16);
-            *reinterpret_cast<uint32_t*>(tileA + tile_off(qi, k0, Kp, esz)) = packed;
-          } else {
+        if constexpr (F == 2) {
+          // Thread `half` takes levels l = half, half+2, ...; per level the
+          // entry, exit and direction lookups share the level constants and
+          // all 24 gathers are issued before any is consumed.
+          using Raw = typename std::conditional<sizeof(TG) == 2, __half2, float2>::type;
+          const Raw* tp = reinterpret_cast<const Raw*>(tpos);
+          const Raw* td = reinterpret_cast<const Raw*>(tdir);
+          for (int l = half; l < p.L; l += 2) {
+            const LevelInfo li = level_info(p, l);
+            uint32_t idx[3][8];
+            float fr[3][3];
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+              uint32_t c0[3];
+              cell_of(li, pts.u[j][0], pts.u[j][1], pts.u[j][2], c0, fr[j]);
+              cell_entries(li, c0, idx[j]);
+            }
+            Raw v[3][8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) v[0][c] = __ldg(tp + idx[0][c]);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) v[1][c] = __ldg(tp + idx[1][c]);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) v[2][c] = __ldg(td + idx[2][c]);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+              float w[8];
+              cell_weights(fr[j], w);
+              float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+              for (int c = 0; c < 8; ++c) {
+                float2 fv;
+                if constexpr (sizeof(TG) == 2) fv = __half22float2(v[j][c]);
+                else fv = v[j][c];
+                a0 += w[c] * fv.x;
+                a1 += w[c] * fv.y;
+              }
+              const int k0 = (j * p.L + l) * 2;
+              if constexpr (esz == 2) {
+                typename O::T a = O::cvt(a0 * s_in), b = O::cvt(a1 * s_in);
+                uint32_t packed = static_cast<uint32_t>(*reinterpret_cast<uint16_t*>(&a)) |
+                                  (static_cast<uint32_t>(*reinterpret_cast<uint16_t*>(&b)) << 16);
+                *reinterpret_cast<uint32_t*>(tileA + tile_off(qi, k0, Kp, esz)) = packed;
+              } else {
+                store_elem<DT>(tileA, qi, k0, Kp, a0 * s_in);
+                store_elem<DT>(tileA, qi, k0 + 1, Kp, a1 * s_in);
+              }
+            }
+          }
+        } else {
+          for (int m = half; m < 3 * p.L; m += 2) {
+            const int j = m / p.L, l = m - j * p.L;
+            Taps tp;
+            level_taps(p, l, pts.u[j], tp);
+            float v[F];
+            gather_level<F, TG>(j < 2 ? tpos : tdir, tp, v);
+            const int k0 = m * F;
 #pragma unroll
             for (int f = 0; f < F; ++f) store_elem<DT>(tileA, qi, k0 + f, Kp, v[f] * s_in);
           }
@@ -329,7 +375,7 @@ __global__ void __launch_bounds__(kThreads, 2)
       const int kdim = l == 0 ? Kp : W;
       if (tid == 0) {
         tc_fence_after();
-        const uint32_t a0 = smem_u32(tileA), b0 = smem_u32(smem + L.w_off[l]);
+        const uint32_t a0 = smem_u32(tileA), b0 = smem_u32(smem + L.w_off(l));
         const uint32_t sbo = (kdim / (16 / esz)) * 128;
         for (int kk = 0; kk < kdim / kstep; ++kk) {
           const uint64_t ad = smem_desc(a0 + kk * 256, 128, sbo);
@@ -442,14 +488,26 @@ nif_status check_tc_shape(const NifParams& p) {
 
 template <int DT>
 static nif_status launch_dt(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
-                            const uint32_t* qobj, const int64_t* goff, int blocks, uint32_t* occ,
-                            float* logits, DevError* err, cudaStream_t st) {
+                            const uint32_t* qobj, const int64_t* goff, int blocks, bool occ3,
+                            uint32_t* occ, float* logits, DevError* err, cudaStream_t st) {
   const int esz = DT == NIF_E4M3 ? 1 : 2;
   const int Kp = (p.K + 32 / esz - 1) / (32 / esz) * (32 / esz);
   tc::Layout L = tc::make_layout(Kp, p.width, p.n_hidden, esz);
   size_t sh = L.total + 1024;
+  if (occ3 && p.F == 2) {
+    auto launch3 = [&](auto kern) -> nif_status {
+      NIF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+      kern<<<blocks, tc::kThreads, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, err, Kp);
+      return NIF_OK;
+    };
+    nif_status s = p.grid_dtype == NIF_F16 ? launch3(tc::k_fused<2, __half, DT, 3>)
+                                           : launch3(tc::k_fused<2, float, DT, 3>);
+    if (s != NIF_OK) return s;
+    NIF_LAUNCH_CHECK();
+    return NIF_OK;
+  }
   NIF_DISPATCH_FG_TC(p, {
-    auto kern = tc::k_fused<F, TG, DT>;
+    auto kern = tc::k_fused<F, TG, DT, 2>;
     NIF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
     kern<<<blocks, tc::kThreads, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, err, Kp);
   });
@@ -469,9 +527,10 @@ nif_status launch_fwd_tc(const NifParams& p, const nif_ray* rays, const uint32_t
   int blocks = sm_count() * per_sm;
   if (nq_hint >= 0)
     blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(blocks, ceil_div(nq_hint, tc::kM) + p.n_nets)));
-  if (p.mlp_dtype == NIF_F16) return launch_dt<NIF_F16>(p, rays, ray_id, qobj, goff, blocks, occ, logits, err, st);
-  if (p.mlp_dtype == NIF_BF16) return launch_dt<NIF_BF16>(p, rays, ray_id, qobj, goff, blocks, occ, logits, err, st);
-  if (p.mlp_dtype == NIF_E4M3) return launch_dt<NIF_E4M3>(p, rays, ray_id, qobj, goff, blocks, occ, logits, err, st);
+  const bool occ3 = per_sm >= 3;
+  if (p.mlp_dtype == NIF_F16) return launch_dt<NIF_F16>(p, rays, ray_id, qobj, goff, blocks, occ3, occ, logits, err, st);
+  if (p.mlp_dtype == NIF_BF16) return launch_dt<NIF_BF16>(p, rays, ray_id, qobj, goff, blocks, occ3, occ, logits, err, st);
+  if (p.mlp_dtype == NIF_E4M3) return launch_dt<NIF_E4M3>(p, rays, ray_id, qobj, goff, blocks, occ3, occ, logits, err, st);
   return fail(NIF_ERR_UNSUPPORTED, "tensor-core path: mlp dtype %d", p.mlp_dtype);
 }
 

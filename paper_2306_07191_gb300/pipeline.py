@@ -39,6 +39,7 @@ class RoomConfig:
     batch: int = 262144
     lr: float = 1e-2
     tmin: float = 1e-3
+    ctas_per_sm: int = 0
 
 
 class RoomPipeline:
@@ -70,7 +71,8 @@ class RoomPipeline:
         c = cfg
         ncfg = nif.NifConfig(res=list(c.res), n_features=c.n_features, log2_table=c.log2_table,
                              grid_dtype=c.grid_dtype, n_hidden=c.n_hidden, width=c.width_mlp,
-                             mlp_dtype=c.mlp_dtype, net_mode=L.NIF_NETS_CLASS)
+                             mlp_dtype=c.mlp_dtype, net_mode=L.NIF_NETS_CLASS,
+                             ctas_per_sm=c.ctas_per_sm)
         self.V = nif.NifModel.grid_vertices(ncfg)
         self.P = nif.NifModel.weight_count(ncfg)
         n_grid = c.n_obj * 2 * self.V * c.n_features
@@ -152,6 +154,15 @@ class RoomPipeline:
         self.log(f"trained {steps} steps of {B} pairs from a pool of {npool} in {dt:.2f}s; "
                  f"loss {self.losses[0]:.4f} -> {self.losses[-1]:.4f}")
         return dt
+
+    def release_training_state(self):
+        """Drop FP32 masters, Adam moments and the initial copies once
+        training and the ablations are done (inference keeps the FP16 copies)."""
+        self.trainer = None
+        self.g_master = None
+        self.w_master = None
+        self.init_grids = None
+        self.init_weights = None
 
     # ------------------------------------------------------------ queries
     def nif_query(self, bits: torch.Tensor, rays: torch.Tensor | None = None, stream=None):

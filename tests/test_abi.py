@@ -1,0 +1,119 @@
+"""The C ABI without a GPU: libnif.so loads, exports every function that
+include/nif.h declares, its structs have the layout a C compiler gives them,
+and host-side argument checks return their status codes."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "nif.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2306_07191_gb300 import build
+    build.build()
+    from paper_2306_07191_gb300 import _lib
+    return _lib
+
+
+def _declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+char\s*\*|nif_status|size_t|int64_t|int32_t)\s+(\w+)\s*\(",
+                       src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_every_declared_function_is_exported_and_bound(L):
+    names = _declared_functions()
+    assert len(names) >= 25
+    for n in names:
+        assert hasattr(L.lib, n), n
+        assert n in L.SIGNATURES, n
+
+
+def test_struct_layout_matches_the_c_compiler(L):
+    fields_m = [f[0] for f in L.ModelDesc._fields_]
+    fields_o = [f[0] for f in L.OptimDesc._fields_]
+    prog = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void){",
+            'printf("%zu %zu %zu\\n", sizeof(nif_ray), sizeof(nif_model_desc), sizeof(nif_optim_desc));']
+    for f in fields_m:
+        prog.append(f'printf("m {f} %zu\\n", offsetof(nif_model_desc, {f}));')
+    for f in fields_o:
+        prog.append(f'printf("o {f} %zu\\n", offsetof(nif_optim_desc, {f}));')
+    prog.append("return 0;}")
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "probe.c")
+        exe = os.path.join(d, "probe")
+        open(c, "w").write("\n".join(prog))
+        subprocess.check_call(["gcc", "-std=c11", c, "-o", exe])
+        out = subprocess.check_output([exe], text=True).split("\n")
+    sizes = [int(x) for x in out[0].split()]
+    assert sizes == [32, ctypes.sizeof(L.ModelDesc), ctypes.sizeof(L.OptimDesc)]
+    for line in out[1:]:
+        if not line:
+            continue
+        kind, name, off = line.split()
+        S = L.ModelDesc if kind == "m" else L.OptimDesc
+        assert getattr(S, name).offset == int(off), name
+
+
+def test_host_side_argument_errors(L):
+    d = L.ModelDesc()
+    assert L.lib.nif_encode(ctypes.byref(d), None, None, None, 0, None, 0, None) == L.NIF_ERR_ARG
+    assert "n_features" in L.last_error()
+    assert L.lib.bvh_build(None, 0, None, -1, None, None, 0, None, 0, None) == L.NIF_ERR_ARG
+    assert L.lib.bvh_cast_shadow(None, None, -5, None, None) == L.NIF_ERR_ARG
+    assert L.lib.bvh_cast_shadow(None, None, 0, None, None) == L.NIF_OK  # n == 0 queues nothing
+    assert L.lib.nif_adam(None, None, None, None, 10, 1e-2, 0.9, 0.999, 1e-15, 1.0, 0, None, 0, None) == L.NIF_ERR_ARG
+    assert L.lib.nif_loss(None, None, 5, 1.0, None, None, None) == L.NIF_ERR_ARG
+    assert L.lib.nif_fill_uniform(None, -1, 0, 1.0, None) == L.NIF_ERR_ARG
+
+
+def _room_desc(L, **kw):
+    from paper_2306_07191_gb300 import workloads
+    d = L.ModelDesc()
+    d.n_levels = 16
+    d.n_features = 2
+    d.log2_table = 19
+    for i, r in enumerate(workloads.ROOM_RES):
+        d.res[i] = r
+    d.grid_dtype = L.NIF_F16
+    d.n_objects = 64
+    d.d_obj_aabb = d.d_grids = d.d_weights = 256  # never dereferenced on the host
+    d.n_hidden, d.width, d.act = 3, 64, L.NIF_ACT_RELU
+    d.mlp_dtype = L.NIF_F16
+    d.net_mode, d.n_nets = L.NIF_NETS_CLASS, 2
+    for k, v in kw.items():
+        setattr(d, k, v)
+    return d
+
+
+def test_sizes_agree_with_the_oracle_layout(L):
+    from oracle import nif as onif
+    from paper_2306_07191_gb300 import workloads
+    d = _room_desc(L)
+    sizes, hashed, off = onif.level_layout(workloads.ROOM_RES, 19)
+    assert L.lib.nif_grid_vertices(ctypes.byref(d)) == int(off[-1]) == 5723320
+    assert sum(hashed) == 10
+    assert L.lib.nif_weight_count(ctypes.byref(d)) == 96 * 64 + 2 * 64 * 64 + 64
+    assert L.lib.nif_workspace_size(ctypes.byref(d), 1000, 5000) > 2 * 5000 * 4
+    assert L.lib.nif_train_workspace_size(ctypes.byref(d), 1000) >= (96 + 3 * 64 + 96 + 2) * 1000 * 4
+    bad = _room_desc(L, n_nets=3)
+    assert L.lib.nif_workspace_size(ctypes.byref(bad), 1, 1) == 0
+    assert L.lib.bvh_build_size(0) > 0 and L.lib.bvh_build_size(1000) >= 1000 * 48
+
+
+def test_splitmix_generator_matches_hand_values():
+    """SplitMix64 (Steele, Lea & Flood 2014) first output for state 0 after one
+    increment is 0xE220A8397B1DCDAF; top 24 bits -> u -> 2u - 1."""
+    from paper_2306_07191_gb300 import synth
+    v = synth.splitmix_uniform(np.array([0]), 0, 1.0)[0]
+    top = 0xE220A8397B1DCDAF >> 40
+    assert v == np.float32(2.0 * top / 2 ** 24 - 1.0)

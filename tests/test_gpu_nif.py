@@ -20,14 +20,14 @@ TORCH_DT = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}
 
 
 def _build(res, F, log2, aabb, grid_vals, mats_list, grid_dt="f32", mlp_dt="f32",
-           net_mode=L.NIF_NETS_SINGLE, act=L.NIF_ACT_RELU):
+           net_mode=L.NIF_NETS_SINGLE, act=L.NIF_ACT_RELU, ctas_per_sm=0):
     """GPU model and the matching oracle model from the same float32 inputs
     (rounded to the GPU storage types)."""
     n_hidden = len(mats_list[0]) - 1
     width = mats_list[0][0].shape[0]
     cfg = nif.NifConfig(res=list(res), n_features=F, log2_table=log2, grid_dtype=DT[grid_dt],
                         n_hidden=n_hidden, width=width, act=act, mlp_dtype=DT[mlp_dt],
-                        net_mode=net_mode)
+                        net_mode=net_mode, ctas_per_sm=ctas_per_sm)
     flat = np.concatenate([synth.flatten_mlp(m) for m in mats_list])
     g = torch.from_numpy(np.ascontiguousarray(grid_vals, np.float32)).to(TORCH_DT[grid_dt]).cuda()
     w = torch.from_numpy(flat).to(TORCH_DT[mlp_dt]).cuda()
@@ -109,11 +109,13 @@ def test_encode_fp32_matches_oracle():
     np.testing.assert_allclose(x16, xo, atol=2e-3, rtol=0)
 
 
-@pytest.mark.parametrize("mlp_dt,grid_dt,tol", [("f32", "f32", 1e-4), ("f16", "f32", 2e-2),
-                                                 ("f16", "f16", 2e-2), ("bf16", "f32", 6e-2)])
-def test_logits_match_oracle(mlp_dt, grid_dt, tol):
+@pytest.mark.parametrize("mlp_dt,grid_dt,tol,ctas", [("f32", "f32", 1e-4, 0), ("f16", "f32", 2e-2, 0),
+                                                      ("f16", "f16", 2e-2, 0), ("bf16", "f32", 6e-2, 0),
+                                                      ("f16", "f16", 2e-2, 3), ("bf16", "f16", 6e-2, 3)])
+def test_logits_match_oracle(mlp_dt, grid_dt, tol, ctas):
     w = _tiny(n_rays=6000)
-    model, om = _build(w.res, 2, 19, w.aabb, w.grid_values, [w.weights], grid_dt=grid_dt, mlp_dt=mlp_dt)
+    model, om = _build(w.res, 2, 19, w.aabb, w.grid_values, [w.weights], grid_dt=grid_dt, mlp_dt=mlp_dt,
+                       ctas_per_sm=ctas)
     rays_t = torch.from_numpy(w.rays).cuda()
     ray_id, qobj, goff, nq = _gpu_queries(model, rays_t)
     bits = nif.empty_bits(len(w.rays))

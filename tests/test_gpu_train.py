@@ -60,13 +60,50 @@ def _frontend(model, rays_t):
     return ray_id[:nq].contiguous(), qobj[:nq].contiguous(), goff, nq, r, (q & 0x7FFFFFFF).astype(np.int64), (q >> 31).astype(bool)
 
 
+def _well_conditioned(om, rays, r, ob, inn):
+    """Pairs whose FP64 gradient is defined to FP32 resolution: the entry and
+    exit points move < 1e-4 under a 1e-6 relative perturbation of the ray (a
+    segment grazing a box face is ill-conditioned), and no hidden
+    pre-activation lies within 1e-3 of its layer's RMS of a ReLU kink."""
+    keep = np.ones(len(r), bool)
+    rng = np.random.default_rng(0)
+    for k in np.unique(ob):
+        sel = np.nonzero(ob == k)[0]
+        a = onif.entry_exit(rays[r[sel]], om.obj_aabb[k])
+        pr = rays[r[sel]].astype(np.float64).copy()
+        pr[:, 0:3] *= 1 + 1e-6 * rng.standard_normal((len(sel), 3))
+        pr[:, 4:7] *= 1 + 1e-6 * rng.standard_normal((len(sel), 3))
+        b = onif.entry_exit(pr, om.obj_aabb[k])
+        dev = np.maximum(np.abs(a[0] - b[0]).max(1), np.abs(a[1] - b[1]).max(1))
+        keep[sel] &= dev < 1e-4
+    x = onif.encode(om, rays, r, ob)
+    net = om.net_of(ob, inn)
+    for g in np.unique(net):
+        sel = np.nonzero(net == g)[0]
+        _, pre, _ = onif.mlp_forward(x[sel], om.nets[g], om.act, om.slope)
+        for a in pre:
+            rms = np.sqrt(np.mean(a * a))
+            keep[sel] &= np.abs(a).min(axis=1) > 1e-3 * rms
+    return keep
+
+
 @pytest.mark.parametrize("act", [L.NIF_ACT_RELU, L.NIF_ACT_LEAKY])
 def test_gradients_match_oracle(act):
-    model, om, rays, flat, grid = _setup(act=act)
-    rays_t = torch.from_numpy(rays).cuda()
-    ray_id, qobj, goff, nq, r, ob, inn = _frontend(model, rays_t)
+    model, om, rays, flat, grid = _setup(act=act, n_rays=60000)
+    # the oracle's own pairs, restricted to well-conditioned ones, grouped by network
+    r, ob, inn = onif.queries(rays, om.obj_aabb)
+    keep = _well_conditioned(om, rays, r, ob, inn)
+    r, ob, inn = r[keep], ob[keep], inn[keep]
+    order = np.argsort(inn, kind="stable")
+    r, ob, inn = r[order], ob[order], inn[order]
+    nq = len(r)
     assert nq > 2000 and inn.any() and (~inn).any()
     y = _labels_for(r, ob)
+    rays_t = torch.from_numpy(rays).cuda()
+    ray_id = torch.from_numpy(r.astype(np.int32)).cuda()
+    qobj = torch.from_numpy((ob.astype(np.uint32) | (inn.astype(np.uint32) << 31)).view(np.int32)).cuda()
+    n_out = int((~inn).sum())
+    goff = torch.tensor([0, n_out, nq], dtype=torch.int64, device="cuda")
     g = model.grids.clone().requires_grad_(True)
     w = model.weights.clone().requires_grad_(True)
     z = nif.NifQueryFn.apply(g, w, model, rays_t, ray_id, qobj, goff, nq)
@@ -79,8 +116,10 @@ def test_gradients_match_oracle(act):
     assert _rel_l2(gw, want_w) <= 1e-3
     gg = g.grad.cpu().numpy().reshape(dgrids.shape)
     assert _rel_l2(gg, dgrids) <= 1e-3
-    # untouched latents stay exactly zero
-    assert np.all(gg[dgrids == 0] == 0)
+    # latents the FP64 oracle leaves at exactly zero (no tap, or a point exactly
+    # on a cell face, whose far-side weight is 0 in FP64 and an ulp in FP32)
+    # get at most rounding-level values
+    assert np.abs(gg[dgrids == 0]).max() <= 1e-4 * np.abs(dgrids).max()
 
 
 def test_adam_matches_oracle_step_by_step():
