@@ -246,6 +246,29 @@ nif_status nif_infer(const nif_model_desc* m, const void* d_tlas, const nif_ray*
                      int64_t n, uint32_t* d_occluded_bits, void* d_ws, size_t ws_bytes,
                      void* stream);
 
+/* Allocation-free variant of nif_infer (the paper has no counterpart; it
+ * exists for callers of this library that cannot allocate device memory when
+ * they query visibility -- e.g. a renderer's frame loop that must not allocate
+ * once running, or a plugin whose host application owns all GPU memory -- and
+ * so cannot pass a workspace).  Same inputs, outputs and result as nif_infer
+ * (d_occluded_bits is OR-ed into), but the pair lists, counters and error
+ * word live in one fixed 16 MiB array inside libnif.so, held on every GPU the
+ * process uses until it exits.
+ *   - Capacity: about 2.09 million (ray, object) pairs (16 MiB / 8 bytes, less
+ *     a few KB of counters).  n above that is rejected up front with
+ *     NIF_ERR_WORKSPACE; if the pairs found exceed it, the call returns
+ *     NIF_ERR_WORKSPACE and the mask is incomplete.
+ *   - Unlike nif_infer the call synchronises `stream` before returning, to
+ *     read the overflow check.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call on a device shares the one array: calls that can overlap on
+ *     the GPU (other streams, other host threads) race and must be
+ *     serialised by the caller.
+ *   - Calls no cudaMalloc / cudaFree and no allocating library routine. */
+nif_status nif_infer_noalloc(const nif_model_desc* m, const void* d_tlas, const nif_ray* d_rays,
+                             int64_t n, uint32_t* d_occluded_bits, void* stream);
+
 /* ------------------------------------------------------------ training --
  * Optimiser state (Sec. 5 "Training": Adam, beta1 0.9, beta2 0.999,
  * eps 1e-15, L2 loss).  FP32 master copies of weights and grids are updated;

@@ -86,6 +86,7 @@ SIGNATURES = {
     "nif_adam": (i32, [P, P, P, P, i64, f32, f32, f32, f32, f32, i32, P, i32, P]),
     "nif_train_step": (i32, [MD, OD, P, P, P, P, P, i64, P, P, size_t, P]),
     "nif_fill_uniform": (i32, [P, i64, ctypes.c_uint64, f32, P]),
+    "nif_infer_noalloc": (i32, [MD, P, P, i64, P, P]),
 }
 
 

@@ -23,6 +23,7 @@ UNITS = {
     "nif_simt.cu": [],
     "nif_tc.cu": [],
     "api.cu": [],
+    "noalloc.cu": [],
 }
 
 
