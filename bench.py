@@ -31,11 +31,27 @@ sys.path.insert(0, ROOT)
 
 METRIC = "shadow rays/sec NIF vs own GPU BVH at <=1% visibility error; tensor-pipe util"
 UNIT = "shadow rays/s"
-ALG_BYTES_PER_QUERY = 3 * 16 * 8 * 2 * 2   # grid taps: 3 lookups x 16 levels x 8 corners x 2 FP16
-FLOPS_PER_QUERY = 2 * (96 * 64 + 2 * 64 * 64 + 64)
-WORKLOAD = ("room: 64 displaced icospheres (1,003,520 tris) + 12-tri room, 1920x1080 primary hits, "
-            "1 point light -> 2,073,600 shadow rays; hashed 16x2 FP16 grids (2^19/level) per object; "
-            "shared outer/inner MLP 3x64 FP16 trained 64 Adam steps x 262,144 pairs")
+WORKLOADS = {
+    "room": ("room: 64 displaced icospheres (1,003,520 tris) + 12-tri room, 1920x1080 primary hits, "
+             "1 point light -> 2,073,600 shadow rays; hashed 16x2 FP16 grids (2^19/level) per object; "
+             "shared outer/inner MLP 3x64 FP16 trained 64 Adam steps x 262,144 pairs"),
+    "full": ("full scale: 480 displaced icospheres x 62,720 tris (30.1M) on a jittered lattice + room, "
+             "1920x1080 primary hits, 4x4 area light x 4 samples -> 8,294,400 shadow rays; dense 8x2 "
+             "FP16 grids (R 4..64) per object; outer/inner MLP 3x64 FP16 trained on 64 shadow "
+             "samples/pixel"),
+    "precision": ("precision sweep: small-configuration object (20,480 tris) in the room, 4 point "
+                  "lights -> 8,294,400 shadow rays; dense 8x2 FP32 grids (R 4..64), MLP 3x64 trained "
+                  "in FP32, inferred in FP32 / BF16 / FP16 / FP8-E4M3"),
+}
+
+
+def per_query_cost(cfg):
+    """Algorithmic grid-tap bytes and MLP flops of one pair."""
+    esz = 2 if cfg.grid_dtype == 1 else 4
+    L_ = len(cfg.res)
+    K = 3 * L_ * cfg.n_features
+    W = cfg.width_mlp
+    return 3 * L_ * 8 * cfg.n_features * esz, 2 * (K * W + (cfg.n_hidden - 1) * W * W + W)
 
 
 def _peaks():
@@ -187,7 +203,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_rays_per_step": n},
+            "data": "synthetic", "config": {"workload": WORKLOADS["room"], "sample_rays_per_step": n},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{n} shadow rays per step, FP64 oracle NIF query"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -195,6 +211,56 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- our arm
+def precision_sweep(pipe, log, steps: int = 10, warmup: int = 3):
+    """The trained FP32 network inferred with FP32 / BF16 / FP16 / FP8-E4M3
+    operands (FP32 accumulation): time per query of all shadow rays,
+    disagreement with BVH truth and with the FP32 decisions."""
+    import statistics as st
+
+    import torch
+
+    from paper_2306_07191_gb300 import _lib as L
+    from paper_2306_07191_gb300 import nif
+
+    model = pipe.model
+    n = pipe.n_rays
+    ref = nif.empty_bits(n)
+    pipe.bvh_query(ref)
+    truth = nif.bits_to_bool(ref, n)
+    q8, sc8 = pipe.calibrate_e4m3(pipe.pairs)
+    w32 = pipe.trainer.w_master.clone()
+    variants = [("f32", L.NIF_F32, w32, None), ("bf16", L.NIF_BF16, w32.bfloat16(), None),
+                ("f16", L.NIF_F16, w32.half(), None), ("e4m3", L.NIF_E4M3, q8, sc8)]
+    out = {}
+    dec32 = None
+    saved = (model.cfg.mlp_dtype, model.weights, model.scales)
+    for name, dt, w, sc in variants:
+        model.cfg.mlp_dtype, model.weights, model.scales = dt, w.contiguous(), sc
+        bits = nif.empty_bits(n)
+        pipe.nif_query(bits)
+        torch.cuda.synchronize()
+        dec = nif.bits_to_bool(bits, n)
+        if dec32 is None:
+            dec32 = dec
+        times = []
+        for i in range(warmup + steps):
+            bits.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            pipe.nif_query(bits)
+            e1.record()
+            torch.cuda.synchronize()
+            if i >= warmup:
+                times.append(e0.elapsed_time(e1))
+        ms = st.mean(times)
+        out[name] = {"ms_per_query": ms, "rays_per_s": n / (ms * 1e-3),
+                     "disagreement_vs_bvh": float((dec != truth).float().mean()),
+                     "disagreement_vs_f32": float((dec != dec32).float().mean())}
+        log(f"precision {name}: {out[name]}")
+    model.cfg.mlp_dtype, model.weights, model.scales = saved
+    return out
+
+
 def run_ours(args):
     import ctypes
 
@@ -210,9 +276,18 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl")
     log = (lambda *a: print(*a, file=sys.stderr, flush=True)) if rank == 0 else (lambda *a: None)
-    cfg = RoomConfig()
+    from paper_2306_07191_gb300.pipeline import full_scale_config, small_object_precision_config
+    if args.workload == "full":
+        cfg = full_scale_config()
+    elif args.workload == "precision":
+        cfg = small_object_precision_config()
+    else:
+        cfg = RoomConfig()
     if args.small:
-        cfg = RoomConfig(n_obj=16, width=640, height=360, train_steps=8, batch=65536, train_spp=1)
+        cfg.width, cfg.height, cfg.train_steps, cfg.batch = 640, 360, 8, 65536
+        cfg.train_spp = min(cfg.train_spp, 2)
+        if cfg.layout == "random":
+            cfg.n_obj = 16
     if args.ctas_per_sm:
         cfg.ctas_per_sm = args.ctas_per_sm
     pipe = RoomPipeline(cfg, log=log)
@@ -220,6 +295,9 @@ def run_ours(args):
     dis = pipe.disagreement()
     abl = pipe.ablations()
     log(f"disagreement {dis}  ablations {abl}")
+    sweep = None
+    if args.workload == "precision":
+        sweep = precision_sweep(pipe, log)
     pipe.release_training_state()
     torch.cuda.empty_cache()
     n = pipe.n_rays
@@ -228,8 +306,8 @@ def run_ours(args):
     dev = rays.device
     stream = torch.cuda.current_stream()
     # explicit sub-steps so CUDA events bracket each kernel group
-    max_q = 4 * n + 1024
-    ws = model.workspace(max_q)
+    max_q = cfg.max_pairs_per_ray * n + 1024
+    ws = model.workspace(max_q, n)
     ray_id = torch.empty(max_q, dtype=torch.int32, device=dev)
     qobj = torch.empty(max_q, dtype=torch.int32, device=dev)
     goff = torch.empty(model.n_nets + 1, dtype=torch.int64, device=dev)
@@ -322,13 +400,15 @@ def run_ours(args):
     value = world * n / (ms * 1e-3)
     hbm, tflops, src = _peaks()
     fused_s = subs["fused_ms"] * 1e-3
-    ach_gbs = nq * ALG_BYTES_PER_QUERY / fused_s / 1e9
-    tc_tflops = nq * FLOPS_PER_QUERY / fused_s / 1e12
+    alg_bytes, flops_q = per_query_cost(cfg)
+    ach_gbs = nq * alg_bytes / fused_s / 1e9
+    tc_tflops = nq * flops_q / fused_s / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f16", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "rays": n, "queries": nq, "triangles": pipe.n_tris,
+        "vs_baseline": None, "dtype": {0: "f32", 1: "f16", 2: "bf16", 3: "e4m3"}[cfg.mlp_dtype],
+        "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "rays": n, "queries": nq, "triangles": pipe.n_tris,
                    "objects": cfg.n_obj, "l2": "flushed (256 MB write) before every timed step",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "bvh_rays_per_s": world * n / (bms * 1e-3), "bvh_ms_per_step": bms,
@@ -340,13 +420,15 @@ def run_ours(args):
                      "traffic": None, "peak_source": src,
                      "tensor_tflops": tc_tflops, "tensor_peak_tflops": tflops,
                      "tensor_frac": tc_tflops / tflops,
-                     "alg_bytes_per_query": ALG_BYTES_PER_QUERY, "flops_per_query": FLOPS_PER_QUERY},
+                     "alg_bytes_per_query": alg_bytes, "flops_per_query": flops_q},
         "e2e": {"value": world * n / (ems * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": n * 32, "d2h_bytes_per_step": bits.numel() * 4},
         "gpu_launches": 5 * args.steps,
         "clocks": clocks,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if sweep is not None:
+        line["precision_sweep"] = sweep
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "room":
         line["cpu_baseline"] = cpu_baseline()
     elif rank == 0:
         line["cpu_baseline"] = None
@@ -365,6 +447,7 @@ def main():
     ap.add_argument("--small", action="store_true", help="reduced workload for quick checks")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--workload", default="room", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

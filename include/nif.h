@@ -198,7 +198,9 @@ nif_status nif_shadow_rays(const nif_ray* d_camera, const float* d_t, int64_t n,
 #define NIF_QUERY_INNER 0x80000000u
 
 /* Workspace for nif_frontend / nif_infer with up to max_rays rays and
- * max_queries queries, and for nif_train_step with a batch of nq queries.
+ * max_queries queries (it includes 33 bytes per ray that let the front end
+ * traverse the top level once; nif_frontend falls back to two traversals when
+ * its workspace has no room for them).
  * The first 256 bytes (the device error word) must be zero before first use;
  * nif_check clears them after reporting an error.  0 on a bad descriptor. */
 size_t nif_workspace_size(const nif_model_desc* m, int64_t max_rays, int64_t max_queries);

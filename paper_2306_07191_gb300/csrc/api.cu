@@ -136,10 +136,12 @@ struct InferWs {
   int64_t* count;
   uint32_t* qray;
   uint32_t* qobj;
+  void* slots;
   size_t bytes;
 };
 
-static InferWs infer_layout(const NifParams& p, void* base, int64_t max_q) {
+// [error word | front-end counters | group offsets | count | pair lists | slots]
+static InferWs infer_layout(const NifParams& p, void* base, int64_t max_q, int64_t n_rays) {
   InferWs w{};
   size_t o = kErrBytes + frontend_ws_bytes(p);
   char* b = static_cast<char*>(base);
@@ -152,17 +154,15 @@ static InferWs infer_layout(const NifParams& p, void* base, int64_t max_q) {
   o += align_up(max_q * sizeof(uint32_t), 256);
   w.qobj = reinterpret_cast<uint32_t*>(b + o);
   o += align_up(max_q * sizeof(uint32_t), 256);
+  w.slots = b + o;
+  o += frontend_slot_bytes(n_rays);
   w.bytes = o;
   return w;
 }
 
-// Queries a nif_infer workspace can hold: encoded in the error block.
-struct WsHeaderExtra {
-  int64_t max_q;
-};
-
-static int64_t ws_max_q(const NifParams& p, size_t ws_bytes) {
-  InferWs w0 = infer_layout(p, nullptr, 0);
+// Pairs a nif_infer workspace of ws_bytes can hold for n_rays rays.
+static int64_t ws_max_q(const NifParams& p, size_t ws_bytes, int64_t n_rays) {
+  InferWs w0 = infer_layout(p, nullptr, 0, n_rays);
   if (ws_bytes <= w0.bytes) return 0;
   return static_cast<int64_t>((ws_bytes - w0.bytes) / 8 / 64 * 64) - 128;
 }
@@ -213,8 +213,7 @@ int64_t nif_weight_count(const nif_model_desc* m) { return weight_count(m); }
 size_t nif_workspace_size(const nif_model_desc* m, int64_t max_rays, int64_t max_queries) {
   NifParams p;
   if (make_params(m, &p) != NIF_OK || max_rays < 0 || max_queries < 0) return 0;
-  (void)max_rays;
-  return infer_layout(p, nullptr, max_queries + 256).bytes;
+  return infer_layout(p, nullptr, max_queries + 256, max_rays).bytes;
 }
 
 size_t nif_train_workspace_size(const nif_model_desc* m, int64_t nq) {
@@ -249,10 +248,12 @@ nif_status nif_frontend(const nif_model_desc* m, const void* d_tlas, const nif_r
   NIF_CHECK_ARG(n == 0 || (d_rays && aligned16(d_rays)), "nif_frontend: rays null or not 16-byte aligned");
   NIF_CHECK_ARG(max_q == 0 || (d_ray_id && d_qobj), "nif_frontend: null query arrays");
   NIF_CHECK_ARG(n < (int64_t(1) << 32), "nif_frontend: at most 2^32 rays");
-  if (ws_bytes < kErrBytes + frontend_ws_bytes(p))
-    return fail(NIF_ERR_WORKSPACE, "nif_frontend: workspace too small");
+  const size_t base = kErrBytes + frontend_ws_bytes(p);
+  if (ws_bytes < base) return fail(NIF_ERR_WORKSPACE, "nif_frontend: workspace too small");
+  // with room for per-ray slots after the counters, the top level is traversed once
+  void* slots = ws_bytes >= base + frontend_slot_bytes(n) ? static_cast<char*>(d_ws) + base : nullptr;
   return launch_frontend(p, d_tlas, d_rays, n, d_ray_id, d_qobj, max_q, d_group_off, d_count, d_ws,
-                         as_stream(stream));
+                         as_stream(stream), slots);
 }
 
 nif_status nif_encode(const nif_model_desc* m, const nif_ray* d_rays, const uint32_t* d_ray_id,
@@ -299,12 +300,12 @@ nif_status nif_infer(const nif_model_desc* m, const void* d_tlas, const nif_ray*
   NIF_CHECK_ARG(d_ws != nullptr, "nif_infer: null workspace");
   if (n == 0) return NIF_OK;
   NIF_CHECK_ARG(d_rays && d_occluded_bits, "nif_infer: null pointer");
-  int64_t max_q = ws_max_q(p, ws_bytes);
+  int64_t max_q = ws_max_q(p, ws_bytes, n);
   if (max_q <= 0) return fail(NIF_ERR_WORKSPACE, "nif_infer: workspace too small");
-  InferWs w = infer_layout(p, d_ws, max_q);
+  InferWs w = infer_layout(p, d_ws, max_q, n);
   if (w.bytes > ws_bytes) return fail(NIF_ERR_WORKSPACE, "nif_infer: workspace too small");
   cudaStream_t st = as_stream(stream);
-  s = launch_frontend(p, d_tlas, d_rays, n, w.qray, w.qobj, max_q, w.goff, w.count, d_ws, st);
+  s = launch_frontend(p, d_tlas, d_rays, n, w.qray, w.qobj, max_q, w.goff, w.count, d_ws, st, w.slots);
   if (s != NIF_OK) return s;
   if (p.mlp_dtype == NIF_F32)
     return launch_fwd_f32(p, d_rays, w.qray, w.qobj, w.goff, -1, d_occluded_bits, nullptr, nullptr,

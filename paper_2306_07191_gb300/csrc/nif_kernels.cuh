@@ -8,10 +8,13 @@ namespace nif {
 
 constexpr int kMaxGroups = 1024;
 
+// slot_area (nullable, frontend_slot_bytes(n) bytes) lets the front end
+// traverse the top level once instead of twice.
 nif_status launch_frontend(const NifParams& p, const void* tlas, const nif_ray* rays, int64_t n,
                            uint32_t* out_ray, uint32_t* out_qobj, int64_t max_q, int64_t* goff,
-                           int64_t* count, void* ws, cudaStream_t st);
+                           int64_t* count, void* ws, cudaStream_t st, void* slot_area = nullptr);
 size_t frontend_ws_bytes(const NifParams& p);
+size_t frontend_slot_bytes(int64_t n);
 
 nif_status launch_encode(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
                          const uint32_t* qobj, int64_t nq, void* out, int out_dtype,

@@ -74,6 +74,52 @@ __device__ __forceinline__ bool exact_slab(const float o[3], const float d[3], f
   return tin <= tout;
 }
 
+// The same two decisions as exact_slab -- overlap (tin <= tout) and inner
+// (entry <= tmin) -- taken with reciprocal multiplies where they are clear by a
+// margin of 2^-20 relative (a product by a correctly rounded reciprocal is
+// within 1.5 ulp of the correctly rounded quotient), and by exact_slab itself
+// otherwise, so the decisions are always exact_slab's.
+// rcp[k] = __frcp_rn(d[k]); `exact_only` forces the exact path (directions
+// with subnormal components).
+__device__ __forceinline__ bool slab_decide(const float o[3], const float d[3], const float rcp[3],
+                                            bool exact_only, float tmin, float tmax,
+                                            const float* box, bool& inner) {
+  if (!exact_only) {
+    float en = -INFINITY, ex = INFINITY, mag = 0.f;
+    bool blocked = false;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const float lo = box[k], hi = box[3 + k];
+      if (d[k] == 0.0f) {
+        if (!(lo <= o[k] && o[k] <= hi)) blocked = true;
+      } else {
+        const float t0 = (lo - o[k]) * rcp[k];
+        const float t1 = (hi - o[k]) * rcp[k];
+        const float n0 = fminf(t0, t1), f0 = fmaxf(t0, t1);
+        en = fmaxf(en, n0);
+        ex = fminf(ex, f0);
+        mag = fmaxf(mag, fmaxf(fabsf(t0), fabsf(t1)));
+      }
+    }
+    if (blocked) return false;
+    const float tin = fmaxf(tmin, en), tout = fminf(tmax, ex);
+    const float delta = 9.5367431640625e-07f * fmaxf(mag, fabsf(tmin));  // 2^-20
+    const bool hit_sure = tin + delta < tout - delta;
+    const bool miss_sure = tin - delta > tout + delta;
+    const bool in_sure = en + delta < tmin;
+    const bool out_sure = en - delta > tmin;
+    if (miss_sure) return false;
+    if (hit_sure && (in_sure || out_sure)) {
+      inner = in_sure;
+      return true;
+    }
+  }
+  float tin, tout, entry;
+  const bool hit = exact_slab(o, d, tmin, tmax, box, tin, tout, entry);
+  inner = entry <= tmin;
+  return hit;
+}
+
 struct QueryPoints {
   float u[3][3];  // entry, exit, direction, each in [0,1]^3
 };

@@ -30,12 +30,19 @@ template <bool kTlas, typename Emit>
 __device__ __forceinline__ void for_each_pair(const NifParams& p, const char* tlas,
                                               const bvh::Header* H, const nif_ray& r, Emit&& emit) {
   float o[3] = {r.ox, r.oy, r.oz}, d[3] = {r.dx, r.dy, r.dz};
+  float rcp[3];
+  bool exact_only = false;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    rcp[k] = d[k] != 0.0f ? __frcp_rn(d[k]) : 0.0f;
+    exact_only |= d[k] != 0.0f && fabsf(d[k]) < 1e-20f;
+  }
   auto test = [&](uint32_t obj) {
     float bx[6];
 #pragma unroll
     for (int k = 0; k < 6; ++k) bx[k] = __ldg(p.aabb + 6 * (size_t)obj + k);
-    float tin, tout, entry;
-    if (exact_slab(o, d, r.tmin, r.tmax, bx, tin, tout, entry)) emit(obj, entry <= r.tmin);
+    bool inner;
+    if (slab_decide(o, d, rcp, exact_only, r.tmin, r.tmax, bx, inner)) emit(obj, inner);
   };
   if (!kTlas) {
     for (int k = 0; k < p.n_obj; ++k) test(static_cast<uint32_t>(k));
@@ -95,6 +102,37 @@ __global__ void __launch_bounds__(256) k_front_count(NifParams p, const char* tl
     for_each_pair<kTlas>(p, tlas, &H, r, [&](uint32_t obj, bool inner) {
       atomicAdd(&s_cnt[bucket_of(p, obj, inner)], 1u);
     });
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x)
+    if (s_cnt[b]) atomicAdd(&g_count[b], s_cnt[b]);
+}
+
+// Count pass that also keeps each ray's first kSlots pairs (slot-major
+// [kSlots][n], with the pair count in nhits[i]) so the scatter pass need not
+// traverse the top level again.
+constexpr int kSlots = 8;
+
+template <bool kTlas>
+__global__ void __launch_bounds__(256) k_front_count_slots(NifParams p, const char* tlas,
+                                                           const nif_ray* rays, int64_t n,
+                                                           int n_buckets, uint32_t* g_count,
+                                                           uint32_t* slots, uint8_t* nhits) {
+  extern __shared__ uint32_t s_cnt[];
+  __shared__ bvh::Header H;
+  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x) s_cnt[b] = 0;
+  if (kTlas && threadIdx.x == 0) H = *reinterpret_cast<const bvh::Header*>(tlas);
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
+    int nh = 0;
+    for_each_pair<kTlas>(p, tlas, &H, r, [&](uint32_t obj, bool inner) {
+      atomicAdd(&s_cnt[bucket_of(p, obj, inner)], 1u);
+      if (nh < kSlots) slots[static_cast<int64_t>(nh) * n + i] = obj | (inner ? NIF_QUERY_INNER : 0u);
+      ++nh;
+    });
+    nhits[i] = static_cast<uint8_t>(nh < 255 ? nh : 255);
   }
   __syncthreads();
   for (int b = threadIdx.x; b < n_buckets; b += blockDim.x)
@@ -176,6 +214,55 @@ __global__ void __launch_bounds__(256) k_front_scatter(NifParams p, const char* 
   __syncthreads();
   for (int k = 0; k < nh; ++k) {
     int64_t pos = static_cast<int64_t>(s_base[slot[k]]) + rank[k];
+    if (pos < max_q) {
+      out_ray[pos] = static_cast<uint32_t>(i);
+      out_qobj[pos] = hits[k];
+    }
+  }
+}
+
+// Scatter from the slots; a ray with more than kSlots pairs is traversed again.
+template <bool kTlas>
+__global__ void __launch_bounds__(256) k_front_scatter_slots(NifParams p, const char* tlas,
+                                                             const nif_ray* rays, int64_t n,
+                                                             int n_buckets, uint32_t* g_cursor,
+                                                             int64_t max_q, const uint32_t* slots,
+                                                             const uint8_t* nhits,
+                                                             uint32_t* out_ray, uint32_t* out_qobj,
+                                                             DevError* err) {
+  extern __shared__ uint32_t s_dyn[];
+  uint32_t* s_cnt = s_dyn;
+  uint32_t* s_base = s_dyn + n_buckets;
+  __shared__ bvh::Header H;
+  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x) s_cnt[b] = 0;
+  if (kTlas && threadIdx.x == 0) H = *reinterpret_cast<const bvh::Header*>(tlas);
+  __syncthreads();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  uint32_t hits[kMaxHits];
+  int nh = 0;
+  if (i < n) {
+    const int c = nhits[i];
+    if (c <= kSlots) {
+      for (int k = 0; k < c; ++k) hits[k] = slots[static_cast<int64_t>(k) * n + i];
+      nh = c;
+    } else {
+      nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
+      for_each_pair<kTlas>(p, tlas, &H, r, [&](uint32_t obj, bool inner) {
+        if (nh < kMaxHits) hits[nh++] = obj | (inner ? NIF_QUERY_INNER : 0u);
+        else raise_error(err, NIF_ERR_BOUNDS, i);
+      });
+    }
+  }
+  uint32_t rank[kMaxHits];
+  for (int k = 0; k < nh; ++k)
+    rank[k] = atomicAdd(&s_cnt[bucket_of(p, hits[k] & 0x7fffffffu, hits[k] & NIF_QUERY_INNER)], 1u);
+  __syncthreads();
+  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x)
+    s_base[b] = s_cnt[b] ? atomicAdd(&g_cursor[b], s_cnt[b]) : 0u;
+  __syncthreads();
+  for (int k = 0; k < nh; ++k) {
+    const int b = bucket_of(p, hits[k] & 0x7fffffffu, hits[k] & NIF_QUERY_INNER);
+    const int64_t pos = static_cast<int64_t>(s_base[b]) + rank[k];
     if (pos < max_q) {
       out_ray[pos] = static_cast<uint32_t>(i);
       out_qobj[pos] = hits[k];
@@ -462,9 +549,14 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ th, float* __r
     }                                                                         \
   } while (0)
 
+size_t frontend_slot_bytes(int64_t n) {
+  return align_up(static_cast<size_t>(n) * kSlots * sizeof(uint32_t), 256) +
+         align_up(static_cast<size_t>(n), 256);
+}
+
 nif_status launch_frontend(const NifParams& p, const void* tlas, const nif_ray* rays, int64_t n,
                            uint32_t* out_ray, uint32_t* out_qobj, int64_t max_q, int64_t* goff,
-                           int64_t* count, void* ws, cudaStream_t st) {
+                           int64_t* count, void* ws, cudaStream_t st, void* slot_area) {
   int n_groups = p.net_mode == NIF_NETS_OBJECT ? p.n_obj : (p.net_mode == NIF_NETS_CLASS ? 2 : 1);
   int n_buckets = (p.net_mode == NIF_NETS_CLASS ? 2 : 1) * p.n_obj;
   int per_group = p.net_mode == NIF_NETS_OBJECT ? 1 : p.n_obj;
@@ -476,9 +568,18 @@ nif_status launch_frontend(const NifParams& p, const void* tlas, const nif_ray* 
   if (blocks < 1) blocks = 1;
   size_t sh1 = sizeof(uint32_t) * n_buckets;
   const char* tl = static_cast<const char*>(tlas);
+  uint32_t* slots = static_cast<uint32_t*>(slot_area);
+  uint8_t* nhits = slot_area ? reinterpret_cast<uint8_t*>(static_cast<char*>(slot_area) +
+                                                         align_up(static_cast<size_t>(n) * kSlots * 4, 256))
+                             : nullptr;
   if (n > 0) {
-    if (tlas) k_front_count<true><<<blocks, 256, sh1, st>>>(p, tl, rays, n, n_buckets, cnt);
-    else k_front_count<false><<<blocks, 256, sh1, st>>>(p, tl, rays, n, n_buckets, cnt);
+    if (slots) {
+      if (tlas) k_front_count_slots<true><<<blocks, 256, sh1, st>>>(p, tl, rays, n, n_buckets, cnt, slots, nhits);
+      else k_front_count_slots<false><<<blocks, 256, sh1, st>>>(p, tl, rays, n, n_buckets, cnt, slots, nhits);
+    } else {
+      if (tlas) k_front_count<true><<<blocks, 256, sh1, st>>>(p, tl, rays, n, n_buckets, cnt);
+      else k_front_count<false><<<blocks, 256, sh1, st>>>(p, tl, rays, n, n_buckets, cnt);
+    }
     NIF_LAUNCH_CHECK();
   }
   k_front_scan<<<1, 1024, 0, st>>>(cnt, n_buckets, per_group, n_groups, max_q, cur, goff, count, err);
@@ -486,7 +587,14 @@ nif_status launch_frontend(const NifParams& p, const void* tlas, const nif_ray* 
   if (n > 0) {
     int sblocks = static_cast<int>(ceil_div(n, 256));
     size_t sh2 = 2 * sizeof(uint32_t) * n_buckets;
-    if (tlas)
+    if (slots) {
+      if (tlas)
+        k_front_scatter_slots<true><<<sblocks, 256, sh2, st>>>(p, tl, rays, n, n_buckets, cur, max_q, slots,
+                                                               nhits, out_ray, out_qobj, err);
+      else
+        k_front_scatter_slots<false><<<sblocks, 256, sh2, st>>>(p, tl, rays, n, n_buckets, cur, max_q, slots,
+                                                                nhits, out_ray, out_qobj, err);
+    } else if (tlas)
       k_front_scatter<true><<<sblocks, 256, sh2, st>>>(p, tl, rays, n, n_buckets, cur, max_q, out_ray,
                                                        out_qobj, err);
     else

@@ -194,9 +194,9 @@ class NifModel:
         d.width = cfg.width
         return int(L.lib.nif_weight_count(ctypes.byref(d)))
 
-    def workspace(self, max_q: int) -> torch.Tensor:
+    def workspace(self, max_q: int, max_rays: int = 0) -> torch.Tensor:
         d = self.desc()
-        need = L.lib.nif_workspace_size(ctypes.byref(d), 0, max_q)
+        need = L.lib.nif_workspace_size(ctypes.byref(d), max_rays, max_q)
         if need == 0:
             raise L.NifError(L.NIF_ERR_ARG, L.last_error())
         if self._ws is None or self._ws.numel() < need:
@@ -217,7 +217,7 @@ class NifModel:
         qobj = torch.empty(max_q, dtype=torch.int32, device=dev)
         goff = torch.empty(self.n_nets + 1, dtype=torch.int64, device=dev)
         count = torch.empty(1, dtype=torch.int64, device=dev)
-        ws = self.workspace(0)
+        ws = self.workspace(0, n)
         d = self.desc()
         L.call("nif_frontend", ctypes.byref(d), _ptr(tlas.buf) if tlas else None, _ptr(rays), n,
                _ptr(ray_id), _ptr(qobj), max_q, _ptr(goff), _ptr(count), _ptr(ws), ws.numel(),
@@ -243,7 +243,7 @@ class NifModel:
 
     def infer(self, rays, bits, tlas: BVH | None = None, max_q: int | None = None, stream=None):
         n = int(rays.shape[0])
-        ws = self.workspace(max_q if max_q is not None else 4 * n + 1024)
+        ws = self.workspace(max_q if max_q is not None else 4 * n + 1024, n)
         d = self.desc()
         L.call("nif_infer", ctypes.byref(d), _ptr(tlas.buf) if tlas else None, _ptr(rays), n,
                _ptr(bits), _ptr(ws), ws.numel(), _stream(stream))
@@ -348,3 +348,31 @@ def adam_(master, grad, m1, m2, step: int, lr: float, beta1=0.9, beta2=0.999, ep
           grad_scale=1.0, copy: torch.Tensor | None = None, copy_dtype: int = L.NIF_F32, stream=None):
     L.call("nif_adam", _ptr(master), _ptr(grad), _ptr(m1), _ptr(m2), master.numel(), lr, beta1, beta2,
            eps, grad_scale, step, _ptr(copy), copy_dtype, _stream(stream))
+
+
+E4M3_MAX = 448.0
+
+
+def quantize_e4m3(weights_f32: torch.Tensor, cfg: NifConfig, n_nets: int, act_amax):
+    """Per-tensor FP8-E4M3 quantisation of every network's layers: weight
+    scale = amax(|W_l|) / 448, activation scale = act_amax[g][l] / 448 for the
+    input of layer l (l = 0..n_hidden-1; the output layer's input stays FP32).
+    Returns (e4m3 weights [n_nets*P], scales [n_nets][n_hidden+1][2] FP32)."""
+    P = NifModel.weight_count(cfg)
+    W, K, H = cfg.width, cfg.K, cfg.n_hidden
+    w = weights_f32.detach().float().reshape(n_nets, P)
+    q = torch.empty_like(w)
+    scales = torch.ones((n_nets, H + 1, 2), dtype=torch.float32, device=w.device)
+    for g in range(n_nets):
+        off, fan_in = 0, K
+        for l in range(H + 1):
+            n = (W * fan_in) if l < H else fan_in
+            blk = w[g, off:off + n]
+            sw = float(blk.abs().max().clamp_min(1e-30)) / E4M3_MAX
+            q[g, off:off + n] = blk / sw
+            scales[g, l, 1] = sw
+            if l < H:
+                scales[g, l, 0] = max(float(act_amax[g][l]), 1e-30) / E4M3_MAX
+            off += n
+            fan_in = W
+    return q.reshape(-1).to(torch.float8_e4m3fn).contiguous(), scales.contiguous()

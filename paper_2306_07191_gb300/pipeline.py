@@ -40,6 +40,30 @@ class RoomConfig:
     lr: float = 1e-2
     tmin: float = 1e-3
     ctas_per_sm: int = 0
+    layout: str = "random"      # "random" | "single" | "lattice" (see workloads.room_scene)
+    n_lights: int = 1           # point lights (one shadow ray per light per pixel)
+    area_light: bool = False    # 4 x 4 ceiling quad light instead of point lights
+    samples: int = 1            # shadow rays per pixel (area-light samples)
+    max_pairs_per_ray: int = 6  # capacity of the front end's pair lists
+    pairs_per_spp: int = 0      # training pairs kept per jittered sample (0 = all)
+
+
+def small_object_precision_config() -> RoomConfig:
+    """The small-configuration object and network (8 dense FP32 levels, R = 4..64,
+    3x64) in the room, 4 point lights -> 8,294,400 shadow rays."""
+    return RoomConfig(layout="single", n_obj=1, res=tuple(workloads.TINY_RES), log2_table=19,
+                      grid_dtype=L.NIF_F32, mlp_dtype=L.NIF_F32, n_lights=4, samples=4,
+                      train_spp=1)
+
+
+def full_scale_config() -> RoomConfig:
+    """480 displaced icospheres of 62,720 triangles (30.1M) on a jittered
+    lattice in the room, a 4 x 4 area light, 4 samples per pixel -> 8,294,400
+    shadow rays; dense 8-level FP16 grids per object, FP16 networks, trained on
+    16 jittered samples x 4 light samples = 64 shadow samples per pixel."""
+    return RoomConfig(layout="lattice", n_obj=480, n=56, res=tuple(workloads.TINY_RES),
+                      log2_table=19, grid_dtype=L.NIF_F16, mlp_dtype=L.NIF_F16, area_light=True,
+                      samples=4, train_spp=16, pairs_per_spp=1 << 20, max_pairs_per_ray=8)
 
 
 class RoomPipeline:
@@ -47,7 +71,8 @@ class RoomPipeline:
         self.cfg = cfg
         self.log = log
         t0 = time.time()
-        ws = workloads.room_scene(cfg.n_obj, cfg.n, cfg.width, cfg.height, cfg.seed)
+        ws = workloads.room_scene(cfg.n_obj, cfg.n, cfg.width, cfg.height, cfg.seed,
+                                  layout=cfg.layout, n_lights=cfg.n_lights)
         self.ws = ws
         sc = ws.scene
         dev = torch.device(device)
@@ -63,9 +88,9 @@ class RoomPipeline:
         room = sc.tri_obj < 0
         self.room_bvh = nif.BVH(self.verts, torch.from_numpy(sc.tris[room]).to(dev))
         self.tlas = nif.BVH.from_boxes(self.obj_aabb)
-        self.light = torch.from_numpy(ws.light.astype(np.float32)).to(dev)
+        self.light = torch.from_numpy(ws.light.astype(np.float32).reshape(-1)).to(dev)
         # evaluation frame: pixel-centre camera rays -> primary hits -> shadow rays
-        self.rays = self._shadow_rays(torch.from_numpy(ws.camera).to(dev))
+        self.rays = self._shadow_rays(torch.from_numpy(ws.camera).to(dev), light_seed=4321)
         self.n_rays = int(self.rays.shape[0])
         # model
         c = cfg
@@ -93,9 +118,20 @@ class RoomPipeline:
                  f"{n_grid / 1e9:.3f}G grid latents ({time.time() - t0:.1f}s)")
 
     # ------------------------------------------------------------ inputs
-    def _shadow_rays(self, camera: torch.Tensor) -> torch.Tensor:
+    def _shadow_rays(self, camera: torch.Tensor, light_seed: int) -> torch.Tensor:
+        """Shadow rays from the primary hits of `camera`: one per point light,
+        or cfg.samples uniform samples of the area light per pixel."""
+        c = self.cfg
         t, _ = self.bvh.cast_closest(camera)
-        return nif.shadow_rays(camera, t, self.light, tmin=self.cfg.tmin)
+        n = int(camera.shape[0])
+        if c.area_light:
+            pts = workloads.area_light_samples(np.random.default_rng(light_seed), n, c.samples)
+            return nif.shadow_rays(camera, t, torch.from_numpy(pts).to(self.dev), spp=c.samples,
+                                   per_ray=True, tmin=c.tmin)
+        if c.n_lights > 1:
+            pts = self.light.reshape(1, c.n_lights, 3).expand(n, c.n_lights, 3).contiguous()
+            return nif.shadow_rays(camera, t, pts, spp=c.n_lights, per_ray=True, tmin=c.tmin)
+        return nif.shadow_rays(camera, t, self.light, tmin=c.tmin)
 
     def training_pairs(self, spp: int | None = None, seed: int = 1234):
         """Shadow rays from jittered primary samples (the first spp of the
@@ -108,11 +144,18 @@ class RoomPipeline:
         for s in range(spp):
             jit = np.random.default_rng(seed + s).uniform(size=(c.width * c.height, 2))
             cam = synth.camera_rays(c.width, c.height, (0.0, 0.0, 19.0), (0.0, 0.0, 0.0), 60.0, jitter=jit)
-            r = self._shadow_rays(torch.from_numpy(cam).to(self.dev))
-            rid, qo, goff, count = self.model.frontend(r, tlas=self.tlas)
+            r = self._shadow_rays(torch.from_numpy(cam).to(self.dev), light_seed=5000 + s)
+            rid, qo, goff, count = self.model.frontend(r, tlas=self.tlas,
+                                                       max_q=c.max_pairs_per_ray * r.shape[0] + 1024)
             torch.cuda.synchronize()
+            self.model.check()
             nq = int(count.item())
             rid, qo = rid[:nq], qo[:nq]
+            if c.pairs_per_spp and nq > c.pairs_per_spp:
+                keep = torch.randperm(nq, device=self.dev,
+                                      generator=torch.Generator(device=self.dev).manual_seed(seed + s))
+                keep = keep[:c.pairs_per_spp].sort().values
+                rid, qo = rid[keep].contiguous(), qo[keep].contiguous()
             hit = self.bvh.cast_pairs(r, rid, qo)
             rays.append(r)
             rids.append(rid.to(torch.int64) + base)
@@ -129,10 +172,41 @@ class RoomPipeline:
         return rays, rid[order].to(torch.int32), qo[order].contiguous(), lab[order].contiguous(), \
             int((inner == 0).sum().item())
 
+    def calibrate_e4m3(self, pairs, n_cal: int = 65536, seed: int = 7):
+        """Per-tensor FP8-E4M3 scales from the FP32 trained network: the amax
+        of every layer's input over n_cal training pairs (per network), and
+        of every weight matrix.  Returns (e4m3 weights, scales)."""
+        rays, rid, qo, lab, n_outer = pairs
+        npool = int(rid.shape[0])
+        rng = np.random.default_rng(seed)
+        idx = np.sort(rng.choice(npool, min(n_cal, npool), replace=False))
+        k = int(np.searchsorted(idx, n_outer))
+        nq = len(idx)
+        it = torch.from_numpy(idx).to(self.dev)
+        ray_id, qobj = rid[it].contiguous(), qo[it].contiguous()
+        goff = torch.tensor([0, k, nq], dtype=torch.int64, device=self.dev)
+        c = self.cfg
+        f32cfg = nif.NifConfig(**{**self.model.cfg.__dict__, "grid_dtype": L.NIF_F32, "mlp_dtype": L.NIF_F32})
+        m32 = nif.NifModel(f32cfg, self.obj_aabb, self.trainer.g_master, self.trainer.w_master)
+        d = m32.desc()
+        z = torch.empty(nq, dtype=torch.float32, device=self.dev)
+        saved = torch.empty(L.lib.nif_saved_size(ctypes.byref(d), nq) // 4, dtype=torch.float32,
+                            device=self.dev)
+        L.call("nif_fwd_train", ctypes.byref(d), nif._ptr(rays), nif._ptr(ray_id), nif._ptr(qobj),
+               nif._ptr(goff), nq, nif._ptr(z), nif._ptr(saved), nif._stream())
+        K, W = f32cfg.K, c.width_mlp
+        sv = saved.reshape(K + c.n_hidden * W, nq)
+        bounds = [(0, K)] + [(K + l * W, K + (l + 1) * W) for l in range(c.n_hidden - 1)]
+        amax = []
+        for g, (a, b) in enumerate(((0, k), (k, nq))):
+            amax.append([float(sv[r0:r1, a:b].abs().max()) if b > a else 1.0 for r0, r1 in bounds])
+        return nif.quantize_e4m3(self.trainer.w_master, f32cfg, 2, amax)
+
     def train(self, steps: int | None = None, seed: int = 99, pairs=None):
         c = self.cfg
         steps = steps if steps is not None else c.train_steps
         rays, rid, qo, lab, n_outer = pairs if pairs is not None else self.training_pairs()
+        self.pairs = (rays, rid, qo, lab, n_outer)
         npool = int(rid.shape[0])
         self.trainer = nif.Trainer(self.model, lr=c.lr, w_master=self.w_master, g_master=self.g_master)
         rng = np.random.default_rng(seed)
@@ -159,6 +233,7 @@ class RoomPipeline:
         """Drop FP32 masters, Adam moments and the initial copies once
         training and the ablations are done (inference keeps the FP16 copies)."""
         self.trainer = None
+        self.pairs = None
         self.g_master = None
         self.w_master = None
         self.init_grids = None
@@ -170,7 +245,8 @@ class RoomPipeline:
         the top-level front end and the fused networks OR-ed into the mask."""
         rays = self.rays if rays is None else rays
         self.room_bvh.cast_shadow(rays, out=bits, stream=stream)
-        self.model.infer(rays, bits, tlas=self.tlas, stream=stream)
+        self.model.infer(rays, bits, tlas=self.tlas, stream=stream,
+                         max_q=self.cfg.max_pairs_per_ray * int(rays.shape[0]) + 1024)
         return bits
 
     def bvh_query(self, bits: torch.Tensor, rays: torch.Tensor | None = None, stream=None):
@@ -184,8 +260,10 @@ class RoomPipeline:
         b = nif.empty_bits(self.n_rays)
         self.nif_query(a)
         self.bvh_query(b)
-        rid, qo, goff, count = self.model.frontend(self.rays, tlas=self.tlas)
+        rid, qo, goff, count = self.model.frontend(self.rays, tlas=self.tlas,
+                                                   max_q=self.cfg.max_pairs_per_ray * self.n_rays + 1024)
         torch.cuda.synchronize()
+        self.model.check()
         nq = int(count.item())
         has = torch.zeros(self.n_rays, dtype=torch.bool, device=self.dev)
         has[rid[:nq].long()] = True
@@ -206,8 +284,10 @@ class RoomPipeline:
         b = nif.empty_bits(self.n_rays)
         self.bvh_query(b)
         vb = nif.bits_to_bool(b, self.n_rays)
-        rid, qo, goff, count = self.model.frontend(self.rays, tlas=self.tlas)
+        rid, qo, goff, count = self.model.frontend(self.rays, tlas=self.tlas,
+                                                   max_q=self.cfg.max_pairs_per_ray * self.n_rays + 1024)
         torch.cuda.synchronize()
+        self.model.check()
         nq = int(count.item())
         aabb_only = torch.zeros(self.n_rays, dtype=torch.bool, device=self.dev)
         aabb_only[rid[:nq].long()] = True

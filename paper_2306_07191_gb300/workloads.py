@@ -64,14 +64,51 @@ class RoomScene:
 
 
 def room_scene(n_obj: int = 64, n: int = 28, width: int = 1920, height: int = 1080,
-               seed: int = 7, jitter_seed: int | None = None) -> RoomScene:
+               seed: int = 7, jitter_seed: int | None = None, layout: str = "random",
+               n_lights: int = 1) -> RoomScene:
+    """Objects in a 12-triangle room [-20,20]^3 seen by a pinhole camera at
+    (0,0,19) looking at the origin.
+
+    layout "random":  n_obj displaced icospheres (frequency n), centres uniform
+                      in [-10,10]^3; n_lights point lights outside every box.
+    layout "single":  the small-configuration object (frequency 32, 20,480
+                      triangles) scaled to the box [-4,4]^3 at the origin.
+    layout "lattice": a jittered 10 x 6 x 8 lattice (spacing 4) of displaced
+                      icospheres of frequency n (480 objects for n_obj=480).
+    Point lights are drawn outside every object box; area-light samples are
+    drawn separately (area_light_samples)."""
     rng = np.random.default_rng(seed)
-    centres = rng.uniform(-10.0, 10.0, size=(n_obj, 3))
-    meshes = [synth.displaced_icosphere(n, rng, centre=c) for c in centres]
+    if layout == "single":
+        v, t = synth.displaced_icosphere(32, rng)
+        v = synth.fit_to_box(v, -4.0, 4.0)
+        meshes = [(v, t)]
+    elif layout == "lattice":
+        gx, gy, gz = 10, 6, 8
+        cells = np.stack(np.meshgrid(np.arange(gx), np.arange(gy), np.arange(gz), indexing="ij"), -1)
+        cells = cells.reshape(-1, 3)[:n_obj].astype(np.float64)
+        centres = (cells - (np.array([gx, gy, gz]) - 1) / 2.0) * 4.0
+        centres += rng.uniform(-0.6, 0.6, size=centres.shape)
+        meshes = [synth.displaced_icosphere(n, rng, centre=c) for c in centres]
+    else:
+        centres = rng.uniform(-10.0, 10.0, size=(n_obj, 3))
+        meshes = [synth.displaced_icosphere(n, rng, centre=c) for c in centres]
     sc = synth.build_scene(meshes, extra_geometry=synth.room_box(20.0))
-    light = synth.outside_point(rng, sc.obj_aabb, -15.0, 15.0)
+    lights = [synth.outside_point(rng, sc.obj_aabb, -15.0, 15.0) for _ in range(n_lights)]
+    light = lights[0] if n_lights == 1 else np.stack(lights)
     jitter = None
     if jitter_seed is not None:
         jitter = np.random.default_rng(jitter_seed).uniform(size=(width * height, 2))
     cam = synth.camera_rays(width, height, (0.0, 0.0, 19.0), (0.0, 0.0, 0.0), 60.0, jitter=jitter)
     return RoomScene(sc, cam, light, width, height)
+
+
+AREA_LIGHT = ((-2.0, 19.9, -2.0), (4.0, 0.0, 0.0), (0.0, 0.0, 4.0))  # corner, edge u, edge v
+
+
+def area_light_samples(rng: np.random.Generator, n_pixels: int, spp: int) -> np.ndarray:
+    """Uniform points on the 4 x 4 ceiling quad light, spp per pixel:
+    float32 [n_pixels * spp, 3]."""
+    c, eu, ev = (np.asarray(x) for x in AREA_LIGHT)
+    a = rng.uniform(size=(n_pixels * spp, 1))
+    b = rng.uniform(size=(n_pixels * spp, 1))
+    return (c[None, :] + a * eu[None, :] + b * ev[None, :]).astype(np.float32)

@@ -198,3 +198,69 @@ def test_zero_rays_and_zero_queries():
     model.infer(torch.from_numpy(far).cuda(), bits)
     model.check()
     assert not nif.bits_to_bool(bits, 100).any()
+
+
+def test_fp8_e4m3_logits_within_reported_bound():
+    """FP8-E4M3 weights and activations with per-tensor scales (amax / 448,
+    activations calibrated on the oracle's FP64 forward of the same queries),
+    FP32 accumulation: logits within 0.25 abs of FP64 on dequantised weights."""
+    w = _tiny(n_rays=6000)
+    flat = np.concatenate([synth.flatten_mlp(w.weights)]).astype(np.float32)
+    K = 48
+    # calibration: the oracle's activations at each layer input
+    om32 = oracle_model(onif, w.res, 2, 19, w.aabb, w.grid_values.astype(np.float64),
+                        [[np.asarray(m, np.float64) for m in w.weights]])
+    rr, oo, ii = onif.queries(w.rays, w.aabb)
+    x = onif.encode(om32, w.rays, rr, oo)
+    _, pre, post = onif.mlp_forward(x, om32.nets[0])
+    amax = [[float(np.abs(post[l]).max()) for l in range(3)]]
+    cfg = nif.NifConfig(res=w.res, n_features=2, log2_table=19, grid_dtype=L.NIF_F32, n_hidden=3,
+                        width=64, mlp_dtype=L.NIF_E4M3)
+    q, sc = nif.quantize_e4m3(torch.from_numpy(flat).cuda(), cfg, 1, amax)
+    model = nif.NifModel(cfg, torch.from_numpy(w.aabb).cuda(), torch.from_numpy(w.grid_values.reshape(-1)).cuda(),
+                         q, scales=sc)
+    # oracle on the dequantised weights
+    deq = (q.float().reshape(-1).cpu().numpy().astype(np.float64))
+    scn = sc.cpu().numpy()
+    mats, off, fan_in = [], 0, K
+    for l in range(4):
+        n = 64 * fan_in if l < 3 else fan_in
+        mats.append(deq[off:off + n].reshape(64 if l < 3 else 1, fan_in) * scn[0, l, 1])
+        off += n
+        fan_in = 64
+    om = oracle_model(onif, w.res, 2, 19, w.aabb, w.grid_values.astype(np.float64), [mats])
+    rays_t = torch.from_numpy(w.rays).cuda()
+    ray_id, qobj, goff, nq = _gpu_queries(model, rays_t)
+    z = model.infer_queries(rays_t, ray_id, qobj, goff, nq)
+    model.check()
+    r, ob, inn = _query_arrays(ray_id, qobj, nq)
+    zo = onif.forward(om, w.rays, r, ob, inn)
+    err = np.abs(z[:nq].cpu().numpy() - zo)
+    assert np.abs(zo).max() > 0.05
+    assert err.max() <= 0.25, err.max()
+    assert err.mean() <= 0.05, err.mean()
+
+
+@pytest.mark.parametrize("use_tlas", [False, True])
+def test_frontend_many_pairs_per_ray(use_tlas):
+    """Rays crossing 16 boxes in a row: more pairs per ray than the front end
+    keeps per ray in its single-traversal slots."""
+    lo = np.stack([np.arange(16) * 1.5, np.zeros(16), np.zeros(16)], 1)
+    boxes = np.concatenate([lo, lo + 1.0], axis=1).astype(np.float32)
+    rng = np.random.default_rng(2)
+    n = 3000
+    o = np.stack([np.full(n, -5.0), rng.uniform(0.05, 0.95, n), rng.uniform(0.05, 0.95, n)], 1)
+    d = np.tile([[1.0, 0.0, 0.0]], (n, 1))
+    d[n // 2:] = synth.unit_vectors(rng, n - n // 2)
+    rays = synth.pack_rays(o, d, 1e-3, np.inf)
+    cfg = nif.NifConfig(res=[2], n_features=1, net_mode=L.NIF_NETS_CLASS)
+    model = nif.NifModel(cfg, torch.from_numpy(boxes).cuda(), torch.zeros(16 * 2 * 27).cuda(),
+                         torch.zeros(2 * nif.NifModel.weight_count(cfg)).cuda())
+    tlas = nif.BVH.from_boxes(torch.from_numpy(boxes).cuda()) if use_tlas else None
+    ray_id, qobj, goff, count = model.frontend(torch.from_numpy(rays).cuda(), tlas=tlas, max_q=20 * n)
+    model.check()
+    nq = int(count.item())
+    r, ob, inn = _query_arrays(ray_id, qobj, nq)
+    rr, oo, ii = onif.queries(rays, boxes)
+    assert np.bincount(rr).max() == 16
+    assert sorted(zip(r.tolist(), ob.tolist(), inn.tolist())) == sorted(zip(rr.tolist(), oo.tolist(), ii.tolist()))
