@@ -300,6 +300,10 @@ def run_ours(args):
         sweep = precision_sweep(pipe, log)
     pipe.release_training_state()
     torch.cuda.empty_cache()
+    if not args.ctas_per_sm and pipe.model.cfg.mlp_dtype != L.NIF_F32:
+        occ = nif.autotune_occupancy(pipe.model, pipe.rays, pipe.tlas,
+                                     max_q=cfg.max_pairs_per_ray * pipe.n_rays + 1024)
+        log(f"autotuned fused kernel occupancy: {occ} CTAs/SM")
     n = pipe.n_rays
     rays = pipe.rays
     model = pipe.model
@@ -410,6 +414,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "rays": n, "queries": nq, "triangles": pipe.n_tris,
                    "objects": cfg.n_obj, "l2": "flushed (256 MB write) before every timed step",
+                   "fused_ctas_per_sm": model.cfg.ctas_per_sm,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "bvh_rays_per_s": world * n / (bms * 1e-3), "bvh_ms_per_step": bms,
         "speedup_vs_bvh": bms / ms,

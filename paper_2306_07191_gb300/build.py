@@ -37,7 +37,8 @@ def nvcc() -> str:
 def _compile(src: str, extra: list[str], verbose: bool) -> str:
     obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
     cmd = [nvcc(), "-std=c++17", "-O3", "-lineinfo", *ARCH, "-Xcompiler", "-fPIC",
-           "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj, *extra]
+           "-I", os.path.join(ROOT, "include"), "-c", src, "-o", obj, *extra,
+           *os.environ.get("NIF_NVCC_FLAGS", "").split()]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

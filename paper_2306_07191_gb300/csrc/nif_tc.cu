@@ -125,6 +125,32 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Stores of 32-bit words into this warp's TMEM lane quarter (one lane per
+// thread, consecutive columns from taddr), and the wait for their completion.
+__device__ __forceinline__ void tmem_st1(uint32_t taddr, uint32_t v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t v[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+      : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+// MMA whose A operand is read from tensor memory (rows = lanes, two 16-bit
+// elements per 32-bit column, K-major), B from shared memory.
+__device__ __forceinline__ void mma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
+                                       uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // Shared-memory matrix descriptor: K-major, no swizzle.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
@@ -448,7 +474,294 @@ __global__ void __launch_bounds__(kThreads, kOcc)
   if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
+
+// ---------------------------------------------------------------------------
+// The same computation with every activation in tensor memory: the encoder
+// writes the layer-1 input with tcgen05.st into TMEM (each warp owns the lane
+// quarter of its 32 query rows), every MMA reads its A operand from TMEM, and
+// the epilogue writes the activated hidden layer back into the same TMEM
+// columns.  Shared memory then holds only the weights, which leaves most of
+// the SM's unified L1/shared storage to L1, where the grid gathers hit.
+// 16-bit operands (F16 / BF16) and an even number of features per level.
+struct LayoutTm {
+  uint32_t w0_off, w1_bytes, wl_bytes, wout_off, zpart_off, pre_off, total;
+  __host__ __device__ uint32_t w_off(int l) const {
+    return l == 0 ? w0_off : w0_off + w1_bytes + static_cast<uint32_t>(l - 1) * wl_bytes;
+  }
+};
+
+__host__ __device__ inline LayoutTm make_layout_tm(int Kp, int W, int H, int n_nets) {
+  LayoutTm L{};
+  L.w0_off = 0;
+  L.w1_bytes = W * Kp * 2;
+  L.wl_bytes = W * W * 2;
+  uint32_t o = L.w1_bytes + static_cast<uint32_t>(H > 1 ? H - 1 : 0) * L.wl_bytes;
+  o = (o + 15) / 16 * 16;
+  L.wout_off = o;
+  o += W * 4;
+  L.zpart_off = o;
+  o += 2 * kM * 4;
+  L.pre_off = o;
+  o += (n_nets + 1) * 8;
+  L.total = o;
+  return L;
+}
+
+// TMEM columns: accumulator [0, W), activations [W, W + max(Kp, W)/2).
+__host__ __device__ inline uint32_t tm_cols(int Kp, int W) {
+  const int need = W + (Kp > W ? Kp : W) / 2;
+  return need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
+}
+
+template <int F, typename TG, int DT, int kOcc>
+__global__ void __launch_bounds__(kThreads, kOcc)
+    k_fused_tm(const __grid_constant__ NifParams p, const nif_ray* __restrict__ rays,
+               const uint32_t* __restrict__ ray_id, const uint32_t* __restrict__ qobj,
+               const int64_t* __restrict__ goff, uint32_t* __restrict__ occ,
+               float* __restrict__ logits, DevError* err, int Kp) {
+  using O = Op<DT>;
+  static_assert(O::esz == 2 && F % 2 == 0, "TMEM activations need 16-bit operands and even F");
+  constexpr int FP = F / 2;  // packed 32-bit columns per level lookup
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ uint32_t s_tmem;
+  __shared__ int s_abort;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int W = p.width, H = p.n_hidden, K = p.K;
+  const LayoutTm L = make_layout_tm(Kp, W, H, p.n_nets);
+  float* wout = reinterpret_cast<float*>(smem + L.wout_off);
+  float* zpart = reinterpret_cast<float*>(smem + L.zpart_off);
+  int64_t* s_pre = reinterpret_cast<int64_t*>(smem + L.pre_off);
+  const uint32_t bar = smem_u32(&s_bar);
+  const uint32_t ncols = tm_cols(Kp, W);
+
+  if (warp == 0) tmem_alloc(smem_u32(&s_tmem), ncols);
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    s_abort = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const uint32_t act_col = static_cast<uint32_t>(W);  // activation columns start here
+
+  const int64_t n_tiles = build_tile_prefix(goff, p.n_nets, kM, s_pre);
+  const uint32_t idesc = instr_desc(kM, W, O::fmt);
+  uint32_t phase = 0;
+  int cur_g = -1;
+
+  const int qi = tid & (kM - 1);  // query row == TMEM lane
+  const int half = tid >> 7;       // level parity handled by this thread
+  const int ecol0 = half * (W / 2);
+  // this warp's lane quarter: rows 32*(warp&3) .. +31
+  const uint32_t lane_base = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
+
+  auto pack2 = [](float a, float b) {
+    typename O::T x = O::cvt(a), y = O::cvt(b);
+    return static_cast<uint32_t>(*reinterpret_cast<uint16_t*>(&x)) |
+           (static_cast<uint32_t>(*reinterpret_cast<uint16_t*>(&y)) << 16);
+  };
+
+  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const int g = find_group(s_pre, p.n_nets, t);
+    const int64_t q0 = goff[g] + (t - s_pre[g]) * kM;
+    const int64_t qend = goff[g + 1];
+
+    // ---- weights of network g into shared memory (B operands, K-major)
+    if (g != cur_g) {
+      const int64_t wbase = static_cast<int64_t>(g) * p.P;
+      int64_t off = 0;
+      for (int l = 0; l < H; ++l) {
+        const int fin = l == 0 ? K : W;
+        const int fpad = l == 0 ? Kp : W;
+        uint8_t* wt = smem + L.w_off(l);
+        for (int e = tid; e < W * fpad; e += kThreads) {
+          const int n = e / fpad, k = e % fpad;
+          const float v = k < fin ? O::load(p.weights, wbase + off + static_cast<int64_t>(n) * fin + k) : 0.f;
+          store_elem<DT>(wt, n, k, fpad, v);
+        }
+        off += static_cast<int64_t>(W) * fin;
+      }
+      for (int e = tid; e < W; e += kThreads) wout[e] = O::load(p.weights, wbase + off + e);
+      cur_g = g;
+      fence_proxy_async();
+    }
+
+    // ---- step a1/a2: encode 128 queries straight into TMEM
+    {
+      const int64_t q = q0 + qi;
+      const bool live = q < qend;
+      QueryPoints pts;
+      const TG* tpos = nullptr;
+      const TG* tdir = nullptr;
+      if (live) {
+        const nif_ray r = load_nif_ray(rays, ray_id[q]);
+        const uint32_t obj = qobj[q] & 0x7fffffffu;
+        float bx[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) bx[k] = __ldg(p.aabb + 6 * static_cast<size_t>(obj) + k);
+        query_points(r, bx, pts);
+        tpos = static_cast<const TG*>(grid_ptr(p, obj, 0));
+        tdir = static_cast<const TG*>(grid_ptr(p, obj, 1));
+      } else {
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) pts.u[j][k] = 0.f;
+      }
+      // every warp walks the same levels, so the warp-wide TMEM stores stay
+      // aligned; rows past the end of the group store zeros
+      for (int l = half; l < p.L; l += 2) {
+        if constexpr (F == 2) {
+          using Raw = typename std::conditional<sizeof(TG) == 2, __half2, float2>::type;
+          // lookups per batch: all three (24 gathers in flight) at 2-3 CTAs
+          // per SM, one at a time when 4 CTAs share the SM's registers
+          constexpr int kJB = kOcc >= 4 ? 1 : 3;
+          const LevelInfo li = level_info(p, l);
+          const Raw* tp = reinterpret_cast<const Raw*>(tpos);
+          const Raw* td = reinterpret_cast<const Raw*>(tdir);
+#pragma unroll
+          for (int jb = 0; jb < 3; jb += kJB) {
+            uint32_t word[kJB];
+#pragma unroll
+            for (int u = 0; u < kJB; ++u) word[u] = 0u;
+            if (live) {
+              uint32_t idx[kJB][8];
+              float fr[kJB][3];
+#pragma unroll
+              for (int u = 0; u < kJB; ++u) {
+                const int j = jb + u;
+                uint32_t c0[3];
+                cell_of(li, pts.u[j][0], pts.u[j][1], pts.u[j][2], c0, fr[u]);
+                cell_entries(li, c0, idx[u]);
+              }
+              Raw v[kJB][8];
+#pragma unroll
+              for (int u = 0; u < kJB; ++u) {
+                const Raw* tab = (jb + u) < 2 ? tp : td;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) v[u][c] = __ldg(tab + idx[u][c]);
+              }
+#pragma unroll
+              for (int u = 0; u < kJB; ++u) {
+                float w[8];
+                cell_weights(fr[u], w);
+                float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                  float2 fv;
+                  if constexpr (sizeof(TG) == 2) fv = __half22float2(v[u][c]);
+                  else fv = v[u][c];
+                  a0 += w[c] * fv.x;
+                  a1 += w[c] * fv.y;
+                }
+                word[u] = pack2(a0, a1);
+              }
+            }
+#pragma unroll
+            for (int u = 0; u < kJB; ++u)
+              tmem_st1(lane_base + act_col + static_cast<uint32_t>((jb + u) * p.L + l), word[u]);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            float v[F];
+            if (live) {
+              Taps tp;
+              level_taps(p, l, pts.u[j], tp);
+              gather_level<F, TG>(j < 2 ? tpos : tdir, tp, v);
+            } else {
+#pragma unroll
+              for (int f = 0; f < F; ++f) v[f] = 0.f;
+            }
+#pragma unroll
+            for (int f2 = 0; f2 < FP; ++f2)
+              tmem_st1(lane_base + act_col + static_cast<uint32_t>((j * p.L + l) * FP + f2),
+                       pack2(v[2 * f2], v[2 * f2 + 1]));
+          }
+        }
+      }
+      if (half == 0)
+        for (int k2 = K / 2; k2 < Kp / 2; ++k2) tmem_st1(lane_base + act_col + k2, 0u);
+    }
+    tmem_wait_st();
+    tc_fence_before();
+    __syncthreads();
+
+    // ---- step a3: hidden layers, A from TMEM, B from shared memory
+    float zacc = 0.f;
+    for (int l = 0; l < H; ++l) {
+      const int kdim = l == 0 ? Kp : W;
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t b0 = smem_u32(smem + L.w_off(l));
+        const uint32_t sbo = (kdim / 8) * 128;
+        for (int kk = 0; kk < kdim / 16; ++kk) {
+          const uint64_t bd = smem_desc(b0 + kk * 256, 128, sbo);
+          mma_ta(tmem, tmem + act_col + static_cast<uint32_t>(kk * 8), bd, idesc, kk > 0 ? 1u : 0u);
+        }
+        mma_commit(bar);
+      }
+      bool ok = mbar_wait(bar, phase, err);
+      phase ^= 1u;
+      if (!ok) s_abort = 1;
+      tc_fence_after();
+      for (int c0 = 0; c0 < W / 2; c0 += 16) {
+        float v[16];
+        tmem_ld16(lane_base + static_cast<uint32_t>(ecol0 + c0), v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const float a = v[i];
+          v[i] = a > 0.f ? a : (p.act == NIF_ACT_LEAKY ? p.slope * a : 0.f);
+        }
+        if (l + 1 < H) {
+          uint32_t pk[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) pk[i] = pack2(v[2 * i], v[2 * i + 1]);
+          tmem_st8(lane_base + act_col + static_cast<uint32_t>((ecol0 + c0) / 2), pk);
+        } else {
+#pragma unroll
+          for (int i = 0; i < 16; ++i) zacc += v[i] * wout[ecol0 + c0 + i];
+        }
+      }
+      if (l + 1 < H) tmem_wait_st();
+      tc_fence_before();
+      __syncthreads();
+      if (s_abort) break;
+    }
+    if (s_abort) break;
+
+    // ---- step a4: logit and visibility
+    zpart[half * kM + qi] = zacc;
+    __syncthreads();
+    if (tid < kM) {
+      const int64_t q = q0 + tid;
+      if (q < qend) {
+        const float z = zpart[tid] + zpart[kM + tid];
+        if (logits) logits[q] = z;
+        if (occ && z < 0.f) {
+          const uint32_t rid = ray_id[q];
+          atomicOr(&occ[rid >> 5], 1u << (rid & 31));
+        }
+      }
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
 }  // namespace tc
+
+// The TMEM-activation kernel is the default for 16-bit operands; building
+// with -DNIF_TC_SMEM_ACTIVATIONS=1 selects the shared-memory kernel instead.
+#ifndef NIF_TC_SMEM_ACTIVATIONS
+#define NIF_TC_SMEM_ACTIVATIONS 0
+#endif
+static bool tc_activations_in_tmem() { return NIF_TC_SMEM_ACTIVATIONS == 0; }
 
 nif_status check_tc_shape(const NifParams& p) {
   const int esz = p.mlp_dtype == NIF_E4M3 ? 1 : 2;
@@ -487,10 +800,46 @@ nif_status check_tc_shape(const NifParams& p) {
   } while (0)
 
 template <int DT>
+static nif_status launch_tm(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
+                            const uint32_t* qobj, const int64_t* goff, int blocks, int per_sm,
+                            uint32_t* occ, float* logits, DevError* err, cudaStream_t st) {
+  const int Kp = (p.K + 15) / 16 * 16;
+  tc::LayoutTm L = tc::make_layout_tm(Kp, p.width, p.n_hidden, p.n_nets);
+  size_t sh = L.total + 1024;
+  auto go = [&](auto kern) -> nif_status {
+    NIF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    kern<<<blocks, tc::kThreads, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, err, Kp);
+    return NIF_OK;
+  };
+  nif_status s;
+  if (p.grid_dtype == NIF_F16) {
+    if (p.F == 2)
+      s = per_sm >= 4 ? go(tc::k_fused_tm<2, __half, DT, 4>)
+          : per_sm == 3 ? go(tc::k_fused_tm<2, __half, DT, 3>) : go(tc::k_fused_tm<2, __half, DT, 2>);
+    else if (p.F == 4) s = go(tc::k_fused_tm<4, __half, DT, 2>);
+    else s = go(tc::k_fused_tm<8, __half, DT, 2>);
+  } else {
+    if (p.F == 2)
+      s = per_sm >= 4 ? go(tc::k_fused_tm<2, float, DT, 4>)
+          : per_sm == 3 ? go(tc::k_fused_tm<2, float, DT, 3>) : go(tc::k_fused_tm<2, float, DT, 2>);
+    else if (p.F == 4) s = go(tc::k_fused_tm<4, float, DT, 2>);
+    else s = go(tc::k_fused_tm<8, float, DT, 2>);
+  }
+  if (s != NIF_OK) return s;
+  NIF_LAUNCH_CHECK();
+  return NIF_OK;
+}
+
+template <int DT>
 static nif_status launch_dt(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
-                            const uint32_t* qobj, const int64_t* goff, int blocks, bool occ3,
+                            const uint32_t* qobj, const int64_t* goff, int blocks, int per_sm,
                             uint32_t* occ, float* logits, DevError* err, cudaStream_t st) {
   const int esz = DT == NIF_E4M3 ? 1 : 2;
+  const bool occ3 = per_sm >= 3;
+  if constexpr (DT != NIF_E4M3) {
+    if (p.F % 2 == 0 && tc_activations_in_tmem())
+      return launch_tm<DT>(p, rays, ray_id, qobj, goff, blocks, per_sm, occ, logits, err, st);
+  }
   const int Kp = (p.K + 32 / esz - 1) / (32 / esz) * (32 / esz);
   tc::Layout L = tc::make_layout(Kp, p.width, p.n_hidden, esz);
   size_t sh = L.total + 1024;
@@ -524,13 +873,20 @@ nif_status launch_fwd_tc(const NifParams& p, const nif_ray* rays, const uint32_t
   if (tile_m != 0 && tile_m != 128)
     return fail(NIF_ERR_UNSUPPORTED, "tensor-core path: tile_m %d (128 supported)", tile_m);
   int per_sm = ctas_per_sm > 0 ? ctas_per_sm : 2;
+  if (p.mlp_dtype != NIF_E4M3 && p.F % 2 == 0 && tc_activations_in_tmem()) {
+    // each CTA holds tm_cols() of the SM's 512 TMEM columns
+    const int Kp16 = (p.K + 15) / 16 * 16;
+    const int cap = 512 / static_cast<int>(tc::tm_cols(Kp16, p.width));
+    per_sm = std::min(std::min(per_sm, cap), 4);
+  } else {
+    per_sm = std::min(per_sm, 3);
+  }
   int blocks = sm_count() * per_sm;
   if (nq_hint >= 0)
     blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(blocks, ceil_div(nq_hint, tc::kM) + p.n_nets)));
-  const bool occ3 = per_sm >= 3;
-  if (p.mlp_dtype == NIF_F16) return launch_dt<NIF_F16>(p, rays, ray_id, qobj, goff, blocks, occ3, occ, logits, err, st);
-  if (p.mlp_dtype == NIF_BF16) return launch_dt<NIF_BF16>(p, rays, ray_id, qobj, goff, blocks, occ3, occ, logits, err, st);
-  if (p.mlp_dtype == NIF_E4M3) return launch_dt<NIF_E4M3>(p, rays, ray_id, qobj, goff, blocks, occ3, occ, logits, err, st);
+  if (p.mlp_dtype == NIF_F16) return launch_dt<NIF_F16>(p, rays, ray_id, qobj, goff, blocks, per_sm, occ, logits, err, st);
+  if (p.mlp_dtype == NIF_BF16) return launch_dt<NIF_BF16>(p, rays, ray_id, qobj, goff, blocks, per_sm, occ, logits, err, st);
+  if (p.mlp_dtype == NIF_E4M3) return launch_dt<NIF_E4M3>(p, rays, ray_id, qobj, goff, blocks, per_sm, occ, logits, err, st);
   return fail(NIF_ERR_UNSUPPORTED, "tensor-core path: mlp dtype %d", p.mlp_dtype);
 }
 

@@ -376,3 +376,54 @@ def quantize_e4m3(weights_f32: torch.Tensor, cfg: NifConfig, n_nets: int, act_am
             off += n
             fan_in = W
     return q.reshape(-1).to(torch.float8_e4m3fn).contiguous(), scales.contiguous()
+
+
+def autotune_occupancy(model: NifModel, rays: torch.Tensor, tlas: BVH | None = None,
+                       candidates=(2, 3, 4), reps: int = 3, max_q: int | None = None,
+                       cache_path: str | None = None) -> int:
+    """Pick the fused kernel's CTAs per SM (2, 3 or 4: more CTAs trade gathers
+    in flight per thread for more warps) by timing nif_infer on the caller's
+    own rays; the choice is cached per (model shape, ray count, GPU) in a JSON
+    file and written into model.cfg.ctas_per_sm."""
+    import hashlib
+    import json
+    import os
+    c = model.cfg
+    key = hashlib.sha1(json.dumps([list(c.res), c.n_features, c.log2_table, c.grid_dtype, c.n_hidden,
+                                   c.width, c.mlp_dtype, c.net_mode, model.n_obj, int(rays.shape[0]),
+                                   torch.cuda.get_device_name()]).encode()).hexdigest()[:16]
+    cache_path = cache_path or os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune.json")
+    try:
+        with open(cache_path) as f:
+            cache = json.load(f)
+    except (OSError, ValueError):
+        cache = {}
+    if key in cache:
+        c.ctas_per_sm = int(cache[key]["ctas_per_sm"])
+        return c.ctas_per_sm
+    n = int(rays.shape[0])
+    bits = empty_bits(n, rays.device)
+    timings = {}
+    for cand in candidates:
+        c.ctas_per_sm = cand
+        model.infer(rays, bits, tlas=tlas, max_q=max_q)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            model.infer(rays, bits, tlas=tlas, max_q=max_q)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        timings[cand] = best
+    choice = min(timings, key=timings.get)
+    c.ctas_per_sm = choice
+    cache[key] = {"ctas_per_sm": choice, "ms": timings}
+    try:
+        with open(cache_path, "w") as f:
+            json.dump(cache, f, indent=1)
+    except OSError:
+        pass
+    return choice

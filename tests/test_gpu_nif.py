@@ -111,7 +111,8 @@ def test_encode_fp32_matches_oracle():
 
 @pytest.mark.parametrize("mlp_dt,grid_dt,tol,ctas", [("f32", "f32", 1e-4, 0), ("f16", "f32", 2e-2, 0),
                                                       ("f16", "f16", 2e-2, 0), ("bf16", "f32", 6e-2, 0),
-                                                      ("f16", "f16", 2e-2, 3), ("bf16", "f16", 6e-2, 3)])
+                                                      ("f16", "f16", 2e-2, 3), ("bf16", "f16", 6e-2, 3),
+                                                      ("f16", "f16", 2e-2, 4), ("bf16", "f32", 6e-2, 4)])
 def test_logits_match_oracle(mlp_dt, grid_dt, tol, ctas):
     w = _tiny(n_rays=6000)
     model, om = _build(w.res, 2, 19, w.aabb, w.grid_values, [w.weights], grid_dt=grid_dt, mlp_dt=mlp_dt,
