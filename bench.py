@@ -45,6 +45,12 @@ WORKLOADS = {
 }
 
 
+# DRAM bytes (read + write) of one k_fused_tm<2, half, F16, 4 CTAs/SM> launch
+# on the room workload, from the ncu capture summarised in
+# profiles/fused_tm_room.md; reported only for that exact kernel and workload.
+ROOM_FUSED_TRAFFIC_BYTES = 2.087331e9 + 4.31488e6
+
+
 def per_query_cost(cfg):
     """Algorithmic grid-tap bytes and MLP flops of one pair."""
     esz = 2 if cfg.grid_dtype == 1 else 4
@@ -422,7 +428,10 @@ def run_ours(args):
         "stages_ms": subs,
         "roofline": {"kernel": "nif fused encode+MLP (tcgen05)", "bound": "hbm",
                      "achieved": ach_gbs, "peak": hbm, "unit": "GB/s", "frac": ach_gbs / hbm,
-                     "traffic": None, "peak_source": src,
+                     "traffic": (ROOM_FUSED_TRAFFIC_BYTES
+                                 if args.workload == "room" and model.cfg.ctas_per_sm == 4 else None),
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch",
+                     "peak_source": src,
                      "tensor_tflops": tc_tflops, "tensor_peak_tflops": tflops,
                      "tensor_frac": tc_tflops / tflops,
                      "alg_bytes_per_query": alg_bytes, "flops_per_query": flops_q},

@@ -216,7 +216,8 @@ nif_status nif_check(void* d_ws, int64_t* detail, void* stream);
  * lo <= o <= hi; overlap iff max(tmin, entry) <= min(tmax, exit)), classify it
  * inner when entry <= tmin, and write the pairs grouped by network, objects
  * ascending inside a group (pairs of one object in no fixed order).  d_tlas is a
- * bvh_build_boxes hierarchy over the object boxes, or NULL to test every box.
+ * bvh_build_boxes hierarchy built from m->d_obj_aabb (its leaves hold copies of
+ * those boxes and are what is tested), or NULL to test every box.
  * Outputs: d_ray_id, d_qobj (capacity max_q), d_group_off [n_nets+1],
  * *d_count (device int64) = number of queries found.  Found > max_q is a
  * device error NIF_ERR_WORKSPACE (the lists then hold max_q of them). */

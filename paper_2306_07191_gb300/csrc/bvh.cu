@@ -288,7 +288,7 @@ __device__ __forceinline__ void child_box(const BuildWs& w, const uint32_t* orde
 // Bottom-up boxes and surface-area costs; the second thread to reach a node
 // processes it.  A subtree of <= kLeafMax primitives whose leaf cost is not
 // above its split cost is marked for collapse into one leaf.
-__global__ void k_bottom_up(BuildWs w, const uint32_t* order, int64_t n) {
+__global__ void k_bottom_up(BuildWs w, const uint32_t* order, int64_t n, int leaf_max) {
   int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (k >= n) return;
   int32_t node = w.leaf_parent[k];
@@ -308,7 +308,7 @@ __global__ void k_bottom_up(BuildWs w, const uint32_t* order, int64_t n) {
     else csplit += c0 + c1;
     int cnt = w.last[node] - w.first[node] + 1;
     float cleaf = kCostIntersect * cnt;
-    bool col = cnt <= kLeafMax && cleaf <= csplit;
+    bool col = cnt <= leaf_max && cleaf <= csplit;
     w.collapse[node] = col ? 1 : 0;
     lo.w = col ? cleaf : csplit;
     w.node_lo[node] = lo;
@@ -466,7 +466,9 @@ nif_status build(int kind, const float* verts, const int32_t* tris, const float*
     k_karras<<<ceil_div(n - 1, T), T, 0, st>>>(sorted_keys, n, w.left, w.right, w.parent,
                                                w.leaf_parent, w.first, w.last);
     NIF_LAUNCH_CHECK();
-    k_bottom_up<<<blocks, T, 0, st>>>(w, order, n);
+    // box hierarchies (the NIF top level) keep leaves of at most 2 boxes: a
+    // failed leaf test costs about as much as a node test there
+    k_bottom_up<<<blocks, T, 0, st>>>(w, order, n, kind == 0 ? kLeafMax : 2);
     NIF_LAUNCH_CHECK();
     k_emit_nodes<<<ceil_div(n - 1, T), T, 0, st>>>(w, order, n, (Node*)(base + off_nodes));
     NIF_LAUNCH_CHECK();

@@ -50,13 +50,27 @@ __device__ __forceinline__ void for_each_pair(const NifParams& p, const char* tl
   }
   const bvh::Node* nodes = reinterpret_cast<const bvh::Node*>(tlas + H->off_nodes);
   const float4* prims = reinterpret_cast<const float4*>(tlas + H->off_prims);
-  bvh::RayF rf;
-  rf.o = make_float3(r.ox, r.oy, r.oz);
-  rf.d = make_float3(r.dx, r.dy, r.dz);
+  // culling: t = lo * (1/d) - o * (1/d) with one FMA per bound, exit widened
+  // as in bvh::cull (conservative; exact decisions are taken at the leaves)
   auto inv = [](float x) { return 1.0f / (fabsf(x) > 1e-30f ? x : copysignf(1e-30f, x)); };
-  rf.id = make_float3(inv(r.dx), inv(r.dy), inv(r.dz));
-  rf.tmin = r.tmin;
-  rf.tmax = r.tmax;
+  const float idx = inv(r.dx), idy = inv(r.dy), idz = inv(r.dz);
+  const float ox = r.ox * idx, oy = r.oy * idy, oz = r.oz * idz;
+  auto cull2 = [&](float lox, float hix, float loy, float hiy, float loz, float hiz) {
+    const float x0 = fmaf(lox, idx, -ox), x1 = fmaf(hix, idx, -ox);
+    const float y0 = fmaf(loy, idy, -oy), y1 = fmaf(hiy, idy, -oy);
+    const float z0 = fmaf(loz, idz, -oz), z1 = fmaf(hiz, idz, -oz);
+    const float tn = fmaxf(fmaxf(fminf(x0, x1), fminf(y0, y1)), fmaxf(fminf(z0, z1), r.tmin));
+    float tf = fminf(fminf(fmaxf(x0, x1), fmaxf(y0, y1)), fmaxf(z0, z1));
+    tf = fminf(tf + fabsf(tf) * 4e-6f, r.tmax);
+    return tn <= tf;
+  };
+  // leaf test on the box stored in the top level (a copy of the object's AABB)
+  auto test_leaf = [&](const float4 lo, const float4 hi) {
+    const float bx[6] = {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z};
+    bool inner;
+    if (slab_decide(o, d, rcp, exact_only, r.tmin, r.tmax, bx, inner))
+      emit(static_cast<uint32_t>(__float_as_int(lo.w)), inner);
+  };
   int32_t stack[bvh::kStack];
   int sp = 0;
   int32_t ref = H->root;
@@ -66,9 +80,8 @@ __device__ __forceinline__ void for_each_pair(const NifParams& p, const char* tl
       const float4* np = reinterpret_cast<const float4*>(nodes + ref);
       float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
       int4 dd = __ldg(reinterpret_cast<const int4*>(np + 3));
-      float t0, t1;
-      bool h0 = bvh::cull(a.x, a.y, a.z, a.w, c.x, c.y, rf, rf.tmax, t0);
-      bool h1 = bvh::cull(b.x, b.y, b.z, b.w, c.z, c.w, rf, rf.tmax, t1);
+      bool h0 = cull2(a.x, a.y, a.z, a.w, c.x, c.y);
+      bool h1 = cull2(b.x, b.y, b.z, b.w, c.z, c.w);
       if (h0 && h1) {
         if (sp < bvh::kStack) stack[sp++] = dd.y;
         ref = dd.x;
@@ -80,7 +93,7 @@ __device__ __forceinline__ void for_each_pair(const NifParams& p, const char* tl
       int32_t code = ~ref;
       int32_t first = code >> 3, count = (code & 7) + 1;
       for (int32_t k = first; k < first + count; ++k)
-        test(static_cast<uint32_t>(__float_as_int(__ldg(prims + 3 * (int64_t)k).w)));
+        test_leaf(__ldg(prims + 3 * (int64_t)k), __ldg(prims + 3 * (int64_t)k + 1));
     }
     if (sp == 0) break;
     ref = stack[--sp];
@@ -564,8 +577,9 @@ nif_status launch_frontend(const NifParams& p, const void* tlas, const nif_ray* 
   uint32_t* cnt = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + kErrBytes);
   uint32_t* cur = cnt + align_up(n_buckets, 64);
   NIF_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * n_buckets, st));
-  int blocks = static_cast<int>(std::min<int64_t>(ceil_div(n, 256), sm_count() * 8));
-  if (blocks < 1) blocks = 1;
+  // one ray per thread: blocks retire independently, so a block with a few
+  // long traversals does not hold a grid-stride loop's barrier
+  int blocks = static_cast<int>(std::max<int64_t>(1, ceil_div(n, 256)));
   size_t sh1 = sizeof(uint32_t) * n_buckets;
   const char* tl = static_cast<const char*>(tlas);
   uint32_t* slots = static_cast<uint32_t*>(slot_area);
