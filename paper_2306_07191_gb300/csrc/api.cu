@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <unordered_map>
 
 #include "nif_kernels.cuh"
 
@@ -25,6 +26,13 @@ nif_status fail(nif_status code, const char* fmt, ...) {
   vsnprintf(g_err, sizeof(g_err), fmt, ap);
   va_end(ap);
   return code;
+}
+
+size_t& smem_granted(const void* kernel) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, size_t> granted;
+  std::lock_guard<std::mutex> lock(mu);
+  return granted[kernel];  // node-based map: the reference stays valid
 }
 
 int sm_count() {

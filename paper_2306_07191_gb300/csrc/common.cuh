@@ -50,6 +50,22 @@ __device__ __forceinline__ void raise_error(DevError* e, int32_t code, int64_t d
   if (e && atomicCAS(&e->code, 0, code) == 0) e->detail = detail;
 }
 
+// Raise a kernel's dynamic shared-memory limit only when a launch needs more
+// than any earlier one, so launches inside CUDA-graph capture make no
+// attribute call once the kernel has run before.
+// (The grant is remembered per kernel address, per process.)
+size_t& smem_granted(const void* kernel);  // guarded by a mutex in api.cu
+
+template <typename Kernel>
+inline cudaError_t ensure_smem(Kernel kern, size_t bytes) {
+  size_t& granted = smem_granted(reinterpret_cast<const void*>(kern));
+  if (bytes <= granted) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(bytes));
+  if (e == cudaSuccess) granted = bytes;
+  return e;
+}
+
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

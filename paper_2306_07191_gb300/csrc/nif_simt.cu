@@ -648,7 +648,7 @@ nif_status launch_fwd_f32(const NifParams& p, const nif_ray* rays, const uint32_
   if (nq_hint >= 0) blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(blocks, ceil_div(nq_hint, kTile) + p.n_nets)));
   NIF_DISPATCH_FG(p, {
     auto kern = k_mlp_fwd_f32<F, TG>;
-    NIF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    NIF_CUDA_TRY(ensure_smem(kern, sh));
     kern<<<blocks, kTile, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, saved, ld_saved);
   });
   NIF_LAUNCH_CHECK();
@@ -670,7 +670,7 @@ nif_status launch_bwd_f32(const NifParams& p, const int64_t* goff, int64_t nq, c
   int maxf = p.K > p.width ? p.K : p.width;
   size_t sh = sizeof(float) * kLd * (p.K + p.n_hidden * p.width + p.width + maxf);
   if (sh > 220 * 1024) return fail(NIF_ERR_UNSUPPORTED, "mlp backward: network too large for one tile");
-  NIF_CUDA_TRY(cudaFuncSetAttribute(k_mlp_bwd_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+  NIF_CUDA_TRY(ensure_smem(k_mlp_bwd_f32, sh));
   int blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(sm_count() * 2, ceil_div(nq, kTile) + p.n_nets)));
   k_mlp_bwd_f32<<<blocks, kTile, sh, st>>>(p, goff, saved, nq, dz, wgrad, dx);
   NIF_LAUNCH_CHECK();

@@ -807,7 +807,7 @@ static nif_status launch_tm(const NifParams& p, const nif_ray* rays, const uint3
   tc::LayoutTm L = tc::make_layout_tm(Kp, p.width, p.n_hidden, p.n_nets);
   size_t sh = L.total + 1024;
   auto go = [&](auto kern) -> nif_status {
-    NIF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    NIF_CUDA_TRY(ensure_smem(kern, sh));
     kern<<<blocks, tc::kThreads, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, err, Kp);
     return NIF_OK;
   };
@@ -845,7 +845,7 @@ static nif_status launch_dt(const NifParams& p, const nif_ray* rays, const uint3
   size_t sh = L.total + 1024;
   if (occ3 && p.F == 2) {
     auto launch3 = [&](auto kern) -> nif_status {
-      NIF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+      NIF_CUDA_TRY(ensure_smem(kern, sh));
       kern<<<blocks, tc::kThreads, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, err, Kp);
       return NIF_OK;
     };
@@ -857,7 +857,7 @@ static nif_status launch_dt(const NifParams& p, const nif_ray* rays, const uint3
   }
   NIF_DISPATCH_FG_TC(p, {
     auto kern = tc::k_fused<F, TG, DT, 2>;
-    NIF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh));
+    NIF_CUDA_TRY(ensure_smem(kern, sh));
     kern<<<blocks, tc::kThreads, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, err, Kp);
   });
   NIF_LAUNCH_CHECK();

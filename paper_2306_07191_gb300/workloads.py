@@ -112,3 +112,35 @@ def area_light_samples(rng: np.random.Generator, n_pixels: int, spp: int) -> np.
     a = rng.uniform(size=(n_pixels * spp, 1))
     b = rng.uniform(size=(n_pixels * spp, 1))
     return (c[None, :] + a * eu[None, :] + b * ev[None, :]).astype(np.float32)
+
+
+@dataclass
+class GroupedObjects:
+    scene: synth.Scene
+    rays: np.ndarray    # [N, 8], rays of object k are contiguous
+    counts: np.ndarray  # pairs (= rays) per object, int64 [n_obj]
+
+
+def grouped_objects(n_obj: int = 32, total_rays: int = 8_000_000, seed: int = 11,
+                    tri_min: int = 10_000, tri_max: int = 500_000, alpha: float = 1.5,
+                    spacing: float = 8.0) -> GroupedObjects:
+    """n_obj displaced icospheres with triangle counts log-uniform in
+    [tri_min, tri_max] (frequency n = round(sqrt(T / 20))), placed on a line
+    `spacing` apart; object k (1-based) gets round(total * k^-alpha / sum_j
+    j^-alpha) rays (the remainder goes to k = 1), each from a sphere of 1.5x the
+    box half-diagonal around its box, aimed at a uniform point in the box."""
+    rng = np.random.default_rng(seed)
+    tris = np.exp(rng.uniform(np.log(tri_min), np.log(tri_max), size=n_obj))
+    freqs = np.maximum(1, np.round(np.sqrt(tris / 20.0))).astype(int)
+    meshes = [synth.displaced_icosphere(int(f), rng, centre=(k * spacing, 0.0, 0.0))
+              for k, f in enumerate(freqs)]
+    sc = synth.build_scene(meshes)
+    w = np.arange(1, n_obj + 1, dtype=np.float64) ** (-alpha)
+    counts = np.round(total_rays * w / w.sum()).astype(np.int64)
+    counts[0] += total_rays - counts.sum()
+    rays = []
+    for k in range(n_obj):
+        box = sc.obj_aabb[k]
+        half_diag = 0.5 * float(np.linalg.norm(box[3:] - box[:3]))
+        rays.append(synth.aimed_rays(rng, int(counts[k]), box, 1.5 * half_diag))
+    return GroupedObjects(sc, np.ascontiguousarray(np.concatenate(rays)), counts)
