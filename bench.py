@@ -87,7 +87,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -181,7 +181,7 @@ def oracle_rays_per_s(n_rays: int, seed: int = 5):
     return n_rays / dt, dt, len(rid)
 
 
-def cpu_baseline(n_rays: int = 150000):
+def cpu_baseline(n_rays: int = 600000):
     """Run the oracle timing in a child process limited to one BLAS thread."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     code = ("import json,sys; sys.path.insert(0, %r); import bench; "
