@@ -126,6 +126,17 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def reduce_max(x: float, world: int, device) -> float:
+    """Max of a per-rank value over all ranks (the slowest replica's time)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -401,16 +412,9 @@ def run_ours(args):
 
     e2e_ms, _ = timed(e2e_step, args.steps, args.warmup)
 
-    def reduce_max(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    ms = reduce_max(statistics.mean(nif_ms))
-    bms = reduce_max(statistics.mean(bvh_ms))
-    ems = reduce_max(statistics.mean(e2e_ms))
+    ms = reduce_max(statistics.mean(nif_ms), world, dev)
+    bms = reduce_max(statistics.mean(bvh_ms), world, dev)
+    ems = reduce_max(statistics.mean(e2e_ms), world, dev)
     value = world * n / (ms * 1e-3)
     hbm, tflops, src = _peaks()
     fused_s = subs["fused_ms"] * 1e-3

@@ -331,6 +331,14 @@ nif_status nif_train_step(nif_model_desc* m, nif_optim_desc* o, const nif_ray* d
                           const int64_t* d_group_off, const uint8_t* d_label, int64_t nq,
                           float* d_loss, void* d_ws, size_t ws_bytes, void* stream);
 
+/* Failure-detection self-test (no counterpart in the paper): runs the
+ * bounded mbarrier wait that guards every tensor-core wait in the library on a
+ * barrier nothing arrives on, with a limit of limit_cycles SM clocks (at most
+ * 2^33).  The wait expires, the kernel records NIF_ERR_TIMEOUT (detail 42) in
+ * the workspace's error word and returns normally; nif_check then reports it
+ * and the context stays usable.  No fault, trap or hang is involved. */
+nif_status nif_wait_selftest(void* d_ws, size_t ws_bytes, int64_t limit_cycles, void* stream);
+
 /* ------------------------------------------------------------ inputs --
  * Seeded uniform fill for large parameter tables such as the grid latents'
  * U(-1e-4, 1e-4) initialisation (Sec. 5 "Initialization"): d_out[i] =

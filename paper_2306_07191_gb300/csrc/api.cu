@@ -436,6 +436,15 @@ nif_status nif_train_step(nif_model_desc* m, nif_optim_desc* o, const nif_ray* d
 
 }  // extern "C"
 
+// ------------------------------------------------------------ self-test
+extern "C" nif_status nif_wait_selftest(void* d_ws, size_t ws_bytes, int64_t limit_cycles,
+                                        void* stream) {
+  NIF_CHECK_ARG(d_ws != nullptr && ws_bytes >= kErrBytes, "nif_wait_selftest: workspace too small");
+  NIF_CHECK_ARG(limit_cycles > 0 && limit_cycles <= (int64_t(1) << 33),
+                "nif_wait_selftest: limit must be in (0, 2^33] cycles");
+  return launch_wait_selftest(static_cast<DevError*>(d_ws), limit_cycles, as_stream(stream));
+}
+
 // ------------------------------------------------------------ input fill
 // Seeded uniform values for large parameter tables (an input generator, not
 // part of the method): value(i) = scale * (2u - 1) with u the top 24 bits of

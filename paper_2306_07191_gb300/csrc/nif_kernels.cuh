@@ -34,6 +34,7 @@ nif_status launch_fwd_tc(const NifParams& p, const nif_ray* rays, const uint32_t
                          uint32_t* occ, float* logits, int tile_m, int ctas_per_sm,
                          DevError* err, cudaStream_t st);
 nif_status check_tc_shape(const NifParams& p);
+nif_status launch_wait_selftest(DevError* err, long long limit_cycles, cudaStream_t st);
 
 nif_status launch_loss(const float* z, const uint8_t* label, int64_t nq, float scale, float* dz,
                        float* loss, cudaStream_t st);

@@ -55,16 +55,32 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: gives up after ~2 s and records NIF_ERR_TIMEOUT.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, DevError* err) {
+// Bounded wait: gives up after `limit` SM cycles (~2 s by default) and
+// records NIF_ERR_TIMEOUT with `site` as the detail.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, DevError* err,
+                                          long long limit = kWaitCycles, int64_t site = 1) {
   long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > kWaitCycles) {
-      raise_error(err, NIF_ERR_TIMEOUT, 1);
+    if (clock64() - t0 > limit) {
+      raise_error(err, NIF_ERR_TIMEOUT, site);
       return false;
     }
   }
   return true;
+}
+
+// Self-test of the bounded wait: waits on an mbarrier that nothing arrives
+// on, so the wait must give up after `limit` cycles and record the timeout;
+// the kernel then returns normally and the context stays usable.
+__global__ void k_wait_selftest(DevError* err, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(smem_u32(&bar), 0, err, limit, 42);
+  __syncthreads();
 }
 __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -888,6 +904,12 @@ nif_status launch_fwd_tc(const NifParams& p, const nif_ray* rays, const uint32_t
   if (p.mlp_dtype == NIF_BF16) return launch_dt<NIF_BF16>(p, rays, ray_id, qobj, goff, blocks, per_sm, occ, logits, err, st);
   if (p.mlp_dtype == NIF_E4M3) return launch_dt<NIF_E4M3>(p, rays, ray_id, qobj, goff, blocks, per_sm, occ, logits, err, st);
   return fail(NIF_ERR_UNSUPPORTED, "tensor-core path: mlp dtype %d", p.mlp_dtype);
+}
+
+nif_status launch_wait_selftest(DevError* err, long long limit_cycles, cudaStream_t st) {
+  tc::k_wait_selftest<<<1, 32, 0, st>>>(err, limit_cycles);
+  NIF_LAUNCH_CHECK();
+  return NIF_OK;
 }
 
 }  // namespace nif
