@@ -22,9 +22,14 @@
 // 8-row x 16-byte core matrices, 128 contiguous bytes each; core matrices
 // adjacent along K are 128 B apart (leading byte offset) and 8-row groups are
 // K*esize*8 B apart (stride byte offset).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_fp8.h>
 
+#include <mutex>
+
 #include <algorithm>
+#include <cstring>
 #include <type_traits>
 
 #include "nif_params.cuh"
@@ -167,6 +172,28 @@ __device__ __forceinline__ void mma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_
       : "memory");
 }
 
+// TMA: one tiled tensor copy global -> shared, completing on an mbarrier.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
+                                            int c2, int c3, int c4, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+      : "memory");
+}
+
+// Tensor maps of the hidden layers' weights (all networks), one per layer:
+// dimensions (k within a 16-byte row, row within 8, 16-byte column block,
+// 8-row group, network), so that one box of a network lands in shared memory
+// exactly in the K-major core-matrix layout the MMA reads.
+struct WeightMaps {
+  CUtensorMap m[8];
+};
+
 // Shared-memory matrix descriptor: K-major, no swizzle.
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
@@ -256,11 +283,13 @@ template <int F, typename TG, int DT, int kOcc>
 __global__ void __launch_bounds__(kThreads, kOcc)
     k_fused(const __grid_constant__ NifParams p, const nif_ray* __restrict__ rays, const uint32_t* __restrict__ ray_id,
             const uint32_t* __restrict__ qobj, const int64_t* __restrict__ goff,
-            uint32_t* __restrict__ occ, float* __restrict__ logits, DevError* err, int Kp) {
+            uint32_t* __restrict__ occ, float* __restrict__ logits, DevError* err, int Kp,
+            const __grid_constant__ WeightMaps wm, int use_tma) {
   using O = Op<DT>;
   constexpr int esz = O::esz;
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t s_bar;
+  __shared__ __align__(8) uint64_t s_wbar;  // weight loads (TMA)
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
   __shared__ int64_t s_pre[kMaxGroups + 1];
@@ -275,8 +304,11 @@ __global__ void __launch_bounds__(kThreads, kOcc)
   const uint32_t ncols = W <= 32 ? 32 : (W <= 64 ? 64 : (W <= 128 ? 128 : 256));
 
   if (warp == 0) tmem_alloc(smem_u32(&s_tmem), ncols);
+  const uint32_t wbar = smem_u32(&s_wbar);
+  uint32_t wphase = 0;
   if (tid == 0) {
     mbar_init(bar, 1);
+    mbar_init(wbar, 1);
     fence_mbar_init();
     s_abort = 0;
   }
@@ -302,23 +334,34 @@ __global__ void __launch_bounds__(kThreads, kOcc)
     const int64_t qend = goff[g + 1];
     const float* sc = p.scales ? p.scales + static_cast<int64_t>(g) * (H + 1) * 2 : nullptr;
 
-    // ---- weights of network g into shared memory (B operands, K-major)
+    // ---- weights of network g into shared memory (B operands, K-major):
+    // TMA boxes that land in the core-matrix layout, or a conversion loop
     if (g != cur_g) {
       const int64_t wbase = static_cast<int64_t>(g) * p.P;
-      int64_t off = 0;
-      for (int l = 0; l < H; ++l) {
-        const int fin = l == 0 ? K : W;
-        const int fpad = l == 0 ? Kp : W;
-        uint8_t* wt = smem + L.w_off(l);
-        for (int e = tid; e < W * fpad; e += kThreads) {
-          const int n = e / fpad, k = e % fpad;
-          const float v = k < fin ? O::load(p.weights, wbase + off + static_cast<int64_t>(n) * fin + k) : 0.f;
-          store_elem<DT>(wt, n, k, fpad, v);
+      const int64_t off_out = static_cast<int64_t>(W) * K + static_cast<int64_t>(H - 1) * W * W;
+      if (use_tma) {
+        if (tid == 0) {
+          mbar_expect_tx(wbar, L.w1_bytes + static_cast<uint32_t>(H - 1) * L.wl_bytes);
+          for (int l = 0; l < H; ++l) tma_load_5d(smem_u32(smem + L.w_off(l)), &wm.m[l], 0, 0, 0, 0, g, wbar);
         }
-        off += static_cast<int64_t>(W) * fin;
+        if (!mbar_wait(wbar, wphase, err, kWaitCycles, 2)) s_abort = 1;
+        wphase ^= 1u;
+      } else {
+        int64_t off = 0;
+        for (int l = 0; l < H; ++l) {
+          const int fin = l == 0 ? K : W;
+          const int fpad = l == 0 ? Kp : W;
+          uint8_t* wt = smem + L.w_off(l);
+          for (int e = tid; e < W * fpad; e += kThreads) {
+            const int n = e / fpad, k = e % fpad;
+            const float v = k < fin ? O::load(p.weights, wbase + off + static_cast<int64_t>(n) * fin + k) : 0.f;
+            store_elem<DT>(wt, n, k, fpad, v);
+          }
+          off += static_cast<int64_t>(W) * fin;
+        }
       }
       for (int e = tid; e < W; e += kThreads) {
-        float v = O::load(p.weights, wbase + off + e);
+        float v = O::load(p.weights, wbase + off_out + e);
         wout[e] = sc ? v * sc[2 * H + 1] : v;
       }
       cur_g = g;
@@ -534,12 +577,14 @@ __global__ void __launch_bounds__(kThreads, kOcc)
     k_fused_tm(const __grid_constant__ NifParams p, const nif_ray* __restrict__ rays,
                const uint32_t* __restrict__ ray_id, const uint32_t* __restrict__ qobj,
                const int64_t* __restrict__ goff, uint32_t* __restrict__ occ,
-               float* __restrict__ logits, DevError* err, int Kp) {
+               float* __restrict__ logits, DevError* err, int Kp,
+               const __grid_constant__ WeightMaps wm, int use_tma) {
   using O = Op<DT>;
   static_assert(O::esz == 2 && F % 2 == 0, "TMEM activations need 16-bit operands and even F");
   constexpr int FP = F / 2;  // packed 32-bit columns per level lookup
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ __align__(8) uint64_t s_bar;
+  __shared__ __align__(8) uint64_t s_wbar;  // weight loads (TMA)
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
 
@@ -553,8 +598,11 @@ __global__ void __launch_bounds__(kThreads, kOcc)
   const uint32_t ncols = tm_cols(Kp, W);
 
   if (warp == 0) tmem_alloc(smem_u32(&s_tmem), ncols);
+  const uint32_t wbar = smem_u32(&s_wbar);
+  uint32_t wphase = 0;
   if (tid == 0) {
     mbar_init(bar, 1);
+    mbar_init(wbar, 1);
     fence_mbar_init();
     s_abort = 0;
   }
@@ -586,24 +634,35 @@ __global__ void __launch_bounds__(kThreads, kOcc)
     const int64_t q0 = goff[g] + (t - s_pre[g]) * kM;
     const int64_t qend = goff[g + 1];
 
-    // ---- weights of network g into shared memory (B operands, K-major)
+    // ---- weights of network g into shared memory (B operands, K-major):
+    // TMA boxes that land in the core-matrix layout, or a conversion loop
     if (g != cur_g) {
       const int64_t wbase = static_cast<int64_t>(g) * p.P;
-      int64_t off = 0;
-      for (int l = 0; l < H; ++l) {
-        const int fin = l == 0 ? K : W;
-        const int fpad = l == 0 ? Kp : W;
-        uint8_t* wt = smem + L.w_off(l);
-        for (int e = tid; e < W * fpad; e += kThreads) {
-          const int n = e / fpad, k = e % fpad;
-          const float v = k < fin ? O::load(p.weights, wbase + off + static_cast<int64_t>(n) * fin + k) : 0.f;
-          store_elem<DT>(wt, n, k, fpad, v);
+      const int64_t off_out = static_cast<int64_t>(W) * K + static_cast<int64_t>(H - 1) * W * W;
+      if (use_tma) {
+        if (tid == 0) {
+          mbar_expect_tx(wbar, L.w1_bytes + static_cast<uint32_t>(H - 1) * L.wl_bytes);
+          for (int l = 0; l < H; ++l) tma_load_5d(smem_u32(smem + L.w_off(l)), &wm.m[l], 0, 0, 0, 0, g, wbar);
         }
-        off += static_cast<int64_t>(W) * fin;
+        if (!mbar_wait(wbar, wphase, err, kWaitCycles, 2)) s_abort = 1;
+        wphase ^= 1u;
+      } else {
+        int64_t off = 0;
+        for (int l = 0; l < H; ++l) {
+          const int fin = l == 0 ? K : W;
+          const int fpad = l == 0 ? Kp : W;
+          uint8_t* wt = smem + L.w_off(l);
+          for (int e = tid; e < W * fpad; e += kThreads) {
+            const int n = e / fpad, k = e % fpad;
+            const float v = k < fin ? O::load(p.weights, wbase + off + static_cast<int64_t>(n) * fin + k) : 0.f;
+            store_elem<DT>(wt, n, k, fpad, v);
+          }
+          off += static_cast<int64_t>(W) * fin;
+        }
+        fence_proxy_async();
       }
-      for (int e = tid; e < W; e += kThreads) wout[e] = O::load(p.weights, wbase + off + e);
+      for (int e = tid; e < W; e += kThreads) wout[e] = O::load(p.weights, wbase + off_out + e);
       cur_g = g;
-      fence_proxy_async();
     }
 
     // ---- step a1/a2: encode 128 queries straight into TMEM
@@ -778,6 +837,58 @@ __global__ void __launch_bounds__(kThreads, kOcc)
 #define NIF_TC_SMEM_ACTIVATIONS 0
 #endif
 static bool tc_activations_in_tmem() { return NIF_TC_SMEM_ACTIVATIONS == 0; }
+// Weights are loaded by TMA unless built with -DNIF_TC_WEIGHT_LOOP=1.
+#ifndef NIF_TC_WEIGHT_LOOP
+#define NIF_TC_WEIGHT_LOOP 0
+#endif
+static bool tc_weights_by_tma() { return NIF_TC_WEIGHT_LOOP == 0; }
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+  });
+  return fn;
+}
+
+// Tensor maps for TMA weight loads; false (use the loop) when the shapes or
+// alignments do not allow them.
+static bool make_weight_maps(const NifParams& p, int esz, int Kp, tc::WeightMaps* wm) {
+  std::memset(wm, 0, sizeof(*wm));
+  auto enc = tensor_map_encoder();
+  const int H = p.n_hidden, W = p.width, cb = 16 / esz;
+  if (!enc || H < 1 || H > 8 || W % 8 != 0 || p.n_nets < 1) return false;
+  if ((static_cast<int64_t>(p.P) * esz) % 16 != 0) return false;
+  const CUtensorMapDataType dt = esz == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8
+                                 : (p.mlp_dtype == NIF_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                            : CU_TENSOR_MAP_DATA_TYPE_FLOAT16);
+  for (int l = 0; l < H; ++l) {
+    const int fin = l == 0 ? p.K : W, fpad = l == 0 ? Kp : W;
+    if (fin % cb != 0 || (fin * esz) % 16 != 0) return false;
+    const int64_t off = l == 0 ? 0 : static_cast<int64_t>(p.K) * W + static_cast<int64_t>(l - 1) * W * W;
+    char* base = static_cast<char*>(const_cast<void*>(p.weights)) + off * esz;
+    if (reinterpret_cast<uintptr_t>(base) % 16 != 0) return false;
+    cuuint64_t dims[5] = {static_cast<cuuint64_t>(cb), 8, static_cast<cuuint64_t>(fin / cb),
+                          static_cast<cuuint64_t>(W / 8), static_cast<cuuint64_t>(p.n_nets)};
+    cuuint64_t strides[4] = {static_cast<cuuint64_t>(fin) * esz, 16,
+                             static_cast<cuuint64_t>(8 * fin) * esz,
+                             static_cast<cuuint64_t>(p.P) * esz};
+    cuuint32_t box[5] = {static_cast<cuuint32_t>(cb), 8, static_cast<cuuint32_t>(fpad / cb),
+                         static_cast<cuuint32_t>(W / 8), 1};
+    cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+    if (enc(&wm->m[l], dt, 5, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
+}
 
 nif_status check_tc_shape(const NifParams& p) {
   const int esz = p.mlp_dtype == NIF_E4M3 ? 1 : 2;
@@ -822,9 +933,12 @@ static nif_status launch_tm(const NifParams& p, const nif_ray* rays, const uint3
   const int Kp = (p.K + 15) / 16 * 16;
   tc::LayoutTm L = tc::make_layout_tm(Kp, p.width, p.n_hidden, p.n_nets);
   size_t sh = L.total + 1024;
+  tc::WeightMaps wm;
+  const int use_tma = make_weight_maps(p, 2, Kp, &wm) && tc_weights_by_tma() ? 1 : 0;
   auto go = [&](auto kern) -> nif_status {
     NIF_CUDA_TRY(ensure_smem(kern, sh));
-    kern<<<blocks, tc::kThreads, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, err, Kp);
+    kern<<<blocks, tc::kThreads, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, err, Kp, wm,
+                                           use_tma);
     return NIF_OK;
   };
   nif_status s;
@@ -859,10 +973,13 @@ static nif_status launch_dt(const NifParams& p, const nif_ray* rays, const uint3
   const int Kp = (p.K + 32 / esz - 1) / (32 / esz) * (32 / esz);
   tc::Layout L = tc::make_layout(Kp, p.width, p.n_hidden, esz);
   size_t sh = L.total + 1024;
+  tc::WeightMaps wm;
+  const int use_tma = make_weight_maps(p, esz, Kp, &wm) && tc_weights_by_tma() ? 1 : 0;
   if (occ3 && p.F == 2) {
     auto launch3 = [&](auto kern) -> nif_status {
       NIF_CUDA_TRY(ensure_smem(kern, sh));
-      kern<<<blocks, tc::kThreads, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, err, Kp);
+      kern<<<blocks, tc::kThreads, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, err, Kp, wm,
+                                             use_tma);
       return NIF_OK;
     };
     nif_status s = p.grid_dtype == NIF_F16 ? launch3(tc::k_fused<2, __half, DT, 3>)
@@ -874,7 +991,7 @@ static nif_status launch_dt(const NifParams& p, const nif_ray* rays, const uint3
   NIF_DISPATCH_FG_TC(p, {
     auto kern = tc::k_fused<F, TG, DT, 2>;
     NIF_CUDA_TRY(ensure_smem(kern, sh));
-    kern<<<blocks, tc::kThreads, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, err, Kp);
+    kern<<<blocks, tc::kThreads, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, err, Kp, wm, use_tma);
   });
   NIF_LAUNCH_CHECK();
   return NIF_OK;
