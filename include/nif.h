@@ -120,7 +120,18 @@ typedef struct nif_model_desc {
   const float* d_scales; /* NIF_E4M3 only, else NULL */
   int32_t tile_m;        /* tensor-core rows per tile: 0 (=128), 128 or 256 */
   int32_t ctas_per_sm;   /* 0 = library default */
+  int32_t schedule;      /* tensor-core forward schedule (NIF_SCHED_*) */
 } nif_model_desc;
+
+/* Schedules of the 16-bit tensor-core forward (ignored elsewhere):
+ *   NIF_SCHED_AUTO    - the library's choice (NIF_SCHED_PIPELINED when its
+ *                       TMEM buffers let 4 CTAs share an SM, else SERIAL);
+ *   NIF_SCHED_SERIAL  - every warp of a CTA encodes a tile into TMEM, then
+ *                       the CTA runs the tile's layers;
+ *   NIF_SCHED_PIPELINED - encode warps fill one of two TMEM activation
+ *                       buffers while four MLP warps run the layers of the
+ *                       tile in the other one.  Same results. */
+enum { NIF_SCHED_AUTO = 0, NIF_SCHED_SERIAL = 1, NIF_SCHED_PIPELINED = 2 };
 
 /* Thread-local description of the last error returned on this thread. */
 const char* nif_last_error(void);

@@ -127,6 +127,9 @@ nif_status make_params(const nif_model_desc* m, NifParams* p) {
   p->weights = m->d_weights;
   p->P = weight_count(m);
   p->scales = m->mlp_dtype == NIF_E4M3 ? m->d_scales : nullptr;
+  NIF_CHECK_ARG(m->schedule >= NIF_SCHED_AUTO && m->schedule <= NIF_SCHED_PIPELINED,
+                "bad schedule %d", m->schedule);
+  p->schedule = m->schedule;
   return NIF_OK;
 }
 

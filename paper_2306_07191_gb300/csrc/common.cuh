@@ -45,6 +45,12 @@ struct DevError {
   int64_t detail;
 };
 constexpr size_t kErrBytes = 256;  // error word + counters, keeps later data aligned
+// Byte 64 of the head: tile counter of the persistent tensor-core forward,
+// zeroed by its launcher before every launch.
+constexpr size_t kTileCtrOffset = 64;
+inline uint32_t* tile_counter(DevError* e) {
+  return e ? reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(e) + kTileCtrOffset) : nullptr;
+}
 
 __device__ __forceinline__ void raise_error(DevError* e, int32_t code, int64_t detail) {
   if (e && atomicCAS(&e->code, 0, code) == 0) e->detail = detail;

@@ -29,6 +29,7 @@ struct NifParams {
   const void* weights;
   int64_t P;  // weights per network
   const float* scales;
+  int schedule;  // NIF_SCHED_* of the tensor-core forward
 };
 
 // Host: validate a descriptor and derive the device view.

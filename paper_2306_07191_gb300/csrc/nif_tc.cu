@@ -146,6 +146,47 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// 32 lanes x 32 columns of FP32 from TMEM, load and wait in one statement.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float v[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t v[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+
+// 32 lanes x 8 columns of FP32 from TMEM (this warp's lane quarter).
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float v[8]) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 // Stores of 32-bit words into this warp's TMEM lane quarter (one lane per
 // thread, consecutive columns from taddr), and the wait for their completion.
 __device__ __forceinline__ void tmem_st1(uint32_t taddr, uint32_t v) {
@@ -156,6 +197,11 @@ __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t v[8]) {
       "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
       "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
       : "memory");
+}
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t v[4]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(v[0]),
+               "r"(v[1]), "r"(v[2]), "r"(v[3])
+               : "memory");
 }
 __device__ __forceinline__ void tmem_wait_st() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
@@ -248,11 +294,26 @@ struct Op<NIF_E4M3> {
   }
 };
 
+__device__ __forceinline__ float act_fn_tc(const NifParams& p, float a) {
+  return a > 0.f ? a : (p.act == NIF_ACT_LEAKY ? p.slope * a : 0.f);
+}
+
 template <int DT>
 __device__ __forceinline__ void store_elem(uint8_t* tile, int row, int k, int kdim, float v) {
   using O = Op<DT>;
   typename O::T t = O::cvt(v);
   *reinterpret_cast<typename O::T*>(tile + tile_off(row, k, kdim, O::esz)) = t;
+}
+
+// Tile claiming of the persistent kernels.  With a counter (zeroed before
+// the launch) each CTA claims its next tile when it is ready for one, so the
+// CTAs an SM's warp scheduler favours take more tiles and all of them finish
+// together; without one, tiles go round-robin by block index.
+__device__ __forceinline__ int64_t first_tile(uint32_t* ctr) {
+  return ctr ? static_cast<int64_t>(atomicAdd(ctr, 1u)) : static_cast<int64_t>(blockIdx.x);
+}
+__device__ __forceinline__ int64_t next_tile(uint32_t* ctr, int64_t t) {
+  return ctr ? static_cast<int64_t>(atomicAdd(ctr, 1u)) : t + gridDim.x;
 }
 
 struct Layout {
@@ -284,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, kOcc)
     k_fused(const __grid_constant__ NifParams p, const nif_ray* __restrict__ rays, const uint32_t* __restrict__ ray_id,
             const uint32_t* __restrict__ qobj, const int64_t* __restrict__ goff,
             uint32_t* __restrict__ occ, float* __restrict__ logits, DevError* err, int Kp,
-            const __grid_constant__ WeightMaps wm, int use_tma) {
+            const __grid_constant__ WeightMaps wm, int use_tma, uint32_t* tile_ctr) {
   using O = Op<DT>;
   constexpr int esz = O::esz;
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -292,6 +353,7 @@ __global__ void __launch_bounds__(kThreads, kOcc)
   __shared__ __align__(8) uint64_t s_wbar;  // weight loads (TMA)
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
+  __shared__ int64_t s_next;  // next tile of this CTA
   __shared__ int64_t s_pre[kMaxGroups + 1];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -328,7 +390,9 @@ __global__ void __launch_bounds__(kThreads, kOcc)
   const int ecol0 = (warp >> 2) * (W / 2);
   const uint32_t taddr_row = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
 
-  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+  if (tid == 0) s_next = first_tile(tile_ctr);
+  __syncthreads();
+  for (int64_t t = s_next; t < n_tiles; t = s_next) {
     const int g = find_group(s_pre, p.n_nets, t);
     const int64_t q0 = goff[g] + (t - s_pre[g]) * kM;
     const int64_t qend = goff[g + 1];
@@ -527,6 +591,7 @@ __global__ void __launch_bounds__(kThreads, kOcc)
         }
       }
     }
+    if (tid == 0) s_next = next_tile(tile_ctr, t);
     __syncthreads();
   }
   __syncthreads();
@@ -578,7 +643,7 @@ __global__ void __launch_bounds__(kThreads, kOcc)
                const uint32_t* __restrict__ ray_id, const uint32_t* __restrict__ qobj,
                const int64_t* __restrict__ goff, uint32_t* __restrict__ occ,
                float* __restrict__ logits, DevError* err, int Kp,
-               const __grid_constant__ WeightMaps wm, int use_tma) {
+               const __grid_constant__ WeightMaps wm, int use_tma, uint32_t* tile_ctr) {
   using O = Op<DT>;
   static_assert(O::esz == 2 && F % 2 == 0, "TMEM activations need 16-bit operands and even F");
   constexpr int FP = F / 2;  // packed 32-bit columns per level lookup
@@ -587,6 +652,7 @@ __global__ void __launch_bounds__(kThreads, kOcc)
   __shared__ __align__(8) uint64_t s_wbar;  // weight loads (TMA)
   __shared__ uint32_t s_tmem;
   __shared__ int s_abort;
+  __shared__ int64_t s_next;  // next tile of this CTA
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int W = p.width, H = p.n_hidden, K = p.K;
@@ -629,7 +695,9 @@ __global__ void __launch_bounds__(kThreads, kOcc)
            (static_cast<uint32_t>(*reinterpret_cast<uint16_t*>(&y)) << 16);
   };
 
-  for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+  if (tid == 0) s_next = first_tile(tile_ctr);
+  __syncthreads();
+  for (int64_t t = s_next; t < n_tiles; t = s_next) {
     const int g = find_group(s_pre, p.n_nets, t);
     const int64_t q0 = goff[g] + (t - s_pre[g]) * kM;
     const int64_t qend = goff[g + 1];
@@ -823,9 +891,293 @@ __global__ void __launch_bounds__(kThreads, kOcc)
         }
       }
     }
+    if (tid == 0) s_next = next_tile(tile_ctr, t);
     __syncthreads();
   }
   __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
+// ------------------------------------------------ pipelined (two buffers)
+// Warp-specialised form of k_fused_tm.  kEW encode warps (kEW/4 per TMEM lane
+// quarter, splitting the levels) write tile i into activation buffer i % 2
+// while four MLP warps (one per lane quarter) run the hidden layers of tile
+// i - 1 from the other buffer, so the grid gathers of one tile overlap the
+// MMAs and epilogues of the previous one.  Hand-offs go through mbarriers:
+// full[b] (kEW warp arrivals: buffer b encoded) and empty[b] (one arrival:
+// the last MMA reading buffer b has completed).  Every wait is bounded.
+//
+// TMEM columns: accumulator [0, W), buffer b at W + b*ka, ka = max(Kp, W)/2.
+__host__ __device__ inline uint32_t ws_act_cols(int Kp, int W) {
+  return static_cast<uint32_t>((Kp > W ? Kp : W) / 2);
+}
+__host__ __device__ inline uint32_t ws_cols(int Kp, int W) {
+  const uint32_t need = static_cast<uint32_t>(W) + 2u * ws_act_cols(Kp, W);
+  return need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+// Named barrier 1 over the four MLP warps, OR-reducing a predicate, so that
+// every MLP thread takes the same branch after it.
+__device__ __forceinline__ bool mlp_sync_or(bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, 1, 128, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"(static_cast<uint32_t>(pred))
+      : "memory");
+  return r != 0;
+}
+
+// Named barrier 2 over the encode warps.
+template <int kEW>
+__device__ __forceinline__ void enc_sync() {
+  asm volatile("bar.sync 2, %0;" ::"n"(32 * kEW) : "memory");
+}
+
+template <int F, typename TG, int DT, int kEW, int kOcc>
+__global__ void __launch_bounds__(32 * (kEW + 4), kOcc)
+    k_fused_ws(const __grid_constant__ NifParams p, const nif_ray* __restrict__ rays,
+               const uint32_t* __restrict__ ray_id, const uint32_t* __restrict__ qobj,
+               const int64_t* __restrict__ goff, uint32_t* __restrict__ occ,
+               float* __restrict__ logits, DevError* err, int Kp,
+               const __grid_constant__ WeightMaps wm, int use_tma, uint32_t* tile_ctr) {
+  using O = Op<DT>;
+  static_assert(O::esz == 2 && F == 2, "pipelined schedule: 16-bit operands, two features");
+  static_assert(kEW % 4 == 0, "encode warps cover the four lane quarters");
+  constexpr int NP = kEW / 4;  // encode warps per lane quarter (level stride)
+  extern __shared__ __align__(1024) uint8_t smem[];
+  __shared__ __align__(8) uint64_t s_full[2];
+  __shared__ __align__(8) uint64_t s_empty[2];
+  __shared__ __align__(8) uint64_t s_mma;
+  __shared__ __align__(8) uint64_t s_wbar;
+  __shared__ uint32_t s_tmem;
+  __shared__ int64_t s_tile[2];  // tile encoded into buffer b (-1: no more)
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int W = p.width, H = p.n_hidden, K = p.K;
+  const LayoutTm L = make_layout_tm(Kp, W, H, p.n_nets);
+  float* wout = reinterpret_cast<float*>(smem + L.wout_off);
+  int64_t* s_pre = reinterpret_cast<int64_t*>(smem + L.pre_off);
+  const uint32_t ka = ws_act_cols(Kp, W);
+  const uint32_t ncols = ws_cols(Kp, W);
+
+  if (warp == 0) tmem_alloc(smem_u32(&s_tmem), ncols);
+  if (tid == 0) {
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&s_full[b]), kEW);
+      mbar_init(smem_u32(&s_empty[b]), 1);
+    }
+    mbar_init(smem_u32(&s_mma), 1);
+    mbar_init(smem_u32(&s_wbar), 1);
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  const int64_t n_tiles = build_tile_prefix(goff, p.n_nets, kM, s_pre);
+  const int quarter = warp & 3;
+  const uint32_t lane_base = tmem + (static_cast<uint32_t>(32 * quarter) << 16);
+  const int qi = 32 * quarter + lane;  // query row == TMEM lane
+
+  auto pack2 = [](float a, float b) {
+    typename O::T x = O::cvt(a), y = O::cvt(b);
+    return static_cast<uint32_t>(*reinterpret_cast<uint16_t*>(&x)) |
+           (static_cast<uint32_t>(*reinterpret_cast<uint16_t*>(&y)) << 16);
+  };
+
+  if (warp < kEW) {
+    // ================================================= encode warps
+    const int part = warp >> 2;
+    for (int it = 0;; ++it) {
+      const int b = it & 1, use = it >> 1;
+      // warp 0 waits until buffer b is free and claims the tile for it
+      if (tid == 0) {
+        int64_t t = -1;
+        if (use == 0 || mbar_wait(smem_u32(&s_empty[b]), (use - 1) & 1, err, kWaitCycles, 3)) {
+          t = tile_ctr ? static_cast<int64_t>(atomicAdd(tile_ctr, 1u))
+                       : blockIdx.x + static_cast<int64_t>(it) * gridDim.x;
+          if (t >= n_tiles) t = -1;
+        }
+        s_tile[b] = t;
+      }
+      enc_sync<kEW>();
+      tc_fence_after();
+      const int64_t t = *reinterpret_cast<volatile int64_t*>(&s_tile[b]);
+      if (t < 0) {
+        // no more tiles: the MLP warps read the same mark after full[b]
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&s_full[b]));
+        break;
+      }
+      const int g = find_group(s_pre, p.n_nets, t);
+      const int64_t q = goff[g] + (t - s_pre[g]) * kM + qi;
+      const bool live = q < goff[g + 1];
+      const uint32_t abase = lane_base + static_cast<uint32_t>(W) + static_cast<uint32_t>(b) * ka;
+      QueryPoints pts;
+      const __half2* tp = nullptr;
+      const __half2* td = nullptr;
+      using Raw = typename std::conditional<sizeof(TG) == 2, __half2, float2>::type;
+      if (live) {
+        const nif_ray r = load_nif_ray(rays, ray_id[q]);
+        const uint32_t obj = qobj[q] & 0x7fffffffu;
+        float bx[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) bx[k] = __ldg(p.aabb + 6 * static_cast<size_t>(obj) + k);
+        query_points(r, bx, pts);
+        tp = static_cast<const __half2*>(grid_ptr(p, obj, 0));
+        td = static_cast<const __half2*>(grid_ptr(p, obj, 1));
+      } else {
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) pts.u[j][k] = 0.f;
+      }
+      for (int l = part; l < p.L; l += NP) {
+        const LevelInfo li = level_info(p, l);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          uint32_t word = 0u;
+          if (live) {
+            uint32_t idx[8];
+            float fr[3];
+            uint32_t c0[3];
+            cell_of(li, pts.u[j][0], pts.u[j][1], pts.u[j][2], c0, fr);
+            cell_entries(li, c0, idx);
+            const Raw* tab = reinterpret_cast<const Raw*>(j < 2 ? tp : td);
+            Raw v[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) v[c] = __ldg(tab + idx[c]);
+            float w[8];
+            cell_weights(fr, w);
+            float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              float2 fv;
+              if constexpr (sizeof(TG) == 2) fv = __half22float2(v[c]);
+              else fv = v[c];
+              a0 += w[c] * fv.x;
+              a1 += w[c] * fv.y;
+            }
+            word = pack2(a0, a1);
+          }
+          tmem_st1(abase + static_cast<uint32_t>(j * p.L + l), word);
+        }
+      }
+      if (part == 0)
+        for (int k2 = K / 2; k2 < Kp / 2; ++k2) tmem_st1(abase + static_cast<uint32_t>(k2), 0u);
+      tmem_wait_st();
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&s_full[b]));
+    }
+  } else {
+    // ==================================================== MLP warps
+    const int mt = tid - 32 * kEW;  // 0..127
+    const bool leader = mt == 0;
+    const uint32_t idesc = instr_desc(kM, W, O::fmt);
+    const uint32_t mbar = smem_u32(&s_mma), wbar = smem_u32(&s_wbar);
+    uint32_t mphase = 0, wphase = 0;
+    int cur_g = -1;
+    for (int it = 0;; ++it) {
+      const int b = it & 1, use = it >> 1;
+      bool fail = !mbar_wait(smem_u32(&s_full[b]), use & 1, err, kWaitCycles, 4);
+      const int64_t t = fail ? -1 : *reinterpret_cast<volatile int64_t*>(&s_tile[b]);
+      // uniform exit; also no MLP thread still reads the previous tile's w_out
+      if (mlp_sync_or(t < 0)) break;
+      const int g = find_group(s_pre, p.n_nets, t);
+      const int64_t q = goff[g] + (t - s_pre[g]) * kM + qi;
+      const bool live = q < goff[g + 1];
+      if (g != cur_g) {
+        const int64_t wbase = static_cast<int64_t>(g) * p.P;
+        const int64_t off_out = static_cast<int64_t>(W) * K + static_cast<int64_t>(H - 1) * W * W;
+        if (use_tma) {
+          if (leader) {
+            mbar_expect_tx(wbar, L.w1_bytes + static_cast<uint32_t>(H - 1) * L.wl_bytes);
+            for (int l = 0; l < H; ++l)
+              tma_load_5d(smem_u32(smem + L.w_off(l)), &wm.m[l], 0, 0, 0, 0, g, wbar);
+          }
+          fail |= !mbar_wait(wbar, wphase, err, kWaitCycles, 2);
+          wphase ^= 1u;
+        } else {
+          int64_t off = 0;
+          for (int l = 0; l < H; ++l) {
+            const int fin = l == 0 ? K : W;
+            const int fpad = l == 0 ? Kp : W;
+            uint8_t* wt = smem + L.w_off(l);
+            for (int e = mt; e < W * fpad; e += 128) {
+              const int n = e / fpad, k = e % fpad;
+              const float v = k < fin ? O::load(p.weights, wbase + off + static_cast<int64_t>(n) * fin + k) : 0.f;
+              store_elem<DT>(wt, n, k, fpad, v);
+            }
+            off += static_cast<int64_t>(W) * fin;
+          }
+          fence_proxy_async();
+        }
+        for (int e = mt; e < W; e += 128) wout[e] = O::load(p.weights, wbase + off_out + e);
+        cur_g = g;
+      }
+      const uint32_t abuf = static_cast<uint32_t>(W) + static_cast<uint32_t>(b) * ka;
+      float zacc = 0.f;
+      for (int l = 0; l < H; ++l) {
+        // previous epilogue's TMEM reads and stores, and w_out, are done
+        tc_fence_before();
+        if (mlp_sync_or(fail)) {
+          fail = true;
+          break;
+        }
+        tc_fence_after();
+        const int kdim = l == 0 ? Kp : W;
+        if (leader) {
+          const uint32_t b0 = smem_u32(smem + L.w_off(l));
+          const uint32_t sbo = (kdim / 8) * 128;
+          for (int kk = 0; kk < kdim / 16; ++kk) {
+            const uint64_t bd = smem_desc(b0 + kk * 256, 128, sbo);
+            mma_ta(tmem, tmem + abuf + static_cast<uint32_t>(kk * 8), bd, idesc, kk > 0 ? 1u : 0u);
+          }
+          mma_commit(mbar);
+        }
+        const bool ok = mbar_wait(mbar, mphase, err);
+        mphase ^= 1u;
+        fail |= !ok;
+        tc_fence_after();
+        // the last MMA reading buffer b is complete: hand it back
+        if (l == H - 1 && leader && ok) mbar_arrive(smem_u32(&s_empty[b]));
+        for (int c0 = 0; c0 < W; c0 += 16) {
+          float v[16];
+          tmem_ld16(lane_base + static_cast<uint32_t>(c0), v);
+          if (l + 1 < H) {
+            uint32_t pk[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) pk[i] = pack2(act_fn_tc(p, v[2 * i]), act_fn_tc(p, v[2 * i + 1]));
+            tmem_st8(lane_base + abuf + static_cast<uint32_t>(c0 / 2), pk);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; ++i) zacc += act_fn_tc(p, v[i]) * wout[c0 + i];
+          }
+        }
+        if (l + 1 < H) tmem_wait_st();
+      }
+      if (mlp_sync_or(fail)) break;
+      // ---- logit and visibility of this thread's row
+      if (live) {
+        if (logits) logits[q] = zacc;
+        if (occ && zacc < 0.f) {
+          const uint32_t rid = ray_id[q];
+          atomicOr(&occ[rid >> 5], 1u << (rid & 31));
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
   if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
@@ -929,7 +1281,8 @@ nif_status check_tc_shape(const NifParams& p) {
 template <int DT>
 static nif_status launch_tm(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
                             const uint32_t* qobj, const int64_t* goff, int blocks, int per_sm,
-                            uint32_t* occ, float* logits, DevError* err, cudaStream_t st) {
+                            uint32_t* occ, float* logits, DevError* err, uint32_t* ctr,
+                            cudaStream_t st) {
   const int Kp = (p.K + 15) / 16 * 16;
   tc::LayoutTm L = tc::make_layout_tm(Kp, p.width, p.n_hidden, p.n_nets);
   size_t sh = L.total + 1024;
@@ -938,7 +1291,7 @@ static nif_status launch_tm(const NifParams& p, const nif_ray* rays, const uint3
   auto go = [&](auto kern) -> nif_status {
     NIF_CUDA_TRY(ensure_smem(kern, sh));
     kern<<<blocks, tc::kThreads, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, err, Kp, wm,
-                                           use_tma);
+                                           use_tma, ctr);
     return NIF_OK;
   };
   nif_status s;
@@ -960,15 +1313,54 @@ static nif_status launch_tm(const NifParams& p, const nif_ray* rays, const uint3
   return NIF_OK;
 }
 
+// Pipelined schedule: 8 encode warps and 4 CTAs per SM when both TMEM
+// buffers fit 128 columns, else 16 encode warps and 2 CTAs per SM.
+static bool ws_supported(const NifParams& p) {
+  return p.F == 2 && p.mlp_dtype != NIF_E4M3 && tc_activations_in_tmem();
+}
+
+template <int DT>
+static nif_status launch_ws(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
+                            const uint32_t* qobj, const int64_t* goff, int64_t nq_hint,
+                            uint32_t* occ, float* logits, DevError* err, uint32_t* ctr,
+                            cudaStream_t st) {
+  const int Kp = (p.K + 15) / 16 * 16;
+  tc::LayoutTm L = tc::make_layout_tm(Kp, p.width, p.n_hidden, p.n_nets);
+  size_t sh = L.total + 1024;
+  tc::WeightMaps wm;
+  const int use_tma = make_weight_maps(p, 2, Kp, &wm) && tc_weights_by_tma() ? 1 : 0;
+  const bool narrow = tc::ws_cols(Kp, p.width) <= 128;
+  const int per_sm = narrow ? 4 : 2;
+  int blocks = sm_count() * per_sm;
+  if (nq_hint >= 0)
+    blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(blocks, ceil_div(nq_hint, tc::kM) + p.n_nets)));
+  auto go = [&](auto kern, int threads) -> nif_status {
+    NIF_CUDA_TRY(ensure_smem(kern, sh));
+    kern<<<blocks, threads, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, err, Kp, wm, use_tma, ctr);
+    return NIF_OK;
+  };
+  nif_status s;
+  if (p.grid_dtype == NIF_F16)
+    s = narrow ? go(tc::k_fused_ws<2, __half, DT, 8, 4>, 32 * 12)
+               : go(tc::k_fused_ws<2, __half, DT, 16, 2>, 32 * 20);
+  else
+    s = narrow ? go(tc::k_fused_ws<2, float, DT, 8, 4>, 32 * 12)
+               : go(tc::k_fused_ws<2, float, DT, 16, 2>, 32 * 20);
+  if (s != NIF_OK) return s;
+  NIF_LAUNCH_CHECK();
+  return NIF_OK;
+}
+
 template <int DT>
 static nif_status launch_dt(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
                             const uint32_t* qobj, const int64_t* goff, int blocks, int per_sm,
-                            uint32_t* occ, float* logits, DevError* err, cudaStream_t st) {
+                            uint32_t* occ, float* logits, DevError* err, uint32_t* ctr,
+                            cudaStream_t st) {
   const int esz = DT == NIF_E4M3 ? 1 : 2;
   const bool occ3 = per_sm >= 3;
   if constexpr (DT != NIF_E4M3) {
     if (p.F % 2 == 0 && tc_activations_in_tmem())
-      return launch_tm<DT>(p, rays, ray_id, qobj, goff, blocks, per_sm, occ, logits, err, st);
+      return launch_tm<DT>(p, rays, ray_id, qobj, goff, blocks, per_sm, occ, logits, err, ctr, st);
   }
   const int Kp = (p.K + 32 / esz - 1) / (32 / esz) * (32 / esz);
   tc::Layout L = tc::make_layout(Kp, p.width, p.n_hidden, esz);
@@ -979,7 +1371,7 @@ static nif_status launch_dt(const NifParams& p, const nif_ray* rays, const uint3
     auto launch3 = [&](auto kern) -> nif_status {
       NIF_CUDA_TRY(ensure_smem(kern, sh));
       kern<<<blocks, tc::kThreads, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, err, Kp, wm,
-                                             use_tma);
+                                             use_tma, ctr);
       return NIF_OK;
     };
     nif_status s = p.grid_dtype == NIF_F16 ? launch3(tc::k_fused<2, __half, DT, 3>)
@@ -991,7 +1383,7 @@ static nif_status launch_dt(const NifParams& p, const nif_ray* rays, const uint3
   NIF_DISPATCH_FG_TC(p, {
     auto kern = tc::k_fused<F, TG, DT, 2>;
     NIF_CUDA_TRY(ensure_smem(kern, sh));
-    kern<<<blocks, tc::kThreads, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, err, Kp, wm, use_tma);
+    kern<<<blocks, tc::kThreads, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, err, Kp, wm, use_tma, ctr);
   });
   NIF_LAUNCH_CHECK();
   return NIF_OK;
@@ -1005,6 +1397,18 @@ nif_status launch_fwd_tc(const NifParams& p, const nif_ray* rays, const uint32_t
   if (s != NIF_OK) return s;
   if (tile_m != 0 && tile_m != 128)
     return fail(NIF_ERR_UNSUPPORTED, "tensor-core path: tile_m %d (128 supported)", tile_m);
+  uint32_t* ctr = tile_counter(err);
+  if (ctr) NIF_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t), st));
+  if (ws_supported(p)) {
+    const int Kp16 = (p.K + 15) / 16 * 16;
+    const bool pick = p.schedule == NIF_SCHED_PIPELINED ||
+                      (p.schedule == NIF_SCHED_AUTO && tc::ws_cols(Kp16, p.width) <= 128);
+    if (pick) {
+      if (p.mlp_dtype == NIF_F16)
+        return launch_ws<NIF_F16>(p, rays, ray_id, qobj, goff, nq_hint, occ, logits, err, ctr, st);
+      return launch_ws<NIF_BF16>(p, rays, ray_id, qobj, goff, nq_hint, occ, logits, err, ctr, st);
+    }
+  }
   int per_sm = ctas_per_sm > 0 ? ctas_per_sm : 2;
   if (p.mlp_dtype != NIF_E4M3 && p.F % 2 == 0 && tc_activations_in_tmem()) {
     // each CTA holds tm_cols() of the SM's 512 TMEM columns
@@ -1017,9 +1421,9 @@ nif_status launch_fwd_tc(const NifParams& p, const nif_ray* rays, const uint32_t
   int blocks = sm_count() * per_sm;
   if (nq_hint >= 0)
     blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(blocks, ceil_div(nq_hint, tc::kM) + p.n_nets)));
-  if (p.mlp_dtype == NIF_F16) return launch_dt<NIF_F16>(p, rays, ray_id, qobj, goff, blocks, per_sm, occ, logits, err, st);
-  if (p.mlp_dtype == NIF_BF16) return launch_dt<NIF_BF16>(p, rays, ray_id, qobj, goff, blocks, per_sm, occ, logits, err, st);
-  if (p.mlp_dtype == NIF_E4M3) return launch_dt<NIF_E4M3>(p, rays, ray_id, qobj, goff, blocks, per_sm, occ, logits, err, st);
+  if (p.mlp_dtype == NIF_F16) return launch_dt<NIF_F16>(p, rays, ray_id, qobj, goff, blocks, per_sm, occ, logits, err, ctr, st);
+  if (p.mlp_dtype == NIF_BF16) return launch_dt<NIF_BF16>(p, rays, ray_id, qobj, goff, blocks, per_sm, occ, logits, err, ctr, st);
+  if (p.mlp_dtype == NIF_E4M3) return launch_dt<NIF_E4M3>(p, rays, ray_id, qobj, goff, blocks, per_sm, occ, logits, err, ctr, st);
   return fail(NIF_ERR_UNSUPPORTED, "tensor-core path: mlp dtype %d", p.mlp_dtype);
 }
 

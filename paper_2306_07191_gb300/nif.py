@@ -118,6 +118,7 @@ class NifConfig:
     net_mode: int = L.NIF_NETS_SINGLE
     tile_m: int = 0
     ctas_per_sm: int = 0
+    schedule: int = L.NIF_SCHED_AUTO
 
     @property
     def n_levels(self):
@@ -170,6 +171,7 @@ class NifModel:
         d.d_scales = self.scales.data_ptr() if self.scales is not None else None
         d.tile_m = c.tile_m
         d.ctas_per_sm = c.ctas_per_sm
+        d.schedule = c.schedule
         return d
 
     @staticmethod

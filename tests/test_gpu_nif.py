@@ -20,14 +20,15 @@ TORCH_DT = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}
 
 
 def _build(res, F, log2, aabb, grid_vals, mats_list, grid_dt="f32", mlp_dt="f32",
-           net_mode=L.NIF_NETS_SINGLE, act=L.NIF_ACT_RELU, ctas_per_sm=0):
+           net_mode=L.NIF_NETS_SINGLE, act=L.NIF_ACT_RELU, ctas_per_sm=0,
+           schedule=L.NIF_SCHED_AUTO):
     """GPU model and the matching oracle model from the same float32 inputs
     (rounded to the GPU storage types)."""
     n_hidden = len(mats_list[0]) - 1
     width = mats_list[0][0].shape[0]
     cfg = nif.NifConfig(res=list(res), n_features=F, log2_table=log2, grid_dtype=DT[grid_dt],
                         n_hidden=n_hidden, width=width, act=act, mlp_dtype=DT[mlp_dt],
-                        net_mode=net_mode, ctas_per_sm=ctas_per_sm)
+                        net_mode=net_mode, ctas_per_sm=ctas_per_sm, schedule=schedule)
     flat = np.concatenate([synth.flatten_mlp(m) for m in mats_list])
     g = torch.from_numpy(np.ascontiguousarray(grid_vals, np.float32)).to(TORCH_DT[grid_dt]).cuda()
     w = torch.from_numpy(flat).to(TORCH_DT[mlp_dt]).cuda()
@@ -109,14 +110,18 @@ def test_encode_fp32_matches_oracle():
     np.testing.assert_allclose(x16, xo, atol=2e-3, rtol=0)
 
 
-@pytest.mark.parametrize("mlp_dt,grid_dt,tol,ctas", [("f32", "f32", 1e-4, 0), ("f16", "f32", 2e-2, 0),
-                                                      ("f16", "f16", 2e-2, 0), ("bf16", "f32", 6e-2, 0),
-                                                      ("f16", "f16", 2e-2, 3), ("bf16", "f16", 6e-2, 3),
-                                                      ("f16", "f16", 2e-2, 4), ("bf16", "f32", 6e-2, 4)])
-def test_logits_match_oracle(mlp_dt, grid_dt, tol, ctas):
+SER, PIPE = L.NIF_SCHED_SERIAL, L.NIF_SCHED_PIPELINED
+
+
+@pytest.mark.parametrize("mlp_dt,grid_dt,tol,ctas,sched", [
+    ("f32", "f32", 1e-4, 0, 0), ("f16", "f32", 2e-2, 0, 0), ("f16", "f16", 2e-2, 0, 0),
+    ("bf16", "f32", 6e-2, 0, 0), ("f16", "f16", 2e-2, 3, SER), ("bf16", "f16", 6e-2, 3, SER),
+    ("f16", "f16", 2e-2, 4, SER), ("bf16", "f32", 6e-2, 4, SER), ("f16", "f16", 2e-2, 0, PIPE),
+    ("bf16", "f32", 6e-2, 0, PIPE)])
+def test_logits_match_oracle(mlp_dt, grid_dt, tol, ctas, sched):
     w = _tiny(n_rays=6000)
     model, om = _build(w.res, 2, 19, w.aabb, w.grid_values, [w.weights], grid_dt=grid_dt, mlp_dt=mlp_dt,
-                       ctas_per_sm=ctas)
+                       ctas_per_sm=ctas, schedule=sched)
     rays_t = torch.from_numpy(w.rays).cuda()
     ray_id, qobj, goff, nq = _gpu_queries(model, rays_t)
     bits = nif.empty_bits(len(w.rays))
@@ -298,3 +303,71 @@ def test_per_object_networks_grouped_launch(mlp_dt, tol):
     err = np.abs(z.cpu().numpy()[:n] - zo)
     assert (gw.counts % 128 != 0).any() and gw.counts.max() > 128  # ragged, multi-tile groups
     assert err.max() <= tol, err.max()
+
+
+@pytest.mark.parametrize("sched", [SER, PIPE])
+@pytest.mark.parametrize("mlp_dt,tol", [("f16", 2e-2), ("bf16", 6e-2)])
+def test_sixteen_level_input_both_schedules(sched, mlp_dt, tol):
+    """K = 96 (16 levels x 2 features x 3 points), hashed fine levels and two
+    networks: the pipelined schedule's wide form (two 48-column TMEM buffers,
+    16 encode warps) and the serial one give the oracle's logits."""
+    rng = np.random.default_rng(57)
+    boxes = random_boxes_scene(rng, n_obj=3)
+    res = [4, 5, 6, 8, 10, 12, 15, 19, 24, 30, 38, 48, 60, 76, 96, 120]
+    log2 = 14
+    sizes, hashed, off = onif.level_layout(res, log2)
+    assert any(hashed) and not all(hashed)
+    V = int(off[-1])
+    grid = rng.uniform(-1, 1, size=(3, 2, V * 2)).astype(np.float32)
+    mats = [synth.mlp_init(rng, 96, 64, 3), synth.mlp_init(rng, 96, 64, 3)]
+    model, om = _build(res, 2, log2, boxes, grid, mats, grid_dt="f16", mlp_dt=mlp_dt,
+                       net_mode=L.NIF_NETS_CLASS, schedule=sched)
+    # rays aimed at a uniform point of a random box, from inside and outside
+    n = 7000
+    o = rng.uniform(-3, 3, size=(n, 3))
+    k = rng.integers(0, 3, size=n)
+    tgt = boxes[k, :3] + rng.uniform(size=(n, 3)) * (boxes[k, 3:] - boxes[k, :3])
+    d = tgt - o
+    rays = synth.pack_rays(o, d / np.linalg.norm(d, axis=1, keepdims=True), 1e-3, np.inf)
+    rays_t = torch.from_numpy(rays).cuda()
+    ray_id, qobj, goff, nq = _gpu_queries(model, rays_t)
+    bits = nif.empty_bits(len(rays))
+    z = model.infer_queries(rays_t, ray_id, qobj, goff, nq, bits=bits)
+    model.check()
+    r, ob, inn = _query_arrays(ray_id, qobj, nq)
+    assert nq > 2000 and nq % 128 != 0 and inn.any() and (~inn).any()
+    zo = onif.forward(om, rays, r, ob, inn)
+    zg = z[:nq].cpu().numpy()
+    assert np.abs(zo).max() > 0.05
+    err = np.abs(zg - zo)
+    assert err.max() <= tol, err.max()
+    occ = nif.bits_to_bool(bits, len(rays)).cpu().numpy()
+    assert np.array_equal(occ, onif.ray_occlusion(len(rays), r, zg))
+
+
+@pytest.mark.parametrize("mlp_dt", ["f16", "bf16"])
+def test_schedules_agree_on_grouped_networks(mlp_dt):
+    """The serial and pipelined schedules on one grouped launch of per-object
+    networks: the same query rows give logits within FP32 summation-order
+    differences (the two sum the output layer in different orders)."""
+    gw = workloads.grouped_objects(n_obj=5, total_rays=30000, tri_min=500, tri_max=5000, seed=5)
+    rng = np.random.default_rng(13)
+    res = [4, 8, 16, 32]
+    V = int(onif.level_layout(res, 19)[2][-1])
+    grid = rng.uniform(-1, 1, size=(5, 2, V * 2)).astype(np.float32)
+    mats = [synth.mlp_init(rng, 24, 64, 3) for _ in range(5)]
+    n = len(gw.rays)
+    rays_t = torch.from_numpy(gw.rays).cuda()
+    ray_id = torch.arange(n, dtype=torch.int32, device="cuda")
+    obj = np.repeat(np.arange(5), gw.counts)
+    qobj = torch.from_numpy(obj.astype(np.int32)).cuda()
+    goff = torch.from_numpy(np.concatenate([[0], np.cumsum(gw.counts)]).astype(np.int64)).cuda()
+    out = {}
+    for sched in (SER, PIPE):
+        model, _ = _build(res, 2, 19, gw.scene.obj_aabb, grid, mats, grid_dt="f16", mlp_dt=mlp_dt,
+                          net_mode=L.NIF_NETS_OBJECT, schedule=sched)
+        out[sched] = model.infer_queries(rays_t, ray_id, qobj, goff, n).cpu().numpy()[:n]
+        model.check()
+    scale = np.abs(out[SER]).max()
+    assert scale > 0.05
+    assert np.abs(out[SER] - out[PIPE]).max() <= 1e-5 * max(1.0, scale)
