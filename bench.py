@@ -29,6 +29,7 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+SCHED_NAME = {0: "auto", 1: "serial", 2: "pipelined"}
 METRIC = "shadow rays/sec NIF vs own GPU BVH at <=1% visibility error; tensor-pipe util"
 UNIT = "shadow rays/s"
 WORKLOADS = {
@@ -49,10 +50,10 @@ WORKLOADS = {
 }
 
 
-# DRAM bytes (read + write) of one k_fused_tm<2, half, F16, 4 CTAs/SM> launch
-# on the room workload, from the ncu capture summarised in
-# profiles/fused_tm_room.md; reported only for that exact kernel and workload.
-ROOM_FUSED_TRAFFIC_BYTES = 2.087331e9 + 4.31488e6
+# DRAM bytes (read + write) of one fused-kernel launch, from the ncu captures
+# summarised under profiles/, keyed by (workload, schedule, CTAs per SM) of the
+# kernel as it stands; a configuration without an entry reports null.
+FUSED_TRAFFIC_BYTES = {}
 
 
 def per_query_cost(cfg):
@@ -311,6 +312,9 @@ def run_ours(args):
             cfg.n_obj = 16
     if args.ctas_per_sm:
         cfg.ctas_per_sm = args.ctas_per_sm
+        cfg.schedule = L.NIF_SCHED_SERIAL
+    if args.schedule:
+        cfg.schedule = {"serial": L.NIF_SCHED_SERIAL, "pipelined": L.NIF_SCHED_PIPELINED}[args.schedule]
     pipe = RoomPipeline(cfg, log=log)
     train_s = pipe.train()
     dis = pipe.disagreement()
@@ -321,10 +325,14 @@ def run_ours(args):
         sweep = precision_sweep(pipe, log)
     pipe.release_training_state()
     torch.cuda.empty_cache()
-    if not args.ctas_per_sm and pipe.model.cfg.mlp_dtype != L.NIF_F32:
-        occ = nif.autotune_occupancy(pipe.model, pipe.rays, pipe.tlas,
-                                     max_q=cfg.max_pairs_per_ray * pipe.n_rays + 1024)
-        log(f"autotuned fused kernel occupancy: {occ} CTAs/SM")
+    tune_ms = None
+    if not (args.ctas_per_sm or args.schedule) and pipe.model.cfg.mlp_dtype != L.NIF_F32:
+        tbits = nif.empty_bits(pipe.n_rays)
+        mq = cfg.max_pairs_per_ray * pipe.n_rays + 1024
+        sched, occ, tune_ms = nif.autotune(
+            pipe.model, lambda: pipe.model.infer(pipe.rays, tbits, tlas=pipe.tlas, max_q=mq),
+            key_extra=(pipe.n_rays, args.workload))
+        log(f"autotuned fused kernel: schedule {sched}, {occ} CTAs/SM ({tune_ms})")
     n = pipe.n_rays
     rays = pipe.rays
     model = pipe.model
@@ -428,7 +436,8 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "rays": n, "queries": nq, "triangles": pipe.n_tris,
                    "objects": cfg.n_obj, "l2": "flushed (256 MB write) before every timed step",
-                   "fused_ctas_per_sm": model.cfg.ctas_per_sm,
+                   "fused_schedule": SCHED_NAME[model.cfg.schedule],
+                   "fused_ctas_per_sm": model.cfg.ctas_per_sm, "autotune_ms": tune_ms,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "bvh_rays_per_s": world * n / (bms * 1e-3), "bvh_ms_per_step": bms,
         "speedup_vs_bvh": bms / ms,
@@ -436,8 +445,8 @@ def run_ours(args):
         "stages_ms": subs,
         "roofline": {"kernel": "nif fused encode+MLP (tcgen05)", "bound": "hbm",
                      "achieved": ach_gbs, "peak": hbm, "unit": "GB/s", "frac": ach_gbs / hbm,
-                     "traffic": (ROOM_FUSED_TRAFFIC_BYTES
-                                 if args.workload == "room" and model.cfg.ctas_per_sm == 4 else None),
+                     "traffic": FUSED_TRAFFIC_BYTES.get(
+                         (args.workload, SCHED_NAME[model.cfg.schedule], model.cfg.ctas_per_sm)),
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch",
                      "peak_source": src,
                      "tensor_tflops": tc_tflops, "tensor_peak_tflops": tflops,
@@ -523,13 +532,14 @@ def run_grouped(args):
             out.append(e0.elapsed_time(e1))
         return statistics.mean(out)
 
-    # project autotuner: CTAs per SM of the persistent grouped launch
-    sweep = {}
-    for c in (2, 3, 4):
-        model.cfg.ctas_per_sm = c
-        sweep[c] = time_fn(query, 3, 1)
-    best = min(sweep, key=sweep.get)
-    model.cfg.ctas_per_sm = best
+    # project autotuner: schedule and CTAs per SM of the persistent grouped launch
+    if args.ctas_per_sm or args.schedule:
+        model.cfg.ctas_per_sm = args.ctas_per_sm
+        model.cfg.schedule = (L.NIF_SCHED_SERIAL if args.ctas_per_sm else
+                              {"serial": L.NIF_SCHED_SERIAL, "pipelined": L.NIF_SCHED_PIPELINED}[args.schedule])
+        sched, best, sweep = model.cfg.schedule, model.cfg.ctas_per_sm, None
+    else:
+        sched, best, sweep = nif.autotune(model, query, key_extra=(n, "grouped"))
     query()
     torch.cuda.synchronize()
     # one persistent grouped launch captured in a CUDA graph
@@ -554,7 +564,8 @@ def run_grouped(args):
             "vs_baseline": None, "dtype": "f16", "data": "synthetic",
             "config": {"workload": WORKLOADS["grouped"], "rays": n, "objects": n_obj,
                        "triangles": int(sc.tris.shape[0]), "pairs_per_object": gw.counts.tolist(),
-                       "fused_ctas_per_sm": best, "autotune_ms": sweep, "cuda_graph": True},
+                       "fused_schedule": SCHED_NAME[sched], "fused_ctas_per_sm": best,
+                       "autotune_ms": sweep, "cuda_graph": True},
             "bvh_rays_per_s": n / (bvh_ms * 1e-3), "bvh_ms_per_step": bvh_ms, "speedup_vs_bvh": bvh_ms / nif_ms,
             "roofline": {"kernel": "nif fused encode+MLP (tcgen05), grouped", "bound": "hbm",
                          "achieved": n * alg_bytes / (nif_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
@@ -571,7 +582,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--small", action="store_true", help="reduced workload for quick checks")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ctas-per-sm", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0,
+                    help="fix the serial schedule's CTAs per SM (skips the autotuner)")
+    ap.add_argument("--schedule", default="", choices=["", "serial", "pipelined"],
+                    help="fix the fused kernel's schedule (skips the autotuner)")
     ap.add_argument("--workload", default="room", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     if args.impl == "reference":

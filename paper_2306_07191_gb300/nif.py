@@ -380,20 +380,28 @@ def quantize_e4m3(weights_f32: torch.Tensor, cfg: NifConfig, n_nets: int, act_am
     return q.reshape(-1).to(torch.float8_e4m3fn).contiguous(), scales.contiguous()
 
 
-def autotune_occupancy(model: NifModel, rays: torch.Tensor, tlas: BVH | None = None,
-                       candidates=(2, 3, 4), reps: int = 3, max_q: int | None = None,
-                       cache_path: str | None = None) -> int:
-    """Pick the fused kernel's CTAs per SM (2, 3 or 4: more CTAs trade gathers
-    in flight per thread for more warps) by timing nif_infer on the caller's
-    own rays; the choice is cached per (model shape, ray count, GPU) in a JSON
-    file and written into model.cfg.ctas_per_sm."""
+# (schedule, CTAs per SM) pairs the autotuner times: the serial schedule at
+# 2, 3 or 4 CTAs per SM (more CTAs trade gathers in flight per thread for more
+# warps) and the pipelined schedule (its own occupancy).
+SCHEDULE_CANDIDATES = ((L.NIF_SCHED_SERIAL, 2), (L.NIF_SCHED_SERIAL, 3), (L.NIF_SCHED_SERIAL, 4),
+                       (L.NIF_SCHED_PIPELINED, 0))
+
+
+def autotune(model: NifModel, run, key_extra=(), candidates=SCHEDULE_CANDIDATES, reps: int = 3,
+             cache_path: str | None = None):
+    """Pick the tensor-core forward's (schedule, CTAs per SM) by timing
+    `run()` (the caller's own query, e.g. nif_infer on its rays) once per
+    candidate; the fastest is written into model.cfg and cached per (model
+    shape, key_extra, GPU) in a JSON file.  Returns (schedule, ctas_per_sm,
+    {candidate label: ms})."""
     import hashlib
     import json
     import os
     c = model.cfg
+    cands = [tuple(x) for x in candidates]
     key = hashlib.sha1(json.dumps([list(c.res), c.n_features, c.log2_table, c.grid_dtype, c.n_hidden,
-                                   c.width, c.mlp_dtype, c.net_mode, model.n_obj, int(rays.shape[0]),
-                                   torch.cuda.get_device_name()]).encode()).hexdigest()[:16]
+                                   c.width, c.mlp_dtype, c.net_mode, model.n_obj, list(key_extra),
+                                   cands, torch.cuda.get_device_name()]).encode()).hexdigest()[:16]
     cache_path = cache_path or os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune.json")
     try:
         with open(cache_path) as f:
@@ -401,31 +409,31 @@ def autotune_occupancy(model: NifModel, rays: torch.Tensor, tlas: BVH | None = N
     except (OSError, ValueError):
         cache = {}
     if key in cache:
-        c.ctas_per_sm = int(cache[key]["ctas_per_sm"])
-        return c.ctas_per_sm
-    n = int(rays.shape[0])
-    bits = empty_bits(n, rays.device)
+        c.schedule, c.ctas_per_sm = (int(x) for x in cache[key]["choice"])
+        return c.schedule, c.ctas_per_sm, cache[key]["ms"]
+    label = {L.NIF_SCHED_SERIAL: "serial", L.NIF_SCHED_PIPELINED: "pipelined", L.NIF_SCHED_AUTO: "auto"}
     timings = {}
-    for cand in candidates:
-        c.ctas_per_sm = cand
-        model.infer(rays, bits, tlas=tlas, max_q=max_q)
+    for sched, ctas in cands:
+        c.schedule, c.ctas_per_sm = sched, ctas
+        run()
         torch.cuda.synchronize()
         best = None
         for _ in range(reps):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            model.infer(rays, bits, tlas=tlas, max_q=max_q)
+            run()
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
             best = ms if best is None else min(best, ms)
-        timings[cand] = best
+        timings[(sched, ctas)] = best
     choice = min(timings, key=timings.get)
-    c.ctas_per_sm = choice
-    cache[key] = {"ctas_per_sm": choice, "ms": timings}
+    c.schedule, c.ctas_per_sm = choice
+    ms = {f"{label[k[0]]}/{k[1]}": v for k, v in timings.items()}
+    cache[key] = {"choice": list(choice), "ms": ms}
     try:
         with open(cache_path, "w") as f:
             json.dump(cache, f, indent=1)
     except OSError:
         pass
-    return choice
+    return choice[0], choice[1], ms

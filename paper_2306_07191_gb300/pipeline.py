@@ -40,6 +40,7 @@ class RoomConfig:
     lr: float = 1e-2
     tmin: float = 1e-3
     ctas_per_sm: int = 0
+    schedule: int = 0  # NIF_SCHED_* of the tensor-core forward (0: library choice)
     layout: str = "random"      # "random" | "single" | "lattice" (see workloads.room_scene)
     n_lights: int = 1           # point lights (one shadow ray per light per pixel)
     area_light: bool = False    # 4 x 4 ceiling quad light instead of point lights
@@ -97,7 +98,7 @@ class RoomPipeline:
         ncfg = nif.NifConfig(res=list(c.res), n_features=c.n_features, log2_table=c.log2_table,
                              grid_dtype=c.grid_dtype, n_hidden=c.n_hidden, width=c.width_mlp,
                              mlp_dtype=c.mlp_dtype, net_mode=L.NIF_NETS_CLASS,
-                             ctas_per_sm=c.ctas_per_sm)
+                             ctas_per_sm=c.ctas_per_sm, schedule=c.schedule)
         self.V = nif.NifModel.grid_vertices(ncfg)
         self.P = nif.NifModel.weight_count(ncfg)
         n_grid = c.n_obj * 2 * self.V * c.n_features
