@@ -254,11 +254,44 @@ nif_status nif_infer_queries(const nif_model_desc* m, const nif_ray* d_rays, int
                              uint32_t* d_occluded_bits, float* d_logits, void* d_ws,
                              size_t ws_bytes, void* stream);
 
-/* The whole query (a0-a4): nif_frontend into the workspace, then
- * nif_infer_queries.  d_occluded_bits is OR-ed into as above. */
+/* The whole query (a0-a4) with the workspace from nif_workspace_size, in two
+ * rounds (the early-out of Sec. 4.1's ray-cast stage): round 1 queries each
+ * ray's nearest pair (smallest entry parameter) of the rays whose bit in
+ * d_occluded_bits is not already set; round 2 queries the other pairs of the
+ * rays still unoccluded.  A ray is occluded iff one of its pairs has z < 0,
+ * so d_occluded_bits (OR-ed into as above) ends exactly as querying every
+ * pair with nif_frontend + nif_infer_queries would leave it. */
 nif_status nif_infer(const nif_model_desc* m, const void* d_tlas, const nif_ray* d_rays,
                      int64_t n, uint32_t* d_occluded_bits, void* d_ws, size_t ws_bytes,
                      void* stream);
+
+/* The two rounds of nif_infer's front end as separate calls, with the pair
+ * lists in the caller's arrays (same layout and group order as nif_frontend)
+ * and d_ws of at least nif_workspace_size(m, n, 0) bytes, the same buffer for
+ * both calls on one stream.
+ * nif_frontend_nearest: each ray whose bit in d_occluded_bits is clear gets
+ *   its nearest pair (smallest entry parameter) listed; *d_count = pairs
+ *   listed.  Every pair of those rays is remembered in d_ws for round 2.
+ * nif_frontend_rest (after the round-1 pairs have been answered into
+ *   d_occluded_bits): the other pairs of the rays still unoccluded, written
+ *   from index *d_count_nearest on; d_group_off gets their absolute group
+ *   ranges and *d_count = *d_count_nearest + pairs listed.
+ * Overflow of max_q is the device error NIF_ERR_WORKSPACE, as in nif_frontend. */
+nif_status nif_frontend_nearest(const nif_model_desc* m, const void* d_tlas, const nif_ray* d_rays,
+                                int64_t n, const uint32_t* d_occluded_bits, uint32_t* d_ray_id,
+                                uint32_t* d_qobj, int64_t max_q, int64_t* d_group_off,
+                                int64_t* d_count, void* d_ws, size_t ws_bytes, void* stream);
+nif_status nif_frontend_rest(const nif_model_desc* m, const void* d_tlas, const nif_ray* d_rays,
+                             int64_t n, const uint32_t* d_occluded_bits, uint32_t* d_ray_id,
+                             uint32_t* d_qobj, int64_t max_q, const int64_t* d_count_nearest,
+                             int64_t* d_group_off, int64_t* d_count, void* d_ws, size_t ws_bytes,
+                             void* stream);
+
+/* After nif_infer on the same workspace (stream-ordered): d_counts[0] = pairs
+ * queried in round 1, d_counts[1] = pairs queried in both rounds (device
+ * int64[2], written asynchronously). */
+nif_status nif_infer_query_counts(const nif_model_desc* m, const void* d_ws, size_t ws_bytes,
+                                  int64_t n, int64_t* d_counts, void* stream);
 
 /* Allocation-free variant of nif_infer (the paper has no counterpart; it
  * exists for callers of this library that cannot allocate device memory when

@@ -79,6 +79,9 @@ SIGNATURES = {
     "nif_encode": (i32, [MD, P, P, P, i64, P, i32, P]),
     "nif_infer_queries": (i32, [MD, P, i64, P, P, P, i64, P, P, P, size_t, P]),
     "nif_infer": (i32, [MD, P, P, i64, P, P, size_t, P]),
+    "nif_infer_query_counts": (i32, [MD, P, size_t, i64, P, P]),
+    "nif_frontend_nearest": (i32, [MD, P, P, i64, P, P, P, i64, P, P, P, size_t, P]),
+    "nif_frontend_rest": (i32, [MD, P, P, i64, P, P, P, i64, P, P, P, P, size_t, P]),
     "nif_saved_size": (size_t, [MD, i64]),
     "nif_fwd_train": (i32, [MD, P, P, P, P, i64, P, P, P]),
     "nif_loss": (i32, [P, P, i64, f32, P, P, P]),

@@ -145,13 +145,18 @@ struct InferWs {
   DevError* err;
   int64_t* goff;
   int64_t* count;
+  int64_t* goff2;    // second round (nif_infer)
+  int64_t* count2;   // first + second round pairs
+  uint32_t* cnt2;    // second round bucket counters and cursors
+  uint8_t* first_k;  // per ray: slot of its nearest pair
   uint32_t* qray;
   uint32_t* qobj;
   void* slots;
   size_t bytes;
 };
 
-// [error word | front-end counters | group offsets | count | pair lists | slots]
+// [error word | front-end counters | group offsets | count | second-round
+//  offsets, count, counters | nearest-pair slots | pair lists | slots]
 static InferWs infer_layout(const NifParams& p, void* base, int64_t max_q, int64_t n_rays) {
   InferWs w{};
   size_t o = kErrBytes + frontend_ws_bytes(p);
@@ -161,6 +166,14 @@ static InferWs infer_layout(const NifParams& p, void* base, int64_t max_q, int64
   o += align_up((p.n_nets + 1) * sizeof(int64_t), 256);
   w.count = reinterpret_cast<int64_t*>(b + o);
   o += 256;
+  w.goff2 = reinterpret_cast<int64_t*>(b + o);
+  o += align_up((p.n_nets + 1) * sizeof(int64_t), 256);
+  w.count2 = reinterpret_cast<int64_t*>(b + o);
+  o += 256;
+  w.cnt2 = reinterpret_cast<uint32_t*>(b + o);
+  o += frontend_ws_bytes(p);
+  w.first_k = reinterpret_cast<uint8_t*>(b + o);
+  o += frontend_first_bytes(n_rays);
   w.qray = reinterpret_cast<uint32_t*>(b + o);
   o += align_up(max_q * sizeof(uint32_t), 256);
   w.qobj = reinterpret_cast<uint32_t*>(b + o);
@@ -316,13 +329,78 @@ nif_status nif_infer(const nif_model_desc* m, const void* d_tlas, const nif_ray*
   InferWs w = infer_layout(p, d_ws, max_q, n);
   if (w.bytes > ws_bytes) return fail(NIF_ERR_WORKSPACE, "nif_infer: workspace too small");
   cudaStream_t st = as_stream(stream);
-  s = launch_frontend(p, d_tlas, d_rays, n, w.qray, w.qobj, max_q, w.goff, w.count, d_ws, st, w.slots);
+  auto forward = [&](const int64_t* goff) -> nif_status {
+    if (p.mlp_dtype == NIF_F32)
+      return launch_fwd_f32(p, d_rays, w.qray, w.qobj, goff, -1, d_occluded_bits, nullptr, nullptr, 0,
+                            st);
+    return launch_fwd_tc(p, d_rays, w.qray, w.qobj, goff, -1, d_occluded_bits, nullptr, m->tile_m,
+                         m->ctas_per_sm, w.err, st);
+  };
+  // round 1: every ray's nearest pair; round 2: the other pairs of the rays
+  // still unoccluded (the OR over pairs is unchanged by skipping the rest)
+  s = launch_frontend_first(p, d_tlas, d_rays, n, d_occluded_bits, w.qray, w.qobj, max_q, w.goff,
+                            w.count, d_ws, w.slots, w.first_k, st);
   if (s != NIF_OK) return s;
-  if (p.mlp_dtype == NIF_F32)
-    return launch_fwd_f32(p, d_rays, w.qray, w.qobj, w.goff, -1, d_occluded_bits, nullptr, nullptr,
-                          0, st);
-  return launch_fwd_tc(p, d_rays, w.qray, w.qobj, w.goff, -1, d_occluded_bits, nullptr, m->tile_m,
-                       m->ctas_per_sm, w.err, st);
+  s = forward(w.goff);
+  if (s != NIF_OK) return s;
+  s = launch_frontend_rest(p, d_tlas, d_rays, n, d_occluded_bits, w.qray, w.qobj, max_q, w.count,
+                           w.goff2, w.count2, d_ws, w.cnt2, w.slots, w.first_k, st);
+  if (s != NIF_OK) return s;
+  return forward(w.goff2);
+}
+
+nif_status nif_frontend_nearest(const nif_model_desc* m, const void* d_tlas, const nif_ray* d_rays,
+                                int64_t n, const uint32_t* d_occluded_bits, uint32_t* d_ray_id,
+                                uint32_t* d_qobj, int64_t max_q, int64_t* d_group_off,
+                                int64_t* d_count, void* d_ws, size_t ws_bytes, void* stream) {
+  NifParams p;
+  nif_status s = make_params(m, &p);
+  if (s != NIF_OK) return s;
+  NIF_CHECK_ARG(n >= 0 && max_q >= 0, "nif_frontend_nearest: negative size");
+  NIF_CHECK_ARG(d_group_off && d_count && d_ws && d_occluded_bits, "nif_frontend_nearest: null pointer");
+  NIF_CHECK_ARG(n == 0 || (d_rays && aligned16(d_rays)), "nif_frontend_nearest: rays null or not 16-byte aligned");
+  NIF_CHECK_ARG(max_q == 0 || (d_ray_id && d_qobj), "nif_frontend_nearest: null query arrays");
+  NIF_CHECK_ARG(n < (int64_t(1) << 32), "nif_frontend_nearest: at most 2^32 rays");
+  InferWs w = infer_layout(p, d_ws, 0, n);
+  if (w.bytes > ws_bytes) return fail(NIF_ERR_WORKSPACE, "nif_frontend_nearest: workspace too small");
+  return launch_frontend_first(p, d_tlas, d_rays, n, d_occluded_bits, d_ray_id, d_qobj, max_q,
+                               d_group_off, d_count, d_ws, w.slots, w.first_k, as_stream(stream));
+}
+
+nif_status nif_frontend_rest(const nif_model_desc* m, const void* d_tlas, const nif_ray* d_rays,
+                             int64_t n, const uint32_t* d_occluded_bits, uint32_t* d_ray_id,
+                             uint32_t* d_qobj, int64_t max_q, const int64_t* d_count_nearest,
+                             int64_t* d_group_off, int64_t* d_count, void* d_ws, size_t ws_bytes,
+                             void* stream) {
+  NifParams p;
+  nif_status s = make_params(m, &p);
+  if (s != NIF_OK) return s;
+  NIF_CHECK_ARG(n >= 0 && max_q >= 0, "nif_frontend_rest: negative size");
+  NIF_CHECK_ARG(d_group_off && d_count && d_count_nearest && d_ws && d_occluded_bits,
+                "nif_frontend_rest: null pointer");
+  NIF_CHECK_ARG(n == 0 || (d_rays && aligned16(d_rays)), "nif_frontend_rest: rays null or not 16-byte aligned");
+  NIF_CHECK_ARG(max_q == 0 || (d_ray_id && d_qobj), "nif_frontend_rest: null query arrays");
+  NIF_CHECK_ARG(n < (int64_t(1) << 32), "nif_frontend_rest: at most 2^32 rays");
+  InferWs w = infer_layout(p, d_ws, 0, n);
+  if (w.bytes > ws_bytes) return fail(NIF_ERR_WORKSPACE, "nif_frontend_rest: workspace too small");
+  return launch_frontend_rest(p, d_tlas, d_rays, n, d_occluded_bits, d_ray_id, d_qobj, max_q,
+                              d_count_nearest, d_group_off, d_count, d_ws, w.cnt2, w.slots, w.first_k,
+                              as_stream(stream));
+}
+
+nif_status nif_infer_query_counts(const nif_model_desc* m, const void* d_ws, size_t ws_bytes,
+                                  int64_t n, int64_t* d_counts, void* stream) {
+  NifParams p;
+  nif_status s = make_params(m, &p);
+  if (s != NIF_OK) return s;
+  NIF_CHECK_ARG(n >= 0 && d_ws && d_counts, "nif_infer_query_counts: bad argument");
+  int64_t max_q = ws_max_q(p, ws_bytes, n);
+  if (max_q <= 0) return fail(NIF_ERR_WORKSPACE, "nif_infer_query_counts: workspace too small");
+  InferWs w = infer_layout(p, const_cast<void*>(d_ws), max_q, n);
+  cudaStream_t st = as_stream(stream);
+  NIF_CUDA_TRY(cudaMemcpyAsync(d_counts, w.count, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+  NIF_CUDA_TRY(cudaMemcpyAsync(d_counts + 1, w.count2, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+  return NIF_OK;
 }
 
 size_t nif_saved_size(const nif_model_desc* m, int64_t nq) {

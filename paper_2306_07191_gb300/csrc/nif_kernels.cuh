@@ -16,6 +16,23 @@ nif_status launch_frontend(const NifParams& p, const void* tlas, const nif_ray* 
 size_t frontend_ws_bytes(const NifParams& p);
 size_t frontend_slot_bytes(int64_t n);
 
+// Two-round front end of nif_infer.  Round 1 writes each ray's nearest pair
+// (rays whose bit is already set are skipped) and keeps every pair in the
+// slots (slot_area of frontend_slot_bytes(n) bytes, plus first_k of
+// frontend_first_bytes(n)); round 2 writes the other pairs of the rays still
+// unoccluded after round 1's forward, after round 1's count_first pairs, with
+// its own bucket counters cnt2 (2 x 64-aligned n_buckets words).
+size_t frontend_first_bytes(int64_t n);
+nif_status launch_frontend_first(const NifParams& p, const void* tlas, const nif_ray* rays, int64_t n,
+                                 const uint32_t* bits, uint32_t* out_ray, uint32_t* out_qobj,
+                                 int64_t max_q, int64_t* goff, int64_t* count, void* ws,
+                                 void* slot_area, uint8_t* first_k, cudaStream_t st);
+nif_status launch_frontend_rest(const NifParams& p, const void* tlas, const nif_ray* rays, int64_t n,
+                                const uint32_t* bits, uint32_t* out_ray, uint32_t* out_qobj,
+                                int64_t max_q, const int64_t* count_first, int64_t* goff,
+                                int64_t* count, void* ws, uint32_t* cnt2, const void* slot_area,
+                                const uint8_t* first_k, cudaStream_t st);
+
 nif_status launch_encode(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
                          const uint32_t* qobj, int64_t nq, void* out, int out_dtype,
                          cudaStream_t st);

@@ -82,9 +82,11 @@ __device__ __forceinline__ bool exact_slab(const float o[3], const float d[3], f
 // otherwise, so the decisions are always exact_slab's.
 // rcp[k] = __frcp_rn(d[k]); `exact_only` forces the exact path (directions
 // with subnormal components).
+// tkey receives the segment's entry parameter (reciprocal-product or exact),
+// used only to order a ray's pairs.
 __device__ __forceinline__ bool slab_decide(const float o[3], const float d[3], const float rcp[3],
                                             bool exact_only, float tmin, float tmax,
-                                            const float* box, bool& inner) {
+                                            const float* box, bool& inner, float& tkey) {
   if (!exact_only) {
     float en = -INFINITY, ex = INFINITY, mag = 0.f;
     bool blocked = false;
@@ -112,12 +114,14 @@ __device__ __forceinline__ bool slab_decide(const float o[3], const float d[3], 
     if (miss_sure) return false;
     if (hit_sure && (in_sure || out_sure)) {
       inner = in_sure;
+      tkey = tin;
       return true;
     }
   }
   float tin, tout, entry;
   const bool hit = exact_slab(o, d, tmin, tmax, box, tin, tout, entry);
   inner = entry <= tmin;
+  tkey = tin;
   return hit;
 }
 

@@ -25,7 +25,8 @@ __device__ __forceinline__ int bucket_of(const NifParams& p, uint32_t obj, bool 
   return (p.net_mode == NIF_NETS_CLASS && inner ? p.n_obj : 0) + static_cast<int>(obj);
 }
 
-// Calls emit(obj, inner) for every object whose box the ray's segment overlaps.
+// Calls emit(obj, inner, tkey) for every object whose box the ray's segment
+// overlaps (tkey: the segment's entry parameter into the box).
 template <bool kTlas, typename Emit>
 __device__ __forceinline__ void for_each_pair(const NifParams& p, const char* tlas,
                                               const bvh::Header* H, const nif_ray& r, Emit&& emit) {
@@ -42,7 +43,8 @@ __device__ __forceinline__ void for_each_pair(const NifParams& p, const char* tl
 #pragma unroll
     for (int k = 0; k < 6; ++k) bx[k] = __ldg(p.aabb + 6 * (size_t)obj + k);
     bool inner;
-    if (slab_decide(o, d, rcp, exact_only, r.tmin, r.tmax, bx, inner)) emit(obj, inner);
+    float tk;
+    if (slab_decide(o, d, rcp, exact_only, r.tmin, r.tmax, bx, inner, tk)) emit(obj, inner, tk);
   };
   if (!kTlas) {
     for (int k = 0; k < p.n_obj; ++k) test(static_cast<uint32_t>(k));
@@ -68,8 +70,9 @@ __device__ __forceinline__ void for_each_pair(const NifParams& p, const char* tl
   auto test_leaf = [&](const float4 lo, const float4 hi) {
     const float bx[6] = {lo.x, lo.y, lo.z, hi.x, hi.y, hi.z};
     bool inner;
-    if (slab_decide(o, d, rcp, exact_only, r.tmin, r.tmax, bx, inner))
-      emit(static_cast<uint32_t>(__float_as_int(lo.w)), inner);
+    float tk;
+    if (slab_decide(o, d, rcp, exact_only, r.tmin, r.tmax, bx, inner, tk))
+      emit(static_cast<uint32_t>(__float_as_int(lo.w)), inner, tk);
   };
   int32_t stack[bvh::kStack];
   int sp = 0;
@@ -112,7 +115,7 @@ __global__ void __launch_bounds__(256) k_front_count(NifParams p, const char* tl
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
-    for_each_pair<kTlas>(p, tlas, &H, r, [&](uint32_t obj, bool inner) {
+    for_each_pair<kTlas>(p, tlas, &H, r, [&](uint32_t obj, bool inner, float) {
       atomicAdd(&s_cnt[bucket_of(p, obj, inner)], 1u);
     });
   }
@@ -140,7 +143,7 @@ __global__ void __launch_bounds__(256) k_front_count_slots(NifParams p, const ch
        i += (int64_t)gridDim.x * blockDim.x) {
     nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
     int nh = 0;
-    for_each_pair<kTlas>(p, tlas, &H, r, [&](uint32_t obj, bool inner) {
+    for_each_pair<kTlas>(p, tlas, &H, r, [&](uint32_t obj, bool inner, float) {
       atomicAdd(&s_cnt[bucket_of(p, obj, inner)], 1u);
       if (nh < kSlots) slots[static_cast<int64_t>(nh) * n + i] = obj | (inner ? NIF_QUERY_INNER : 0u);
       ++nh;
@@ -158,7 +161,7 @@ __global__ void __launch_bounds__(1024) k_front_scan(const uint32_t* count, int 
                                                      int buckets_per_group, int n_groups,
                                                      int64_t max_q, uint32_t* cursor,
                                                      int64_t* goff, int64_t* total,
-                                                     DevError* err) {
+                                                     DevError* err, const int64_t* base = nullptr) {
   __shared__ int64_t s_part[1024];
   int t = threadIdx.x;
   int per = (n_buckets + blockDim.x - 1) / blockDim.x;
@@ -173,7 +176,8 @@ __global__ void __launch_bounds__(1024) k_front_scan(const uint32_t* count, int 
     s_part[t] += v;
     __syncthreads();
   }
-  int64_t run = s_part[t] - sum;
+  const int64_t start = base ? *base : 0;
+  int64_t run = start + s_part[t] - sum;
   for (int b = b0; b < b1; ++b) {
     int64_t c = run < max_q ? run : max_q;
     cursor[b] = static_cast<uint32_t>(c);
@@ -181,7 +185,7 @@ __global__ void __launch_bounds__(1024) k_front_scan(const uint32_t* count, int 
     run += count[b];
   }
   if (t == blockDim.x - 1) {
-    int64_t all = s_part[t];
+    int64_t all = start + s_part[t];
     goff[n_groups] = all < max_q ? all : max_q;
     *total = all;
     if (all > max_q) raise_error(err, NIF_ERR_WORKSPACE, all);
@@ -207,7 +211,7 @@ __global__ void __launch_bounds__(256) k_front_scatter(NifParams p, const char* 
   int nh = 0;
   if (i < n) {
     nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
-    for_each_pair<kTlas>(p, tlas, &H, r, [&](uint32_t obj, bool inner) {
+    for_each_pair<kTlas>(p, tlas, &H, r, [&](uint32_t obj, bool inner, float) {
       if (nh < kMaxHits) {
         uint32_t b = static_cast<uint32_t>(bucket_of(p, obj, inner));
         hits[nh] = obj | (inner ? NIF_QUERY_INNER : 0u);
@@ -260,7 +264,7 @@ __global__ void __launch_bounds__(256) k_front_scatter_slots(NifParams p, const 
       nh = c;
     } else {
       nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
-      for_each_pair<kTlas>(p, tlas, &H, r, [&](uint32_t obj, bool inner) {
+      for_each_pair<kTlas>(p, tlas, &H, r, [&](uint32_t obj, bool inner, float) {
         if (nh < kMaxHits) hits[nh++] = obj | (inner ? NIF_QUERY_INNER : 0u);
         else raise_error(err, NIF_ERR_BOUNDS, i);
       });
@@ -279,6 +283,183 @@ __global__ void __launch_bounds__(256) k_front_scatter_slots(NifParams p, const 
     if (pos < max_q) {
       out_ray[pos] = static_cast<uint32_t>(i);
       out_qobj[pos] = hits[k];
+    }
+  }
+}
+
+// ------------------------------------------------- front end, two rounds
+// nif_infer answers each ray's nearest pair first (smallest entry parameter:
+// the first object box its segment enters) and then only the other pairs of
+// the rays still unoccluded.  A ray is occluded iff some pair says so (or the
+// caller's bits already say so), so skipping pairs of occluded rays leaves
+// every output bit as querying all pairs would.
+
+__device__ __forceinline__ bool ray_occluded(const uint32_t* bits, int64_t i) {
+  return (__ldg(bits + (i >> 5)) >> (i & 31)) & 1u;
+}
+
+// The pairs of ray i (from its slots, or by traversing again when it has more
+// than kSlots) and the index of its nearest pair; returns the pair count.
+template <bool kTlas>
+__device__ __forceinline__ int ray_pairs(const NifParams& p, const char* tlas, const bvh::Header* H,
+                                         const nif_ray* rays, int64_t i, int64_t n,
+                                         const uint32_t* slots, const uint8_t* nhits,
+                                         const uint8_t* first_k, uint32_t hits[kMaxHits],
+                                         int& first, DevError* err) {
+  const int c = nhits[i];
+  if (c <= kSlots) {
+    for (int k = 0; k < c; ++k) hits[k] = slots[static_cast<int64_t>(k) * n + i];
+    first = first_k[i];
+    return c;
+  }
+  int nh = 0;
+  float bt = INFINITY;
+  first = 0;
+  const nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
+  for_each_pair<kTlas>(p, tlas, H, r, [&](uint32_t obj, bool inner, float tk) {
+    if (nh < kMaxHits) {
+      if (tk < bt) {
+        bt = tk;
+        first = nh;
+      }
+      hits[nh++] = obj | (inner ? NIF_QUERY_INNER : 0u);
+    } else {
+      raise_error(err, NIF_ERR_BOUNDS, i);
+    }
+  });
+  return nh;
+}
+
+__device__ __forceinline__ int bucket_of_q(const NifParams& p, uint32_t q) {
+  return bucket_of(p, q & 0x7fffffffu, (q & NIF_QUERY_INNER) != 0);
+}
+
+// Round 1, count: traverses the top level once per ray not already occluded,
+// keeps the pairs in slots with the nearest one's index, and counts the
+// nearest pairs per bucket.
+template <bool kTlas>
+__global__ void __launch_bounds__(256) k_front_count_first(NifParams p, const char* tlas,
+                                                           const nif_ray* rays, int64_t n,
+                                                           int n_buckets, const uint32_t* bits,
+                                                           uint32_t* g_count, uint32_t* slots,
+                                                           uint8_t* nhits, uint8_t* first_k) {
+  extern __shared__ uint32_t s_cnt[];
+  __shared__ bvh::Header H;
+  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x) s_cnt[b] = 0;
+  if (kTlas && threadIdx.x == 0) H = *reinterpret_cast<const bvh::Header*>(tlas);
+  __syncthreads();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) {
+    int nh = 0, best = 0;
+    float bt = INFINITY;
+    uint32_t bq = 0;
+    if (!ray_occluded(bits, i)) {
+      const nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
+      for_each_pair<kTlas>(p, tlas, &H, r, [&](uint32_t obj, bool inner, float tk) {
+        const uint32_t q = obj | (inner ? NIF_QUERY_INNER : 0u);
+        if (nh < kSlots) slots[static_cast<int64_t>(nh) * n + i] = q;
+        if (tk < bt) {
+          bt = tk;
+          best = nh;
+          bq = q;
+        }
+        ++nh;
+      });
+    }
+    nhits[i] = static_cast<uint8_t>(nh < 255 ? nh : 255);
+    first_k[i] = static_cast<uint8_t>(best < kSlots ? best : 0);
+    if (nh > 0) atomicAdd(&s_cnt[bucket_of_q(p, bq)], 1u);
+  }
+  __syncthreads();
+  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x)
+    if (s_cnt[b]) atomicAdd(&g_count[b], s_cnt[b]);
+}
+
+// Round 1, scatter: each ray's nearest pair into its bucket's range.
+template <bool kTlas>
+__global__ void __launch_bounds__(256) k_front_scatter_first(NifParams p, const char* tlas,
+                                                             const nif_ray* rays, int64_t n,
+                                                             int n_buckets, uint32_t* g_cursor,
+                                                             int64_t max_q, const uint32_t* slots,
+                                                             const uint8_t* nhits,
+                                                             const uint8_t* first_k,
+                                                             uint32_t* out_ray, uint32_t* out_qobj,
+                                                             DevError* err) {
+  extern __shared__ uint32_t s_dyn[];
+  uint32_t* s_cnt = s_dyn;
+  uint32_t* s_base = s_dyn + n_buckets;
+  __shared__ bvh::Header H;
+  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x) s_cnt[b] = 0;
+  if (kTlas && threadIdx.x == 0) H = *reinterpret_cast<const bvh::Header*>(tlas);
+  __syncthreads();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  uint32_t q = 0, rank = 0;
+  int b = -1;
+  if (i < n && nhits[i] > 0) {
+    if (nhits[i] <= kSlots) {
+      q = slots[static_cast<int64_t>(first_k[i]) * n + i];
+    } else {
+      uint32_t hits[kMaxHits];
+      int first = 0;
+      ray_pairs<kTlas>(p, tlas, &H, rays, i, n, slots, nhits, first_k, hits, first, err);
+      q = hits[first];
+    }
+    b = bucket_of_q(p, q);
+    rank = atomicAdd(&s_cnt[b], 1u);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < n_buckets; k += blockDim.x)
+    s_base[k] = s_cnt[k] ? atomicAdd(&g_cursor[k], s_cnt[k]) : 0u;
+  __syncthreads();
+  if (b >= 0) {
+    const int64_t pos = static_cast<int64_t>(s_base[b]) + rank;
+    if (pos < max_q) {
+      out_ray[pos] = static_cast<uint32_t>(i);
+      out_qobj[pos] = q;
+    }
+  }
+}
+
+// Round 2: the other pairs of the rays round 1 left unoccluded, counted
+// (kScatter false) or written after round 1's pairs (kScatter true).
+template <bool kTlas, bool kScatter>
+__global__ void __launch_bounds__(256) k_front_rest(NifParams p, const char* tlas,
+                                                    const nif_ray* rays, int64_t n, int n_buckets,
+                                                    const uint32_t* bits, uint32_t* g_count_or_cursor,
+                                                    int64_t max_q, const uint32_t* slots,
+                                                    const uint8_t* nhits, const uint8_t* first_k,
+                                                    uint32_t* out_ray, uint32_t* out_qobj,
+                                                    DevError* err) {
+  extern __shared__ uint32_t s_dyn[];
+  uint32_t* s_cnt = s_dyn;
+  uint32_t* s_base = s_dyn + n_buckets;
+  __shared__ bvh::Header H;
+  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x) s_cnt[b] = 0;
+  if (kTlas && threadIdx.x == 0) H = *reinterpret_cast<const bvh::Header*>(tlas);
+  __syncthreads();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  uint32_t hits[kMaxHits];
+  uint32_t rank[kMaxHits];
+  int nh = 0, first = -1;
+  if (i < n && nhits[i] > 1 && !ray_occluded(bits, i))
+    nh = ray_pairs<kTlas>(p, tlas, &H, rays, i, n, slots, nhits, first_k, hits, first, err);
+  for (int k = 0; k < nh; ++k)
+    if (k != first) rank[k] = atomicAdd(&s_cnt[bucket_of_q(p, hits[k])], 1u);
+  __syncthreads();
+  if constexpr (!kScatter) {
+    for (int b = threadIdx.x; b < n_buckets; b += blockDim.x)
+      if (s_cnt[b]) atomicAdd(&g_count_or_cursor[b], s_cnt[b]);
+  } else {
+    for (int b = threadIdx.x; b < n_buckets; b += blockDim.x)
+      s_base[b] = s_cnt[b] ? atomicAdd(&g_count_or_cursor[b], s_cnt[b]) : 0u;
+    __syncthreads();
+    for (int k = 0; k < nh; ++k) {
+      if (k == first) continue;
+      const int64_t pos = static_cast<int64_t>(s_base[bucket_of_q(p, hits[k])]) + rank[k];
+      if (pos < max_q) {
+        out_ray[pos] = static_cast<uint32_t>(i);
+        out_qobj[pos] = hits[k];
+      }
     }
   }
 }
@@ -614,6 +795,87 @@ nif_status launch_frontend(const NifParams& p, const void* tlas, const nif_ray* 
     else
       k_front_scatter<false><<<sblocks, 256, sh2, st>>>(p, tl, rays, n, n_buckets, cur, max_q,
                                                         out_ray, out_qobj, err);
+    NIF_LAUNCH_CHECK();
+  }
+  return NIF_OK;
+}
+
+size_t frontend_first_bytes(int64_t n) { return align_up(static_cast<size_t>(n), 256); }
+
+nif_status launch_frontend_first(const NifParams& p, const void* tlas, const nif_ray* rays, int64_t n,
+                                 const uint32_t* bits, uint32_t* out_ray, uint32_t* out_qobj,
+                                 int64_t max_q, int64_t* goff, int64_t* count, void* ws,
+                                 void* slot_area, uint8_t* first_k, cudaStream_t st) {
+  const int n_groups = p.net_mode == NIF_NETS_OBJECT ? p.n_obj : (p.net_mode == NIF_NETS_CLASS ? 2 : 1);
+  const int n_buckets = (p.net_mode == NIF_NETS_CLASS ? 2 : 1) * p.n_obj;
+  const int per_group = p.net_mode == NIF_NETS_OBJECT ? 1 : p.n_obj;
+  DevError* err = static_cast<DevError*>(ws);
+  uint32_t* cnt = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + kErrBytes);
+  uint32_t* cur = cnt + align_up(n_buckets, 64);
+  NIF_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * n_buckets, st));
+  const char* tl = static_cast<const char*>(tlas);
+  uint32_t* slots = static_cast<uint32_t*>(slot_area);
+  uint8_t* nhits = reinterpret_cast<uint8_t*>(static_cast<char*>(slot_area) +
+                                              align_up(static_cast<size_t>(n) * kSlots * 4, 256));
+  const int blocks = static_cast<int>(std::max<int64_t>(1, ceil_div(n, 256)));
+  const size_t sh1 = sizeof(uint32_t) * n_buckets, sh2 = 2 * sh1;
+  if (n > 0) {
+    if (tlas)
+      k_front_count_first<true><<<blocks, 256, sh1, st>>>(p, tl, rays, n, n_buckets, bits, cnt, slots, nhits, first_k);
+    else
+      k_front_count_first<false><<<blocks, 256, sh1, st>>>(p, tl, rays, n, n_buckets, bits, cnt, slots, nhits, first_k);
+    NIF_LAUNCH_CHECK();
+  }
+  k_front_scan<<<1, 1024, 0, st>>>(cnt, n_buckets, per_group, n_groups, max_q, cur, goff, count, err);
+  NIF_LAUNCH_CHECK();
+  if (n > 0) {
+    if (tlas)
+      k_front_scatter_first<true><<<blocks, 256, sh2, st>>>(p, tl, rays, n, n_buckets, cur, max_q, slots,
+                                                             nhits, first_k, out_ray, out_qobj, err);
+    else
+      k_front_scatter_first<false><<<blocks, 256, sh2, st>>>(p, tl, rays, n, n_buckets, cur, max_q, slots,
+                                                              nhits, first_k, out_ray, out_qobj, err);
+    NIF_LAUNCH_CHECK();
+  }
+  return NIF_OK;
+}
+
+nif_status launch_frontend_rest(const NifParams& p, const void* tlas, const nif_ray* rays, int64_t n,
+                                const uint32_t* bits, uint32_t* out_ray, uint32_t* out_qobj,
+                                int64_t max_q, const int64_t* count_first, int64_t* goff,
+                                int64_t* count, void* ws, uint32_t* cnt2, const void* slot_area,
+                                const uint8_t* first_k, cudaStream_t st) {
+  const int n_groups = p.net_mode == NIF_NETS_OBJECT ? p.n_obj : (p.net_mode == NIF_NETS_CLASS ? 2 : 1);
+  const int n_buckets = (p.net_mode == NIF_NETS_CLASS ? 2 : 1) * p.n_obj;
+  const int per_group = p.net_mode == NIF_NETS_OBJECT ? 1 : p.n_obj;
+  DevError* err = static_cast<DevError*>(ws);
+  uint32_t* cur2 = cnt2 + align_up(n_buckets, 64);
+  NIF_CUDA_TRY(cudaMemsetAsync(cnt2, 0, sizeof(uint32_t) * n_buckets, st));
+  const char* tl = static_cast<const char*>(tlas);
+  const uint32_t* slots = static_cast<const uint32_t*>(slot_area);
+  const uint8_t* nhits = reinterpret_cast<const uint8_t*>(static_cast<const char*>(slot_area) +
+                                                          align_up(static_cast<size_t>(n) * kSlots * 4, 256));
+  const int blocks = static_cast<int>(std::max<int64_t>(1, ceil_div(n, 256)));
+  const size_t sh2 = 2 * sizeof(uint32_t) * n_buckets;
+  if (n > 0) {
+    if (tlas)
+      k_front_rest<true, false><<<blocks, 256, sh2, st>>>(p, tl, rays, n, n_buckets, bits, cnt2, max_q, slots,
+                                                          nhits, first_k, nullptr, nullptr, err);
+    else
+      k_front_rest<false, false><<<blocks, 256, sh2, st>>>(p, tl, rays, n, n_buckets, bits, cnt2, max_q, slots,
+                                                           nhits, first_k, nullptr, nullptr, err);
+    NIF_LAUNCH_CHECK();
+  }
+  k_front_scan<<<1, 1024, 0, st>>>(cnt2, n_buckets, per_group, n_groups, max_q, cur2, goff, count, err,
+                                   count_first);
+  NIF_LAUNCH_CHECK();
+  if (n > 0) {
+    if (tlas)
+      k_front_rest<true, true><<<blocks, 256, sh2, st>>>(p, tl, rays, n, n_buckets, bits, cur2, max_q, slots,
+                                                         nhits, first_k, out_ray, out_qobj, err);
+    else
+      k_front_rest<false, true><<<blocks, 256, sh2, st>>>(p, tl, rays, n, n_buckets, bits, cur2, max_q, slots,
+                                                          nhits, first_k, out_ray, out_qobj, err);
     NIF_LAUNCH_CHECK();
   }
   return NIF_OK;

@@ -251,6 +251,14 @@ class NifModel:
                _ptr(bits), _ptr(ws), ws.numel(), _stream(stream))
         return bits
 
+    def infer_query_counts(self, n_rays: int, stream=None) -> torch.Tensor:
+        """Pairs the last infer() queried: [round 1, both rounds] (device int64)."""
+        out = torch.empty(2, dtype=torch.int64, device=self.obj_aabb.device)
+        d = self.desc()
+        L.call("nif_infer_query_counts", ctypes.byref(d), _ptr(self._ws), self._ws.numel(), n_rays,
+               _ptr(out), _stream(stream))
+        return out
+
 
 class Trainer:
     """Adam state for a NifModel (Sec. 5 'Training'): FP32 masters, FP32

@@ -371,3 +371,52 @@ def test_schedules_agree_on_grouped_networks(mlp_dt):
     scale = np.abs(out[SER]).max()
     assert scale > 0.05
     assert np.abs(out[SER] - out[PIPE]).max() <= 1e-5 * max(1.0, scale)
+
+
+@pytest.mark.parametrize("mlp_dt,sched", [("f32", 0), ("f16", SER), ("f16", PIPE), ("bf16", 0)])
+def test_two_round_infer_equals_all_pairs(mlp_dt, sched):
+    """nif_infer's early-out (each ray's nearest pair first, then the other
+    pairs of rays still unoccluded) leaves exactly the bits of querying every
+    pair; rays already occluded on entry are not queried at all."""
+    rng = np.random.default_rng(71)
+    boxes = random_boxes_scene(rng, n_obj=12, extent=3.0)
+    res = [4, 8, 16, 32]
+    V = int(onif.level_layout(res, 12)[2][-1])
+    grid = rng.uniform(-1, 1, size=(12, 2, V * 2)).astype(np.float32)
+    mats = [synth.mlp_init(rng, 24, 64, 3), synth.mlp_init(rng, 24, 64, 3)]
+    model, om = _build(res, 2, 12, boxes, grid, mats, grid_dt="f16", mlp_dt=mlp_dt,
+                       net_mode=L.NIF_NETS_CLASS, schedule=sched)
+    n = 20000
+    o = rng.uniform(-4, 4, size=(n, 3))
+    rays = synth.pack_rays(o, synth.unit_vectors(rng, n), 1e-3, np.inf)
+    rays_t = torch.from_numpy(rays).cuda()
+    tlas = nif.BVH.from_boxes(torch.from_numpy(boxes).cuda())
+    # every pair at once
+    ray_id, qobj, goff, nq = _gpu_queries(model, rays_t, tlas=tlas)
+    all_bits = nif.empty_bits(n)
+    model.infer_queries(rays_t, ray_id, qobj, goff, nq, bits=all_bits)
+    model.check()
+    # two rounds, from zero and from a pre-set mask
+    two = nif.empty_bits(n)
+    model.infer(rays_t, two, tlas=tlas)
+    model.check()
+    counts = model.infer_query_counts(n).cpu().numpy()
+    va = nif.bits_to_bool(all_bits, n).cpu().numpy()
+    vt = nif.bits_to_bool(two, n).cpu().numpy()
+    assert np.array_equal(va, vt)
+    r = ray_id[:nq].cpu().numpy()
+    with_pair = np.unique(r)
+    assert counts[0] == len(with_pair)            # one nearest pair per ray with a pair
+    assert counts[0] < counts[1] < nq             # round 2 skipped pairs of occluded rays
+    assert va.any() and (~va[with_pair]).any()
+    pre = rng.uniform(size=n) < 0.3
+    pre_bits = torch.from_numpy(np.packbits(pre, bitorder="little").view(np.uint8)).cuda()
+    words = torch.zeros((n + 31) // 32 * 4, dtype=torch.uint8, device="cuda")
+    words[:pre_bits.numel()] = pre_bits
+    bits_pre = words.view(torch.int32).clone()
+    model.infer(rays_t, bits_pre, tlas=tlas)
+    model.check()
+    vp = nif.bits_to_bool(bits_pre, n).cpu().numpy()
+    assert np.array_equal(vp, va | pre)
+    c2 = model.infer_query_counts(n).cpu().numpy()
+    assert c2[0] == len(np.setdiff1d(with_pair, np.nonzero(pre)[0]))
