@@ -92,7 +92,13 @@ def queries(rays: np.ndarray, obj_aabb: np.ndarray):
 def entry_exit(rays: np.ndarray, box: np.ndarray):
     """FP64 normalised entry point, exit point and direction of ray segments
     clipped to one box (Eq. 2 with the origin moved onto the box, Sec. 3.1).
-    Returns three float64 [n,3] arrays in [0,1]^3."""
+    Returns three float64 [n,3] arrays in [0,1]^3.
+
+    A segment that enters (leaves) the box through a face has its entry (exit)
+    point on that face, so the coordinate across the face is exactly 0 (the
+    low face) or 1 (the high face): it is set so, not left to o + t d, whose
+    rounding would put the point a hair off the face.  The face is the slab
+    whose near (far) parameter is the segment's t_in (t_out)."""
     r = np.asarray(rays, dtype=np.float64)
     b = np.asarray(box, dtype=np.float64)
     o, d = r[:, 0:3], r[:, 4:7]
@@ -107,6 +113,11 @@ def entry_exit(rays: np.ndarray, box: np.ndarray):
     lo, ext = b[None, 0:3], (b[3:6] - b[0:3])[None, :]
     p_in = np.clip((o + tin[:, None] * d - lo) / ext, 0.0, 1.0)
     p_out = np.clip((o + tout[:, None] * d - lo) / ext, 0.0, 1.0)
+    # moving +: enter through the low face, leave through the high one
+    on_in = ~par & (near == tin[:, None])
+    on_out = ~par & (far == tout[:, None])
+    p_in = np.where(on_in, np.where(d > 0, 0.0, 1.0), p_in)
+    p_out = np.where(on_out, np.where(d > 0, 1.0, 0.0), p_out)
     u_dir = (d + 1.0) * 0.5
     return p_in, p_out, u_dir
 

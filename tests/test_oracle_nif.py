@@ -44,6 +44,42 @@ def test_entry_exit_closed_forms():
     np.testing.assert_allclose(u_dir[0], [0.5, 0.0, 0.5], atol=1e-15)
 
 
+def test_entry_and_exit_points_lie_exactly_on_their_faces():
+    """Eq. 2: the entry point of an outside origin is on the face it enters,
+    the exit point on the face it leaves (the coordinate across the face is
+    exactly 0 or 1, low or high face by the direction's sign); the other two
+    coordinates are the closed form o + t d for t from that face's plane."""
+    box = np.array([0.0, 0.0, 0.0, 1.0, 2.0, 4.0], np.float32)
+    o = np.array([[-0.3, 0.37, 0.91], [1.7, 1.13, 2.2], [0.41, 0.5, 5.3]])
+    d = np.array([[0.93, 0.27, 0.25], [-0.8, 0.1, -0.59], [0.05, 0.11, -0.99]])
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    r = synth.pack_rays(o, d, 0.0, np.inf)
+    p_in, p_out, _ = onif.entry_exit(r, box)
+    rf = r.astype(np.float64)
+    o, d = rf[:, 0:3], rf[:, 4:7]
+    lo, ext = box[:3].astype(np.float64), (box[3:] - box[:3]).astype(np.float64)
+    # slab parameters by hand: ray 0 enters x = 0 (t 0.32/|d|) before y and z
+    # and leaves x = 1 (t 1.40) before y = 2 (6.0) and z = 4 (12.4); ray 1
+    # enters x = 1 (0.875) and leaves x = 0 (2.125) before z = 0 (3.73); ray 2
+    # enters z = 4 (1.31) and leaves z = 0 (5.35) before x = 1 (11.8)
+    faces_in = [(0, 0.0, 0.0), (0, 1.0, 1.0), (2, 4.0, 1.0)]
+    faces_out = [(0, 1.0, 1.0), (0, 0.0, 0.0), (2, 0.0, 0.0)]
+    for i, ((ki, pi, ui), (ko, po, uo)) in enumerate(zip(faces_in, faces_out)):
+        assert p_in[i, ki] == ui and p_out[i, ko] == uo
+        t_in = (pi - o[i, ki]) / d[i, ki]
+        t_out = (po - o[i, ko]) / d[i, ko]
+        for k in range(3):
+            if k != ki:
+                assert abs(p_in[i, k] - (o[i, k] + t_in * d[i, k] - lo[k]) / ext[k]) < 1e-12
+            if k != ko:
+                assert abs(p_out[i, k] - (o[i, k] + t_out * d[i, k] - lo[k]) / ext[k]) < 1e-12
+    # every outer pair of random aimed rays has an entry coordinate of exactly 0 or 1
+    rays = synth.aimed_rays(np.random.default_rng(8), 500, BOX, 6.0)
+    p_in, p_out, _ = onif.entry_exit(rays, BOX)
+    assert np.all(np.any((p_in == 0.0) | (p_in == 1.0), axis=1))
+    assert np.all(np.any((p_out == 0.0) | (p_out == 1.0), axis=1))
+
+
 def test_aliased_rays_share_an_input():
     """Sec. 2 / Sec. 3.1: moving an outside origin along its direction leaves
     the encoder input unchanged."""
