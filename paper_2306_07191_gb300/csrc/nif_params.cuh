@@ -130,21 +130,60 @@ struct QueryPoints {
 };
 
 // Entry and exit points of the clipped segment, normalised to the box, and
-// the direction mapped to (d+1)/2 (Eq. 2 in its 3D form).
+// the direction mapped to (d+1)/2 (Eq. 2 in its 3D form).  The slab
+// parameters are exact_slab's; a point where the segment crosses a face (the
+// slab whose near / far parameter is t_in / t_out) gets the coordinate
+// across that face set to exactly 0 or 1, as the exact entry / exit point
+// has it, so that half of its trilinear corners carry weight exactly zero.
 __device__ __forceinline__ void query_points(const nif_ray& r, const float* box, QueryPoints& q) {
-  float o[3] = {r.ox, r.oy, r.oz}, d[3] = {r.dx, r.dy, r.dz};
-  float tin, tout, entry;
-  exact_slab(o, d, r.tmin, r.tmax, box, tin, tout, entry);
+  const float o[3] = {r.ox, r.oy, r.oz}, d[3] = {r.dx, r.dy, r.dz};
+  float nr[3], fr[3];
+  float en = -INFINITY, ex = INFINITY;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    float lo = box[k], ext = box[3 + k] - box[k];
+    nr[k] = -INFINITY;
+    fr[k] = INFINITY;
+    if (d[k] != 0.0f) {
+      const float t0 = __fdiv_rn(box[k] - o[k], d[k]);
+      const float t1 = __fdiv_rn(box[3 + k] - o[k], d[k]);
+      nr[k] = fminf(t0, t1);
+      fr[k] = fmaxf(t0, t1);
+      en = fmaxf(en, nr[k]);
+      ex = fminf(ex, fr[k]);
+    }
+  }
+  const float tin = fmaxf(r.tmin, en), tout = fminf(r.tmax, ex);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float lo = box[k], ext = box[3 + k] - box[k];
     float a = (o[k] + tin * d[k] - lo) / ext;
     float b = (o[k] + tout * d[k] - lo) / ext;
-    q.u[0][k] = fminf(fmaxf(a, 0.f), 1.f);
-    q.u[1][k] = fminf(fmaxf(b, 0.f), 1.f);
+    a = fminf(fmaxf(a, 0.f), 1.f);
+    b = fminf(fmaxf(b, 0.f), 1.f);
+    if (d[k] != 0.0f && nr[k] == tin) a = d[k] > 0.0f ? 0.f : 1.f;
+    if (d[k] != 0.0f && fr[k] == tout) b = d[k] > 0.0f ? 1.f : 0.f;
+    q.u[0][k] = a;
+    q.u[1][k] = b;
     q.u[2][k] = (d[k] + 1.0f) * 0.5f;
   }
 }
+
+// Corner values of one lookup; corners of weight exactly zero (a point on a
+// cell face) add nothing and are not loaded.
+template <typename Raw>
+__device__ __forceinline__ Raw raw_zero();
+template <>
+__device__ __forceinline__ __half2 raw_zero<__half2>() { return __floats2half2_rn(0.f, 0.f); }
+template <>
+__device__ __forceinline__ float2 raw_zero<float2>() { return make_float2(0.f, 0.f); }
+
+template <typename Raw>
+__device__ __forceinline__ void load_corners(const Raw* tab, const uint32_t idx[8], const float w[8],
+                                             Raw v[8]) {
+#pragma unroll
+  for (int c = 0; c < 8; ++c) v[c] = w[c] != 0.f ? __ldg(tab + idx[c]) : raw_zero<Raw>();
+}
+
 
 // Cell, fractions and the 8 vertex indices of a point at one level.
 struct Taps {
@@ -305,9 +344,7 @@ __device__ __forceinline__ void gather_level(const TG* table, const Taps& t, flo
   for (int f = 0; f < F; ++f) out[f] = 0.f;
   if constexpr (F == 2 && sizeof(TG) == 2) {
     __half2 v[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c)
-      v[c] = __ldg(reinterpret_cast<const __half2*>(table) + t.idx[c]);
+    load_corners(reinterpret_cast<const __half2*>(table), t.idx, t.w, v);
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       float2 fv = __half22float2(v[c]);
@@ -316,8 +353,7 @@ __device__ __forceinline__ void gather_level(const TG* table, const Taps& t, flo
     }
   } else if constexpr (F == 2 && sizeof(TG) == 4) {
     float2 v[8];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) v[c] = __ldg(reinterpret_cast<const float2*>(table) + t.idx[c]);
+    load_corners(reinterpret_cast<const float2*>(table), t.idx, t.w, v);
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
       out[0] += t.w[c] * v[c].x;
@@ -326,6 +362,7 @@ __device__ __forceinline__ void gather_level(const TG* table, const Taps& t, flo
   } else {
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
+      if (t.w[c] == 0.f) continue;  // a point on a cell face: corner adds nothing
 #pragma unroll
       for (int f = 0; f < F; ++f) {
         float v;

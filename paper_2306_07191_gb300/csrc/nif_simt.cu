@@ -103,56 +103,69 @@ __device__ __forceinline__ void for_each_pair(const NifParams& p, const char* tl
   }
 }
 
-template <bool kTlas>
-__global__ void __launch_bounds__(256) k_front_count(NifParams p, const char* tlas,
-                                                     const nif_ray* rays, int64_t n, int n_buckets,
-                                                     uint32_t* g_count) {
-  extern __shared__ uint32_t s_cnt[];
-  __shared__ bvh::Header H;
-  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x) s_cnt[b] = 0;
-  if (kTlas && threadIdx.x == 0) H = *reinterpret_cast<const bvh::Header*>(tlas);
-  __syncthreads();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
-    for_each_pair<kTlas>(p, tlas, &H, r, [&](uint32_t obj, bool inner, float) {
-      atomicAdd(&s_cnt[bucket_of(p, obj, inner)], 1u);
-    });
+// Warp-aggregated claim on counters[key] for every lane with `valid`: lanes
+// sharing a key get consecutive values from one atomicAdd by their leader.
+// Returns this lane's value.  All 32 lanes must call it together.
+__device__ __forceinline__ uint32_t warp_claim(uint32_t* counters, int key, bool valid) {
+  const uint32_t act = __ballot_sync(0xffffffffu, valid);
+  uint32_t out = 0;
+  if (valid) {
+    const uint32_t peers = __match_any_sync(act, key);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&counters[key], static_cast<uint32_t>(__popc(peers)));
+    base = __shfl_sync(peers, base, leader);
+    out = base + static_cast<uint32_t>(__popc(peers & ((1u << lane) - 1u)));
   }
-  __syncthreads();
-  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x)
-    if (s_cnt[b]) atomicAdd(&g_count[b], s_cnt[b]);
+  return out;
 }
 
-// Count pass that also keeps each ray's first kSlots pairs (slot-major
-// [kSlots][n], with the pair count in nhits[i]) so the scatter pass need not
-// traverse the top level again.
-constexpr int kSlots = 8;
+__device__ __forceinline__ int bucket_of_q(const NifParams& p, uint32_t q) {
+  return bucket_of(p, q & 0x7fffffffu, (q & NIF_QUERY_INNER) != 0);
+}
 
-template <bool kTlas>
-__global__ void __launch_bounds__(256) k_front_count_slots(NifParams p, const char* tlas,
-                                                           const nif_ray* rays, int64_t n,
-                                                           int n_buckets, uint32_t* g_count,
-                                                           uint32_t* slots, uint8_t* nhits) {
-  extern __shared__ uint32_t s_cnt[];
-  __shared__ bvh::Header H;
-  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x) s_cnt[b] = 0;
-  if (kTlas && threadIdx.x == 0) H = *reinterpret_cast<const bvh::Header*>(tlas);
-  __syncthreads();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
-    int nh = 0;
-    for_each_pair<kTlas>(p, tlas, &H, r, [&](uint32_t obj, bool inner, float) {
-      atomicAdd(&s_cnt[bucket_of(p, obj, inner)], 1u);
-      if (nh < kSlots) slots[static_cast<int64_t>(nh) * n + i] = obj | (inner ? NIF_QUERY_INNER : 0u);
+__device__ __forceinline__ const bvh::Header* tlas_header(const char* tlas) {
+  return reinterpret_cast<const bvh::Header*>(tlas);
+}
+
+// Count pass (one ray per thread, no block barriers: each warp retires on
+// its own): pairs per bucket; with slots, also each ray's first kSlots pairs
+// (slot-major [kSlots][n]) and its pair count, so that the scatter pass need
+// not traverse the top level again.
+#ifndef NIF_FRONT_SLOTS
+#define NIF_FRONT_SLOTS 8
+#endif
+constexpr int kSlots = NIF_FRONT_SLOTS;
+static_assert(kSlots >= 1 && kSlots <= 64, "slots per ray");
+
+template <bool kTlas, bool kKeep>
+__global__ void __launch_bounds__(128) k_front_count(NifParams p, const char* tlas,
+                                                     const nif_ray* rays, int64_t n,
+                                                     uint32_t* g_count, uint32_t* slots,
+                                                     uint8_t* nhits) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int nh = 0;
+  uint32_t hits[kSlots];  // the first kSlots pairs, claimed after the traversal
+  if (i < n) {
+    const nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
+    for_each_pair<kTlas>(p, tlas, tlas_header(tlas), r, [&](uint32_t obj, bool inner, float) {
+      const uint32_t v = obj | (inner ? NIF_QUERY_INNER : 0u);
+      if (nh < kSlots) {
+        hits[nh] = v;
+        if (kKeep) slots[static_cast<int64_t>(nh) * n + i] = v;
+      } else {
+        atomicAdd(&g_count[bucket_of_q(p, v)], 1u);  // rare: beyond the slots
+      }
       ++nh;
     });
-    nhits[i] = static_cast<uint8_t>(nh < 255 ? nh : 255);
+    if (kKeep) nhits[i] = static_cast<uint8_t>(nh < 255 ? nh : 255);
   }
-  __syncthreads();
-  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x)
-    if (s_cnt[b]) atomicAdd(&g_count[b], s_cnt[b]);
+  const int most = __reduce_max_sync(0xffffffffu, nh < kSlots ? nh : kSlots);
+  for (int k = 0; k < most; ++k) {
+    const bool v = k < nh;
+    warp_claim(g_count, v ? bucket_of_q(p, hits[k]) : 0, v);
+  }
 }
 
 // Single block: exclusive scan of bucket counts into bucket cursors, group
@@ -192,99 +205,44 @@ __global__ void __launch_bounds__(1024) k_front_scan(const uint32_t* count, int 
   }
 }
 
-template <bool kTlas>
-__global__ void __launch_bounds__(256) k_front_scatter(NifParams p, const char* tlas,
+// Scatter pass: each pair to its bucket's range, ranks claimed per warp.
+// Pairs come from the slots or, for rays with more than kSlots (or without
+// slots), from traversing again.
+template <bool kTlas, bool kSlotsIn>
+__global__ void __launch_bounds__(128) k_front_scatter(NifParams p, const char* tlas,
                                                        const nif_ray* rays, int64_t n,
-                                                       int n_buckets, uint32_t* g_cursor,
-                                                       int64_t max_q, uint32_t* out_ray,
-                                                       uint32_t* out_qobj, DevError* err) {
-  extern __shared__ uint32_t s_dyn[];
-  uint32_t* s_cnt = s_dyn;
-  uint32_t* s_base = s_dyn + n_buckets;
-  __shared__ bvh::Header H;
-  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x) s_cnt[b] = 0;
-  if (kTlas && threadIdx.x == 0) H = *reinterpret_cast<const bvh::Header*>(tlas);
-  __syncthreads();
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+                                                       uint32_t* g_cursor, int64_t max_q,
+                                                       const uint32_t* slots, const uint8_t* nhits,
+                                                       uint32_t* out_ray, uint32_t* out_qobj,
+                                                       DevError* err) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  auto put = [&](uint32_t v, bool valid) {
+    const uint32_t pos = warp_claim(g_cursor, valid ? bucket_of_q(p, v) : 0, valid);
+    if (valid && pos < max_q) {
+      out_ray[pos] = static_cast<uint32_t>(i);
+      out_qobj[pos] = v;
+    }
+  };
+  const int c = (kSlotsIn && i < n) ? nhits[i] : 0;
+  const bool from_slots = kSlotsIn && c <= kSlots;
+  // slot path: claimed slot by slot, up to the warp's longest slot list
+  const int ms = __reduce_max_sync(0xffffffffu, from_slots ? c : 0);
+  for (int k = 0; k < ms; ++k) {
+    const bool v = from_slots && k < c;
+    put(v ? slots[static_cast<int64_t>(k) * n + i] : 0u, v);
+  }
+  // traversal path (warp-uniform loop over the longest pair list in the warp)
   uint32_t hits[kMaxHits];
-  uint32_t slot[kMaxHits];
   int nh = 0;
-  if (i < n) {
-    nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
-    for_each_pair<kTlas>(p, tlas, &H, r, [&](uint32_t obj, bool inner, float) {
-      if (nh < kMaxHits) {
-        uint32_t b = static_cast<uint32_t>(bucket_of(p, obj, inner));
-        hits[nh] = obj | (inner ? NIF_QUERY_INNER : 0u);
-        slot[nh] = b;
-        ++nh;
-      } else {
-        raise_error(err, NIF_ERR_BOUNDS, i);
-      }
+  if (i < n && !from_slots) {
+    const nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
+    for_each_pair<kTlas>(p, tlas, tlas_header(tlas), r, [&](uint32_t obj, bool inner, float) {
+      if (nh < kMaxHits) hits[nh++] = obj | (inner ? NIF_QUERY_INNER : 0u);
+      else raise_error(err, NIF_ERR_BOUNDS, i);
     });
   }
-  // local ranks inside the block
-  uint32_t rank[kMaxHits];
-  for (int k = 0; k < nh; ++k) rank[k] = atomicAdd(&s_cnt[slot[k]], 1u);
-  __syncthreads();
-  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x)
-    s_base[b] = s_cnt[b] ? atomicAdd(&g_cursor[b], s_cnt[b]) : 0u;
-  __syncthreads();
-  for (int k = 0; k < nh; ++k) {
-    int64_t pos = static_cast<int64_t>(s_base[slot[k]]) + rank[k];
-    if (pos < max_q) {
-      out_ray[pos] = static_cast<uint32_t>(i);
-      out_qobj[pos] = hits[k];
-    }
-  }
-}
-
-// Scatter from the slots; a ray with more than kSlots pairs is traversed again.
-template <bool kTlas>
-__global__ void __launch_bounds__(256) k_front_scatter_slots(NifParams p, const char* tlas,
-                                                             const nif_ray* rays, int64_t n,
-                                                             int n_buckets, uint32_t* g_cursor,
-                                                             int64_t max_q, const uint32_t* slots,
-                                                             const uint8_t* nhits,
-                                                             uint32_t* out_ray, uint32_t* out_qobj,
-                                                             DevError* err) {
-  extern __shared__ uint32_t s_dyn[];
-  uint32_t* s_cnt = s_dyn;
-  uint32_t* s_base = s_dyn + n_buckets;
-  __shared__ bvh::Header H;
-  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x) s_cnt[b] = 0;
-  if (kTlas && threadIdx.x == 0) H = *reinterpret_cast<const bvh::Header*>(tlas);
-  __syncthreads();
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  uint32_t hits[kMaxHits];
-  int nh = 0;
-  if (i < n) {
-    const int c = nhits[i];
-    if (c <= kSlots) {
-      for (int k = 0; k < c; ++k) hits[k] = slots[static_cast<int64_t>(k) * n + i];
-      nh = c;
-    } else {
-      nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
-      for_each_pair<kTlas>(p, tlas, &H, r, [&](uint32_t obj, bool inner, float) {
-        if (nh < kMaxHits) hits[nh++] = obj | (inner ? NIF_QUERY_INNER : 0u);
-        else raise_error(err, NIF_ERR_BOUNDS, i);
-      });
-    }
-  }
-  uint32_t rank[kMaxHits];
-  for (int k = 0; k < nh; ++k)
-    rank[k] = atomicAdd(&s_cnt[bucket_of(p, hits[k] & 0x7fffffffu, hits[k] & NIF_QUERY_INNER)], 1u);
-  __syncthreads();
-  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x)
-    s_base[b] = s_cnt[b] ? atomicAdd(&g_cursor[b], s_cnt[b]) : 0u;
-  __syncthreads();
-  for (int k = 0; k < nh; ++k) {
-    const int b = bucket_of(p, hits[k] & 0x7fffffffu, hits[k] & NIF_QUERY_INNER);
-    const int64_t pos = static_cast<int64_t>(s_base[b]) + rank[k];
-    if (pos < max_q) {
-      out_ray[pos] = static_cast<uint32_t>(i);
-      out_qobj[pos] = hits[k];
-    }
-  }
+  const int most = __reduce_max_sync(0xffffffffu, nh);
+  for (int k = 0; k < most; ++k) put(k < nh ? hits[k] : 0u, k < nh);
 }
 
 // ------------------------------------------------- front end, two rounds
@@ -298,25 +256,18 @@ __device__ __forceinline__ bool ray_occluded(const uint32_t* bits, int64_t i) {
   return (__ldg(bits + (i >> 5)) >> (i & 31)) & 1u;
 }
 
-// The pairs of ray i (from its slots, or by traversing again when it has more
-// than kSlots) and the index of its nearest pair; returns the pair count.
+// The pairs of a ray with more than kSlots of them, by traversing again, and
+// the index of its nearest pair; returns the pair count.
 template <bool kTlas>
-__device__ __forceinline__ int ray_pairs(const NifParams& p, const char* tlas, const bvh::Header* H,
-                                         const nif_ray* rays, int64_t i, int64_t n,
-                                         const uint32_t* slots, const uint8_t* nhits,
-                                         const uint8_t* first_k, uint32_t hits[kMaxHits],
-                                         int& first, DevError* err) {
-  const int c = nhits[i];
-  if (c <= kSlots) {
-    for (int k = 0; k < c; ++k) hits[k] = slots[static_cast<int64_t>(k) * n + i];
-    first = first_k[i];
-    return c;
-  }
+__device__ __forceinline__ int ray_pairs_traverse(const NifParams& p, const char* tlas,
+                                                  const nif_ray* rays, int64_t i,
+                                                  uint32_t hits[kMaxHits], int& first,
+                                                  DevError* err) {
   int nh = 0;
   float bt = INFINITY;
   first = 0;
   const nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
-  for_each_pair<kTlas>(p, tlas, H, r, [&](uint32_t obj, bool inner, float tk) {
+  for_each_pair<kTlas>(p, tlas, tlas_header(tlas), r, [&](uint32_t obj, bool inner, float tk) {
     if (nh < kMaxHits) {
       if (tk < bt) {
         bt = tk;
@@ -330,32 +281,23 @@ __device__ __forceinline__ int ray_pairs(const NifParams& p, const char* tlas, c
   return nh;
 }
 
-__device__ __forceinline__ int bucket_of_q(const NifParams& p, uint32_t q) {
-  return bucket_of(p, q & 0x7fffffffu, (q & NIF_QUERY_INNER) != 0);
-}
-
 // Round 1, count: traverses the top level once per ray not already occluded,
-// keeps the pairs in slots with the nearest one's index, and counts the
-// nearest pairs per bucket.
+// keeps the first kSlots pairs in slots with the nearest one's index, and
+// counts the nearest pairs per bucket.
 template <bool kTlas>
-__global__ void __launch_bounds__(256) k_front_count_first(NifParams p, const char* tlas,
+__global__ void __launch_bounds__(128) k_front_count_first(NifParams p, const char* tlas,
                                                            const nif_ray* rays, int64_t n,
-                                                           int n_buckets, const uint32_t* bits,
-                                                           uint32_t* g_count, uint32_t* slots,
-                                                           uint8_t* nhits, uint8_t* first_k) {
-  extern __shared__ uint32_t s_cnt[];
-  __shared__ bvh::Header H;
-  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x) s_cnt[b] = 0;
-  if (kTlas && threadIdx.x == 0) H = *reinterpret_cast<const bvh::Header*>(tlas);
-  __syncthreads();
+                                                           const uint32_t* bits, uint32_t* g_count,
+                                                           uint32_t* slots, uint8_t* nhits,
+                                                           uint8_t* first_k) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int nh = 0, best = 0;
+  float bt = INFINITY;
+  uint32_t bq = 0;
   if (i < n) {
-    int nh = 0, best = 0;
-    float bt = INFINITY;
-    uint32_t bq = 0;
     if (!ray_occluded(bits, i)) {
       const nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
-      for_each_pair<kTlas>(p, tlas, &H, r, [&](uint32_t obj, bool inner, float tk) {
+      for_each_pair<kTlas>(p, tlas, tlas_header(tlas), r, [&](uint32_t obj, bool inner, float tk) {
         const uint32_t q = obj | (inner ? NIF_QUERY_INNER : 0u);
         if (nh < kSlots) slots[static_cast<int64_t>(nh) * n + i] = q;
         if (tk < bt) {
@@ -368,100 +310,71 @@ __global__ void __launch_bounds__(256) k_front_count_first(NifParams p, const ch
     }
     nhits[i] = static_cast<uint8_t>(nh < 255 ? nh : 255);
     first_k[i] = static_cast<uint8_t>(best < kSlots ? best : 0);
-    if (nh > 0) atomicAdd(&s_cnt[bucket_of_q(p, bq)], 1u);
   }
-  __syncthreads();
-  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x)
-    if (s_cnt[b]) atomicAdd(&g_count[b], s_cnt[b]);
+  warp_claim(g_count, nh > 0 ? bucket_of_q(p, bq) : 0, nh > 0);
 }
 
 // Round 1, scatter: each ray's nearest pair into its bucket's range.
 template <bool kTlas>
-__global__ void __launch_bounds__(256) k_front_scatter_first(NifParams p, const char* tlas,
+__global__ void __launch_bounds__(128) k_front_scatter_first(NifParams p, const char* tlas,
                                                              const nif_ray* rays, int64_t n,
-                                                             int n_buckets, uint32_t* g_cursor,
-                                                             int64_t max_q, const uint32_t* slots,
+                                                             uint32_t* g_cursor, int64_t max_q,
+                                                             const uint32_t* slots,
                                                              const uint8_t* nhits,
                                                              const uint8_t* first_k,
                                                              uint32_t* out_ray, uint32_t* out_qobj,
                                                              DevError* err) {
-  extern __shared__ uint32_t s_dyn[];
-  uint32_t* s_cnt = s_dyn;
-  uint32_t* s_base = s_dyn + n_buckets;
-  __shared__ bvh::Header H;
-  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x) s_cnt[b] = 0;
-  if (kTlas && threadIdx.x == 0) H = *reinterpret_cast<const bvh::Header*>(tlas);
-  __syncthreads();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  uint32_t q = 0, rank = 0;
-  int b = -1;
-  if (i < n && nhits[i] > 0) {
-    if (nhits[i] <= kSlots) {
-      q = slots[static_cast<int64_t>(first_k[i]) * n + i];
-    } else {
-      uint32_t hits[kMaxHits];
-      int first = 0;
-      ray_pairs<kTlas>(p, tlas, &H, rays, i, n, slots, nhits, first_k, hits, first, err);
-      q = hits[first];
-    }
-    b = bucket_of_q(p, q);
-    rank = atomicAdd(&s_cnt[b], 1u);
+  const int c = i < n ? nhits[i] : 0;
+  uint32_t q = 0;
+  if (c > 0 && c <= kSlots) {
+    q = slots[static_cast<int64_t>(first_k[i]) * n + i];
+  } else if (c > kSlots) {
+    uint32_t hits[kMaxHits];
+    int first = 0;
+    ray_pairs_traverse<kTlas>(p, tlas, rays, i, hits, first, err);
+    q = hits[first];
   }
-  __syncthreads();
-  for (int k = threadIdx.x; k < n_buckets; k += blockDim.x)
-    s_base[k] = s_cnt[k] ? atomicAdd(&g_cursor[k], s_cnt[k]) : 0u;
-  __syncthreads();
-  if (b >= 0) {
-    const int64_t pos = static_cast<int64_t>(s_base[b]) + rank;
-    if (pos < max_q) {
-      out_ray[pos] = static_cast<uint32_t>(i);
-      out_qobj[pos] = q;
-    }
+  const uint32_t pos = warp_claim(g_cursor, c > 0 ? bucket_of_q(p, q) : 0, c > 0);
+  if (c > 0 && pos < max_q) {
+    out_ray[pos] = static_cast<uint32_t>(i);
+    out_qobj[pos] = q;
   }
 }
 
 // Round 2: the other pairs of the rays round 1 left unoccluded, counted
 // (kScatter false) or written after round 1's pairs (kScatter true).
 template <bool kTlas, bool kScatter>
-__global__ void __launch_bounds__(256) k_front_rest(NifParams p, const char* tlas,
-                                                    const nif_ray* rays, int64_t n, int n_buckets,
-                                                    const uint32_t* bits, uint32_t* g_count_or_cursor,
+__global__ void __launch_bounds__(128) k_front_rest(NifParams p, const char* tlas,
+                                                    const nif_ray* rays, int64_t n,
+                                                    const uint32_t* bits, uint32_t* g_counter,
                                                     int64_t max_q, const uint32_t* slots,
                                                     const uint8_t* nhits, const uint8_t* first_k,
                                                     uint32_t* out_ray, uint32_t* out_qobj,
                                                     DevError* err) {
-  extern __shared__ uint32_t s_dyn[];
-  uint32_t* s_cnt = s_dyn;
-  uint32_t* s_base = s_dyn + n_buckets;
-  __shared__ bvh::Header H;
-  for (int b = threadIdx.x; b < n_buckets; b += blockDim.x) s_cnt[b] = 0;
-  if (kTlas && threadIdx.x == 0) H = *reinterpret_cast<const bvh::Header*>(tlas);
-  __syncthreads();
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  uint32_t hits[kMaxHits];
-  uint32_t rank[kMaxHits];
-  int nh = 0, first = -1;
-  if (i < n && nhits[i] > 1 && !ray_occluded(bits, i))
-    nh = ray_pairs<kTlas>(p, tlas, &H, rays, i, n, slots, nhits, first_k, hits, first, err);
-  for (int k = 0; k < nh; ++k)
-    if (k != first) rank[k] = atomicAdd(&s_cnt[bucket_of_q(p, hits[k])], 1u);
-  __syncthreads();
-  if constexpr (!kScatter) {
-    for (int b = threadIdx.x; b < n_buckets; b += blockDim.x)
-      if (s_cnt[b]) atomicAdd(&g_count_or_cursor[b], s_cnt[b]);
-  } else {
-    for (int b = threadIdx.x; b < n_buckets; b += blockDim.x)
-      s_base[b] = s_cnt[b] ? atomicAdd(&g_count_or_cursor[b], s_cnt[b]) : 0u;
-    __syncthreads();
-    for (int k = 0; k < nh; ++k) {
-      if (k == first) continue;
-      const int64_t pos = static_cast<int64_t>(s_base[bucket_of_q(p, hits[k])]) + rank[k];
-      if (pos < max_q) {
-        out_ray[pos] = static_cast<uint32_t>(i);
-        out_qobj[pos] = hits[k];
-      }
+  int c = i < n ? nhits[i] : 0;
+  if (c > 1 && ray_occluded(bits, i)) c = 0;
+  const bool from_slots = c > 1 && c <= kSlots;
+  const int first = from_slots ? first_k[i] : -1;
+  auto put = [&](uint32_t v, bool valid) {
+    const uint32_t pos = warp_claim(g_counter, valid ? bucket_of_q(p, v) : 0, valid);
+    if (kScatter && valid && pos < max_q) {
+      out_ray[pos] = static_cast<uint32_t>(i);
+      out_qobj[pos] = v;
     }
+  };
+  const int ms = __reduce_max_sync(0xffffffffu, from_slots ? c : 0);
+  for (int k = 0; k < ms; ++k) {
+    const bool v = from_slots && k < c && k != first;
+    put(v ? slots[static_cast<int64_t>(k) * n + i] : 0u, v);
   }
+  // rays with more pairs than slots: traverse again
+  uint32_t hits[kMaxHits];
+  int nh = 0, f2 = -1;
+  if (c > kSlots) nh = ray_pairs_traverse<kTlas>(p, tlas, rays, i, hits, f2, err);
+  const int most = __reduce_max_sync(0xffffffffu, nh);
+  for (int k = 0; k < most; ++k) put(k < nh ? hits[k] : 0u, k < nh && k != f2);
 }
 
 // ------------------------------------------------------------ encode only
@@ -681,6 +594,7 @@ __global__ void __launch_bounds__(128) k_grid_bwd(NifParams p, const nif_ray* ra
       for (int f = 0; f < F; ++f) d[f] = dx[static_cast<int64_t>((j * p.L + l) * F + f) * ld + q];
 #pragma unroll
       for (int c = 0; c < 8; ++c) {
+        if (t.w[c] == 0.f) continue;  // a point on a cell face: nothing to add
         if constexpr (F == 2) {
           atomicAdd(reinterpret_cast<float2*>(g) + t.idx[c], make_float2(t.w[c] * d[0], t.w[c] * d[1]));
         } else {
@@ -748,53 +662,66 @@ size_t frontend_slot_bytes(int64_t n) {
          align_up(static_cast<size_t>(n), 256);
 }
 
+// Bucket bookkeeping of the front end: buckets are (object) or (object,
+// inner) for class networks; groups are networks.
+struct FrontShape {
+  int n_groups, n_buckets, per_group;
+};
+static FrontShape front_shape(const NifParams& p) {
+  FrontShape f;
+  f.n_groups = p.net_mode == NIF_NETS_OBJECT ? p.n_obj : (p.net_mode == NIF_NETS_CLASS ? 2 : 1);
+  f.n_buckets = (p.net_mode == NIF_NETS_CLASS ? 2 : 1) * p.n_obj;
+  f.per_group = p.net_mode == NIF_NETS_OBJECT ? 1 : p.n_obj;
+  return f;
+}
+static uint8_t* slot_counts(void* slot_area, int64_t n) {
+  return reinterpret_cast<uint8_t*>(static_cast<char*>(slot_area) +
+                                    align_up(static_cast<size_t>(n) * kSlots * 4, 256));
+}
+
+// One ray per thread, 128-thread blocks without barriers: warps retire as
+// soon as their own rays are done.
+constexpr int kFrontThreads = 128;
+
 nif_status launch_frontend(const NifParams& p, const void* tlas, const nif_ray* rays, int64_t n,
                            uint32_t* out_ray, uint32_t* out_qobj, int64_t max_q, int64_t* goff,
                            int64_t* count, void* ws, cudaStream_t st, void* slot_area) {
-  int n_groups = p.net_mode == NIF_NETS_OBJECT ? p.n_obj : (p.net_mode == NIF_NETS_CLASS ? 2 : 1);
-  int n_buckets = (p.net_mode == NIF_NETS_CLASS ? 2 : 1) * p.n_obj;
-  int per_group = p.net_mode == NIF_NETS_OBJECT ? 1 : p.n_obj;
+  const FrontShape f = front_shape(p);
   DevError* err = static_cast<DevError*>(ws);
   uint32_t* cnt = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + kErrBytes);
-  uint32_t* cur = cnt + align_up(n_buckets, 64);
-  NIF_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * n_buckets, st));
-  // one ray per thread: blocks retire independently, so a block with a few
-  // long traversals does not hold a grid-stride loop's barrier
-  int blocks = static_cast<int>(std::max<int64_t>(1, ceil_div(n, 256)));
-  size_t sh1 = sizeof(uint32_t) * n_buckets;
+  uint32_t* cur = cnt + align_up(f.n_buckets, 64);
+  NIF_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * f.n_buckets, st));
+  const int blocks = static_cast<int>(std::max<int64_t>(1, ceil_div(n, kFrontThreads)));
   const char* tl = static_cast<const char*>(tlas);
   uint32_t* slots = static_cast<uint32_t*>(slot_area);
-  uint8_t* nhits = slot_area ? reinterpret_cast<uint8_t*>(static_cast<char*>(slot_area) +
-                                                         align_up(static_cast<size_t>(n) * kSlots * 4, 256))
-                             : nullptr;
+  uint8_t* nhits = slot_area ? slot_counts(slot_area, n) : nullptr;
   if (n > 0) {
     if (slots) {
-      if (tlas) k_front_count_slots<true><<<blocks, 256, sh1, st>>>(p, tl, rays, n, n_buckets, cnt, slots, nhits);
-      else k_front_count_slots<false><<<blocks, 256, sh1, st>>>(p, tl, rays, n, n_buckets, cnt, slots, nhits);
+      if (tlas) k_front_count<true, true><<<blocks, kFrontThreads, 0, st>>>(p, tl, rays, n, cnt, slots, nhits);
+      else k_front_count<false, true><<<blocks, kFrontThreads, 0, st>>>(p, tl, rays, n, cnt, slots, nhits);
     } else {
-      if (tlas) k_front_count<true><<<blocks, 256, sh1, st>>>(p, tl, rays, n, n_buckets, cnt);
-      else k_front_count<false><<<blocks, 256, sh1, st>>>(p, tl, rays, n, n_buckets, cnt);
+      if (tlas) k_front_count<true, false><<<blocks, kFrontThreads, 0, st>>>(p, tl, rays, n, cnt, nullptr, nullptr);
+      else k_front_count<false, false><<<blocks, kFrontThreads, 0, st>>>(p, tl, rays, n, cnt, nullptr, nullptr);
     }
     NIF_LAUNCH_CHECK();
   }
-  k_front_scan<<<1, 1024, 0, st>>>(cnt, n_buckets, per_group, n_groups, max_q, cur, goff, count, err);
+  k_front_scan<<<1, 1024, 0, st>>>(cnt, f.n_buckets, f.per_group, f.n_groups, max_q, cur, goff, count, err);
   NIF_LAUNCH_CHECK();
   if (n > 0) {
-    int sblocks = static_cast<int>(ceil_div(n, 256));
-    size_t sh2 = 2 * sizeof(uint32_t) * n_buckets;
     if (slots) {
       if (tlas)
-        k_front_scatter_slots<true><<<sblocks, 256, sh2, st>>>(p, tl, rays, n, n_buckets, cur, max_q, slots,
-                                                               nhits, out_ray, out_qobj, err);
+        k_front_scatter<true, true><<<blocks, kFrontThreads, 0, st>>>(p, tl, rays, n, cur, max_q, slots, nhits,
+                                                                      out_ray, out_qobj, err);
       else
-        k_front_scatter_slots<false><<<sblocks, 256, sh2, st>>>(p, tl, rays, n, n_buckets, cur, max_q, slots,
-                                                                nhits, out_ray, out_qobj, err);
-    } else if (tlas)
-      k_front_scatter<true><<<sblocks, 256, sh2, st>>>(p, tl, rays, n, n_buckets, cur, max_q, out_ray,
-                                                       out_qobj, err);
-    else
-      k_front_scatter<false><<<sblocks, 256, sh2, st>>>(p, tl, rays, n, n_buckets, cur, max_q,
-                                                        out_ray, out_qobj, err);
+        k_front_scatter<false, true><<<blocks, kFrontThreads, 0, st>>>(p, tl, rays, n, cur, max_q, slots, nhits,
+                                                                       out_ray, out_qobj, err);
+    } else if (tlas) {
+      k_front_scatter<true, false><<<blocks, kFrontThreads, 0, st>>>(p, tl, rays, n, cur, max_q, nullptr,
+                                                                     nullptr, out_ray, out_qobj, err);
+    } else {
+      k_front_scatter<false, false><<<blocks, kFrontThreads, 0, st>>>(p, tl, rays, n, cur, max_q, nullptr,
+                                                                      nullptr, out_ray, out_qobj, err);
+    }
     NIF_LAUNCH_CHECK();
   }
   return NIF_OK;
@@ -806,35 +733,31 @@ nif_status launch_frontend_first(const NifParams& p, const void* tlas, const nif
                                  const uint32_t* bits, uint32_t* out_ray, uint32_t* out_qobj,
                                  int64_t max_q, int64_t* goff, int64_t* count, void* ws,
                                  void* slot_area, uint8_t* first_k, cudaStream_t st) {
-  const int n_groups = p.net_mode == NIF_NETS_OBJECT ? p.n_obj : (p.net_mode == NIF_NETS_CLASS ? 2 : 1);
-  const int n_buckets = (p.net_mode == NIF_NETS_CLASS ? 2 : 1) * p.n_obj;
-  const int per_group = p.net_mode == NIF_NETS_OBJECT ? 1 : p.n_obj;
+  const FrontShape f = front_shape(p);
   DevError* err = static_cast<DevError*>(ws);
   uint32_t* cnt = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + kErrBytes);
-  uint32_t* cur = cnt + align_up(n_buckets, 64);
-  NIF_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * n_buckets, st));
+  uint32_t* cur = cnt + align_up(f.n_buckets, 64);
+  NIF_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * f.n_buckets, st));
   const char* tl = static_cast<const char*>(tlas);
   uint32_t* slots = static_cast<uint32_t*>(slot_area);
-  uint8_t* nhits = reinterpret_cast<uint8_t*>(static_cast<char*>(slot_area) +
-                                              align_up(static_cast<size_t>(n) * kSlots * 4, 256));
-  const int blocks = static_cast<int>(std::max<int64_t>(1, ceil_div(n, 256)));
-  const size_t sh1 = sizeof(uint32_t) * n_buckets, sh2 = 2 * sh1;
+  uint8_t* nhits = slot_counts(slot_area, n);
+  const int blocks = static_cast<int>(std::max<int64_t>(1, ceil_div(n, kFrontThreads)));
   if (n > 0) {
     if (tlas)
-      k_front_count_first<true><<<blocks, 256, sh1, st>>>(p, tl, rays, n, n_buckets, bits, cnt, slots, nhits, first_k);
+      k_front_count_first<true><<<blocks, kFrontThreads, 0, st>>>(p, tl, rays, n, bits, cnt, slots, nhits, first_k);
     else
-      k_front_count_first<false><<<blocks, 256, sh1, st>>>(p, tl, rays, n, n_buckets, bits, cnt, slots, nhits, first_k);
+      k_front_count_first<false><<<blocks, kFrontThreads, 0, st>>>(p, tl, rays, n, bits, cnt, slots, nhits, first_k);
     NIF_LAUNCH_CHECK();
   }
-  k_front_scan<<<1, 1024, 0, st>>>(cnt, n_buckets, per_group, n_groups, max_q, cur, goff, count, err);
+  k_front_scan<<<1, 1024, 0, st>>>(cnt, f.n_buckets, f.per_group, f.n_groups, max_q, cur, goff, count, err);
   NIF_LAUNCH_CHECK();
   if (n > 0) {
     if (tlas)
-      k_front_scatter_first<true><<<blocks, 256, sh2, st>>>(p, tl, rays, n, n_buckets, cur, max_q, slots,
-                                                             nhits, first_k, out_ray, out_qobj, err);
+      k_front_scatter_first<true><<<blocks, kFrontThreads, 0, st>>>(p, tl, rays, n, cur, max_q, slots, nhits,
+                                                                    first_k, out_ray, out_qobj, err);
     else
-      k_front_scatter_first<false><<<blocks, 256, sh2, st>>>(p, tl, rays, n, n_buckets, cur, max_q, slots,
-                                                              nhits, first_k, out_ray, out_qobj, err);
+      k_front_scatter_first<false><<<blocks, kFrontThreads, 0, st>>>(p, tl, rays, n, cur, max_q, slots, nhits,
+                                                                     first_k, out_ray, out_qobj, err);
     NIF_LAUNCH_CHECK();
   }
   return NIF_OK;
@@ -845,37 +768,33 @@ nif_status launch_frontend_rest(const NifParams& p, const void* tlas, const nif_
                                 int64_t max_q, const int64_t* count_first, int64_t* goff,
                                 int64_t* count, void* ws, uint32_t* cnt2, const void* slot_area,
                                 const uint8_t* first_k, cudaStream_t st) {
-  const int n_groups = p.net_mode == NIF_NETS_OBJECT ? p.n_obj : (p.net_mode == NIF_NETS_CLASS ? 2 : 1);
-  const int n_buckets = (p.net_mode == NIF_NETS_CLASS ? 2 : 1) * p.n_obj;
-  const int per_group = p.net_mode == NIF_NETS_OBJECT ? 1 : p.n_obj;
+  const FrontShape f = front_shape(p);
   DevError* err = static_cast<DevError*>(ws);
-  uint32_t* cur2 = cnt2 + align_up(n_buckets, 64);
-  NIF_CUDA_TRY(cudaMemsetAsync(cnt2, 0, sizeof(uint32_t) * n_buckets, st));
+  uint32_t* cur2 = cnt2 + align_up(f.n_buckets, 64);
+  NIF_CUDA_TRY(cudaMemsetAsync(cnt2, 0, sizeof(uint32_t) * f.n_buckets, st));
   const char* tl = static_cast<const char*>(tlas);
   const uint32_t* slots = static_cast<const uint32_t*>(slot_area);
-  const uint8_t* nhits = reinterpret_cast<const uint8_t*>(static_cast<const char*>(slot_area) +
-                                                          align_up(static_cast<size_t>(n) * kSlots * 4, 256));
-  const int blocks = static_cast<int>(std::max<int64_t>(1, ceil_div(n, 256)));
-  const size_t sh2 = 2 * sizeof(uint32_t) * n_buckets;
+  const uint8_t* nhits = slot_counts(const_cast<void*>(slot_area), n);
+  const int blocks = static_cast<int>(std::max<int64_t>(1, ceil_div(n, kFrontThreads)));
   if (n > 0) {
     if (tlas)
-      k_front_rest<true, false><<<blocks, 256, sh2, st>>>(p, tl, rays, n, n_buckets, bits, cnt2, max_q, slots,
-                                                          nhits, first_k, nullptr, nullptr, err);
+      k_front_rest<true, false><<<blocks, kFrontThreads, 0, st>>>(p, tl, rays, n, bits, cnt2, max_q, slots, nhits,
+                                                                  first_k, nullptr, nullptr, err);
     else
-      k_front_rest<false, false><<<blocks, 256, sh2, st>>>(p, tl, rays, n, n_buckets, bits, cnt2, max_q, slots,
-                                                           nhits, first_k, nullptr, nullptr, err);
+      k_front_rest<false, false><<<blocks, kFrontThreads, 0, st>>>(p, tl, rays, n, bits, cnt2, max_q, slots, nhits,
+                                                                   first_k, nullptr, nullptr, err);
     NIF_LAUNCH_CHECK();
   }
-  k_front_scan<<<1, 1024, 0, st>>>(cnt2, n_buckets, per_group, n_groups, max_q, cur2, goff, count, err,
+  k_front_scan<<<1, 1024, 0, st>>>(cnt2, f.n_buckets, f.per_group, f.n_groups, max_q, cur2, goff, count, err,
                                    count_first);
   NIF_LAUNCH_CHECK();
   if (n > 0) {
     if (tlas)
-      k_front_rest<true, true><<<blocks, 256, sh2, st>>>(p, tl, rays, n, n_buckets, bits, cur2, max_q, slots,
-                                                         nhits, first_k, out_ray, out_qobj, err);
+      k_front_rest<true, true><<<blocks, kFrontThreads, 0, st>>>(p, tl, rays, n, bits, cur2, max_q, slots, nhits,
+                                                                 first_k, out_ray, out_qobj, err);
     else
-      k_front_rest<false, true><<<blocks, 256, sh2, st>>>(p, tl, rays, n, n_buckets, bits, cur2, max_q, slots,
-                                                          nhits, first_k, out_ray, out_qobj, err);
+      k_front_rest<false, true><<<blocks, kFrontThreads, 0, st>>>(p, tl, rays, n, bits, cur2, max_q, slots, nhits,
+                                                                  first_k, out_ray, out_qobj, err);
     NIF_LAUNCH_CHECK();
   }
   return NIF_OK;

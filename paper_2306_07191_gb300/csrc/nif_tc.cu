@@ -466,16 +466,15 @@ __global__ void __launch_bounds__(kThreads, kOcc)
               cell_entries(li, c0, idx[j]);
             }
             Raw v[3][8];
+            float wt[3][8];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) v[0][c] = __ldg(tp + idx[0][c]);
-#pragma unroll
-            for (int c = 0; c < 8; ++c) v[1][c] = __ldg(tp + idx[1][c]);
-#pragma unroll
-            for (int c = 0; c < 8; ++c) v[2][c] = __ldg(td + idx[2][c]);
+            for (int j = 0; j < 3; ++j) cell_weights(fr[j], wt[j]);
+            load_corners(tp, idx[0], wt[0], v[0]);
+            load_corners(tp, idx[1], wt[1], v[1]);
+            load_corners(td, idx[2], wt[2], v[2]);
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
-              float w[8];
-              cell_weights(fr[j], w);
+              const float* w = wt[j];
               float a0 = 0.f, a1 = 0.f;
 #pragma unroll
               for (int c = 0; c < 8; ++c) {
@@ -782,16 +781,15 @@ __global__ void __launch_bounds__(kThreads, kOcc)
                 cell_entries(li, c0, idx[u]);
               }
               Raw v[kJB][8];
+              float wt[kJB][8];
 #pragma unroll
               for (int u = 0; u < kJB; ++u) {
-                const Raw* tab = (jb + u) < 2 ? tp : td;
-#pragma unroll
-                for (int c = 0; c < 8; ++c) v[u][c] = __ldg(tab + idx[u][c]);
+                cell_weights(fr[u], wt[u]);
+                load_corners((jb + u) < 2 ? tp : td, idx[u], wt[u], v[u]);
               }
 #pragma unroll
               for (int u = 0; u < kJB; ++u) {
-                float w[8];
-                cell_weights(fr[u], w);
+                const float* w = wt[u];
                 float a0 = 0.f, a1 = 0.f;
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
@@ -1051,11 +1049,10 @@ __global__ void __launch_bounds__(32 * (kEW + 4), kOcc)
             cell_of(li, pts.u[j][0], pts.u[j][1], pts.u[j][2], c0, fr);
             cell_entries(li, c0, idx);
             const Raw* tab = reinterpret_cast<const Raw*>(j < 2 ? tp : td);
-            Raw v[8];
-#pragma unroll
-            for (int c = 0; c < 8; ++c) v[c] = __ldg(tab + idx[c]);
             float w[8];
             cell_weights(fr, w);
+            Raw v[8];
+            load_corners(tab, idx, w, v);
             float a0 = 0.f, a1 = 0.f;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
