@@ -317,6 +317,16 @@ def run_ours(args):
         cfg.schedule = {"serial": L.NIF_SCHED_SERIAL, "pipelined": L.NIF_SCHED_PIPELINED}[args.schedule]
     pipe = RoomPipeline(cfg, log=log)
     train_s = pipe.train()
+    n_par = int(pipe.g_master.numel() + pipe.w_master.numel())
+    tms = sorted(pipe.train_step_ms[1:]) or pipe.train_step_ms
+    train_stats = {
+        "steps": len(pipe.train_step_ms), "batch_pairs": min(cfg.batch, int(pipe.pairs[1].shape[0])),
+        "gpu_ms_per_step_median": tms[len(tms) // 2], "params": n_par,
+        # dense Adam reads master, grad, m, v and writes master, m, v, the
+        # 16-bit copy and the zeroed grad: 34 B per parameter per step
+        "adam_bytes_per_step": 34 * n_par,
+        "adam_floor_ms": 34 * n_par / (_peaks()[0] * 1e9) * 1e3,
+        "wall_includes": "host-side batch draw (numpy) and copies"}
     dis = pipe.disagreement()
     abl = pipe.ablations()
     log(f"disagreement {dis}  ablations {abl}")
@@ -463,6 +473,7 @@ def run_ours(args):
         "bvh_rays_per_s": world * n / (bms * 1e-3), "bvh_ms_per_step": bms,
         "speedup_vs_bvh": bms / ms,
         "visibility_disagreement": dis, "ablations": abl, "train_s": train_s,
+        "train": train_stats,
         "stages_ms": subs,
         "roofline": {"kernel": "nif fused encode+MLP (tcgen05), both rounds", "bound": "hbm",
                      "achieved": ach_gbs, "peak": hbm, "unit": "GB/s", "frac": ach_gbs / hbm,

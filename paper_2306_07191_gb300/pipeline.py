@@ -212,6 +212,7 @@ class RoomPipeline:
         self.trainer = nif.Trainer(self.model, lr=c.lr, w_master=self.w_master, g_master=self.g_master)
         rng = np.random.default_rng(seed)
         losses = []
+        step_ev = []
         t0 = time.time()
         B = min(c.batch, npool)
         for s in range(steps):
@@ -219,11 +220,18 @@ class RoomPipeline:
             k = int(np.searchsorted(idx, n_outer))
             goff = torch.tensor([0, k, B], dtype=torch.int64, device=self.dev)
             it = torch.from_numpy(idx).to(self.dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
             loss = self.trainer.step(rays, rid[it].contiguous(), qo[it].contiguous(), goff,
                                      lab[it].contiguous(), B)
+            e1.record()
+            step_ev.append((e0, e1))
             losses.append(loss.clone())
         torch.cuda.synchronize()
         dt = time.time() - t0
+        # device time of nif_train_step alone (forward, loss, backward, grid
+        # scatter, Adam), without the host-side batch draw
+        self.train_step_ms = [a.elapsed_time(b) for a, b in step_ev]
         self.model.check(self.trainer._ws)
         self.losses = [float(x.item()) for x in losses]
         self.log(f"trained {steps} steps of {B} pairs from a pool of {npool} in {dt:.2f}s; "
