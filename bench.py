@@ -53,7 +53,12 @@ WORKLOADS = {
 # DRAM bytes (read + write) of one fused-kernel launch, from the ncu captures
 # summarised under profiles/, keyed by (workload, schedule, CTAs per SM) of the
 # kernel as it stands; a configuration without an entry reports null.
-FUSED_TRAFFIC_BYTES = {}
+FUSED_TRAFFIC_BYTES = {
+    # profiles/fused_tm_room.md: rounds 1 + 2 of one step
+    ("room", "serial", 4): 1.260896e9 + 4.304384e6 + 0.425591e9 + 3.661056e6,
+    # profiles/fused_ws_full.md: rounds 1 + 2 of one step
+    ("full", "pipelined", 0): 492070912 + 6069760 + 259748608 + 2402048,
+}
 
 
 def per_query_cost(cfg):
@@ -165,17 +170,20 @@ def oracle_rays_per_s(n_rays: int, seed: int = 5):
     ob = oracle.OracleBVH(sc.verts, sc.tris)
     _, t, _ = ob.cast(ws.camera[pick], closest=True)
     cam = ws.camera[pick]
-    p = np.stack([cam[:, k] + t * cam[:, 4 + k] for k in range(3)], 1).astype(np.float32)
+    # primary misses become empty segments (tmin = tmax = 0), as on the GPU
+    hit = np.isfinite(t)
+    th = np.where(hit, t, 0.0).astype(np.float32)
+    p = np.stack([cam[:, k] + th * cam[:, 4 + k] for k in range(3)], 1).astype(np.float32)
     v = (ws.light[None, :].astype(np.float32) - p).astype(np.float32)
     ss = v[:, 0] * v[:, 0]
     ss = ss + v[:, 1] * v[:, 1]
     ss = ss + v[:, 2] * v[:, 2]
     ln = np.sqrt(ss).astype(np.float32)
     rays = np.zeros((n_rays, 8), np.float32)
-    rays[:, 0:3] = p
-    rays[:, 3] = np.float32(c.tmin)
-    rays[:, 4:7] = v / ln[:, None]
-    rays[:, 7] = ln
+    rays[:, 0:3] = np.where(hit[:, None], p, cam[:, 0:3])
+    rays[:, 3] = np.where(hit, np.float32(c.tmin), np.float32(0.0))
+    rays[:, 4:7] = np.where(hit[:, None], v / np.where(hit, ln, 1.0)[:, None], cam[:, 4:7])
+    rays[:, 7] = np.where(hit, ln, np.float32(0.0))
     sizes, _, off = onif.level_layout(list(c.res), c.log2_table)
     V = int(off[-1])
     rng = np.random.default_rng(c.seed + 101)

@@ -389,10 +389,13 @@ def quantize_e4m3(weights_f32: torch.Tensor, cfg: NifConfig, n_nets: int, act_am
 
 
 # (schedule, CTAs per SM) pairs the autotuner times: the serial schedule at
-# 2, 3 or 4 CTAs per SM (more CTAs trade gathers in flight per thread for more
-# warps) and the pipelined schedule (its own occupancy).
-SCHEDULE_CANDIDATES = ((L.NIF_SCHED_SERIAL, 2), (L.NIF_SCHED_SERIAL, 3), (L.NIF_SCHED_SERIAL, 4),
-                       (L.NIF_SCHED_PIPELINED, 0))
+# 4, 3 or 2 CTAs per SM (more CTAs trade gathers in flight per thread for more
+# warps) and the pipelined schedule (its own occupancy).  A later candidate
+# replaces the choice only when it is faster by more than TUNE_MARGIN, so that
+# timing noise between near-equal candidates does not flip the choice.
+SCHEDULE_CANDIDATES = ((L.NIF_SCHED_SERIAL, 4), (L.NIF_SCHED_PIPELINED, 0), (L.NIF_SCHED_SERIAL, 3),
+                       (L.NIF_SCHED_SERIAL, 2))
+TUNE_MARGIN = 0.02
 
 
 def autotune(model: NifModel, run, key_extra=(), candidates=SCHEDULE_CANDIDATES, reps: int = 3,
@@ -435,7 +438,10 @@ def autotune(model: NifModel, run, key_extra=(), candidates=SCHEDULE_CANDIDATES,
             ms = e0.elapsed_time(e1)
             best = ms if best is None else min(best, ms)
         timings[(sched, ctas)] = best
-    choice = min(timings, key=timings.get)
+    choice = cands[0]
+    for k in cands[1:]:
+        if timings[k] < timings[choice] * (1.0 - TUNE_MARGIN):
+            choice = k
     c.schedule, c.ctas_per_sm = choice
     ms = {f"{label[k[0]]}/{k[1]}": v for k, v in timings.items()}
     cache[key] = {"choice": list(choice), "ms": ms}
