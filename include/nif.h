@@ -121,7 +121,33 @@ typedef struct nif_model_desc {
   int32_t tile_m;        /* tensor-core rows per tile: 0 (=128), 128 or 256 */
   int32_t ctas_per_sm;   /* 0 = library default */
   int32_t schedule;      /* tensor-core forward schedule (NIF_SCHED_*) */
+  int32_t encoding;      /* NIF_ENC_* (below) */
+  int32_t res_1d;        /* NIF_ENC_SPHERICAL_INNER: cells of the distance grid */
+  int32_t n_features_1d; /* NIF_ENC_SPHERICAL_INNER: latents per distance cell */
 } nif_model_desc;
+
+/* Encodings of a query (the network input x):
+ *   NIF_ENC_MULTIRES - the multi-resolution 3D grids described above.
+ *   NIF_ENC_SPHERICAL_OUTER, NIF_ENC_SPHERICAL_INNER - the paper's own form
+ *     (Sec. 3.1, Sec. 3.2, Table 1).  The AABB entry point p (outer; for
+ *     inner pairs the segment start o + tmin d) and the direction d are mapped
+ *     to spherical coordinates, p from p - c (c the box centre):
+ *     (u, v) = (atan2(sqrt(x^2+y^2), z) / pi, (atan2(y, x) + pi) / (2 pi)).
+ *     Each indexes a 2D grid of res[0] x res[0] cells of n_features latents,
+ *     bilinearly interpolated between cell centres (s = u R - 1/2, clamped
+ *     along u, wrapping around along v).  Inner pairs add the distance
+ *     r = |p - c| / half diagonal (clamped to [0, 1]) into a 1D grid of
+ *     res_1d cells of n_features_1d latents, linearly interpolated.
+ *     x = [v_p | v_d] (K = 2 n_features) or [v_p | v_d | v_r]
+ *     (K = 2 n_features + n_features_1d).  n_levels must be 1 and log2_table
+ *     is ignored; grids are d_grids = [n_objects][G] with per object
+ *     [position R*R*F | direction R*R*F | distance res_1d*F1 (inner)], cell
+ *     (i, j) at (i R + j) F; nif_grid_vertices returns G.  One encoding is
+ *     one network class, so net_mode NIF_NETS_CLASS is accepted only by the
+ *     front-end calls (to bin pairs into outer and inner); the forward calls
+ *     take NIF_NETS_SINGLE or NIF_NETS_OBJECT.  R >= 2, res_1d >= 2,
+ *     1 <= n_features, n_features_1d <= 16. */
+enum { NIF_ENC_MULTIRES = 0, NIF_ENC_SPHERICAL_OUTER = 1, NIF_ENC_SPHERICAL_INNER = 2 };
 
 /* Schedules of the 16-bit tensor-core forward (ignored elsewhere):
  *   NIF_SCHED_AUTO    - the library's choice (NIF_SCHED_PIPELINED when its

@@ -69,9 +69,33 @@ static bool level_layout(const nif_model_desc* m, uint32_t* off, uint32_t* hashe
   return true;
 }
 
+static bool spherical(const nif_model_desc* m) {
+  return m->encoding == NIF_ENC_SPHERICAL_OUTER || m->encoding == NIF_ENC_SPHERICAL_INNER;
+}
+
+// Spherical encodings: elements of one object's grid block, or -1.
+static int64_t spherical_elems(const nif_model_desc* m) {
+  const int R = m->res[0], F = m->n_features;
+  if (m->n_levels != 1 || R < 2 || R > 4096 || F < 1 || F > 16) return -1;
+  int64_t g = 2LL * R * R * F;
+  if (m->encoding == NIF_ENC_SPHERICAL_INNER) {
+    if (m->res_1d < 2 || m->res_1d > (1 << 20) || m->n_features_1d < 1 || m->n_features_1d > 16) return -1;
+    g += static_cast<int64_t>(m->res_1d) * m->n_features_1d;
+  }
+  return g;
+}
+
+static int64_t input_width(const nif_model_desc* m) {
+  if (m->encoding == NIF_ENC_SPHERICAL_OUTER) return 2LL * m->n_features;
+  if (m->encoding == NIF_ENC_SPHERICAL_INNER) return 2LL * m->n_features + m->n_features_1d;
+  return 3LL * m->n_levels * m->n_features;
+}
+
 int64_t grid_vertices(const nif_model_desc* m) {
+  if (!m) return -1;
+  if (spherical(m)) return spherical_elems(m);
   uint32_t off[NIF_MAX_LEVELS + 1];
-  if (!m || !level_layout(m, off, nullptr)) return -1;
+  if (!level_layout(m, off, nullptr)) return -1;
   return off[m->n_levels];
 }
 
@@ -79,19 +103,29 @@ int64_t weight_count(const nif_model_desc* m) {
   if (!m || m->n_hidden < 0 || m->n_hidden > 8 || m->width < 1 || m->n_levels < 1 ||
       m->n_features < 1)
     return -1;
-  int64_t K = 3LL * m->n_levels * m->n_features;
+  if (spherical(m) && spherical_elems(m) < 0) return -1;
+  int64_t K = input_width(m);
   if (m->n_hidden == 0) return K;
   return K * m->width + (int64_t)(m->n_hidden - 1) * m->width * m->width + m->width;
 }
 
 nif_status make_params(const nif_model_desc* m, NifParams* p) {
   NIF_CHECK_ARG(m != nullptr, "null model descriptor");
-  NIF_CHECK_ARG(m->n_features == 1 || m->n_features == 2 || m->n_features == 4 || m->n_features == 8,
-                "n_features must be 1, 2, 4 or 8 (got %d)", m->n_features);
+  NIF_CHECK_ARG(m->encoding >= NIF_ENC_MULTIRES && m->encoding <= NIF_ENC_SPHERICAL_INNER,
+                "bad encoding %d", m->encoding);
   std::memset(p, 0, sizeof(*p));
-  NIF_CHECK_ARG(level_layout(m, p->off, &p->hashed),
-                "bad grid levels (n_levels 1..%d, log2_table 1..30, res >= 1, < 2^32 vertices)",
-                NIF_MAX_LEVELS);
+  if (spherical(m)) {
+    NIF_CHECK_ARG(spherical_elems(m) > 0,
+                  "spherical encoding: n_levels 1, res[0] 2..4096, n_features 1..16 (inner: "
+                  "res_1d >= 2, n_features_1d 1..16)");
+    p->obj_elems = spherical_elems(m);
+  } else {
+    NIF_CHECK_ARG(m->n_features == 1 || m->n_features == 2 || m->n_features == 4 || m->n_features == 8,
+                  "n_features must be 1, 2, 4 or 8 (got %d)", m->n_features);
+    NIF_CHECK_ARG(level_layout(m, p->off, &p->hashed),
+                  "bad grid levels (n_levels 1..%d, log2_table 1..30, res >= 1, < 2^32 vertices)",
+                  NIF_MAX_LEVELS);
+  }
   NIF_CHECK_ARG(m->grid_dtype == NIF_F32 || m->grid_dtype == NIF_F16, "grid_dtype must be F32 or F16");
   NIF_CHECK_ARG(m->n_objects >= 1, "n_objects must be >= 1");
   NIF_CHECK_ARG(m->d_obj_aabb && m->d_grids && m->d_weights, "null model pointer");
@@ -110,9 +144,15 @@ nif_status make_params(const nif_model_desc* m, NifParams* p) {
   p->L = m->n_levels;
   p->F = m->n_features;
   p->log2T = m->log2_table;
-  p->K = 3 * p->L * p->F;
+  p->K = static_cast<int>(input_width(m));
+  p->enc = m->encoding;
+  p->R1 = m->encoding == NIF_ENC_SPHERICAL_INNER ? m->res_1d : 0;
+  p->F1 = m->encoding == NIF_ENC_SPHERICAL_INNER ? m->n_features_1d : 0;
   for (int l = 0; l < p->L; ++l) p->res[l] = m->res[l];
-  p->grid_elems = (int64_t)p->off[p->L] * p->F;
+  if (!spherical(m)) {
+    p->grid_elems = (int64_t)p->off[p->L] * p->F;
+    p->obj_elems = 2 * p->grid_elems;
+  }
   p->grid_dtype = m->grid_dtype;
   p->n_obj = m->n_objects;
   p->aabb = m->d_obj_aabb;
@@ -502,7 +542,7 @@ nif_status nif_train_step(nif_model_desc* m, nif_optim_desc* o, const nif_ray* d
   if (s != NIF_OK) return s;
   const int step = o->step + 1;
   const int64_t nw = (int64_t)p.n_nets * p.P;
-  const int64_t ng = (int64_t)p.n_obj * 2 * p.grid_elems;
+  const int64_t ng = (int64_t)p.n_obj * p.obj_elems;
   void* wcopy = m->mlp_dtype == NIF_E4M3 ? nullptr : const_cast<void*>(m->d_weights);
   s = launch_adam(o->d_w_master, o->d_w_grad, o->d_w_m, o->d_w_v, nw, o->lr, o->beta1, o->beta2, o->eps,
                   o->loss_scale, step, wcopy == o->d_w_master ? nullptr : wcopy, m->mlp_dtype, st);

@@ -30,6 +30,9 @@ struct NifParams {
   int64_t P;  // weights per network
   const float* scales;
   int schedule;  // NIF_SCHED_* of the tensor-core forward
+  int enc;       // NIF_ENC_*
+  int R1, F1;    // spherical inner: distance grid cells and latents
+  int64_t obj_elems;  // spherical: elements of one object's grid block
 };
 
 // Host: validate a descriptor and derive the device view.
@@ -376,11 +379,139 @@ __device__ __forceinline__ void gather_level(const TG* table, const Taps& t, flo
   }
 }
 
+// ------------------------------------------- the paper's own encoding
+// (Sec. 3.1, Sec. 3.2, Table 1): spherical coordinates of the AABB entry
+// point (outer) or the segment start (inner) about the box centre and of the
+// direction, each into a 2D grid of R x R cells (bilinear between cell
+// centres, clamped along u, wrapping along v); inner pairs add the distance
+// to the centre over the half diagonal into a 1D grid.
+__device__ __forceinline__ void sph_uv(float x, float y, float z, float& u, float& v) {
+  constexpr float kPi = 3.14159265358979323846f;
+  u = atan2f(sqrtf(x * x + y * y), z) * (1.0f / kPi);
+  v = (atan2f(y, x) + kPi) * (0.5f / kPi);
+}
+
+struct SphTaps2 {
+  uint32_t idx[4];
+  float w[4];
+};
+
+__device__ __forceinline__ void sph_taps2(int R, float u, float v, SphTaps2& t) {
+  const float s = u * static_cast<float>(R) - 0.5f;
+  int i0 = static_cast<int>(floorf(s));
+  i0 = i0 < 0 ? 0 : (i0 > R - 2 ? R - 2 : i0);
+  const float f = fminf(fmaxf(s - static_cast<float>(i0), 0.f), 1.f);
+  const float tt = v * static_cast<float>(R) - 0.5f;
+  const float jf = floorf(tt);
+  const float g = tt - jf;
+  int j0 = static_cast<int>(jf) % R;
+  j0 = j0 < 0 ? j0 + R : j0;
+  const int j1 = j0 + 1 == R ? 0 : j0 + 1;
+  t.idx[0] = static_cast<uint32_t>(i0 * R + j0);
+  t.idx[1] = static_cast<uint32_t>((i0 + 1) * R + j0);
+  t.idx[2] = static_cast<uint32_t>(i0 * R + j1);
+  t.idx[3] = static_cast<uint32_t>((i0 + 1) * R + j1);
+  t.w[0] = (1.f - f) * (1.f - g);
+  t.w[1] = f * (1.f - g);
+  t.w[2] = (1.f - f) * g;
+  t.w[3] = f * g;
+}
+
+__device__ __forceinline__ void sph_taps1(int R1, float r, uint32_t idx[2], float w[2]) {
+  const float s = r * static_cast<float>(R1) - 0.5f;
+  int i0 = static_cast<int>(floorf(s));
+  i0 = i0 < 0 ? 0 : (i0 > R1 - 2 ? R1 - 2 : i0);
+  const float f = fminf(fmaxf(s - static_cast<float>(i0), 0.f), 1.f);
+  idx[0] = static_cast<uint32_t>(i0);
+  idx[1] = static_cast<uint32_t>(i0 + 1);
+  w[0] = 1.f - f;
+  w[1] = f;
+}
+
+struct SphPoints {
+  float pu, pv, du, dv, r;
+};
+
+__device__ __forceinline__ void sph_points(const NifParams& p, const nif_ray& r, const float* box,
+                                           SphPoints& s) {
+  const float ext[3] = {box[3] - box[0], box[4] - box[1], box[5] - box[2]};
+  float v[3];
+  s.r = 0.f;
+  if (p.enc == NIF_ENC_SPHERICAL_OUTER) {
+    QueryPoints q;
+    query_points(r, box, q);  // entry point on its face, normalised
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[k] = (q.u[0][k] - 0.5f) * ext[k];
+  } else {
+    const float o[3] = {r.ox, r.oy, r.oz}, d[3] = {r.dx, r.dy, r.dz};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) v[k] = (o[k] + r.tmin * d[k]) - 0.5f * (box[k] + box[3 + k]);
+    const float half_diag = 0.5f * sqrtf(ext[0] * ext[0] + ext[1] * ext[1] + ext[2] * ext[2]);
+    s.r = fminf(fmaxf(sqrtf(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]) / half_diag, 0.f), 1.f);
+  }
+  sph_uv(v[0], v[1], v[2], s.pu, s.pv);
+  sph_uv(r.dx, r.dy, r.dz, s.du, s.dv);
+}
+
+template <typename TG>
+__device__ __forceinline__ float grid_value(const TG* t, int64_t i) {
+  if constexpr (sizeof(TG) == 2) return __half2float(__ldg(reinterpret_cast<const __half*>(t) + i));
+  else return __ldg(reinterpret_cast<const float*>(t) + i);
+}
+
+// One object's grid block of a spherical encoding.
+__device__ __forceinline__ const void* sph_block(const NifParams& p, uint32_t obj) {
+  const size_t esz = p.grid_dtype == NIF_F16 ? 2 : 4;
+  return static_cast<const char*>(p.grids) + static_cast<int64_t>(obj) * p.obj_elems * static_cast<int64_t>(esz);
+}
+
+template <typename TG, typename Sink>
+__device__ __forceinline__ void encode_spherical(const NifParams& p, const nif_ray& r, uint32_t qobj,
+                                                 Sink&& sink) {
+  const uint32_t obj = qobj & 0x7fffffffu;
+  float bx[6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) bx[k] = __ldg(p.aabb + 6 * static_cast<size_t>(obj) + k);
+  SphPoints sp;
+  sph_points(p, r, bx, sp);
+  const int R = p.res[0], F = p.F;
+  const TG* blk = static_cast<const TG*>(sph_block(p, obj));
+  const int64_t t2 = static_cast<int64_t>(R) * R * F;
+  SphTaps2 tp, td;
+  sph_taps2(R, sp.pu, sp.pv, tp);
+  sph_taps2(R, sp.du, sp.dv, td);
+  for (int f = 0; f < F; ++f) {
+    float a = 0.f, b = 0.f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      a += tp.w[c] * grid_value(blk, static_cast<int64_t>(tp.idx[c]) * F + f);
+      b += td.w[c] * grid_value(blk + t2, static_cast<int64_t>(td.idx[c]) * F + f);
+    }
+    sink(f, a);
+    sink(F + f, b);
+  }
+  if (p.enc == NIF_ENC_SPHERICAL_INNER) {
+    uint32_t i1[2];
+    float w1[2];
+    sph_taps1(p.R1, sp.r, i1, w1);
+    for (int f = 0; f < p.F1; ++f) {
+      float a = 0.f;
+#pragma unroll
+      for (int c = 0; c < 2; ++c) a += w1[c] * grid_value(blk + 2 * t2, static_cast<int64_t>(i1[c]) * p.F1 + f);
+      sink(2 * F + f, a);
+    }
+  }
+}
+
 // Full network input of one query: calls sink(k, value) for k = 0..K-1 in
 // the order [entry levels | exit levels | direction levels].
 template <int F, typename TG, typename Sink>
 __device__ __forceinline__ void encode_query(const NifParams& p, const nif_ray& r, uint32_t qobj,
                                              Sink&& sink) {
+  if (p.enc != NIF_ENC_MULTIRES) {
+    encode_spherical<TG>(p, r, qobj, sink);
+    return;
+  }
   uint32_t obj = qobj & 0x7fffffffu;
   const float* box = p.aabb + 6 * static_cast<size_t>(obj);
   float bx[6];

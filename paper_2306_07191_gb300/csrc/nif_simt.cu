@@ -582,6 +582,36 @@ __global__ void __launch_bounds__(128) k_grid_bwd(NifParams p, const nif_ray* ra
   uint32_t obj = qobj[q] & 0x7fffffffu;
   float bx[6];
   for (int k = 0; k < 6; ++k) bx[k] = __ldg(p.aabb + 6 * (size_t)obj + k);
+  if (p.enc != NIF_ENC_MULTIRES) {
+    // the paper's encoding: 4 bilinear taps each of the position and
+    // direction cells, 2 linear taps of the distance cell (inner)
+    SphPoints sp;
+    sph_points(p, r, bx, sp);
+    float* g = ggrad + static_cast<int64_t>(obj) * p.obj_elems;
+    const int R = p.res[0], Fs = p.F;
+    const int64_t t2 = static_cast<int64_t>(R) * R * Fs;
+    SphTaps2 tp, td;
+    sph_taps2(R, sp.pu, sp.pv, tp);
+    sph_taps2(R, sp.du, sp.dv, td);
+    for (int f = 0; f < Fs; ++f) {
+      const float a = dx[static_cast<int64_t>(f) * ld + q], b = dx[static_cast<int64_t>(Fs + f) * ld + q];
+      for (int c = 0; c < 4; ++c) {
+        if (tp.w[c] != 0.f) atomicAdd(g + static_cast<int64_t>(tp.idx[c]) * Fs + f, tp.w[c] * a);
+        if (td.w[c] != 0.f) atomicAdd(g + t2 + static_cast<int64_t>(td.idx[c]) * Fs + f, td.w[c] * b);
+      }
+    }
+    if (p.enc == NIF_ENC_SPHERICAL_INNER) {
+      uint32_t i1[2];
+      float w1[2];
+      sph_taps1(p.R1, sp.r, i1, w1);
+      for (int f = 0; f < p.F1; ++f) {
+        const float a = dx[static_cast<int64_t>(2 * Fs + f) * ld + q];
+        for (int c = 0; c < 2; ++c)
+          if (w1[c] != 0.f) atomicAdd(g + 2 * t2 + static_cast<int64_t>(i1[c]) * p.F1 + f, w1[c] * a);
+      }
+    }
+    return;
+  }
   QueryPoints pts;
   query_points(r, bx, pts);
   for (int j = 0; j < 3; ++j) {
@@ -803,6 +833,8 @@ nif_status launch_frontend_rest(const NifParams& p, const void* tlas, const nif_
 nif_status launch_encode(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
                          const uint32_t* qobj, int64_t nq, void* out, int out_dtype,
                          cudaStream_t st) {
+  if (p.enc != NIF_ENC_MULTIRES && p.net_mode == NIF_NETS_CLASS)
+    return fail(NIF_ERR_ARG, "spherical encodings: one class per model (net_mode single or object)");
   if (nq == 0) return NIF_OK;
   int64_t blocks = ceil_div(nq, 128);
   NIF_DISPATCH_FG(p, {
@@ -824,6 +856,8 @@ nif_status launch_fwd_f32(const NifParams& p, const nif_ray* rays, const uint32_
                           const uint32_t* qobj, const int64_t* goff, int64_t nq_hint,
                           uint32_t* occ, float* logits, float* saved, int64_t ld_saved,
                           cudaStream_t st) {
+  if (p.enc != NIF_ENC_MULTIRES && p.net_mode == NIF_NETS_CLASS)
+    return fail(NIF_ERR_ARG, "spherical encodings: one class per model (net_mode single or object)");
   size_t sh = fwd_f32_smem(p);
   int blocks = sm_count() * 8;
   if (nq_hint >= 0) blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(blocks, ceil_div(nq_hint, kTile) + p.n_nets)));

@@ -448,7 +448,11 @@ __global__ void __launch_bounds__(kThreads, kOcc)
         query_points(r, bx, pts);
         const TG* tpos = static_cast<const TG*>(grid_ptr(p, obj, 0));
         const TG* tdir = static_cast<const TG*>(grid_ptr(p, obj, 1));
-        if constexpr (F == 2) {
+        if (p.enc != NIF_ENC_MULTIRES) {
+          // the paper's encoding: a handful of taps, one thread per query
+          if (half == 0)
+            encode_query<F, TG>(p, r, qo, [&](int k, float v) { store_elem<DT>(tileA, qi, k, Kp, v * s_in); });
+        } else if constexpr (F == 2) {
           // Thread `half` takes levels l = half, half+2, ...; per level the
           // entry, exit and direction lookups share the level constants and
           // all 24 gathers are issued before any is consumed.
@@ -1313,7 +1317,7 @@ static nif_status launch_tm(const NifParams& p, const nif_ray* rays, const uint3
 // Pipelined schedule: 8 encode warps and 4 CTAs per SM when both TMEM
 // buffers fit 128 columns, else 16 encode warps and 2 CTAs per SM.
 static bool ws_supported(const NifParams& p) {
-  return p.F == 2 && p.mlp_dtype != NIF_E4M3 && tc_activations_in_tmem();
+  return p.enc == NIF_ENC_MULTIRES && p.F == 2 && p.mlp_dtype != NIF_E4M3 && tc_activations_in_tmem();
 }
 
 template <int DT>
@@ -1356,7 +1360,7 @@ static nif_status launch_dt(const NifParams& p, const nif_ray* rays, const uint3
   const int esz = DT == NIF_E4M3 ? 1 : 2;
   const bool occ3 = per_sm >= 3;
   if constexpr (DT != NIF_E4M3) {
-    if (p.F % 2 == 0 && tc_activations_in_tmem())
+    if (p.enc == NIF_ENC_MULTIRES && p.F % 2 == 0 && tc_activations_in_tmem())
       return launch_tm<DT>(p, rays, ray_id, qobj, goff, blocks, per_sm, occ, logits, err, ctr, st);
   }
   const int Kp = (p.K + 32 / esz - 1) / (32 / esz) * (32 / esz);
@@ -1392,6 +1396,8 @@ nif_status launch_fwd_tc(const NifParams& p, const nif_ray* rays, const uint32_t
                          cudaStream_t st) {
   nif_status s = check_tc_shape(p);
   if (s != NIF_OK) return s;
+  if (p.enc != NIF_ENC_MULTIRES && p.net_mode == NIF_NETS_CLASS)
+    return fail(NIF_ERR_ARG, "spherical encodings: one class per model (net_mode single or object)");
   if (tile_m != 0 && tile_m != 128)
     return fail(NIF_ERR_UNSUPPORTED, "tensor-core path: tile_m %d (128 supported)", tile_m);
   uint32_t* ctr = tile_counter(err);
@@ -1407,7 +1413,7 @@ nif_status launch_fwd_tc(const NifParams& p, const nif_ray* rays, const uint32_t
     }
   }
   int per_sm = ctas_per_sm > 0 ? ctas_per_sm : 2;
-  if (p.mlp_dtype != NIF_E4M3 && p.F % 2 == 0 && tc_activations_in_tmem()) {
+  if (p.enc == NIF_ENC_MULTIRES && p.mlp_dtype != NIF_E4M3 && p.F % 2 == 0 && tc_activations_in_tmem()) {
     // each CTA holds tm_cols() of the SM's 512 TMEM columns
     const int Kp16 = (p.K + 15) / 16 * 16;
     const int cap = 512 / static_cast<int>(tc::tm_cols(Kp16, p.width));

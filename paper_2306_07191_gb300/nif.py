@@ -119,6 +119,11 @@ class NifConfig:
     tile_m: int = 0
     ctas_per_sm: int = 0
     schedule: int = L.NIF_SCHED_AUTO
+    # the paper's own encoding (NIF_ENC_SPHERICAL_OUTER / _INNER): res = [R]
+    # for the 2D grids, n_features = N; inner pairs add res_1d x n_features_1d
+    encoding: int = L.NIF_ENC_MULTIRES
+    res_1d: int = 0
+    n_features_1d: int = 0
 
     @property
     def n_levels(self):
@@ -126,7 +131,25 @@ class NifConfig:
 
     @property
     def K(self):
+        if self.encoding == L.NIF_ENC_SPHERICAL_OUTER:
+            return 2 * self.n_features
+        if self.encoding == L.NIF_ENC_SPHERICAL_INNER:
+            return 2 * self.n_features + self.n_features_1d
         return 3 * len(self.res) * self.n_features
+
+    def fill(self, d: "L.ModelDesc") -> "L.ModelDesc":
+        """Write the shape fields of this configuration into a descriptor."""
+        d.n_levels = len(self.res)
+        d.n_features = self.n_features
+        d.log2_table = self.log2_table
+        for i, r in enumerate(self.res):
+            d.res[i] = int(r)
+        d.n_hidden = self.n_hidden
+        d.width = self.width
+        d.encoding = self.encoding
+        d.res_1d = self.res_1d
+        d.n_features_1d = self.n_features_1d
+        return d
 
 
 class NifModel:
@@ -150,18 +173,11 @@ class NifModel:
 
     def desc(self) -> L.ModelDesc:
         c = self.cfg
-        d = L.ModelDesc()
-        d.n_levels = len(c.res)
-        d.n_features = c.n_features
-        d.log2_table = c.log2_table
-        for i, r in enumerate(c.res):
-            d.res[i] = int(r)
+        d = c.fill(L.ModelDesc())
         d.grid_dtype = c.grid_dtype
         d.n_objects = self.n_obj
         d.d_obj_aabb = self.obj_aabb.data_ptr()
         d.d_grids = self.grids.data_ptr()
-        d.n_hidden = c.n_hidden
-        d.width = c.width
         d.act = c.act
         d.leaky_slope = c.leaky_slope
         d.mlp_dtype = c.mlp_dtype
@@ -176,25 +192,16 @@ class NifModel:
 
     @staticmethod
     def grid_vertices(cfg: NifConfig) -> int:
-        d = L.ModelDesc()
-        d.n_levels = len(cfg.res)
-        d.n_features = cfg.n_features
-        d.log2_table = cfg.log2_table
-        for i, r in enumerate(cfg.res):
-            d.res[i] = int(r)
-        v = L.lib.nif_grid_vertices(ctypes.byref(d))
+        """Vertices V of one grid (multi-resolution: grids are [obj][2][V][F]),
+        or the elements G of one object's block (spherical: [obj][G])."""
+        v = L.lib.nif_grid_vertices(ctypes.byref(cfg.fill(L.ModelDesc())))
         if v < 0:
             raise L.NifError(L.NIF_ERR_ARG, "bad grid configuration")
         return int(v)
 
     @staticmethod
     def weight_count(cfg: NifConfig) -> int:
-        d = L.ModelDesc()
-        d.n_levels = len(cfg.res)
-        d.n_features = cfg.n_features
-        d.n_hidden = cfg.n_hidden
-        d.width = cfg.width
-        return int(L.lib.nif_weight_count(ctypes.byref(d)))
+        return int(L.lib.nif_weight_count(ctypes.byref(cfg.fill(L.ModelDesc()))))
 
     def workspace(self, max_q: int, max_rays: int = 0) -> torch.Tensor:
         d = self.desc()
