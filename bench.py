@@ -33,6 +33,11 @@ SCHED_NAME = {0: "auto", 1: "serial", 2: "pipelined"}
 METRIC = "shadow rays/sec NIF vs own GPU BVH at <=1% visibility error; tensor-pipe util"
 UNIT = "shadow rays/s"
 WORKLOADS = {
+    "paper": ("paper's encoding on the room scene: 64 displaced icospheres (1,003,520 tris) + 12-tri "
+              "room, 1920x1080 primary hits, 1 point light -> 2,073,600 shadow rays; per object spherical "
+              "2D grids (outer R 256 N 3; inner R 128 N 5 + 1D R 128 N 3) FP16; outer 2x64 and inner "
+              "3x48 leaky-ReLU networks (inner padded to 64 for the tensor cores), trained 64 Adam "
+              "steps x 262,144 pairs"),
     "room": ("room: 64 displaced icospheres (1,003,520 tris) + 12-tri room, 1920x1080 primary hits, "
              "1 point light -> 2,073,600 shadow rays; hashed 16x2 FP16 grids (2^19/level) per object; "
              "shared outer/inner MLP 3x64 FP16 trained 64 Adam steps x 262,144 pairs"),
@@ -59,15 +64,6 @@ FUSED_TRAFFIC_BYTES = {
     # profiles/fused_ws_full.md: rounds 1 + 2 of one step
     ("full", "pipelined", 0): 492070912 + 6069760 + 259748608 + 2402048,
 }
-
-
-def per_query_cost(cfg):
-    """Algorithmic grid-tap bytes and MLP flops of one pair."""
-    esz = 2 if cfg.grid_dtype == 1 else 4
-    L_ = len(cfg.res)
-    K = 3 * L_ * cfg.n_features
-    W = cfg.width_mlp
-    return 3 * L_ * 8 * cfg.n_features * esz, 2 * (K * W + (cfg.n_hidden - 1) * W * W + W)
 
 
 def _peaks():
@@ -306,8 +302,13 @@ def run_ours(args):
     if world > 1:
         dist.init_process_group("nccl")
     log = (lambda *a: print(*a, file=sys.stderr, flush=True)) if rank == 0 else (lambda *a: None)
-    from paper_2306_07191_gb300.pipeline import full_scale_config, small_object_precision_config
-    if args.workload == "full":
+    from paper_2306_07191_gb300.pipeline import (PaperEncodingConfig, PaperEncodingPipeline,
+                                                 full_scale_config, small_object_precision_config)
+    pipe_cls = RoomPipeline
+    if args.workload == "paper":
+        cfg = PaperEncodingConfig()
+        pipe_cls = PaperEncodingPipeline
+    elif args.workload == "full":
         cfg = full_scale_config()
     elif args.workload == "precision":
         cfg = small_object_precision_config()
@@ -323,9 +324,9 @@ def run_ours(args):
         cfg.schedule = L.NIF_SCHED_SERIAL
     if args.schedule:
         cfg.schedule = {"serial": L.NIF_SCHED_SERIAL, "pipelined": L.NIF_SCHED_PIPELINED}[args.schedule]
-    pipe = RoomPipeline(cfg, log=log)
+    pipe = pipe_cls(cfg, log=log)
     train_s = pipe.train()
-    n_par = int(pipe.g_master.numel() + pipe.w_master.numel())
+    n_par = pipe.param_count()
     tms = sorted(pipe.train_step_ms[1:]) or pipe.train_step_ms
     train_stats = {
         "steps": len(pipe.train_step_ms), "batch_pairs": min(cfg.batch, int(pipe.pairs[1].shape[0])),
@@ -344,7 +345,8 @@ def run_ours(args):
     pipe.release_training_state()
     torch.cuda.empty_cache()
     tune_ms = None
-    if not (args.ctas_per_sm or args.schedule) and pipe.model.cfg.mlp_dtype != L.NIF_F32:
+    if not (args.ctas_per_sm or args.schedule) and pipe.model.cfg.mlp_dtype != L.NIF_F32 \
+            and args.workload != "paper":
         tbits = nif.empty_bits(pipe.n_rays)
         mq = cfg.max_pairs_per_ray * pipe.n_rays + 1024
         sched, occ, tune_ms = nif.autotune(
@@ -361,9 +363,8 @@ def run_ours(args):
     ws = model.workspace(max_q, n)
     ray_id = torch.empty(max_q, dtype=torch.int32, device=dev)
     qobj = torch.empty(max_q, dtype=torch.int32, device=dev)
-    goff1 = torch.empty(model.n_nets + 1, dtype=torch.int64, device=dev)
-    goff2 = torch.empty(model.n_nets + 1, dtype=torch.int64, device=dev)
     count = torch.empty(2, dtype=torch.int64, device=dev)
+    goff1 = torch.empty(model.n_nets + 1, dtype=torch.int64, device=dev)
     bits = nif.empty_bits(n, dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     sp = nif._stream()
@@ -372,27 +373,7 @@ def run_ours(args):
     def nif_step(ev=None):
         # the calls nif_infer makes, with events between them: nearest pair
         # per ray, its forward, the other pairs of still-unoccluded rays, theirs
-        pipe.room_bvh.cast_shadow(rays, out=bits)
-        d = model.desc()
-        common = (ctypes.byref(d), vp(pipe.tlas.buf.data_ptr()), vp(rays.data_ptr()), n,
-                  vp(bits.data_ptr()), vp(ray_id.data_ptr()), vp(qobj.data_ptr()), max_q)
-        fwd = (ctypes.byref(d), vp(rays.data_ptr()), n, vp(ray_id.data_ptr()), vp(qobj.data_ptr()))
-        if ev is not None:
-            ev[0].record(stream)
-        L.call("nif_frontend_nearest", *common, vp(goff1.data_ptr()), vp(count.data_ptr()),
-               vp(ws.data_ptr()), ws.numel(), sp)
-        if ev is not None:
-            ev[1].record(stream)
-        L.call("nif_infer_queries", *fwd, vp(goff1.data_ptr()), max_q, vp(bits.data_ptr()), None,
-               vp(ws.data_ptr()), ws.numel(), sp)
-        if ev is not None:
-            ev[2].record(stream)
-        L.call("nif_frontend_rest", *common, vp(count.data_ptr()), vp(goff2.data_ptr()),
-               vp(count.data_ptr() + 8), vp(ws.data_ptr()), ws.numel(), sp)
-        if ev is not None:
-            ev[3].record(stream)
-        L.call("nif_infer_queries", *fwd, vp(goff2.data_ptr()), max_q, vp(bits.data_ptr()), None,
-               vp(ws.data_ptr()), ws.numel(), sp)
+        pipe.query_step(bits, ev=ev)
 
     def timed(fn, K, W, sub=False):
         for _ in range(W):
@@ -435,8 +416,8 @@ def run_ours(args):
         bvh_ms, _ = timed(lambda: pipe.bvh.cast_shadow(rays, out=bits), args.steps, args.warmup)
         torch.cuda.profiler.stop()
     clocks = clk.summary()
-    nq1, nq = (int(x) for x in count.tolist())
-    model.check(ws)
+    nq1, nq = pipe.last_query_counts()
+    pipe.check()
     # pairs of the single-round query (every pair of every ray), for reference
     d = model.desc()
     L.call("nif_frontend", ctypes.byref(d), vp(pipe.tlas.buf.data_ptr()), vp(rays.data_ptr()), n,
@@ -452,8 +433,7 @@ def run_ours(args):
 
     def e2e_step():
         dev_rays.copy_(host_rays, non_blocking=True)
-        pipe.room_bvh.cast_shadow(dev_rays, out=bits)
-        model.infer(dev_rays, bits, tlas=pipe.tlas)
+        pipe.nif_query(bits, dev_rays)
         host_bits.copy_(bits, non_blocking=True)
 
     e2e_ms, _ = timed(e2e_step, args.steps, args.warmup)
@@ -464,7 +444,7 @@ def run_ours(args):
     value = world * n / (ms * 1e-3)
     hbm, tflops, src = _peaks()
     fused_s = subs["fused_ms"] * 1e-3
-    alg_bytes, flops_q = per_query_cost(cfg)
+    alg_bytes, flops_q = pipe.query_cost()
     ach_gbs = nq * alg_bytes / fused_s / 1e9
     tc_tflops = nq * flops_q / fused_s / 1e12
     line = {

@@ -93,8 +93,15 @@ class RoomPipeline:
         # evaluation frame: pixel-centre camera rays -> primary hits -> shadow rays
         self.rays = self._shadow_rays(torch.from_numpy(ws.camera).to(dev), light_seed=4321)
         self.n_rays = int(self.rays.shape[0])
-        # model
-        c = cfg
+        n_grid = self._build_model()
+        torch.cuda.synchronize()
+        self.log(f"room scene ready: {self.n_tris} triangles, {self.n_rays} shadow rays, "
+                 f"{n_grid / 1e9:.3f}G grid latents ({time.time() - t0:.1f}s)")
+
+    def _build_model(self) -> int:
+        """The multi-resolution model (shared outer/inner networks over
+        per-object grids); returns the number of grid latents."""
+        c, dev = self.cfg, self.dev
         ncfg = nif.NifConfig(res=list(c.res), n_features=c.n_features, log2_table=c.log2_table,
                              grid_dtype=c.grid_dtype, n_hidden=c.n_hidden, width=c.width_mlp,
                              mlp_dtype=c.mlp_dtype, net_mode=L.NIF_NETS_CLASS,
@@ -114,9 +121,7 @@ class RoomPipeline:
         self.model = nif.NifModel(ncfg, self.obj_aabb, self.g_master.to(gdt), self.w_master.to(mdt))
         self.init_weights = self.model.weights.clone()
         self.init_grids = self.model.grids.clone()
-        torch.cuda.synchronize()
-        self.log(f"room scene ready: {self.n_tris} triangles, {self.n_rays} shadow rays, "
-                 f"{n_grid / 1e9:.3f}G grid latents ({time.time() - t0:.1f}s)")
+        return n_grid
 
     # ------------------------------------------------------------ inputs
     def _shadow_rays(self, camera: torch.Tensor, light_seed: int) -> torch.Tensor:
@@ -249,6 +254,88 @@ class RoomPipeline:
         self.init_weights = None
 
     # ------------------------------------------------------------ queries
+    def front_model(self) -> nif.NifModel:
+        """The model whose descriptor drives the front end (class bucketing)."""
+        return self.model
+
+    def forward_models(self):
+        """(model, first group) pairs the forward runs on each round's pairs."""
+        return [(self.model, 0)]
+
+    def _query_buffers(self):
+        if getattr(self, "_qb", None) is None:
+            n = self.n_rays
+            mq = self.cfg.max_pairs_per_ray * n + 1024
+            fe = self.front_model()
+            self._qb = {
+                "max_q": mq,
+                "ray_id": torch.empty(mq, dtype=torch.int32, device=self.dev),
+                "qobj": torch.empty(mq, dtype=torch.int32, device=self.dev),
+                "goff1": torch.empty(fe.n_nets + 1, dtype=torch.int64, device=self.dev),
+                "goff2": torch.empty(fe.n_nets + 1, dtype=torch.int64, device=self.dev),
+                "count": torch.zeros(2, dtype=torch.int64, device=self.dev),
+                "ws": fe.workspace(mq, n),
+            }
+        return self._qb
+
+    def query_step(self, bits: torch.Tensor, rays: torch.Tensor | None = None, ev=None):
+        """The calls of one two-round visibility query, with optional CUDA
+        events ev[0..3] recorded between them: the non-NIF cast, then
+        nif_frontend_nearest, the forward of round 1, nif_frontend_rest and the
+        forward of round 2 (what nif_infer does for one model)."""
+        rays = self.rays if rays is None else rays
+        b = self._query_buffers()
+        vp, sp, n = ctypes.c_void_p, nif._stream(), int(rays.shape[0])
+        stream = torch.cuda.current_stream()
+        self.room_bvh.cast_shadow(rays, out=bits)
+        d = self.front_model().desc()
+        ws = b["ws"]
+        common = (ctypes.byref(d), vp(self.tlas.buf.data_ptr()), vp(rays.data_ptr()), n, vp(bits.data_ptr()),
+                  vp(b["ray_id"].data_ptr()), vp(b["qobj"].data_ptr()), b["max_q"])
+
+        def forward(goff):
+            for m, g0 in self.forward_models():
+                md = m.desc()
+                L.call("nif_infer_queries", ctypes.byref(md), vp(rays.data_ptr()), n, vp(b["ray_id"].data_ptr()),
+                       vp(b["qobj"].data_ptr()), vp(goff.data_ptr() + 8 * g0), b["max_q"], vp(bits.data_ptr()),
+                       None, vp(ws.data_ptr()), ws.numel(), sp)
+
+        if ev is not None:
+            ev[0].record(stream)
+        L.call("nif_frontend_nearest", *common, vp(b["goff1"].data_ptr()), vp(b["count"].data_ptr()),
+               vp(ws.data_ptr()), ws.numel(), sp)
+        if ev is not None:
+            ev[1].record(stream)
+        forward(b["goff1"])
+        if ev is not None:
+            ev[2].record(stream)
+        L.call("nif_frontend_rest", *common, vp(b["count"].data_ptr()), vp(b["goff2"].data_ptr()),
+               vp(b["count"].data_ptr() + 8), vp(ws.data_ptr()), ws.numel(), sp)
+        if ev is not None:
+            ev[3].record(stream)
+        forward(b["goff2"])
+        return bits
+
+    def query_cost(self):
+        """Algorithmic grid-tap bytes and MLP flops of one queried pair."""
+        c = self.cfg
+        esz = 2 if c.grid_dtype == L.NIF_F16 else 4
+        L_ = len(c.res)
+        K = 3 * L_ * c.n_features
+        W = c.width_mlp
+        return 3 * L_ * 8 * c.n_features * esz, 2 * (K * W + (c.n_hidden - 1) * W * W + W)
+
+    def param_count(self) -> int:
+        return int(self.g_master.numel() + self.w_master.numel())
+
+    def last_query_counts(self):
+        """Pairs the last query_step queried: (round 1, both rounds)."""
+        c = self._query_buffers()["count"].tolist()
+        return int(c[0]), int(c[1])
+
+    def check(self):
+        self.front_model().check(self._query_buffers()["ws"])
+
     def nif_query(self, bits: torch.Tensor, rays: torch.Tensor | None = None, stream=None):
         """NIF visibility: exact cast of the non-NIF geometry (the room), then
         the top-level front end and the fused networks OR-ed into the mask."""
@@ -308,3 +395,197 @@ class RoomPipeline:
         self.model.weights, self.model.grids = w, g
         return {"aabb_only": float((aabb_only != vb).float().mean().item()),
                 "untrained": float((untrained != vb).float().mean().item())}
+
+
+# --------------------------------------------------------------------------
+# The paper's own encoding on the same scene (Sec. 3.1, Sec. 3.2, Table 1,
+# Sec. 5 'Architecture'): an outer and an inner network with their own
+# spherical grids per object.
+
+@dataclass
+class PaperEncodingConfig(RoomConfig):
+    outer_res: int = 256        # Table 1: outer 2D grids R = 256, N = 3
+    outer_features: int = 3
+    outer_hidden: int = 2       # Sec. 5: outer 2 x 64, inner 3 x 48, leaky ReLU
+    outer_width: int = 64
+    inner_res: int = 128        # Table 1: inner 2D grids R = 128, N = 5; 1D R = 128, N = 3
+    inner_features: int = 5
+    inner_res_1d: int = 128
+    inner_features_1d: int = 3
+    inner_hidden: int = 3
+    inner_width: int = 48
+    lr: float = 5e-3            # Sec. 5 'Training'
+
+
+def _pad_width(flat: torch.Tensor, K: int, W: int, H: int, Wp: int) -> torch.Tensor:
+    """The same bias-free network with Wp >= W hidden units: the extra units
+    get zero weights in and out, so they stay at zero (ReLU and leaky ReLU map
+    0 to 0) and the output is unchanged."""
+    out, off, fan, fanp = [], 0, K, K
+    for _ in range(H):
+        m = flat[off:off + W * fan].view(W, fan)
+        mp = torch.zeros(Wp, fanp, dtype=flat.dtype, device=flat.device)
+        mp[:W, :fan] = m
+        out.append(mp.reshape(-1))
+        off += W * fan
+        fan, fanp = W, Wp
+    wo = torch.zeros(Wp, dtype=flat.dtype, device=flat.device)
+    wo[:W] = flat[off:off + W]
+    out.append(wo)
+    return torch.cat(out).contiguous()
+
+
+class PaperEncodingPipeline(RoomPipeline):
+    """The room workload with the paper's encoding and its two networks.
+    Outer pairs go to the outer model, inner pairs to the inner one; one
+    class-mode front end bins them.  The inner network (48 wide) is trained in
+    FP32 and queried on the tensor cores as the same network padded to 64."""
+
+    def _build_model(self) -> int:
+        c, dev = self.cfg, self.dev
+        total = 0
+        self.cls = {}
+        for k, (name, enc, R, N, R1, N1, H, W) in enumerate((
+                ("outer", L.NIF_ENC_SPHERICAL_OUTER, c.outer_res, c.outer_features, 0, 0, c.outer_hidden,
+                 c.outer_width),
+                ("inner", L.NIF_ENC_SPHERICAL_INNER, c.inner_res, c.inner_features, c.inner_res_1d,
+                 c.inner_features_1d, c.inner_hidden, c.inner_width))):
+            ncfg = nif.NifConfig(res=[R], n_features=N, grid_dtype=L.NIF_F16, n_hidden=H, width=W,
+                                 act=L.NIF_ACT_LEAKY, mlp_dtype=L.NIF_F16, net_mode=L.NIF_NETS_SINGLE,
+                                 encoding=enc, res_1d=R1, n_features_1d=N1)
+            n_grid = c.n_obj * nif.NifModel.grid_vertices(ncfg)
+            g = torch.empty(n_grid, dtype=torch.float32, device=dev)
+            L.call("nif_fill_uniform", ctypes.c_void_p(g.data_ptr()), n_grid, GRID_SEED + 17 * (k + 1),
+                   GRID_SCALE, nif._stream())
+            wr = np.random.default_rng(c.seed + 101 + k)
+            w = torch.from_numpy(synth.flatten_mlp(synth.mlp_init(wr, ncfg.K, W, H))).to(dev)
+            model = nif.NifModel(ncfg, self.obj_aabb, g.half(), w.half())
+            self.cls[name] = {"model": model, "g_master": g, "w_master": w,
+                              "init_grids": model.grids.clone(), "init_weights": model.weights.clone()}
+            total += n_grid
+        self._make_inference_models(init=True)
+        oc = self.cls["outer"]["model"]
+        fe_cfg = nif.NifConfig(**{**oc.cfg.__dict__, "net_mode": L.NIF_NETS_CLASS})
+        self.model = nif.NifModel(fe_cfg, self.obj_aabb, oc.grids, torch.cat([oc.weights, oc.weights]))
+        self.g_master = self.w_master = None
+        return total
+
+    def _make_inference_models(self, init: bool = False):
+        """Tensor-core copies: the outer model as is, the inner one padded to a
+        width the tensor cores take."""
+        inner = self.cls["inner"]["model"]
+        c = inner.cfg
+        Wp = 64 if c.width <= 64 else 128
+        src = self.cls["inner"]["init_weights"] if init else self.cls["inner"]["w_master"]
+        wp = _pad_width(src.float(), c.K, c.width, c.n_hidden, Wp).half()
+        icfg = nif.NifConfig(**{**c.__dict__, "width": Wp})
+        self.inner_inf = nif.NifModel(icfg, self.obj_aabb, inner.grids, wp)
+        if init:
+            self.inner_inf_init_weights = wp.clone()
+
+    def front_model(self) -> nif.NifModel:
+        return self.model
+
+    def forward_models(self):
+        return [(self.cls["outer"]["model"], 0), (self.inner_inf, 1)]
+
+    def param_count(self) -> int:
+        return int(sum(cl["model"].grids.numel() + cl["model"].weights.numel() for cl in self.cls.values()))
+
+    def query_cost(self):
+        """Per queried pair, averaged over the class mix of the last query:
+        grid-tap bytes (4 bilinear taps per 2D lookup, 2 linear taps of the
+        distance grid, FP16) and MLP flops of the unpadded networks."""
+        b = self._query_buffers()
+        n_cls = [0, 0]
+        for g in (b["goff1"].tolist(), b["goff2"].tolist()):
+            n_cls[0] += g[1] - g[0]
+            n_cls[1] += g[2] - g[1]
+        cost = []
+        for name in ("outer", "inner"):
+            c = self.cls[name]["model"].cfg
+            taps = 2 * 4 * c.n_features + 2 * c.n_features_1d
+            W, H, K = c.width, c.n_hidden, c.K
+            cost.append((taps * 2, 2 * (K * W + (H - 1) * W * W + W)))
+        tot = max(1, sum(n_cls))
+        return (sum(n * c[0] for n, c in zip(n_cls, cost)) / tot,
+                sum(n * c[1] for n, c in zip(n_cls, cost)) / tot)
+
+    def nif_query(self, bits: torch.Tensor, rays: torch.Tensor | None = None, stream=None):
+        return self.query_step(bits, rays)
+
+    def train(self, steps: int | None = None, seed: int = 99, pairs=None):
+        c = self.cfg
+        steps = steps if steps is not None else c.train_steps
+        rays, rid, qo, lab, n_outer = pairs if pairs is not None else self.training_pairs()
+        self.pairs = (rays, rid, qo, lab, n_outer)
+        npool = int(rid.shape[0])
+        parts = {"outer": (0, n_outer), "inner": (n_outer, npool)}
+        trainers = {}
+        for name in ("outer", "inner"):
+            cl = self.cls[name]
+            trainers[name] = nif.Trainer(cl["model"], lr=c.lr, w_master=cl["w_master"], g_master=cl["g_master"])
+        self.trainers = trainers
+        rng = np.random.default_rng(seed)
+        B = min(c.batch, npool)
+        losses, step_ev = [], []
+        t0 = time.time()
+        for s in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            step_loss = []
+            for name, (a, b) in parts.items():
+                nb = int(round(B * (b - a) / npool))
+                if nb == 0:
+                    continue
+                idx = np.sort(rng.choice(b - a, nb, replace=False)) + a
+                it = torch.from_numpy(idx).to(self.dev)
+                goff = torch.tensor([0, nb], dtype=torch.int64, device=self.dev)
+                loss = trainers[name].step(rays, rid[it].contiguous(), qo[it].contiguous(), goff,
+                                           lab[it].contiguous(), nb)
+                step_loss.append((loss.clone(), nb))
+            e1.record()
+            step_ev.append((e0, e1))
+            losses.append(step_loss)
+        torch.cuda.synchronize()
+        dt = time.time() - t0
+        self.train_step_ms = [a.elapsed_time(b) for a, b in step_ev]
+        for name in ("outer", "inner"):
+            self.cls[name]["model"].check(trainers[name]._ws)
+            self.cls[name]["w_master"] = trainers[name].w_master
+        self._make_inference_models()
+        tot = [sum(float(l.item()) * nb for l, nb in st) / max(1, sum(nb for _, nb in st)) for st in losses]
+        self.losses = tot
+        self.log(f"trained outer + inner networks for {steps} steps of {B} pairs from a pool of {npool} "
+                 f"({n_outer} outer) in {dt:.2f}s; loss {tot[0]:.4f} -> {tot[-1]:.4f}")
+        return dt
+
+    def ablations(self):
+        b = nif.empty_bits(self.n_rays)
+        self.bvh_query(b)
+        vb = nif.bits_to_bool(b, self.n_rays)
+        rid, qo, goff, count = self.model.frontend(self.rays, tlas=self.tlas,
+                                                   max_q=self.cfg.max_pairs_per_ray * self.n_rays + 1024)
+        torch.cuda.synchronize()
+        self.model.check()
+        nq = int(count.item())
+        aabb_only = torch.zeros(self.n_rays, dtype=torch.bool, device=self.dev)
+        aabb_only[rid[:nq].long()] = True
+        om, inf = self.cls["outer"]["model"], self.inner_inf
+        saved = (om.weights, om.grids, inf.weights, inf.grids)
+        om.weights, om.grids = self.cls["outer"]["init_weights"], self.cls["outer"]["init_grids"]
+        inf.weights, inf.grids = self.inner_inf_init_weights, self.cls["inner"]["init_grids"]
+        a = nif.empty_bits(self.n_rays)
+        self.nif_query(a)
+        untrained = nif.bits_to_bool(a, self.n_rays)
+        om.weights, om.grids, inf.weights, inf.grids = saved
+        return {"aabb_only": float((aabb_only != vb).float().mean().item()),
+                "untrained": float((untrained != vb).float().mean().item())}
+
+    def release_training_state(self):
+        self.trainers = None
+        self.pairs = None
+        for cl in self.cls.values():
+            cl["g_master"] = cl["w_master"] = None
+            cl["init_grids"] = cl["init_weights"] = None
+        self.inner_inf_init_weights = None
