@@ -345,13 +345,14 @@ def run_ours(args):
     pipe.release_training_state()
     torch.cuda.empty_cache()
     tune_ms = None
-    if not (args.ctas_per_sm or args.schedule) and pipe.model.cfg.mlp_dtype != L.NIF_F32 \
-            and args.workload != "paper":
+    if not (args.ctas_per_sm or args.schedule) and pipe.model.cfg.mlp_dtype != L.NIF_F32:
         tbits = nif.empty_bits(pipe.n_rays)
-        mq = cfg.max_pairs_per_ray * pipe.n_rays + 1024
-        sched, occ, tune_ms = nif.autotune(
-            pipe.model, lambda: pipe.model.infer(pipe.rays, tbits, tlas=pipe.tlas, max_q=mq),
-            key_extra=(pipe.n_rays, args.workload))
+        fwd = [m for m, _ in pipe.forward_models()]
+        # the spherical encodings run the serial schedule only
+        cands = nif.SCHEDULE_CANDIDATES if args.workload != "paper" else \
+            tuple(c for c in nif.SCHEDULE_CANDIDATES if c[0] == L.NIF_SCHED_SERIAL)
+        sched, occ, tune_ms = nif.autotune(fwd[0], lambda: pipe.query_step(tbits), also=fwd[1:],
+                                           candidates=cands, key_extra=(pipe.n_rays, args.workload))
         log(f"autotuned fused kernel: schedule {sched}, {occ} CTAs/SM ({tune_ms})")
     n = pipe.n_rays
     rays = pipe.rays
@@ -455,8 +456,8 @@ def run_ours(args):
         "config": {"workload": WORKLOADS[args.workload], "rays": n, "queries": nq,
                    "queries_round1": nq1, "queries_all_pairs": nq_all, "triangles": pipe.n_tris,
                    "objects": cfg.n_obj, "l2": "flushed (256 MB write) before every timed step",
-                   "fused_schedule": SCHED_NAME[model.cfg.schedule],
-                   "fused_ctas_per_sm": model.cfg.ctas_per_sm, "autotune_ms": tune_ms,
+                   "fused_schedule": SCHED_NAME[pipe.forward_models()[0][0].cfg.schedule],
+                   "fused_ctas_per_sm": pipe.forward_models()[0][0].cfg.ctas_per_sm, "autotune_ms": tune_ms,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "bvh_rays_per_s": world * n / (bms * 1e-3), "bvh_ms_per_step": bms,
         "speedup_vs_bvh": bms / ms,
@@ -466,7 +467,8 @@ def run_ours(args):
         "roofline": {"kernel": "nif fused encode+MLP (tcgen05), both rounds", "bound": "hbm",
                      "achieved": ach_gbs, "peak": hbm, "unit": "GB/s", "frac": ach_gbs / hbm,
                      "traffic": FUSED_TRAFFIC_BYTES.get(
-                         (args.workload, SCHED_NAME[model.cfg.schedule], model.cfg.ctas_per_sm)),
+                         (args.workload, SCHED_NAME[pipe.forward_models()[0][0].cfg.schedule],
+                          pipe.forward_models()[0][0].cfg.ctas_per_sm)),
                      "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum summed "
                                         "over the step's two fused launches"),
                      "peak_source": src,

@@ -40,6 +40,7 @@ namespace tc {
 
 constexpr int kM = 128;
 constexpr int kThreads = 256;
+constexpr int kSphMaxK = 32;  // widest spherical input the TMEM kernel builds per thread
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 // ------------------------------------------------------------ PTX wrappers
@@ -737,7 +738,28 @@ __global__ void __launch_bounds__(kThreads, kOcc)
     }
 
     // ---- step a1/a2: encode 128 queries straight into TMEM
-    {
+    if (p.enc != NIF_ENC_MULTIRES) {
+      // the paper's encoding: a few taps per query, so the first four warps
+      // (one per lane quarter) build whole rows and store them packed
+      if (half == 0) {
+        const int64_t q = q0 + qi;
+        float x[kSphMaxK];
+#pragma unroll
+        for (int k = 0; k < kSphMaxK; ++k) x[k] = 0.f;
+        if (q < qend) {
+          const nif_ray r = load_nif_ray(rays, ray_id[q]);
+          encode_query<F, TG>(p, r, qobj[q], [&](int k, float v) { x[k] = v; });
+        }
+#pragma unroll
+        for (int c = 0; c < kSphMaxK / 2; c += 8) {
+          if (c >= Kp / 2) break;
+          uint32_t pk[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) pk[i] = pack2(x[2 * (c + i)], x[2 * (c + i) + 1]);
+          tmem_st8(lane_base + act_col + static_cast<uint32_t>(c), pk);
+        }
+      }
+    } else {
       const int64_t q = q0 + qi;
       const bool live = q < qend;
       QueryPoints pts;
@@ -1296,22 +1318,31 @@ static nif_status launch_tm(const NifParams& p, const nif_ray* rays, const uint3
     return NIF_OK;
   };
   nif_status s;
+  // the spherical encodings do not use F at compile time: take the F = 2 forms
+  const int fsel = p.enc != NIF_ENC_MULTIRES ? 2 : p.F;
   if (p.grid_dtype == NIF_F16) {
-    if (p.F == 2)
+    if (fsel == 2)
       s = per_sm >= 4 ? go(tc::k_fused_tm<2, __half, DT, 4>)
           : per_sm == 3 ? go(tc::k_fused_tm<2, __half, DT, 3>) : go(tc::k_fused_tm<2, __half, DT, 2>);
-    else if (p.F == 4) s = go(tc::k_fused_tm<4, __half, DT, 2>);
+    else if (fsel == 4) s = go(tc::k_fused_tm<4, __half, DT, 2>);
     else s = go(tc::k_fused_tm<8, __half, DT, 2>);
   } else {
-    if (p.F == 2)
+    if (fsel == 2)
       s = per_sm >= 4 ? go(tc::k_fused_tm<2, float, DT, 4>)
           : per_sm == 3 ? go(tc::k_fused_tm<2, float, DT, 3>) : go(tc::k_fused_tm<2, float, DT, 2>);
-    else if (p.F == 4) s = go(tc::k_fused_tm<4, float, DT, 2>);
+    else if (fsel == 4) s = go(tc::k_fused_tm<4, float, DT, 2>);
     else s = go(tc::k_fused_tm<8, float, DT, 2>);
   }
   if (s != NIF_OK) return s;
   NIF_LAUNCH_CHECK();
   return NIF_OK;
+}
+
+// The TMEM-activation kernels take the multi-resolution encoding with an
+// even feature count, and the spherical ones up to kSphMaxK inputs.
+static bool tm_supported(const NifParams& p) {
+  if (!tc_activations_in_tmem()) return false;
+  return p.enc == NIF_ENC_MULTIRES ? p.F % 2 == 0 : p.K <= tc::kSphMaxK;
 }
 
 // Pipelined schedule: 8 encode warps and 4 CTAs per SM when both TMEM
@@ -1360,7 +1391,7 @@ static nif_status launch_dt(const NifParams& p, const nif_ray* rays, const uint3
   const int esz = DT == NIF_E4M3 ? 1 : 2;
   const bool occ3 = per_sm >= 3;
   if constexpr (DT != NIF_E4M3) {
-    if (p.enc == NIF_ENC_MULTIRES && p.F % 2 == 0 && tc_activations_in_tmem())
+    if (tm_supported(p))
       return launch_tm<DT>(p, rays, ray_id, qobj, goff, blocks, per_sm, occ, logits, err, ctr, st);
   }
   const int Kp = (p.K + 32 / esz - 1) / (32 / esz) * (32 / esz);
@@ -1413,7 +1444,7 @@ nif_status launch_fwd_tc(const NifParams& p, const nif_ray* rays, const uint32_t
     }
   }
   int per_sm = ctas_per_sm > 0 ? ctas_per_sm : 2;
-  if (p.enc == NIF_ENC_MULTIRES && p.mlp_dtype != NIF_E4M3 && p.F % 2 == 0 && tc_activations_in_tmem()) {
+  if (p.mlp_dtype != NIF_E4M3 && tm_supported(p)) {
     // each CTA holds tm_cols() of the SM's 512 TMEM columns
     const int Kp16 = (p.K + 15) / 16 * 16;
     const int cap = 512 / static_cast<int>(tc::tm_cols(Kp16, p.width));

@@ -405,21 +405,29 @@ SCHEDULE_CANDIDATES = ((L.NIF_SCHED_SERIAL, 4), (L.NIF_SCHED_PIPELINED, 0), (L.N
 TUNE_MARGIN = 0.02
 
 
-def autotune(model: NifModel, run, key_extra=(), candidates=SCHEDULE_CANDIDATES, reps: int = 3,
-             cache_path: str | None = None):
+def autotune(model: NifModel, run, key_extra=(), candidates=SCHEDULE_CANDIDATES, reps: int = 5,
+             cache_path: str | None = None, also=()):
     """Pick the tensor-core forward's (schedule, CTAs per SM) by timing
-    `run()` (the caller's own query, e.g. nif_infer on its rays) once per
-    candidate; the fastest is written into model.cfg and cached per (model
-    shape, key_extra, GPU) in a JSON file.  Returns (schedule, ctas_per_sm,
-    {candidate label: ms})."""
+    `run()` (the caller's own query, e.g. nif_infer on its rays): the median
+    of `reps` runs per candidate, each after an L2 flush.  The choice is
+    written into model.cfg (and the cfg of every model in `also`, other
+    networks the same run() queries) and cached per (model shape, key_extra,
+    GPU) in a JSON file.  Returns (schedule, ctas_per_sm, {candidate: ms})."""
     import hashlib
     import json
     import os
     c = model.cfg
+    cfgs = [c] + [m.cfg for m in also]
+
+    def apply(sched, ctas):
+        for cf in cfgs:
+            cf.schedule, cf.ctas_per_sm = int(sched), int(ctas)
+
     cands = [tuple(x) for x in candidates]
     key = hashlib.sha1(json.dumps([list(c.res), c.n_features, c.log2_table, c.grid_dtype, c.n_hidden,
-                                   c.width, c.mlp_dtype, c.net_mode, model.n_obj, list(key_extra),
-                                   cands, torch.cuda.get_device_name()]).encode()).hexdigest()[:16]
+                                   c.width, c.mlp_dtype, c.net_mode, c.encoding, model.n_obj,
+                                   list(key_extra), cands, torch.cuda.get_device_name()]).encode()
+                       ).hexdigest()[:16]
     cache_path = cache_path or os.path.join(os.path.dirname(os.path.abspath(__file__)), "_autotune.json")
     try:
         with open(cache_path) as f:
@@ -427,29 +435,31 @@ def autotune(model: NifModel, run, key_extra=(), candidates=SCHEDULE_CANDIDATES,
     except (OSError, ValueError):
         cache = {}
     if key in cache:
-        c.schedule, c.ctas_per_sm = (int(x) for x in cache[key]["choice"])
+        apply(*cache[key]["choice"])
         return c.schedule, c.ctas_per_sm, cache[key]["ms"]
     label = {L.NIF_SCHED_SERIAL: "serial", L.NIF_SCHED_PIPELINED: "pipelined", L.NIF_SCHED_AUTO: "auto"}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=model.obj_aabb.device)  # > L2
     timings = {}
     for sched, ctas in cands:
-        c.schedule, c.ctas_per_sm = sched, ctas
+        apply(sched, ctas)
         run()
         torch.cuda.synchronize()
-        best = None
+        got = []
         for _ in range(reps):
+            flush.zero_()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             run()
             e1.record()
             torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1)
-            best = ms if best is None else min(best, ms)
-        timings[(sched, ctas)] = best
+            got.append(e0.elapsed_time(e1))
+        timings[(sched, ctas)] = sorted(got)[len(got) // 2]
+    del flush
     choice = cands[0]
     for k in cands[1:]:
         if timings[k] < timings[choice] * (1.0 - TUNE_MARGIN):
             choice = k
-    c.schedule, c.ctas_per_sm = choice
+    apply(*choice)
     ms = {f"{label[k[0]]}/{k[1]}": v for k, v in timings.items()}
     cache[key] = {"choice": list(choice), "ms": ms}
     try:
