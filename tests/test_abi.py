@@ -117,3 +117,20 @@ def test_splitmix_generator_matches_hand_values():
     v = synth.splitmix_uniform(np.array([0]), 0, 1.0)[0]
     top = 0xE220A8397B1DCDAF >> 40
     assert v == np.float32(2.0 * top / 2 ** 24 - 1.0)
+
+
+def test_spherical_descriptor_sizes(L):
+    """nif_grid_vertices / nif_weight_count of the paper's encoding: per
+    object [position R*R*N | direction R*R*N | distance R1*N1], K = 2N or
+    2N + N1 (the weight counts of Sec. 5's 18 kB / 21 kB networks)."""
+    d = _room_desc(L)
+    d.n_levels, d.res[0], d.n_features = 1, 256, 3
+    d.encoding, d.n_hidden, d.width = L.NIF_ENC_SPHERICAL_OUTER, 2, 64
+    assert L.lib.nif_grid_vertices(ctypes.byref(d)) == 2 * 256 * 256 * 3
+    assert L.lib.nif_weight_count(ctypes.byref(d)) == 6 * 64 + 64 * 64 + 64
+    d.encoding, d.res[0], d.n_features, d.res_1d, d.n_features_1d = L.NIF_ENC_SPHERICAL_INNER, 128, 5, 128, 3
+    d.n_hidden, d.width = 3, 48
+    assert L.lib.nif_grid_vertices(ctypes.byref(d)) == 2 * 128 * 128 * 5 + 128 * 3
+    assert L.lib.nif_weight_count(ctypes.byref(d)) == 13 * 48 + 2 * 48 * 48 + 48
+    d.res_1d = 1  # a 1D grid needs two cells
+    assert L.lib.nif_grid_vertices(ctypes.byref(d)) == -1

@@ -172,3 +172,19 @@ def test_outer_encoding_of_aliased_rays_is_identical():
     s = rng.uniform(0.5, 2.0, size=40).astype(np.float32)
     moved[:, 0:3] = rays[:, 0:3] - s[:, None] * rays[:, 4:7]
     np.testing.assert_allclose(osph.encode(m, rays, rid, obj), osph.encode(m, moved, rid, obj), atol=1e-5)
+
+
+def test_network_sizes_match_the_papers_figures():
+    """Sec. 5 'Memory Footprint' gives 18 kB for the outer network and 21 kB
+    for the inner one.  With the inputs of this encoding (K = 2N outer,
+    2N + N1 inner; Table 1: N = 3, N = 5 and N1 = 3) and the architectures of
+    Sec. 5 (2 x 64, 3 x 48), the bias-free weight counts in 4-byte floats come
+    to 18.2 kB and 21.1 kB."""
+    def count(K, W, H):
+        return K * W + (H - 1) * W * W + W
+    outer = osph.SphericalModel(kind="outer", R=256, N=3, obj_aabb=BOX[None], grids=np.zeros((1, 1)), net=[])
+    inner = osph.SphericalModel(kind="inner", R=128, N=5, R1=128, N1=3, obj_aabb=BOX[None],
+                                grids=np.zeros((1, 1)), net=[])
+    assert outer.K == 6 and inner.K == 13
+    assert round(count(outer.K, 64, 2) * 4 / 1000, 1) == 18.2
+    assert round(count(inner.K, 48, 3) * 4 / 1000, 1) == 21.1
