@@ -1,0 +1,80 @@
+"""The two room pipelines end to end at a reduced size (640 x 360, 12
+objects): the explicit query step (the calls nif_infer makes) against
+nif_infer itself, the paper-encoding pipeline's two-round query against
+querying every pair of each class, and the inner network padded for the
+tensor cores against the unpadded one."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2306_07191_gb300 import _lib as L  # noqa: E402
+from paper_2306_07191_gb300 import nif, pipeline  # noqa: E402
+
+
+def _small(cfg):
+    cfg.width, cfg.height, cfg.n_obj = 640, 360, 12
+    cfg.train_steps, cfg.batch, cfg.train_spp = 8, 32768, 1
+    return cfg
+
+
+def test_room_query_step_equals_nif_infer():
+    p = pipeline.RoomPipeline(_small(pipeline.RoomConfig()), log=lambda *a: None)
+    p.train()
+    a = nif.empty_bits(p.n_rays)
+    b = nif.empty_bits(p.n_rays)
+    p.query_step(a)
+    p.nif_query(b)
+    p.check()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    n1, n = p.last_query_counts()
+    assert 0 < n1 <= n
+
+
+def test_paper_pipeline_two_rounds_equal_every_pair_per_class():
+    p = pipeline.PaperEncodingPipeline(_small(pipeline.PaperEncodingConfig()), log=lambda *a: None)
+    p.train()
+    two = nif.empty_bits(p.n_rays)
+    p.query_step(two)
+    p.check()
+    # every pair at once: the room cast, one front end, each class its own range
+    full = nif.empty_bits(p.n_rays)
+    p.room_bvh.cast_shadow(p.rays, out=full)
+    rid, qo, goff, count = p.model.frontend(p.rays, tlas=p.tlas)
+    torch.cuda.synchronize()
+    nq = int(count.item())
+    for m, g0 in p.forward_models():
+        m.infer_queries(p.rays, rid, qo, goff[g0:], nq, bits=full)
+        m.check()
+    torch.cuda.synchronize()
+    assert torch.equal(two, full)
+    n1, n = p.last_query_counts()
+    g = goff.tolist()
+    assert g[1] > 0 and g[2] > g[1] and n1 < n < nq
+
+
+def test_padded_inner_network_gives_the_same_logits():
+    p = pipeline.PaperEncodingPipeline(_small(pipeline.PaperEncodingConfig()), log=lambda *a: None)
+    p.train()
+    rid, qo, goff, count = p.model.frontend(p.rays, tlas=p.tlas)
+    torch.cuda.synchronize()
+    nq = int(count.item())
+    g = goff.tolist()
+    inner = p.cls["inner"]["model"]                     # 48 wide, trained
+    w32 = p.cls["inner"]["w_master"]
+    f32 = nif.NifModel(nif.NifConfig(**{**inner.cfg.__dict__, "mlp_dtype": L.NIF_F32, "grid_dtype": L.NIF_F32}),
+                       inner.obj_aabb, inner.grids.float(), w32)
+    pad = nif.NifModel(nif.NifConfig(**{**p.inner_inf.cfg.__dict__, "mlp_dtype": L.NIF_F32,
+                                        "grid_dtype": L.NIF_F32}),
+                       inner.obj_aabb, inner.grids.float(),
+                       pipeline._pad_width(w32, inner.cfg.K, inner.cfg.width, inner.cfg.n_hidden, 64))
+    z48 = f32.infer_queries(p.rays, rid, qo, goff[1:], nq)[g[1]:g[2]]
+    z64 = pad.infer_queries(p.rays, rid, qo, goff[1:], nq)[g[1]:g[2]]
+    torch.cuda.synchronize()
+    assert g[2] - g[1] > 1000
+    assert float((z48 - z64).abs().max()) <= 1e-5 * max(1.0, float(z48.abs().max()))
