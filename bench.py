@@ -287,6 +287,48 @@ def precision_sweep(pipe, log, steps: int = 10, warmup: int = 3):
     return out
 
 
+def r_sweep(log, steps: int = 5, warmup: int = 3):
+    """The paper's resolution sweep (Fig. 4: outer grid R = 64 / 256 / 1024)
+    on the paper-encoding workload: per R a freshly trained pipeline, its
+    visibility disagreement with the BVH and the device time of the query
+    step (L2 flushed before each)."""
+    import statistics
+
+    import torch
+
+    from paper_2306_07191_gb300 import nif
+    from paper_2306_07191_gb300.pipeline import PaperEncodingConfig, PaperEncodingPipeline
+    out = {}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for R in (64, 256, 1024):
+        pipe = PaperEncodingPipeline(PaperEncodingConfig(outer_res=R), log=log)
+        train_s = pipe.train()
+        dis = pipe.disagreement()
+        pipe.release_training_state()
+        for m, _ in pipe.forward_models():
+            m.cfg.ctas_per_sm, m.cfg.schedule = 4, 1
+        bits = nif.empty_bits(pipe.n_rays)
+        ts = []
+        for k in range(warmup + steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            pipe.query_step(bits)
+            e1.record()
+            torch.cuda.synchronize()
+            if k >= warmup:
+                ts.append(e0.elapsed_time(e1))
+        pipe.check()
+        ms = statistics.mean(ts)
+        out[R] = {"ms_per_step": ms, "rays_per_s": pipe.n_rays / (ms * 1e-3),
+                  "disagreement": dis["all"], "disagreement_queried": dis["queried"],
+                  "outer_grid_latents": int(pipe.cls["outer"]["model"].grids.numel()), "train_s": train_s}
+        log(f"R {R}: {out[R]}")
+        del pipe
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import ctypes
 
@@ -483,6 +525,8 @@ def run_ours(args):
     }
     if sweep is not None:
         line["precision_sweep"] = sweep
+    if args.r_sweep and args.workload == "paper" and rank == 0:
+        line["r_sweep"] = r_sweep(log)
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "room":
         line["cpu_baseline"] = cpu_baseline()
     elif rank == 0:
@@ -608,6 +652,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ctas-per-sm", type=int, default=0,
                     help="fix the serial schedule's CTAs per SM (skips the autotuner)")
+    ap.add_argument("--r-sweep", action="store_true",
+                    help="paper workload: also sweep the outer grid resolution R = 64, 256, 1024")
     ap.add_argument("--schedule", default="", choices=["", "serial", "pipelined"],
                     help="fix the fused kernel's schedule (skips the autotuner)")
     ap.add_argument("--workload", default="room", choices=sorted(WORKLOADS))
