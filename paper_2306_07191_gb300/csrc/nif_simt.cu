@@ -393,59 +393,118 @@ __global__ void __launch_bounds__(128) k_encode(NifParams p, const nif_ray* rays
 }
 
 // ------------------------------------------------------- FP32 MLP forward
-// One block of kTile threads handles a tile of queries of one network; the
-// activations live in shared memory as [feature][query] (+1 padding).
+// A block of kFThreads threads takes a tile of kTile queries of one network.
+// Activations live in shared memory as [feature][query] rows of kLq floats
+// (16-byte aligned); each thread computes 4 outputs x 4 queries of a layer
+// from 128-bit shared loads of the transposed weights and the activations
+// (8 FMAs per load), the weights staged in chunks of kKc input features.
 constexpr int kTile = 64;
-constexpr int kLd = kTile + 1;
+constexpr int kLq = kTile + 4;   // row stride of the [feature][query] tiles
+constexpr int kFThreads = 256;
+constexpr int kKc = 32;          // input features per staged weight chunk
+constexpr int kJb = 64;          // output units per pass
 
 __device__ __forceinline__ float act_fn(const NifParams& p, float a) {
   return a > 0.f ? a : (p.act == NIF_ACT_LEAKY ? p.slope * a : 0.f);
 }
 
+__host__ __device__ inline int round4(int x) { return (x + 3) & ~3; }
+
+// out[j][q] = act(sum_k w[j * fan_in + k] in[k][q]) for j < n_out, all kTile
+// queries; w row-major [n_out][fan_in] in global memory.
+__device__ __forceinline__ void layer_fwd_f32(const NifParams& p, const float* __restrict__ w,
+                                              int fan_in, int n_out, const float* in, float* out,
+                                              float* wt, bool activate) {
+  const int tid = threadIdx.x;
+  const int tq = tid & 15, tj = tid >> 4;  // 16 query blocks x 16 unit blocks of 4
+  for (int j0 = 0; j0 < n_out; j0 += kJb) {
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    for (int k0 = 0; k0 < fan_in; k0 += kKc) {
+      __syncthreads();
+      // stage wt[k][j] = w[j0 + j][k0 + k] (zero outside the matrix)
+      for (int e = tid; e < kKc * kJb; e += kFThreads) {
+        const int k = e / kJb, j = e % kJb;
+        const int gj = j0 + j, gk = k0 + k;
+        wt[k * kJb + j] = (gj < n_out && gk < fan_in) ? __ldg(w + static_cast<int64_t>(gj) * fan_in + gk) : 0.f;
+      }
+      __syncthreads();
+      const int kn = fan_in - k0 < kKc ? fan_in - k0 : kKc;
+      for (int k = 0; k < kn; ++k) {
+        const float4 wv = *reinterpret_cast<const float4*>(wt + k * kJb + 4 * tj);
+        const float4 xv = *reinterpret_cast<const float4*>(in + (k0 + k) * kLq + 4 * tq);
+        const float wa[4] = {wv.x, wv.y, wv.z, wv.w}, xa[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(wa[a], xa[b], acc[a][b]);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      const int j = j0 + 4 * tj + a;
+      if (j < n_out) {
+        float4 v;
+        v.x = activate ? act_fn(p, acc[a][0]) : acc[a][0];
+        v.y = activate ? act_fn(p, acc[a][1]) : acc[a][1];
+        v.z = activate ? act_fn(p, acc[a][2]) : acc[a][2];
+        v.w = activate ? act_fn(p, acc[a][3]) : acc[a][3];
+        *reinterpret_cast<float4*>(out + j * kLq + 4 * tq) = v;
+      }
+    }
+  }
+  __syncthreads();
+}
+
 template <int F, typename TG>
-__global__ void __launch_bounds__(kTile) k_mlp_fwd_f32(NifParams p, const nif_ray* rays,
-                                                       const uint32_t* ray_id,
-                                                       const uint32_t* qobj, const int64_t* goff,
-                                                       uint32_t* occ_bits, float* logits,
-                                                       float* saved, int64_t ld_saved) {
-  extern __shared__ float s_act[];
+__global__ void __launch_bounds__(kFThreads) k_mlp_fwd_f32(NifParams p, const nif_ray* rays,
+                                                           const uint32_t* ray_id,
+                                                           const uint32_t* qobj, const int64_t* goff,
+                                                           uint32_t* occ_bits, float* logits,
+                                                           float* saved, int64_t ld_saved) {
+  extern __shared__ __align__(16) float s_act[];
   __shared__ int64_t s_pre[kMaxGroups + 1];
   const int W = p.width, K = p.K, H = p.n_hidden;
-  const int maxf = K > W ? K : W;
-  float* A = s_act;               // [maxf][kLd]
-  float* B = s_act + maxf * kLd;  // [maxf][kLd]
-  int64_t n_tiles = build_tile_prefix(goff, p.n_nets, kTile, s_pre);
+  const int maxf = round4(K > W ? K : W);
+  float* A = s_act;                // [maxf][kLq]
+  float* B = A + maxf * kLq;       // [maxf][kLq]
+  float* wt = B + maxf * kLq;      // [kKc][kJb]
+  const int64_t n_tiles = build_tile_prefix(goff, p.n_nets, kTile, s_pre);
   const float* wall = static_cast<const float*>(p.weights);
+  const int tid = threadIdx.x;
   for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-    int g = find_group(s_pre, p.n_nets, t);
-    int64_t q0 = goff[g] + (t - s_pre[g]) * kTile;
-    int64_t qend = goff[g + 1];
-    int64_t q = q0 + threadIdx.x;
-    bool live = q < qend;
-    int tid = threadIdx.x;
-    if (live) {
-      nif_ray r = load_nif_ray(rays, ray_id[q]);
-      encode_query<F, TG>(p, r, qobj[q], [&](int k, float v) { A[k * kLd + tid] = v; });
-      if (saved)
-        for (int k = 0; k < K; ++k) saved[k * ld_saved + q] = A[k * kLd + tid];
+    const int g = find_group(s_pre, p.n_nets, t);
+    const int64_t q0 = goff[g] + (t - s_pre[g]) * kTile;
+    const int64_t qend = goff[g + 1];
+    const int nrow = static_cast<int>(qend - q0 < kTile ? qend - q0 : kTile);
+    // encode: one thread per query; rows past the end and padding are zero
+    for (int e = tid; e < maxf * kTile; e += kFThreads) A[(e / kTile) * kLq + e % kTile] = 0.f;
+    __syncthreads();
+    if (tid < nrow) {
+      const int64_t q = q0 + tid;
+      const nif_ray r = load_nif_ray(rays, ray_id[q]);
+      encode_query<F, TG>(p, r, qobj[q], [&](int k, float v) { A[k * kLq + tid] = v; });
     }
     __syncthreads();
+    if (saved)
+      for (int e = tid; e < K * kTile; e += kFThreads) {
+        const int k = e / kTile, c = e % kTile;
+        if (c < nrow) saved[k * ld_saved + q0 + c] = A[k * kLq + c];
+      }
     const float* w = wall + static_cast<int64_t>(g) * p.P;
-    int fan_in = K;
+    int fan_in = K, soff = K;
     float* in = A;
     float* out = B;
-    int soff = K;
     for (int l = 0; l < H; ++l) {
-      if (live) {
-        for (int j = 0; j < W; ++j) {
-          const float* wr = w + static_cast<int64_t>(j) * fan_in;
-          float acc = 0.f;
-          for (int k = 0; k < fan_in; ++k) acc += __ldg(wr + k) * in[k * kLd + tid];
-          float h = act_fn(p, acc);
-          out[j * kLd + tid] = h;
-          if (saved) saved[(soff + j) * ld_saved + q] = h;
+      layer_fwd_f32(p, w, fan_in, W, in, out, wt, true);
+      if (saved)
+        for (int e = tid; e < W * kTile; e += kFThreads) {
+          const int j = e / kTile, c = e % kTile;
+          if (c < nrow) saved[(soff + j) * ld_saved + q0 + c] = out[j * kLq + c];
         }
-      }
       w += static_cast<int64_t>(W) * fan_in;
       fan_in = W;
       soff += W;
@@ -453,9 +512,10 @@ __global__ void __launch_bounds__(kTile) k_mlp_fwd_f32(NifParams p, const nif_ra
       in = out;
       out = tmp;
     }
-    if (live) {
+    if (tid < nrow) {
       float z = 0.f;
-      for (int k = 0; k < fan_in; ++k) z += __ldg(w + k) * in[k * kLd + tid];
+      for (int k = 0; k < fan_in; ++k) z = fmaf(__ldg(w + k), in[k * kLq + tid], z);
+      const int64_t q = q0 + tid;
       if (logits) logits[q] = z;
       if (occ_bits && z < 0.f) atomicOr(&occ_bits[ray_id[q] >> 5], 1u << (ray_id[q] & 31));
     }
@@ -481,38 +541,53 @@ __global__ void k_loss(const float* z, const uint8_t* label, int64_t nq, float s
 }
 
 // ----------------------------------------------------- FP32 MLP backward
-// Tile of kTile queries of one network: loads the saved activations, walks
-// the layers backwards, accumulates the tile's weight gradient in registers
-// (one output row per thread) and adds it to the global gradient.
-__global__ void __launch_bounds__(kTile) k_mlp_bwd_f32(NifParams p, const int64_t* goff,
-                                                       const float* saved, int64_t ld_saved,
-                                                       const float* dz, float* wgrad, float* dx) {
-  extern __shared__ float s_act[];
+// A block of kFThreads threads takes a tile of kTile queries of one network:
+// it loads the tile's saved activations, walks the layers backwards and adds
+// the tile's weight gradient to the global one.  Both contractions of a
+// layer run on 4 x 4 register micro-tiles from 128-bit shared loads:
+// dW[j][k] = sum_q da[j][q] h_in[k][q] and dh_in[k][q] = sum_j da[j][q] W[j][k]
+// (W staged in chunks of kJb input features, transposed to [j][k]).
+__global__ void __launch_bounds__(kFThreads) k_mlp_bwd_f32(NifParams p, const int64_t* goff,
+                                                           const float* saved, int64_t ld_saved,
+                                                           const float* dz, float* wgrad, float* dx) {
+  extern __shared__ __align__(16) float s_act[];
   __shared__ int64_t s_pre[kMaxGroups + 1];
   const int W = p.width, K = p.K, H = p.n_hidden;
-  const int maxf = K > W ? K : W;
-  float* Hs = s_act;                                   // [K + H*W][kLd]
-  float* DA = s_act + (K + H * W) * kLd;               // [W][kLd]
-  float* DH = DA + W * kLd;                            // [maxf][kLd]
-  int64_t n_tiles = build_tile_prefix(goff, p.n_nets, kTile, s_pre);
+  const int maxf = round4(K > W ? K : W);
+  const int W4 = round4(W);
+  // saved rows: inputs [0, K), layer l outputs at off_h(l) (each group of rows 4-aligned)
+  auto off_h = [&](int l) { return round4(K) + l * W4; };
+  float* Hs = s_act;                                   // [round4(K) + H * W4][kLq]
+  float* DA = Hs + (round4(K) + H * W4) * kLq;         // [W4][kLq]
+  float* DH = DA + W4 * kLq;                           // [maxf][kLq]
+  float* wc = DH + maxf * kLq;                         // [W4][kJb + 4]
+  constexpr int kLw = kJb + 4;
+  const int64_t n_tiles = build_tile_prefix(goff, p.n_nets, kTile, s_pre);
   const float* wall = static_cast<const float*>(p.weights);
   const int tid = threadIdx.x;
+  const int tq = tid & 15, tb = tid >> 4;
   for (int64_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-    int g = find_group(s_pre, p.n_nets, t);
-    int64_t q0 = goff[g] + (t - s_pre[g]) * kTile;
-    int64_t qend = goff[g + 1];
-    int nrow = static_cast<int>(qend - q0 < kTile ? qend - q0 : kTile);
-    const int S = K + H * W;
-    for (int idx = tid; idx < S * kTile; idx += blockDim.x) {
-      int f = idx / kTile, c = idx % kTile;
-      Hs[f * kLd + c] = c < nrow ? saved[f * ld_saved + q0 + c] : 0.f;
+    const int g = find_group(s_pre, p.n_nets, t);
+    const int64_t q0 = goff[g] + (t - s_pre[g]) * kTile;
+    const int64_t qend = goff[g + 1];
+    const int nrow = static_cast<int>(qend - q0 < kTile ? qend - q0 : kTile);
+    // saved activations of the tile (zero past the end and in the padding rows)
+    const int S = round4(K) + H * W4;
+    for (int e = tid; e < S * kTile; e += kFThreads) {
+      const int f = e / kTile, c = e % kTile;
+      int src = -1;
+      if (f < K) src = f;
+      else if (f >= round4(K)) {
+        const int l = (f - round4(K)) / W4, j = (f - round4(K)) % W4;
+        if (j < W) src = K + l * W + j;
+      }
+      Hs[f * kLq + c] = (src >= 0 && c < nrow) ? saved[src * ld_saved + q0 + c] : 0.f;
     }
-    float dzq = tid < nrow ? dz[q0 + tid] : 0.f;
+    for (int e = tid; e < W4 * kTile; e += kFThreads) DA[(e / kTile) * kLq + e % kTile] = 0.f;
     __syncthreads();
-    // offsets of each layer's weights inside the network's block
     const float* w = wall + static_cast<int64_t>(g) * p.P;
     float* gw = wgrad + static_cast<int64_t>(g) * p.P;
-    int64_t woff[NIF_MAX_LEVELS];  // H <= NIF_MAX_LEVELS
+    int64_t woff[NIF_MAX_LEVELS + 1];
     {
       int64_t o = 0;
       int fi = K;
@@ -524,48 +599,96 @@ __global__ void __launch_bounds__(kTile) k_mlp_bwd_f32(NifParams p, const int64_
       woff[H] = o;
     }
     const int fan_last = H > 0 ? W : K;
-    const float* hl = Hs + (H > 0 ? (K + (H - 1) * W) : 0) * kLd;
+    const float* hl = Hs + (H > 0 ? off_h(H - 1) : 0) * kLq;
     // output layer: dw_out[j] = sum_q dz_q h_H[j][q]; dh[j][q] = dz_q w_out[j]
-    // (dz staged in row 0 of DA so every thread can read all of them)
-    DA[tid] = dzq;  // row 0 of DA used as scratch for dz
+    float* dzs = DA;  // row 0 of DA as scratch for dz
+    if (tid < kTile) dzs[tid] = tid < nrow ? dz[q0 + tid] : 0.f;
     __syncthreads();
-    for (int j = tid; j < fan_last; j += blockDim.x) {
+    for (int j = tid; j < fan_last; j += kFThreads) {
       float acc = 0.f;
-      for (int c = 0; c < nrow; ++c) acc += DA[c] * hl[j * kLd + c];
+      for (int c = 0; c < nrow; ++c) acc = fmaf(dzs[c], hl[j * kLq + c], acc);
       atomicAdd(&gw[woff[H] + j], acc);
     }
-    __syncthreads();
-    for (int j = 0; j < fan_last; ++j) DH[j * kLd + tid] = dzq * __ldg(w + woff[H] + j);
+    for (int e = tid; e < fan_last * kTile; e += kFThreads) {
+      const int j = e / kTile, c = e % kTile;
+      DH[j * kLq + c] = dzs[c] * __ldg(w + woff[H] + j);
+    }
     __syncthreads();
     for (int l = H - 1; l >= 0; --l) {
       const int fan_in = l == 0 ? K : W;
-      const float* hin = Hs + (l == 0 ? 0 : (K + (l - 1) * W)) * kLd;
-      const float* hout = Hs + (K + l * W) * kLd;
-      // da = dh * act'(a); act'(a) from the sign of the saved activation
-      for (int j = 0; j < W; ++j) {
-        float h = hout[j * kLd + tid];
-        float gdr = h > 0.f ? 1.f : (p.act == NIF_ACT_LEAKY ? p.slope : 0.f);
-        DA[j * kLd + tid] = tid < nrow ? DH[j * kLd + tid] * gdr : 0.f;
+      const float* hin = Hs + (l == 0 ? 0 : off_h(l - 1)) * kLq;
+      const float* hout = Hs + off_h(l) * kLq;
+      // da = dh * act'(a), act'(a) from the sign of the saved activation
+      for (int e = tid; e < W * kTile; e += kFThreads) {
+        const int j = e / kTile, c = e % kTile;
+        const float h = hout[j * kLq + c];
+        const float gdr = h > 0.f ? 1.f : (p.act == NIF_ACT_LEAKY ? p.slope : 0.f);
+        DA[j * kLq + c] = c < nrow ? DH[j * kLq + c] * gdr : 0.f;
       }
       __syncthreads();
-      // dW_l[j][k] += sum_q da[j][q] hin[k][q]
-      for (int j = tid; j < W; j += blockDim.x) {
-        for (int k = 0; k < fan_in; ++k) {
-          float acc = 0.f;
-          for (int c = 0; c < nrow; ++c) acc += DA[j * kLd + c] * hin[k * kLd + c];
-          atomicAdd(&gw[woff[l] + static_cast<int64_t>(j) * fan_in + k], acc);
+      // dW_l[j][k] += sum_q da[j][q] hin[k][q]: micro-tiles of 4 units x 4 inputs
+      const int njb = W4 / 4, nkb = round4(fan_in) / 4;
+      for (int mt = tid; mt < njb * nkb; mt += kFThreads) {
+        const int j0 = 4 * (mt / nkb), k0 = 4 * (mt % nkb);
+        float acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+        for (int c = 0; c < kTile; c += 4) {
+          float4 da[4], hv[4];
+#pragma unroll
+          for (int a = 0; a < 4; ++a) da[a] = *reinterpret_cast<const float4*>(DA + (j0 + a) * kLq + c);
+#pragma unroll
+          for (int b = 0; b < 4; ++b) hv[b] = *reinterpret_cast<const float4*>(hin + (k0 + b) * kLq + c);
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+              acc[a][b] += da[a].x * hv[b].x + da[a].y * hv[b].y + da[a].z * hv[b].z + da[a].w * hv[b].w;
         }
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b)
+            if (j0 + a < W && k0 + b < fan_in)
+              atomicAdd(&gw[woff[l] + static_cast<int64_t>(j0 + a) * fan_in + k0 + b], acc[a][b]);
       }
-      // dh_prev[k][q] = sum_j da[j][q] W_l[j][k]
-      for (int k = 0; k < fan_in; ++k) {
-        float acc = 0.f;
-        for (int j = 0; j < W; ++j) acc += DA[j * kLd + tid] * __ldg(w + woff[l] + static_cast<int64_t>(j) * fan_in + k);
-        DH[k * kLd + tid] = acc;
+      // dh_prev[k][q] = sum_j da[j][q] W_l[j][k], in passes of kJb inputs
+      for (int kb = 0; kb < fan_in; kb += kJb) {
+        __syncthreads();
+        for (int e = tid; e < W * kJb; e += kFThreads) {
+          const int j = e / kJb, k = e % kJb;
+          wc[j * kLw + k] = kb + k < fan_in ? __ldg(w + woff[l] + static_cast<int64_t>(j) * fan_in + kb + k) : 0.f;
+        }
+        __syncthreads();
+        float acc[4][4];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+          for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+        for (int j = 0; j < W; ++j) {
+          const float4 wv = *reinterpret_cast<const float4*>(wc + j * kLw + 4 * tb);
+          const float4 dv = *reinterpret_cast<const float4*>(DA + j * kLq + 4 * tq);
+          const float wa[4] = {wv.x, wv.y, wv.z, wv.w}, da[4] = {dv.x, dv.y, dv.z, dv.w};
+#pragma unroll
+          for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int b = 0; b < 4; ++b) acc[a][b] = fmaf(wa[a], da[b], acc[a][b]);
+        }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          const int k = kb + 4 * tb + a;
+          if (k < fan_in)
+            *reinterpret_cast<float4*>(DH + k * kLq + 4 * tq) = make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
+        }
       }
       __syncthreads();
     }
-    if (tid < nrow)
-      for (int k = 0; k < K; ++k) dx[k * ld_saved + q0 + tid] = DH[k * kLd + tid];
+    for (int e = tid; e < K * kTile; e += kFThreads) {
+      const int k = e / kTile, c = e % kTile;
+      if (c < nrow) dx[k * ld_saved + q0 + c] = DH[k * kLq + c];
+    }
     __syncthreads();
   }
 }
@@ -660,6 +783,56 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ th, float* __r
         else copy[i] = __float2bfloat16_rn(t);
       } else {
         copy[i] = t;
+      }
+    }
+  }
+}
+
+// The same update four parameters at a time (128-bit loads and stores of
+// the FP32 state, 64-bit stores of a 16-bit copy); the launcher uses it when
+// every buffer is 16-byte aligned and runs the scalar kernel on the tail.
+__device__ __forceinline__ void adam_one(float& t, float& g, float& m, float& v, float lr, float b1,
+                                         float b2, float eps, float inv_scale, float c1, float c2) {
+  const float gs = g * inv_scale;
+  m = b1 * m + (1.f - b1) * gs;
+  v = b2 * v + (1.f - b2) * gs * gs;
+  const float mh = m * c1, vh = v * c2;
+  t = t - lr * mh / (sqrtf(vh) + eps);
+  g = 0.f;
+}
+
+template <typename TC>
+__global__ void __launch_bounds__(256) k_adam4(float4* __restrict__ th, float4* __restrict__ gr,
+                                               float4* __restrict__ m1, float4* __restrict__ m2,
+                                               int64_t n4, float lr, float b1, float b2, float eps,
+                                               float inv_scale, float c1, float c2,
+                                               TC* __restrict__ copy) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    float4 t = th[i], g = gr[i], m = m1[i], v = m2[i];
+    adam_one(t.x, g.x, m.x, v.x, lr, b1, b2, eps, inv_scale, c1, c2);
+    adam_one(t.y, g.y, m.y, v.y, lr, b1, b2, eps, inv_scale, c1, c2);
+    adam_one(t.z, g.z, m.z, v.z, lr, b1, b2, eps, inv_scale, c1, c2);
+    adam_one(t.w, g.w, m.w, v.w, lr, b1, b2, eps, inv_scale, c1, c2);
+    th[i] = t;
+    gr[i] = g;
+    m1[i] = m;
+    m2[i] = v;
+    if (copy) {
+      if constexpr (std::is_same<TC, __half>::value) {
+        const __half2 a = __floats2half2_rn(t.x, t.y), b = __floats2half2_rn(t.z, t.w);
+        uint2 u;
+        u.x = *reinterpret_cast<const uint32_t*>(&a);
+        u.y = *reinterpret_cast<const uint32_t*>(&b);
+        reinterpret_cast<uint2*>(copy)[i] = u;
+      } else if constexpr (std::is_same<TC, __nv_bfloat16>::value) {
+        const __nv_bfloat162 a = __floats2bfloat162_rn(t.x, t.y), b = __floats2bfloat162_rn(t.z, t.w);
+        uint2 u;
+        u.x = *reinterpret_cast<const uint32_t*>(&a);
+        u.y = *reinterpret_cast<const uint32_t*>(&b);
+        reinterpret_cast<uint2*>(copy)[i] = u;
+      } else {
+        reinterpret_cast<float4*>(copy)[i] = t;
       }
     }
   }
@@ -848,8 +1021,8 @@ nif_status launch_encode(const NifParams& p, const nif_ray* rays, const uint32_t
 }
 
 size_t fwd_f32_smem(const NifParams& p) {
-  int maxf = p.K > p.width ? p.K : p.width;
-  return 2 * sizeof(float) * maxf * kLd;
+  const int maxf = round4(p.K > p.width ? p.K : p.width);
+  return sizeof(float) * (2 * maxf * kLq + kKc * kJb);
 }
 
 nif_status launch_fwd_f32(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
@@ -859,12 +1032,13 @@ nif_status launch_fwd_f32(const NifParams& p, const nif_ray* rays, const uint32_
   if (p.enc != NIF_ENC_MULTIRES && p.net_mode == NIF_NETS_CLASS)
     return fail(NIF_ERR_ARG, "spherical encodings: one class per model (net_mode single or object)");
   size_t sh = fwd_f32_smem(p);
-  int blocks = sm_count() * 8;
+  if (sh > 200 * 1024) return fail(NIF_ERR_UNSUPPORTED, "FP32 forward: network input too wide");
+  int blocks = sm_count() * 3;
   if (nq_hint >= 0) blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(blocks, ceil_div(nq_hint, kTile) + p.n_nets)));
   NIF_DISPATCH_FG(p, {
     auto kern = k_mlp_fwd_f32<F, TG>;
     NIF_CUDA_TRY(ensure_smem(kern, sh));
-    kern<<<blocks, kTile, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, saved, ld_saved);
+    kern<<<blocks, kFThreads, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, saved, ld_saved);
   });
   NIF_LAUNCH_CHECK();
   return NIF_OK;
@@ -882,12 +1056,13 @@ nif_status launch_loss(const float* z, const uint8_t* label, int64_t nq, float s
 
 nif_status launch_bwd_f32(const NifParams& p, const int64_t* goff, int64_t nq, const float* saved,
                           const float* dz, float* wgrad, float* dx, cudaStream_t st) {
-  int maxf = p.K > p.width ? p.K : p.width;
-  size_t sh = sizeof(float) * kLd * (p.K + p.n_hidden * p.width + p.width + maxf);
+  const int maxf = round4(p.K > p.width ? p.K : p.width), W4 = round4(p.width);
+  const size_t sh = sizeof(float) * (static_cast<size_t>(kLq) * (round4(p.K) + p.n_hidden * W4 + W4 + maxf) +
+                                     static_cast<size_t>(W4) * (kJb + 4));
   if (sh > 220 * 1024) return fail(NIF_ERR_UNSUPPORTED, "mlp backward: network too large for one tile");
   NIF_CUDA_TRY(ensure_smem(k_mlp_bwd_f32, sh));
   int blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(sm_count() * 2, ceil_div(nq, kTile) + p.n_nets)));
-  k_mlp_bwd_f32<<<blocks, kTile, sh, st>>>(p, goff, saved, nq, dz, wgrad, dx);
+  k_mlp_bwd_f32<<<blocks, kFThreads, sh, st>>>(p, goff, saved, nq, dz, wgrad, dx);
   NIF_LAUNCH_CHECK();
   return NIF_OK;
 }
@@ -910,6 +1085,35 @@ nif_status launch_adam(float* th, float* gr, float* m1, float* m2, int64_t n, fl
   double c2 = 1.0 / (1.0 - std::pow(static_cast<double>(b2), step));
   int blocks = static_cast<int>(std::min<int64_t>(ceil_div(n, 256), sm_count() * 16));
   float inv = 1.0f / grad_scale;
+  auto a16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+  const int csz = copy_dtype == NIF_F32 ? 4 : 2;
+  if (n >= 4 && a16(th) && a16(gr) && a16(m1) && a16(m2) &&
+      (copy == nullptr || (reinterpret_cast<uintptr_t>(copy) & (4 * csz - 1)) == 0)) {
+    const int64_t n4 = n / 4;
+    const int b4 = static_cast<int>(std::min<int64_t>(ceil_div(n4, 256), sm_count() * 16));
+    auto v4 = [](float* q) { return reinterpret_cast<float4*>(q); };
+    if (copy == nullptr || copy_dtype == NIF_F32)
+      k_adam4<float><<<b4, 256, 0, st>>>(v4(th), v4(gr), v4(m1), v4(m2), n4, lr, b1, b2, eps, inv, (float)c1,
+                                         (float)c2, (float*)copy);
+    else if (copy_dtype == NIF_F16)
+      k_adam4<__half><<<b4, 256, 0, st>>>(v4(th), v4(gr), v4(m1), v4(m2), n4, lr, b1, b2, eps, inv, (float)c1,
+                                          (float)c2, (__half*)copy);
+    else if (copy_dtype == NIF_BF16)
+      k_adam4<__nv_bfloat16><<<b4, 256, 0, st>>>(v4(th), v4(gr), v4(m1), v4(m2), n4, lr, b1, b2, eps, inv,
+                                                 (float)c1, (float)c2, (__nv_bfloat16*)copy);
+    else
+      return fail(NIF_ERR_UNSUPPORTED, "adam: unsupported copy dtype %d", copy_dtype);
+    NIF_LAUNCH_CHECK();
+    const int64_t done = n4 * 4;
+    if (done == n) return NIF_OK;
+    th += done;
+    gr += done;
+    m1 += done;
+    m2 += done;
+    if (copy) copy = static_cast<char*>(copy) + done * csz;
+    n -= done;
+    blocks = 1;
+  }
   if (copy == nullptr || copy_dtype == NIF_F32)
     k_adam<float><<<blocks, 256, 0, st>>>(th, gr, m1, m2, n, lr, b1, b2, eps, inv, (float)c1, (float)c2, (float*)copy);
   else if (copy_dtype == NIF_F16)
