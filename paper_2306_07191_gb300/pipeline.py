@@ -20,6 +20,25 @@ GRID_SEED = 0x5EED0001
 GRID_SCALE = 1e-4  # latent init U(-1e-4, 1e-4), Sec. 5 "Initialization"
 
 
+class BatchDraw:
+    """Training batches drawn without replacement: a seeded permutation of
+    the pool per epoch, cut into consecutive batches of pool indices."""
+
+    def __init__(self, n: int, seed: int):
+        self.n = n
+        self.rng = np.random.default_rng(seed)
+        self.perm = self.rng.permutation(n)
+        self.pos = 0
+
+    def __call__(self, b: int) -> np.ndarray:
+        if self.pos + b > self.n:
+            self.perm = self.rng.permutation(self.n)
+            self.pos = 0
+        sel = self.perm[self.pos:self.pos + b]
+        self.pos += b
+        return sel
+
+
 @dataclass
 class RoomConfig:
     n_obj: int = 64
@@ -215,14 +234,17 @@ class RoomPipeline:
         self.pairs = (rays, rid, qo, lab, n_outer)
         npool = int(rid.shape[0])
         self.trainer = nif.Trainer(self.model, lr=c.lr, w_master=self.w_master, g_master=self.g_master)
-        rng = np.random.default_rng(seed)
+        draw = BatchDraw(npool, seed)
         losses = []
         step_ev = []
         t0 = time.time()
         B = min(c.batch, npool)
         for s in range(steps):
-            idx = np.sort(rng.choice(npool, B, replace=False))
-            k = int(np.searchsorted(idx, n_outer))
+            idx = draw(B)
+            # outer pairs first, then inner ones (the pool is ordered that way)
+            inner = idx >= n_outer
+            k = int(B - np.count_nonzero(inner))
+            idx = np.concatenate([idx[~inner], idx[inner]])
             goff = torch.tensor([0, k, B], dtype=torch.int64, device=self.dev)
             it = torch.from_numpy(idx).to(self.dev)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -452,7 +474,8 @@ class PaperEncodingPipeline(RoomPipeline):
                  c.inner_features_1d, c.inner_hidden, c.inner_width))):
             ncfg = nif.NifConfig(res=[R], n_features=N, grid_dtype=L.NIF_F16, n_hidden=H, width=W,
                                  act=L.NIF_ACT_LEAKY, mlp_dtype=L.NIF_F16, net_mode=L.NIF_NETS_SINGLE,
-                                 encoding=enc, res_1d=R1, n_features_1d=N1)
+                                 encoding=enc, res_1d=R1, n_features_1d=N1,
+                                 ctas_per_sm=c.ctas_per_sm, schedule=c.schedule)
             n_grid = c.n_obj * nif.NifModel.grid_vertices(ncfg)
             g = torch.empty(n_grid, dtype=torch.float32, device=dev)
             L.call("nif_fill_uniform", ctypes.c_void_p(g.data_ptr()), n_grid, GRID_SEED + 17 * (k + 1),
@@ -526,7 +549,7 @@ class PaperEncodingPipeline(RoomPipeline):
             cl = self.cls[name]
             trainers[name] = nif.Trainer(cl["model"], lr=c.lr, w_master=cl["w_master"], g_master=cl["g_master"])
         self.trainers = trainers
-        rng = np.random.default_rng(seed)
+        draws = {name: BatchDraw(b - a, seed + k) for k, (name, (a, b)) in enumerate(parts.items())}
         B = min(c.batch, npool)
         losses, step_ev = [], []
         t0 = time.time()
@@ -538,7 +561,7 @@ class PaperEncodingPipeline(RoomPipeline):
                 nb = int(round(B * (b - a) / npool))
                 if nb == 0:
                     continue
-                idx = np.sort(rng.choice(b - a, nb, replace=False)) + a
+                idx = draws[name](nb) + a
                 it = torch.from_numpy(idx).to(self.dev)
                 goff = torch.tensor([0, nb], dtype=torch.int64, device=self.dev)
                 loss = trainers[name].step(rays, rid[it].contiguous(), qo[it].contiguous(), goff,
