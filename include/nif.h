@@ -401,6 +401,30 @@ nif_status nif_train_step(nif_model_desc* m, nif_optim_desc* o, const nif_ray* d
                           const int64_t* d_group_off, const uint8_t* d_label, int64_t nq,
                           float* d_loss, void* d_ws, size_t ws_bytes, void* stream);
 
+/* Checkpoint and resume of online training (Sec. 4.2 trains while rendering;
+ * resuming after an interruption needs the optimiser state).  The state is
+ * the FP32 master weights and grids, the Adam moments and o->step; the
+ * gradients are zero between steps and are not stored.  Host buffer layout
+ * (nif_state_size(m) bytes, caller-owned):
+ *   header: 8 x int64 {magic 0x5346494E ("NIFS"), version 1, K, width,
+ *           n_hidden, n_nets, weights (n_nets * P), grid elements (all objects)},
+ *           int64 step;
+ *   then FP32 arrays w_master | w_m | w_v | g_master | g_m | g_v.
+ * nif_state_save writes the header on the host and enqueues the device-to-host
+ *   copies on `stream`; the buffer is complete once the stream has reached
+ *   that point (synchronise before reading it).
+ * nif_state_load checks the header against m (NIF_ERR_ARG on a mismatch, before
+ *   any device work), enqueues the host-to-device copies, zeroes the
+ *   gradients, sets o->step and refreshes m->d_weights / m->d_grids from the
+ *   masters in their own dtypes.  h_buf must stay valid until the stream
+ *   has passed the copies.
+ * Returns 0 from nif_state_size on a bad descriptor. */
+size_t nif_state_size(const nif_model_desc* m);
+nif_status nif_state_save(const nif_model_desc* m, const nif_optim_desc* o, void* h_buf, size_t bytes,
+                          void* stream);
+nif_status nif_state_load(nif_model_desc* m, nif_optim_desc* o, const void* h_buf, size_t bytes,
+                          void* stream);
+
 /* Failure-detection self-test (no counterpart in the paper): runs the
  * bounded mbarrier wait that guards every tensor-core wait in the library on a
  * barrier nothing arrives on, with a limit of limit_cycles SM clocks (at most

@@ -82,6 +82,9 @@ SIGNATURES = {
     "nif_infer_queries": (i32, [MD, P, i64, P, P, P, i64, P, P, P, size_t, P]),
     "nif_infer": (i32, [MD, P, P, i64, P, P, size_t, P]),
     "nif_infer_query_counts": (i32, [MD, P, size_t, i64, P, P]),
+    "nif_state_size": (size_t, [MD]),
+    "nif_state_save": (i32, [MD, OD, P, size_t, P]),
+    "nif_state_load": (i32, [MD, OD, P, size_t, P]),
     "nif_frontend_nearest": (i32, [MD, P, P, i64, P, P, P, i64, P, P, P, size_t, P]),
     "nif_frontend_rest": (i32, [MD, P, P, i64, P, P, P, i64, P, P, P, P, size_t, P]),
     "nif_saved_size": (size_t, [MD, i64]),

@@ -555,6 +555,107 @@ nif_status nif_train_step(nif_model_desc* m, nif_optim_desc* o, const nif_ray* d
   return NIF_OK;
 }
 
+// ------------------------------------------------------------ checkpoint
+namespace {
+constexpr int64_t kStateMagic = 0x5346494E;  // "NIFS"
+constexpr int kStateHeader = 9;              // int64 words
+
+struct StateShape {
+  int64_t nw, ng;
+};
+
+bool state_shape(const NifParams& p, StateShape* s) {
+  s->nw = static_cast<int64_t>(p.n_nets) * p.P;
+  s->ng = static_cast<int64_t>(p.n_obj) * p.obj_elems;
+  return s->nw > 0 && s->ng > 0;
+}
+
+void state_header(const NifParams& p, const StateShape& sh, int64_t step, int64_t h[kStateHeader]) {
+  h[0] = kStateMagic;
+  h[1] = 1;
+  h[2] = p.K;
+  h[3] = p.width;
+  h[4] = p.n_hidden;
+  h[5] = p.n_nets;
+  h[6] = sh.nw;
+  h[7] = sh.ng;
+  h[8] = step;
+}
+}  // namespace
+
+size_t nif_state_size(const nif_model_desc* m) {
+  NifParams p;
+  StateShape sh;
+  if (make_params(m, &p) != NIF_OK || !state_shape(p, &sh)) return 0;
+  return sizeof(int64_t) * kStateHeader + sizeof(float) * 3 * static_cast<size_t>(sh.nw + sh.ng);
+}
+
+nif_status nif_state_save(const nif_model_desc* m, const nif_optim_desc* o, void* h_buf, size_t bytes,
+                          void* stream) {
+  NifParams p;
+  nif_status s = make_params(m, &p);
+  if (s != NIF_OK) return s;
+  StateShape sh;
+  NIF_CHECK_ARG(o && h_buf && state_shape(p, &sh), "nif_state_save: bad argument");
+  NIF_CHECK_ARG(bytes >= nif_state_size(m), "nif_state_save: buffer too small");
+  NIF_CHECK_ARG(o->d_w_master && o->d_w_m && o->d_w_v && o->d_g_master && o->d_g_m && o->d_g_v,
+                "nif_state_save: null optimiser buffer");
+  int64_t* h = static_cast<int64_t*>(h_buf);
+  state_header(p, sh, o->step, h);
+  float* f = reinterpret_cast<float*>(h + kStateHeader);
+  cudaStream_t st = as_stream(stream);
+  const float* src[6] = {o->d_w_master, o->d_w_m, o->d_w_v, o->d_g_master, o->d_g_m, o->d_g_v};
+  const int64_t len[6] = {sh.nw, sh.nw, sh.nw, sh.ng, sh.ng, sh.ng};
+  for (int i = 0; i < 6; ++i) {
+    NIF_CUDA_TRY(cudaMemcpyAsync(f, src[i], sizeof(float) * len[i], cudaMemcpyDeviceToHost, st));
+    f += len[i];
+  }
+  return NIF_OK;
+}
+
+nif_status nif_state_load(nif_model_desc* m, nif_optim_desc* o, const void* h_buf, size_t bytes,
+                          void* stream) {
+  NifParams p;
+  nif_status s = make_params(m, &p);
+  if (s != NIF_OK) return s;
+  StateShape sh;
+  NIF_CHECK_ARG(o && h_buf && state_shape(p, &sh), "nif_state_load: bad argument");
+  NIF_CHECK_ARG(bytes >= nif_state_size(m), "nif_state_load: buffer too small");
+  const int64_t* h = static_cast<const int64_t*>(h_buf);
+  int64_t want[kStateHeader];
+  state_header(p, sh, h[8], want);
+  for (int i = 0; i < kStateHeader - 1; ++i)
+    NIF_CHECK_ARG(h[i] == want[i], "nif_state_load: header word %d is %lld, the model needs %lld", i,
+                  static_cast<long long>(h[i]), static_cast<long long>(want[i]));
+  NIF_CHECK_ARG(h[8] >= 0 && h[8] < (int64_t(1) << 31), "nif_state_load: bad step count");
+  NIF_CHECK_ARG(o->d_w_master && o->d_w_m && o->d_w_v && o->d_g_master && o->d_g_m && o->d_g_v &&
+                    o->d_w_grad && o->d_g_grad,
+                "nif_state_load: null optimiser buffer");
+  const float* f = reinterpret_cast<const float*>(h + kStateHeader);
+  cudaStream_t st = as_stream(stream);
+  float* dst[6] = {o->d_w_master, o->d_w_m, o->d_w_v, o->d_g_master, o->d_g_m, o->d_g_v};
+  const int64_t len[6] = {sh.nw, sh.nw, sh.nw, sh.ng, sh.ng, sh.ng};
+  for (int i = 0; i < 6; ++i) {
+    NIF_CUDA_TRY(cudaMemcpyAsync(dst[i], f, sizeof(float) * len[i], cudaMemcpyHostToDevice, st));
+    f += len[i];
+  }
+  NIF_CUDA_TRY(cudaMemsetAsync(o->d_w_grad, 0, sizeof(float) * sh.nw, st));
+  NIF_CUDA_TRY(cudaMemsetAsync(o->d_g_grad, 0, sizeof(float) * sh.ng, st));
+  o->step = static_cast<int32_t>(h[8]);
+  // 16-bit (or FP32) copies the forward reads
+  void* wcopy = m->mlp_dtype == NIF_E4M3 ? nullptr : const_cast<void*>(m->d_weights);
+  if (wcopy && wcopy != o->d_w_master) {
+    s = launch_cast(o->d_w_master, sh.nw, wcopy, m->mlp_dtype, st);
+    if (s != NIF_OK) return s;
+  }
+  void* gcopy = const_cast<void*>(m->d_grids);
+  if (gcopy != o->d_g_master) {
+    s = launch_cast(o->d_g_master, sh.ng, gcopy, m->grid_dtype, st);
+    if (s != NIF_OK) return s;
+  }
+  return NIF_OK;
+}
+
 }  // extern "C"
 
 // ------------------------------------------------------------ self-test

@@ -60,6 +60,8 @@ nif_status launch_bwd_f32(const NifParams& p, const int64_t* goff, int64_t nq, c
 nif_status launch_grid_bwd(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
                            const uint32_t* qobj, int64_t nq, const float* dx, int64_t ld,
                            float* ggrad, cudaStream_t st);
+// dst[i] = src[i] converted to dtype (NIF_F32, NIF_F16 or NIF_BF16).
+nif_status launch_cast(const float* src, int64_t n, void* dst, int dtype, cudaStream_t st);
 nif_status launch_adam(float* th, float* gr, float* m1, float* m2, int64_t n, float lr, float b1,
                        float b2, float eps, float grad_scale, int step, void* copy, int copy_dtype,
                        cudaStream_t st);

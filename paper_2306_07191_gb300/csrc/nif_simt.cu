@@ -1077,6 +1077,26 @@ nif_status launch_grid_bwd(const NifParams& p, const nif_ray* rays, const uint32
   return NIF_OK;
 }
 
+template <typename TC>
+__global__ void __launch_bounds__(256) k_cast(const float* __restrict__ src, int64_t n, TC* __restrict__ dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if constexpr (std::is_same<TC, __half>::value) dst[i] = __float2half_rn(src[i]);
+    else if constexpr (std::is_same<TC, __nv_bfloat16>::value) dst[i] = __float2bfloat16_rn(src[i]);
+    else dst[i] = src[i];
+  }
+}
+
+nif_status launch_cast(const float* src, int64_t n, void* dst, int dtype, cudaStream_t st) {
+  if (n == 0) return NIF_OK;
+  const int blocks = static_cast<int>(std::min<int64_t>(ceil_div(n, 256), sm_count() * 16));
+  if (dtype == NIF_F32) k_cast<float><<<blocks, 256, 0, st>>>(src, n, static_cast<float*>(dst));
+  else if (dtype == NIF_F16) k_cast<__half><<<blocks, 256, 0, st>>>(src, n, static_cast<__half*>(dst));
+  else if (dtype == NIF_BF16) k_cast<__nv_bfloat16><<<blocks, 256, 0, st>>>(src, n, static_cast<__nv_bfloat16*>(dst));
+  else return fail(NIF_ERR_UNSUPPORTED, "cast: dtype %d", dtype);
+  NIF_LAUNCH_CHECK();
+  return NIF_OK;
+}
+
 nif_status launch_adam(float* th, float* gr, float* m1, float* m2, int64_t n, float lr, float b1,
                        float b2, float eps, float grad_scale, int step, void* copy, int copy_dtype,
                        cudaStream_t st) {

@@ -14,6 +14,7 @@ from __future__ import annotations
 import ctypes
 from dataclasses import dataclass, field
 
+import numpy as np
 import torch
 
 from . import _lib as L
@@ -292,6 +293,32 @@ class Trainer:
             setattr(self.o, "d_" + name, getattr(self, name).data_ptr())
         self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
         self._ws = None
+
+    def state_bytes(self, stream=None) -> np.ndarray:
+        """The optimiser state (nif_state_save): FP32 masters, Adam moments and
+        the step count in one host buffer, complete when this returns."""
+        d = self.model.desc()
+        buf = np.empty(int(L.lib.nif_state_size(ctypes.byref(d))), dtype=np.uint8)
+        L.call("nif_state_save", ctypes.byref(d), ctypes.byref(self.o), buf.ctypes.data_as(ctypes.c_void_p),
+               buf.nbytes, _stream(stream))
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        return buf
+
+    def load_state_bytes(self, buf: np.ndarray, stream=None):
+        """Resume from nif_state_save's buffer (nif_state_load): masters,
+        moments and step restored, gradients zeroed, the model's copies
+        refreshed."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        d = self.model.desc()
+        L.call("nif_state_load", ctypes.byref(d), ctypes.byref(self.o), buf.ctypes.data_as(ctypes.c_void_p),
+               buf.nbytes, _stream(stream))
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+
+    def save(self, path: str):
+        self.state_bytes().tofile(path)
+
+    def load(self, path: str):
+        self.load_state_bytes(np.fromfile(path, dtype=np.uint8))
 
     def step(self, rays, ray_id, qobj, goff, label, nq: int, stream=None):
         d = self.model.desc()

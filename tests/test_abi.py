@@ -134,3 +134,24 @@ def test_spherical_descriptor_sizes(L):
     assert L.lib.nif_weight_count(ctypes.byref(d)) == 13 * 48 + 2 * 48 * 48 + 48
     d.res_1d = 1  # a 1D grid needs two cells
     assert L.lib.nif_grid_vertices(ctypes.byref(d)) == -1
+
+
+def test_state_checkpoint_size_and_header_checks(L):
+    """nif_state_size follows the documented layout; nif_state_load refuses a
+    buffer whose header does not match the model (before any device work)."""
+    import numpy as np
+    d = _room_desc(L)
+    P = 96 * 64 + 2 * 64 * 64 + 64
+    V = 5723320
+    nw, ng = 2 * P, 64 * 2 * V * 2
+    size = L.lib.nif_state_size(ctypes.byref(d))
+    assert size == 9 * 8 + 4 * 3 * (nw + ng)
+    o = L.OptimDesc()
+    for name in ("d_w_master", "d_w_grad", "d_w_m", "d_w_v", "d_g_master", "d_g_grad", "d_g_m", "d_g_v"):
+        setattr(o, name, 256)  # never dereferenced: the header check fails first
+    buf = np.zeros(64, dtype=np.int64)
+    assert L.lib.nif_state_load(ctypes.byref(d), ctypes.byref(o), buf.ctypes.data_as(ctypes.c_void_p), size,
+                                None) == L.NIF_ERR_ARG
+    assert "header word 0" in L.last_error()
+    assert L.lib.nif_state_load(ctypes.byref(d), ctypes.byref(o), buf.ctypes.data_as(ctypes.c_void_p), 16,
+                                None) == L.NIF_ERR_ARG

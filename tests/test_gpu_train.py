@@ -163,3 +163,42 @@ def test_train_step_reduces_loss_and_beats_untrained_net():
     assert acc > 0.9, acc
     # the trained master weights were copied into the model
     assert torch.equal(model.weights, tr.w_master)
+
+
+def test_checkpoint_resume_restores_state_and_continues():
+    """nif_state_save / nif_state_load: a fresh trainer loaded from a
+    checkpoint holds the same masters, moments and step and the same model
+    copies, and the next steps of both runs agree (to FP32 atomic-order
+    rounding of the gradient sums)."""
+    model, om, rays, flat, grid = _setup(n_rays=8000, seed=7)
+    rays_t = torch.from_numpy(rays).cuda()
+    ray_id, qobj, goff, nq, r, ob, inn = _frontend(model, rays_t)
+    lab = torch.from_numpy(_labels_for(r, ob)).cuda()
+    tr = nif.Trainer(model, lr=1e-2)
+    for _ in range(5):
+        tr.step(rays_t, ray_id, qobj, goff, lab, nq)
+    buf = tr.state_bytes()
+    # a second model and trainer from the initial values
+    model2 = nif.NifModel(model.cfg, model.obj_aabb, torch.from_numpy(grid.reshape(-1)).cuda(),
+                          torch.from_numpy(flat).cuda())
+    tr2 = nif.Trainer(model2, lr=1e-2)
+    tr2.load_state_bytes(buf)
+    assert tr2.o.step == tr.o.step == 5
+    for name in ("w_master", "w_m", "w_v", "g_master", "g_m", "g_v"):
+        assert torch.equal(getattr(tr, name), getattr(tr2, name)), name
+    assert torch.equal(model.weights, model2.weights) and torch.equal(model.grids, model2.grids)
+    assert float(tr2.w_grad.abs().max()) == 0.0 and float(tr2.g_grad.abs().max()) == 0.0
+    for _ in range(3):
+        tr.step(rays_t, ray_id, qobj, goff, lab, nq)
+        tr2.step(rays_t, ray_id, qobj, goff, lab, nq)
+    torch.cuda.synchronize()
+    for name in ("w_master", "g_master"):
+        a, b = getattr(tr, name), getattr(tr2, name)
+        assert float((a - b).abs().max()) <= 1e-5 * max(1.0, float(a.abs().max())), name
+    # a model of another shape refuses the checkpoint
+    other = nif.NifModel(nif.NifConfig(**{**model.cfg.__dict__, "width": 32}), model.obj_aabb, model.grids,
+                         torch.zeros(nif.NifModel.weight_count(nif.NifConfig(**{**model.cfg.__dict__, "width": 32})) * 2,
+                                     device="cuda"))
+    tr3 = nif.Trainer(other, lr=1e-2)
+    with pytest.raises(L.NifError):
+        tr3.load_state_bytes(buf)
