@@ -28,8 +28,18 @@
  *     NIF_ERR_UNSUPPORTED, too small a buffer -> NIF_ERR_WORKSPACE) before any
  *     work is queued; nif_last_error() then describes the error.  A failed
  *     launch returns NIF_ERR_CUDA.  Errors found on the device (capacity
- *     overflow, bounded waits that expired, non-finite loss) are recorded in
- *     the first 16 bytes of the workspace and read by nif_check().
+ *     overflow, bounded waits that expired, non-finite loss or parameter)
+ *     are recorded in the first 16 bytes of the workspace and read by
+ *     nif_check().
+ *   - Query lists are validated on the device: a query whose object id
+ *     (qobj & 0x7fffffff) is not below n_obj, or whose ray id is not below
+ *     the call's ray count (where the call takes one), is skipped before any
+ *     memory it names is touched: its features and logit are 0 and no
+ *     occlusion bit is set for it, and calls with a workspace record it as
+ *     NIF_ERR_BOUNDS (detail = its index).  The other queries of the call
+ *     are unaffected.
+ *   - Every call is wrapped in an NVTX range named after it (NVTX 3,
+ *     header-only: inert unless a profiler attaches).
  *   - n == 0 is valid everywhere and queues nothing.
  */
 #ifndef NIF_H

@@ -304,6 +304,7 @@ nif_status nif_check(void* d_ws, int64_t* detail, void* stream) {
 nif_status nif_frontend(const nif_model_desc* m, const void* d_tlas, const nif_ray* d_rays, int64_t n,
                         uint32_t* d_ray_id, uint32_t* d_qobj, int64_t max_q, int64_t* d_group_off,
                         int64_t* d_count, void* d_ws, size_t ws_bytes, void* stream) {
+  CallRange nvtx_range("nif_frontend");
   NifParams p;
   nif_status s = make_params(m, &p);
   if (s != NIF_OK) return s;
@@ -323,6 +324,7 @@ nif_status nif_frontend(const nif_model_desc* m, const void* d_tlas, const nif_r
 nif_status nif_encode(const nif_model_desc* m, const nif_ray* d_rays, const uint32_t* d_ray_id,
                       const uint32_t* d_qobj, int64_t nq, void* d_features, int32_t features_dtype,
                       void* stream) {
+  CallRange nvtx_range("nif_encode");
   NifParams p;
   nif_status s = make_params(m, &p);
   if (s != NIF_OK) return s;
@@ -338,6 +340,7 @@ nif_status nif_infer_queries(const nif_model_desc* m, const nif_ray* d_rays, int
                              const uint32_t* d_ray_id, const uint32_t* d_qobj,
                              const int64_t* d_group_off, int64_t nq_max, uint32_t* d_occluded_bits,
                              float* d_logits, void* d_ws, size_t ws_bytes, void* stream) {
+  CallRange nvtx_range("nif_infer_queries");
   NifParams p;
   nif_status s = make_params(m, &p);
   if (s != NIF_OK) return s;
@@ -347,6 +350,8 @@ nif_status nif_infer_queries(const nif_model_desc* m, const nif_ray* d_rays, int
   NIF_CHECK_ARG(d_rays && d_ray_id && d_qobj, "nif_infer_queries: null pointer");
   NIF_CHECK_ARG(aligned16(d_rays), "nif_infer_queries: rays not 16-byte aligned");
   NIF_CHECK_ARG(d_ws == nullptr || ws_bytes >= kErrBytes, "nif_infer_queries: workspace too small");
+  p.n_rays = n_rays;
+  p.err = static_cast<DevError*>(d_ws);
   cudaStream_t st = as_stream(stream);
   if (p.mlp_dtype == NIF_F32)
     return launch_fwd_f32(p, d_rays, d_ray_id, d_qobj, d_group_off, nq_max, d_occluded_bits,
@@ -357,6 +362,7 @@ nif_status nif_infer_queries(const nif_model_desc* m, const nif_ray* d_rays, int
 
 nif_status nif_infer(const nif_model_desc* m, const void* d_tlas, const nif_ray* d_rays, int64_t n,
                      uint32_t* d_occluded_bits, void* d_ws, size_t ws_bytes, void* stream) {
+  CallRange nvtx_range("nif_infer");
   NifParams p;
   nif_status s = make_params(m, &p);
   if (s != NIF_OK) return s;
@@ -368,6 +374,8 @@ nif_status nif_infer(const nif_model_desc* m, const void* d_tlas, const nif_ray*
   if (max_q <= 0) return fail(NIF_ERR_WORKSPACE, "nif_infer: workspace too small");
   InferWs w = infer_layout(p, d_ws, max_q, n);
   if (w.bytes > ws_bytes) return fail(NIF_ERR_WORKSPACE, "nif_infer: workspace too small");
+  p.n_rays = n;
+  p.err = w.err;
   cudaStream_t st = as_stream(stream);
   auto forward = [&](const int64_t* goff) -> nif_status {
     if (p.mlp_dtype == NIF_F32)
@@ -393,6 +401,7 @@ nif_status nif_frontend_nearest(const nif_model_desc* m, const void* d_tlas, con
                                 int64_t n, const uint32_t* d_occluded_bits, uint32_t* d_ray_id,
                                 uint32_t* d_qobj, int64_t max_q, int64_t* d_group_off,
                                 int64_t* d_count, void* d_ws, size_t ws_bytes, void* stream) {
+  CallRange nvtx_range("nif_frontend_nearest");
   NifParams p;
   nif_status s = make_params(m, &p);
   if (s != NIF_OK) return s;
@@ -412,6 +421,7 @@ nif_status nif_frontend_rest(const nif_model_desc* m, const void* d_tlas, const 
                              uint32_t* d_qobj, int64_t max_q, const int64_t* d_count_nearest,
                              int64_t* d_group_off, int64_t* d_count, void* d_ws, size_t ws_bytes,
                              void* stream) {
+  CallRange nvtx_range("nif_frontend_rest");
   NifParams p;
   nif_status s = make_params(m, &p);
   if (s != NIF_OK) return s;
@@ -452,6 +462,7 @@ size_t nif_saved_size(const nif_model_desc* m, int64_t nq) {
 nif_status nif_fwd_train(const nif_model_desc* m, const nif_ray* d_rays, const uint32_t* d_ray_id,
                          const uint32_t* d_qobj, const int64_t* d_group_off, int64_t nq, float* d_z,
                          void* d_saved, void* stream) {
+  CallRange nvtx_range("nif_fwd_train");
   NifParams p;
   nif_status s = make_params(m, &p);
   if (s != NIF_OK) return s;
@@ -473,6 +484,7 @@ nif_status nif_loss(const float* d_z, const uint8_t* d_label, int64_t nq, float 
 nif_status nif_mlp_bwd(const nif_model_desc* m, const uint32_t* d_qobj, const int64_t* d_group_off,
                        int64_t nq, const void* d_saved, const float* d_dz, float* d_w_grad, float* d_dx,
                        void* stream) {
+  CallRange nvtx_range("nif_mlp_bwd");
   NifParams p;
   nif_status s = make_params(m, &p);
   if (s != NIF_OK) return s;
@@ -488,6 +500,7 @@ nif_status nif_mlp_bwd(const nif_model_desc* m, const uint32_t* d_qobj, const in
 nif_status nif_grid_bwd(const nif_model_desc* m, const nif_ray* d_rays, const uint32_t* d_ray_id,
                         const uint32_t* d_qobj, int64_t nq, const float* d_dx, float* d_g_grad,
                         void* stream) {
+  CallRange nvtx_range("nif_grid_bwd");
   NifParams p;
   nif_status s = make_params(m, &p);
   if (s != NIF_OK) return s;
@@ -500,6 +513,7 @@ nif_status nif_grid_bwd(const nif_model_desc* m, const nif_ray* d_rays, const ui
 nif_status nif_adam(float* d_master, float* d_grad, float* d_m, float* d_v, int64_t n, float lr,
                     float beta1, float beta2, float eps, float grad_scale, int32_t step, void* d_copy,
                     int32_t copy_dtype, void* stream) {
+  CallRange nvtx_range("nif_adam");
   NIF_CHECK_ARG(n >= 0, "nif_adam: negative n");
   NIF_CHECK_ARG(step >= 1, "nif_adam: step is 1-based");
   NIF_CHECK_ARG(grad_scale > 0.f, "nif_adam: grad_scale must be positive");
@@ -513,6 +527,7 @@ nif_status nif_train_step(nif_model_desc* m, nif_optim_desc* o, const nif_ray* d
                           const uint32_t* d_ray_id, const uint32_t* d_qobj, const int64_t* d_group_off,
                           const uint8_t* d_label, int64_t nq, float* d_loss, void* d_ws, size_t ws_bytes,
                           void* stream) {
+  CallRange nvtx_range("nif_train_step");
   NifParams p;
   nif_status s = make_params(m, &p);
   if (s != NIF_OK) return s;
@@ -526,6 +541,7 @@ nif_status nif_train_step(nif_model_desc* m, nif_optim_desc* o, const nif_ray* d
   if (w.bytes > ws_bytes) return fail(NIF_ERR_WORKSPACE, "nif_train_step: workspace too small (%zu < %zu)", ws_bytes, w.bytes);
   // FP32 master view of the model: forward and backward run on the masters.
   NifParams pm = p;
+  pm.err = w.err;
   pm.grids = o->d_g_master;
   pm.grid_dtype = NIF_F32;
   pm.weights = o->d_w_master;
@@ -545,11 +561,11 @@ nif_status nif_train_step(nif_model_desc* m, nif_optim_desc* o, const nif_ray* d
   const int64_t ng = (int64_t)p.n_obj * p.obj_elems;
   void* wcopy = m->mlp_dtype == NIF_E4M3 ? nullptr : const_cast<void*>(m->d_weights);
   s = launch_adam(o->d_w_master, o->d_w_grad, o->d_w_m, o->d_w_v, nw, o->lr, o->beta1, o->beta2, o->eps,
-                  o->loss_scale, step, wcopy == o->d_w_master ? nullptr : wcopy, m->mlp_dtype, st);
+                  o->loss_scale, step, wcopy == o->d_w_master ? nullptr : wcopy, m->mlp_dtype, st, w.err);
   if (s != NIF_OK) return s;
   void* gcopy = const_cast<void*>(m->d_grids);
   s = launch_adam(o->d_g_master, o->d_g_grad, o->d_g_m, o->d_g_v, ng, o->lr, o->beta1, o->beta2, o->eps,
-                  o->loss_scale, step, gcopy == o->d_g_master ? nullptr : gcopy, m->grid_dtype, st);
+                  o->loss_scale, step, gcopy == o->d_g_master ? nullptr : gcopy, m->grid_dtype, st, w.err);
   if (s != NIF_OK) return s;
   o->step = step;
   return NIF_OK;
@@ -592,6 +608,7 @@ size_t nif_state_size(const nif_model_desc* m) {
 
 nif_status nif_state_save(const nif_model_desc* m, const nif_optim_desc* o, void* h_buf, size_t bytes,
                           void* stream) {
+  CallRange nvtx_range("nif_state_save");
   NifParams p;
   nif_status s = make_params(m, &p);
   if (s != NIF_OK) return s;
@@ -615,6 +632,7 @@ nif_status nif_state_save(const nif_model_desc* m, const nif_optim_desc* o, void
 
 nif_status nif_state_load(nif_model_desc* m, nif_optim_desc* o, const void* h_buf, size_t bytes,
                           void* stream) {
+  CallRange nvtx_range("nif_state_load");
   NifParams p;
   nif_status s = make_params(m, &p);
   if (s != NIF_OK) return s;

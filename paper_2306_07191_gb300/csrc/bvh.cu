@@ -681,6 +681,7 @@ size_t bvh_build_workspace_size(int64_t n_tris) {
 nif_status bvh_build(const float* d_verts, int64_t n_verts, const int32_t* d_tris, int64_t n_tris,
                      const int32_t* d_tri_tag, void* d_bvh, size_t bvh_bytes, void* d_ws,
                      size_t ws_bytes, void* stream) {
+  CallRange nvtx_range("bvh_build");
   NIF_CHECK_ARG(n_tris >= 0 && n_verts >= 0, "bvh_build: negative size");
   NIF_CHECK_ARG(d_bvh != nullptr, "bvh_build: null output");
   NIF_CHECK_ARG(n_tris == 0 || (d_verts && d_tris && d_ws), "bvh_build: null input");
@@ -692,6 +693,7 @@ nif_status bvh_build(const float* d_verts, int64_t n_verts, const int32_t* d_tri
 
 nif_status bvh_build_boxes(const float* d_boxes, int64_t n, void* d_bvh, size_t bvh_bytes, void* d_ws,
                            size_t ws_bytes, void* stream) {
+  CallRange nvtx_range("bvh_build_boxes");
   NIF_CHECK_ARG(n >= 0, "bvh_build_boxes: negative size");
   NIF_CHECK_ARG(d_bvh != nullptr, "bvh_build_boxes: null output");
   NIF_CHECK_ARG(n == 0 || (d_boxes && d_ws), "bvh_build_boxes: null input");
@@ -717,6 +719,7 @@ nif_status bvh_info(const void* d_bvh, int64_t* n_nodes, int64_t* n_prims, int32
 
 nif_status bvh_cast_shadow(const void* d_bvh, const nif_ray* d_rays, int64_t n,
                            uint32_t* d_occluded_bits, void* stream) {
+  CallRange nvtx_range("bvh_cast_shadow");
   NIF_CHECK_ARG(n >= 0, "bvh_cast_shadow: negative n");
   if (n == 0) return NIF_OK;
   NIF_CHECK_ARG(d_bvh && d_rays && d_occluded_bits, "bvh_cast_shadow: null pointer");
@@ -729,6 +732,7 @@ nif_status bvh_cast_shadow(const void* d_bvh, const nif_ray* d_rays, int64_t n,
 
 nif_status bvh_cast_closest(const void* d_bvh, const nif_ray* d_rays, int64_t n, float* d_t,
                             int32_t* d_prim, void* stream) {
+  CallRange nvtx_range("bvh_cast_closest");
   NIF_CHECK_ARG(n >= 0, "bvh_cast_closest: negative n");
   if (n == 0) return NIF_OK;
   NIF_CHECK_ARG(d_bvh && d_rays, "bvh_cast_closest: null pointer");
@@ -741,6 +745,7 @@ nif_status bvh_cast_closest(const void* d_bvh, const nif_ray* d_rays, int64_t n,
 
 nif_status bvh_cast_pairs(const void* d_bvh, const nif_ray* d_rays, const uint32_t* d_ray_id,
                           const uint32_t* d_obj, int64_t nq, uint8_t* d_hit, void* stream) {
+  CallRange nvtx_range("bvh_cast_pairs");
   NIF_CHECK_ARG(nq >= 0, "bvh_cast_pairs: negative n");
   if (nq == 0) return NIF_OK;
   NIF_CHECK_ARG(d_bvh && d_rays && d_ray_id && d_obj && d_hit, "bvh_cast_pairs: null pointer");

@@ -9,6 +9,7 @@
 #include <stdint.h>
 #include <stdio.h>
 #include <stdarg.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/nif.h"
 
@@ -73,6 +74,16 @@ inline cudaError_t ensure_smem(Kernel kern, size_t bytes) {
 }
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// NVTX range around a C-ABI call, named after it, so that a profiler's
+// timeline groups each call's kernels (header-only NVTX 3: nothing is loaded
+// unless a tool injects itself).
+struct CallRange {
+  explicit CallRange(const char* name) { nvtxRangePushA(name); }
+  ~CallRange() { nvtxRangePop(); }
+  CallRange(const CallRange&) = delete;
+  CallRange& operator=(const CallRange&) = delete;
+};
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline size_t align_up(size_t a, size_t b) { return (a + b - 1) / b * b; }

@@ -62,8 +62,10 @@ nif_status launch_grid_bwd(const NifParams& p, const nif_ray* rays, const uint32
                            float* ggrad, cudaStream_t st);
 // dst[i] = src[i] converted to dtype (NIF_F32, NIF_F16 or NIF_BF16).
 nif_status launch_cast(const float* src, int64_t n, void* dst, int dtype, cudaStream_t st);
+// err (nullable): a non-finite updated parameter is recorded as
+// NIF_ERR_NUMERIC with its index as the detail.
 nif_status launch_adam(float* th, float* gr, float* m1, float* m2, int64_t n, float lr, float b1,
                        float b2, float eps, float grad_scale, int step, void* copy, int copy_dtype,
-                       cudaStream_t st);
+                       cudaStream_t st, DevError* err = nullptr);
 
 }  // namespace nif

@@ -33,7 +33,24 @@ struct NifParams {
   int enc;       // NIF_ENC_*
   int R1, F1;    // spherical inner: distance grid cells and latents
   int64_t obj_elems;  // spherical: elements of one object's grid block
+  int64_t n_rays;     // rays the query lists index (0: not known to the call)
+  DevError* err;      // device error word of the call's workspace (nullable)
 };
+
+// A query's inputs are in range: its object below n_objects and, when the
+// call knows the ray count, its ray below n_rays.  check_query records an
+// invalid query as NIF_ERR_BOUNDS (detail: the query index); the kernels then
+// treat it as an empty row and touch nothing it indexes.
+__device__ __forceinline__ bool query_ok(const NifParams& p, uint32_t rid, uint32_t qobj) {
+  return (qobj & 0x7fffffffu) < static_cast<uint32_t>(p.n_obj) &&
+         (p.n_rays == 0 || static_cast<int64_t>(rid) < p.n_rays);
+}
+__device__ __forceinline__ bool check_query(const NifParams& p, const uint32_t* ray_id,
+                                            const uint32_t* qobj, int64_t q) {
+  const bool ok = query_ok(p, ray_id[q], qobj[q]);
+  if (!ok) raise_error(p.err, NIF_ERR_BOUNDS, q);
+  return ok;
+}
 
 // Host: validate a descriptor and derive the device view.
 nif_status make_params(const nif_model_desc* m, NifParams* p);

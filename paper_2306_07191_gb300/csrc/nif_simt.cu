@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(128) k_encode(NifParams p, const nif_ray* rays
                                                 const uint32_t* ray_id, const uint32_t* qobj,
                                                 int64_t nq, TO* out) {
   int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= nq) return;
+  if (q >= nq || !check_query(p, ray_id, qobj, q)) return;
   nif_ray r = load_nif_ray(rays, ray_id[q]);
   TO* row = out + q * p.K;
   encode_query<F, TG>(p, r, qobj[q], [&](int k, float v) {
@@ -483,7 +483,7 @@ __global__ void __launch_bounds__(kFThreads) k_mlp_fwd_f32(NifParams p, const ni
     // encode: one thread per query; rows past the end and padding are zero
     for (int e = tid; e < maxf * kTile; e += kFThreads) A[(e / kTile) * kLq + e % kTile] = 0.f;
     __syncthreads();
-    if (tid < nrow) {
+    if (tid < nrow && check_query(p, ray_id, qobj, q0 + tid)) {
       const int64_t q = q0 + tid;
       const nif_ray r = load_nif_ray(rays, ray_id[q]);
       encode_query<F, TG>(p, r, qobj[q], [&](int k, float v) { A[k * kLq + tid] = v; });
@@ -517,7 +517,8 @@ __global__ void __launch_bounds__(kFThreads) k_mlp_fwd_f32(NifParams p, const ni
       for (int k = 0; k < fan_in; ++k) z = fmaf(__ldg(w + k), in[k * kLq + tid], z);
       const int64_t q = q0 + tid;
       if (logits) logits[q] = z;
-      if (occ_bits && z < 0.f) atomicOr(&occ_bits[ray_id[q] >> 5], 1u << (ray_id[q] & 31));
+      if (occ_bits && z < 0.f && query_ok(p, ray_id[q], qobj[q]))
+        atomicOr(&occ_bits[ray_id[q] >> 5], 1u << (ray_id[q] & 31));
     }
     __syncthreads();
   }
@@ -700,7 +701,7 @@ __global__ void __launch_bounds__(128) k_grid_bwd(NifParams p, const nif_ray* ra
                                                   int64_t nq, const float* dx, int64_t ld,
                                                   float* ggrad) {
   int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= nq) return;
+  if (q >= nq || !check_query(p, ray_id, qobj, q)) return;
   nif_ray r = load_nif_ray(rays, ray_id[q]);
   uint32_t obj = qobj[q] & 0x7fffffffu;
   float bx[6];
@@ -765,7 +766,8 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ th, float* __r
                                               float* __restrict__ m1, float* __restrict__ m2,
                                               int64_t n, float lr, float b1, float b2, float eps,
                                               float inv_scale, float c1, float c2,
-                                              TC* __restrict__ copy) {
+                                              TC* __restrict__ copy, DevError* err,
+                                              int64_t i0) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     float g = gr[i] * inv_scale;
@@ -773,6 +775,7 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ th, float* __r
     float v = b2 * m2[i] + (1.f - b2) * g * g;
     float mh = m * c1, vh = v * c2;
     float t = th[i] - lr * mh / (sqrtf(vh) + eps);
+    if (err && !isfinite(t)) raise_error(err, NIF_ERR_NUMERIC, i0 + i);
     th[i] = t;
     m1[i] = m;
     m2[i] = v;
@@ -806,7 +809,7 @@ __global__ void __launch_bounds__(256) k_adam4(float4* __restrict__ th, float4* 
                                                float4* __restrict__ m1, float4* __restrict__ m2,
                                                int64_t n4, float lr, float b1, float b2, float eps,
                                                float inv_scale, float c1, float c2,
-                                               TC* __restrict__ copy) {
+                                               TC* __restrict__ copy, DevError* err) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
        i += (int64_t)gridDim.x * blockDim.x) {
     float4 t = th[i], g = gr[i], m = m1[i], v = m2[i];
@@ -814,6 +817,9 @@ __global__ void __launch_bounds__(256) k_adam4(float4* __restrict__ th, float4* 
     adam_one(t.y, g.y, m.y, v.y, lr, b1, b2, eps, inv_scale, c1, c2);
     adam_one(t.z, g.z, m.z, v.z, lr, b1, b2, eps, inv_scale, c1, c2);
     adam_one(t.w, g.w, m.w, v.w, lr, b1, b2, eps, inv_scale, c1, c2);
+    if (err && !(isfinite(t.x) && isfinite(t.y) && isfinite(t.z) && isfinite(t.w)))
+      raise_error(err, NIF_ERR_NUMERIC,
+                  4 * i + (!isfinite(t.x) ? 0 : !isfinite(t.y) ? 1 : !isfinite(t.z) ? 2 : 3));
     th[i] = t;
     gr[i] = g;
     m1[i] = m;
@@ -1099,7 +1105,7 @@ nif_status launch_cast(const float* src, int64_t n, void* dst, int dtype, cudaSt
 
 nif_status launch_adam(float* th, float* gr, float* m1, float* m2, int64_t n, float lr, float b1,
                        float b2, float eps, float grad_scale, int step, void* copy, int copy_dtype,
-                       cudaStream_t st) {
+                       cudaStream_t st, DevError* err) {
   if (n == 0) return NIF_OK;
   double c1 = 1.0 / (1.0 - std::pow(static_cast<double>(b1), step));
   double c2 = 1.0 / (1.0 - std::pow(static_cast<double>(b2), step));
@@ -1107,6 +1113,7 @@ nif_status launch_adam(float* th, float* gr, float* m1, float* m2, int64_t n, fl
   float inv = 1.0f / grad_scale;
   auto a16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
   const int csz = copy_dtype == NIF_F32 ? 4 : 2;
+  int64_t i0 = 0;  // index of th[0] in the caller's array (the tail starts past the vector part)
   if (n >= 4 && a16(th) && a16(gr) && a16(m1) && a16(m2) &&
       (copy == nullptr || (reinterpret_cast<uintptr_t>(copy) & (4 * csz - 1)) == 0)) {
     const int64_t n4 = n / 4;
@@ -1114,13 +1121,13 @@ nif_status launch_adam(float* th, float* gr, float* m1, float* m2, int64_t n, fl
     auto v4 = [](float* q) { return reinterpret_cast<float4*>(q); };
     if (copy == nullptr || copy_dtype == NIF_F32)
       k_adam4<float><<<b4, 256, 0, st>>>(v4(th), v4(gr), v4(m1), v4(m2), n4, lr, b1, b2, eps, inv, (float)c1,
-                                         (float)c2, (float*)copy);
+                                         (float)c2, (float*)copy, err);
     else if (copy_dtype == NIF_F16)
       k_adam4<__half><<<b4, 256, 0, st>>>(v4(th), v4(gr), v4(m1), v4(m2), n4, lr, b1, b2, eps, inv, (float)c1,
-                                          (float)c2, (__half*)copy);
+                                          (float)c2, (__half*)copy, err);
     else if (copy_dtype == NIF_BF16)
       k_adam4<__nv_bfloat16><<<b4, 256, 0, st>>>(v4(th), v4(gr), v4(m1), v4(m2), n4, lr, b1, b2, eps, inv,
-                                                 (float)c1, (float)c2, (__nv_bfloat16*)copy);
+                                                 (float)c1, (float)c2, (__nv_bfloat16*)copy, err);
     else
       return fail(NIF_ERR_UNSUPPORTED, "adam: unsupported copy dtype %d", copy_dtype);
     NIF_LAUNCH_CHECK();
@@ -1132,14 +1139,15 @@ nif_status launch_adam(float* th, float* gr, float* m1, float* m2, int64_t n, fl
     m2 += done;
     if (copy) copy = static_cast<char*>(copy) + done * csz;
     n -= done;
+    i0 = done;
     blocks = 1;
   }
   if (copy == nullptr || copy_dtype == NIF_F32)
-    k_adam<float><<<blocks, 256, 0, st>>>(th, gr, m1, m2, n, lr, b1, b2, eps, inv, (float)c1, (float)c2, (float*)copy);
+    k_adam<float><<<blocks, 256, 0, st>>>(th, gr, m1, m2, n, lr, b1, b2, eps, inv, (float)c1, (float)c2, (float*)copy, err, i0);
   else if (copy_dtype == NIF_F16)
-    k_adam<__half><<<blocks, 256, 0, st>>>(th, gr, m1, m2, n, lr, b1, b2, eps, inv, (float)c1, (float)c2, (__half*)copy);
+    k_adam<__half><<<blocks, 256, 0, st>>>(th, gr, m1, m2, n, lr, b1, b2, eps, inv, (float)c1, (float)c2, (__half*)copy, err, i0);
   else if (copy_dtype == NIF_BF16)
-    k_adam<__nv_bfloat16><<<blocks, 256, 0, st>>>(th, gr, m1, m2, n, lr, b1, b2, eps, inv, (float)c1, (float)c2, (__nv_bfloat16*)copy);
+    k_adam<__nv_bfloat16><<<blocks, 256, 0, st>>>(th, gr, m1, m2, n, lr, b1, b2, eps, inv, (float)c1, (float)c2, (__nv_bfloat16*)copy, err, i0);
   else
     return fail(NIF_ERR_UNSUPPORTED, "adam: unsupported copy dtype %d", copy_dtype);
   NIF_LAUNCH_CHECK();

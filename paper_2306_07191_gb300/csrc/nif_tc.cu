@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(kThreads, kOcc)
       const int half = tid >> 7;
       const int64_t q = q0 + qi;
       const float s_in = sc ? 1.0f / sc[0] : 1.0f;
-      if (q < qend) {
+      if (q < qend && check_query(p, ray_id, qobj, q)) {
         const nif_ray r = load_nif_ray(rays, ray_id[q]);
         const uint32_t qo = qobj[q];
         const uint32_t obj = qo & 0x7fffffffu;
@@ -587,9 +587,11 @@ __global__ void __launch_bounds__(kThreads, kOcc)
     if (tid < kM) {
       const int64_t q = q0 + tid;
       if (q < qend) {
-        const float z = zpart[tid] + zpart[kM + tid];
+        // a rejected query's logit is 0 and its ray's bit is left alone
+        const bool ok = query_ok(p, ray_id[q], qobj[q]);
+        const float z = ok ? zpart[tid] + zpart[kM + tid] : 0.f;
         if (logits) logits[q] = z;
-        if (occ && z < 0.f) {
+        if (ok && occ && z < 0.f) {
           const uint32_t rid = ray_id[q];
           atomicOr(&occ[rid >> 5], 1u << (rid & 31));
         }
@@ -746,7 +748,7 @@ __global__ void __launch_bounds__(kThreads, kOcc)
         float x[kSphMaxK];
 #pragma unroll
         for (int k = 0; k < kSphMaxK; ++k) x[k] = 0.f;
-        if (q < qend) {
+        if (q < qend && check_query(p, ray_id, qobj, q)) {
           const nif_ray r = load_nif_ray(rays, ray_id[q]);
           encode_query<F, TG>(p, r, qobj[q], [&](int k, float v) { x[k] = v; });
         }
@@ -761,7 +763,7 @@ __global__ void __launch_bounds__(kThreads, kOcc)
       }
     } else {
       const int64_t q = q0 + qi;
-      const bool live = q < qend;
+      const bool live = q < qend && check_query(p, ray_id, qobj, q);
       QueryPoints pts;
       const TG* tpos = nullptr;
       const TG* tdir = nullptr;
@@ -907,9 +909,11 @@ __global__ void __launch_bounds__(kThreads, kOcc)
     if (tid < kM) {
       const int64_t q = q0 + tid;
       if (q < qend) {
-        const float z = zpart[tid] + zpart[kM + tid];
+        // a rejected query's logit is 0 and its ray's bit is left alone
+        const bool ok = query_ok(p, ray_id[q], qobj[q]);
+        const float z = ok ? zpart[tid] + zpart[kM + tid] : 0.f;
         if (logits) logits[q] = z;
-        if (occ && z < 0.f) {
+        if (ok && occ && z < 0.f) {
           const uint32_t rid = ray_id[q];
           atomicOr(&occ[rid >> 5], 1u << (rid & 31));
         }
@@ -1042,7 +1046,7 @@ __global__ void __launch_bounds__(32 * (kEW + 4), kOcc)
       }
       const int g = find_group(s_pre, p.n_nets, t);
       const int64_t q = goff[g] + (t - s_pre[g]) * kM + qi;
-      const bool live = q < goff[g + 1];
+      const bool live = q < goff[g + 1] && check_query(p, ray_id, qobj, q);
       const uint32_t abase = lane_base + static_cast<uint32_t>(W) + static_cast<uint32_t>(b) * ka;
       QueryPoints pts;
       const __half2* tp = nullptr;
@@ -1116,7 +1120,8 @@ __global__ void __launch_bounds__(32 * (kEW + 4), kOcc)
       if (mlp_sync_or(t < 0)) break;
       const int g = find_group(s_pre, p.n_nets, t);
       const int64_t q = goff[g] + (t - s_pre[g]) * kM + qi;
-      const bool live = q < goff[g + 1];
+      const bool inr = q < goff[g + 1];
+      const bool live = inr && query_ok(p, ray_id[q], qobj[q]);
       if (g != cur_g) {
         const int64_t wbase = static_cast<int64_t>(g) * p.P;
         const int64_t off_out = static_cast<int64_t>(W) * K + static_cast<int64_t>(H - 1) * W * W;
@@ -1188,10 +1193,11 @@ __global__ void __launch_bounds__(32 * (kEW + 4), kOcc)
         if (l + 1 < H) tmem_wait_st();
       }
       if (mlp_sync_or(fail)) break;
-      // ---- logit and visibility of this thread's row
-      if (live) {
-        if (logits) logits[q] = zacc;
-        if (occ && zacc < 0.f) {
+      // ---- logit and visibility of this thread's row (a rejected query's
+      // logit is 0 and its ray's bit is left alone)
+      if (inr) {
+        if (logits) logits[q] = live ? zacc : 0.f;
+        if (live && occ && zacc < 0.f) {
           const uint32_t rid = ray_id[q];
           atomicOr(&occ[rid >> 5], 1u << (rid & 31));
         }

@@ -79,6 +79,7 @@ using namespace nif;
 extern "C" nif_status nif_infer_noalloc(const nif_model_desc* m, const void* d_tlas,
                                         const nif_ray* d_rays, int64_t n,
                                         uint32_t* d_occluded_bits, void* stream) {
+  CallRange nvtx_range("nif_infer_noalloc");
   NifParams p;
   nif_status s = make_params(m, &p);
   if (s != NIF_OK) return s;
@@ -99,6 +100,8 @@ extern "C" nif_status nif_infer_noalloc(const nif_model_desc* m, const void* d_t
                 "nif_infer_noalloc: %lld rays exceed the fixed scratch (at most %lld pairs in "
                 "%zu bytes); use nif_infer with a caller-provided workspace",
                 (long long)n, (long long)L.max_q, noalloc::kNoAllocScratchBytes);
+  p.n_rays = n;
+  p.err = L.err;
   cudaStream_t st = as_stream(stream);
   // the scratch keeps the previous call's contents: clear the error word
   NIF_CUDA_TRY(cudaMemsetAsync(L.err, 0, sizeof(DevError), st));
