@@ -49,6 +49,11 @@ WORKLOADS = {
                 "rays aimed at each object's box, power-law (alpha 1.5) pair counts totalling 8M; one "
                 "3x64 FP16 network and dense 8x2 FP16 grid per object; one persistent grouped launch "
                 "replayed from a CUDA graph"),
+    "mixed": ("mixed NIF/BVH scene: 32 displaced icospheres (radius 1.5) with 10k-500k tris "
+              "(log-uniform) + 12-tri room, 1920x1080 primary hits, 1 point light -> 2,073,600 shadow "
+              "rays; NIF (hashed 16x2 FP16 grids, 3x64 FP16 networks, trained 64 Adam steps x 262,144 "
+              "pairs) only for objects above 100k tris, the exact BVH for the rest and the room; "
+              "compared with the exact BVH over every triangle"),
     "precision": ("precision sweep: small-configuration object (20,480 tris) in the room, 4 point "
                   "lights -> 8,294,400 shadow rays; dense 8x2 FP32 grids (R 4..64), MLP 3x64 trained "
                   "in FP32, inferred in FP32 / BF16 / FP16 / FP8-E4M3"),
@@ -345,7 +350,8 @@ def run_ours(args):
         dist.init_process_group("nccl")
     log = (lambda *a: print(*a, file=sys.stderr, flush=True)) if rank == 0 else (lambda *a: None)
     from paper_2306_07191_gb300.pipeline import (PaperEncodingConfig, PaperEncodingPipeline,
-                                                 full_scale_config, small_object_precision_config)
+                                                 full_scale_config, mixed_scene_config,
+                                                 small_object_precision_config)
     pipe_cls = RoomPipeline
     if args.workload == "paper":
         cfg = PaperEncodingConfig()
@@ -354,6 +360,8 @@ def run_ours(args):
         cfg = full_scale_config()
     elif args.workload == "precision":
         cfg = small_object_precision_config()
+    elif args.workload == "mixed":
+        cfg = mixed_scene_config()
     else:
         cfg = RoomConfig()
     if args.small:
@@ -366,6 +374,8 @@ def run_ours(args):
         cfg.schedule = L.NIF_SCHED_SERIAL
     if args.schedule:
         cfg.schedule = {"serial": L.NIF_SCHED_SERIAL, "pipelined": L.NIF_SCHED_PIPELINED}[args.schedule]
+    if args.exact_cast:
+        cfg.exact_cast = args.exact_cast
     pipe = pipe_cls(cfg, log=log)
     train_s = pipe.train()
     n_par = pipe.param_count()
@@ -449,6 +459,10 @@ def run_ours(args):
                 return statistics.mean(e[a].elapsed_time(e[b]) for e in parts)
             subs = {"room_cast_ms": m(0, 1), "frontend_nearest_ms": m(1, 2), "fused_round1_ms": m(2, 3),
                     "frontend_rest_ms": m(3, 4), "fused_round2_ms": m(4, 5)}
+            if cfg.exact_cast != "first":
+                # the exact cast runs beside or after the NIF calls (the last
+                # interval then holds it); the first is the mask clear
+                subs["mask_clear_ms"] = subs.pop("room_cast_ms")
             subs["frontend_ms"] = subs["frontend_nearest_ms"] + subs["frontend_rest_ms"]
             subs["fused_ms"] = subs["fused_round1_ms"] + subs["fused_round2_ms"]
         return tot, subs
@@ -497,7 +511,9 @@ def run_ours(args):
         "data": "synthetic",
         "config": {"workload": WORKLOADS[args.workload], "rays": n, "queries": nq,
                    "queries_round1": nq1, "queries_all_pairs": nq_all, "triangles": pipe.n_tris,
-                   "objects": cfg.n_obj, "l2": "flushed (256 MB write) before every timed step",
+                   "objects": cfg.n_obj, "nif_objects": pipe.n_obj, "triangles_nif": pipe.n_tris_nif,
+                   "l2": "flushed (256 MB write) before every timed step",
+                   "exact_cast": cfg.exact_cast,
                    "fused_schedule": SCHED_NAME[pipe.forward_models()[0][0].cfg.schedule],
                    "fused_ctas_per_sm": pipe.forward_models()[0][0].cfg.ctas_per_sm, "autotune_ms": tune_ms,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -519,8 +535,9 @@ def run_ours(args):
                      "alg_bytes_per_query": alg_bytes, "flops_per_query": flops_q},
         "e2e": {"value": world * n / (ems * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": n * 32, "d2h_bytes_per_step": bits.numel() * 4},
-        # per step: room cast, 3 + 3 front-end kernels, 2 fused forwards
-        "gpu_launches": 9 * args.steps,
+        # per step: the exact cast, 3 + 3 front-end kernels, one fused
+        # forward per network model and round
+        "gpu_launches": (7 + 2 * len(pipe.forward_models())) * args.steps,
         "clocks": clocks,
     }
     if sweep is not None:
@@ -657,6 +674,9 @@ def main():
     ap.add_argument("--schedule", default="", choices=["", "serial", "pipelined"],
                     help="fix the fused kernel's schedule (skips the autotuner)")
     ap.add_argument("--workload", default="room", choices=sorted(WORKLOADS))
+    ap.add_argument("--exact-cast", choices=("first", "after", "overlap"), default=None,
+                    help="when the non-NIF geometry is cast: before the NIF query (default), after it, "
+                         "or beside it on a second stream")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

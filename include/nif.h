@@ -214,6 +214,19 @@ nif_status bvh_info(const void* d_bvh, int64_t* n_nodes, int64_t* n_prims, int32
 nif_status bvh_cast_shadow(const void* d_bvh, const nif_ray* d_rays, int64_t n,
                            uint32_t* d_occluded_bits, void* stream);
 
+/* The same cast, OR-ing the occluded bits into d_occluded_bits (atomically,
+ * one atomic per 32 rays with a hit) instead of overwriting the words.  Rays
+ * whose bit is already set are not traversed (they are occluded whatever the
+ * cast finds).  It may run after a NIF query into the same mask, or on
+ * another stream concurrently with one (Sec. 4.1 combines the exact answer
+ * for non-NIF geometry and the NIF answer by OR); the caller initialises the
+ * mask, e.g. with nif_bits_clear. */
+nif_status bvh_cast_shadow_or(const void* d_bvh, const nif_ray* d_rays, int64_t n,
+                              uint32_t* d_occluded_bits, void* stream);
+
+/* Zero the ceil(n/32) words of an occlusion mask (cudaMemsetAsync). */
+nif_status nif_bits_clear(uint32_t* d_bits, int64_t n, void* stream);
+
 /* Closest-hit cast (primary visibility, Sec. 5 "Primary Visibility
  * Computation"): d_t[i] = nearest hit t or +inf, d_prim[i] = that triangle's
  * input index (smallest on a tie) or -1.  Either output may be NULL. */

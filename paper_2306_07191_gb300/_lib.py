@@ -71,6 +71,8 @@ SIGNATURES = {
     "bvh_build_boxes": (i32, [P, i64, P, size_t, P, size_t, P]),
     "bvh_info": (i32, [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32), P]),
     "bvh_cast_shadow": (i32, [P, P, i64, P, P]),
+    "bvh_cast_shadow_or": (i32, [P, P, i64, P, P]),
+    "nif_bits_clear": (i32, [P, i64, P]),
     "bvh_cast_closest": (i32, [P, P, i64, P, P, P]),
     "bvh_cast_pairs": (i32, [P, P, P, P, i64, P, P]),
     "nif_shadow_rays": (i32, [P, P, i64, i32, P, i32, f32, P, P]),

@@ -591,6 +591,7 @@ __device__ __forceinline__ bool traverse(const char* bvh, const Header& H, const
   return hit;
 }
 
+template <bool kOr>
 __global__ void __launch_bounds__(128) k_cast_shadow(const char* bvh, const nif_ray* rays, int64_t n,
                                                      uint32_t* bits) {
   __shared__ Header H;
@@ -598,14 +599,24 @@ __global__ void __launch_bounds__(128) k_cast_shadow(const char* bvh, const nif_
   __syncthreads();
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   bool occ = false;
-  if (i < n) {
+  // OR-ing: a ray whose bit is already set is occluded whatever this cast
+  // finds, so it is not traversed
+  const bool known = kOr && i < n && ((bits[i >> 5] >> (i & 31)) & 1u);
+  if (i < n && !known) {
     RayF r = load_ray(rays, i);
     float t;
     int32_t id;
     occ = traverse<kAny>(bvh, H, r, 0, t, id);
   }
   uint32_t word = __ballot_sync(0xffffffffu, occ);
-  if ((threadIdx.x & 31) == 0 && i < n) bits[i >> 5] = word;
+  if ((threadIdx.x & 31) == 0 && i < n) {
+    if constexpr (kOr) {
+      // other work (a concurrent NIF query) may OR into the same words
+      if (word) atomicOr(&bits[i >> 5], word);
+    } else {
+      bits[i >> 5] = word;
+    }
+  }
 }
 
 __global__ void __launch_bounds__(128) k_cast_closest(const char* bvh, const nif_ray* rays,
@@ -717,16 +728,40 @@ nif_status bvh_info(const void* d_bvh, int64_t* n_nodes, int64_t* n_prims, int32
   return NIF_OK;
 }
 
+static nif_status cast_shadow(const char* name, bool or_into, const void* d_bvh, const nif_ray* d_rays,
+                              int64_t n, uint32_t* d_occluded_bits, void* stream) {
+  NIF_CHECK_ARG(n >= 0, "%s: negative n", name);
+  if (n == 0) return NIF_OK;
+  NIF_CHECK_ARG(d_bvh && d_rays && d_occluded_bits, "%s: null pointer", name);
+  NIF_CHECK_ARG((reinterpret_cast<uintptr_t>(d_rays) & 15) == 0, "%s: rays not 16-byte aligned", name);
+  if (or_into)
+    bvh::k_cast_shadow<true><<<ceil_div(n, 128), 128, 0, as_stream(stream)>>>((const char*)d_bvh, d_rays, n,
+                                                                              d_occluded_bits);
+  else
+    bvh::k_cast_shadow<false><<<ceil_div(n, 128), 128, 0, as_stream(stream)>>>((const char*)d_bvh, d_rays, n,
+                                                                               d_occluded_bits);
+  NIF_LAUNCH_CHECK();
+  return NIF_OK;
+}
+
 nif_status bvh_cast_shadow(const void* d_bvh, const nif_ray* d_rays, int64_t n,
                            uint32_t* d_occluded_bits, void* stream) {
   CallRange nvtx_range("bvh_cast_shadow");
-  NIF_CHECK_ARG(n >= 0, "bvh_cast_shadow: negative n");
+  return cast_shadow("bvh_cast_shadow", false, d_bvh, d_rays, n, d_occluded_bits, stream);
+}
+
+nif_status bvh_cast_shadow_or(const void* d_bvh, const nif_ray* d_rays, int64_t n,
+                              uint32_t* d_occluded_bits, void* stream) {
+  CallRange nvtx_range("bvh_cast_shadow_or");
+  return cast_shadow("bvh_cast_shadow_or", true, d_bvh, d_rays, n, d_occluded_bits, stream);
+}
+
+nif_status nif_bits_clear(uint32_t* d_bits, int64_t n, void* stream) {
+  CallRange nvtx_range("nif_bits_clear");
+  NIF_CHECK_ARG(n >= 0, "nif_bits_clear: negative n");
   if (n == 0) return NIF_OK;
-  NIF_CHECK_ARG(d_bvh && d_rays && d_occluded_bits, "bvh_cast_shadow: null pointer");
-  NIF_CHECK_ARG((reinterpret_cast<uintptr_t>(d_rays) & 15) == 0, "bvh_cast_shadow: rays not 16-byte aligned");
-  bvh::k_cast_shadow<<<ceil_div(n, 128), 128, 0, as_stream(stream)>>>((const char*)d_bvh, d_rays, n,
-                                                                        d_occluded_bits);
-  NIF_LAUNCH_CHECK();
+  NIF_CHECK_ARG(d_bits, "nif_bits_clear: null pointer");
+  NIF_CUDA_TRY(cudaMemsetAsync(d_bits, 0, static_cast<size_t>(ceil_div(n, 32)) * 4, as_stream(stream)));
   return NIF_OK;
 }
 

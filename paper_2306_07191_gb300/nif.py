@@ -39,6 +39,12 @@ def bits_to_bool(bits: torch.Tensor, n: int) -> torch.Tensor:
     return (((w[:, None] >> sh[None, :]) & 1).reshape(-1)[:n]).bool()
 
 
+def clear_bits(bits: torch.Tensor, n: int, stream=None) -> torch.Tensor:
+    """Zero an occlusion mask of n rays on the stream (nif_bits_clear)."""
+    L.call("nif_bits_clear", _ptr(bits), n, _stream(stream))
+    return bits
+
+
 def empty_bits(n: int, device="cuda") -> torch.Tensor:
     return torch.zeros((n + 31) // 32, dtype=torch.int32, device=device)
 
@@ -75,10 +81,14 @@ class BVH:
                _stream())
         return {"nodes": nn.value, "prims": npr.value, "depth": dep.value}
 
-    def cast_shadow(self, rays: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+    def cast_shadow(self, rays: torch.Tensor, out: torch.Tensor | None = None, stream=None,
+                    or_into: bool = False):
+        """Any-hit cast into an occlusion mask; or_into ORs the bits into
+        `out` (which may be written concurrently) instead of overwriting."""
         n = int(rays.shape[0])
         bits = out if out is not None else empty_bits(n, rays.device)
-        L.call("bvh_cast_shadow", _ptr(self.buf), _ptr(rays), n, _ptr(bits), _stream(stream))
+        L.call("bvh_cast_shadow_or" if or_into else "bvh_cast_shadow", _ptr(self.buf), _ptr(rays), n,
+               _ptr(bits), _stream(stream))
         return bits
 
     def cast_closest(self, rays: torch.Tensor, stream=None):

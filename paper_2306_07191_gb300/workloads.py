@@ -65,7 +65,7 @@ class RoomScene:
 
 def room_scene(n_obj: int = 64, n: int = 28, width: int = 1920, height: int = 1080,
                seed: int = 7, jitter_seed: int | None = None, layout: str = "random",
-               n_lights: int = 1) -> RoomScene:
+               n_lights: int = 1, tri_min: int = 10_000, tri_max: int = 500_000) -> RoomScene:
     """Objects in a 12-triangle room [-20,20]^3 seen by a pinhole camera at
     (0,0,19) looking at the origin.
 
@@ -75,6 +75,9 @@ def room_scene(n_obj: int = 64, n: int = 28, width: int = 1920, height: int = 10
                       triangles) scaled to the box [-4,4]^3 at the origin.
     layout "lattice": a jittered 10 x 6 x 8 lattice (spacing 4) of displaced
                       icospheres of frequency n (480 objects for n_obj=480).
+    layout "mixed":   n_obj displaced icospheres of radius 1.5 with triangle
+                      counts log-uniform in [tri_min, tri_max] (frequency
+                      round(sqrt(T / 20))), centres uniform in [-10,10]^3.
     Point lights are drawn outside every object box; area-light samples are
     drawn separately (area_light_samples)."""
     rng = np.random.default_rng(seed)
@@ -89,6 +92,11 @@ def room_scene(n_obj: int = 64, n: int = 28, width: int = 1920, height: int = 10
         centres = (cells - (np.array([gx, gy, gz]) - 1) / 2.0) * 4.0
         centres += rng.uniform(-0.6, 0.6, size=centres.shape)
         meshes = [synth.displaced_icosphere(n, rng, centre=c) for c in centres]
+    elif layout == "mixed":
+        tris = np.exp(rng.uniform(np.log(tri_min), np.log(tri_max), size=n_obj))
+        freqs = np.maximum(1, np.round(np.sqrt(tris / 20.0))).astype(int)
+        centres = rng.uniform(-10.0, 10.0, size=(n_obj, 3))
+        meshes = [synth.displaced_icosphere(int(f), rng, radius=1.5, centre=c) for f, c in zip(freqs, centres)]
     else:
         centres = rng.uniform(-10.0, 10.0, size=(n_obj, 3))
         meshes = [synth.displaced_icosphere(n, rng, centre=c) for c in centres]

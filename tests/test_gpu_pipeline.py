@@ -34,6 +34,17 @@ def test_room_query_step_equals_nif_infer():
     assert torch.equal(a, b)
     n1, n = p.last_query_counts()
     assert 0 < n1 <= n
+    # the exact cast after the NIF query or beside it on a second stream
+    # (OR-ing into the mask) gives the same mask as casting it first
+    assert p.cfg.exact_cast == "first"
+    for mode in ("after", "overlap"):
+        p.cfg.exact_cast = mode
+        for step in (p.query_step, p.nif_query):
+            c = nif.empty_bits(p.n_rays)
+            c.fill_(-1)  # cleared first
+            step(c)
+            torch.cuda.synchronize()
+            assert torch.equal(a, c), (mode, step)
 
 
 def test_paper_pipeline_two_rounds_equal_every_pair_per_class():
@@ -78,3 +89,41 @@ def test_padded_inner_network_gives_the_same_logits():
     torch.cuda.synchronize()
     assert g[2] - g[1] > 1000
     assert float((z48 - z64).abs().max()) <= 1e-5 * max(1.0, float(z48.abs().max()))
+
+
+def test_mixed_scene_splits_geometry_between_nif_and_exact_cast():
+    """Sec. 6.6's mixed scene: objects above 100K triangles go to NIF, the
+    rest stay in the exact cast with the room.  With each NIF pair answered
+    exactly (the pair's own triangles, bvh_cast_pairs) instead of by its
+    network, the split query equals the exact cast over every triangle, bit
+    for bit; the learned query is the same calls as nif_infer."""
+    cfg = _small(pipeline.mixed_scene_config())
+    cfg.n_obj = 32
+    p = pipeline.RoomPipeline(cfg, log=lambda *a: None)
+    sc = p.ws.scene
+    big = sc.obj_tri_range[:, 1] > cfg.nif_min_tris
+    assert 0 < p.n_obj == int(big.sum()) < 32
+    assert p.n_tris_nif == int(sc.obj_tri_range[big, 1].sum())
+    assert p.room_bvh.info()["prims"] == p.n_tris - p.n_tris_nif
+    truth = nif.empty_bits(p.n_rays)
+    p.bvh.cast_shadow(p.rays, out=truth)
+    split = nif.empty_bits(p.n_rays)
+    p.room_bvh.cast_shadow(p.rays, out=split)
+    rid, qo, goff, count = p.model.frontend(p.rays, tlas=p.tlas)
+    torch.cuda.synchronize()
+    p.model.check()
+    nq = int(count.item())
+    assert nq > 1000
+    hit = p.bvh.cast_pairs(p.rays, rid[:nq].contiguous(), qo[:nq].contiguous())
+    occ = nif.bits_to_bool(split, p.n_rays)
+    occ[rid[:nq].long()[hit.bool()]] = True
+    assert torch.equal(occ, nif.bits_to_bool(truth, p.n_rays))
+    p.train()
+    a = nif.empty_bits(p.n_rays)
+    b = nif.empty_bits(p.n_rays)
+    p.query_step(a)
+    p.nif_query(b)
+    p.check()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert p.disagreement()["all"] < 0.05
