@@ -46,6 +46,7 @@ def lib():
         L.oracle_mt_hit.restype = ctypes.c_int
         L.oracle_brute_cast.argtypes = [P, P, i64, P, i64, P, P, P, ctypes.c_int]
         L.oracle_brute_pairs.argtypes = [P, P, P, P, P, P, P, i64, P, ctypes.c_int]
+        L.oracle_brute_pairs_closest.argtypes = [P, P, P, P, P, P, P, i64, P, P, ctypes.c_int]
         L.oracle_bvh_build.argtypes = [P, P, i64]
         L.oracle_bvh_build.restype = P
         L.oracle_bvh_free.argtypes = [P]
@@ -104,6 +105,24 @@ def brute_pairs(verts, tris, obj_first, obj_count, rays, ray_id, obj, nthreads=N
     lib().oracle_brute_pairs(_p(v), _p(t), _p(of), _p(oc), _p(r), _p(rid), _p(ob), len(rid),
                              _p(hit), nthreads or threads())
     return hit
+
+
+def brute_pairs_closest(verts, tris, obj_first, obj_count, rays, ray_id, obj, nthreads=None):
+    """Per (ray, object) pair: the closest hit of that object's triangles
+    inside the ray's segment.  Returns (t float32 [nq] (+inf if none), prim
+    int32 [nq] (-1 if none))."""
+    v = np.ascontiguousarray(verts, dtype=np.float32)
+    t = np.ascontiguousarray(tris, dtype=np.int32)
+    of = np.ascontiguousarray(obj_first, dtype=np.int64)
+    oc = np.ascontiguousarray(obj_count, dtype=np.int64)
+    r = np.ascontiguousarray(rays, dtype=np.float32)
+    rid = np.ascontiguousarray(ray_id, dtype=np.int32)
+    ob = np.ascontiguousarray(obj, dtype=np.int32)
+    th = np.zeros(len(rid), np.float32)
+    pr = np.zeros(len(rid), np.int32)
+    lib().oracle_brute_pairs_closest(_p(v), _p(t), _p(of), _p(oc), _p(r), _p(rid), _p(ob), len(rid),
+                                     _p(th), _p(pr), nthreads or threads())
+    return th, pr
 
 
 class OracleBVH:

@@ -261,6 +261,35 @@ void oracle_brute_pairs(const float* verts, const int32_t* tris, const int64_t* 
   });
 }
 
+// Closest hit restricted to (ray, object) pairs: t_hit[q] = the smallest t of
+// a triangle of object obj[q] hit strictly inside the segment of ray
+// ray_id[q] (+inf if none), prim[q] = that triangle's index (smallest on a
+// tie) or -1.
+void oracle_brute_pairs_closest(const float* verts, const int32_t* tris, const int64_t* obj_first,
+                                const int64_t* obj_count, const float* rays, const int32_t* ray_id,
+                                const int32_t* obj, int64_t n_pairs, float* t_hit, int32_t* prim,
+                                int nthreads) {
+  parallel_for(n_pairs, nthreads, [&](int64_t a, int64_t b) {
+    for (int64_t q = a; q < b; ++q) {
+      Ray r = load_ray(rays + 8 * (int64_t)ray_id[q]);
+      int64_t s = obj_first[obj[q]], c = obj_count[obj[q]];
+      float best = std::numeric_limits<float>::infinity();
+      int32_t bp = -1;
+      for (int64_t k = s; k < s + c; ++k) {
+        float t;
+        if (mt_hit(r, vert(verts, tris[3 * k]), vert(verts, tris[3 * k + 1]),
+                   vert(verts, tris[3 * k + 2]), &t) &&
+            t < best) {
+          best = t;
+          bp = (int32_t)k;
+        }
+      }
+      t_hit[q] = best;
+      prim[q] = bp;
+    }
+  });
+}
+
 void* oracle_bvh_build(const float* verts, const int32_t* tris, int64_t n_tris) {
   Bvh* bvh = new Bvh();
   std::vector<Box> tb(n_tris);
