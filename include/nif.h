@@ -101,10 +101,19 @@ typedef int32_t nif_status;
  * The network input is x = [entry levels | exit levels | direction levels],
  * level-major, n_features per level: K = 3 * n_levels * n_features.
  *
- * Network (Sec. 5): bias-free, n_hidden layers of `width` units, one output
- * logit.  d_weights = [n_nets][P] in mlp_dtype with, per net, row-major
- * W_1 [width][K], W_2..W_H [width][width], w_out [1][width];
- * P = nif_weight_count().  mlp_dtype NIF_F32 runs on CUDA cores;
+ * Network (Sec. 5): bias-free, n_hidden layers of `width` units, O output
+ * rows (O = n_outputs, 0 meaning 1).  d_weights = [n_nets][P] in mlp_dtype
+ * with, per net, row-major W_1 [width][K], W_2..W_H [width][width],
+ * W_out [O][width]; P = nif_weight_count().  Output 0 is the occupancy logit
+ * z (occluded iff z < 0).  With O > 1 the other outputs are linear
+ * regressions of surface properties at the hit (Sec. 3.2: the network may
+ * output auxiliary data at the hit point; Sec. 6.1, Fig. 5: for primary
+ * rays, the shading normal and the depth): the primary-ray layout is O = 5,
+ * [z | n_x n_y n_z | delta], n the unit normal facing the ray and delta the
+ * hit's position in the pair's AABB segment, t_hit = t_in + delta
+ * (t_out - t_in).  Logit outputs are then [nq][O].  O > 1 runs on the FP32
+ * path and on the 16-bit tensor-core path with FP16 grids and the serial
+ * schedule (not E4M3, not the pipelined schedule).  mlp_dtype NIF_F32 runs on CUDA cores;
  * NIF_F16/NIF_BF16/NIF_E4M3 run on tcgen05 tensor cores with FP32
  * accumulation (width 64 or 128, K a multiple of 16 (32 for E4M3)).
  * NIF_E4M3 also needs d_scales = [n_nets][n_hidden+1][2] FP32 pairs
@@ -134,6 +143,7 @@ typedef struct nif_model_desc {
   int32_t encoding;      /* NIF_ENC_* (below) */
   int32_t res_1d;        /* NIF_ENC_SPHERICAL_INNER: cells of the distance grid */
   int32_t n_features_1d; /* NIF_ENC_SPHERICAL_INNER: latents per distance cell */
+  int32_t n_outputs;     /* output rows O, 0 or 1 = the occupancy logit only; at most 8 */
 } nif_model_desc;
 
 /* Encodings of a query (the network input x):
@@ -238,6 +248,14 @@ nif_status bvh_cast_closest(const void* d_bvh, const nif_ray* d_rays, int64_t n,
  * d_ray_id[q], else 0.  Needs a BVH built with tags. */
 nif_status bvh_cast_pairs(const void* d_bvh, const nif_ray* d_rays, const uint32_t* d_ray_id,
                           const uint32_t* d_obj, int64_t nq, uint8_t* d_hit, void* stream);
+
+/* Per-pair closest hit (the targets of primary-ray training, Sec. 6.1): d_t[q]
+ * = the nearest hit t of the triangles tagged d_obj[q] (bit 31 ignored)
+ * inside the segment of ray d_ray_id[q], or +inf; d_prim[q] = that
+ * triangle's input index (smallest on a tie) or -1. */
+nif_status bvh_cast_pairs_closest(const void* d_bvh, const nif_ray* d_rays,
+                                  const uint32_t* d_ray_id, const uint32_t* d_obj, int64_t nq,
+                                  float* d_t, int32_t* d_prim, void* stream);
 
 /* Shadow rays from primary hits (Sec. 6.5: rays from the shading points to
  * a light): ray i*spp+s starts at o_i + t_i d_i of camera ray i and points at
@@ -380,7 +398,7 @@ typedef struct nif_optim_desc {
 } nif_optim_desc;
 
 /* Forward for training (FP32 weights and grids on the CUDA cores): per query
- * the logit d_z[q] and the saved activations d_saved (nif_saved_size bytes,
+ * the outputs d_z[q][O] (the logit d_z[q] when O = 1) and the saved activations d_saved (nif_saved_size bytes,
  * FP32, feature-major [K + n_hidden*width][nq]: x then every hidden layer). */
 size_t nif_saved_size(const nif_model_desc* m, int64_t nq);
 nif_status nif_fwd_train(const nif_model_desc* m, const nif_ray* d_rays,
@@ -393,8 +411,18 @@ nif_status nif_fwd_train(const nif_model_desc* m, const nif_ray* d_rays,
 nif_status nif_loss(const float* d_z, const uint8_t* d_label, int64_t nq, float loss_scale,
                     float* d_dz, float* d_loss, void* stream);
 
-/* MLP backward: accumulates dL/dW into d_w_grad ([n_nets*P] FP32, +=) and
- * writes dL/dx into d_dx, FP32 feature-major [K][nq]. */
+/* The loss of a network with O = n_outputs > 1 outputs d_z [nq][O] and
+ * targets d_aux [nq][O-1] (read on hit pairs, y = 0):
+ *   L = (1/B) sum_q [(sigmoid(z_q0) - y_q)^2 + (1 - y_q) sum_k (z_qk - aux_q,k-1)^2],
+ * the regression terms counting on hit pairs only.  d_dz [nq][O] receives
+ * dL/dz times loss_scale, d_loss (nullable) L. */
+nif_status nif_loss_aux(const float* d_z, const uint8_t* d_label, const float* d_aux, int64_t nq,
+                        int32_t n_outputs, float loss_scale, float* d_dz, float* d_loss,
+                        void* stream);
+
+/* MLP backward: from d_dz [nq][O] accumulates dL/dW into d_w_grad
+ * ([n_nets*P] FP32, +=) and writes dL/dx into d_dx, FP32 feature-major
+ * [K][nq]. */
 nif_status nif_mlp_bwd(const nif_model_desc* m, const uint32_t* d_qobj,
                        const int64_t* d_group_off, int64_t nq, const void* d_saved,
                        const float* d_dz, float* d_w_grad, float* d_dx, void* stream);
@@ -423,6 +451,32 @@ nif_status nif_train_step(nif_model_desc* m, nif_optim_desc* o, const nif_ray* d
                           const uint32_t* d_ray_id, const uint32_t* d_qobj,
                           const int64_t* d_group_off, const uint8_t* d_label, int64_t nq,
                           float* d_loss, void* d_ws, size_t ws_bytes, void* stream);
+
+/* The same step for a network with O > 1 outputs, with the loss of
+ * nif_loss_aux and its targets d_aux [nq][O-1] (nif_train_step refuses
+ * O > 1; d_aux NULL here is the same as nif_train_step). */
+nif_status nif_train_step_aux(nif_model_desc* m, nif_optim_desc* o, const nif_ray* d_rays,
+                              const uint32_t* d_ray_id, const uint32_t* d_qobj,
+                              const int64_t* d_group_off, const uint8_t* d_label,
+                              const float* d_aux, int64_t nq, float* d_loss, void* d_ws,
+                              size_t ws_bytes, void* stream);
+
+/* Closest NIF hit per ray for primary rays (Sec. 6.1, Fig. 5), from the
+ * outputs d_out [nq][O] (O >= 5, the primary-ray layout above) of a grouped
+ * query list (nq = d_group_off[n_nets], at most nq_max).  Per pair with
+ * z_0 < 0: t = t_in + clamp(delta, 0, 1) (t_out - t_in) in FP32 with each
+ * operation rounded alone (t_in, t_out from the FP32 slab test of the front
+ * end); per ray the smallest t, ties to the smallest query index.
+ * d_t [n_rays] is in/out: where the ray's NIF hit is nearer than d_t[i] (the
+ * caller's exact cast of the other geometry, or +inf), d_t[i] becomes that t,
+ * d_normal[i] (FP32 [n_rays][3]) the winner's (z_1, z_2, z_3) normalised and
+ * d_winner[i] (int32, nullable) its query index; elsewhere d_normal and
+ * d_winner are left alone.  d_key is scratch of n_rays uint64. */
+nif_status nif_primary_resolve(const nif_model_desc* m, const nif_ray* d_rays, int64_t n_rays,
+                               const uint32_t* d_ray_id, const uint32_t* d_qobj,
+                               const int64_t* d_group_off, int64_t nq_max, const float* d_out,
+                               uint64_t* d_key, float* d_t, float* d_normal, int32_t* d_winner,
+                               void* stream);
 
 /* Checkpoint and resume of online training (Sec. 4.2 trains while rendering;
  * resuming after an interruption needs the optimiser state).  The state is

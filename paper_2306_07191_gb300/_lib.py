@@ -44,6 +44,7 @@ class ModelDesc(ctypes.Structure):
         ("d_weights", P), ("d_scales", P),
         ("tile_m", i32), ("ctas_per_sm", i32), ("schedule", i32),
         ("encoding", i32), ("res_1d", i32), ("n_features_1d", i32),
+        ("n_outputs", i32),
     ]
 
 
@@ -75,6 +76,7 @@ SIGNATURES = {
     "nif_bits_clear": (i32, [P, i64, P]),
     "bvh_cast_closest": (i32, [P, P, i64, P, P, P]),
     "bvh_cast_pairs": (i32, [P, P, P, P, i64, P, P]),
+    "bvh_cast_pairs_closest": (i32, [P, P, P, P, i64, P, P, P]),
     "nif_shadow_rays": (i32, [P, P, i64, i32, P, i32, f32, P, P]),
     "nif_workspace_size": (size_t, [MD, i64, i64]),
     "nif_train_workspace_size": (size_t, [MD, i64]),
@@ -92,10 +94,13 @@ SIGNATURES = {
     "nif_saved_size": (size_t, [MD, i64]),
     "nif_fwd_train": (i32, [MD, P, P, P, P, i64, P, P, P]),
     "nif_loss": (i32, [P, P, i64, f32, P, P, P]),
+    "nif_loss_aux": (i32, [P, P, P, i64, i32, f32, P, P, P]),
     "nif_mlp_bwd": (i32, [MD, P, P, i64, P, P, P, P, P]),
     "nif_grid_bwd": (i32, [MD, P, P, P, i64, P, P, P]),
     "nif_adam": (i32, [P, P, P, P, i64, f32, f32, f32, f32, f32, i32, P, i32, P]),
     "nif_train_step": (i32, [MD, OD, P, P, P, P, P, i64, P, P, size_t, P]),
+    "nif_train_step_aux": (i32, [MD, OD, P, P, P, P, P, P, i64, P, P, size_t, P]),
+    "nif_primary_resolve": (i32, [MD, P, i64, P, P, P, i64, P, P, P, P, P, P]),
     "nif_fill_uniform": (i32, [P, i64, ctypes.c_uint64, f32, P]),
     "nif_infer_noalloc": (i32, [MD, P, P, i64, P, P]),
     "nif_wait_selftest": (i32, [P, size_t, i64, P]),

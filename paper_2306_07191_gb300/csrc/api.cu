@@ -104,9 +104,11 @@ int64_t weight_count(const nif_model_desc* m) {
       m->n_features < 1)
     return -1;
   if (spherical(m) && spherical_elems(m) < 0) return -1;
+  if (m->n_outputs < 0 || m->n_outputs > 8) return -1;
+  const int64_t O = m->n_outputs > 1 ? m->n_outputs : 1;
   int64_t K = input_width(m);
-  if (m->n_hidden == 0) return K;
-  return K * m->width + (int64_t)(m->n_hidden - 1) * m->width * m->width + m->width;
+  if (m->n_hidden == 0) return O * K;
+  return K * m->width + (int64_t)(m->n_hidden - 1) * m->width * m->width + O * m->width;
 }
 
 nif_status make_params(const nif_model_desc* m, NifParams* p) {
@@ -133,6 +135,9 @@ nif_status make_params(const nif_model_desc* m, NifParams* p) {
   NIF_CHECK_ARG(m->width >= 1 && m->width <= 256, "width must be 1..256");
   NIF_CHECK_ARG(m->act == NIF_ACT_RELU || m->act == NIF_ACT_LEAKY, "bad activation");
   NIF_CHECK_ARG(m->mlp_dtype >= NIF_F32 && m->mlp_dtype <= NIF_E4M3, "bad mlp dtype");
+  NIF_CHECK_ARG(m->n_outputs >= 0 && m->n_outputs <= 8, "n_outputs must be 0..8");
+  NIF_CHECK_ARG(m->n_outputs <= ((m->width + 3) & ~3), "n_outputs %d exceeds the width rounded up to 4",
+                m->n_outputs);
   int want_nets = m->net_mode == NIF_NETS_SINGLE ? 1
                   : m->net_mode == NIF_NETS_CLASS ? 2
                   : m->net_mode == NIF_NETS_OBJECT ? m->n_objects : -1;
@@ -166,6 +171,7 @@ nif_status make_params(const nif_model_desc* m, NifParams* p) {
   p->n_nets = m->n_nets;
   p->weights = m->d_weights;
   p->P = weight_count(m);
+  p->O = m->n_outputs > 1 ? m->n_outputs : 1;
   p->scales = m->mlp_dtype == NIF_E4M3 ? m->d_scales : nullptr;
   NIF_CHECK_ARG(m->schedule >= NIF_SCHED_AUTO && m->schedule <= NIF_SCHED_PIPELINED,
                 "bad schedule %d", m->schedule);
@@ -247,9 +253,9 @@ static TrainWs train_layout(const NifParams& p, void* base, int64_t nq) {
   size_t o = kErrBytes;
   w.err = reinterpret_cast<DevError*>(b);
   w.z = reinterpret_cast<float*>(b + o);
-  o += align_up(nq * 4, 256);
+  o += align_up(nq * p.O * 4, 256);
   w.dz = reinterpret_cast<float*>(b + o);
-  o += align_up(nq * 4, 256);
+  o += align_up(nq * p.O * 4, 256);
   w.saved = reinterpret_cast<float*>(b + o);
   o += align_up((size_t)(p.K + p.n_hidden * p.width) * nq * 4, 256);
   w.dx = reinterpret_cast<float*>(b + o);
@@ -481,6 +487,14 @@ nif_status nif_loss(const float* d_z, const uint8_t* d_label, int64_t nq, float 
   return launch_loss(d_z, d_label, nq, loss_scale, d_dz, d_loss, as_stream(stream));
 }
 
+nif_status nif_loss_aux(const float* d_z, const uint8_t* d_label, const float* d_aux, int64_t nq,
+                        int32_t n_outputs, float loss_scale, float* d_dz, float* d_loss, void* stream) {
+  NIF_CHECK_ARG(nq >= 0, "nif_loss_aux: negative nq");
+  NIF_CHECK_ARG(n_outputs >= 2 && n_outputs <= 8, "nif_loss_aux: n_outputs must be 2..8");
+  NIF_CHECK_ARG(nq == 0 || (d_z && d_label && d_aux && d_dz), "nif_loss_aux: null pointer");
+  return launch_loss_aux(d_z, d_label, d_aux, nq, n_outputs, loss_scale, d_dz, d_loss, as_stream(stream));
+}
+
 nif_status nif_mlp_bwd(const nif_model_desc* m, const uint32_t* d_qobj, const int64_t* d_group_off,
                        int64_t nq, const void* d_saved, const float* d_dz, float* d_w_grad, float* d_dx,
                        void* stream) {
@@ -528,9 +542,19 @@ nif_status nif_train_step(nif_model_desc* m, nif_optim_desc* o, const nif_ray* d
                           const uint8_t* d_label, int64_t nq, float* d_loss, void* d_ws, size_t ws_bytes,
                           void* stream) {
   CallRange nvtx_range("nif_train_step");
+  return nif_train_step_aux(m, o, d_rays, d_ray_id, d_qobj, d_group_off, d_label, nullptr, nq, d_loss,
+                            d_ws, ws_bytes, stream);
+}
+
+nif_status nif_train_step_aux(nif_model_desc* m, nif_optim_desc* o, const nif_ray* d_rays,
+                              const uint32_t* d_ray_id, const uint32_t* d_qobj,
+                              const int64_t* d_group_off, const uint8_t* d_label, const float* d_aux,
+                              int64_t nq, float* d_loss, void* d_ws, size_t ws_bytes, void* stream) {
+  CallRange nvtx_range("nif_train_step_aux");
   NifParams p;
   nif_status s = make_params(m, &p);
   if (s != NIF_OK) return s;
+  NIF_CHECK_ARG(p.O == 1 || d_aux, "nif_train_step: a network with %d outputs needs targets (nif_train_step_aux)", p.O);
   NIF_CHECK_ARG(o != nullptr, "nif_train_step: null optimiser");
   NIF_CHECK_ARG(o->d_w_master && o->d_w_grad && o->d_w_m && o->d_w_v, "nif_train_step: null weight state");
   NIF_CHECK_ARG(o->d_g_master && o->d_g_grad && o->d_g_m && o->d_g_v, "nif_train_step: null grid state");
@@ -550,7 +574,8 @@ nif_status nif_train_step(nif_model_desc* m, nif_optim_desc* o, const nif_ray* d
   cudaStream_t st = as_stream(stream);
   s = launch_fwd_f32(pm, d_rays, d_ray_id, d_qobj, d_group_off, nq, nullptr, w.z, w.saved, nq, st);
   if (s != NIF_OK) return s;
-  s = launch_loss(w.z, d_label, nq, o->loss_scale, w.dz, d_loss, st);
+  s = p.O == 1 ? launch_loss(w.z, d_label, nq, o->loss_scale, w.dz, d_loss, st)
+               : launch_loss_aux(w.z, d_label, d_aux, nq, p.O, o->loss_scale, w.dz, d_loss, st);
   if (s != NIF_OK) return s;
   s = launch_bwd_f32(pm, d_group_off, nq, w.saved, w.dz, o->d_w_grad, w.dx, st);
   if (s != NIF_OK) return s;
@@ -569,6 +594,27 @@ nif_status nif_train_step(nif_model_desc* m, nif_optim_desc* o, const nif_ray* d
   if (s != NIF_OK) return s;
   o->step = step;
   return NIF_OK;
+}
+
+nif_status nif_primary_resolve(const nif_model_desc* m, const nif_ray* d_rays, int64_t n_rays,
+                               const uint32_t* d_ray_id, const uint32_t* d_qobj,
+                               const int64_t* d_group_off, int64_t nq_max, const float* d_out,
+                               uint64_t* d_key, float* d_t, float* d_normal, int32_t* d_winner,
+                               void* stream) {
+  CallRange nvtx_range("nif_primary_resolve");
+  NifParams p;
+  nif_status s = make_params(m, &p);
+  if (s != NIF_OK) return s;
+  NIF_CHECK_ARG(p.O >= 5, "nif_primary_resolve: the primary-ray layout has 5 outputs (n_outputs %d)", p.O);
+  NIF_CHECK_ARG(n_rays >= 0 && nq_max >= 0, "nif_primary_resolve: negative size");
+  NIF_CHECK_ARG(nq_max < (int64_t(1) << 32), "nif_primary_resolve: at most 2^32 - 1 queries");
+  if (n_rays == 0) return NIF_OK;
+  NIF_CHECK_ARG(d_rays && d_ray_id && d_qobj && d_group_off && d_out && d_key && d_t && d_normal,
+                "nif_primary_resolve: null pointer");
+  p.n_rays = n_rays;
+  return launch_primary_resolve(p, d_rays, n_rays, d_ray_id, d_qobj, d_group_off, nq_max, d_out,
+                                reinterpret_cast<unsigned long long*>(d_key), d_t, d_normal, d_winner,
+                                as_stream(stream));
 }
 
 // ------------------------------------------------------------ checkpoint

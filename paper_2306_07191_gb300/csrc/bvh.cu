@@ -526,7 +526,7 @@ __device__ __forceinline__ bool mt(const RayF& r, float4 p0, float4 p1, float4 p
   return true;
 }
 
-enum Mode { kAny = 0, kClosest = 1, kPairs = 2 };
+enum Mode { kAny = 0, kClosest = 1, kPairs = 2, kPairsClosest = 3 };
 
 // Returns true on a hit; for kClosest also the nearest t and prim id.
 template <int kMode>
@@ -571,11 +571,13 @@ __device__ __forceinline__ bool traverse(const char* bvh, const Header& H, const
       for (int32_t k = first; k < first + count; ++k) {
         float4 p0 = __ldg(prims + 3 * (int64_t)k), p1 = __ldg(prims + 3 * (int64_t)k + 1),
                p2 = __ldg(prims + 3 * (int64_t)k + 2);
-        if (kMode == kPairs && __float_as_int(p2.z) != want_tag) continue;
+        constexpr bool kTagged = kMode == kPairs || kMode == kPairsClosest;
+        constexpr bool kNearest = kMode == kClosest || kMode == kPairsClosest;
+        if (kTagged && __float_as_int(p2.z) != want_tag) continue;
         float t;
         if (mt(r, p0, p1, p2, tmax, t)) {
           hit = true;
-          if (kMode != kClosest) return true;
+          if (!kNearest) return true;
           int32_t id = __float_as_int(p2.y);
           if (t < best_t || (t == best_t && id < best_id)) {
             best_t = t;
@@ -583,7 +585,8 @@ __device__ __forceinline__ bool traverse(const char* bvh, const Header& H, const
           }
         }
       }
-      if (kMode == kClosest && hit) tmax = fminf(r.tmax, nextafterf(best_t, INFINITY));
+      if ((kMode == kClosest || kMode == kPairsClosest) && hit)
+        tmax = fminf(r.tmax, nextafterf(best_t, INFINITY));
     }
     if (sp == 0) break;
     ref = stack[--sp];
@@ -646,6 +649,22 @@ __global__ void __launch_bounds__(128) k_cast_pairs(const char* bvh, const nif_r
   float t;
   int32_t id;
   hit[q] = traverse<kPairs>(bvh, H, r, static_cast<int32_t>(obj[q] & 0x7fffffffu), t, id) ? 1 : 0;
+}
+
+__global__ void __launch_bounds__(128) k_cast_pairs_closest(const char* bvh, const nif_ray* rays,
+                                                            const uint32_t* ray_id, const uint32_t* obj,
+                                                            int64_t nq, float* tout, int32_t* pout) {
+  __shared__ Header H;
+  if (threadIdx.x == 0) H = *reinterpret_cast<const Header*>(bvh);
+  __syncthreads();
+  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  RayF r = load_ray(rays, ray_id[q]);
+  float t;
+  int32_t id;
+  traverse<kPairsClosest>(bvh, H, r, static_cast<int32_t>(obj[q] & 0x7fffffffu), t, id);
+  tout[q] = t;
+  pout[q] = id;
 }
 
 __global__ void k_shadow_rays(const nif_ray* cam, const float* tcam, int64_t n, int spp,
@@ -786,6 +805,20 @@ nif_status bvh_cast_pairs(const void* d_bvh, const nif_ray* d_rays, const uint32
   NIF_CHECK_ARG(d_bvh && d_rays && d_ray_id && d_obj && d_hit, "bvh_cast_pairs: null pointer");
   bvh::k_cast_pairs<<<ceil_div(nq, 128), 128, 0, as_stream(stream)>>>((const char*)d_bvh, d_rays,
                                                                         d_ray_id, d_obj, nq, d_hit);
+  NIF_LAUNCH_CHECK();
+  return NIF_OK;
+}
+
+nif_status bvh_cast_pairs_closest(const void* d_bvh, const nif_ray* d_rays,
+                                  const uint32_t* d_ray_id, const uint32_t* d_obj, int64_t nq,
+                                  float* d_t, int32_t* d_prim, void* stream) {
+  CallRange nvtx_range("bvh_cast_pairs_closest");
+  NIF_CHECK_ARG(nq >= 0, "bvh_cast_pairs_closest: negative n");
+  if (nq == 0) return NIF_OK;
+  NIF_CHECK_ARG(d_bvh && d_rays && d_ray_id && d_obj && d_t && d_prim,
+                "bvh_cast_pairs_closest: null pointer");
+  bvh::k_cast_pairs_closest<<<ceil_div(nq, 128), 128, 0, as_stream(stream)>>>(
+      (const char*)d_bvh, d_rays, d_ray_id, d_obj, nq, d_t, d_prim);
   NIF_LAUNCH_CHECK();
   return NIF_OK;
 }

@@ -55,6 +55,14 @@ nif_status launch_wait_selftest(DevError* err, long long limit_cycles, cudaStrea
 
 nif_status launch_loss(const float* z, const uint8_t* label, int64_t nq, float scale, float* dz,
                        float* loss, cudaStream_t st);
+nif_status launch_loss_aux(const float* z, const uint8_t* label, const float* aux, int64_t nq, int n_out,
+                           float scale, float* dz, float* loss, cudaStream_t st);
+// Closest NIF hit per ray from O-output pairs (z_0 < 0: a hit at
+// t_in + clamp(z_4, 0, 1) (t_out - t_in)); writes where nearer than t[i].
+nif_status launch_primary_resolve(const NifParams& p, const nif_ray* rays, int64_t n_rays,
+                                  const uint32_t* ray_id, const uint32_t* qobj, const int64_t* goff,
+                                  int64_t nq_max, const float* out, unsigned long long* key, float* t,
+                                  float* normal, int32_t* winner, cudaStream_t st);
 nif_status launch_bwd_f32(const NifParams& p, const int64_t* goff, int64_t nq, const float* saved,
                           const float* dz, float* wgrad, float* dx, cudaStream_t st);
 nif_status launch_grid_bwd(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,

@@ -28,6 +28,7 @@ struct NifParams {
   int mlp_dtype, net_mode, n_nets;
   const void* weights;
   int64_t P;  // weights per network
+  int O;      // output rows (1: the occupancy logit)
   const float* scales;
   int schedule;  // NIF_SCHED_* of the tensor-core forward
   int enc;       // NIF_ENC_*

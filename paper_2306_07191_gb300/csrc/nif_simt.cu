@@ -513,11 +513,16 @@ __global__ void __launch_bounds__(kFThreads) k_mlp_fwd_f32(NifParams p, const ni
       out = tmp;
     }
     if (tid < nrow) {
-      float z = 0.f;
-      for (int k = 0; k < fan_in; ++k) z = fmaf(__ldg(w + k), in[k * kLq + tid], z);
+      // output rows: z_0 the occupancy logit, z_1.. the regressions
       const int64_t q = q0 + tid;
-      if (logits) logits[q] = z;
-      if (occ_bits && z < 0.f && query_ok(p, ray_id[q], qobj[q]))
+      float z0 = 0.f;
+      for (int o = 0; o < p.O; ++o) {
+        float z = 0.f;
+        for (int k = 0; k < fan_in; ++k) z = fmaf(__ldg(w + static_cast<int64_t>(o) * fan_in + k), in[k * kLq + tid], z);
+        if (logits) logits[q * p.O + o] = z;
+        if (o == 0) z0 = z;
+      }
+      if (occ_bits && z0 < 0.f && query_ok(p, ray_id[q], qobj[q]))
         atomicOr(&occ_bits[ray_id[q] >> 5], 1u << (ray_id[q] & 31));
     }
     __syncthreads();
@@ -536,6 +541,32 @@ __global__ void k_loss(const float* z, const uint8_t* label, int64_t nq, float s
     float e = s - y;
     part += e * e;
     dz[q] = scale * 2.0f * invB * e * s * (1.0f - s);
+  }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if (loss && (threadIdx.x & 31) == 0) atomicAdd(loss, part * invB);
+}
+
+// Loss of an O-output network: the occupancy term on z_0 plus, on hit pairs
+// (y = 0), squared errors of z_1..z_{O-1} against the targets aux[q][O-1].
+__global__ void k_loss_aux(const float* z, const uint8_t* label, const float* aux, int64_t nq,
+                           int O, float scale, float* dz, float* loss) {
+  float part = 0.f;
+  const float invB = 1.0f / static_cast<float>(nq);
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const float* zq = z + q * O;
+    float* dq = dz + q * O;
+    const float s = 1.0f / (1.0f + expf(-zq[0]));
+    const float y = label[q] ? 1.0f : 0.0f;
+    const float e = s - y;
+    part += e * e;
+    dq[0] = scale * 2.0f * invB * e * s * (1.0f - s);
+    const float hit = 1.0f - y;
+    for (int k = 1; k < O; ++k) {
+      const float r = hit > 0.f ? zq[k] - aux[q * (O - 1) + (k - 1)] : 0.f;
+      part += r * r;
+      dq[k] = scale * 2.0f * invB * r;
+    }
   }
   for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
   if (loss && (threadIdx.x & 31) == 0) atomicAdd(loss, part * invB);
@@ -600,19 +631,27 @@ __global__ void __launch_bounds__(kFThreads) k_mlp_bwd_f32(NifParams p, const in
       woff[H] = o;
     }
     const int fan_last = H > 0 ? W : K;
+    const int O = p.O;
     const float* hl = Hs + (H > 0 ? off_h(H - 1) : 0) * kLq;
-    // output layer: dw_out[j] = sum_q dz_q h_H[j][q]; dh[j][q] = dz_q w_out[j]
-    float* dzs = DA;  // row 0 of DA as scratch for dz
-    if (tid < kTile) dzs[tid] = tid < nrow ? dz[q0 + tid] : 0.f;
+    // output layer: dW_out[o][j] = sum_q dz_qo h_H[j][q];
+    // dh[j][q] = sum_o dz_qo W_out[o][j]
+    float* dzs = DA;  // rows 0..O-1 of DA as scratch for dz (O <= 8 <= W4)
+    for (int e = tid; e < O * kTile; e += kFThreads) {
+      const int o = e / kTile, c = e % kTile;
+      dzs[o * kLq + c] = c < nrow ? dz[(q0 + c) * O + o] : 0.f;
+    }
     __syncthreads();
-    for (int j = tid; j < fan_last; j += kFThreads) {
+    for (int e = tid; e < O * fan_last; e += kFThreads) {
+      const int o = e / fan_last, j = e % fan_last;
       float acc = 0.f;
-      for (int c = 0; c < nrow; ++c) acc = fmaf(dzs[c], hl[j * kLq + c], acc);
-      atomicAdd(&gw[woff[H] + j], acc);
+      for (int c = 0; c < nrow; ++c) acc = fmaf(dzs[o * kLq + c], hl[j * kLq + c], acc);
+      atomicAdd(&gw[woff[H] + e], acc);
     }
     for (int e = tid; e < fan_last * kTile; e += kFThreads) {
       const int j = e / kTile, c = e % kTile;
-      DH[j * kLq + c] = dzs[c] * __ldg(w + woff[H] + j);
+      float acc = 0.f;
+      for (int o = 0; o < O; ++o) acc = fmaf(dzs[o * kLq + c], __ldg(w + woff[H] + static_cast<int64_t>(o) * fan_last + j), acc);
+      DH[j * kLq + c] = acc;
     }
     __syncthreads();
     for (int l = H - 1; l >= 0; --l) {
@@ -1056,6 +1095,89 @@ nif_status launch_loss(const float* z, const uint8_t* label, int64_t nq, float s
   if (nq == 0) return NIF_OK;
   int blocks = static_cast<int>(std::min<int64_t>(ceil_div(nq, 256), sm_count() * 4));
   k_loss<<<blocks, 256, 0, st>>>(z, label, nq, scale, dz, loss);
+  NIF_LAUNCH_CHECK();
+  return NIF_OK;
+}
+
+nif_status launch_loss_aux(const float* z, const uint8_t* label, const float* aux, int64_t nq, int n_out,
+                           float scale, float* dz, float* loss, cudaStream_t st) {
+  if (loss) NIF_CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(float), st));
+  if (nq == 0) return NIF_OK;
+  int blocks = static_cast<int>(std::min<int64_t>(ceil_div(nq, 256), sm_count() * 8));
+  k_loss_aux<<<blocks, 256, 0, st>>>(z, label, aux, nq, n_out, scale, dz, loss);
+  NIF_LAUNCH_CHECK();
+  return NIF_OK;
+}
+
+// ------------------------------------------------- primary-ray resolution
+// A float's bits turned into an unsigned key with the float's order.
+__device__ __forceinline__ uint32_t order_key(float t) {
+  const uint32_t u = __float_as_uint(t);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float order_key_float(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// Per hit pair (z_0 < 0): its hit parameter in FP32 from the exact slab test,
+// each operation rounded alone, and an atomic minimum of (t, query index) on
+// the ray's key.
+__global__ void __launch_bounds__(256) k_primary_min(NifParams p, const nif_ray* rays,
+                                                     const uint32_t* ray_id, const uint32_t* qobj,
+                                                     const int64_t* goff, int64_t nq_max,
+                                                     const float* out, unsigned long long* key) {
+  const int64_t nq = goff[p.n_nets] < nq_max ? goff[p.n_nets] : nq_max;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const float* zq = out + q * p.O;
+    if (!(zq[0] < 0.f)) continue;
+    const uint32_t rid = ray_id[q], qo = qobj[q];
+    if (!query_ok(p, rid, qo)) continue;
+    const nif_ray r = load_nif_ray(rays, rid);
+    const float o[3] = {r.ox, r.oy, r.oz}, d[3] = {r.dx, r.dy, r.dz};
+    float box[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) box[k] = __ldg(p.aabb + 6 * static_cast<size_t>(qo & 0x7fffffffu) + k);
+    float tin, tout, entry;
+    exact_slab(o, d, r.tmin, r.tmax, box, tin, tout, entry);
+    const float dc = fminf(fmaxf(zq[4], 0.f), 1.f);  // a NaN delta clamps to 0
+    const float t = __fadd_rn(tin, __fmul_rn(dc, __fsub_rn(tout, tin)));
+    const unsigned long long k = (static_cast<unsigned long long>(order_key(t)) << 32) |
+                                 static_cast<unsigned long long>(static_cast<uint32_t>(q));
+    atomicMin(&key[rid], k);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_primary_write(int64_t n, const unsigned long long* key,
+                                                       const float* out, int n_out, float* t,
+                                                       float* normal, int32_t* winner) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const unsigned long long k = key[i];
+  if (k == ~0ull) return;
+  const float th = order_key_float(static_cast<uint32_t>(k >> 32));
+  if (!(th < t[i])) return;  // the exact cast is as near or nearer
+  const int64_t q = static_cast<int64_t>(k & 0xffffffffull);
+  const float* zq = out + q * n_out;
+  const float nx = zq[1], ny = zq[2], nz = zq[3];
+  const float len2 = __fadd_rn(__fadd_rn(__fmul_rn(nx, nx), __fmul_rn(ny, ny)), __fmul_rn(nz, nz));
+  const float inv = len2 > 0.f ? 1.0f / sqrtf(len2) : 0.f;
+  t[i] = th;
+  normal[3 * i] = nx * inv;
+  normal[3 * i + 1] = ny * inv;
+  normal[3 * i + 2] = nz * inv;
+  if (winner) winner[i] = static_cast<int32_t>(q);
+}
+
+nif_status launch_primary_resolve(const NifParams& p, const nif_ray* rays, int64_t n_rays,
+                                  const uint32_t* ray_id, const uint32_t* qobj, const int64_t* goff,
+                                  int64_t nq_max, const float* out, unsigned long long* key, float* t,
+                                  float* normal, int32_t* winner, cudaStream_t st) {
+  NIF_CUDA_TRY(cudaMemsetAsync(key, 0xff, static_cast<size_t>(n_rays) * sizeof(unsigned long long), st));
+  if (nq_max == 0) return NIF_OK;
+  k_primary_min<<<sm_count() * 8, 256, 0, st>>>(p, rays, ray_id, qobj, goff, nq_max, out, key);
+  NIF_LAUNCH_CHECK();
+  k_primary_write<<<ceil_div(n_rays, 256), 256, 0, st>>>(n_rays, key, out, p.O, t, normal, winner);
   NIF_LAUNCH_CHECK();
   return NIF_OK;
 }

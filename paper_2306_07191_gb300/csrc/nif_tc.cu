@@ -620,7 +620,7 @@ struct LayoutTm {
   }
 };
 
-__host__ __device__ inline LayoutTm make_layout_tm(int Kp, int W, int H, int n_nets) {
+__host__ __device__ inline LayoutTm make_layout_tm(int Kp, int W, int H, int n_nets, int n_out = 1) {
   LayoutTm L{};
   L.w0_off = 0;
   L.w1_bytes = W * Kp * 2;
@@ -628,9 +628,9 @@ __host__ __device__ inline LayoutTm make_layout_tm(int Kp, int W, int H, int n_n
   uint32_t o = L.w1_bytes + static_cast<uint32_t>(H > 1 ? H - 1 : 0) * L.wl_bytes;
   o = (o + 15) / 16 * 16;
   L.wout_off = o;
-  o += W * 4;
+  o += n_out * W * 4;
   L.zpart_off = o;
-  o += 2 * kM * 4;
+  o += 2 * n_out * kM * 4;
   L.pre_off = o;
   o += (n_nets + 1) * 8;
   L.total = o;
@@ -643,7 +643,11 @@ __host__ __device__ inline uint32_t tm_cols(int Kp, int W) {
   return need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
 }
 
-template <int F, typename TG, int DT, int kOcc>
+// kMulti: an output layer of p.O <= kMaxOut rows (the primary-ray outputs)
+// instead of the single occupancy logit.
+constexpr int kMaxOut = 8;
+
+template <int F, typename TG, int DT, int kOcc, bool kMulti = false>
 __global__ void __launch_bounds__(kThreads, kOcc)
     k_fused_tm(const __grid_constant__ NifParams p, const nif_ray* __restrict__ rays,
                const uint32_t* __restrict__ ray_id, const uint32_t* __restrict__ qobj,
@@ -662,7 +666,8 @@ __global__ void __launch_bounds__(kThreads, kOcc)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int W = p.width, H = p.n_hidden, K = p.K;
-  const LayoutTm L = make_layout_tm(Kp, W, H, p.n_nets);
+  const int nout = kMulti ? p.O : 1;
+  const LayoutTm L = make_layout_tm(Kp, W, H, p.n_nets, nout);
   float* wout = reinterpret_cast<float*>(smem + L.wout_off);
   float* zpart = reinterpret_cast<float*>(smem + L.zpart_off);
   int64_t* s_pre = reinterpret_cast<int64_t*>(smem + L.pre_off);
@@ -735,7 +740,7 @@ __global__ void __launch_bounds__(kThreads, kOcc)
         }
         fence_proxy_async();
       }
-      for (int e = tid; e < W; e += kThreads) wout[e] = O::load(p.weights, wbase + off_out + e);
+      for (int e = tid; e < W * nout; e += kThreads) wout[e] = O::load(p.weights, wbase + off_out + e);
       cur_g = g;
     }
 
@@ -861,7 +866,9 @@ __global__ void __launch_bounds__(kThreads, kOcc)
     __syncthreads();
 
     // ---- step a3: hidden layers, A from TMEM, B from shared memory
-    float zacc = 0.f;
+    float zacc[kMulti ? kMaxOut : 1];
+#pragma unroll
+    for (int o = 0; o < (kMulti ? kMaxOut : 1); ++o) zacc[o] = 0.f;
     for (int l = 0; l < H; ++l) {
       const int kdim = l == 0 ? Kp : W;
       if (tid == 0) {
@@ -891,9 +898,15 @@ __global__ void __launch_bounds__(kThreads, kOcc)
 #pragma unroll
           for (int i = 0; i < 8; ++i) pk[i] = pack2(v[2 * i], v[2 * i + 1]);
           tmem_st8(lane_base + act_col + static_cast<uint32_t>((ecol0 + c0) / 2), pk);
+        } else if constexpr (kMulti) {
+#pragma unroll
+          for (int o = 0; o < kMaxOut; ++o)
+            if (o < nout)
+#pragma unroll
+              for (int i = 0; i < 16; ++i) zacc[o] += v[i] * wout[o * W + ecol0 + c0 + i];
         } else {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) zacc += v[i] * wout[ecol0 + c0 + i];
+          for (int i = 0; i < 16; ++i) zacc[0] += v[i] * wout[ecol0 + c0 + i];
         }
       }
       if (l + 1 < H) tmem_wait_st();
@@ -903,16 +916,24 @@ __global__ void __launch_bounds__(kThreads, kOcc)
     }
     if (s_abort) break;
 
-    // ---- step a4: logit and visibility
-    zpart[half * kM + qi] = zacc;
+    // ---- step a4: logit (and the other outputs) and visibility
+#pragma unroll
+    for (int o = 0; o < (kMulti ? kMaxOut : 1); ++o)
+      if (o < nout) zpart[(half * nout + o) * kM + qi] = zacc[o];
     __syncthreads();
     if (tid < kM) {
       const int64_t q = q0 + tid;
       if (q < qend) {
-        // a rejected query's logit is 0 and its ray's bit is left alone
+        // a rejected query's outputs are 0 and its ray's bit is left alone
         const bool ok = query_ok(p, ray_id[q], qobj[q]);
-        const float z = ok ? zpart[tid] + zpart[kM + tid] : 0.f;
-        if (logits) logits[q] = z;
+        const float z = ok ? zpart[tid] + zpart[nout * kM + tid] : 0.f;
+        if constexpr (kMulti) {
+          if (logits)
+            for (int o = 0; o < nout; ++o)
+              logits[q * nout + o] = ok ? zpart[o * kM + tid] + zpart[(nout + o) * kM + tid] : 0.f;
+        } else {
+          if (logits) logits[q] = z;
+        }
         if (ok && occ && z < 0.f) {
           const uint32_t rid = ray_id[q];
           atomicOr(&occ[rid >> 5], 1u << (rid & 31));
@@ -1313,7 +1334,7 @@ static nif_status launch_tm(const NifParams& p, const nif_ray* rays, const uint3
                             uint32_t* occ, float* logits, DevError* err, uint32_t* ctr,
                             cudaStream_t st) {
   const int Kp = (p.K + 15) / 16 * 16;
-  tc::LayoutTm L = tc::make_layout_tm(Kp, p.width, p.n_hidden, p.n_nets);
+  tc::LayoutTm L = tc::make_layout_tm(Kp, p.width, p.n_hidden, p.n_nets, p.O);
   size_t sh = L.total + 1024;
   tc::WeightMaps wm;
   const int use_tma = make_weight_maps(p, 2, Kp, &wm) && tc_weights_by_tma() ? 1 : 0;
@@ -1326,7 +1347,12 @@ static nif_status launch_tm(const NifParams& p, const nif_ray* rays, const uint3
   nif_status s;
   // the spherical encodings do not use F at compile time: take the F = 2 forms
   const int fsel = p.enc != NIF_ENC_MULTIRES ? 2 : p.F;
-  if (p.grid_dtype == NIF_F16) {
+  if (p.O > 1) {
+    // several outputs (primary rays): FP16 grids, an even F of 2
+    if (p.grid_dtype != NIF_F16 || fsel != 2)
+      return fail(NIF_ERR_UNSUPPORTED, "tensor-core path with %d outputs: FP16 grids and 2 features", p.O);
+    s = per_sm >= 4 ? go(tc::k_fused_tm<2, __half, DT, 4, true>) : go(tc::k_fused_tm<2, __half, DT, 2, true>);
+  } else if (p.grid_dtype == NIF_F16) {
     if (fsel == 2)
       s = per_sm >= 4 ? go(tc::k_fused_tm<2, __half, DT, 4>)
           : per_sm == 3 ? go(tc::k_fused_tm<2, __half, DT, 3>) : go(tc::k_fused_tm<2, __half, DT, 2>);
@@ -1437,9 +1463,12 @@ nif_status launch_fwd_tc(const NifParams& p, const nif_ray* rays, const uint32_t
     return fail(NIF_ERR_ARG, "spherical encodings: one class per model (net_mode single or object)");
   if (tile_m != 0 && tile_m != 128)
     return fail(NIF_ERR_UNSUPPORTED, "tensor-core path: tile_m %d (128 supported)", tile_m);
+  if (p.O > 1 && (p.mlp_dtype == NIF_E4M3 || !tm_supported(p) || p.schedule == NIF_SCHED_PIPELINED))
+    return fail(NIF_ERR_UNSUPPORTED,
+                "tensor-core path with %d outputs: 16-bit operands and the serial schedule", p.O);
   uint32_t* ctr = tile_counter(err);
   if (ctr) NIF_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t), st));
-  if (ws_supported(p)) {
+  if (ws_supported(p) && p.O == 1) {
     const int Kp16 = (p.K + 15) / 16 * 16;
     const bool pick = p.schedule == NIF_SCHED_PIPELINED ||
                       (p.schedule == NIF_SCHED_AUTO && tc::ws_cols(Kp16, p.width) <= 128);

@@ -105,6 +105,16 @@ class BVH:
                _stream(stream))
         return hit
 
+    def cast_pairs_closest(self, rays, ray_id, obj, stream=None):
+        """Per pair: the nearest hit t of the pair's object (+inf) and the
+        triangle (-1)."""
+        nq = int(ray_id.shape[0])
+        t = torch.empty(nq, dtype=torch.float32, device=rays.device)
+        prim = torch.empty(nq, dtype=torch.int32, device=rays.device)
+        L.call("bvh_cast_pairs_closest", _ptr(self.buf), _ptr(rays), _ptr(ray_id), _ptr(obj), nq,
+               _ptr(t), _ptr(prim), _stream(stream))
+        return t, prim
+
 
 def shadow_rays(camera: torch.Tensor, t: torch.Tensor, light: torch.Tensor, spp: int = 1,
                 per_ray: bool = False, tmin: float = 1e-3, stream=None) -> torch.Tensor:
@@ -135,6 +145,9 @@ class NifConfig:
     encoding: int = L.NIF_ENC_MULTIRES
     res_1d: int = 0
     n_features_1d: int = 0
+    # output rows: 1 = the occupancy logit; 5 = the primary-ray outputs
+    # [z | normal | delta] (Sec. 3.2, Sec. 6.1)
+    n_outputs: int = 1
 
     @property
     def n_levels(self):
@@ -160,6 +173,7 @@ class NifConfig:
         d.encoding = self.encoding
         d.res_1d = self.res_1d
         d.n_features_1d = self.n_features_1d
+        d.n_outputs = self.n_outputs
         return d
 
 
@@ -253,7 +267,11 @@ class NifModel:
 
     def infer_queries(self, rays, ray_id, qobj, goff, nq_max: int, bits=None, logits=True,
                       stream=None):
-        z = torch.empty(max(nq_max, 1), dtype=torch.float32, device=rays.device) if logits else None
+        """Outputs of a grouped query list: logits [nq_max] (or [nq_max, O]
+        with O > 1 outputs), occlusion bits OR-ed into `bits`."""
+        O = self.cfg.n_outputs
+        shape = (max(nq_max, 1),) if O == 1 else (max(nq_max, 1), O)
+        z = torch.empty(shape, dtype=torch.float32, device=rays.device) if logits else None
         ws = self.workspace(0)
         d = self.desc()
         L.call("nif_infer_queries", ctypes.byref(d), _ptr(rays), int(rays.shape[0]), _ptr(ray_id),
@@ -330,15 +348,40 @@ class Trainer:
     def load(self, path: str):
         self.load_state_bytes(np.fromfile(path, dtype=np.uint8))
 
-    def step(self, rays, ray_id, qobj, goff, label, nq: int, stream=None):
+    def step(self, rays, ray_id, qobj, goff, label, nq: int, stream=None, aux=None):
+        """One nif_train_step (or nif_train_step_aux with the targets aux
+        [nq, O-1] of an O-output network)."""
         d = self.model.desc()
         need = L.lib.nif_train_workspace_size(ctypes.byref(d), nq)
         if self._ws is None or self._ws.numel() < need:
             self._ws = torch.zeros(need, dtype=torch.uint8, device=rays.device)
-        L.call("nif_train_step", ctypes.byref(d), ctypes.byref(self.o), _ptr(rays), _ptr(ray_id),
-               _ptr(qobj), _ptr(goff), _ptr(label), nq, _ptr(self.loss), _ptr(self._ws),
-               self._ws.numel(), _stream(stream))
+        if aux is None:
+            L.call("nif_train_step", ctypes.byref(d), ctypes.byref(self.o), _ptr(rays), _ptr(ray_id),
+                   _ptr(qobj), _ptr(goff), _ptr(label), nq, _ptr(self.loss), _ptr(self._ws),
+                   self._ws.numel(), _stream(stream))
+        else:
+            L.call("nif_train_step_aux", ctypes.byref(d), ctypes.byref(self.o), _ptr(rays), _ptr(ray_id),
+                   _ptr(qobj), _ptr(goff), _ptr(label), _ptr(aux), nq, _ptr(self.loss), _ptr(self._ws),
+                   self._ws.numel(), _stream(stream))
         return self.loss
+
+
+def primary_resolve(model: NifModel, rays, ray_id, qobj, goff, nq_max: int, out, t=None, normal=None,
+                    winner=None, key=None, stream=None):
+    """Closest NIF hit per ray from the O >= 5 outputs `out` [nq_max, O] of a
+    grouped query list (nif_primary_resolve).  t (in/out, +inf when None)
+    holds the exact cast's t of the other geometry; where a NIF hit is
+    nearer, t, normal [n, 3] and winner (query index) are written."""
+    n = int(rays.shape[0])
+    dev = rays.device
+    t = t if t is not None else torch.full((n,), float("inf"), dtype=torch.float32, device=dev)
+    normal = normal if normal is not None else torch.zeros((n, 3), dtype=torch.float32, device=dev)
+    winner = winner if winner is not None else torch.full((n,), -1, dtype=torch.int32, device=dev)
+    key = key if key is not None else torch.empty(n, dtype=torch.int64, device=dev)
+    d = model.desc()
+    L.call("nif_primary_resolve", ctypes.byref(d), _ptr(rays), n, _ptr(ray_id), _ptr(qobj), _ptr(goff),
+           nq_max, _ptr(out), _ptr(key), _ptr(t), _ptr(normal), _ptr(winner), _stream(stream))
+    return t, normal, winner
 
 
 def _f32_view(model: NifModel, grids: torch.Tensor, weights: torch.Tensor) -> NifModel:

@@ -312,14 +312,15 @@ def xavier_uniform(rng: np.random.Generator, fan_out: int, fan_in: int) -> np.nd
     return rng.uniform(-a, a, size=(fan_out, fan_in)).astype(np.float32)
 
 
-def mlp_init(rng: np.random.Generator, n_in: int, width: int, n_hidden: int) -> list[np.ndarray]:
-    """Bias-free MLP n_in -> width (x n_hidden) -> 1, Xavier-uniform."""
+def mlp_init(rng: np.random.Generator, n_in: int, width: int, n_hidden: int,
+             n_out: int = 1) -> list[np.ndarray]:
+    """Bias-free MLP n_in -> width (x n_hidden) -> n_out, Xavier-uniform."""
     mats = []
     fan_in = n_in
     for _ in range(n_hidden):
         mats.append(xavier_uniform(rng, width, fan_in))
         fan_in = width
-    mats.append(xavier_uniform(rng, 1, fan_in))
+    mats.append(xavier_uniform(rng, n_out, fan_in))
     return mats
 
 
@@ -332,13 +333,14 @@ def flatten_mlp(mats: list[np.ndarray]) -> np.ndarray:
     return np.concatenate([m.reshape(-1) for m in mats]).astype(np.float32)
 
 
-def unflatten_mlp(flat: np.ndarray, n_in: int, width: int, n_hidden: int) -> list[np.ndarray]:
+def unflatten_mlp(flat: np.ndarray, n_in: int, width: int, n_hidden: int,
+                  n_out: int = 1) -> list[np.ndarray]:
     mats, off, fan_in = [], 0, n_in
     for _ in range(n_hidden):
         mats.append(flat[off:off + width * fan_in].reshape(width, fan_in))
         off += width * fan_in
         fan_in = width
-    mats.append(flat[off:off + fan_in].reshape(1, fan_in))
+    mats.append(flat[off:off + n_out * fan_in].reshape(n_out, fan_in))
     return mats
 
 
