@@ -54,6 +54,11 @@ WORKLOADS = {
               "rays; NIF (hashed 16x2 FP16 grids, 3x64 FP16 networks, trained 64 Adam steps x 262,144 "
               "pairs) only for objects above 100k tris, the exact BVH for the rest and the room; "
               "compared with the exact BVH over every triangle"),
+    "primary": ("primary rays (NIF outputs occupancy, shading normal and depth, Sec. 6.1): the room "
+                "scene (64 displaced icospheres, 1,003,520 tris, + 12-tri room), 1920x1080 pixel-centre "
+                "camera rays -> 2,073,600 primary rays; hashed 16x2 FP16 grids per object, outer/inner 3x64 "
+                "FP16 networks with 5 outputs trained 64 Adam steps x 262,144 pairs from 4 jittered "
+                "samples per pixel; compared with the exact closest-hit BVH cast over every triangle"),
     "precision": ("precision sweep: small-configuration object (20,480 tris) in the room, 4 point "
                   "lights -> 8,294,400 shadow rays; dense 8x2 FP32 grids (R 4..64), MLP 3x64 trained "
                   "in FP32, inferred in FP32 / BF16 / FP16 / FP8-E4M3"),
@@ -659,6 +664,121 @@ def run_grouped(args):
     print(json.dumps(line), flush=True)
 
 
+PRIMARY_METRIC = "primary rays/sec NIF (hit, normal, depth) vs own GPU BVH closest hit"
+
+
+def run_primary(args):
+    """NIF for primary rays on the room frame: one step = the exact
+    closest-hit cast of the room, the front end (every pair), the fused
+    five-output network and the closest-hit resolution, against the exact
+    closest-hit cast over every triangle."""
+    import torch
+
+    from paper_2306_07191_gb300 import _lib as L
+    from paper_2306_07191_gb300 import nif
+    from paper_2306_07191_gb300.pipeline import PrimaryPipeline, primary_config
+
+    log = lambda *a: print(*a, file=sys.stderr, flush=True)
+    cfg = primary_config()
+    if args.small:
+        cfg.width, cfg.height, cfg.train_steps, cfg.batch, cfg.train_spp, cfg.n_obj = 640, 360, 8, 65536, 2, 16
+    if args.ctas_per_sm:
+        cfg.ctas_per_sm = args.ctas_per_sm
+    pipe = PrimaryPipeline(cfg, log=log)
+    train_s = pipe.train()
+    tms = sorted(pipe.train_step_ms[1:]) or pipe.train_step_ms
+    acc = pipe.disagreement()
+    abl = pipe.ablations()
+    log(f"primary accuracy {acc}  ablations {abl}")
+    pipe.release_training_state()
+    torch.cuda.empty_cache()
+    tune_ms = None
+    if not args.ctas_per_sm:
+        cands = tuple(c for c in nif.SCHEDULE_CANDIDATES if c[0] == L.NIF_SCHED_SERIAL)
+        sched, occ, tune_ms = nif.autotune(pipe.model, lambda: pipe.primary_step(), candidates=cands,
+                                           key_extra=(pipe.n_rays, "primary"))
+        log(f"autotuned fused kernel: {occ} CTAs/SM ({tune_ms})")
+    n = pipe.n_rays
+    rays = pipe.rays
+    dev = rays.device
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def timed(fn, sub=False):
+        for _ in range(args.warmup):
+            flush.zero_()
+            fn()
+        torch.cuda.synchronize()
+        parts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            if sub:
+                fn(e[0:4])
+            else:
+                e[0].record(stream)
+                fn()
+            e[4].record(stream)
+            parts.append(e)
+        torch.cuda.synchronize()
+        tot = statistics.mean(e[0].elapsed_time(e[4]) for e in parts)
+        subs = None
+        if sub:
+            def m(a, b):
+                return statistics.mean(e[a].elapsed_time(e[b]) for e in parts)
+            subs = {"room_cast_ms": m(0, 1), "frontend_ms": m(1, 2), "fused_ms": m(2, 3), "resolve_ms": m(3, 4)}
+        return tot, subs
+
+    with ClockSampler(0) as clk:
+        nif_ms, subs = timed(lambda ev=None: pipe.primary_step(ev=ev), sub=True)
+        bvh_ms, _ = timed(lambda: pipe.bvh_step())
+    clocks = clk.summary()
+    pipe.check()
+    nq = int(pipe._primary_buffers()["count"].item())
+    host_rays = torch.empty((n, 8), dtype=torch.float32, pin_memory=True)
+    host_rays.copy_(rays.cpu())
+    host_t = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    host_n = torch.empty((n, 3), dtype=torch.float32, pin_memory=True)
+    dev_rays = torch.empty_like(rays)
+
+    def e2e_step():
+        dev_rays.copy_(host_rays, non_blocking=True)
+        t, nrm, _ = pipe.primary_step(dev_rays)
+        host_t.copy_(t, non_blocking=True)
+        host_n.copy_(nrm, non_blocking=True)
+
+    e2e_ms, _ = timed(e2e_step)
+    hbm, tflops, src = _peaks()
+    alg_bytes, flops_q = pipe.query_cost()
+    fused_s = subs["fused_ms"] * 1e-3
+    ach = nq * alg_bytes / fused_s / 1e9
+    line = {
+        "metric": PRIMARY_METRIC, "value": n / (nif_ms * 1e-3), "unit": "primary rays/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": nif_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+        "config": {"workload": WORKLOADS["primary"], "rays": n, "queries": nq, "triangles": pipe.n_tris,
+                   "objects": pipe.n_obj, "outputs": pipe.n_outputs,
+                   "l2": "flushed (256 MB write) before every timed step", "fused_schedule": "serial",
+                   "fused_ctas_per_sm": pipe.model.cfg.ctas_per_sm, "autotune_ms": tune_ms,
+                   "parallelism": "single GPU"},
+        "bvh_rays_per_s": n / (bvh_ms * 1e-3), "bvh_ms_per_step": bvh_ms, "speedup_vs_bvh": bvh_ms / nif_ms,
+        "accuracy": acc, "ablations": abl, "train_s": train_s,
+        "train": {"steps": len(pipe.train_step_ms), "gpu_ms_per_step_median": tms[len(tms) // 2]},
+        "stages_ms": subs,
+        "roofline": {"kernel": "nif fused encode+MLP (tcgen05), 5 outputs", "bound": "hbm", "achieved": ach,
+                     "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None, "peak_source": src,
+                     "tensor_tflops": nq * flops_q / fused_s / 1e12, "tensor_peak_tflops": tflops,
+                     "alg_bytes_per_query": alg_bytes, "flops_per_query": flops_q},
+        "e2e": {"value": n / (e2e_ms * 1e-3), "unit": "primary rays/s", "h2d_bytes_per_step": n * 32,
+                "d2h_bytes_per_step": n * 16},
+        # per step: room cast, 3 front-end kernels, the fused forward, 2 resolution kernels
+        "gpu_launches": 7 * args.steps,
+        "clocks": clocks,
+        "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -682,6 +802,8 @@ def main():
         run_reference(args)
     elif args.workload == "grouped":
         run_grouped(args)
+    elif args.workload == "primary":
+        run_primary(args)
     else:
         run_ours(args)
 

@@ -103,6 +103,8 @@ def full_scale_config() -> RoomConfig:
 
 
 class RoomPipeline:
+    n_outputs = 1  # network output rows (the occupancy logit)
+
     def __init__(self, cfg: RoomConfig, device="cuda", log=print):
         self.cfg = cfg
         self.log = log
@@ -139,12 +141,12 @@ class RoomPipeline:
         self.tlas = nif.BVH.from_boxes(self.obj_aabb)
         self.light = torch.from_numpy(ws.light.astype(np.float32).reshape(-1)).to(dev)
         # evaluation frame: pixel-centre camera rays -> primary hits -> shadow rays
-        self.rays = self._shadow_rays(torch.from_numpy(ws.camera).to(dev), light_seed=4321)
+        self.rays = self._eval_rays(torch.from_numpy(ws.camera).to(dev))
         self.n_rays = int(self.rays.shape[0])
         n_grid = self._build_model()
         torch.cuda.synchronize()
         self.log(f"room scene ready: {self.n_tris} triangles ({self.n_tris_nif} in {self.n_obj} NIF objects), "
-                 f"{self.n_rays} shadow rays, "
+                 f"{self.n_rays} rays, "
                  f"{n_grid / 1e9:.3f}G grid latents ({time.time() - t0:.1f}s)")
 
     def _build_model(self) -> int:
@@ -154,7 +156,7 @@ class RoomPipeline:
         ncfg = nif.NifConfig(res=list(c.res), n_features=c.n_features, log2_table=c.log2_table,
                              grid_dtype=c.grid_dtype, n_hidden=c.n_hidden, width=c.width_mlp,
                              mlp_dtype=c.mlp_dtype, net_mode=L.NIF_NETS_CLASS,
-                             ctas_per_sm=c.ctas_per_sm, schedule=c.schedule)
+                             ctas_per_sm=c.ctas_per_sm, schedule=c.schedule, n_outputs=self.n_outputs)
         self.V = nif.NifModel.grid_vertices(ncfg)
         self.P = nif.NifModel.weight_count(ncfg)
         n_grid = self.n_obj * 2 * self.V * c.n_features
@@ -162,7 +164,8 @@ class RoomPipeline:
         L.call("nif_fill_uniform", ctypes.c_void_p(self.g_master.data_ptr()), n_grid, GRID_SEED,
                GRID_SCALE, nif._stream())
         wr = np.random.default_rng(c.seed + 101)
-        flat = np.concatenate([synth.flatten_mlp(synth.mlp_init(wr, ncfg.K, c.width_mlp, c.n_hidden))
+        flat = np.concatenate([synth.flatten_mlp(synth.mlp_init(wr, ncfg.K, c.width_mlp, c.n_hidden,
+                                                                n_out=self.n_outputs))
                                for _ in range(2)])
         self.w_master = torch.from_numpy(flat).to(dev)
         gdt = {L.NIF_F16: torch.float16, L.NIF_F32: torch.float32}[c.grid_dtype]
@@ -173,6 +176,10 @@ class RoomPipeline:
         return n_grid
 
     # ------------------------------------------------------------ inputs
+    def _eval_rays(self, camera: torch.Tensor) -> torch.Tensor:
+        """The rays of the evaluation frame: shadow rays from the primary hits."""
+        return self._shadow_rays(camera, light_seed=4321)
+
     def _shadow_rays(self, camera: torch.Tensor, light_seed: int) -> torch.Tensor:
         """Shadow rays from the primary hits of `camera`: one per point light,
         or cfg.samples uniform samples of the area light per pixel."""
@@ -260,8 +267,10 @@ class RoomPipeline:
     def train(self, steps: int | None = None, seed: int = 99, pairs=None):
         c = self.cfg
         steps = steps if steps is not None else c.train_steps
-        rays, rid, qo, lab, n_outer = pairs if pairs is not None else self.training_pairs()
-        self.pairs = (rays, rid, qo, lab, n_outer)
+        pairs = pairs if pairs is not None else self.training_pairs()
+        rays, rid, qo, lab, n_outer = pairs[:5]
+        aux = pairs[5] if len(pairs) > 5 else None  # regression targets (several outputs)
+        self.pairs = pairs
         npool = int(rid.shape[0])
         self.trainer = nif.Trainer(self.model, lr=c.lr, w_master=self.w_master, g_master=self.g_master)
         draw = BatchDraw(npool, seed)
@@ -280,7 +289,8 @@ class RoomPipeline:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
             loss = self.trainer.step(rays, rid[it].contiguous(), qo[it].contiguous(), goff,
-                                     lab[it].contiguous(), B)
+                                     lab[it].contiguous(), B,
+                                     aux=aux[it].contiguous() if aux is not None else None)
             e1.record()
             step_ev.append((e0, e1))
             losses.append(loss.clone())
@@ -677,3 +687,224 @@ class PaperEncodingPipeline(RoomPipeline):
             cl["g_master"] = cl["w_master"] = None
             cl["init_grids"] = cl["init_weights"] = None
         self.inner_inf_init_weights = None
+
+
+# ---------------------------------------------------------------------------
+# NIF for primary rays (Sec. 3.2, Sec. 6.1 with Fig. 5)
+# ---------------------------------------------------------------------------
+def primary_config() -> RoomConfig:
+    """The room scene seen directly by the camera: 2,073,600 pixel-centre
+    primary rays; per object the room's hashed FP16 grids, outer/inner 3x64
+    FP16 networks with five outputs (occupancy, normal, depth in the box),
+    trained on 4 jittered samples per pixel."""
+    return RoomConfig(schedule=L.NIF_SCHED_SERIAL)
+
+
+def face_normals(verts: torch.Tensor, tris: torch.Tensor, prim: torch.Tensor, d: torch.Tensor) -> torch.Tensor:
+    """Unit geometric normals of triangles prim (>= 0) facing against the
+    ray directions d: the regression targets and the truth of the normal."""
+    t = tris[prim.long()].long()
+    v0, v1, v2 = verts[t[:, 0]], verts[t[:, 1]], verts[t[:, 2]]
+    n = torch.linalg.cross(v1 - v0, v2 - v0)
+    n = n / n.norm(dim=1, keepdim=True).clamp_min(1e-30)
+    flip = (n * d).sum(dim=1, keepdim=True) > 0
+    return torch.where(flip, -n, n)
+
+
+def slab_params(rays: torch.Tensor, boxes: torch.Tensor):
+    """FP32 t_in, t_out of ray segments against their boxes (one box per
+    ray), as the front end computes them: IEEE divisions, an axis with
+    d == 0 inside its slab passes."""
+    o, d = rays[:, 0:3], rays[:, 4:7]
+    lo, hi = boxes[:, 0:3], boxes[:, 3:6]
+    par = d == 0
+    dd = torch.where(par, torch.ones_like(d), d)
+    t0, t1 = (lo - o) / dd, (hi - o) / dd
+    near = torch.where(par, torch.full_like(d, -float("inf")), torch.minimum(t0, t1))
+    far = torch.where(par, torch.full_like(d, float("inf")), torch.maximum(t0, t1))
+    tin = torch.maximum(rays[:, 3], near.max(dim=1).values)
+    tout = torch.minimum(rays[:, 7], far.min(dim=1).values)
+    return tin, tout
+
+
+class PrimaryPipeline(RoomPipeline):
+    """Primary visibility with NIF: per pixel the nearest hit, its depth and
+    its shading normal (Sec. 6.1, Fig. 5).  One step: the exact closest-hit
+    cast of the non-NIF geometry (the room), the front end over the object
+    boxes (every pair: a closest hit needs them all), the fused network with
+    five outputs, and the closest-hit resolution.  The comparison is the
+    exact closest-hit cast over every triangle."""
+    n_outputs = 5
+
+    def _eval_rays(self, camera: torch.Tensor) -> torch.Tensor:
+        return camera.contiguous()
+
+    def training_pairs(self, spp: int | None = None, seed: int = 1234):
+        """Jittered camera rays (the first spp of the frame, Sec. 4.2), their
+        (ray, object) pairs, the per-pair labels (1 = the ray misses the
+        object) and targets [normal | delta] from the exact closest hit of
+        the pair's own object."""
+        c = self.cfg
+        spp = spp or c.train_spp
+        rays, rids, qobjs, labels, auxs = [], [], [], [], []
+        base = 0
+        for s in range(spp):
+            jit = np.random.default_rng(seed + s).uniform(size=(c.width * c.height, 2))
+            cam = synth.camera_rays(c.width, c.height, (0.0, 0.0, 19.0), (0.0, 0.0, 0.0), 60.0, jitter=jit)
+            r = torch.from_numpy(cam).to(self.dev)
+            rid, qo, goff, count = self.model.frontend(r, tlas=self.tlas,
+                                                       max_q=c.max_pairs_per_ray * r.shape[0] + 1024)
+            torch.cuda.synchronize()
+            self.model.check()
+            nq = int(count.item())
+            rid, qo = rid[:nq].contiguous(), qo[:nq].contiguous()
+            t_hit, prim = self.bvh.cast_pairs_closest(r, rid, qo)
+            hit = prim >= 0
+            rr = r[rid.long()]
+            obj = (qo.to(torch.int64) & 0x7FFFFFFF)
+            tin, tout = slab_params(rr, self.obj_aabb[obj])
+            aux = torch.zeros((nq, 4), dtype=torch.float32, device=self.dev)
+            h = hit.nonzero().squeeze(1)
+            aux[h, 0:3] = face_normals(self.verts, self.tris, prim[h], rr[h, 4:7])
+            span = (tout[h] - tin[h]).clamp_min(1e-30)
+            aux[h, 3] = ((t_hit[h] - tin[h]) / span).clamp(0.0, 1.0)
+            rays.append(r)
+            rids.append(rid.to(torch.int64) + base)
+            qobjs.append(qo)
+            labels.append((~hit).to(torch.uint8))
+            auxs.append(aux)
+            base += r.shape[0]
+        rays = torch.cat(rays)
+        rid = torch.cat(rids)
+        qo = torch.cat(qobjs)
+        lab = torch.cat(labels)
+        aux = torch.cat(auxs)
+        inner = ((qo.to(torch.int64) >> 31) & 1)
+        order = torch.argsort(inner, stable=True)
+        return (rays, rid[order].to(torch.int32), qo[order].contiguous(), lab[order].contiguous(),
+                int((inner == 0).sum().item()), aux[order].contiguous())
+
+    # ------------------------------------------------------------ queries
+    def _primary_buffers(self):
+        if getattr(self, "_pb", None) is None:
+            n = self.n_rays
+            mq = self.cfg.max_pairs_per_ray * n + 1024
+            dev = self.dev
+            self._pb = {
+                "max_q": mq,
+                "ray_id": torch.empty(mq, dtype=torch.int32, device=dev),
+                "qobj": torch.empty(mq, dtype=torch.int32, device=dev),
+                "goff": torch.empty(self.model.n_nets + 1, dtype=torch.int64, device=dev),
+                "count": torch.zeros(1, dtype=torch.int64, device=dev),
+                "ws": self.model.workspace(mq, n),
+                "out": torch.empty((mq, self.n_outputs), dtype=torch.float32, device=dev),
+                "key": torch.empty(n, dtype=torch.int64, device=dev),
+                "t": torch.empty(n, dtype=torch.float32, device=dev),
+                "prim": torch.empty(n, dtype=torch.int32, device=dev),
+                "normal": torch.empty((n, 3), dtype=torch.float32, device=dev),
+                "winner": torch.empty(n, dtype=torch.int32, device=dev),
+            }
+        return self._pb
+
+    def primary_step(self, rays: torch.Tensor | None = None, winner: bool = False, ev=None):
+        """One primary-visibility query; returns (t, normal, winner or None).
+        ev (optional, 4 CUDA events) brackets the exact cast, the front end,
+        the fused forward and the resolution."""
+        rays = self.rays if rays is None else rays
+        b = self._primary_buffers()
+        vp, sp, n = ctypes.c_void_p, nif._stream(), int(rays.shape[0])
+        stream = torch.cuda.current_stream()
+        d = self.model.desc()
+        ws = b["ws"]
+        if ev is not None:
+            ev[0].record(stream)
+        L.call("bvh_cast_closest", vp(self.room_bvh.buf.data_ptr()), vp(rays.data_ptr()), n,
+               vp(b["t"].data_ptr()), vp(b["prim"].data_ptr()), sp)
+        if ev is not None:
+            ev[1].record(stream)
+        L.call("nif_frontend", ctypes.byref(d), vp(self.tlas.buf.data_ptr()), vp(rays.data_ptr()), n,
+               vp(b["ray_id"].data_ptr()), vp(b["qobj"].data_ptr()), b["max_q"], vp(b["goff"].data_ptr()),
+               vp(b["count"].data_ptr()), vp(ws.data_ptr()), ws.numel(), sp)
+        if ev is not None:
+            ev[2].record(stream)
+        L.call("nif_infer_queries", ctypes.byref(d), vp(rays.data_ptr()), n, vp(b["ray_id"].data_ptr()),
+               vp(b["qobj"].data_ptr()), vp(b["goff"].data_ptr()), b["max_q"], None, vp(b["out"].data_ptr()),
+               vp(ws.data_ptr()), ws.numel(), sp)
+        if ev is not None:
+            ev[3].record(stream)
+        if winner:
+            b["winner"].fill_(-1)
+        L.call("nif_primary_resolve", ctypes.byref(d), vp(rays.data_ptr()), n, vp(b["ray_id"].data_ptr()),
+               vp(b["qobj"].data_ptr()), vp(b["goff"].data_ptr()), b["max_q"], vp(b["out"].data_ptr()),
+               vp(b["key"].data_ptr()), vp(b["t"].data_ptr()), vp(b["normal"].data_ptr()),
+               vp(b["winner"].data_ptr()) if winner else None, sp)
+        return b["t"], b["normal"], b["winner"] if winner else None
+
+    def bvh_step(self, rays: torch.Tensor | None = None):
+        """The exact closest-hit cast over every triangle (the comparison)."""
+        rays = self.rays if rays is None else rays
+        b = self._primary_buffers()
+        vp = ctypes.c_void_p
+        L.call("bvh_cast_closest", vp(self.bvh.buf.data_ptr()), vp(rays.data_ptr()), int(rays.shape[0]),
+               vp(b["t"].data_ptr()), vp(b["prim"].data_ptr()), nif._stream())
+        return b["t"], b["prim"]
+
+    def query_cost(self):
+        c = self.cfg
+        esz = 2 if c.grid_dtype == L.NIF_F16 else 4
+        K = 3 * len(c.res) * c.n_features
+        W = c.width_mlp
+        return 3 * len(c.res) * 8 * c.n_features * esz, 2 * (K * W + (c.n_hidden - 1) * W * W + self.n_outputs * W)
+
+    def check(self):
+        self.model.check(self._primary_buffers()["ws"])
+
+    def disagreement(self):
+        """Accuracy against the exact closest-hit cast over every triangle:
+        pixels whose hit is a NIF object for one and not the other; over the
+        pixels where both see a NIF object, the relative depth error and the
+        angle between the normals; and the PSNR of the normal image
+        ((n + 1) / 2) and of the depth image (t over the frame's depth range)
+        over the pixels that see an object, as Fig. 5 compares them."""
+        t_b, prim_b = (x.clone() for x in self.bvh_step())
+        t_n, n_n, win = (x.clone() for x in self.primary_step(winner=True))
+        torch.cuda.synchronize()
+        self.check()
+        tags = self.tags
+        obj_b = torch.where(prim_b >= 0, tags[prim_b.clamp_min(0).long()], torch.full_like(prim_b, -1))
+        nif_b = obj_b >= 0
+        nif_n = win >= 0
+        both = nif_b & nif_n
+        d = self.rays[:, 4:7]
+        n_true = torch.zeros_like(n_n)
+        n_true[nif_b] = face_normals(self.verts, self.tris, prim_b[nif_b], d[nif_b])
+        rel = ((t_n - t_b).abs() / t_b)[both]
+        cosang = (n_n[both] * n_true[both]).sum(dim=1).clamp(-1.0, 1.0)
+        ang = torch.rad2deg(torch.arccos(cosang))
+        either = nif_b | nif_n
+        img_n = torch.where(nif_n[:, None], (n_n + 1) * 0.5, torch.zeros_like(n_n))
+        img_b = torch.where(nif_b[:, None], (n_true + 1) * 0.5, torch.zeros_like(n_n))
+        mse_n = float(((img_n - img_b)[either] ** 2).mean())
+        tmax = float(t_b[nif_b].max())
+        dep_n = torch.where(nif_n, t_n / tmax, torch.zeros_like(t_n))
+        dep_b = torch.where(nif_b, t_b / tmax, torch.zeros_like(t_b))
+        mse_d = float(((dep_n - dep_b)[either] ** 2).mean())
+        return {
+            "hit_disagreement": float((nif_b != nif_n).float().mean()),
+            "hit_disagreement_on_object_pixels": float((nif_b != nif_n)[either].float().mean()),
+            "object_pixels": int(nif_b.sum()),
+            "depth_rel_err_mean": float(rel.mean()), "depth_rel_err_median": float(rel.median()),
+            "normal_err_deg_mean": float(ang.mean()), "normal_err_deg_median": float(ang.median()),
+            "psnr_normal_db": 10.0 * float(np.log10(1.0 / max(mse_n, 1e-30))),
+            "psnr_depth_db": 10.0 * float(np.log10(1.0 / max(mse_d, 1e-30))),
+            "queries": int(self._primary_buffers()["count"].item()),
+        }
+
+    def ablations(self):
+        """The untrained network's hit disagreement and normal error."""
+        w, g = self.model.weights, self.model.grids
+        self.model.weights, self.model.grids = self.init_weights, self.init_grids
+        r = self.disagreement()
+        self.model.weights, self.model.grids = w, g
+        return {"untrained_hit_disagreement": r["hit_disagreement"],
+                "untrained_normal_err_deg_mean": r["normal_err_deg_mean"]}

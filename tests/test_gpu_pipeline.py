@@ -127,3 +127,28 @@ def test_mixed_scene_splits_geometry_between_nif_and_exact_cast():
     torch.cuda.synchronize()
     assert torch.equal(a, b)
     assert p.disagreement()["all"] < 0.05
+
+
+def test_primary_pipeline_learns_depth_and_normals():
+    """NIF for primary rays (Sec. 6.1) at a reduced size: after training, the
+    per-pixel hit, depth and normal follow the exact closest-hit cast far
+    better than the untrained network; where the room is nearer than every
+    NIF hit, the step returns the room's exact t."""
+    cfg = _small(pipeline.primary_config())
+    cfg.train_spp, cfg.train_steps = 2, 40
+    p = pipeline.PrimaryPipeline(cfg, log=lambda *a: None)
+    p.train()
+    acc = p.disagreement()
+    abl = p.ablations()
+    assert acc["object_pixels"] > 10000
+    assert acc["hit_disagreement"] < 0.5 * abl["untrained_hit_disagreement"]
+    assert acc["normal_err_deg_mean"] < 0.5 * abl["untrained_normal_err_deg_mean"]
+    assert acc["depth_rel_err_median"] < 0.05
+    t, nrm, win = (x.clone() for x in p.primary_step(winner=True))
+    t_room, _ = p.room_bvh.cast_closest(p.rays)
+    torch.cuda.synchronize()
+    room = win < 0
+    assert torch.equal(t[room], t_room[room])
+    assert bool((t[~room] < t_room[~room]).all())
+    ln = nrm[~room].norm(dim=1)
+    assert float((ln - 1).abs().max()) < 1e-5
