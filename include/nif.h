@@ -267,6 +267,38 @@ nif_status nif_shadow_rays(const nif_ray* d_camera, const float* d_t, int64_t n,
                            const float* d_light, int32_t light_per_ray, float tmin,
                            nif_ray* d_out, void* stream);
 
+/* Direct lighting around the shadow query (Sec. 4.1 renders direct
+ * illumination; Sec. 5 'Training' samples the lights by radiant flux from a
+ * tabulated CDF searched by bisection; Sec. 6.2 compares it with uniform
+ * selection).  Lights are one-sided Lambertian quads, d_lights [K][10] FP32:
+ * corner xyz, edge e1 xyz, edge e2 xyz, radiance L_e; they emit on the side of
+ * e1 x e2; area A = |e1 x e2|, flux pi L_e A.
+ *
+ * nif_light_cdf: d_cdf[k] = (w_0 + ... + w_k) / (w_0 + ... + w_{K-1}), summed
+ * in order in FP32 (w = flux for importance sampling, 1 for uniform).
+ *
+ * nif_light_samples: for camera ray i with closest hit (d_t[i], d_prim[i]; t
+ * = +inf: none) on triangle d_tris[prim] of d_verts and sample j < spp, with
+ * d_u [n*spp][3] uniform in [0, 1): the light k = first index with
+ * u0 < cdf_k (probability p_k = cdf_k - cdf_{k-1}), the point
+ * y = c + u1 e1 + u2 e2, the shadow ray d_out[i*spp+j] from the hit point x
+ * towards y with segment (tmin, |y - x|), and its value without visibility
+ * d_f = (albedo/pi) L_e cos_x cos_y / |y - x|^2 * A / p_k (cos_x against the
+ * triangle's normal turned to face the camera, cos_y against the light's).
+ * Samples with cos_x <= 0, cos_y <= 0 or no hit get d_f = 0 and an empty
+ * segment.  FP32, one rounding per operation in that order (no FMA).
+ *
+ * nif_shade: d_radiance[i] = (sum over visible samples j of d_f[i*spp+j]) / spp
+ * (visible: bit i*spp+j of d_occluded_bits clear), summed in sample order. */
+nif_status nif_light_cdf(const float* d_weight, int32_t n_lights, float* d_cdf, void* stream);
+nif_status nif_light_samples(const nif_ray* d_camera, const float* d_t, const int32_t* d_prim,
+                             const float* d_verts, const int32_t* d_tris, int64_t n, int32_t spp,
+                             const float* d_lights, const float* d_cdf, int32_t n_lights,
+                             const float* d_u, float tmin, float albedo, nif_ray* d_out, float* d_f,
+                             void* stream);
+nif_status nif_shade(const float* d_f, const uint32_t* d_occluded_bits, int64_t n, int32_t spp,
+                     float* d_radiance, void* stream);
+
 /* ------------------------------------------------------------ NIF path --
  * Queries.  A query is a (ray, object) pair: d_ray_id[q] (uint32) and
  * d_qobj[q] = object id | (1u << 31 when the pair is inner).  Query lists

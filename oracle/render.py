@@ -91,7 +91,7 @@ def light_samples(cam, t, prim, verts, tris, lights, cdf, u, spp: int, tmin: flo
     u = np.asarray(u, f32).reshape(n * spp, 3)
     lights = np.asarray(lights, f32)
     cdf = np.asarray(cdf, f32)
-    hit = th < np.inf
+    hit = (th < np.inf) & (pr >= 0)
     k = pick_light(cdf, u[:, 0])
     p_k = np.where(k > 0, (cdf[k] - cdf[np.maximum(k - 1, 0)]).astype(f32), cdf[k]).astype(f32)
     Lk = lights[k]
@@ -120,7 +120,7 @@ def light_samples(cam, t, prim, verts, tris, lights, cdf, u, spp: int, tmin: flo
     cos_y = (-_dot(nl, om)).astype(f32)
     live = hit & (cos_x > 0) & (cos_y > 0) & (r > 0)
     # f = (albedo/pi) L_e cos_x cos_y / r^2 * A / p_k, left to right
-    f = (f32(albedo / np.pi) * Lk[:, 9]).astype(f32)
+    f = (f32(f32(albedo) / f32(np.pi)) * Lk[:, 9]).astype(f32)
     f = (f * cos_x).astype(f32)
     f = (f * cos_y).astype(f32)
     f = (f / r2).astype(f32)

@@ -77,6 +77,9 @@ SIGNATURES = {
     "bvh_cast_closest": (i32, [P, P, i64, P, P, P]),
     "bvh_cast_pairs": (i32, [P, P, P, P, i64, P, P]),
     "bvh_cast_pairs_closest": (i32, [P, P, P, P, i64, P, P, P]),
+    "nif_light_cdf": (i32, [P, i32, P, P]),
+    "nif_light_samples": (i32, [P, P, P, P, P, i64, i32, P, P, i32, P, f32, f32, P, P, P]),
+    "nif_shade": (i32, [P, P, i64, i32, P, P]),
     "nif_shadow_rays": (i32, [P, P, i64, i32, P, i32, f32, P, P]),
     "nif_workspace_size": (size_t, [MD, i64, i64]),
     "nif_train_workspace_size": (size_t, [MD, i64]),

@@ -695,6 +695,110 @@ __global__ void k_shadow_rays(const nif_ray* cam, const float* tcam, int64_t n, 
   out[k] = s;
 }
 
+// ----------------------------------------------------- direct lighting
+// Light selection table: cum_k summed in order, cdf_k = cum_k / cum_{K-1}
+// (one thread: K is small and the order is fixed).
+__global__ void k_light_cdf(const float* w, int K, float* cdf) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  float c = 0.f;
+  for (int k = 0; k < K; ++k) {
+    c = c + w[k];
+    cdf[k] = c;
+  }
+  for (int k = 0; k < K; ++k) cdf[k] = cdf[k] / c;
+}
+
+__device__ __forceinline__ float dot3(float ax, float ay, float az, float bx, float by, float bz) {
+  float s = ax * bx;
+  s = s + ay * by;
+  return s + az * bz;
+}
+
+// One light sample per thread (this unit is built without FMA contraction,
+// so every product and sum rounds on its own, in the order written): pick a
+// light by bisection of the table, a point on it, the shadow segment from
+// the camera ray's closest hit and the sample's value without visibility.
+__global__ void k_light_samples(const nif_ray* cam, const float* tcam, const int32_t* prim,
+                                const float* verts, const int32_t* tris, int64_t n, int spp,
+                                const float* lights, const float* cdf, int K, const float* u,
+                                float tmin, float albedo_over_pi, nif_ray* out, float* fval) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n * spp) return;
+  const int64_t i = j / spp;
+  const nif_ray c = cam[i];
+  const float t = tcam[i];
+  const float u0 = u[3 * j], u1 = u[3 * j + 1], u2 = u[3 * j + 2];
+  // first k with u0 < cdf_k
+  int lo = 0, hi = K - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (u0 < cdf[mid]) hi = mid;
+    else lo = mid + 1;
+  }
+  const int k = lo;
+  const float pk = k > 0 ? cdf[k] - cdf[k - 1] : cdf[0];
+  const float* Lk = lights + 10 * k;
+  nif_ray s;
+  s.ox = c.ox; s.oy = c.oy; s.oz = c.oz;
+  s.dx = c.dx; s.dy = c.dy; s.dz = c.dz;
+  s.tmin = 0.f; s.tmax = 0.f;
+  float f = 0.f;
+  const int32_t p = prim[i];
+  if (t < INFINITY && p >= 0) {
+    const float px = c.ox + t * c.dx, py = c.oy + t * c.dy, pz = c.oz + t * c.dz;
+    const int32_t a = tris[3 * p], b = tris[3 * p + 1], d = tris[3 * p + 2];
+    const float v0x = verts[3 * a], v0y = verts[3 * a + 1], v0z = verts[3 * a + 2];
+    const float e1x = verts[3 * b] - v0x, e1y = verts[3 * b + 1] - v0y, e1z = verts[3 * b + 2] - v0z;
+    const float e2x = verts[3 * d] - v0x, e2y = verts[3 * d + 1] - v0y, e2z = verts[3 * d + 2] - v0z;
+    float nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+    const float nlen = sqrtf(dot3(nx, ny, nz, nx, ny, nz));
+    const float nd = nlen > 0.f ? nlen : 1.f;
+    nx = nx / nd; ny = ny / nd; nz = nz / nd;
+    if (dot3(nx, ny, nz, c.dx, c.dy, c.dz) > 0.f) { nx = -nx; ny = -ny; nz = -nz; }
+    float yx = Lk[0] + u1 * Lk[3], yy = Lk[1] + u1 * Lk[4], yz = Lk[2] + u1 * Lk[5];
+    yx = yx + u2 * Lk[6]; yy = yy + u2 * Lk[7]; yz = yz + u2 * Lk[8];
+    const float wx = yx - px, wy = yy - py, wz = yz - pz;
+    const float r2 = dot3(wx, wy, wz, wx, wy, wz);
+    const float r = sqrtf(r2);
+    const float rd = r > 0.f ? r : 1.f;
+    const float ox = wx / rd, oy = wy / rd, oz = wz / rd;
+    float lx = Lk[4] * Lk[8] - Lk[5] * Lk[7], ly = Lk[5] * Lk[6] - Lk[3] * Lk[8],
+          lz = Lk[3] * Lk[7] - Lk[4] * Lk[6];
+    const float A = sqrtf(dot3(lx, ly, lz, lx, ly, lz));
+    lx = lx / A; ly = ly / A; lz = lz / A;
+    const float cos_x = dot3(nx, ny, nz, ox, oy, oz);
+    const float cos_y = -dot3(lx, ly, lz, ox, oy, oz);
+    if (cos_x > 0.f && cos_y > 0.f && r > 0.f) {
+      f = albedo_over_pi * Lk[9];
+      f = f * cos_x;
+      f = f * cos_y;
+      f = f / r2;
+      f = f * A;
+      f = f / pk;
+      s.ox = px; s.oy = py; s.oz = pz;
+      s.dx = ox; s.dy = oy; s.dz = oz;
+      s.tmin = tmin;
+      s.tmax = r;
+    }
+  }
+  out[j] = s;
+  fval[j] = f;
+}
+
+// Pixel radiance: the mean of its samples' values over the visible ones,
+// summed in sample order.
+__global__ void k_shade(const float* fval, const uint32_t* occ, int64_t n, int spp, float* L) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float s = 0.f;
+  for (int j = 0; j < spp; ++j) {
+    const int64_t q = i * spp + j;
+    const float v = ((occ[q >> 5] >> (q & 31)) & 1u) ? 0.f : fval[q];
+    s = s + v;
+  }
+  L[i] = s / static_cast<float>(spp);
+}
+
 }  // namespace bvh
 }  // namespace nif
 
@@ -819,6 +923,44 @@ nif_status bvh_cast_pairs_closest(const void* d_bvh, const nif_ray* d_rays,
                 "bvh_cast_pairs_closest: null pointer");
   bvh::k_cast_pairs_closest<<<ceil_div(nq, 128), 128, 0, as_stream(stream)>>>(
       (const char*)d_bvh, d_rays, d_ray_id, d_obj, nq, d_t, d_prim);
+  NIF_LAUNCH_CHECK();
+  return NIF_OK;
+}
+
+nif_status nif_light_cdf(const float* d_weight, int32_t n_lights, float* d_cdf, void* stream) {
+  CallRange nvtx_range("nif_light_cdf");
+  NIF_CHECK_ARG(n_lights >= 1, "nif_light_cdf: at least one light");
+  NIF_CHECK_ARG(d_weight && d_cdf, "nif_light_cdf: null pointer");
+  bvh::k_light_cdf<<<1, 32, 0, as_stream(stream)>>>(d_weight, n_lights, d_cdf);
+  NIF_LAUNCH_CHECK();
+  return NIF_OK;
+}
+
+nif_status nif_light_samples(const nif_ray* d_camera, const float* d_t, const int32_t* d_prim,
+                             const float* d_verts, const int32_t* d_tris, int64_t n, int32_t spp,
+                             const float* d_lights, const float* d_cdf, int32_t n_lights,
+                             const float* d_u, float tmin, float albedo, nif_ray* d_out, float* d_f,
+                             void* stream) {
+  CallRange nvtx_range("nif_light_samples");
+  NIF_CHECK_ARG(n >= 0 && spp >= 1 && n_lights >= 1, "nif_light_samples: bad size");
+  if (n == 0) return NIF_OK;
+  NIF_CHECK_ARG(d_camera && d_t && d_prim && d_verts && d_tris && d_lights && d_cdf && d_u && d_out && d_f,
+                "nif_light_samples: null pointer");
+  const float albedo_over_pi = albedo / 3.14159265358979323846f;
+  bvh::k_light_samples<<<ceil_div(n * spp, 256), 256, 0, as_stream(stream)>>>(
+      d_camera, d_t, d_prim, d_verts, d_tris, n, spp, d_lights, d_cdf, n_lights, d_u, tmin, albedo_over_pi,
+      d_out, d_f);
+  NIF_LAUNCH_CHECK();
+  return NIF_OK;
+}
+
+nif_status nif_shade(const float* d_f, const uint32_t* d_occluded_bits, int64_t n, int32_t spp,
+                     float* d_radiance, void* stream) {
+  CallRange nvtx_range("nif_shade");
+  NIF_CHECK_ARG(n >= 0 && spp >= 1, "nif_shade: bad size");
+  if (n == 0) return NIF_OK;
+  NIF_CHECK_ARG(d_f && d_occluded_bits && d_radiance, "nif_shade: null pointer");
+  bvh::k_shade<<<ceil_div(n, 256), 256, 0, as_stream(stream)>>>(d_f, d_occluded_bits, n, spp, d_radiance);
   NIF_LAUNCH_CHECK();
   return NIF_OK;
 }

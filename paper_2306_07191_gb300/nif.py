@@ -39,6 +39,34 @@ def bits_to_bool(bits: torch.Tensor, n: int) -> torch.Tensor:
     return (((w[:, None] >> sh[None, :]) & 1).reshape(-1)[:n]).bool()
 
 
+def light_cdf(weight: torch.Tensor, stream=None) -> torch.Tensor:
+    """Light selection table from per-light weights (nif_light_cdf)."""
+    w = weight.float().contiguous()
+    cdf = torch.empty_like(w)
+    L.call("nif_light_cdf", _ptr(w), int(w.numel()), _ptr(cdf), _stream(stream))
+    return cdf
+
+
+def light_samples(camera, t, prim, verts, tris, lights, cdf, u, spp: int, tmin: float = 1e-3,
+                  albedo: float = 0.8, stream=None):
+    """Shadow rays [n*spp, 8] towards sampled points of quad lights and the
+    samples' values without visibility [n*spp] (nif_light_samples)."""
+    n = int(camera.shape[0])
+    out = torch.empty((n * spp, 8), dtype=torch.float32, device=camera.device)
+    f = torch.empty(n * spp, dtype=torch.float32, device=camera.device)
+    L.call("nif_light_samples", _ptr(camera), _ptr(t), _ptr(prim), _ptr(verts), _ptr(tris), n, spp,
+           _ptr(lights), _ptr(cdf), int(lights.shape[0]), _ptr(u), tmin, albedo, _ptr(out), _ptr(f),
+           _stream(stream))
+    return out, f
+
+
+def shade(f, bits, n: int, spp: int, out=None, stream=None) -> torch.Tensor:
+    """Pixel radiance from sample values and their occlusion bits (nif_shade)."""
+    out = out if out is not None else torch.empty(n, dtype=torch.float32, device=f.device)
+    L.call("nif_shade", _ptr(f), _ptr(bits), n, spp, _ptr(out), _stream(stream))
+    return out
+
+
 def clear_bits(bits: torch.Tensor, n: int, stream=None) -> torch.Tensor:
     """Zero an occlusion mask of n rays on the stream (nif_bits_clear)."""
     L.call("nif_bits_clear", _ptr(bits), n, _stream(stream))
