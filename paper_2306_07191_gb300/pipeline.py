@@ -908,3 +908,88 @@ class PrimaryPipeline(RoomPipeline):
         self.model.weights, self.model.grids = w, g
         return {"untrained_hit_disagreement": r["hit_disagreement"],
                 "untrained_normal_err_deg_mean": r["normal_err_deg_mean"]}
+
+
+# ---------------------------------------------------------------------------
+# Direct lighting with importance-sampled lights (Sec. 5 'Training', Sec. 6.2)
+# ---------------------------------------------------------------------------
+def ceiling_lights() -> np.ndarray:
+    """Eight one-sided quad lights under the room's ceiling (y = 19.9),
+    emitting downwards, with radiant fluxes spread over two orders of
+    magnitude: [K, 10] = corner, edge e1, edge e2, radiance."""
+    rows = []
+    spec = [(-16, -12, 4, 4, 6.0), (-6, -14, 2, 2, 24.0), (4, -12, 3, 5, 2.0), (12, -6, 2, 6, 0.5),
+            (-14, 6, 5, 3, 0.25), (-4, 8, 1, 1, 60.0), (6, 4, 4, 2, 1.0), (12, 10, 6, 4, 0.02)]
+    for x, z, a, b, Le in spec:
+        # e1 along +x, e2 along +z: e1 x e2 points down (-y)
+        rows.append([x, 19.9, z, a, 0, 0, 0, 0, b, Le])
+    return np.asarray(rows, np.float32)
+
+
+@dataclass
+class RenderConfig(PaperEncodingConfig):
+    sampling: str = "importance"  # light selection of the training rays: "importance" (flux) or "uniform"
+    render_spp: int = 4           # light samples per pixel of the rendered frame (importance)
+    albedo: float = 0.8
+    train_spp: int = 4
+
+
+def render_config(sampling: str = "importance", train_spp: int = 4) -> RenderConfig:
+    return RenderConfig(sampling=sampling, train_spp=train_spp, max_pairs_per_ray=8)
+
+
+class RenderPipeline(PaperEncodingPipeline):
+    """The paper-encoding pipeline inside a direct-lighting renderer: the
+    shadow rays of the rendered frame are render_spp light samples per pixel,
+    lights picked by flux from a tabulated CDF (Sec. 5); the training rays are
+    one light sample per jittered camera sample, picked by flux or uniformly
+    (the comparison of Sec. 6.2).  A frame is light sampling, the shadow
+    query and shading; the exact frame uses the BVH cast instead of NIF."""
+
+    def _light_setup(self):
+        if getattr(self, "_lt", None) is None:
+            lights = ceiling_lights()
+            A = np.linalg.norm(np.cross(lights[:, 3:6], lights[:, 6:9]), axis=1)
+            power = np.pi * lights[:, 9] * A
+            self._lt = torch.from_numpy(lights).to(self.dev)
+            self._cdf = {"importance": nif.light_cdf(torch.from_numpy(power.astype(np.float32)).to(self.dev)),
+                         "uniform": nif.light_cdf(torch.ones(len(lights), device=self.dev))}
+        return self._lt
+
+    def _light_rays(self, camera: torch.Tensor, seed: int, spp: int, sampling: str):
+        lights = self._light_setup()
+        n = int(camera.shape[0])
+        t, prim = self.bvh.cast_closest(camera)
+        u = torch.from_numpy(np.random.default_rng(seed).random((n * spp, 3), dtype=np.float32)).to(self.dev)
+        return nif.light_samples(camera, t, prim, self.verts, self.tris, lights, self._cdf[sampling], u, spp,
+                                 self.cfg.tmin, self.cfg.albedo)
+
+    def _eval_rays(self, camera: torch.Tensor) -> torch.Tensor:
+        self.n_pix = int(camera.shape[0])
+        self.eval_camera = camera
+        self.eval_u = torch.from_numpy(np.random.default_rng(4321).random(
+            (self.n_pix * self.cfg.render_spp, 3), dtype=np.float32)).to(self.dev)
+        rays, self.eval_f = self._light_rays(camera, 4321, self.cfg.render_spp, "importance")
+        return rays
+
+    def _shadow_rays(self, camera: torch.Tensor, light_seed: int) -> torch.Tensor:
+        rays, _ = self._light_rays(camera, light_seed, 1, self.cfg.sampling)
+        return rays
+
+    def render(self, visibility: str = "nif") -> torch.Tensor:
+        """Pixel radiance of the frame with NIF or exact (BVH) visibility."""
+        bits = nif.empty_bits(self.n_rays)
+        (self.nif_query if visibility == "nif" else self.bvh_query)(bits)
+        return nif.shade(self.eval_f, bits, self.n_pix, self.cfg.render_spp)
+
+    def psnr(self) -> float:
+        """PSNR (dB) of the NIF frame against the exact frame, both scaled by
+        the exact frame's 99.5th percentile and clamped to [0, 1]."""
+        ref = self.render("bvh")
+        img = self.render("nif")
+        torch.cuda.synchronize()
+        s = float(torch.quantile(ref[ref > 0][::max(1, int((ref > 0).sum()) // 1_000_000)].float(), 0.995))
+        a = (ref / s).clamp(0, 1)
+        b = (img / s).clamp(0, 1)
+        mse = float(((a - b) ** 2).mean())
+        return 10.0 * float(np.log10(1.0 / max(mse, 1e-30)))

@@ -152,3 +152,18 @@ def test_primary_pipeline_learns_depth_and_normals():
     assert bool((t[~room] < t_room[~room]).all())
     ln = nrm[~room].norm(dim=1)
     assert float((ln - 1).abs().max()) < 1e-5
+
+
+def test_render_pipeline_trains_a_useful_shadow_network():
+    """The direct-lighting frame at a reduced size: after training, the NIF
+    frame is within 25 dB PSNR of the exact frame, and the exact frame is the
+    shading of the exact cast of its own samples."""
+    cfg = _small(pipeline.render_config("importance", 2))
+    cfg.train_steps = 24
+    p = pipeline.RenderPipeline(cfg, log=lambda *a: None)
+    p.train()
+    trained = p.psnr()
+    bits = p.bvh.cast_shadow(p.rays)
+    ref = nif.shade(p.eval_f, bits, p.n_pix, cfg.render_spp)
+    assert torch.equal(ref, p.render("bvh"))
+    assert trained > 25.0, trained
