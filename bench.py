@@ -397,7 +397,9 @@ def run_ours(args):
         # 16-bit copy and the zeroed grad: 34 B per parameter per step
         "adam_bytes_per_step": 34 * n_par,
         "adam_floor_ms": 34 * n_par / (_peaks()[0] * 1e9) * 1e3,
-        "wall_includes": "host-side batch draw (numpy) and copies"}
+        "wall_includes": "host-side batch draw (numpy) and copies",
+        # batch loss every 8 steps and at the last one
+        "loss_curve": [round(v, 6) for v in pipe.losses[::8] + pipe.losses[-1:]]}
     dis = pipe.disagreement()
     abl = pipe.ablations()
     log(f"disagreement {dis}  ablations {abl}")
@@ -768,7 +770,8 @@ def run_primary(args):
                    "parallelism": "single GPU"},
         "bvh_rays_per_s": n / (bvh_ms * 1e-3), "bvh_ms_per_step": bvh_ms, "speedup_vs_bvh": bvh_ms / nif_ms,
         "accuracy": acc, "ablations": abl, "train_s": train_s,
-        "train": {"steps": len(pipe.train_step_ms), "gpu_ms_per_step_median": tms[len(tms) // 2]},
+        "train": {"steps": len(pipe.train_step_ms), "gpu_ms_per_step_median": tms[len(tms) // 2],
+                  "loss_curve": [round(v, 6) for v in pipe.losses[::8] + pipe.losses[-1:]]},
         "stages_ms": subs,
         "roofline": {"kernel": "nif fused encode+MLP (tcgen05), 5 outputs", "bound": "hbm", "achieved": ach,
                      "peak": hbm, "unit": "GB/s", "frac": ach / hbm, "traffic": None, "peak_source": src,

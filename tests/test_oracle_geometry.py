@@ -195,3 +195,25 @@ def test_numpy_slab_equals_scalar_slab_bitwise():
             assert a.view(np.uint32) == tin[i].view(np.uint32)
             assert b.view(np.uint32) == tout[i].view(np.uint32)
             assert e.view(np.uint32) == entry[i].view(np.uint32)
+
+
+def test_geometry_oracle_is_clean_under_host_sanitizers(tmp_path):
+    """AddressSanitizer and UndefinedBehaviorSanitizer over every entry point
+    of the C oracle (oracle/sanitize_check.cpp drives them on a random soup,
+    empty scenes and zero rays, and checks the BVH against brute force)."""
+    import os
+    import shutil
+    import subprocess
+    if shutil.which("g++") is None:
+        pytest.skip("needs g++")
+    src = os.path.join(os.path.dirname(oracle.__file__), "sanitize_check.cpp")
+    exe = str(tmp_path / "sanitize_check")
+    r = subprocess.run(["g++", "-std=c++17", "-O1", "-g", "-ffp-contract=off", "-fsanitize=address,undefined",
+                        "-fno-sanitize-recover=all", "-fno-omit-frame-pointer", "-pthread", src, "-o", exe],
+                       capture_output=True, text=True)
+    if r.returncode != 0 and "sanitize" in r.stderr:
+        pytest.skip("sanitizer runtime not available: " + r.stderr.splitlines()[-1])
+    assert r.returncode == 0, r.stderr
+    run = subprocess.run([exe], capture_output=True, text=True, timeout=120)
+    assert run.returncode == 0 and run.stdout.strip() == "OK", run.stdout + run.stderr
+    assert "runtime error" not in run.stderr
