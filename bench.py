@@ -479,10 +479,31 @@ def run_ours(args):
             subs["fused_ms"] = subs["fused_round1_ms"] + subs["fused_round2_ms"]
         return tot, subs
 
+    # the whole step captured once in a CUDA graph and replayed: no host
+    # launch overhead between its kernels (the stage split comes from an
+    # eager run with events between the calls)
+    graphs = {}
+    if not args.no_graph:
+        def capture(fn):
+            g = torch.cuda.CUDAGraph()
+            gs = torch.cuda.Stream()
+            gs.wait_stream(stream)
+            with torch.cuda.stream(gs):
+                fn()
+                torch.cuda.synchronize()
+                with torch.cuda.graph(g, stream=gs):
+                    fn()
+            stream.wait_stream(gs)
+            torch.cuda.synchronize()
+            return g
+        graphs["nif"] = capture(nif_step)
+        graphs["bvh"] = capture(lambda: pipe.bvh.cast_shadow(rays, out=bits))
     with ClockSampler(local) as clk:
         torch.cuda.profiler.start()
-        nif_ms, subs = timed(nif_step, args.steps, args.warmup, sub=True)
-        bvh_ms, _ = timed(lambda: pipe.bvh.cast_shadow(rays, out=bits), args.steps, args.warmup)
+        eager_ms, subs = timed(nif_step, args.steps, args.warmup, sub=True)
+        nif_ms = timed(graphs["nif"].replay, args.steps, args.warmup)[0] if graphs else eager_ms
+        bvh_ms, _ = timed(graphs["bvh"].replay if graphs else (lambda: pipe.bvh.cast_shadow(rays, out=bits)),
+                          args.steps, args.warmup)
         torch.cuda.profiler.stop()
     clocks = clk.summary()
     nq1, nq = pipe.last_query_counts()
@@ -508,6 +529,7 @@ def run_ours(args):
     e2e_ms, _ = timed(e2e_step, args.steps, args.warmup)
 
     ms = reduce_max(statistics.mean(nif_ms), world, dev)
+    ms_eager = reduce_max(statistics.mean(eager_ms), world, dev)
     bms = reduce_max(statistics.mean(bvh_ms), world, dev)
     ems = reduce_max(statistics.mean(e2e_ms), world, dev)
     value = world * n / (ms * 1e-3)
@@ -525,10 +547,11 @@ def run_ours(args):
                    "queries_round1": nq1, "queries_all_pairs": nq_all, "triangles": pipe.n_tris,
                    "objects": cfg.n_obj, "nif_objects": pipe.n_obj, "triangles_nif": pipe.n_tris_nif,
                    "l2": "flushed (256 MB write) before every timed step",
-                   "exact_cast": cfg.exact_cast,
+                   "exact_cast": cfg.exact_cast, "cuda_graph": bool(graphs),
                    "fused_schedule": SCHED_NAME[pipe.forward_models()[0][0].cfg.schedule],
                    "fused_ctas_per_sm": pipe.forward_models()[0][0].cfg.ctas_per_sm, "autotune_ms": tune_ms,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "ms_per_step_eager": ms_eager,
         "bvh_rays_per_s": world * n / (bms * 1e-3), "bvh_ms_per_step": bms,
         "speedup_vs_bvh": bms / ms,
         "visibility_disagreement": dis, "ablations": abl, "train_s": train_s,
@@ -920,6 +943,8 @@ def main():
     ap.add_argument("--schedule", default="", choices=["", "serial", "pipelined"],
                     help="fix the fused kernel's schedule (skips the autotuner)")
     ap.add_argument("--workload", default="room", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-graph", action="store_true",
+                    help="time the step's calls one by one instead of replaying a CUDA graph of them")
     ap.add_argument("--exact-cast", choices=("first", "after", "overlap"), default=None,
                     help="when the non-NIF geometry is cast: before the NIF query (default), after it, "
                          "or beside it on a second stream")
