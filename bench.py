@@ -75,7 +75,7 @@ WORKLOADS = {
 # kernel as it stands; a configuration without an entry reports null.
 FUSED_TRAFFIC_BYTES = {
     # profiles/fused_tm_room.md: rounds 1 + 2 of one step
-    ("room", "serial", 4): 1.260896e9 + 4.304384e6 + 0.425591e9 + 3.661056e6,
+    ("room", "serial", 4): 1.265874e9 + 3.877632e6 + 0.426952e9 + 3.930880e6,
     # profiles/fused_ws_full.md: rounds 1 + 2 of one step
     ("full", "pipelined", 0): 492070912 + 6069760 + 259748608 + 2402048,
 }
