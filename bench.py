@@ -77,7 +77,11 @@ FUSED_TRAFFIC_BYTES = {
     # profiles/fused_tm_room.md: rounds 1 + 2 of one step
     ("room", "serial", 4): 1.265874e9 + 3.877632e6 + 0.426952e9 + 3.930880e6,
     # profiles/fused_ws_full.md: rounds 1 + 2 of one step
-    ("full", "pipelined", 0): 492070912 + 6069760 + 259748608 + 2402048,
+    ("full", "pipelined", 0): 492390656 + 6461440 + 260415232 + 3136768,
+    # profiles/fused_tm_paper_mixed_dram.md: outer and inner networks, rounds 1 + 2
+    ("paper", "serial", 4): 16448256 + 7936 + 26381312 + 13568 + 14667776 + 7680 + 417536 + 0,
+    # profiles/fused_tm_paper_mixed_dram.md: rounds 1 + 2 of one step
+    ("mixed", "serial", 4): 301272576 + 3251712 + 60928000 + 7936,
 }
 
 
