@@ -764,8 +764,10 @@ def run_primary(args):
         return tot, subs
 
     with ClockSampler(0) as clk:
+        torch.cuda.profiler.start()
         nif_ms, subs = timed(lambda ev=None: pipe.primary_step(ev=ev), sub=True)
         bvh_ms, _ = timed(lambda: pipe.bvh_step())
+        torch.cuda.profiler.stop()
     clocks = clk.summary()
     pipe.check()
     nq = int(pipe._primary_buffers()["count"].item())
@@ -906,8 +908,10 @@ def run_render(args):
                 statistics.mean(e[1].elapsed_time(e[2]) for e in parts))
 
     with ClockSampler(0) as clk:
+        torch.cuda.profiler.start()
         nif_ms, nif_shadow_ms = timed(True)
         bvh_ms, bvh_shadow_ms = timed(False)
+        torch.cuda.profiler.stop()
     clocks = clk.summary()
     pipe.check()
     line = {
