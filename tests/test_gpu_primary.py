@@ -225,3 +225,26 @@ def test_pair_closest_hit_matches_brute_force():
     assert np.array_equal(t.cpu().numpy().view(np.uint32), to.view(np.uint32))
     assert np.array_equal(prim.cpu().numpy(), po)
     assert 0.2 < (po >= 0).mean() < 0.95
+
+
+def test_resolution_of_empty_lists_leaves_the_exact_answer():
+    rng = np.random.default_rng(65)
+    boxes = random_boxes_scene(rng, n_obj=3)
+    cfg = nif.NifConfig(res=[2], n_features=2, n_hidden=1, width=8, n_outputs=O)
+    model = nif.NifModel(cfg, torch.from_numpy(boxes).cuda(), torch.zeros(3 * 2 * 27 * 2).cuda(),
+                         torch.zeros(nif.NifModel.weight_count(cfg)).cuda())
+    rays = torch.from_numpy(synth.pack_rays(rng.uniform(-3, 3, (100, 3)), synth.unit_vectors(rng, 100),
+                                            0.0, np.inf)).cuda()
+    t0 = torch.rand(100, device="cuda")
+    t = t0.clone()
+    e = torch.empty(0, dtype=torch.int32, device="cuda")
+    goff = torch.zeros(2, dtype=torch.int64, device="cuda")
+    nif.primary_resolve(model, rays, e, e, goff, 0, torch.empty((0, O), device="cuda"), t=t)
+    torch.cuda.synchronize()
+    assert torch.equal(t, t0)
+    # the shadow-ray descriptor (one output) is refused by the resolution
+    m1 = nif.NifModel(nif.NifConfig(res=[2], n_features=2, n_hidden=1, width=8), model.obj_aabb,
+                      model.grids, torch.zeros(nif.NifModel.weight_count(nif.NifConfig(res=[2], n_hidden=1,
+                                                                                         width=8))).cuda())
+    with pytest.raises(L.NifError):
+        nif.primary_resolve(m1, rays, e, e, goff, 0, torch.empty((0, O), device="cuda"))

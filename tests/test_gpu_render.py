@@ -64,3 +64,39 @@ def test_samples_and_shading_match_oracle_bit_for_bit(spp, importance):
     # the case is not degenerate: lit, shadowed and unlit samples, every light picked
     assert (of > 0).mean() > 0.3 and (occ[of > 0] == 1).mean() > 0.02 and (of == 0).any()
     assert len(np.unique(ok)) == len(lights)
+
+
+def test_empty_calls_and_or_cast():
+    """Zero-sized calls queue nothing; the OR-ing cast leaves set bits set,
+    skips those rays and ORs the rest, so it equals the overwriting cast OR
+    the mask it started from."""
+    from paper_2306_07191_gb300 import _lib as L
+    sc, lights, cam, rng = _scene(seed=73)
+    dev = "cuda"
+    verts, tris = torch.from_numpy(sc.verts).to(dev), torch.from_numpy(sc.tris).to(dev)
+    bvh = nif.BVH(verts, tris)
+    z = torch.empty(0, device=dev)
+    zi = torch.empty(0, dtype=torch.int32, device=dev)
+    lt = torch.from_numpy(lights).to(dev)
+    cdf = nif.light_cdf(torch.ones(len(lights), device=dev))
+    rays0, f0 = nif.light_samples(torch.empty((0, 8), device=dev), z, zi, verts, tris, lt, cdf,
+                                  torch.empty((0, 3), device=dev), 2)
+    assert rays0.shape == (0, 8) and f0.shape == (0,)
+    nif.shade(f0, torch.zeros(1, dtype=torch.int32, device=dev), 0, 2)
+    nif.clear_bits(torch.zeros(1, dtype=torch.int32, device=dev), 0)
+    with pytest.raises(L.NifError):
+        nif.light_cdf(torch.empty(0, device=dev))
+    # OR cast against the overwriting cast
+    n = cam.shape[0]
+    r_np = synth.pack_rays(cam[:, 0:3], cam[:, 4:7], 0.0, np.inf)
+    r_np[:, 7] = rng.uniform(1.0, 9.0, n)  # some segments end before any surface
+    rays = torch.from_numpy(r_np).to(dev)
+    start = torch.from_numpy(rng.integers(0, 2**31, size=(n + 31) // 32, dtype=np.int64).astype(np.int32)).to(dev)
+    ored = start.clone()
+    bvh.cast_shadow(rays, out=ored, or_into=True)
+    plain = bvh.cast_shadow(rays)
+    torch.cuda.synchronize()
+    a = nif.bits_to_bool(ored, n)
+    b = nif.bits_to_bool(plain, n) | nif.bits_to_bool(start, n)
+    hit = nif.bits_to_bool(plain, n)
+    assert torch.equal(a, b) and 0.05 < float(hit.float().mean()) < 0.95
