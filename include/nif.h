@@ -354,10 +354,11 @@ nif_status nif_infer_queries(const nif_model_desc* m, const nif_ray* d_rays, int
                              size_t ws_bytes, void* stream);
 
 /* The whole query (a0-a4) with the workspace from nif_workspace_size, in two
- * rounds (the early-out of Sec. 4.1's ray-cast stage): round 1 queries each
- * ray's nearest pair (smallest entry parameter) of the rays whose bit in
- * d_occluded_bits is not already set; round 2 queries the other pairs of the
- * rays still unoccluded.  A ray is occluded iff one of its pairs has z < 0,
+ * rounds (the early-out of Sec. 4.1's ray-cast stage): round 1 queries one
+ * pair of each ray whose bit in d_occluded_bits is not already set -- its
+ * nearest outer pair (smallest entry parameter), or its inner pair when it
+ * has no outer one; round 2 queries the other pairs of the rays still
+ * unoccluded.  A ray is occluded iff one of its pairs has z < 0,
  * so d_occluded_bits (OR-ed into as above) ends exactly as querying every
  * pair with nif_frontend + nif_infer_queries would leave it. */
 nif_status nif_infer(const nif_model_desc* m, const void* d_tlas, const nif_ray* d_rays,
@@ -369,8 +370,8 @@ nif_status nif_infer(const nif_model_desc* m, const void* d_tlas, const nif_ray*
  * and d_ws of at least nif_workspace_size(m, n, 0) bytes, the same buffer for
  * both calls on one stream.
  * nif_frontend_nearest: each ray whose bit in d_occluded_bits is clear gets
- *   its nearest pair (smallest entry parameter) listed; *d_count = pairs
- *   listed.  Every pair of those rays is remembered in d_ws for round 2.
+ *   one pair listed, its nearest outer pair (else its inner pair); *d_count =
+ *   pairs listed.  Every pair of those rays is remembered in d_ws for round 2.
  * nif_frontend_rest (after the round-1 pairs have been answered into
  *   d_occluded_bits): the other pairs of the rays still unoccluded, written
  *   from index *d_count_nearest on; d_group_off gets their absolute group

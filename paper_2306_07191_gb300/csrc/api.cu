@@ -609,8 +609,8 @@ nif_status nif_primary_resolve(const nif_model_desc* m, const nif_ray* d_rays, i
   NIF_CHECK_ARG(n_rays >= 0 && nq_max >= 0, "nif_primary_resolve: negative size");
   NIF_CHECK_ARG(nq_max < (int64_t(1) << 32), "nif_primary_resolve: at most 2^32 - 1 queries");
   if (n_rays == 0) return NIF_OK;
-  NIF_CHECK_ARG(d_rays && d_ray_id && d_qobj && d_group_off && d_out && d_key && d_t && d_normal,
-                "nif_primary_resolve: null pointer");
+  NIF_CHECK_ARG(d_rays && d_group_off && d_key && d_t && d_normal, "nif_primary_resolve: null pointer");
+  NIF_CHECK_ARG(nq_max == 0 || (d_ray_id && d_qobj && d_out), "nif_primary_resolve: null query list");
   p.n_rays = n_rays;
   return launch_primary_resolve(p, d_rays, n_rays, d_ray_id, d_qobj, d_group_off, nq_max, d_out,
                                 reinterpret_cast<unsigned long long*>(d_key), d_t, d_normal, d_winner,

@@ -246,9 +246,9 @@ __global__ void __launch_bounds__(128) k_front_scatter(NifParams p, const char* 
 }
 
 // ------------------------------------------------- front end, two rounds
-// nif_infer answers each ray's nearest pair first (smallest entry parameter:
-// the first object box its segment enters) and then only the other pairs of
-// the rays still unoccluded.  A ray is occluded iff some pair says so (or the
+// nif_infer answers one pair per ray first (its nearest outer pair, else its
+// inner pair; see round1_before) and then only the other pairs of the rays
+// still unoccluded.  A ray is occluded iff some pair says so (or the
 // caller's bits already say so), so skipping pairs of occluded rays leaves
 // every output bit as querying all pairs would.
 
@@ -256,8 +256,18 @@ __device__ __forceinline__ bool ray_occluded(const uint32_t* bits, int64_t i) {
   return (__ldg(bits + (i >> 5)) >> (i & 31)) & 1u;
 }
 
+// The pair round 1 queries for a ray: its nearest outer pair (smallest entry
+// parameter), else its inner pair.  (A shadow ray leaves its own object's
+// surface, so the inner pair is the nearest; the outer pairs are the other
+// objects between the shading point and the light.)
+__device__ __forceinline__ bool round1_before(bool inner, float tk, bool b_inner, float bt, bool none) {
+  if (none) return true;
+  if (inner != b_inner) return !inner;
+  return tk < bt;
+}
+
 // The pairs of a ray with more than kSlots of them, by traversing again, and
-// the index of its nearest pair; returns the pair count.
+// the index of the pair round 1 queries; returns the pair count.
 template <bool kTlas>
 __device__ __forceinline__ int ray_pairs_traverse(const NifParams& p, const char* tlas,
                                                   const nif_ray* rays, int64_t i,
@@ -265,12 +275,14 @@ __device__ __forceinline__ int ray_pairs_traverse(const NifParams& p, const char
                                                   DevError* err) {
   int nh = 0;
   float bt = INFINITY;
+  bool binner = true;
   first = 0;
   const nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
   for_each_pair<kTlas>(p, tlas, tlas_header(tlas), r, [&](uint32_t obj, bool inner, float tk) {
     if (nh < kMaxHits) {
-      if (tk < bt) {
+      if (round1_before(inner, tk, binner, bt, nh == 0)) {
         bt = tk;
+        binner = inner;
         first = nh;
       }
       hits[nh++] = obj | (inner ? NIF_QUERY_INNER : 0u);
@@ -282,8 +294,8 @@ __device__ __forceinline__ int ray_pairs_traverse(const NifParams& p, const char
 }
 
 // Round 1, count: traverses the top level once per ray not already occluded,
-// keeps the first kSlots pairs in slots with the nearest one's index, and
-// counts the nearest pairs per bucket.
+// keeps the first kSlots pairs in slots with the index of the pair round 1
+// queries, and counts those pairs per bucket.
 template <bool kTlas>
 __global__ void __launch_bounds__(128) k_front_count_first(NifParams p, const char* tlas,
                                                            const nif_ray* rays, int64_t n,
@@ -293,6 +305,7 @@ __global__ void __launch_bounds__(128) k_front_count_first(NifParams p, const ch
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int nh = 0, best = 0;
   float bt = INFINITY;
+  bool binner = true;
   uint32_t bq = 0;
   if (i < n) {
     if (!ray_occluded(bits, i)) {
@@ -300,8 +313,9 @@ __global__ void __launch_bounds__(128) k_front_count_first(NifParams p, const ch
       for_each_pair<kTlas>(p, tlas, tlas_header(tlas), r, [&](uint32_t obj, bool inner, float tk) {
         const uint32_t q = obj | (inner ? NIF_QUERY_INNER : 0u);
         if (nh < kSlots) slots[static_cast<int64_t>(nh) * n + i] = q;
-        if (tk < bt) {
+        if (round1_before(inner, tk, binner, bt, nh == 0)) {
           bt = tk;
+          binner = inner;
           best = nh;
           bq = q;
         }
@@ -314,7 +328,7 @@ __global__ void __launch_bounds__(128) k_front_count_first(NifParams p, const ch
   warp_claim(g_count, nh > 0 ? bucket_of_q(p, bq) : 0, nh > 0);
 }
 
-// Round 1, scatter: each ray's nearest pair into its bucket's range.
+// Round 1, scatter: each ray's round-1 pair into its bucket's range.
 template <bool kTlas>
 __global__ void __launch_bounds__(128) k_front_scatter_first(NifParams p, const char* tlas,
                                                              const nif_ray* rays, int64_t n,

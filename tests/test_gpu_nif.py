@@ -375,9 +375,9 @@ def test_schedules_agree_on_grouped_networks(mlp_dt):
 
 @pytest.mark.parametrize("mlp_dt,sched", [("f32", 0), ("f16", SER), ("f16", PIPE), ("bf16", 0)])
 def test_two_round_infer_equals_all_pairs(mlp_dt, sched):
-    """nif_infer's early-out (each ray's nearest pair first, then the other
-    pairs of rays still unoccluded) leaves exactly the bits of querying every
-    pair; rays already occluded on entry are not queried at all."""
+    """nif_infer's early-out (one pair per ray first, then the other pairs of
+    rays still unoccluded) leaves exactly the bits of querying every pair;
+    rays already occluded on entry are not queried at all."""
     rng = np.random.default_rng(71)
     boxes = random_boxes_scene(rng, n_obj=12, extent=3.0)
     res = [4, 8, 16, 32]
@@ -406,7 +406,7 @@ def test_two_round_infer_equals_all_pairs(mlp_dt, sched):
     assert np.array_equal(va, vt)
     r = ray_id[:nq].cpu().numpy()
     with_pair = np.unique(r)
-    assert counts[0] == len(with_pair)            # one nearest pair per ray with a pair
+    assert counts[0] == len(with_pair)            # one round-1 pair per ray with a pair
     assert counts[0] < counts[1] < nq             # round 2 skipped pairs of occluded rays
     assert va.any() and (~va[with_pair]).any()
     pre = rng.uniform(size=n) < 0.3
@@ -420,3 +420,59 @@ def test_two_round_infer_equals_all_pairs(mlp_dt, sched):
     assert np.array_equal(vp, va | pre)
     c2 = model.infer_query_counts(n).cpu().numpy()
     assert c2[0] == len(np.setdiff1d(with_pair, np.nonzero(pre)[0]))
+
+
+def test_round_one_takes_the_nearest_outer_pair():
+    """nif_frontend_nearest lists, per ray, its nearest outer pair (smallest
+    entry parameter), or its inner pair when it has no outer one; the
+    choice is checked against the oracle's query set and FP32 slab entries."""
+    import ctypes
+    rng = np.random.default_rng(75)
+    boxes = random_boxes_scene(rng, n_obj=10, extent=3.0)
+    n = 20000
+    o = rng.uniform(-4, 4, size=(n, 3))
+    ki = rng.integers(0, 10, n // 2)
+    o[: n // 2] = boxes[ki, :3] + rng.uniform(0.05, 0.95, size=(n // 2, 3)) * (boxes[ki, 3:] - boxes[ki, :3])
+    rays = synth.pack_rays(o, synth.unit_vectors(rng, n), 1e-3, np.inf)
+    cfg = nif.NifConfig(res=[2], n_features=1, net_mode=L.NIF_NETS_CLASS)
+    model = nif.NifModel(cfg, torch.from_numpy(boxes).cuda(), torch.zeros(10 * 2 * 27).cuda(),
+                         torch.zeros(2 * nif.NifModel.weight_count(cfg)).cuda())
+    rays_t = torch.from_numpy(rays).cuda()
+    tlas = nif.BVH.from_boxes(torch.from_numpy(boxes).cuda())
+    max_q = 8 * n
+    ray_id = torch.empty(max_q, dtype=torch.int32, device="cuda")
+    qobj = torch.empty(max_q, dtype=torch.int32, device="cuda")
+    goff = torch.empty(3, dtype=torch.int64, device="cuda")
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    bits = nif.empty_bits(n)
+    ws = model.workspace(max_q, n)
+    d = model.desc()
+    vp = ctypes.c_void_p
+    L.call("nif_frontend_nearest", ctypes.byref(d), vp(tlas.buf.data_ptr()), vp(rays_t.data_ptr()), n,
+           vp(bits.data_ptr()), vp(ray_id.data_ptr()), vp(qobj.data_ptr()), max_q, vp(goff.data_ptr()),
+           vp(count.data_ptr()), vp(ws.data_ptr()), ws.numel(), nif._stream())
+    torch.cuda.synchronize()
+    model.check(ws)
+    nq = int(count.item())
+    r, ob, inn = _query_arrays(ray_id, qobj, nq)
+    rr, oo, ii = onif.queries(rays, boxes)
+    assert nq == len(np.unique(rr)) and len(np.unique(r)) == nq
+    chosen = {int(a): (int(b), bool(c)) for a, b, c in zip(r, ob, inn)}
+    entry = np.full(len(rr), np.inf)
+    for k in range(len(boxes)):
+        sel = np.nonzero(oo == k)[0]
+        entry[sel] = onif.slab_fp32(rays[rr[sel]], boxes[k])[1]
+    n_outer_first = 0
+    for ray in np.unique(rr):
+        sel = np.nonzero(rr == ray)[0]
+        obj, inner = chosen[int(ray)]
+        outer = sel[~ii[sel]]
+        if len(outer):
+            assert not inner, ray
+            best = entry[outer].min()
+            got = entry[sel[(oo[sel] == obj) & ~ii[sel]]][0]
+            assert got <= best * (1 + 1e-5) + 1e-6, (ray, got, best)
+            n_outer_first += int(ii[sel].any())
+        else:
+            assert inner and len(sel) == 1
+    assert n_outer_first > 1000  # rays with both kinds took the outer pair
