@@ -428,7 +428,18 @@ typedef struct nif_optim_desc {
   int32_t step; /* number of completed steps; nif_train_step increments it */
   float* d_w_master; float* d_w_grad; float* d_w_m; float* d_w_v; /* [n_nets*P] */
   float* d_g_master; float* d_g_grad; float* d_g_m; float* d_g_v; /* [n_obj*2*V*F] */
+  /* Deterministic gradients (0 = off): the weight gradient is summed over
+   * tiles in tile order and the grid gradient per latent in pair order
+   * (after a stable sort of (latent, value) records) instead of by FP32
+   * atomics, so a step gives the same bits on every run, and a run resumed
+   * from nif_state_save continues bit for bit.  Needs d_det_ws of
+   * nif_deterministic_workspace_size(m, nq) bytes. */
+  int32_t deterministic;
+  void* d_det_ws;
+  size_t det_ws_bytes;
 } nif_optim_desc;
+
+size_t nif_deterministic_workspace_size(const nif_model_desc* m, int64_t nq);
 
 /* Forward for training (FP32 weights and grids on the CUDA cores): per query
  * the outputs d_z[q][O] (the logit d_z[q] when O = 1) and the saved activations d_saved (nif_saved_size bytes,

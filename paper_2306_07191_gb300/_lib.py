@@ -54,6 +54,7 @@ class OptimDesc(ctypes.Structure):
         ("step", i32),
         ("d_w_master", P), ("d_w_grad", P), ("d_w_m", P), ("d_w_v", P),
         ("d_g_master", P), ("d_g_grad", P), ("d_g_m", P), ("d_g_v", P),
+        ("deterministic", i32), ("d_det_ws", P), ("det_ws_bytes", size_t),
     ]
 
 
@@ -83,6 +84,7 @@ SIGNATURES = {
     "nif_shadow_rays": (i32, [P, P, i64, i32, P, i32, f32, P, P]),
     "nif_workspace_size": (size_t, [MD, i64, i64]),
     "nif_train_workspace_size": (size_t, [MD, i64]),
+    "nif_deterministic_workspace_size": (size_t, [MD, i64]),
     "nif_check": (i32, [P, ctypes.POINTER(i64), P]),
     "nif_frontend": (i32, [MD, P, P, i64, P, P, i64, P, P, P, size_t, P]),
     "nif_encode": (i32, [MD, P, P, P, i64, P, i32, P]),

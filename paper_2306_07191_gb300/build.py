@@ -24,6 +24,7 @@ UNITS = {
     "nif_tc.cu": [],
     "api.cu": [],
     "noalloc.cu": [],
+    "det.cu": [],
 }
 
 

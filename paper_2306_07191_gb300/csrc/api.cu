@@ -286,6 +286,40 @@ size_t nif_workspace_size(const nif_model_desc* m, int64_t max_rays, int64_t max
   return infer_layout(p, nullptr, max_queries + 256, max_rays).bytes;
 }
 
+// Deterministic scratch: per-tile weight slices, grid records, sort buffers.
+struct DetWs {
+  float* part;
+  uint32_t* rkey;
+  float* rval;
+  void* sort;
+  size_t sort_bytes;
+  size_t bytes;
+};
+
+static DetWs det_layout(const NifParams& p, void* base, int64_t nq) {
+  DetWs w{};
+  char* b = static_cast<char*>(base);
+  size_t o = 0;
+  w.part = reinterpret_cast<float*>(b + o);
+  o += align_up(static_cast<size_t>(mlp_tiles_max(p, nq)) * p.P * 4, 256);
+  const int64_t n_rec = nq * grid_taps_per_pair(p);
+  w.rkey = reinterpret_cast<uint32_t*>(b + o);
+  o += align_up(static_cast<size_t>(n_rec) * 4, 256);
+  w.rval = reinterpret_cast<float*>(b + o);
+  o += align_up(static_cast<size_t>(n_rec) * 4, 256);
+  w.sort = b + o;
+  w.sort_bytes = det_sort_scratch_bytes(n_rec);
+  o += w.sort_bytes;
+  w.bytes = o;
+  return w;
+}
+
+size_t nif_deterministic_workspace_size(const nif_model_desc* m, int64_t nq) {
+  NifParams p;
+  if (make_params(m, &p) != NIF_OK || nq < 0) return 0;
+  return det_layout(p, nullptr, nq).bytes;
+}
+
 size_t nif_train_workspace_size(const nif_model_desc* m, int64_t nq) {
   NifParams p;
   if (make_params(m, &p) != NIF_OK || nq < 0) return 0;
@@ -577,10 +611,30 @@ nif_status nif_train_step_aux(nif_model_desc* m, nif_optim_desc* o, const nif_ra
   s = p.O == 1 ? launch_loss(w.z, d_label, nq, o->loss_scale, w.dz, d_loss, st)
                : launch_loss_aux(w.z, d_label, d_aux, nq, p.O, o->loss_scale, w.dz, d_loss, st);
   if (s != NIF_OK) return s;
-  s = launch_bwd_f32(pm, d_group_off, nq, w.saved, w.dz, o->d_w_grad, w.dx, st);
-  if (s != NIF_OK) return s;
-  s = launch_grid_bwd(pm, d_rays, d_ray_id, d_qobj, nq, w.dx, nq, o->d_g_grad, st);
-  if (s != NIF_OK) return s;
+  if (o->deterministic) {
+    DetWs dw = det_layout(p, o->d_det_ws, nq);
+    if (!o->d_det_ws || o->det_ws_bytes < dw.bytes)
+      return fail(NIF_ERR_WORKSPACE, "nif_train_step: deterministic workspace too small (%zu < %zu)",
+                  o->det_ws_bytes, dw.bytes);
+    const int64_t total = static_cast<int64_t>(p.n_obj) * p.obj_elems;
+    if (total >= 0xffffffffLL)
+      return fail(NIF_ERR_UNSUPPORTED, "deterministic grid gradient: %lld latents exceed 32-bit ids",
+                  (long long)total);
+    s = launch_bwd_f32(pm, d_group_off, nq, w.saved, w.dz, o->d_w_grad, w.dx, st, dw.part);
+    if (s != NIF_OK) return s;
+    s = launch_reduce_tiles(pm, d_group_off, dw.part, o->d_w_grad, st);
+    if (s != NIF_OK) return s;
+    s = launch_grid_bwd(pm, d_rays, d_ray_id, d_qobj, nq, w.dx, nq, o->d_g_grad, st, dw.rkey, dw.rval);
+    if (s != NIF_OK) return s;
+    s = launch_sum_records(dw.rkey, dw.rval, nq * grid_taps_per_pair(p), o->d_g_grad, dw.sort, dw.sort_bytes,
+                           st);
+    if (s != NIF_OK) return s;
+  } else {
+    s = launch_bwd_f32(pm, d_group_off, nq, w.saved, w.dz, o->d_w_grad, w.dx, st);
+    if (s != NIF_OK) return s;
+    s = launch_grid_bwd(pm, d_rays, d_ray_id, d_qobj, nq, w.dx, nq, o->d_g_grad, st);
+    if (s != NIF_OK) return s;
+  }
   const int step = o->step + 1;
   const int64_t nw = (int64_t)p.n_nets * p.P;
   const int64_t ng = (int64_t)p.n_obj * p.obj_elems;

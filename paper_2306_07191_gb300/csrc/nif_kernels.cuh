@@ -63,11 +63,27 @@ nif_status launch_primary_resolve(const NifParams& p, const nif_ray* rays, int64
                                   const uint32_t* ray_id, const uint32_t* qobj, const int64_t* goff,
                                   int64_t nq_max, const float* out, unsigned long long* key, float* t,
                                   float* normal, int32_t* winner, cudaStream_t st);
+// part (nullable): per-tile weight-gradient slices [mlp_tiles_max][P] for the
+// deterministic mode, summed by launch_reduce_tiles instead of atomics.
 nif_status launch_bwd_f32(const NifParams& p, const int64_t* goff, int64_t nq, const float* saved,
-                          const float* dz, float* wgrad, float* dx, cudaStream_t st);
+                          const float* dz, float* wgrad, float* dx, cudaStream_t st,
+                          float* part = nullptr);
+// rkey/rval (nullable): [nq][grid_taps_per_pair] (element, value) records for
+// the deterministic mode instead of atomics.
 nif_status launch_grid_bwd(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
                            const uint32_t* qobj, int64_t nq, const float* dx, int64_t ld,
-                           float* ggrad, cudaStream_t st);
+                           float* ggrad, cudaStream_t st, uint32_t* rkey = nullptr,
+                           float* rval = nullptr);
+int grid_taps_per_pair(const NifParams& p);
+int64_t mlp_tiles_max(const NifParams& p, int64_t nq);
+// Deterministic reductions: the tile slices of launch_bwd_f32 summed in tile
+// order into wgrad; the grid records stably sorted by element and summed per
+// element in record order into ggrad.  `scratch` holds the sort buffers.
+nif_status launch_reduce_tiles(const NifParams& p, const int64_t* goff, const float* part, float* wgrad,
+                               cudaStream_t st);
+size_t det_sort_scratch_bytes(int64_t n_records);
+nif_status launch_sum_records(uint32_t* rkey, float* rval, int64_t n_records, float* ggrad, void* scratch,
+                              size_t scratch_bytes, cudaStream_t st);
 // dst[i] = src[i] converted to dtype (NIF_F32, NIF_F16 or NIF_BF16).
 nif_status launch_cast(const float* src, int64_t n, void* dst, int dtype, cudaStream_t st);
 // err (nullable): a non-finite updated parameter is recorded as

@@ -595,7 +595,8 @@ __global__ void k_loss_aux(const float* z, const uint8_t* label, const float* au
 // (W staged in chunks of kJb input features, transposed to [j][k]).
 __global__ void __launch_bounds__(kFThreads) k_mlp_bwd_f32(NifParams p, const int64_t* goff,
                                                            const float* saved, int64_t ld_saved,
-                                                           const float* dz, float* wgrad, float* dx) {
+                                                           const float* dz, float* wgrad, float* dx,
+                                                           float* part) {
   extern __shared__ __align__(16) float s_act[];
   __shared__ int64_t s_pre[kMaxGroups + 1];
   const int W = p.width, K = p.K, H = p.n_hidden;
@@ -633,6 +634,13 @@ __global__ void __launch_bounds__(kFThreads) k_mlp_bwd_f32(NifParams p, const in
     __syncthreads();
     const float* w = wall + static_cast<int64_t>(g) * p.P;
     float* gw = wgrad + static_cast<int64_t>(g) * p.P;
+    // deterministic mode: the tile's weight gradient goes to its own slice of
+    // `part` (every element written once), summed over tiles in order later
+    float* tp = part ? part + t * p.P : nullptr;
+    auto add_w = [&](int64_t e, float v) {
+      if (tp) tp[e] = v;
+      else atomicAdd(gw + e, v);
+    };
     int64_t woff[NIF_MAX_LEVELS + 1];
     {
       int64_t o = 0;
@@ -659,7 +667,7 @@ __global__ void __launch_bounds__(kFThreads) k_mlp_bwd_f32(NifParams p, const in
       const int o = e / fan_last, j = e % fan_last;
       float acc = 0.f;
       for (int c = 0; c < nrow; ++c) acc = fmaf(dzs[o * kLq + c], hl[j * kLq + c], acc);
-      atomicAdd(&gw[woff[H] + e], acc);
+      add_w(woff[H] + e, acc);
     }
     for (int e = tid; e < fan_last * kTile; e += kFThreads) {
       const int j = e / kTile, c = e % kTile;
@@ -706,7 +714,7 @@ __global__ void __launch_bounds__(kFThreads) k_mlp_bwd_f32(NifParams p, const in
 #pragma unroll
           for (int b = 0; b < 4; ++b)
             if (j0 + a < W && k0 + b < fan_in)
-              atomicAdd(&gw[woff[l] + static_cast<int64_t>(j0 + a) * fan_in + k0 + b], acc[a][b]);
+              add_w(woff[l] + static_cast<int64_t>(j0 + a) * fan_in + k0 + b, acc[a][b]);
       }
       // dh_prev[k][q] = sum_j da[j][q] W_l[j][k], in passes of kJb inputs
       for (int kb = 0; kb < fan_in; kb += kJb) {
@@ -752,9 +760,35 @@ template <int F, typename TG>
 __global__ void __launch_bounds__(128) k_grid_bwd(NifParams p, const nif_ray* rays,
                                                   const uint32_t* ray_id, const uint32_t* qobj,
                                                   int64_t nq, const float* dx, int64_t ld,
-                                                  float* ggrad) {
+                                                  float* ggrad, uint32_t* rkey, float* rval,
+                                                  int max_taps) {
   int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (q >= nq || !check_query(p, ray_id, qobj, q)) return;
+  if (q >= nq) return;
+  // deterministic mode: each tap becomes a (grid element, value) record in
+  // the pair's max_taps slots (unused slots keep the sentinel key), summed
+  // per element in pair order after a stable sort
+  int64_t slot = q * max_taps;
+  const int64_t slot_end = slot + max_taps;
+  auto add = [&](float* dst, float v) {
+    if (rkey) {
+      rkey[slot] = static_cast<uint32_t>(dst - ggrad);
+      rval[slot] = v;
+      ++slot;
+    } else {
+      atomicAdd(dst, v);
+    }
+  };
+  auto finish = [&]() {
+    if (rkey)
+      for (; slot < slot_end; ++slot) {
+        rkey[slot] = 0xffffffffu;
+        rval[slot] = 0.f;
+      }
+  };
+  if (!check_query(p, ray_id, qobj, q)) {
+    finish();
+    return;
+  }
   nif_ray r = load_nif_ray(rays, ray_id[q]);
   uint32_t obj = qobj[q] & 0x7fffffffu;
   float bx[6];
@@ -773,8 +807,8 @@ __global__ void __launch_bounds__(128) k_grid_bwd(NifParams p, const nif_ray* ra
     for (int f = 0; f < Fs; ++f) {
       const float a = dx[static_cast<int64_t>(f) * ld + q], b = dx[static_cast<int64_t>(Fs + f) * ld + q];
       for (int c = 0; c < 4; ++c) {
-        if (tp.w[c] != 0.f) atomicAdd(g + static_cast<int64_t>(tp.idx[c]) * Fs + f, tp.w[c] * a);
-        if (td.w[c] != 0.f) atomicAdd(g + t2 + static_cast<int64_t>(td.idx[c]) * Fs + f, td.w[c] * b);
+        if (tp.w[c] != 0.f) add(g + static_cast<int64_t>(tp.idx[c]) * Fs + f, tp.w[c] * a);
+        if (td.w[c] != 0.f) add(g + t2 + static_cast<int64_t>(td.idx[c]) * Fs + f, td.w[c] * b);
       }
     }
     if (p.enc == NIF_ENC_SPHERICAL_INNER) {
@@ -784,9 +818,10 @@ __global__ void __launch_bounds__(128) k_grid_bwd(NifParams p, const nif_ray* ra
       for (int f = 0; f < p.F1; ++f) {
         const float a = dx[static_cast<int64_t>(2 * Fs + f) * ld + q];
         for (int c = 0; c < 2; ++c)
-          if (w1[c] != 0.f) atomicAdd(g + 2 * t2 + static_cast<int64_t>(i1[c]) * p.F1 + f, w1[c] * a);
+          if (w1[c] != 0.f) add(g + 2 * t2 + static_cast<int64_t>(i1[c]) * p.F1 + f, w1[c] * a);
       }
     }
+    finish();
     return;
   }
   QueryPoints pts;
@@ -803,14 +838,20 @@ __global__ void __launch_bounds__(128) k_grid_bwd(NifParams p, const nif_ray* ra
       for (int c = 0; c < 8; ++c) {
         if (t.w[c] == 0.f) continue;  // a point on a cell face: nothing to add
         if constexpr (F == 2) {
-          atomicAdd(reinterpret_cast<float2*>(g) + t.idx[c], make_float2(t.w[c] * d[0], t.w[c] * d[1]));
+          if (rkey) {
+            add(g + static_cast<int64_t>(t.idx[c]) * 2, t.w[c] * d[0]);
+            add(g + static_cast<int64_t>(t.idx[c]) * 2 + 1, t.w[c] * d[1]);
+          } else {
+            atomicAdd(reinterpret_cast<float2*>(g) + t.idx[c], make_float2(t.w[c] * d[0], t.w[c] * d[1]));
+          }
         } else {
 #pragma unroll
-          for (int f = 0; f < F; ++f) atomicAdd(g + static_cast<int64_t>(t.idx[c]) * F + f, t.w[c] * d[f]);
+          for (int f = 0; f < F; ++f) add(g + static_cast<int64_t>(t.idx[c]) * F + f, t.w[c] * d[f]);
         }
       }
     }
   }
+  finish();
 }
 
 // ------------------------------------------------------------------- Adam
@@ -1197,24 +1238,59 @@ nif_status launch_primary_resolve(const NifParams& p, const nif_ray* rays, int64
 }
 
 nif_status launch_bwd_f32(const NifParams& p, const int64_t* goff, int64_t nq, const float* saved,
-                          const float* dz, float* wgrad, float* dx, cudaStream_t st) {
+                          const float* dz, float* wgrad, float* dx, cudaStream_t st, float* part) {
   const int maxf = round4(p.K > p.width ? p.K : p.width), W4 = round4(p.width);
   const size_t sh = sizeof(float) * (static_cast<size_t>(kLq) * (round4(p.K) + p.n_hidden * W4 + W4 + maxf) +
                                      static_cast<size_t>(W4) * (kJb + 4));
   if (sh > 220 * 1024) return fail(NIF_ERR_UNSUPPORTED, "mlp backward: network too large for one tile");
   NIF_CUDA_TRY(ensure_smem(k_mlp_bwd_f32, sh));
   int blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(sm_count() * 2, ceil_div(nq, kTile) + p.n_nets)));
-  k_mlp_bwd_f32<<<blocks, kFThreads, sh, st>>>(p, goff, saved, nq, dz, wgrad, dx);
+  k_mlp_bwd_f32<<<blocks, kFThreads, sh, st>>>(p, goff, saved, nq, dz, wgrad, dx, part);
   NIF_LAUNCH_CHECK();
   return NIF_OK;
 }
 
+// Deterministic weight gradient: per network g and weight e, the tiles'
+// slices summed in tile order.
+__global__ void __launch_bounds__(256) k_reduce_tiles(NifParams p, const int64_t* goff, const float* part,
+                                                      float* wgrad) {
+  __shared__ int64_t s_pre[kMaxGroups + 1];
+  build_tile_prefix(goff, p.n_nets, kTile, s_pre);
+  const int64_t total = static_cast<int64_t>(p.n_nets) * p.P;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int g = static_cast<int>(i / p.P);
+    const int64_t e = i % p.P;
+    float s = 0.f;
+    for (int64_t t = s_pre[g]; t < s_pre[g + 1]; ++t) s += part[t * p.P + e];
+    wgrad[i] += s;
+  }
+}
+
+nif_status launch_reduce_tiles(const NifParams& p, const int64_t* goff, const float* part, float* wgrad,
+                               cudaStream_t st) {
+  const int64_t total = static_cast<int64_t>(p.n_nets) * p.P;
+  const int blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(total, 256), sm_count() * 8)));
+  k_reduce_tiles<<<blocks, 256, 0, st>>>(p, goff, part, wgrad);
+  NIF_LAUNCH_CHECK();
+  return NIF_OK;
+}
+
+int grid_taps_per_pair(const NifParams& p) {
+  if (p.enc != NIF_ENC_MULTIRES) return 8 * p.F + (p.enc == NIF_ENC_SPHERICAL_INNER ? 2 * p.F1 : 0);
+  return 3 * p.L * 8 * p.F;
+}
+
+int64_t mlp_tiles_max(const NifParams& p, int64_t nq) { return ceil_div(nq, kTile) + p.n_nets; }
+
 nif_status launch_grid_bwd(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
                            const uint32_t* qobj, int64_t nq, const float* dx, int64_t ld,
-                           float* ggrad, cudaStream_t st) {
+                           float* ggrad, cudaStream_t st, uint32_t* rkey, float* rval) {
   if (nq == 0) return NIF_OK;
   int64_t blocks = ceil_div(nq, 128);
-  NIF_DISPATCH_FG(p, { k_grid_bwd<F, TG><<<blocks, 128, 0, st>>>(p, rays, ray_id, qobj, nq, dx, ld, ggrad); });
+  const int taps = grid_taps_per_pair(p);
+  NIF_DISPATCH_FG(p, { k_grid_bwd<F, TG><<<blocks, 128, 0, st>>>(p, rays, ray_id, qobj, nq, dx, ld, ggrad,
+                                                                  rkey, rval, taps); });
   NIF_LAUNCH_CHECK();
   return NIF_OK;
 }

@@ -330,7 +330,7 @@ class Trainer:
 
     def __init__(self, model: NifModel, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-15,
                  loss_scale=1.0, w_master: torch.Tensor | None = None,
-                 g_master: torch.Tensor | None = None):
+                 g_master: torch.Tensor | None = None, deterministic: bool = False):
         self.model = model
         dev = model.obj_aabb.device
         self.w_master = (w_master if w_master is not None else model.weights.float()).clone().contiguous()
@@ -345,6 +345,8 @@ class Trainer:
         self.o.lr, self.o.beta1, self.o.beta2, self.o.eps = lr, beta1, beta2, eps
         self.o.loss_scale = loss_scale
         self.o.step = 0
+        self.o.deterministic = int(deterministic)
+        self._det_ws = None
         for name in ("w_master", "w_grad", "w_m", "w_v", "g_master", "g_grad", "g_m", "g_v"):
             setattr(self.o, "d_" + name, getattr(self, name).data_ptr())
         self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
@@ -383,6 +385,12 @@ class Trainer:
         need = L.lib.nif_train_workspace_size(ctypes.byref(d), nq)
         if self._ws is None or self._ws.numel() < need:
             self._ws = torch.zeros(need, dtype=torch.uint8, device=rays.device)
+        if self.o.deterministic:
+            dn = L.lib.nif_deterministic_workspace_size(ctypes.byref(d), nq)
+            if self._det_ws is None or self._det_ws.numel() < dn:
+                self._det_ws = torch.empty(dn, dtype=torch.uint8, device=rays.device)
+            self.o.d_det_ws = self._det_ws.data_ptr()
+            self.o.det_ws_bytes = self._det_ws.numel()
         if aux is None:
             L.call("nif_train_step", ctypes.byref(d), ctypes.byref(self.o), _ptr(rays), _ptr(ray_id),
                    _ptr(qobj), _ptr(goff), _ptr(label), nq, _ptr(self.loss), _ptr(self._ws),
