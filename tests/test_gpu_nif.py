@@ -424,8 +424,9 @@ def test_two_round_infer_equals_all_pairs(mlp_dt, sched):
 
 def test_round_one_takes_the_nearest_outer_pair():
     """nif_frontend_nearest lists, per ray, its nearest outer pair (smallest
-    entry parameter), or its inner pair when it has no outer one; the
-    choice is checked against the oracle's query set and FP32 slab entries."""
+    entry parameter), or one of its inner pairs when it has no outer one;
+    the choice is checked against the oracle's query set and FP32 slab
+    entries."""
     import ctypes
     rng = np.random.default_rng(75)
     boxes = random_boxes_scene(rng, n_obj=10, extent=3.0)
@@ -473,6 +474,6 @@ def test_round_one_takes_the_nearest_outer_pair():
             got = entry[sel[(oo[sel] == obj) & ~ii[sel]]][0]
             assert got <= best * (1 + 1e-5) + 1e-6, (ray, got, best)
             n_outer_first += int(ii[sel].any())
-        else:
-            assert inner and len(sel) == 1
+        else:  # only inner pairs (the origin inside overlapping boxes): one of them
+            assert inner and obj in set(oo[sel].tolist())
     assert n_outer_first > 1000  # rays with both kinds took the outer pair
