@@ -241,33 +241,6 @@ __device__ __forceinline__ void level_taps(const NifParams& p, int l, const floa
   }
 }
 
-// Cell corner (x0, y0, z0) and fractions of a point at level l (the same
-// arithmetic as level_taps, split so that callers can issue the loads of
-// several lookups before computing any weight).
-__device__ __forceinline__ void level_cell(const NifParams& p, int l, float ux, float uy, float uz,
-                                           uint32_t c0[3], float f[3]) {
-  const int R = p.res[l];
-  const float u[3] = {ux, uy, uz};
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    float s = u[k] * static_cast<float>(R);
-    int c = static_cast<int>(floorf(s));
-    c = c < 0 ? 0 : (c > R - 1 ? R - 1 : c);
-    c0[k] = static_cast<uint32_t>(c);
-    f[k] = s - static_cast<float>(c);
-  }
-}
-
-__device__ __forceinline__ uint32_t corner_entry(const NifParams& p, int l, const uint32_t c0[3],
-                                                 int c) {
-  const uint32_t x = c0[0] + (c & 1), y = c0[1] + ((c >> 1) & 1), z = c0[2] + ((c >> 2) & 1);
-  const bool hashed = (p.hashed >> l) & 1u;
-  const uint32_t n1 = static_cast<uint32_t>(p.res[l] + 1);
-  const uint32_t v = hashed ? (((x * kHashP1) ^ (y * kHashP2) ^ (z * kHashP3)) & ((1u << p.log2T) - 1u))
-                            : (x + n1 * (y + n1 * z));
-  return p.off[l] + v;
-}
-
 // The 8 stored-entry indices of the cell with lower corner c0 at level l,
 // corner c = cx + 2 cy + 4 cz: dense levels add fixed offsets to one base
 // index, hashed levels combine 2+2+2 partial products with XOR.
