@@ -422,6 +422,11 @@ def run_ours(args):
         sched, occ, tune_ms = nif.autotune(fwd[0], lambda: pipe.query_step(tbits), also=fwd[1:],
                                            candidates=cands, key_extra=(pipe.n_rays, args.workload))
         log(f"autotuned fused kernel: schedule {sched}, {occ} CTAs/SM ({tune_ms})")
+    # the round-1 rule that queries fewer pairs on this frame
+    round1_pairs = pipe.tune_round1()
+    from paper_2306_07191_gb300.pipeline import ROUND1_NAME
+    round1 = ROUND1_NAME[pipe.front_model().cfg.round1]
+    log(f"round 1 takes each ray's {round1} pair ({round1_pairs})")
     n = pipe.n_rays
     rays = pipe.rays
     model = pipe.model
@@ -552,6 +557,7 @@ def run_ours(args):
                    "objects": cfg.n_obj, "nif_objects": pipe.n_obj, "triangles_nif": pipe.n_tris_nif,
                    "l2": "flushed (256 MB write) before every timed step",
                    "exact_cast": cfg.exact_cast, "cuda_graph": bool(graphs),
+                   "round1": round1, "round1_pairs": round1_pairs,
                    "fused_schedule": SCHED_NAME[pipe.forward_models()[0][0].cfg.schedule],
                    "fused_ctas_per_sm": pipe.forward_models()[0][0].cfg.ctas_per_sm, "autotune_ms": tune_ms,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -859,6 +865,9 @@ def run_render(args):
     cands = tuple(c for c in nif.SCHEDULE_CANDIDATES if c[0] == L.NIF_SCHED_SERIAL)
     sched, occ, tune_ms = nif.autotune(fwd[0], lambda: pipe.query_step(tbits), also=fwd[1:], candidates=cands,
                                        key_extra=(pipe.n_rays, "render"))
+    round1_pairs = pipe.tune_round1()
+    from paper_2306_07191_gb300.pipeline import ROUND1_NAME
+    round1 = ROUND1_NAME[pipe.front_model().cfg.round1]
     cam, u, spp = pipe.eval_camera, pipe.eval_u, pipe.cfg.render_spp
     n_pix, n = pipe.n_pix, pipe.n_rays
     lights, cdf = pipe._light_setup(), pipe._cdf["importance"]
@@ -921,7 +930,8 @@ def run_render(args):
         "config": {"workload": WORKLOADS["render"], "rays": n, "pixels": n_pix, "light_spp": spp,
                    "objects": pipe.n_obj, "triangles": pipe.n_tris,
                    "l2": "flushed (256 MB write) before every timed step", "fused_schedule": "serial",
-                   "fused_ctas_per_sm": occ, "autotune_ms": tune_ms, "parallelism": "single GPU"},
+                   "fused_ctas_per_sm": occ, "autotune_ms": tune_ms, "round1": round1,
+                   "round1_pairs": round1_pairs, "parallelism": "single GPU"},
         "bvh_rays_per_s": n / (bvh_shadow_ms * 1e-3), "bvh_ms_per_step": bvh_shadow_ms,
         "speedup_vs_bvh": bvh_shadow_ms / nif_shadow_ms,
         "frame_ms": {"nif": nif_ms, "bvh": bvh_ms},

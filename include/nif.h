@@ -144,7 +144,18 @@ typedef struct nif_model_desc {
   int32_t res_1d;        /* NIF_ENC_SPHERICAL_INNER: cells of the distance grid */
   int32_t n_features_1d; /* NIF_ENC_SPHERICAL_INNER: latents per distance cell */
   int32_t n_outputs;     /* output rows O, 0 or 1 = the occupancy logit only; at most 8 */
+  int32_t round1;        /* NIF_ROUND1_*: which pair nif_infer queries first per ray */
 } nif_model_desc;
+
+/* The pair of each ray that round 1 of nif_infer queries (every other pair
+ * of the rays still unoccluded follows in round 2; the mask is the same
+ * either way, only the work differs):
+ *   NIF_ROUND1_NEAREST - its nearest pair (smallest entry parameter);
+ *   NIF_ROUND1_OUTER   - its nearest outer pair, else an inner pair.  A
+ *                        shadow ray leaves its own object's surface, so its
+ *                        inner pair is the nearest; which rule answers more
+ *                        rays in round 1 depends on the scene and lights. */
+enum { NIF_ROUND1_NEAREST = 0, NIF_ROUND1_OUTER = 1 };
 
 /* Encodings of a query (the network input x):
  *   NIF_ENC_MULTIRES - the multi-resolution 3D grids described above.
@@ -355,9 +366,8 @@ nif_status nif_infer_queries(const nif_model_desc* m, const nif_ray* d_rays, int
 
 /* The whole query (a0-a4) with the workspace from nif_workspace_size, in two
  * rounds (the early-out of Sec. 4.1's ray-cast stage): round 1 queries one
- * pair of each ray whose bit in d_occluded_bits is not already set -- its
- * nearest outer pair (smallest entry parameter), or its inner pair when it
- * has no outer one; round 2 queries the other pairs of the rays still
+ * pair of each ray whose bit in d_occluded_bits is not already set (chosen
+ * by m->round1); round 2 queries the other pairs of the rays still
  * unoccluded.  A ray is occluded iff one of its pairs has z < 0,
  * so d_occluded_bits (OR-ed into as above) ends exactly as querying every
  * pair with nif_frontend + nif_infer_queries would leave it. */
@@ -370,8 +380,7 @@ nif_status nif_infer(const nif_model_desc* m, const void* d_tlas, const nif_ray*
  * and d_ws of at least nif_workspace_size(m, n, 0) bytes, the same buffer for
  * both calls on one stream.
  * nif_frontend_nearest: each ray whose bit in d_occluded_bits is clear gets
- *   one pair listed, its nearest outer pair (else its inner pair); *d_count =
- *   pairs listed.  Every pair of those rays is remembered in d_ws for round 2.
+ *   one pair listed (chosen by m->round1); *d_count = pairs listed.  Every pair of those rays is remembered in d_ws for round 2.
  * nif_frontend_rest (after the round-1 pairs have been answered into
  *   d_occluded_bits): the other pairs of the rays still unoccluded, written
  *   from index *d_count_nearest on; d_group_off gets their absolute group

@@ -22,6 +22,7 @@ NIF_MAX_LEVELS = 24
 NIF_F32, NIF_F16, NIF_BF16, NIF_E4M3 = 0, 1, 2, 3
 NIF_SCHED_AUTO, NIF_SCHED_SERIAL, NIF_SCHED_PIPELINED = 0, 1, 2
 NIF_ENC_MULTIRES, NIF_ENC_SPHERICAL_OUTER, NIF_ENC_SPHERICAL_INNER = 0, 1, 2
+NIF_ROUND1_NEAREST, NIF_ROUND1_OUTER = 0, 1
 NIF_ACT_RELU, NIF_ACT_LEAKY = 0, 1
 NIF_NETS_SINGLE, NIF_NETS_CLASS, NIF_NETS_OBJECT = 0, 1, 2
 NIF_QUERY_INNER = 0x80000000
@@ -44,7 +45,7 @@ class ModelDesc(ctypes.Structure):
         ("d_weights", P), ("d_scales", P),
         ("tile_m", i32), ("ctas_per_sm", i32), ("schedule", i32),
         ("encoding", i32), ("res_1d", i32), ("n_features_1d", i32),
-        ("n_outputs", i32),
+        ("n_outputs", i32), ("round1", i32),
     ]
 
 

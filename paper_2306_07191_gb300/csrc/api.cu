@@ -176,6 +176,8 @@ nif_status make_params(const nif_model_desc* m, NifParams* p) {
   NIF_CHECK_ARG(m->schedule >= NIF_SCHED_AUTO && m->schedule <= NIF_SCHED_PIPELINED,
                 "bad schedule %d", m->schedule);
   p->schedule = m->schedule;
+  NIF_CHECK_ARG(m->round1 == NIF_ROUND1_NEAREST || m->round1 == NIF_ROUND1_OUTER, "bad round1 %d", m->round1);
+  p->round1 = m->round1;
   return NIF_OK;
 }
 

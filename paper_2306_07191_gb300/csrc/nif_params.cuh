@@ -31,6 +31,7 @@ struct NifParams {
   int O;      // output rows (1: the occupancy logit)
   const float* scales;
   int schedule;  // NIF_SCHED_* of the tensor-core forward
+  int round1;    // NIF_ROUND1_*: the pair nif_infer queries first per ray
   int enc;       // NIF_ENC_*
   int R1, F1;    // spherical inner: distance grid cells and latents
   int64_t obj_elems;  // spherical: elements of one object's grid block

@@ -246,9 +246,8 @@ __global__ void __launch_bounds__(128) k_front_scatter(NifParams p, const char* 
 }
 
 // ------------------------------------------------- front end, two rounds
-// nif_infer answers one pair per ray first (its nearest outer pair, else its
-// inner pair; see round1_before) and then only the other pairs of the rays
-// still unoccluded.  A ray is occluded iff some pair says so (or the
+// nif_infer answers one pair per ray first (see round1_before) and then only
+// the other pairs of the rays still unoccluded.  A ray is occluded iff some pair says so (or the
 // caller's bits already say so), so skipping pairs of occluded rays leaves
 // every output bit as querying all pairs would.
 
@@ -256,13 +255,15 @@ __device__ __forceinline__ bool ray_occluded(const uint32_t* bits, int64_t i) {
   return (__ldg(bits + (i >> 5)) >> (i & 31)) & 1u;
 }
 
-// The pair round 1 queries for a ray: its nearest outer pair (smallest entry
-// parameter), else its inner pair.  (A shadow ray leaves its own object's
-// surface, so the inner pair is the nearest; the outer pairs are the other
-// objects between the shading point and the light.)
-__device__ __forceinline__ bool round1_before(bool inner, float tk, bool b_inner, float bt, bool none) {
+// The pair round 1 queries for a ray: its nearest pair (smallest entry
+// parameter; NIF_ROUND1_NEAREST), or its nearest outer pair, else an inner
+// pair (NIF_ROUND1_OUTER: a shadow ray leaves its own object's surface, so
+// the inner pair is always the nearest, while the outer pairs are the other
+// objects between the shading point and the light).
+__device__ __forceinline__ bool round1_before(int rule, bool inner, float tk, bool b_inner, float bt,
+                                              bool none) {
   if (none) return true;
-  if (inner != b_inner) return !inner;
+  if (rule == NIF_ROUND1_OUTER && inner != b_inner) return !inner;
   return tk < bt;
 }
 
@@ -280,7 +281,7 @@ __device__ __forceinline__ int ray_pairs_traverse(const NifParams& p, const char
   const nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
   for_each_pair<kTlas>(p, tlas, tlas_header(tlas), r, [&](uint32_t obj, bool inner, float tk) {
     if (nh < kMaxHits) {
-      if (round1_before(inner, tk, binner, bt, nh == 0)) {
+      if (round1_before(p.round1, inner, tk, binner, bt, nh == 0)) {
         bt = tk;
         binner = inner;
         first = nh;
@@ -313,7 +314,7 @@ __global__ void __launch_bounds__(128) k_front_count_first(NifParams p, const ch
       for_each_pair<kTlas>(p, tlas, tlas_header(tlas), r, [&](uint32_t obj, bool inner, float tk) {
         const uint32_t q = obj | (inner ? NIF_QUERY_INNER : 0u);
         if (nh < kSlots) slots[static_cast<int64_t>(nh) * n + i] = q;
-        if (round1_before(inner, tk, binner, bt, nh == 0)) {
+        if (round1_before(p.round1, inner, tk, binner, bt, nh == 0)) {
           bt = tk;
           binner = inner;
           best = nh;

@@ -176,6 +176,8 @@ class NifConfig:
     # output rows: 1 = the occupancy logit; 5 = the primary-ray outputs
     # [z | normal | delta] (Sec. 3.2, Sec. 6.1)
     n_outputs: int = 1
+    # the pair nif_infer queries first per ray (NIF_ROUND1_*)
+    round1: int = L.NIF_ROUND1_NEAREST
 
     @property
     def n_levels(self):
@@ -202,6 +204,7 @@ class NifConfig:
         d.res_1d = self.res_1d
         d.n_features_1d = self.n_features_1d
         d.n_outputs = self.n_outputs
+        d.round1 = self.round1
         return d
 
 

@@ -17,6 +17,7 @@ from . import _lib as L
 from . import nif, synth, workloads
 
 GRID_SEED = 0x5EED0001
+ROUND1_NAME = {L.NIF_ROUND1_NEAREST: "nearest", L.NIF_ROUND1_OUTER: "outer"}
 GRID_SCALE = 1e-4  # latent init U(-1e-4, 1e-4), Sec. 5 "Initialization"
 
 
@@ -411,6 +412,21 @@ class RoomPipeline:
         forward(b["goff2"])
         self._exact_end(join, bits, rays, stream)
         return bits
+
+    def tune_round1(self):
+        """Pick the round-1 rule (NIF_ROUND1_NEAREST or _OUTER) that queries
+        fewer pairs on this frame; the mask is the same either way.  Returns
+        {rule name: pairs queried}."""
+        bits = nif.empty_bits(self.n_rays)
+        cfg = self.front_model().cfg
+        pairs = {}
+        for rule in (L.NIF_ROUND1_NEAREST, L.NIF_ROUND1_OUTER):
+            cfg.round1 = rule
+            self.query_step(bits)
+            torch.cuda.synchronize()
+            pairs[rule] = self.last_query_counts()[1]
+        cfg.round1 = min(pairs, key=lambda r: (pairs[r], r))
+        return {ROUND1_NAME[r]: v for r, v in pairs.items()}
 
     def query_cost(self):
         """Algorithmic grid-tap bytes and MLP flops of one queried pair."""

@@ -404,6 +404,12 @@ def test_two_round_infer_equals_all_pairs(mlp_dt, sched):
     va = nif.bits_to_bool(all_bits, n).cpu().numpy()
     vt = nif.bits_to_bool(two, n).cpu().numpy()
     assert np.array_equal(va, vt)
+    model.cfg.round1 = L.NIF_ROUND1_OUTER
+    two_o = nif.empty_bits(n)
+    model.infer(rays_t, two_o, tlas=tlas)
+    model.check()
+    assert torch.equal(two_o, two)
+    model.cfg.round1 = L.NIF_ROUND1_NEAREST
     r = ray_id[:nq].cpu().numpy()
     with_pair = np.unique(r)
     assert counts[0] == len(with_pair)            # one round-1 pair per ray with a pair
@@ -422,11 +428,12 @@ def test_two_round_infer_equals_all_pairs(mlp_dt, sched):
     assert c2[0] == len(np.setdiff1d(with_pair, np.nonzero(pre)[0]))
 
 
-def test_round_one_takes_the_nearest_outer_pair():
-    """nif_frontend_nearest lists, per ray, its nearest outer pair (smallest
-    entry parameter), or one of its inner pairs when it has no outer one;
-    the choice is checked against the oracle's query set and FP32 slab
-    entries."""
+@pytest.mark.parametrize("rule", [L.NIF_ROUND1_NEAREST, L.NIF_ROUND1_OUTER])
+def test_round_one_choice(rule):
+    """nif_frontend_nearest lists one pair per ray: its nearest pair
+    (NIF_ROUND1_NEAREST), or its nearest outer pair, else one of its inner
+    pairs (NIF_ROUND1_OUTER); the choice is checked against the oracle's
+    query set and FP32 slab entries."""
     import ctypes
     rng = np.random.default_rng(75)
     boxes = random_boxes_scene(rng, n_obj=10, extent=3.0)
@@ -435,7 +442,7 @@ def test_round_one_takes_the_nearest_outer_pair():
     ki = rng.integers(0, 10, n // 2)
     o[: n // 2] = boxes[ki, :3] + rng.uniform(0.05, 0.95, size=(n // 2, 3)) * (boxes[ki, 3:] - boxes[ki, :3])
     rays = synth.pack_rays(o, synth.unit_vectors(rng, n), 1e-3, np.inf)
-    cfg = nif.NifConfig(res=[2], n_features=1, net_mode=L.NIF_NETS_CLASS)
+    cfg = nif.NifConfig(res=[2], n_features=1, net_mode=L.NIF_NETS_CLASS, round1=rule)
     model = nif.NifModel(cfg, torch.from_numpy(boxes).cuda(), torch.zeros(10 * 2 * 27).cuda(),
                          torch.zeros(2 * nif.NifModel.weight_count(cfg)).cuda())
     rays_t = torch.from_numpy(rays).cuda()
@@ -468,7 +475,11 @@ def test_round_one_takes_the_nearest_outer_pair():
         sel = np.nonzero(rr == ray)[0]
         obj, inner = chosen[int(ray)]
         outer = sel[~ii[sel]]
-        if len(outer):
+        if rule == L.NIF_ROUND1_NEAREST:
+            got = entry[sel[(oo[sel] == obj) & (ii[sel] == inner)]][0]
+            assert got <= entry[sel].min() * (1 + 1e-5) + 1e-6, (ray, got)
+            n_outer_first += int(inner and len(outer) > 0)
+        elif len(outer):
             assert not inner, ray
             best = entry[outer].min()
             got = entry[sel[(oo[sel] == obj) & ~ii[sel]]][0]
@@ -476,4 +487,4 @@ def test_round_one_takes_the_nearest_outer_pair():
             n_outer_first += int(ii[sel].any())
         else:  # only inner pairs (the origin inside overlapping boxes): one of them
             assert inner and obj in set(oo[sel].tolist())
-    assert n_outer_first > 1000  # rays with both kinds took the outer pair
+    assert n_outer_first > 1000  # rays with both kinds: the inner (nearest) or the outer pair
