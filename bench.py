@@ -70,18 +70,19 @@ WORKLOADS = {
 }
 
 
-# DRAM bytes (read + write) of one fused-kernel launch, from the ncu captures
-# summarised under profiles/, keyed by (workload, schedule, CTAs per SM) of the
-# kernel as it stands; a configuration without an entry reports null.
+# DRAM bytes (read + write) of one step's fused-kernel launches, from the ncu
+# captures summarised under profiles/, keyed by (workload, schedule, CTAs per
+# SM, round-1 rule) of the kernel as it stands; a configuration without an
+# entry reports null.
 FUSED_TRAFFIC_BYTES = {
     # profiles/fused_tm_room.md: rounds 1 + 2 of one step
-    ("room", "serial", 4): 1.265874e9 + 3.877632e6 + 0.426952e9 + 3.930880e6,
+    ("room", "serial", 4, "outer"): 1092881000 + 3713536 + 625983000 + 3601408,
     # profiles/fused_ws_full.md: rounds 1 + 2 of one step
-    ("full", "pipelined", 0): 492390656 + 6461440 + 260415232 + 3136768,
+    ("full", "pipelined", 0, "nearest"): 492514560 + 6791168 + 260741888 + 2782464,
     # profiles/fused_tm_paper_mixed_dram.md: outer and inner networks, rounds 1 + 2
-    ("paper", "serial", 4): 16448256 + 7936 + 26381312 + 13568 + 14667776 + 7680 + 417536 + 0,
+    ("paper", "serial", 4, "outer"): 31652352 + 29184 + 10637568 + 5376 + 7505152 + 5888 + 8780544 + 4608,
     # profiles/fused_tm_paper_mixed_dram.md: rounds 1 + 2 of one step
-    ("mixed", "serial", 4): 301272576 + 3251712 + 60928000 + 7936,
+    ("mixed", "serial", 4, "outer"): 249415424 + 3222528 + 55454976 + 3072,
 }
 
 
@@ -571,7 +572,7 @@ def run_ours(args):
                      "achieved": ach_gbs, "peak": hbm, "unit": "GB/s", "frac": ach_gbs / hbm,
                      "traffic": FUSED_TRAFFIC_BYTES.get(
                          (args.workload, SCHED_NAME[pipe.forward_models()[0][0].cfg.schedule],
-                          pipe.forward_models()[0][0].cfg.ctas_per_sm)),
+                          pipe.forward_models()[0][0].cfg.ctas_per_sm, round1)),
                      "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum summed "
                                         "over the step's two fused launches"),
                      "peak_source": src,
