@@ -462,6 +462,40 @@ class RoomPipeline:
         rays = self.rays if rays is None else rays
         return self.bvh.cast_shadow(rays, out=bits, stream=stream)
 
+    def nif_query_host(self, host_rays: torch.Tensor, host_bits: torch.Tensor, dev_rays: torch.Tensor,
+                       bits: torch.Tensor, n_chunks: int = 4) -> torch.Tensor:
+        """NIF visibility of rays in pinned host memory into a pinned host
+        mask.  The rays go up and the mask comes back in n_chunks pieces on a
+        copy stream, so each piece's copies overlap the queries of the others
+        (pieces are multiples of 32 rays: whole mask words).  dev_rays and
+        bits are device buffers of the full size."""
+        n = int(host_rays.shape[0])
+        step = (-(-n // max(1, n_chunks)) + 31) // 32 * 32
+        main = torch.cuda.current_stream()
+        if getattr(self, "_copy", None) is None:
+            self._copy = torch.cuda.Stream(device=self.dev)
+        cp = self._copy
+        cp.wait_stream(main)  # earlier work on these buffers comes first
+        bounds = [(a, min(n, a + step)) for a in range(0, n, step)]
+        ready = []
+        for a, b in bounds:
+            with torch.cuda.stream(cp):
+                dev_rays[a:b].copy_(host_rays[a:b], non_blocking=True)
+            e = torch.cuda.Event()
+            e.record(cp)
+            ready.append(e)
+        for (a, b), e in zip(bounds, ready):
+            main.wait_event(e)
+            w0, w1 = a // 32, (b + 31) // 32
+            self.nif_query(bits[w0:w1], dev_rays[a:b])
+            done = torch.cuda.Event()
+            done.record(main)
+            cp.wait_event(done)
+            with torch.cuda.stream(cp):
+                host_bits[w0:w1].copy_(bits[w0:w1], non_blocking=True)
+        main.wait_stream(cp)
+        return host_bits
+
     def disagreement(self):
         """Fraction of shadow rays where NIF and the BVH disagree, over all rays
         and over rays with at least one NIF query."""

@@ -167,3 +167,22 @@ def test_render_pipeline_trains_a_useful_shadow_network():
     ref = nif.shade(p.eval_f, bits, p.n_pix, cfg.render_spp)
     assert torch.equal(ref, p.render("bvh"))
     assert trained > 25.0, trained
+
+
+@pytest.mark.parametrize("chunks", [1, 3])
+def test_query_from_host_memory_in_overlapped_pieces(chunks):
+    """nif_query_host (rays up and mask back in pieces on a copy stream)
+    gives the mask nif_query gives on device-resident rays."""
+    p = pipeline.RoomPipeline(_small(pipeline.RoomConfig()), log=lambda *a: None)
+    p.train(steps=4)
+    want = nif.empty_bits(p.n_rays)
+    p.nif_query(want)
+    host_rays = torch.empty(p.rays.shape, dtype=torch.float32, pin_memory=True)
+    host_rays.copy_(p.rays.cpu())
+    host_bits = torch.zeros(want.numel(), dtype=torch.int32, pin_memory=True)
+    dev_rays = torch.empty_like(p.rays)
+    bits = nif.empty_bits(p.n_rays)
+    p.nif_query_host(host_rays, host_bits, dev_rays, bits, n_chunks=chunks)
+    torch.cuda.synchronize()
+    assert torch.equal(host_bits, want.cpu())
+    assert bool(want.any())
