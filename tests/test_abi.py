@@ -155,3 +155,49 @@ def test_state_checkpoint_size_and_header_checks(L):
     assert "header word 0" in L.last_error()
     assert L.lib.nif_state_load(ctypes.byref(d), ctypes.byref(o), buf.ctypes.data_as(ctypes.c_void_p), 16,
                                 None) == L.NIF_ERR_ARG
+
+
+def test_argument_errors_of_the_widened_calls(L):
+    """Host-side checks of the primary-ray, lighting, deterministic and
+    round-1 additions: every bad argument returns before any work is
+    queued (no GPU is needed to see it)."""
+    P = ctypes.c_void_p
+    assert L.lib.nif_loss_aux(None, None, None, 4, 1, 1.0, None, None, None) == L.NIF_ERR_ARG  # O < 2
+    assert L.lib.nif_loss_aux(None, None, None, -1, 5, 1.0, None, None, None) == L.NIF_ERR_ARG
+    assert L.lib.nif_loss_aux(None, None, None, 0, 5, 1.0, None, None, None) == L.NIF_OK
+    assert L.lib.nif_light_cdf(None, 0, None, None) == L.NIF_ERR_ARG
+    assert L.lib.nif_light_samples(None, None, None, None, None, 4, 0, None, None, 1, None, 1e-3, 0.8,
+                                   None, None, None) == L.NIF_ERR_ARG          # spp 0
+    assert L.lib.nif_light_samples(None, None, None, None, None, 0, 2, None, None, 1, None, 1e-3, 0.8,
+                                   None, None, None) == L.NIF_OK               # no rays
+    assert L.lib.nif_shade(None, None, -1, 1, None, None) == L.NIF_ERR_ARG
+    assert L.lib.nif_bits_clear(None, -1, None) == L.NIF_ERR_ARG
+    assert L.lib.nif_bits_clear(None, 0, None) == L.NIF_OK
+    assert L.lib.bvh_cast_pairs_closest(None, None, None, None, -1, None, None, None) == L.NIF_ERR_ARG
+    assert L.lib.bvh_cast_shadow_or(None, None, -1, None, None) == L.NIF_ERR_ARG
+    # five outputs: weights grow by four output rows; too narrow a network refuses them
+    d1, d5 = _room_desc(L), _room_desc(L, n_outputs=5)
+    assert L.lib.nif_weight_count(ctypes.byref(d5)) - L.lib.nif_weight_count(ctypes.byref(d1)) == 4 * 64
+    narrow = _room_desc(L, n_outputs=5, width=4)
+    assert L.lib.nif_weight_count(ctypes.byref(narrow)) > 0
+    assert L.lib.nif_workspace_size(ctypes.byref(narrow), 10, 10) == 0
+    assert L.lib.nif_workspace_size(ctypes.byref(_room_desc(L, n_outputs=9)), 10, 10) == 0
+    # the resolution needs the primary-ray layout; a shadow-ray model is refused
+    assert L.lib.nif_primary_resolve(ctypes.byref(d1), None, 10, None, None, None, 0, None, None, None, None,
+                                     None, None) == L.NIF_ERR_ARG
+    assert "5 outputs" in L.last_error()
+    # a train step of a five-output network without targets is refused
+    o = L.OptimDesc()
+    for f in ("d_w_master", "d_w_grad", "d_w_m", "d_w_v", "d_g_master", "d_g_grad", "d_g_m", "d_g_v"):
+        setattr(o, f, 256)
+    o.loss_scale = 1.0
+    assert L.lib.nif_train_step(ctypes.byref(d5), ctypes.byref(o), P(256), P(256), P(256), P(256), P(256), 8,
+                                None, P(256), 1 << 20, None) == L.NIF_ERR_ARG
+    assert "targets" in L.last_error()
+    # round-1 rule: only the two defined values
+    assert L.lib.nif_workspace_size(ctypes.byref(_room_desc(L, round1=L.NIF_ROUND1_OUTER)), 10, 10) > 0
+    assert L.lib.nif_workspace_size(ctypes.byref(_room_desc(L, round1=7)), 10, 10) == 0
+    # deterministic scratch: at least the records (element, value) of every grid tap
+    taps = 3 * 16 * 8 * 2
+    assert L.lib.nif_deterministic_workspace_size(ctypes.byref(d1), 1000) >= 1000 * taps * 8
+    assert L.lib.nif_deterministic_workspace_size(ctypes.byref(d1), -1) == 0
