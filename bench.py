@@ -731,6 +731,7 @@ def run_primary(args):
     if args.ctas_per_sm:
         cfg.ctas_per_sm = args.ctas_per_sm
     pipe = PrimaryPipeline(cfg, log=log)
+    pipe.two_rounds = args.primary_two_rounds
     train_s = pipe.train()
     tms = sorted(pipe.train_step_ms[1:]) or pipe.train_step_ms
     acc = pipe.disagreement()
@@ -758,21 +759,33 @@ def run_primary(args):
         parts = []
         for _ in range(args.steps):
             flush.zero_()
-            e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
             if sub:
-                fn(e[0:4])
+                fn(e[0:6])
+                if not pipe.two_rounds:  # events 4 and 5 are not recorded
+                    e[4].record(stream)
+                    e[5].record(stream)
             else:
                 e[0].record(stream)
                 fn()
-            e[4].record(stream)
+            e[6].record(stream)
             parts.append(e)
         torch.cuda.synchronize()
-        tot = statistics.mean(e[0].elapsed_time(e[4]) for e in parts)
+        tot = statistics.mean(e[0].elapsed_time(e[6]) for e in parts)
         subs = None
         if sub:
             def m(a, b):
                 return statistics.mean(e[a].elapsed_time(e[b]) for e in parts)
-            subs = {"room_cast_ms": m(0, 1), "frontend_ms": m(1, 2), "fused_ms": m(2, 3), "resolve_ms": m(3, 4)}
+            if pipe.two_rounds:
+                # start, exact cast, front end 1, fused 1, resolve 1 + front
+                # end 2, fused 2, resolve 2 (end)
+                subs = {"room_cast_ms": m(0, 1), "frontend_nearest_ms": m(1, 2), "fused_round1_ms": m(2, 3),
+                        "resolve1_frontend_rest_ms": m(3, 4), "fused_round2_ms": m(4, 5),
+                        "resolve2_ms": m(5, 6)}
+                subs["fused_ms"] = subs["fused_round1_ms"] + subs["fused_round2_ms"]
+            else:
+                subs = {"room_cast_ms": m(0, 1), "frontend_ms": m(1, 2), "fused_ms": m(2, 3),
+                        "resolve_ms": m(3, 6)}
         return tot, subs
 
     with ClockSampler(0) as clk:
@@ -782,7 +795,7 @@ def run_primary(args):
         torch.cuda.profiler.stop()
     clocks = clk.summary()
     pipe.check()
-    nq = int(pipe._primary_buffers()["count"].item())
+    nq = int(pipe._primary_buffers()["count"][1 if pipe.two_rounds else 0].item())
     host_rays = torch.empty((n, 8), dtype=torch.float32, pin_memory=True)
     host_rays.copy_(rays.cpu())
     host_t = torch.empty(n, dtype=torch.float32, pin_memory=True)
@@ -820,8 +833,9 @@ def run_primary(args):
                      "alg_bytes_per_query": alg_bytes, "flops_per_query": flops_q},
         "e2e": {"value": n / (e2e_ms * 1e-3), "unit": "primary rays/s", "h2d_bytes_per_step": n * 32,
                 "d2h_bytes_per_step": n * 16},
-        # per step: room cast, 3 front-end kernels, the fused forward, 2 resolution kernels
-        "gpu_launches": 7 * args.steps,
+        # per step: room cast; per round 3 front-end kernels, the fused
+        # forward and 2 resolution kernels
+        "gpu_launches": (13 if pipe.two_rounds else 7) * args.steps,
         "clocks": clocks,
         "cpu_baseline": None,
     }
@@ -967,6 +981,8 @@ def main():
     ap.add_argument("--schedule", default="", choices=["", "serial", "pipelined"],
                     help="fix the fused kernel's schedule (skips the autotuner)")
     ap.add_argument("--workload", default="room", choices=sorted(WORKLOADS))
+    ap.add_argument("--primary-two-rounds", action="store_true",
+                    help="primary workload: nearest pair first, then only pairs entered before the nearest hit")
     ap.add_argument("--no-graph", action="store_true",
                     help="time the step's calls one by one instead of replaying a CUDA graph of them")
     ap.add_argument("--exact-cast", choices=("first", "after", "overlap"), default=None,

@@ -399,6 +399,20 @@ nif_status nif_frontend_rest(const nif_model_desc* m, const void* d_tlas, const 
 /* After nif_infer on the same workspace (stream-ordered): d_counts[0] = pairs
  * queried in round 1, d_counts[1] = pairs queried in both rounds (device
  * int64[2], written asynchronously). */
+/* Round 2 for closest hits (primary rays, Sec. 6.1): after round 1's pairs
+ * (nif_frontend_nearest with NIF_ROUND1_NEAREST and a clear mask) have been
+ * answered and resolved into d_t (the ray's nearest hit so far, e.g. by
+ * nif_primary_resolve over the exact cast), the other pairs of every ray whose
+ * box it enters before d_t[i] (exact FP32 slab entry < d_t[i]) are listed as
+ * nif_frontend_rest lists them.  A pair entered later cannot hold a nearer
+ * hit (its t lies in [t_in, t_out]), so resolving these pairs into d_t ends
+ * with the nearest hit over every pair; only an exact tie in t between a
+ * round-1 and a round-2 pair may keep the round-1 pair instead. */
+nif_status nif_frontend_rest_nearer(const nif_model_desc* m, const void* d_tlas, const nif_ray* d_rays,
+                                    int64_t n, const float* d_t, uint32_t* d_ray_id, uint32_t* d_qobj,
+                                    int64_t max_q, const int64_t* d_count_nearest, int64_t* d_group_off,
+                                    int64_t* d_count, void* d_ws, size_t ws_bytes, void* stream);
+
 nif_status nif_infer_query_counts(const nif_model_desc* m, const void* d_ws, size_t ws_bytes,
                                   int64_t n, int64_t* d_counts, void* stream);
 
@@ -516,7 +530,8 @@ nif_status nif_train_step_aux(nif_model_desc* m, nif_optim_desc* o, const nif_ra
 
 /* Closest NIF hit per ray for primary rays (Sec. 6.1, Fig. 5), from the
  * outputs d_out [nq][O] (O >= 5, the primary-ray layout above) of a grouped
- * query list (nq = d_group_off[n_nets], at most nq_max).  Per pair with
+ * query list: queries [d_group_off[0], d_group_off[n_nets]) (a second
+ * round's list starts after the first's), at most nq_max.  Per pair with
  * z_0 < 0: t = t_in + clamp(delta, 0, 1) (t_out - t_in) in FP32 with each
  * operation rounded alone (t_in, t_out from the FP32 slab test of the front
  * end); per ray the smallest t, ties to the smallest query index.

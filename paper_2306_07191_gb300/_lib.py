@@ -107,6 +107,7 @@ SIGNATURES = {
     "nif_train_step": (i32, [MD, OD, P, P, P, P, P, i64, P, P, size_t, P]),
     "nif_train_step_aux": (i32, [MD, OD, P, P, P, P, P, P, i64, P, P, size_t, P]),
     "nif_primary_resolve": (i32, [MD, P, i64, P, P, P, i64, P, P, P, P, P, P]),
+    "nif_frontend_rest_nearer": (i32, [MD, P, P, i64, P, P, P, i64, P, P, P, P, size_t, P]),
     "nif_fill_uniform": (i32, [P, i64, ctypes.c_uint64, f32, P]),
     "nif_infer_noalloc": (i32, [MD, P, P, i64, P, P]),
     "nif_wait_selftest": (i32, [P, size_t, i64, P]),

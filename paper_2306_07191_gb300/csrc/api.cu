@@ -480,6 +480,27 @@ nif_status nif_frontend_rest(const nif_model_desc* m, const void* d_tlas, const 
                               as_stream(stream));
 }
 
+nif_status nif_frontend_rest_nearer(const nif_model_desc* m, const void* d_tlas, const nif_ray* d_rays,
+                                    int64_t n, const float* d_t, uint32_t* d_ray_id, uint32_t* d_qobj,
+                                    int64_t max_q, const int64_t* d_count_nearest, int64_t* d_group_off,
+                                    int64_t* d_count, void* d_ws, size_t ws_bytes, void* stream) {
+  CallRange nvtx_range("nif_frontend_rest_nearer");
+  NifParams p;
+  nif_status s = make_params(m, &p);
+  if (s != NIF_OK) return s;
+  NIF_CHECK_ARG(n >= 0 && max_q >= 0, "nif_frontend_rest_nearer: negative size");
+  NIF_CHECK_ARG(d_group_off && d_count && d_count_nearest && d_ws && d_t, "nif_frontend_rest_nearer: null pointer");
+  NIF_CHECK_ARG(n == 0 || (d_rays && aligned16(d_rays)), "nif_frontend_rest_nearer: rays null or not 16-byte aligned");
+  NIF_CHECK_ARG(max_q == 0 || (d_ray_id && d_qobj), "nif_frontend_rest_nearer: null query arrays");
+  NIF_CHECK_ARG(n < (int64_t(1) << 32), "nif_frontend_rest_nearer: at most 2^32 rays");
+  InferWs w = infer_layout(p, d_ws, 0, n);
+  if (w.bytes > ws_bytes) return fail(NIF_ERR_WORKSPACE, "nif_frontend_rest_nearer: workspace too small");
+  // the occlusion mask is not read in this mode; any non-null pointer will do
+  return launch_frontend_rest(p, d_tlas, d_rays, n, reinterpret_cast<const uint32_t*>(d_t), d_ray_id, d_qobj,
+                              max_q, d_count_nearest, d_group_off, d_count, d_ws, w.cnt2, w.slots, w.first_k,
+                              as_stream(stream), d_t);
+}
+
 nif_status nif_infer_query_counts(const nif_model_desc* m, const void* d_ws, size_t ws_bytes,
                                   int64_t n, int64_t* d_counts, void* stream) {
   NifParams p;

@@ -27,11 +27,12 @@ nif_status launch_frontend_first(const NifParams& p, const void* tlas, const nif
                                  const uint32_t* bits, uint32_t* out_ray, uint32_t* out_qobj,
                                  int64_t max_q, int64_t* goff, int64_t* count, void* ws,
                                  void* slot_area, uint8_t* first_k, cudaStream_t st);
+// t_bound (nullable): closest-hit mode, see nif_frontend_rest_nearer.
 nif_status launch_frontend_rest(const NifParams& p, const void* tlas, const nif_ray* rays, int64_t n,
                                 const uint32_t* bits, uint32_t* out_ray, uint32_t* out_qobj,
                                 int64_t max_q, const int64_t* count_first, int64_t* goff,
                                 int64_t* count, void* ws, uint32_t* cnt2, const void* slot_area,
-                                const uint8_t* first_k, cudaStream_t st);
+                                const uint8_t* first_k, cudaStream_t st, const float* t_bound = nullptr);
 
 nif_status launch_encode(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
                          const uint32_t* qobj, int64_t nq, void* out, int out_dtype,

@@ -366,12 +366,33 @@ __global__ void __launch_bounds__(128) k_front_rest(NifParams p, const char* tla
                                                     int64_t max_q, const uint32_t* slots,
                                                     const uint8_t* nhits, const uint8_t* first_k,
                                                     uint32_t* out_ray, uint32_t* out_qobj,
-                                                    DevError* err) {
+                                                    DevError* err, const float* t_bound) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   int c = i < n ? nhits[i] : 0;
-  if (c > 1 && ray_occluded(bits, i)) c = 0;
+  if (c > 1 && !t_bound && ray_occluded(bits, i)) c = 0;
   const bool from_slots = c > 1 && c <= kSlots;
   const int first = from_slots ? first_k[i] : -1;
+  // closest-hit mode: only pairs whose box the ray enters before its current
+  // nearest hit t_bound[i] (a later box cannot hold a nearer hit)
+  float tb = INFINITY;
+  float o[3] = {0.f, 0.f, 0.f}, d[3] = {0.f, 0.f, 0.f}, tmin = 0.f, tmax = 0.f;
+  if (t_bound && c > 1) {
+    tb = t_bound[i];
+    const nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
+    o[0] = r.ox; o[1] = r.oy; o[2] = r.oz;
+    d[0] = r.dx; d[1] = r.dy; d[2] = r.dz;
+    tmin = r.tmin;
+    tmax = r.tmax;
+  }
+  auto nearer = [&](uint32_t q) {
+    if (!t_bound) return true;
+    float box[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) box[k] = __ldg(p.aabb + 6 * static_cast<size_t>(q & 0x7fffffffu) + k);
+    float tin, tout, entry;
+    exact_slab(o, d, tmin, tmax, box, tin, tout, entry);
+    return tin < tb;
+  };
   auto put = [&](uint32_t v, bool valid) {
     const uint32_t pos = warp_claim(g_counter, valid ? bucket_of_q(p, v) : 0, valid);
     if (kScatter && valid && pos < max_q) {
@@ -381,15 +402,20 @@ __global__ void __launch_bounds__(128) k_front_rest(NifParams p, const char* tla
   };
   const int ms = __reduce_max_sync(0xffffffffu, from_slots ? c : 0);
   for (int k = 0; k < ms; ++k) {
-    const bool v = from_slots && k < c && k != first;
-    put(v ? slots[static_cast<int64_t>(k) * n + i] : 0u, v);
+    bool v = from_slots && k < c && k != first;
+    const uint32_t q = v ? slots[static_cast<int64_t>(k) * n + i] : 0u;
+    v = v && nearer(q);
+    put(q, v);
   }
   // rays with more pairs than slots: traverse again
   uint32_t hits[kMaxHits];
   int nh = 0, f2 = -1;
   if (c > kSlots) nh = ray_pairs_traverse<kTlas>(p, tlas, rays, i, hits, f2, err);
   const int most = __reduce_max_sync(0xffffffffu, nh);
-  for (int k = 0; k < most; ++k) put(k < nh ? hits[k] : 0u, k < nh && k != f2);
+  for (int k = 0; k < most; ++k) {
+    const uint32_t q = k < nh ? hits[k] : 0u;
+    put(q, k < nh && k != f2 && nearer(q));
+  }
 }
 
 // ------------------------------------------------------------ encode only
@@ -1071,7 +1097,7 @@ nif_status launch_frontend_rest(const NifParams& p, const void* tlas, const nif_
                                 const uint32_t* bits, uint32_t* out_ray, uint32_t* out_qobj,
                                 int64_t max_q, const int64_t* count_first, int64_t* goff,
                                 int64_t* count, void* ws, uint32_t* cnt2, const void* slot_area,
-                                const uint8_t* first_k, cudaStream_t st) {
+                                const uint8_t* first_k, cudaStream_t st, const float* t_bound) {
   const FrontShape f = front_shape(p);
   DevError* err = static_cast<DevError*>(ws);
   uint32_t* cur2 = cnt2 + align_up(f.n_buckets, 64);
@@ -1083,10 +1109,10 @@ nif_status launch_frontend_rest(const NifParams& p, const void* tlas, const nif_
   if (n > 0) {
     if (tlas)
       k_front_rest<true, false><<<blocks, kFrontThreads, 0, st>>>(p, tl, rays, n, bits, cnt2, max_q, slots, nhits,
-                                                                  first_k, nullptr, nullptr, err);
+                                                                  first_k, nullptr, nullptr, err, t_bound);
     else
       k_front_rest<false, false><<<blocks, kFrontThreads, 0, st>>>(p, tl, rays, n, bits, cnt2, max_q, slots, nhits,
-                                                                   first_k, nullptr, nullptr, err);
+                                                                   first_k, nullptr, nullptr, err, t_bound);
     NIF_LAUNCH_CHECK();
   }
   k_front_scan<<<1, 1024, 0, st>>>(cnt2, f.n_buckets, f.per_group, f.n_groups, max_q, cur2, goff, count, err,
@@ -1095,10 +1121,10 @@ nif_status launch_frontend_rest(const NifParams& p, const void* tlas, const nif_
   if (n > 0) {
     if (tlas)
       k_front_rest<true, true><<<blocks, kFrontThreads, 0, st>>>(p, tl, rays, n, bits, cur2, max_q, slots, nhits,
-                                                                 first_k, out_ray, out_qobj, err);
+                                                                 first_k, out_ray, out_qobj, err, t_bound);
     else
       k_front_rest<false, true><<<blocks, kFrontThreads, 0, st>>>(p, tl, rays, n, bits, cur2, max_q, slots, nhits,
-                                                                  first_k, out_ray, out_qobj, err);
+                                                                  first_k, out_ray, out_qobj, err, t_bound);
     NIF_LAUNCH_CHECK();
   }
   return NIF_OK;
@@ -1182,8 +1208,10 @@ __global__ void __launch_bounds__(256) k_primary_min(NifParams p, const nif_ray*
                                                      const uint32_t* ray_id, const uint32_t* qobj,
                                                      const int64_t* goff, int64_t nq_max,
                                                      const float* out, unsigned long long* key) {
+  // the list's queries: [goff[0], goff[n_nets]) (a second round's lists
+  // start after the first round's)
   const int64_t nq = goff[p.n_nets] < nq_max ? goff[p.n_nets] : nq_max;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
+  for (int64_t q = goff[0] + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
        q += (int64_t)gridDim.x * blockDim.x) {
     const float* zq = out + q * p.O;
     if (!(zq[0] < 0.f)) continue;

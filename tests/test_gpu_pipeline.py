@@ -144,7 +144,8 @@ def test_primary_pipeline_learns_depth_and_normals():
     assert acc["hit_disagreement"] < 0.5 * abl["untrained_hit_disagreement"]
     assert acc["normal_err_deg_mean"] < 0.5 * abl["untrained_normal_err_deg_mean"]
     assert acc["depth_rel_err_median"] < 0.05
-    t, nrm, win = (x.clone() for x in p.primary_step(winner=True))
+    t, nrm, win = (x.clone() for x in p.primary_step(winner=True, two_rounds=True))
+    n2 = int(p._primary_buffers()["count"][1].item())
     t_room, _ = p.room_bvh.cast_closest(p.rays)
     torch.cuda.synchronize()
     room = win < 0
@@ -152,6 +153,13 @@ def test_primary_pipeline_learns_depth_and_normals():
     assert bool((t[~room] < t_room[~room]).all())
     ln = nrm[~room].norm(dim=1)
     assert float((ln - 1).abs().max()) < 1e-5
+    # two rounds (nearest pair, then pairs entered before the nearest hit)
+    # give the nearest hit of every pair at once, with fewer pairs queried
+    t1, nrm1, win1 = (x.clone() for x in p.primary_step(winner=True, two_rounds=False))
+    n1 = int(p._primary_buffers()["count"][0].item())
+    torch.cuda.synchronize()
+    assert torch.equal(t, t1) and torch.equal(nrm, nrm1) and torch.equal(win < 0, win1 < 0)
+    assert n2 < n1
 
 
 def test_render_pipeline_trains_a_useful_shadow_network():
