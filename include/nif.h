@@ -478,7 +478,9 @@ nif_status nif_fwd_train(const nif_model_desc* m, const nif_ray* d_rays,
 nif_status nif_loss(const float* d_z, const uint8_t* d_label, int64_t nq, float loss_scale,
                     float* d_dz, float* d_loss, void* stream);
 
-/* The loss of a network with O = n_outputs > 1 outputs d_z [nq][O] and
+/* The loss of a network with O = n_outputs > 1 outputs (surface data at the
+ * hit, Sec. 3.2; normal and depth for primary rays, Sec. 6.1; the L2 loss of
+ * Sec. 5 'Training' extended to the regression outputs) d_z [nq][O] and
  * targets d_aux [nq][O-1] (read on hit pairs, y = 0):
  *   L = (1/B) sum_q [(sigmoid(z_q0) - y_q)^2 + (1 - y_q) sum_k (z_qk - aux_q,k-1)^2],
  * the regression terms counting on hit pairs only.  d_dz [nq][O] receives
