@@ -772,8 +772,13 @@ def slab_params(rays: torch.Tensor, boxes: torch.Tensor):
     t0, t1 = (lo - o) / dd, (hi - o) / dd
     near = torch.where(par, torch.full_like(d, -float("inf")), torch.minimum(t0, t1))
     far = torch.where(par, torch.full_like(d, float("inf")), torch.maximum(t0, t1))
-    tin = torch.maximum(rays[:, 3], near.max(dim=1).values)
-    tout = torch.minimum(rays[:, 7], far.min(dim=1).values)
+    # a parallel axis with the origin outside its slab misses the box
+    blocked = (par & ~((lo <= o) & (o <= hi))).any(dim=1)
+    inf = torch.full_like(rays[:, 3], float("inf"))
+    entry = torch.where(blocked, inf, near.max(dim=1).values)
+    exitv = torch.where(blocked, -inf, far.min(dim=1).values)
+    tin = torch.maximum(rays[:, 3], entry)
+    tout = torch.minimum(rays[:, 7], exitv)
     return tin, tout
 
 
