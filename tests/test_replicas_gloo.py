@@ -34,7 +34,7 @@ def _rank(rank, world, port, out):
 
 def test_max_over_two_gloo_ranks():
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()  # no fork of a process that has torch threads
     out = mgr.dict()
     mp.spawn(_rank, args=(2, port, out), nprocs=2, join=True)
     assert out[0] == (2.5, 2, 0) and out[1] == (2.5, 2, 1)
