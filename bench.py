@@ -525,22 +525,41 @@ def run_ours(args):
            vp(count.data_ptr()), vp(ws.data_ptr()), ws.numel(), sp)
     nq_all = int(count[0].item())
 
-    # end to end through the C ABI with host buffers: H2D rays, query, D2H mask
+    # end to end through the C ABI with host buffers: every frame's rays go
+    # up from pinned memory and its mask comes back.  Two frames are in
+    # flight (frame k + 1's rays go up while frame k is queried, its mask
+    # comes back while k + 1 is queried); the L2 flush before every frame's
+    # query is inside the timed span.  The per-frame latency (rays up,
+    # query, mask back, one frame at a time) is reported beside it.
     host_rays = torch.empty((n, 8), dtype=torch.float32, pin_memory=True)
     host_rays.copy_(rays.cpu())
-    host_bits = torch.empty(bits.numel(), dtype=torch.int32, pin_memory=True)
-    dev_rays = torch.empty_like(rays)
+    host_bits = [torch.empty(bits.numel(), dtype=torch.int32, pin_memory=True) for _ in range(2)]
+    dev_rays2 = [torch.empty_like(rays) for _ in range(2)]
+    bits2 = [nif.empty_bits(n, dev) for _ in range(2)]
 
-    # large frames: the rays go up and the mask comes back in 4 pieces on a
-    # copy stream, overlapping the queries of the other pieces (on a 2M-ray
-    # frame the pieces' extra calls cost more than the copies they hide:
-    # 1.70 vs 1.91 G rays/s on the room; 8.3M rays gain 15%)
-    e2e_chunks = 4 if n >= 4_000_000 else 1
+    def e2e_frames(K):
+        frames = [(host_rays, host_bits[k % 2]) for k in range(K)]
+        pipe.nif_query_host_frames(frames, dev_rays2, bits2, on_frame=lambda k: flush.zero_())
 
-    def e2e_step():
-        pipe.nif_query_host(host_rays, host_bits, dev_rays, bits, n_chunks=e2e_chunks)
+    e2e_frames(args.warmup)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e_a.record(stream)
+    e2e_frames(args.steps)
+    e_b.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e2e_ms = [e_a.elapsed_time(e_b) / args.steps]
 
-    e2e_ms, _ = timed(e2e_step, args.steps, args.warmup)
+    def e2e_one():
+        pipe.nif_query_host(host_rays, host_bits[0], dev_rays2[0], bits2[0], n_chunks=1)
+
+    lat_ms, _ = timed(e2e_one, args.steps, args.warmup)
 
     ms = reduce_max(statistics.mean(nif_ms), world, dev)
     ms_eager = reduce_max(statistics.mean(eager_ms), world, dev)
@@ -585,7 +604,8 @@ def run_ours(args):
                      "alg_bytes_per_query": alg_bytes, "flops_per_query": flops_q},
         "e2e": {"value": world * n / (ems * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": n * 32, "d2h_bytes_per_step": bits.numel() * 4,
-                "copy_overlap_chunks": e2e_chunks},
+                "frames_in_flight": 2, "l2": "flushed before every frame's query, inside the timed span",
+                "latency_ms_per_frame": reduce_max(statistics.mean(lat_ms), world, dev)},
         # per step: the exact cast, 3 + 3 front-end kernels, one fused
         # forward per network model and round
         "gpu_launches": (7 + 2 * len(pipe.forward_models())) * args.steps,

@@ -496,6 +496,51 @@ class RoomPipeline:
         main.wait_stream(cp)
         return host_bits
 
+    def nif_query_host_frames(self, frames, dev_rays, bits, on_frame=None):
+        """NIF visibility of a sequence of frames in pinned host memory:
+        frames is a list of (host_rays [n, 8] float32, host_bits int32 mask)
+        pairs, all of this pipeline's ray count.  Two frames are in flight:
+        frame k + 1's rays go up on a copy stream while frame k is queried,
+        and frame k's mask comes back while frame k + 1 is queried.  dev_rays
+        and bits are two device buffers each (alternate frames use them).
+        on_frame(k), if given, runs on the host just before frame k's query
+        is enqueued on the current stream."""
+        K = len(frames)
+        main = torch.cuda.current_stream()
+        if getattr(self, "_copy", None) is None:
+            self._copy = torch.cuda.Stream(device=self.dev)
+        cp = self._copy
+        cp.wait_stream(main)  # earlier work on these buffers comes first
+        up = [None] * K
+        queried = [None] * K
+
+        def upload(k):
+            j = k % 2
+            with torch.cuda.stream(cp):
+                if k >= 2:
+                    cp.wait_event(queried[k - 2])  # frame k - 2 is done with this buffer
+                dev_rays[j].copy_(frames[k][0], non_blocking=True)
+            up[k] = torch.cuda.Event()
+            up[k].record(cp)
+
+        if K:
+            upload(0)
+        for k in range(K):
+            j = k % 2
+            if k + 1 < K:
+                upload(k + 1)
+            main.wait_event(up[k])  # also orders after frame k - 2's mask copy on cp
+            if on_frame is not None:
+                on_frame(k)
+            self.nif_query(bits[j], dev_rays[j])
+            queried[k] = torch.cuda.Event()
+            queried[k].record(main)
+            with torch.cuda.stream(cp):
+                cp.wait_event(queried[k])
+                frames[k][1].copy_(bits[j], non_blocking=True)
+        main.wait_stream(cp)
+        return [f[1] for f in frames]
+
     def disagreement(self):
         """Fraction of shadow rays where NIF and the BVH disagree, over all rays
         and over rays with at least one NIF query."""

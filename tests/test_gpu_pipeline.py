@@ -196,6 +196,40 @@ def test_query_from_host_memory_in_overlapped_pieces(chunks):
     assert bool(want.any())
 
 
+def test_frames_from_host_memory_two_in_flight():
+    """nif_query_host_frames (frame k + 1's rays up while frame k is queried,
+    two device buffers in turn) gives every frame the mask nif_query gives
+    it alone; the frames differ, so a buffer mix-up shows."""
+    p = pipeline.RoomPipeline(_small(pipeline.RoomConfig()), log=lambda *a: None)
+    p.train(steps=4)
+    g = torch.Generator(device="cpu").manual_seed(5)
+    base = p.rays.cpu()
+    shorter = base.clone()
+    shorter[:, 7] *= 0.5
+    perm = base[torch.randperm(base.shape[0], generator=g)]
+    sets = [base, shorter, perm, base, shorter]
+    wants = []
+    for r in sets:
+        w = nif.empty_bits(p.n_rays)
+        p.nif_query(w, r.to(p.dev))
+        wants.append(w.cpu())
+    torch.cuda.synchronize()
+    frames = []
+    for r in sets:
+        hr = torch.empty(r.shape, dtype=torch.float32, pin_memory=True)
+        hr.copy_(r)
+        frames.append((hr, torch.full((wants[0].numel(),), -1, dtype=torch.int32, pin_memory=True)))
+    dev_rays = [torch.empty_like(p.rays) for _ in range(2)]
+    bits = [nif.empty_bits(p.n_rays) for _ in range(2)]
+    calls = []
+    p.nif_query_host_frames(frames, dev_rays, bits, on_frame=calls.append)
+    torch.cuda.synchronize()
+    assert calls == list(range(len(sets)))
+    for (hr, hb), w in zip(frames, wants):
+        assert torch.equal(hb, w)
+    assert not torch.equal(wants[0], wants[1]) and not torch.equal(wants[0], wants[2])
+
+
 class _F16Table:
     """Entries of a counter-generated FP32 table, rounded to FP16 as the
     model's copy holds them (inputs only)."""
