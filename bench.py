@@ -1,11 +1,13 @@
 """Shadow-ray throughput of the NIF query vs the exact BVH cast on one GB300.
 
-Workload (default): the room scene -- 64 displaced icospheres (1.0M
-triangles) in a 12-triangle room, 1920x1080 pixel-centre primary hits, one
-point light -> 2,073,600 shadow rays; hashed 16-level x 2-feature FP16 grids
-(2^19 entries per level) per object, shared outer/inner 3x64 networks in
-FP16 on the tensor cores, trained online for 64 Adam steps of 262,144
-BVH-labelled pairs from 4 jittered samples per pixel before timing.
+Workload (default, --workload full): 480 displaced icospheres of 62,720
+triangles (30.1M) on a jittered lattice in a 12-triangle room, 1920x1080
+pixel-centre primary hits, a 4 x 4 ceiling area light sampled 4 times per
+pixel -> 8,294,400 shadow rays; dense 8-level x 2-feature FP16 grids (R 4..64)
+per object, shared outer/inner 3x64 networks in FP16 on the tensor cores,
+trained online on 64 shadow samples per pixel before timing.  --workload room
+is the 1.0M-triangle scene with hashed 16-level grids and one point light
+(2,073,600 shadow rays); the other workloads are listed in WORKLOADS.
 
 One step = one full visibility query of all shadow rays: exact cast of the
 non-NIF geometry (the room), the top-level front end (pairs binned by
@@ -167,91 +169,112 @@ def dist_env():
 
 
 # ---------------------------------------------------------------- oracle arm
-def oracle_rays_per_s(n_rays: int, seed: int = 5):
-    """Time the CPU oracle (FP64 NIF query: box tests, encoding, MLP,
-    threshold) on n_rays shadow rays of the room frame.  The oracle derives
-    its own primary hits (its own BVH) and shadow rays from the generator's
-    camera, scene and light; the grids are the seeded initial latents."""
-    import numpy as np
+class OracleFrame:
+    """The CPU oracle's own view of a workload's evaluation frame: the scene
+    from the seeded generator, the oracle's BVH over it, and the FP64 oracle
+    model with the seeded initial latents and weights.  Imports only the
+    oracle and the seeded input generators (no CUDA library)."""
 
-    import oracle
-    from oracle import nif as onif
-    from paper_2306_07191_gb300 import synth, workloads
-    from paper_2306_07191_gb300.pipeline import GRID_SCALE, GRID_SEED, RoomConfig
+    def __init__(self, name: str):
+        import numpy as np
 
-    c = RoomConfig()
-    ws = workloads.room_scene(c.n_obj, c.n, c.width, c.height, c.seed)
-    sc = ws.scene
-    pick = np.sort(np.random.default_rng(seed).choice(ws.camera.shape[0], n_rays, replace=False))
-    ob = oracle.OracleBVH(sc.verts, sc.tris)
-    _, t, _ = ob.cast(ws.camera[pick], closest=True)
-    cam = ws.camera[pick]
-    # primary misses become empty segments (tmin = tmax = 0), as on the GPU
-    hit = np.isfinite(t)
-    th = np.where(hit, t, 0.0).astype(np.float32)
-    p = np.stack([cam[:, k] + th * cam[:, 4 + k] for k in range(3)], 1).astype(np.float32)
-    v = (ws.light[None, :].astype(np.float32) - p).astype(np.float32)
-    ss = v[:, 0] * v[:, 0]
-    ss = ss + v[:, 1] * v[:, 1]
-    ss = ss + v[:, 2] * v[:, 2]
-    ln = np.sqrt(ss).astype(np.float32)
-    rays = np.zeros((n_rays, 8), np.float32)
-    rays[:, 0:3] = np.where(hit[:, None], p, cam[:, 0:3])
-    rays[:, 3] = np.where(hit, np.float32(c.tmin), np.float32(0.0))
-    rays[:, 4:7] = np.where(hit[:, None], v / np.where(hit, ln, 1.0)[:, None], cam[:, 4:7])
-    rays[:, 7] = np.where(hit, ln, np.float32(0.0))
-    sizes, _, off = onif.level_layout(list(c.res), c.log2_table)
-    V = int(off[-1])
-    rng = np.random.default_rng(c.seed + 101)
-    K = 3 * len(c.res) * c.n_features
-    nets = [[np.asarray(w, np.float64) for w in synth.mlp_init(rng, K, c.width_mlp, c.n_hidden)]
-            for _ in range(2)]
-    m = onif.Model(res=list(c.res), F=c.n_features, log2_table=c.log2_table, obj_aabb=sc.obj_aabb,
-                   grids=synth.SplitMixGrids(V * c.n_features, GRID_SEED, GRID_SCALE), nets=nets,
-                   net_mode="class")
-    t0 = time.perf_counter()
-    rid, obj, inner = onif.queries(rays, sc.obj_aabb)
-    z = onif.forward(m, rays, rid, obj, inner)
-    onif.ray_occlusion(n_rays, rid, z)
-    dt = time.perf_counter() - t0
-    return n_rays / dt, dt, len(rid)
+        import oracle
+        from oracle import nif as onif
+        from paper_2306_07191_gb300 import synth, workloads
+
+        f = workloads.FRAMES[name]
+        self.f = f
+        self.ws = workloads.room_scene(f.n_obj, f.n, f.width, f.height, f.seed, layout=f.layout)
+        sc = self.ws.scene
+        self.bvh = oracle.OracleBVH(sc.verts, sc.tris)
+        npix = self.ws.camera.shape[0]
+        self.light = (workloads.area_light_samples(np.random.default_rng(workloads.EVAL_LIGHT_SEED), npix,
+                                                   f.samples).reshape(npix, f.samples, 3)
+                      if f.area_light else None)
+        _, _, off = onif.level_layout(list(f.res), f.log2_table)
+        V = int(off[-1])
+        rng = np.random.default_rng(f.seed + 101)
+        nets = [[np.asarray(w, np.float64) for w in synth.mlp_init(rng, f.K, f.width_mlp, f.n_hidden)]
+                for _ in range(2)]
+        self.model = onif.Model(res=list(f.res), F=f.n_features, log2_table=f.log2_table,
+                                obj_aabb=sc.obj_aabb,
+                                grids=synth.SplitMixGrids(V * f.n_features, workloads.GRID_SEED,
+                                                          workloads.GRID_SCALE),
+                                nets=nets, net_mode="class")
+
+    def rays(self, n_pixels: int | None = None, seed: int = 5):
+        """Shadow rays of n_pixels sampled pixels (all if None), derived by
+        the oracle from the camera rays, its own closest hits and the light."""
+        import numpy as np
+
+        from oracle import frames
+        npix = self.ws.camera.shape[0]
+        pix = (np.arange(npix) if n_pixels is None else
+               np.sort(np.random.default_rng(seed).choice(npix, n_pixels, replace=False)))
+        pts = self.light[pix].reshape(-1, 3) if self.light is not None else self.ws.light
+        return frames.frame_rays(self.bvh, self.ws.camera[pix], pts, self.f.tmin, self.f.samples)
 
 
-def cpu_baseline(n_rays: int = 600000):
-    """Run the oracle timing in a child process limited to one BLAS thread."""
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
-            "r = bench.oracle_rays_per_s(%d); print('ORACLE ' + json.dumps(r))" % (ROOT, n_rays))
-    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
-                         timeout=900)
-    for line in out.stdout.splitlines():
-        if line.startswith("ORACLE "):
-            v, dt, nq = json.loads(line[7:])
-            return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                    "sample": f"{n_rays} shadow rays of the room frame ({nq} queries), FP64 NIF "
-                              f"query on initial latents, {dt:.1f} s"}
-    return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "oracle run failed: " + (out.stderr[-300:] if out.stderr else "no output")}
+# pixels of the CPU-baseline sample (x the workload's shadow rays per pixel)
+CPU_BASELINE_PIXELS = {"room": 1 << 20, "full": 1 << 19}
+# pixels per step of the reference arm
+REFERENCE_PIXELS = {"room": 1 << 18, "full": 1 << 16}
+
+
+def cpu_baseline(name: str):
+    """The FP64 oracle's visibility query (box tests, encoding, MLP,
+    threshold) timed on a sample of the workload's frame, on every host core
+    (one worker process per core, chunks of rays)."""
+    from oracle import frames
+    npix = CPU_BASELINE_PIXELS[name]
+    fr = OracleFrame(name)
+    rays = fr.rays(npix)
+    pool = frames.QueryPool(fr.model)
+    try:
+        v, dt, nq, _ = pool.timed_query(rays)
+    finally:
+        pool.close()
+    return {"value": v, "unit": UNIT, "cores": pool.processes, "kind": "oracle",
+            "sample": f"{rays.shape[0]} shadow rays of {npix} sampled pixels of the {name} frame "
+                      f"({nq} pairs), FP64 NIF query on the initial latents, {pool.processes} worker "
+                      f"processes, {dt:.1f} s"}
 
 
 def run_reference(args):
+    """The oracle arm: the FP64 CPU oracle's query of a bounded sample of
+    the same workload per step, on every host core."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    n = 20000
+    from oracle import frames
+    from paper_2306_07191_gb300 import workloads
+    name = args.workload if args.workload in workloads.FRAMES else "full"
+    f = workloads.FRAMES[name]
+    npix = REFERENCE_PIXELS[name]
+    fr = OracleFrame(name)
+    pool = frames.QueryPool(fr.model)
     times = []
-    for s in range(args.warmup + args.steps):
-        v, dt, nq = oracle_rays_per_s(n, seed=100 + s)
-        if s >= args.warmup:
-            times.append(dt)
-    mean = sum(times) / len(times)
-    val = n / mean
+    n = 0
+    try:
+        for s in range(args.warmup + args.steps):
+            rays = fr.rays(npix, seed=100 + s)
+            n = int(rays.shape[0])
+            _, dt, _, _ = pool.timed_query(rays)
+            if s >= args.warmup:
+                times.append(dt)
+    finally:
+        pool.close()
+    med = statistics.median(times)
+    val = n / med
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": med * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOADS["room"], "sample_rays_per_step": n},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{n} shadow rays per step, FP64 oracle NIF query"},
+            "data": "synthetic",
+            "config": {"workload": WORKLOADS[name], "rays": f.width * f.height * f.samples,
+                       "sample_rays_per_step": n},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": pool.processes, "kind": "oracle",
+                             "sample": f"{n} shadow rays of {npix} sampled pixels per step, FP64 oracle "
+                                       f"NIF query, {pool.processes} worker processes"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -298,7 +321,7 @@ def precision_sweep(pipe, log, steps: int = 10, warmup: int = 3):
             torch.cuda.synchronize()
             if i >= warmup:
                 times.append(e0.elapsed_time(e1))
-        ms = st.mean(times)
+        ms = st.median(times)
         out[name] = {"ms_per_query": ms, "rays_per_s": n / (ms * 1e-3),
                      "disagreement_vs_bvh": float((dec != truth).float().mean()),
                      "disagreement_vs_f32": float((dec != dec32).float().mean())}
@@ -339,7 +362,7 @@ def r_sweep(log, steps: int = 5, warmup: int = 3):
             if k >= warmup:
                 ts.append(e0.elapsed_time(e1))
         pipe.check()
-        ms = statistics.mean(ts)
+        ms = statistics.median(ts)
         out[R] = {"ms_per_step": ms, "rays_per_s": pipe.n_rays / (ms * 1e-3),
                   "disagreement": dis["all"], "disagreement_queried": dis["queried"],
                   "outer_grid_latents": int(pipe.cls["outer"]["model"].grids.numel()), "train_s": train_s}
@@ -478,7 +501,7 @@ def run_ours(args):
         subs = None
         if sub:
             def m(a, b):
-                return statistics.mean(e[a].elapsed_time(e[b]) for e in parts)
+                return statistics.median(e[a].elapsed_time(e[b]) for e in parts)
             subs = {"room_cast_ms": m(0, 1), "frontend_nearest_ms": m(1, 2), "fused_round1_ms": m(2, 3),
                     "frontend_rest_ms": m(3, 4), "fused_round2_ms": m(4, 5)}
             if cfg.exact_cast != "first":
@@ -561,9 +584,10 @@ def run_ours(args):
 
     lat_ms, _ = timed(e2e_one, args.steps, args.warmup)
 
-    ms = reduce_max(statistics.mean(nif_ms), world, dev)
-    ms_eager = reduce_max(statistics.mean(eager_ms), world, dev)
-    bms = reduce_max(statistics.mean(bvh_ms), world, dev)
+    # medians of the timed steps (the e2e figure is one span over all steps)
+    ms = reduce_max(statistics.median(nif_ms), world, dev)
+    ms_eager = reduce_max(statistics.median(eager_ms), world, dev)
+    bms = reduce_max(statistics.median(bvh_ms), world, dev)
     ems = reduce_max(statistics.mean(e2e_ms), world, dev)
     value = world * n / (ms * 1e-3)
     hbm, tflops, src = _peaks()
@@ -605,7 +629,7 @@ def run_ours(args):
         "e2e": {"value": world * n / (ems * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": n * 32, "d2h_bytes_per_step": bits.numel() * 4,
                 "frames_in_flight": 2, "l2": "flushed before every frame's query, inside the timed span",
-                "latency_ms_per_frame": reduce_max(statistics.mean(lat_ms), world, dev)},
+                "latency_ms_per_frame": reduce_max(statistics.median(lat_ms), world, dev)},
         # per step: the exact cast, 3 + 3 front-end kernels, one fused
         # forward per network model and round
         "gpu_launches": (7 + 2 * len(pipe.forward_models())) * args.steps,
@@ -615,8 +639,8 @@ def run_ours(args):
         line["precision_sweep"] = sweep
     if args.r_sweep and args.workload == "paper" and rank == 0:
         line["r_sweep"] = r_sweep(log)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "room":
-        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload in ("room", "full"):
+        line["cpu_baseline"] = cpu_baseline(args.workload)
     elif rank == 0:
         line["cpu_baseline"] = None
     if rank == 0:
@@ -686,7 +710,7 @@ def run_grouped(args):
             e1.record()
             torch.cuda.synchronize()
             out.append(e0.elapsed_time(e1))
-        return statistics.mean(out)
+        return statistics.median(out)
 
     # project autotuner: schedule and CTAs per SM of the persistent grouped launch
     if args.ctas_per_sm or args.schedule:
@@ -791,11 +815,11 @@ def run_primary(args):
             e[6].record(stream)
             parts.append(e)
         torch.cuda.synchronize()
-        tot = statistics.mean(e[0].elapsed_time(e[6]) for e in parts)
+        tot = statistics.median(e[0].elapsed_time(e[6]) for e in parts)
         subs = None
         if sub:
             def m(a, b):
-                return statistics.mean(e[a].elapsed_time(e[b]) for e in parts)
+                return statistics.median(e[a].elapsed_time(e[b]) for e in parts)
             if pipe.two_rounds:
                 # start, exact cast, front end 1, fused 1, resolve 1 + front
                 # end 2, fused 2, resolve 2 (end)
@@ -953,8 +977,8 @@ def run_render(args):
             e[3].record(stream)
             parts.append(e)
         torch.cuda.synchronize()
-        return (statistics.mean(e[0].elapsed_time(e[3]) for e in parts),
-                statistics.mean(e[1].elapsed_time(e[2]) for e in parts))
+        return (statistics.median(e[0].elapsed_time(e[3]) for e in parts),
+                statistics.median(e[1].elapsed_time(e[2]) for e in parts))
 
     with ClockSampler(0) as clk:
         torch.cuda.profiler.start()
@@ -1000,7 +1024,7 @@ def main():
                     help="paper workload: also sweep the outer grid resolution R = 64, 256, 1024")
     ap.add_argument("--schedule", default="", choices=["", "serial", "pipelined"],
                     help="fix the fused kernel's schedule (skips the autotuner)")
-    ap.add_argument("--workload", default="room", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="full", choices=sorted(WORKLOADS))
     ap.add_argument("--primary-two-rounds", action="store_true",
                     help="primary workload: nearest pair first, then only pairs entered before the nearest hit")
     ap.add_argument("--no-graph", action="store_true",

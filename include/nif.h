@@ -229,6 +229,25 @@ nif_status bvh_build_boxes(const float* d_boxes, int64_t n, void* d_bvh, size_t 
 nif_status bvh_info(const void* d_bvh, int64_t* n_nodes, int64_t* n_prims, int32_t* depth,
                     void* stream);
 
+/* Status of a BVH buffer (synchronises the stream).  The build and every
+ * traversal through the buffer (the casts below, and the NIF front ends'
+ * top-level walks, which report into their own workspace instead) record the
+ * first failure in the buffer's 256-byte header, so that a result is never
+ * silently wrong:
+ *   NIF_ERR_UNSUPPORTED - the tree is deeper than the 96-entry traversal
+ *                         stack (recorded by the build; the builder's trees
+ *                         are at most about 92 levels deep, so this needs a
+ *                         buffer not made by bvh_build);
+ *   NIF_ERR_BOUNDS      - a traversal's stack would have overflowed, so a
+ *                         subtree was skipped (detail: the ray or query
+ *                         index) and that cast's results are not exact;
+ *   NIF_ERR_TIMEOUT     - a traversal reached the bound of 2^22 node visits
+ *                         (a corrupt or cyclic buffer); results not exact.
+ * Returns NIF_OK, one of those codes (with the detail in nif_last_error()),
+ * or NIF_ERR_ARG for a buffer that is not a BVH.  The status is sticky: it
+ * stays in the buffer until it is rebuilt. */
+nif_status bvh_check(const void* d_bvh, void* stream);
+
 /* Any-hit shadow cast (Eq. 1): bit i of d_occluded_bits (uint32 words,
  * ceil(n/32) of them, bit i%32 of word i/32) is set to 1 when ray i is
  * occluded, 0 when visible.  The words are overwritten, not OR-ed. */
@@ -396,9 +415,6 @@ nif_status nif_frontend_rest(const nif_model_desc* m, const void* d_tlas, const 
                              int64_t* d_group_off, int64_t* d_count, void* d_ws, size_t ws_bytes,
                              void* stream);
 
-/* After nif_infer on the same workspace (stream-ordered): d_counts[0] = pairs
- * queried in round 1, d_counts[1] = pairs queried in both rounds (device
- * int64[2], written asynchronously). */
 /* Round 2 for closest hits (primary rays, Sec. 6.1): after round 1's pairs
  * (nif_frontend_nearest with NIF_ROUND1_NEAREST and a clear mask) have been
  * answered and resolved into d_t (the ray's nearest hit so far, e.g. by
@@ -413,6 +429,9 @@ nif_status nif_frontend_rest_nearer(const nif_model_desc* m, const void* d_tlas,
                                     int64_t max_q, const int64_t* d_count_nearest, int64_t* d_group_off,
                                     int64_t* d_count, void* d_ws, size_t ws_bytes, void* stream);
 
+/* After nif_infer on the same workspace (stream-ordered): d_counts[0] = pairs
+ * queried in round 1, d_counts[1] = pairs queried in both rounds (device
+ * int64[2], written asynchronously). */
 nif_status nif_infer_query_counts(const nif_model_desc* m, const void* d_ws, size_t ws_bytes,
                                   int64_t n, int64_t* d_counts, void* stream);
 

@@ -73,6 +73,7 @@ SIGNATURES = {
     "bvh_build": (i32, [P, i64, P, i64, P, P, size_t, P, size_t, P]),
     "bvh_build_boxes": (i32, [P, i64, P, size_t, P, size_t, P]),
     "bvh_info": (i32, [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32), P]),
+    "bvh_check": (i32, [P, P]),
     "bvh_cast_shadow": (i32, [P, P, i64, P, P]),
     "bvh_cast_shadow_or": (i32, [P, P, i64, P, P]),
     "nif_bits_clear": (i32, [P, i64, P]),

@@ -359,6 +359,7 @@ nif_status nif_frontend(const nif_model_desc* m, const void* d_tlas, const nif_r
   if (ws_bytes < base) return fail(NIF_ERR_WORKSPACE, "nif_frontend: workspace too small");
   // with room for per-ray slots after the counters, the top level is traversed once
   void* slots = ws_bytes >= base + frontend_slot_bytes(n) ? static_cast<char*>(d_ws) + base : nullptr;
+  p.err = static_cast<DevError*>(d_ws);
   return launch_frontend(p, d_tlas, d_rays, n, d_ray_id, d_qobj, max_q, d_group_off, d_count, d_ws,
                          as_stream(stream), slots);
 }
@@ -454,6 +455,7 @@ nif_status nif_frontend_nearest(const nif_model_desc* m, const void* d_tlas, con
   NIF_CHECK_ARG(n < (int64_t(1) << 32), "nif_frontend_nearest: at most 2^32 rays");
   InferWs w = infer_layout(p, d_ws, 0, n);
   if (w.bytes > ws_bytes) return fail(NIF_ERR_WORKSPACE, "nif_frontend_nearest: workspace too small");
+  p.err = static_cast<DevError*>(d_ws);
   return launch_frontend_first(p, d_tlas, d_rays, n, d_occluded_bits, d_ray_id, d_qobj, max_q,
                                d_group_off, d_count, d_ws, w.slots, w.first_k, as_stream(stream));
 }
@@ -475,6 +477,7 @@ nif_status nif_frontend_rest(const nif_model_desc* m, const void* d_tlas, const 
   NIF_CHECK_ARG(n < (int64_t(1) << 32), "nif_frontend_rest: at most 2^32 rays");
   InferWs w = infer_layout(p, d_ws, 0, n);
   if (w.bytes > ws_bytes) return fail(NIF_ERR_WORKSPACE, "nif_frontend_rest: workspace too small");
+  p.err = static_cast<DevError*>(d_ws);
   return launch_frontend_rest(p, d_tlas, d_rays, n, d_occluded_bits, d_ray_id, d_qobj, max_q,
                               d_count_nearest, d_group_off, d_count, d_ws, w.cnt2, w.slots, w.first_k,
                               as_stream(stream));
@@ -495,6 +498,7 @@ nif_status nif_frontend_rest_nearer(const nif_model_desc* m, const void* d_tlas,
   NIF_CHECK_ARG(n < (int64_t(1) << 32), "nif_frontend_rest_nearer: at most 2^32 rays");
   InferWs w = infer_layout(p, d_ws, 0, n);
   if (w.bytes > ws_bytes) return fail(NIF_ERR_WORKSPACE, "nif_frontend_rest_nearer: workspace too small");
+  p.err = static_cast<DevError*>(d_ws);
   // the occlusion mask is not read in this mode; any non-null pointer will do
   return launch_frontend_rest(p, d_tlas, d_rays, n, reinterpret_cast<const uint32_t*>(d_t), d_ray_id, d_qobj,
                               max_q, d_count_nearest, d_group_off, d_count, d_ws, w.cnt2, w.slots, w.first_k,

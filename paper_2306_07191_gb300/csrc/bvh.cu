@@ -421,6 +421,10 @@ __global__ void k_header(Header* h, int kind, int64_t n, const uint32_t* cb, con
     H.scene_hi[k] = n ? ord2f(cb[3 + k]) : 0.f;
   }
   H.has_tags = has_tags;
+  if (H.depth > kStack) {
+    H.status.code = NIF_ERR_UNSUPPORTED;
+    H.status.detail = H.depth;
+  }
   *h = H;
 }
 
@@ -529,9 +533,13 @@ __device__ __forceinline__ bool mt(const RayF& r, float4 p0, float4 p1, float4 p
 enum Mode { kAny = 0, kClosest = 1, kPairs = 2, kPairsClosest = 3 };
 
 // Returns true on a hit; for kClosest also the nearest t and prim id.
+// Errors (a stack that would overflow, the visit bound reached) are recorded
+// in the buffer's status word with the index `who` of the ray or query.
 template <int kMode>
 __device__ __forceinline__ bool traverse(const char* bvh, const Header& H, const RayF& r,
-                                         int32_t want_tag, float& best_t, int32_t& best_id) {
+                                         int32_t want_tag, float& best_t, int32_t& best_id,
+                                         int64_t who) {
+  DevError* status = &reinterpret_cast<Header*>(const_cast<char*>(bvh))->status;
   const Node* nodes = reinterpret_cast<const Node*>(bvh + H.off_nodes);
   const float4* prims = reinterpret_cast<const float4*>(bvh + H.off_prims);
   int32_t stack[kStack];
@@ -554,6 +562,7 @@ __device__ __forceinline__ bool traverse(const char* bvh, const Header& H, const
         bool swap = t1 < t0;
         int32_t nearc = swap ? d.y : d.x, farc = swap ? d.x : d.y;
         if (sp < kStack) stack[sp++] = farc;
+        else raise_error(status, NIF_ERR_BOUNDS, who);
         ref = nearc;
         continue;
       }
@@ -588,9 +597,10 @@ __device__ __forceinline__ bool traverse(const char* bvh, const Header& H, const
       if ((kMode == kClosest || kMode == kPairsClosest) && hit)
         tmax = fminf(r.tmax, nextafterf(best_t, INFINITY));
     }
-    if (sp == 0) break;
+    if (sp == 0) return hit;
     ref = stack[--sp];
   }
+  raise_error(status, NIF_ERR_TIMEOUT, who);
   return hit;
 }
 
@@ -609,7 +619,7 @@ __global__ void __launch_bounds__(128) k_cast_shadow(const char* bvh, const nif_
     RayF r = load_ray(rays, i);
     float t;
     int32_t id;
-    occ = traverse<kAny>(bvh, H, r, 0, t, id);
+    occ = traverse<kAny>(bvh, H, r, 0, t, id, i);
   }
   uint32_t word = __ballot_sync(0xffffffffu, occ);
   if ((threadIdx.x & 31) == 0 && i < n) {
@@ -632,7 +642,7 @@ __global__ void __launch_bounds__(128) k_cast_closest(const char* bvh, const nif
   RayF r = load_ray(rays, i);
   float t;
   int32_t id;
-  traverse<kClosest>(bvh, H, r, 0, t, id);
+  traverse<kClosest>(bvh, H, r, 0, t, id, i);
   if (tout) tout[i] = t;
   if (pout) pout[i] = id;
 }
@@ -648,7 +658,7 @@ __global__ void __launch_bounds__(128) k_cast_pairs(const char* bvh, const nif_r
   RayF r = load_ray(rays, ray_id[q]);
   float t;
   int32_t id;
-  hit[q] = traverse<kPairs>(bvh, H, r, static_cast<int32_t>(obj[q] & 0x7fffffffu), t, id) ? 1 : 0;
+  hit[q] = traverse<kPairs>(bvh, H, r, static_cast<int32_t>(obj[q] & 0x7fffffffu), t, id, q) ? 1 : 0;
 }
 
 __global__ void __launch_bounds__(128) k_cast_pairs_closest(const char* bvh, const nif_ray* rays,
@@ -662,7 +672,7 @@ __global__ void __launch_bounds__(128) k_cast_pairs_closest(const char* bvh, con
   RayF r = load_ray(rays, ray_id[q]);
   float t;
   int32_t id;
-  traverse<kPairsClosest>(bvh, H, r, static_cast<int32_t>(obj[q] & 0x7fffffffu), t, id);
+  traverse<kPairsClosest>(bvh, H, r, static_cast<int32_t>(obj[q] & 0x7fffffffu), t, id, q);
   tout[q] = t;
   pout[q] = id;
 }
@@ -849,6 +859,30 @@ nif_status bvh_info(const void* d_bvh, int64_t* n_nodes, int64_t* n_prims, int32
   if (depth) *depth = h.depth;
   if (h.depth > bvh::kStack) return fail(NIF_ERR_UNSUPPORTED, "bvh depth %d exceeds stack", h.depth);
   return NIF_OK;
+}
+
+nif_status bvh_check(const void* d_bvh, void* stream) {
+  NIF_CHECK_ARG(d_bvh != nullptr, "bvh_check: null bvh");
+  bvh::Header h;
+  NIF_CUDA_TRY(cudaMemcpyAsync(&h, d_bvh, sizeof(h), cudaMemcpyDeviceToHost, as_stream(stream)));
+  NIF_CUDA_TRY(cudaStreamSynchronize(as_stream(stream)));
+  if (h.magic != bvh::kMagic) return fail(NIF_ERR_ARG, "bvh_check: not a bvh buffer");
+  switch (h.status.code) {
+    case NIF_OK:
+      return NIF_OK;
+    case NIF_ERR_UNSUPPORTED:
+      return fail(NIF_ERR_UNSUPPORTED, "bvh: depth %lld exceeds the traversal stack (%d)",
+                  static_cast<long long>(h.status.detail), bvh::kStack);
+    case NIF_ERR_BOUNDS:
+      return fail(NIF_ERR_BOUNDS, "bvh: traversal stack overflow (ray or query %lld)",
+                  static_cast<long long>(h.status.detail));
+    case NIF_ERR_TIMEOUT:
+      return fail(NIF_ERR_TIMEOUT, "bvh: node-visit bound reached (ray or query %lld)",
+                  static_cast<long long>(h.status.detail));
+    default:
+      return fail(h.status.code, "bvh: error %d (detail %lld)", h.status.code,
+                  static_cast<long long>(h.status.detail));
+  }
 }
 
 static nif_status cast_shadow(const char* name, bool or_into, const void* d_bvh, const nif_ray* d_rays,

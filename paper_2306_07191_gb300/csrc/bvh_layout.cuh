@@ -13,6 +13,10 @@ namespace nif {
 namespace bvh {
 
 constexpr uint32_t kMagic = 0x4E425648u;  // "NBVH"
+// Traversal stack entries.  The builder's trees are at most about 92 levels
+// deep (63 bits of Morton code, then at most 28 levels splitting equal codes
+// by index), so a tree it built never fills the stack; the build records an
+// error for a deeper tree and a traversal records one when it would overflow.
 constexpr int kStack = 96;
 // Bound on node visits per ray: a valid tree never gets near it, a corrupt
 // one cannot make a traversal loop forever.
@@ -28,7 +32,15 @@ struct Header {
   int64_t off_nodes, off_prims, off_ids;
   float scene_lo[3], scene_hi[3];
   int32_t has_tags;
-  int32_t pad[43];
+  int32_t pad0;
+  // First error recorded by the build or by any cast through this buffer
+  // (0 = none): NIF_ERR_UNSUPPORTED (detail: depth) when the tree is deeper
+  // than the traversal stack, NIF_ERR_BOUNDS (detail: ray or query index)
+  // when a traversal's stack would overflow, NIF_ERR_TIMEOUT (detail: ray or
+  // query index) when a traversal hits the node-visit bound.  Read by
+  // bvh_check.
+  DevError status;
+  int32_t pad[38];
 };
 static_assert(sizeof(Header) == 256, "header size");
 

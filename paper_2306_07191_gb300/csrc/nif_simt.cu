@@ -26,10 +26,14 @@ __device__ __forceinline__ int bucket_of(const NifParams& p, uint32_t obj, bool 
 }
 
 // Calls emit(obj, inner, tkey) for every object whose box the ray's segment
-// overlaps (tkey: the segment's entry parameter into the box).
+// overlaps (tkey: the segment's entry parameter into the box).  A top-level
+// walk whose stack would overflow, or that reaches the visit bound, records
+// NIF_ERR_BOUNDS or NIF_ERR_TIMEOUT with the ray index `who` in the call's
+// error word.
 template <bool kTlas, typename Emit>
 __device__ __forceinline__ void for_each_pair(const NifParams& p, const char* tlas,
-                                              const bvh::Header* H, const nif_ray& r, Emit&& emit) {
+                                              const bvh::Header* H, const nif_ray& r, int64_t who,
+                                              Emit&& emit) {
   float o[3] = {r.ox, r.oy, r.oz}, d[3] = {r.dx, r.dy, r.dz};
   float rcp[3];
   bool exact_only = false;
@@ -87,6 +91,7 @@ __device__ __forceinline__ void for_each_pair(const NifParams& p, const char* tl
       bool h1 = cull2(b.x, b.y, b.z, b.w, c.z, c.w);
       if (h0 && h1) {
         if (sp < bvh::kStack) stack[sp++] = dd.y;
+        else raise_error(p.err, NIF_ERR_BOUNDS, who);
         ref = dd.x;
         continue;
       }
@@ -98,9 +103,10 @@ __device__ __forceinline__ void for_each_pair(const NifParams& p, const char* tl
       for (int32_t k = first; k < first + count; ++k)
         test_leaf(__ldg(prims + 3 * (int64_t)k), __ldg(prims + 3 * (int64_t)k + 1));
     }
-    if (sp == 0) break;
+    if (sp == 0) return;
     ref = stack[--sp];
   }
+  raise_error(p.err, NIF_ERR_TIMEOUT, who);
 }
 
 // Warp-aggregated claim on counters[key] for every lane with `valid`: lanes
@@ -149,7 +155,7 @@ __global__ void __launch_bounds__(128) k_front_count(NifParams p, const char* tl
   uint32_t hits[kSlots];  // the first kSlots pairs, claimed after the traversal
   if (i < n) {
     const nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
-    for_each_pair<kTlas>(p, tlas, tlas_header(tlas), r, [&](uint32_t obj, bool inner, float) {
+    for_each_pair<kTlas>(p, tlas, tlas_header(tlas), r, i, [&](uint32_t obj, bool inner, float) {
       const uint32_t v = obj | (inner ? NIF_QUERY_INNER : 0u);
       if (nh < kSlots) {
         hits[nh] = v;
@@ -236,7 +242,7 @@ __global__ void __launch_bounds__(128) k_front_scatter(NifParams p, const char* 
   int nh = 0;
   if (i < n && !from_slots) {
     const nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
-    for_each_pair<kTlas>(p, tlas, tlas_header(tlas), r, [&](uint32_t obj, bool inner, float) {
+    for_each_pair<kTlas>(p, tlas, tlas_header(tlas), r, i, [&](uint32_t obj, bool inner, float) {
       if (nh < kMaxHits) hits[nh++] = obj | (inner ? NIF_QUERY_INNER : 0u);
       else raise_error(err, NIF_ERR_BOUNDS, i);
     });
@@ -279,7 +285,7 @@ __device__ __forceinline__ int ray_pairs_traverse(const NifParams& p, const char
   bool binner = true;
   first = 0;
   const nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
-  for_each_pair<kTlas>(p, tlas, tlas_header(tlas), r, [&](uint32_t obj, bool inner, float tk) {
+  for_each_pair<kTlas>(p, tlas, tlas_header(tlas), r, i, [&](uint32_t obj, bool inner, float tk) {
     if (nh < kMaxHits) {
       if (round1_before(p.round1, inner, tk, binner, bt, nh == 0)) {
         bt = tk;
@@ -311,7 +317,7 @@ __global__ void __launch_bounds__(128) k_front_count_first(NifParams p, const ch
   if (i < n) {
     if (!ray_occluded(bits, i)) {
       const nif_ray r = load_nif_ray(rays, static_cast<uint32_t>(i));
-      for_each_pair<kTlas>(p, tlas, tlas_header(tlas), r, [&](uint32_t obj, bool inner, float tk) {
+      for_each_pair<kTlas>(p, tlas, tlas_header(tlas), r, i, [&](uint32_t obj, bool inner, float tk) {
         const uint32_t q = obj | (inner ? NIF_QUERY_INNER : 0u);
         if (nh < kSlots) slots[static_cast<int64_t>(nh) * n + i] = q;
         if (round1_before(p.round1, inner, tk, binner, bt, nh == 0)) {

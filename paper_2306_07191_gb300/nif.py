@@ -98,6 +98,13 @@ class BVH:
         torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
         del ws
         self._inputs = None
+        self.check(stream)
+
+    def check(self, stream=None):
+        """Raise NifError if the build or any traversal through this buffer
+        recorded a failure (bvh_check: a tree deeper than the traversal
+        stack, a stack overflow or the node-visit bound)."""
+        L.call("bvh_check", _ptr(self.buf), _stream(stream))
 
     @classmethod
     def from_boxes(cls, boxes: torch.Tensor, stream=None) -> "BVH":

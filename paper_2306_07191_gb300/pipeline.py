@@ -16,9 +16,11 @@ import torch
 from . import _lib as L
 from . import nif, synth, workloads
 
-GRID_SEED = 0x5EED0001
+GRID_SEED = workloads.GRID_SEED
 ROUND1_NAME = {L.NIF_ROUND1_NEAREST: "nearest", L.NIF_ROUND1_OUTER: "outer"}
-GRID_SCALE = 1e-4  # latent init U(-1e-4, 1e-4), Sec. 5 "Initialization"
+GRID_SCALE = workloads.GRID_SCALE  # latent init U(-1e-4, 1e-4), Sec. 5 "Initialization"
+_ROOM = workloads.ROOM_FRAME
+_FULL = workloads.FULL_FRAME
 
 
 class BatchDraw:
@@ -42,23 +44,23 @@ class BatchDraw:
 
 @dataclass
 class RoomConfig:
-    n_obj: int = 64
-    n: int = 28                 # icosphere frequency: 20 n^2 triangles
-    width: int = 1920
-    height: int = 1080
-    seed: int = 7
-    res: tuple = tuple(workloads.ROOM_RES)
-    n_features: int = 2
-    log2_table: int = 19
+    n_obj: int = _ROOM.n_obj
+    n: int = _ROOM.n            # icosphere frequency: 20 n^2 triangles
+    width: int = _ROOM.width
+    height: int = _ROOM.height
+    seed: int = _ROOM.seed
+    res: tuple = _ROOM.res
+    n_features: int = _ROOM.n_features
+    log2_table: int = _ROOM.log2_table
     grid_dtype: int = L.NIF_F16
     mlp_dtype: int = L.NIF_F16
-    n_hidden: int = 3
-    width_mlp: int = 64
+    n_hidden: int = _ROOM.n_hidden
+    width_mlp: int = _ROOM.width_mlp
     train_spp: int = 4          # jittered samples per pixel collected for training
     train_steps: int = 64
     batch: int = 262144
     lr: float = 1e-2
-    tmin: float = 1e-3
+    tmin: float = _ROOM.tmin
     ctas_per_sm: int = 0
     schedule: int = 0  # NIF_SCHED_* of the tensor-core forward (0: library choice)
     layout: str = "random"      # "random" | "single" | "lattice" | "mixed" (see workloads.room_scene)
@@ -98,9 +100,10 @@ def full_scale_config() -> RoomConfig:
     lattice in the room, a 4 x 4 area light, 4 samples per pixel -> 8,294,400
     shadow rays; dense 8-level FP16 grids per object, FP16 networks, trained on
     16 jittered samples x 4 light samples = 64 shadow samples per pixel."""
-    return RoomConfig(layout="lattice", n_obj=480, n=56, res=tuple(workloads.TINY_RES),
-                      log2_table=19, grid_dtype=L.NIF_F16, mlp_dtype=L.NIF_F16, area_light=True,
-                      samples=4, train_spp=16, pairs_per_spp=1 << 20, max_pairs_per_ray=8)
+    return RoomConfig(layout=_FULL.layout, n_obj=_FULL.n_obj, n=_FULL.n, res=_FULL.res,
+                      log2_table=_FULL.log2_table, grid_dtype=L.NIF_F16, mlp_dtype=L.NIF_F16,
+                      area_light=_FULL.area_light, samples=_FULL.samples, train_spp=16,
+                      pairs_per_spp=1 << 20, max_pairs_per_ray=8)
 
 
 class RoomPipeline:
@@ -179,7 +182,7 @@ class RoomPipeline:
     # ------------------------------------------------------------ inputs
     def _eval_rays(self, camera: torch.Tensor) -> torch.Tensor:
         """The rays of the evaluation frame: shadow rays from the primary hits."""
-        return self._shadow_rays(camera, light_seed=4321)
+        return self._shadow_rays(camera, light_seed=workloads.EVAL_LIGHT_SEED)
 
     def _shadow_rays(self, camera: torch.Tensor, light_seed: int) -> torch.Tensor:
         """Shadow rays from the primary hits of `camera`: one per point light,
@@ -447,6 +450,8 @@ class RoomPipeline:
 
     def check(self):
         self.front_model().check(self._query_buffers()["ws"])
+        for b in (self.bvh, self.room_bvh, self.tlas):
+            b.check()
 
     def nif_query(self, bits: torch.Tensor, rays: torch.Tensor | None = None, stream=None):
         """NIF visibility: exact cast of the non-NIF geometry (the room), then
@@ -988,6 +993,8 @@ class PrimaryPipeline(RoomPipeline):
 
     def check(self):
         self.model.check(self._primary_buffers()["ws"])
+        for b in (self.bvh, self.room_bvh, self.tlas):
+            b.check()
 
     def disagreement(self):
         """Accuracy against the exact closest-hit cast over every triangle:

@@ -24,6 +24,47 @@ from . import synth
 TINY_RES = [4, 5, 8, 13, 19, 28, 43, 64]
 ROOM_RES = [16, 21, 27, 36, 48, 64, 84, 111, 147, 194, 256, 337, 445, 588, 776, 1024]
 
+GRID_SEED = 0x5EED0001  # SplitMix64 seed of the grid latents
+GRID_SCALE = 1e-4       # latent initialisation U(-1e-4, 1e-4), Sec. 5 "Initialization"
+EVAL_LIGHT_SEED = 4321  # area-light samples of the evaluation frame
+
+
+@dataclass(frozen=True)
+class FrameSpec:
+    """The evaluation frame of a room-style workload and its network, as
+    plain numbers: what the GPU pipeline and the CPU oracle both build from.
+
+    n_obj objects of icosphere frequency n in the given layout, a width x
+    height pixel-centre frame, shadow rays to one point light or `samples`
+    area-light points per pixel, segments starting at tmin; per object a
+    position and a direction grid of len(res) levels x n_features, 2^log2_table
+    entries per hashed level; outer and inner networks of n_hidden x width."""
+    name: str
+    n_obj: int
+    n: int
+    layout: str
+    res: tuple
+    n_features: int = 2
+    log2_table: int = 19
+    n_hidden: int = 3
+    width_mlp: int = 64
+    width: int = 1920
+    height: int = 1080
+    seed: int = 7
+    tmin: float = 1e-3
+    area_light: bool = False
+    samples: int = 1
+
+    @property
+    def K(self) -> int:
+        return 3 * len(self.res) * self.n_features
+
+
+ROOM_FRAME = FrameSpec("room", n_obj=64, n=28, layout="random", res=tuple(ROOM_RES))
+FULL_FRAME = FrameSpec("full", n_obj=480, n=56, layout="lattice", res=tuple(TINY_RES),
+                       area_light=True, samples=4)
+FRAMES = {"room": ROOM_FRAME, "full": FULL_FRAME}
+
 
 @dataclass
 class TinyObject:

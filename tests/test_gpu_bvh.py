@@ -131,3 +131,34 @@ def test_room_scene_full_size_sampled():
     s_occ, _, _ = ob.cast(ors, closest=False)
     assert np.array_equal(s_occ.astype(bool), occ[sample])
     assert 0.05 < occ.mean() < 0.95
+
+
+def test_degenerate_triangle_sets_build_shallow_exact_trees():
+    """Inputs that are hard on a Morton-code builder: 4,096 copies of one
+    triangle spun about a shared centroid (every key equal), and a chain of
+    triangles at x = 2^-k clustered exponentially towards the origin (keys
+    sharing ever longer prefixes).  The trees stay within the traversal
+    stack, bvh_check is clean after the casts, and the casts equal brute
+    force bit for bit."""
+    rng = np.random.default_rng(8)
+    base = np.array([[1.0, 0.0, 0.0], [-0.5, 0.8660254, 0.0], [-0.5, -0.8660254, 0.0]])
+    axes = synth.unit_vectors(rng, 4096)
+    ang = rng.uniform(0, 2 * np.pi, 4096)
+    spun = []
+    for a, th in zip(axes, ang):
+        K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+        R = np.eye(3) + np.sin(th) * K + (1 - np.cos(th)) * K @ K
+        spun.append(base @ R.T)
+    chain = [base * 2.0 ** -k * 0.25 + np.array([2.0 ** -k, 0.0, 0.0]) for k in range(100)]
+    for tris3 in (spun, chain):
+        v = np.concatenate(tris3).astype(np.float32)
+        t = np.arange(len(v), dtype=np.int32).reshape(-1, 3)
+        rays = synth.shell_rays(rng, 4096, radius=2.0)
+        occ_ref, t_ref, p_ref = oracle.brute_cast(v, t, rays)
+        bvh, occ, tt, pp = _gpu_cast(v, t, rays)
+        bvh.check()
+        assert 0 < bvh.info()["depth"] <= 96
+        assert occ_ref.any()
+        assert np.array_equal(occ.astype(np.uint8), occ_ref)
+        assert np.array_equal(tt.view(np.uint32), t_ref.view(np.uint32))
+        assert np.array_equal(pp, p_ref)

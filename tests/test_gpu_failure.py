@@ -128,3 +128,81 @@ def test_non_finite_parameter_after_adam_is_reported():
     det = ctypes.c_int64()
     st = L.lib.nif_check(ctypes.c_void_p(tr._ws.data_ptr()), ctypes.byref(det), nif._stream())
     assert st == L.NIF_ERR_NUMERIC and det.value == 12345
+
+
+# ------------------------------------------------------------ BVH status
+def _box_nodes_buffer(bvh, both_children_hit):
+    """A copy of a built BVH buffer whose root node is rewritten into a cycle
+    (host-side fault injection): child 0 is the root itself with the box
+    [-10, 10]^3; child 1 is the root too (both_children_hit: every visit
+    pushes, so the 96-entry stack fills) or a leaf behind a box no ray meets
+    (the walk loops on child 0 until the node-visit bound).  Every read stays
+    inside the root node."""
+    buf = bvh.buf.cpu().numpy().copy()
+    off = int(buf[32:40].view(np.int64)[0])
+    buf[24:28] = np.array([0], np.int32).view(np.uint8)             # root = node 0
+    node = buf[off:off + 64]
+    f = node[0:48].view(np.float32)
+    d = node[48:64].view(np.int32)
+    big = [-10.0, 10.0]
+    f[0:4] = big + big                                                # child 0: x, y
+    f[8:10] = big                                                     # child 0: z
+    if both_children_hit:
+        f[4:8] = big + big
+        f[10:12] = big
+        d[0:2] = [0, 0]
+    else:
+        f[4:8] = [1e30, 2e30, 1e30, 2e30]
+        f[10:12] = [1e30, 2e30]
+        d[0:2] = [0, ~((0 << 3) | 0)]
+    out = torch.from_numpy(buf).cuda()
+    b2 = nif.BVH.__new__(nif.BVH)
+    b2.buf, b2.n, b2._inputs = out, bvh.n, None
+    return b2
+
+
+@pytest.mark.parametrize("both,code", [(True, L.NIF_ERR_BOUNDS), (False, L.NIF_ERR_TIMEOUT)])
+def test_bvh_traversal_failures_are_reported(both, code):
+    """A cast through a cyclic tree (planted on the host) does not return a
+    silent "no hit": the overflowing stack or the exhausted visit bound is
+    recorded in the buffer's status and bvh_check reports it; a cast through
+    a sound tree stays clean."""
+    w = workloads.tiny_object(n_rays=64, aimed=True)
+    v, t = torch.from_numpy(w.verts).cuda(), torch.from_numpy(w.tris).cuda()
+    good = nif.BVH(v, t)
+    rays = synth.pack_rays(np.array([[0.0, 0.0, -15.0]] * 32), np.array([[0.0, 0.0, 1.0]] * 32), 0.0, 30.0)
+    r = torch.from_numpy(rays).cuda()
+    good.cast_shadow(r)
+    good.check()
+    bad = _box_nodes_buffer(good, both)
+    bad.check()                       # nothing recorded before a cast
+    bad.cast_shadow(r)
+    torch.cuda.synchronize()
+    with pytest.raises(L.NifError) as e:
+        bad.check()
+    assert e.value.code == code
+    # sticky until rebuilt; the sound tree and the context are unaffected
+    with pytest.raises(L.NifError):
+        bad.check()
+    bits = good.cast_shadow(torch.from_numpy(w.rays).cuda())
+    torch.cuda.synchronize()
+    good.check()
+    assert bool(nif.bits_to_bool(bits, 64).any())
+
+
+def test_front_end_top_level_failure_is_reported():
+    """The NIF front end's top-level walk through a cyclic tree records
+    NIF_ERR_TIMEOUT in the call's error word instead of dropping pairs."""
+    w = workloads.tiny_object(n_rays=256, aimed=True)
+    cfg = nif.NifConfig(res=w.res, n_features=2, mlp_dtype=L.NIF_F16)
+    boxes = torch.from_numpy(np.concatenate([w.aabb, w.aabb + 3.0])).cuda()
+    model = nif.NifModel(cfg, boxes, torch.from_numpy(np.tile(w.grid_values.reshape(-1), 2)).cuda(),
+                         torch.from_numpy(synth.flatten_mlp(w.weights)).half().cuda())
+    tlas = nif.BVH.from_boxes(boxes)
+    bad = _box_nodes_buffer(tlas, False)
+    rays = synth.pack_rays(np.array([[0.0, 0.0, -15.0]] * 32), np.array([[0.0, 0.0, 1.0]] * 32), 0.0, 30.0)
+    model.frontend(torch.from_numpy(rays).cuda(), tlas=bad)
+    torch.cuda.synchronize()
+    with pytest.raises(L.NifError) as e:
+        model.check()
+    assert e.value.code == L.NIF_ERR_TIMEOUT

@@ -315,6 +315,73 @@ def test_room_logits_full_size_sampled():
     assert np.abs(zg - zo).max() <= 2e-2, np.abs(zg - zo).max()
 
 
+def test_full_scale_logits_sampled():
+    """The full-scale workload in the bench's launch configurations (480
+    objects, 30.1M triangles, 8,294,400 area-light shadow rays; dense 8 x 2
+    FP16 grids per object; outer/inner 3 x 64 FP16 networks) on both
+    tensor-core schedules: on 2,000 sampled pixels (8,000 shadow rays) the
+    oracle derives its own primary hits, area-light shadow rays (bit-equal to
+    the GPU's) and pairs (a subset of the front end's), and FP64 logits from
+    the counter-generated latents and the seeded weights; the GPU logits
+    agree within the FP16 tolerance (2e-2) on every pair."""
+    import ctypes
+
+    import oracle
+    from oracle import frames
+    from oracle import nif as onif
+    from paper_2306_07191_gb300 import _lib as L
+    from paper_2306_07191_gb300 import workloads
+    cfg = pipeline.full_scale_config()
+    p = pipeline.RoomPipeline(cfg, log=lambda *a: None)          # untrained
+    scale = 1.0
+    L.call("nif_fill_uniform", ctypes.c_void_p(p.g_master.data_ptr()), p.g_master.numel(), pipeline.GRID_SEED,
+           scale, nif._stream())
+    p.model.grids = p.g_master.half()
+    rid, qo, goff, count = p.model.frontend(p.rays, tlas=p.tlas, max_q=cfg.max_pairs_per_ray * p.n_rays + 1024)
+    torch.cuda.synchronize()
+    p.model.check()
+    nq = int(count.item())
+    zs = {}
+    for sched, occ in ((L.NIF_SCHED_SERIAL, 4), (L.NIF_SCHED_PIPELINED, 0)):
+        p.model.cfg.schedule, p.model.cfg.ctas_per_sm = sched, occ
+        zs[sched] = p.model.infer_queries(p.rays, rid, qo, goff, nq)[:nq].cpu().numpy()
+    p.model.check()
+    r = rid[:nq].cpu().numpy().astype(np.int64)
+    q = qo[:nq].cpu().numpy().view(np.uint32)
+    ob = (q & 0x7FFFFFFF).astype(np.int64)
+    spp = cfg.samples
+    ws = p.ws
+    npix = ws.camera.shape[0]
+    pix = np.sort(np.random.default_rng(3).choice(np.unique(r // spp), 2000, replace=False))
+    lp = workloads.area_light_samples(np.random.default_rng(workloads.EVAL_LIGHT_SEED), npix, spp)
+    lp = lp.reshape(npix, spp, 3)[pix].reshape(-1, 3)
+    bvh = oracle.OracleBVH(ws.scene.verts, ws.scene.tris)
+    ors = frames.frame_rays(bvh, ws.camera[pix], lp, cfg.tmin, spp)
+    del bvh
+    gids = (pix[:, None] * spp + np.arange(spp)[None, :]).reshape(-1)
+    assert np.array_equal(ors.view(np.uint32), p.rays[torch.from_numpy(gids).cuda()].cpu().numpy().view(np.uint32))
+    orr, oob, oinn = onif.queries(ors, ws.scene.obj_aabb)
+    assert len(orr) > 8000
+    ncfg = p.model.cfg
+    wr = np.random.default_rng(cfg.seed + 101)
+    nets = []
+    for _ in range(2):
+        flat = synth.flatten_mlp(synth.mlp_init(wr, ncfg.K, cfg.width_mlp, cfg.n_hidden))
+        nets.append(synth.unflatten_mlp(flat.astype(np.float16).astype(np.float64), ncfg.K, cfg.width_mlp,
+                                        cfg.n_hidden))
+    grids = _F16Grids(synth.SplitMixGrids(p.V * cfg.n_features, pipeline.GRID_SEED, scale))
+    om = onif.Model(res=list(cfg.res), F=cfg.n_features, log2_table=cfg.log2_table, obj_aabb=ws.scene.obj_aabb,
+                    grids=grids, nets=nets, net_mode="class")
+    zo = onif.forward(om, ors, orr, oob, oinn)
+    assert np.abs(zo).max() > 0.1
+    for sched, z in zs.items():
+        gpu = {(int(a), int(b)): float(v) for a, b, v in zip(r, ob, z)}
+        keys = [(int(gids[a]), int(b)) for a, b in zip(orr, oob)]
+        assert set(keys) <= set(gpu)
+        zg = np.array([gpu[k] for k in keys])
+        assert np.abs(zg - zo).max() <= 2e-2, (sched, np.abs(zg - zo).max())
+
+
 def test_paper_logits_full_size_sampled():
     """The paper-encoding workload at full size in the bench's launch
     configuration (64 objects, spherical outer R 256 / inner R 128 + 1D
