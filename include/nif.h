@@ -444,13 +444,16 @@ nif_status nif_infer_query_counts(const nif_model_desc* m, const void* d_ws, siz
  * word live in one fixed 16 MiB array inside libnif.so, held on every GPU the
  * process uses until it exits.
  *   - Capacity: about 2.09 million (ray, object) pairs (16 MiB / 8 bytes, less
- *     a few KB of counters).  n above that is rejected up front with
- *     NIF_ERR_WORKSPACE; if the pairs found exceed it, the call returns
- *     NIF_ERR_WORKSPACE and the mask is incomplete.
+ *     a few KB of counters), which is about one 1920x1080 frame of shadow
+ *     rays to one light (2,073,600 rays) when most rays have at most one
+ *     pair.  n above that is rejected up front with NIF_ERR_WORKSPACE (every
+ *     ray could have a pair); if the pairs found exceed it, the call returns
+ *     NIF_ERR_WORKSPACE naming the count and the mask is incomplete.
  *   - Unlike nif_infer the call synchronises `stream` before returning, to
- *     read the overflow check.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *     read the overflow check, so it must never be called while `stream` is
+ *     being captured into a CUDA graph.
+ *   - The first call on a device also looks up the array's device address
+ *     (cudaGetSymbolAddress).
  *   - Every call on a device shares the one array: calls that can overlap on
  *     the GPU (other streams, other host threads) race and must be
  *     serialised by the caller.
@@ -572,10 +575,15 @@ nif_status nif_primary_resolve(const nif_model_desc* m, const nif_ray* d_rays, i
  * the FP32 master weights and grids, the Adam moments and o->step; the
  * gradients are zero between steps and are not stored.  Host buffer layout
  * (nif_state_size(m) bytes, caller-owned):
- *   header: 8 x int64 {magic 0x5346494E ("NIFS"), version 1, K, width,
- *           n_hidden, n_nets, weights (n_nets * P), grid elements (all objects)},
- *           int64 step;
+ *   header: 16 x int64 {magic 0x5346494E ("NIFS"), version 2, K, width,
+ *           n_hidden, n_nets, weights (n_nets * P), grid elements (all objects),
+ *           step, encoding, net_mode, outputs O, levels L, features F,
+ *           grid dtype, level layout (a hash of the resolutions, log2_table,
+ *           res_1d and n_features_1d)};
  *   then FP32 arrays w_master | w_m | w_v | g_master | g_m | g_v.
+ *   Every word but the step must equal the model's, so a state saved from a
+ *   model with other encodings, networks, outputs or grid layout (even with
+ *   the same array sizes) is refused.
  * nif_state_save writes the header on the host and enqueues the device-to-host
  *   copies on `stream`; the buffer is complete once the stream has reached
  *   that point (synchronise before reading it).

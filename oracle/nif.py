@@ -290,10 +290,14 @@ def ray_occlusion(n_rays: int, ray_id, z) -> np.ndarray:
 
 
 # ---------------------------------------------------------------- step 5
-def loss_and_grads(m: Model, rays, ray_id, obj, inner, label):
+def loss_and_grads(m: Model, rays, ray_id, obj, inner, label, sparse_grids: bool = False):
     """L = (1/B) sum (sigmoid(z) - y)^2 with y = 1 for visible pairs, and its
     gradients w.r.t. every network weight and every grid latent.
-    Returns (L, dnets (same structure as m.nets), dgrids (same shape as m.grids))."""
+    Returns (L, dnets (same structure as m.nets), dgrids (same shape as m.grids)).
+    With sparse_grids the grid gradient is returned as (flat index, value)
+    over the latents the pairs tap (flat index ((obj * 2 + grid) * V + vertex)
+    * F + feature), for grids too large to hold densely; the arithmetic is
+    the same sum of weight x dL/dx per tap."""
     B = len(ray_id)
     y = np.asarray(label, dtype=np.float64)
     x, tap_idx, tap_w = encode(m, rays, ray_id, obj, want_taps=True)
@@ -315,9 +319,23 @@ def loss_and_grads(m: Model, rays, ray_id, obj, inner, label):
             dnets[g][li] += da.T @ post[li]
             dh = da @ np.asarray(mats[li], dtype=np.float64)
         dx[sel] = dh
-    dgrids = np.zeros_like(m.grids, dtype=np.float64)
     L_F = len(m.res) * m.F
     obj = np.asarray(obj)
+    if sparse_grids:
+        GF = int(level_layout(m.res, m.log2_table)[2][-1]) * m.F
+        keys, vals = [], []
+        for j in range(3):
+            g = 0 if j < 2 else 1
+            for l in range(len(m.res)):
+                for c in range(8):
+                    for fi in range(m.F):
+                        keys.append((obj * 2 + g) * GF + tap_idx[:, j, l, c] * m.F + fi)
+                        vals.append(tap_w[:, j, l, c] * dx[:, j * L_F + l * m.F + fi])
+        uk, inv = np.unique(np.concatenate(keys), return_inverse=True)
+        acc = np.zeros(len(uk))
+        np.add.at(acc, inv, np.concatenate(vals))
+        return L, dnets, (uk, acc)
+    dgrids = np.zeros_like(m.grids, dtype=np.float64)
     for j in range(3):
         g = 0 if j < 2 else 1
         for l in range(len(m.res)):

@@ -701,7 +701,8 @@ nif_status nif_primary_resolve(const nif_model_desc* m, const nif_ray* d_rays, i
 // ------------------------------------------------------------ checkpoint
 namespace {
 constexpr int64_t kStateMagic = 0x5346494E;  // "NIFS"
-constexpr int kStateHeader = 9;              // int64 words
+constexpr int kStateHeader = 16;             // int64 words
+constexpr int kStepWord = 8;
 
 struct StateShape {
   int64_t nw, ng;
@@ -713,16 +714,39 @@ bool state_shape(const NifParams& p, StateShape* s) {
   return s->nw > 0 && s->ng > 0;
 }
 
+// FNV-1a over the level layout: resolutions, table size, 1D grid shape.
+int64_t layout_word(const NifParams& p) {
+  uint64_t x = 1469598103934665603ull;
+  auto mix = [&](int64_t v) {
+    for (int b = 0; b < 8; ++b) {
+      x ^= static_cast<uint64_t>(v >> (8 * b)) & 0xffu;
+      x *= 1099511628211ull;
+    }
+  };
+  for (int l = 0; l < p.L; ++l) mix(p.res[l]);
+  mix(p.log2T);
+  mix(p.R1);
+  mix(p.F1);
+  return static_cast<int64_t>(x >> 1);
+}
+
 void state_header(const NifParams& p, const StateShape& sh, int64_t step, int64_t h[kStateHeader]) {
   h[0] = kStateMagic;
-  h[1] = 1;
+  h[1] = 2;
   h[2] = p.K;
   h[3] = p.width;
   h[4] = p.n_hidden;
   h[5] = p.n_nets;
   h[6] = sh.nw;
   h[7] = sh.ng;
-  h[8] = step;
+  h[kStepWord] = step;
+  h[9] = p.enc;
+  h[10] = p.net_mode;
+  h[11] = p.O;
+  h[12] = p.L;
+  h[13] = p.F;
+  h[14] = p.grid_dtype;
+  h[15] = layout_word(p);
 }
 }  // namespace
 
@@ -768,11 +792,12 @@ nif_status nif_state_load(nif_model_desc* m, nif_optim_desc* o, const void* h_bu
   NIF_CHECK_ARG(bytes >= nif_state_size(m), "nif_state_load: buffer too small");
   const int64_t* h = static_cast<const int64_t*>(h_buf);
   int64_t want[kStateHeader];
-  state_header(p, sh, h[8], want);
-  for (int i = 0; i < kStateHeader - 1; ++i)
-    NIF_CHECK_ARG(h[i] == want[i], "nif_state_load: header word %d is %lld, the model needs %lld", i,
+  state_header(p, sh, h[kStepWord], want);
+  for (int i = 0; i < kStateHeader; ++i)
+    NIF_CHECK_ARG(i == kStepWord || h[i] == want[i],
+                  "nif_state_load: header word %d is %lld, the model needs %lld", i,
                   static_cast<long long>(h[i]), static_cast<long long>(want[i]));
-  NIF_CHECK_ARG(h[8] >= 0 && h[8] < (int64_t(1) << 31), "nif_state_load: bad step count");
+  NIF_CHECK_ARG(h[kStepWord] >= 0 && h[kStepWord] < (int64_t(1) << 31), "nif_state_load: bad step count");
   NIF_CHECK_ARG(o->d_w_master && o->d_w_m && o->d_w_v && o->d_g_master && o->d_g_m && o->d_g_v &&
                     o->d_w_grad && o->d_g_grad,
                 "nif_state_load: null optimiser buffer");
@@ -786,7 +811,7 @@ nif_status nif_state_load(nif_model_desc* m, nif_optim_desc* o, const void* h_bu
   }
   NIF_CUDA_TRY(cudaMemsetAsync(o->d_w_grad, 0, sizeof(float) * sh.nw, st));
   NIF_CUDA_TRY(cudaMemsetAsync(o->d_g_grad, 0, sizeof(float) * sh.ng, st));
-  o->step = static_cast<int32_t>(h[8]);
+  o->step = static_cast<int32_t>(h[kStepWord]);
   // 16-bit (or FP32) copies the forward reads
   void* wcopy = m->mlp_dtype == NIF_E4M3 ? nullptr : const_cast<void*>(m->d_weights);
   if (wcopy && wcopy != o->d_w_master) {

@@ -145,7 +145,7 @@ def test_state_checkpoint_size_and_header_checks(L):
     V = 5723320
     nw, ng = 2 * P, 64 * 2 * V * 2
     size = L.lib.nif_state_size(ctypes.byref(d))
-    assert size == 9 * 8 + 4 * 3 * (nw + ng)
+    assert size == 16 * 8 + 4 * 3 * (nw + ng)
     o = L.OptimDesc()
     for name in ("d_w_master", "d_w_grad", "d_w_m", "d_w_v", "d_g_master", "d_g_grad", "d_g_m", "d_g_v"):
         setattr(o, name, 256)  # never dereferenced: the header check fails first
@@ -155,6 +155,21 @@ def test_state_checkpoint_size_and_header_checks(L):
     assert "header word 0" in L.last_error()
     assert L.lib.nif_state_load(ctypes.byref(d), ctypes.byref(o), buf.ctypes.data_as(ctypes.c_void_p), 16,
                                 None) == L.NIF_ERR_ARG
+    # the same array sizes saved from a model with another encoding, network
+    # mode, output count, level count, feature count, grid dtype or level
+    # layout: refused at that header word
+    good = [0x5346494E, 2, 96, 64, 3, 2, nw, ng, 7, L.NIF_ENC_MULTIRES, L.NIF_NETS_CLASS, 1, 16, 2, L.NIF_F16]
+    for word, bad in ((9, L.NIF_ENC_SPHERICAL_OUTER), (10, L.NIF_NETS_OBJECT), (11, 5), (12, 8), (13, 4),
+                      (14, L.NIF_F32), (15, 12345)):
+        h = np.zeros(64, dtype=np.int64)
+        h[:15] = good
+        if word < 15:
+            h[word] = bad
+        else:
+            h[15] = bad
+        assert L.lib.nif_state_load(ctypes.byref(d), ctypes.byref(o), h.ctypes.data_as(ctypes.c_void_p), size,
+                                    None) == L.NIF_ERR_ARG
+        assert f"header word {word} " in L.last_error(), (word, L.last_error())
 
 
 def test_argument_errors_of_the_widened_calls(L):

@@ -60,22 +60,16 @@ def _frontend(model, rays_t):
     return ray_id[:nq].contiguous(), qobj[:nq].contiguous(), goff, nq, r, (q & 0x7FFFFFFF).astype(np.int64), (q >> 31).astype(bool)
 
 
-def _well_conditioned(om, rays, r, ob, inn):
-    """Pairs whose FP64 gradient is defined to FP32 resolution: the entry and
-    exit points move < 1e-4 under a 1e-6 relative perturbation of the ray (a
-    segment grazing a box face is ill-conditioned), and no hidden
-    pre-activation lies within 1e-3 of its layer's RMS of a ReLU kink."""
+def _away_from_kinks(om, rays, r, ob, inn, thr=1e-4):
+    """Pairs whose FP64 gradient is defined to FP32 resolution: no hidden
+    pre-activation within thr x its layer's RMS of the activation's kink.
+    At a kink the gradient of a pair jumps, so an FP32 and an FP64 forward of
+    the same pair can take different sides of it.  Measured on the CPU with
+    exact face points: over all pairs, the FP64 gradient itself moves by
+    2.6e-3 (ReLU) and 5.5e-3 (leaky) relative L2 when the rays are perturbed
+    by one FP32 ulp; over the pairs kept at thr = 1e-4 (98.3-98.5% of them)
+    it moves by 2e-5."""
     keep = np.ones(len(r), bool)
-    rng = np.random.default_rng(0)
-    for k in np.unique(ob):
-        sel = np.nonzero(ob == k)[0]
-        a = onif.entry_exit(rays[r[sel]], om.obj_aabb[k])
-        pr = rays[r[sel]].astype(np.float64).copy()
-        pr[:, 0:3] *= 1 + 1e-6 * rng.standard_normal((len(sel), 3))
-        pr[:, 4:7] *= 1 + 1e-6 * rng.standard_normal((len(sel), 3))
-        b = onif.entry_exit(pr, om.obj_aabb[k])
-        dev = np.maximum(np.abs(a[0] - b[0]).max(1), np.abs(a[1] - b[1]).max(1))
-        keep[sel] &= dev < 1e-4
     x = onif.encode(om, rays, r, ob)
     net = om.net_of(ob, inn)
     for g in np.unique(net):
@@ -83,16 +77,50 @@ def _well_conditioned(om, rays, r, ob, inn):
         _, pre, _ = onif.mlp_forward(x[sel], om.nets[g], om.act, om.slope)
         for a in pre:
             rms = np.sqrt(np.mean(a * a))
-            keep[sel] &= np.abs(a).min(axis=1) > 1e-3 * rms
+            keep[sel] &= np.abs(a).min(axis=1) > thr * rms
     return keep
+
+
+def _tapped(om, rays, r, ob, margin=1e-4):
+    """Flat indices ((obj * 2 + grid) * V + vertex) * F + feature of every
+    latent a pair may tap: the corners of the oracle's own cells, widened by
+    one cell along an axis where the point lies within `margin` of a cell face
+    (there an FP32 evaluation may take the neighbouring cell, whose far
+    corners then get a weight of a few ulps)."""
+    sizes, hashed, off = onif.level_layout(om.res, om.log2_table)
+    GF = int(off[-1]) * om.F
+    keys = []
+    for k in np.unique(ob):
+        sel = np.nonzero(ob == k)[0]
+        pts = onif.entry_exit(rays[r[sel]], om.obj_aabb[k])
+        for j, u in enumerate(pts):
+            g = 0 if j < 2 else 1
+            for l, R in enumerate(om.res):
+                s = u * R
+                i = np.clip(np.floor(s), 0, R - 1).astype(np.int64)
+                f = s - i
+                lo = np.where(f < margin, np.maximum(i - 1, 0), i)
+                hi = np.where(f > 1 - margin, np.minimum(i + 2, R), i + 1)
+                for dx in range(-1, 3):
+                    for dy in range(-1, 3):
+                        for dz in range(-1, 3):
+                            c = i[:, None] + np.array([[dx, dy, dz]])
+                            ok = np.all((c >= lo) & (c <= hi), axis=1)
+                            if not ok.any():
+                                continue
+                            v = onif.corner_index(c[ok, 0], c[ok, 1], c[ok, 2], R, hashed[l], om.log2_table)
+                            for fi in range(om.F):
+                                keys.append((k * 2 + g) * GF + (off[l] + v) * om.F + fi)
+    return np.unique(np.concatenate(keys))
 
 
 @pytest.mark.parametrize("act", [L.NIF_ACT_RELU, L.NIF_ACT_LEAKY])
 def test_gradients_match_oracle(act):
     model, om, rays, flat, grid = _setup(act=act, n_rays=60000)
-    # the oracle's own pairs, restricted to well-conditioned ones, grouped by network
+    # the oracle's own pairs away from activation kinks, grouped by network
     r, ob, inn = onif.queries(rays, om.obj_aabb)
-    keep = _well_conditioned(om, rays, r, ob, inn)
+    keep = _away_from_kinks(om, rays, r, ob, inn)
+    assert keep.mean() > 0.98
     r, ob, inn = r[keep], ob[keep], inn[keep]
     order = np.argsort(inn, kind="stable")
     r, ob, inn = r[order], ob[order], inn[order]
@@ -116,10 +144,115 @@ def test_gradients_match_oracle(act):
     assert _rel_l2(gw, want_w) <= 1e-3
     gg = g.grad.cpu().numpy().reshape(dgrids.shape)
     assert _rel_l2(gg, dgrids) <= 1e-3
-    # latents the FP64 oracle leaves at exactly zero (no tap, or a point exactly
-    # on a cell face, whose far-side weight is 0 in FP64 and an ulp in FP32)
-    # get at most rounding-level values
-    assert np.abs(gg[dgrids == 0]).max() <= 1e-4 * np.abs(dgrids).max()
+    # a latent no pair taps is never written: exactly zero
+    untouched = np.ones(gg.size, bool)
+    untouched[_tapped(om, rays, r, ob)] = False
+    assert untouched.sum() > 0.5 * gg.size
+    assert not np.any(gg.reshape(-1)[untouched])
+
+
+class _Recorder:
+    """A grid table that records the entries a lookup asks for (and answers
+    zeros): the oracle's own tap indices, before any value is known."""
+
+    def __init__(self, sink, base):
+        self.sink, self.base = sink, base
+
+    def __getitem__(self, idx):
+        self.sink.append(self.base + np.asarray(idx, np.int64).reshape(-1))
+        return np.zeros(np.shape(idx))
+
+
+class _Sparse:
+    """Entries of a large grid held as sorted (flat index, value) pairs."""
+
+    def __init__(self, keys, vals, base):
+        self.keys, self.vals, self.base = keys, vals, base
+
+    def __getitem__(self, idx):
+        k = self.base + np.asarray(idx, np.int64)
+        pos = np.searchsorted(self.keys, k)
+        assert np.array_equal(self.keys[pos], k)
+        return self.vals[pos]
+
+
+class _Grids:
+    def __init__(self, GF, make):
+        self.GF, self.make = GF, make
+
+    def __getitem__(self, kg):
+        k, g = kg
+        return self.make((int(k) * 2 + int(g)) * self.GF)
+
+
+def test_room_subset_gradients_match_oracle():
+    """Sec. 5 'Training' on the room workload: after the 64 Adam steps of
+    online training, the gradients of the L2 loss on 1,000 sampled pixels
+    of the frame (their shadow rays and pairs derived by the oracle itself:
+    hashed 16 x 2 grids with 2^19 entries per level, 1.465G FP32 master
+    latents, the trained 3 x 64 outer and inner networks) agree with the FP64
+    oracle within relative L2 1e-3, for the weights and for the latents; the
+    pairs away from activation kinks are compared (the fraction excluded is
+    asserted below 3%), and every latent no pair taps stays exactly zero."""
+    import oracle
+    from oracle import frames
+    from paper_2306_07191_gb300 import pipeline
+    cfg = pipeline.RoomConfig()
+    p = pipeline.RoomPipeline(cfg, log=lambda *a: None)
+    p.train()
+    gm, wm = p.trainer.g_master, p.trainer.w_master
+    ws = p.ws
+    pix = np.sort(np.random.default_rng(9).choice(ws.camera.shape[0], 1000, replace=False))
+    ors = frames.frame_rays(oracle.OracleBVH(ws.scene.verts, ws.scene.tris), ws.camera[pix], ws.light, cfg.tmin)
+    assert np.array_equal(ors.view(np.uint32), p.rays[torch.from_numpy(pix).cuda()].cpu().numpy().view(np.uint32))
+    r, ob, inn = onif.queries(ors, ws.scene.obj_aabb)
+    assert len(r) > 300 and inn.any() and (~inn).any()
+    GF = p.V * cfg.n_features
+    # the oracle's tap indices, then the trained latents at those entries
+    asked = []
+    nets = []
+    wflat = wm.cpu().numpy().astype(np.float64)
+    P = wflat.size // 2
+    for g in range(2):
+        nets.append(synth.unflatten_mlp(wflat[g * P:(g + 1) * P], 3 * len(cfg.res) * cfg.n_features,
+                                        cfg.width_mlp, cfg.n_hidden))
+    rec = onif.Model(res=list(cfg.res), F=cfg.n_features, log2_table=cfg.log2_table, obj_aabb=ws.scene.obj_aabb,
+                     grids=_Grids(GF, lambda base: _Recorder(asked, base)), nets=nets, net_mode="class")
+    onif.encode(rec, ors, r, ob)
+    keys = np.unique(np.concatenate(asked))
+    vals = gm[torch.from_numpy(keys).cuda()].cpu().numpy().astype(np.float64)
+    om = onif.Model(res=list(cfg.res), F=cfg.n_features, log2_table=cfg.log2_table, obj_aabb=ws.scene.obj_aabb,
+                    grids=_Grids(GF, lambda base: _Sparse(keys, vals, base)), nets=nets, net_mode="class")
+    keep = _away_from_kinks(om, ors, r, ob, inn)
+    assert keep.mean() > 0.97
+    r, ob, inn = r[keep], ob[keep], inn[keep]
+    order = np.argsort(inn, kind="stable")
+    r, ob, inn = r[order], ob[order], inn[order]
+    nq = len(r)
+    y = _labels_for(r, ob)
+    Lo, dnets, (gk, gv) = onif.loss_and_grads(om, ors, r, ob, inn, y.astype(np.float64), sparse_grids=True)
+    # the same pairs on the GPU: the FP32 masters through nif_fwd_train,
+    # nif_loss, nif_mlp_bwd and nif_grid_bwd
+    rays_t = torch.from_numpy(ors).cuda()
+    ray_id = torch.from_numpy(r.astype(np.int32)).cuda()
+    qobj = torch.from_numpy((ob.astype(np.uint32) | (inn.astype(np.uint32) << 31)).view(np.int32)).cuda()
+    goff = torch.tensor([0, int((~inn).sum()), nq], dtype=torch.int64, device="cuda")
+    g = gm.detach().clone().requires_grad_(True)
+    w = wm.detach().clone().requires_grad_(True)
+    z = nif.NifQueryFn.apply(g, w, p.model, rays_t, ray_id, qobj, goff, nq)
+    loss = nif.NifLossFn.apply(z, torch.from_numpy(y).cuda())
+    loss.backward()
+    assert abs(float(loss.item()) - Lo) <= 1e-5 * max(1.0, Lo)
+    gw = w.grad.cpu().numpy()
+    want_w = np.concatenate([np.concatenate([m.reshape(-1) for m in net]) for net in dnets])
+    assert _rel_l2(gw, want_w) <= 1e-3
+    gk_t = torch.from_numpy(gk).cuda()
+    gg = g.grad[gk_t].cpu().numpy()
+    assert np.abs(gv).max() > 0 and _rel_l2(gg, gv) <= 1e-3
+    # every latent no pair taps (of the 1.465G) is exactly zero
+    rest = g.grad.detach()
+    rest[torch.from_numpy(_tapped(om, ors, r, ob)).cuda()] = 0
+    assert int(torch.count_nonzero(rest).item()) == 0
 
 
 def test_adam_matches_oracle_step_by_step():
@@ -202,6 +335,16 @@ def test_checkpoint_resume_restores_state_and_continues():
     tr3 = nif.Trainer(other, lr=1e-2)
     with pytest.raises(L.NifError):
         tr3.load_state_bytes(buf)
+    # the same array sizes with another level layout (resolutions permuted)
+    # or grid dtype refuse it too
+    for change in ({"res": [9, 4, 20, 70]}, {"grid_dtype": L.NIF_F16}):
+        cfg4 = nif.NifConfig(**{**model.cfg.__dict__, **change})
+        gdt = torch.float16 if cfg4.grid_dtype == L.NIF_F16 else torch.float32
+        m4 = nif.NifModel(cfg4, model.obj_aabb, model.grids.to(gdt), model.weights.clone())
+        assert nif.NifModel.grid_vertices(cfg4) == nif.NifModel.grid_vertices(model.cfg)
+        with pytest.raises(L.NifError) as e:
+            nif.Trainer(m4, lr=1e-2).load_state_bytes(buf)
+        assert "header word" in str(e.value)
 
 
 def test_deterministic_steps_repeat_and_resume_bit_for_bit():

@@ -328,6 +328,12 @@ def test_gradients_match_central_finite_differences(act, n_hidden, res):
     y = rng.integers(0, 2, size=len(rid)).astype(np.float64)
     L, dnets, dgrids = onif.loss_and_grads(m, rays, rid, obj, inner, y)
     assert abs(L - _loss_only(m, rays, rid, obj, inner, y)) < 1e-14
+    # the sparse form holds the same sums at the tapped latents, nothing else
+    _, _, (keys, vals) = onif.loss_and_grads(m, rays, rid, obj, inner, y, sparse_grids=True)
+    dense = np.zeros(dgrids.size)
+    dense[keys] = vals
+    np.testing.assert_allclose(dense, dgrids.reshape(-1), rtol=1e-13, atol=1e-16)
+    assert np.all(dgrids.reshape(-1)[np.setdiff1d(np.arange(dgrids.size), keys)] == 0)
 
     def fd(get, set_):
         th = get()

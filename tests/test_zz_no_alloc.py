@@ -89,3 +89,69 @@ def test_noalloc_rejects_work_beyond_its_scratch():
     assert st == L.NIF_ERR_WORKSPACE
     assert "scratch" in L.last_error()
     assert L.lib.nif_infer_noalloc(ctypes.byref(d), None, None, 10, None, None) == L.NIF_ERR_ARG
+
+
+def test_noalloc_first_call_matches_oracle():
+    """The first call's mask against the FP64 oracle directly: every ray
+    whose oracle logit is farther from 0 than the FP16 tolerance (2e-2) gets
+    the oracle's decision (occluded iff z < 0)."""
+    from oracle import nif as onif
+    w = workloads.tiny_object(n_rays=20000, aimed=True, grid_scale=1.0)
+    model, rays, _ = _tiny_model(L.NIF_F16)
+    n = int(rays.shape[0])
+    bits = nif.empty_bits(n)
+    assert _noalloc(model, rays, bits) == L.NIF_OK, L.last_error()
+    torch.cuda.synchronize()
+    got = nif.bits_to_bool(bits, n).cpu().numpy()
+    r, ob, inn = onif.queries(w.rays, w.aabb)
+    grids = w.grid_values.astype(np.float16).astype(np.float64)
+    nets = [synth.unflatten_mlp(synth.flatten_mlp(w.weights).astype(np.float16).astype(np.float64),
+                                model.cfg.K, 64, 3)]
+    om = onif.Model(res=w.res, F=2, log2_table=19, obj_aabb=w.aabb, grids=grids, nets=nets)
+    z = onif.forward(om, w.rays, r, ob, inn)
+    clear = np.abs(z) > 2e-2
+    assert clear.sum() > 0.9 * len(z) and (z[clear] < 0).any() and (z[clear] > 0).any()
+    want = np.zeros(n, bool)
+    want[r[z < 0]] = True
+    sure = np.zeros(n, bool)
+    sure[np.setdiff1d(np.arange(n), r)] = True      # no pair: visible for certain
+    sure[r[clear]] = True                            # one pair per ray here
+    assert np.array_equal(got[sure], want[sure])
+
+
+def test_noalloc_reports_pairs_beyond_its_scratch_after_the_call():
+    """A ray count within the scratch whose pairs are not: 200,000 rays
+    through the common core of 16 nested boxes make 3.2M pairs, more than
+    the ~2.09M the scratch holds.  The call is not refused up front; the
+    front end drops the pairs beyond capacity on the device and the call
+    returns NIF_ERR_WORKSPACE naming the count found.  A call within
+    capacity afterwards is exact again."""
+    rng = np.random.default_rng(5)
+    k = np.arange(16, dtype=np.float32)[:, None]
+    aabb = np.concatenate([-(1.0 + k) * np.ones((16, 3), np.float32), (1.0 + k) * np.ones((16, 3), np.float32)],
+                          axis=1).astype(np.float32)
+    res = [4, 8]
+    cfg = nif.NifConfig(res=res, n_features=2, log2_table=14, grid_dtype=L.NIF_F16, n_hidden=3, width=64,
+                        mlp_dtype=L.NIF_F16, net_mode=L.NIF_NETS_CLASS)
+    V = nif.NifModel.grid_vertices(cfg)
+    grids = torch.from_numpy(rng.uniform(-1, 1, 16 * 2 * V * 2).astype(np.float32)).half().cuda()
+    mats = np.concatenate([synth.flatten_mlp(synth.mlp_init(rng, cfg.K, 64, 3)) for _ in range(2)])
+    model = nif.NifModel(cfg, torch.from_numpy(aabb).cuda(), grids, torch.from_numpy(mats).half().cuda())
+    n = 200_000
+    o = synth.unit_vectors(rng, n) * 40.0
+    rays = synth.pack_rays(o, -o / 40.0, 0.0, np.inf)     # every ray crosses all 16 boxes
+    rays_t = torch.from_numpy(rays).cuda()
+    bits = nif.empty_bits(n)
+    st = _noalloc(model, rays_t, bits)
+    assert st == L.NIF_ERR_WORKSPACE
+    msg = L.last_error()
+    assert "3200000" in msg and "incomplete" in msg
+    # within capacity (100,000 rays, 1.6M pairs): equal to nif_infer
+    half = rays_t[: n // 2].contiguous()
+    ref = nif.empty_bits(n // 2)
+    model.infer(half, ref, max_q=17 * (n // 2))
+    model.check()
+    got = nif.empty_bits(n // 2)
+    assert _noalloc(model, half, got) == L.NIF_OK, L.last_error()
+    torch.cuda.synchronize()
+    assert torch.equal(got, ref)
