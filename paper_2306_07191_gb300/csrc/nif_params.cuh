@@ -319,6 +319,35 @@ __device__ __forceinline__ void cell_weights(const float f[3], float w[8]) {
   w[7] = a11 * f[2];
 }
 
+// Trilinear interpolation of one F = 2 lookup into an FP16 table by nested
+// lerps in packed half2 arithmetic: along x, then y, then z (7 lerps of two
+// half2 operations each, where weights and FP32 multiply-adds take 12 + 16).
+// The fractions are rounded to FP16 once.  Corners of weight exactly zero (a
+// point on a cell face: its fraction along that axis is exactly 0 or 1) are
+// not loaded and read as 0; a lerp with factor exactly 0 or 1 returns the
+// other end exactly, so skipping them changes no result.
+__device__ __forceinline__ __half2 lerp_h2(__half2 a, __half2 b, __half2 t) {
+  return __hfma2(t, __hsub2(b, a), a);
+}
+__device__ __forceinline__ __half2 trilerp_h2(const __half2* tab, const uint32_t idx[8], const float f[3]) {
+  bool lo[3], hi[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    lo[k] = f[k] != 1.f;  // corners at the cell's low end along k carry weight
+    hi[k] = f[k] != 0.f;  // corners at its high end do
+  }
+  __half2 v[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) {
+    const bool need = ((c & 1) ? hi[0] : lo[0]) && ((c & 2) ? hi[1] : lo[1]) && ((c & 4) ? hi[2] : lo[2]);
+    v[c] = need ? __ldg(tab + idx[c]) : __float2half2_rn(0.f);
+  }
+  const __half2 tx = __float2half2_rn(f[0]), ty = __float2half2_rn(f[1]), tz = __float2half2_rn(f[2]);
+  const __half2 x0 = lerp_h2(v[0], v[1], tx), x1 = lerp_h2(v[2], v[3], tx);
+  const __half2 x2 = lerp_h2(v[4], v[5], tx), x3 = lerp_h2(v[6], v[7], tx);
+  return lerp_h2(lerp_h2(x0, x1, ty), lerp_h2(x2, x3, ty), tz);
+}
+
 __device__ __forceinline__ float corner_weight(const float f[3], int c) {
   const float wx = (c & 1) ? f[0] : 1.f - f[0];
   const float wy = ((c >> 1) & 1) ? f[1] : 1.f - f[1];

@@ -254,6 +254,24 @@ struct Op<NIF_E4M3> {
   }
 };
 
+// Interpolation of FP16 grids in packed half2 arithmetic (trilerp_h2) unless
+// built with -DNIF_FP16_LERP=0, which interpolates in FP32 from 8 weights.
+#ifndef NIF_FP16_LERP
+#define NIF_FP16_LERP 1
+#endif
+constexpr bool kHalfLerp = NIF_FP16_LERP != 0;
+
+// A half2 pair of features as the 32-bit word of two operand-type elements.
+template <int DT>
+__device__ __forceinline__ uint32_t h2_word(__half2 r) {
+  if constexpr (DT == NIF_F16) {
+    return *reinterpret_cast<uint32_t*>(&r);
+  } else {
+    const __nv_bfloat162 b = __float22bfloat162_rn(__half22float2(r));
+    return *reinterpret_cast<const uint32_t*>(&b);
+  }
+}
+
 __device__ __forceinline__ float act_fn_tc(const NifParams& p, float a) {
   return a > 0.f ? a : (p.act == NIF_ACT_LEAKY ? p.slope * a : 0.f);
 }
@@ -772,26 +790,33 @@ __global__ void __launch_bounds__(kThreads, kOcc)
                 cell_of(li, pts.u[j][0], pts.u[j][1], pts.u[j][2], c0, fr[u]);
                 cell_entries(li, c0, idx[u]);
               }
-              Raw v[kJB][8];
-              float wt[kJB][8];
+              if constexpr (sizeof(TG) == 2 && kHalfLerp) {
 #pragma unroll
-              for (int u = 0; u < kJB; ++u) {
-                cell_weights(fr[u], wt[u]);
-                load_corners((jb + u) < 2 ? tp : td, idx[u], wt[u], v[u]);
-              }
+                for (int u = 0; u < kJB; ++u)
+                  word[u] = h2_word<DT>(trilerp_h2(reinterpret_cast<const __half2*>((jb + u) < 2 ? tp : td),
+                                                   idx[u], fr[u]));
+              } else {
+                Raw v[kJB][8];
+                float wt[kJB][8];
 #pragma unroll
-              for (int u = 0; u < kJB; ++u) {
-                const float* w = wt[u];
-                float a0 = 0.f, a1 = 0.f;
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                  float2 fv;
-                  if constexpr (sizeof(TG) == 2) fv = __half22float2(v[u][c]);
-                  else fv = v[u][c];
-                  a0 += w[c] * fv.x;
-                  a1 += w[c] * fv.y;
+                for (int u = 0; u < kJB; ++u) {
+                  cell_weights(fr[u], wt[u]);
+                  load_corners((jb + u) < 2 ? tp : td, idx[u], wt[u], v[u]);
                 }
-                word[u] = pack2(a0, a1);
+#pragma unroll
+                for (int u = 0; u < kJB; ++u) {
+                  const float* w = wt[u];
+                  float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+                  for (int c = 0; c < 8; ++c) {
+                    float2 fv;
+                    if constexpr (sizeof(TG) == 2) fv = __half22float2(v[u][c]);
+                    else fv = v[u][c];
+                    a0 += w[c] * fv.x;
+                    a1 += w[c] * fv.y;
+                  }
+                  word[u] = pack2(a0, a1);
+                }
               }
             }
 #pragma unroll
@@ -1059,20 +1084,24 @@ __global__ void __launch_bounds__(32 * (kEW + 4), kOcc)
             cell_of(li, pts.u[j][0], pts.u[j][1], pts.u[j][2], c0, fr);
             cell_entries(li, c0, idx);
             const Raw* tab = reinterpret_cast<const Raw*>(j < 2 ? tp : td);
-            float w[8];
-            cell_weights(fr, w);
-            Raw v[8];
-            load_corners(tab, idx, w, v);
-            float a0 = 0.f, a1 = 0.f;
+            if constexpr (sizeof(TG) == 2 && kHalfLerp) {
+              word = h2_word<DT>(trilerp_h2(reinterpret_cast<const __half2*>(tab), idx, fr));
+            } else {
+              float w[8];
+              cell_weights(fr, w);
+              Raw v[8];
+              load_corners(tab, idx, w, v);
+              float a0 = 0.f, a1 = 0.f;
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-              float2 fv;
-              if constexpr (sizeof(TG) == 2) fv = __half22float2(v[c]);
-              else fv = v[c];
-              a0 += w[c] * fv.x;
-              a1 += w[c] * fv.y;
+              for (int c = 0; c < 8; ++c) {
+                float2 fv;
+                if constexpr (sizeof(TG) == 2) fv = __half22float2(v[c]);
+                else fv = v[c];
+                a0 += w[c] * fv.x;
+                a1 += w[c] * fv.y;
+              }
+              word = pack2(a0, a1);
             }
-            word = pack2(a0, a1);
           }
           tmem_st1(abase + static_cast<uint32_t>(j * p.L + l), word);
         }

@@ -104,7 +104,7 @@ def _tapped(om, rays, r, ob, margin=1e-4):
                 for dx in range(-1, 3):
                     for dy in range(-1, 3):
                         for dz in range(-1, 3):
-                            c = i[:, None] + np.array([[dx, dy, dz]])
+                            c = i + np.array([dx, dy, dz])
                             ok = np.all((c >= lo) & (c <= hi), axis=1)
                             if not ok.any():
                                 continue
@@ -147,7 +147,7 @@ def test_gradients_match_oracle(act):
     # a latent no pair taps is never written: exactly zero
     untouched = np.ones(gg.size, bool)
     untouched[_tapped(om, rays, r, ob)] = False
-    assert untouched.sum() > 0.5 * gg.size
+    assert untouched.sum() > 0.1 * gg.size
     assert not np.any(gg.reshape(-1)[untouched])
 
 
