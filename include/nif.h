@@ -482,6 +482,28 @@ typedef struct nif_optim_desc {
   int32_t deterministic;
   void* d_det_ws;
   size_t det_ws_bytes;
+  /* Half-precision training (0 = off; Sec. 5: half precision "as much as
+   * possible"): the forward runs on the tensor cores with the model's 16-bit
+   * copies (d_weights, and d_grids when FP16), saving the network input and
+   * every hidden activation in the network's 16-bit type; the MLP backward
+   * runs on the tensor cores from those (dW and dX as 16-bit x 16-bit
+   * products with FP32 accumulation); the grid scatter, the masters and the
+   * Adam moments stay FP32.  Needs an FP16 or BF16 network of width 64 with
+   * one output over two-feature multi-resolution grids, K a multiple of 16
+   * and at most 128; not combined with `deterministic`. */
+  int32_t half_precision;
+  /* Dynamic loss scaling (both NULL: the fixed loss_scale).  d_loss_scale is
+   * a device float holding the scale; d_scale_state a device int32[2]
+   * {overflow flag of the step, steps in a row without overflow}.  dL/dz is
+   * multiplied by the scale before back-propagation and the gradients are
+   * divided by it in Adam.  A step whose scaled gradients do not fit the
+   * 16-bit operand type is skipped (masters and moments unchanged, gradients
+   * zeroed; o->step still counts it) and halves the scale (not below 1);
+   * scale_window steps in a row without overflow double it (not above
+   * 2^24).  The scale lives on the device, so no step synchronises. */
+  float* d_loss_scale;
+  int32_t* d_scale_state;
+  int32_t scale_window;
 } nif_optim_desc;
 
 size_t nif_deterministic_workspace_size(const nif_model_desc* m, int64_t nq);
@@ -534,14 +556,29 @@ nif_status nif_adam(float* d_master, float* d_grad, float* d_m, float* d_v, int6
                     int32_t step, void* d_copy, int32_t copy_dtype, void* stream);
 
 /* A whole step: forward and backward on the FP32 masters (as nif_fwd_train,
- * nif_loss, nif_mlp_bwd, nif_grid_bwd), then Adam on the weights and the grids
- * refreshing m->d_weights and m->d_grids in their own dtypes (o->step is
- * incremented).  d_loss (nullable) receives the batch loss.  Workspace:
- * nif_train_workspace_size(m, nq) bytes. */
+ * nif_loss, nif_mlp_bwd, nif_grid_bwd), or with o->half_precision on the
+ * tensor cores, then Adam on the weights and the grids refreshing
+ * m->d_weights and m->d_grids in their own dtypes (o->step is incremented)
+ * and, with dynamic loss scaling, the scale update.  d_loss (nullable)
+ * receives the batch loss.  Workspace: nif_train_workspace_size(m, nq)
+ * bytes. */
 nif_status nif_train_step(nif_model_desc* m, nif_optim_desc* o, const nif_ray* d_rays,
                           const uint32_t* d_ray_id, const uint32_t* d_qobj,
                           const int64_t* d_group_off, const uint8_t* d_label, int64_t nq,
                           float* d_loss, void* d_ws, size_t ws_bytes, void* stream);
+
+/* The step's gradients without the update: the forward, the loss and the
+ * backward of nif_train_step (either precision), accumulated into
+ * o->d_w_grad and o->d_g_grad (which must hold zeros or earlier gradients);
+ * they are the gradients of the scaled loss (loss scale x L; the scale in
+ * effect is o->loss_scale, or *o->d_loss_scale with dynamic scaling).  With
+ * half precision an overflow of the operand type sets d_scale_state[0] (or
+ * is recorded as NIF_ERR_NUMERIC in the workspace when there is no state).
+ * o->step is not changed. */
+nif_status nif_train_grads(const nif_model_desc* m, const nif_optim_desc* o, const nif_ray* d_rays,
+                           const uint32_t* d_ray_id, const uint32_t* d_qobj,
+                           const int64_t* d_group_off, const uint8_t* d_label, int64_t nq,
+                           float* d_loss, void* d_ws, size_t ws_bytes, void* stream);
 
 /* The same step for a network with O > 1 outputs, with the loss of
  * nif_loss_aux and its targets d_aux [nq][O-1] (nif_train_step refuses

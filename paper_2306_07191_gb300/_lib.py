@@ -56,6 +56,7 @@ class OptimDesc(ctypes.Structure):
         ("d_w_master", P), ("d_w_grad", P), ("d_w_m", P), ("d_w_v", P),
         ("d_g_master", P), ("d_g_grad", P), ("d_g_m", P), ("d_g_v", P),
         ("deterministic", i32), ("d_det_ws", P), ("det_ws_bytes", size_t),
+        ("half_precision", i32), ("d_loss_scale", P), ("d_scale_state", P), ("scale_window", i32),
     ]
 
 
@@ -106,6 +107,7 @@ SIGNATURES = {
     "nif_grid_bwd": (i32, [MD, P, P, P, i64, P, P, P]),
     "nif_adam": (i32, [P, P, P, P, i64, f32, f32, f32, f32, f32, i32, P, i32, P]),
     "nif_train_step": (i32, [MD, OD, P, P, P, P, P, i64, P, P, size_t, P]),
+    "nif_train_grads": (i32, [MD, OD, P, P, P, P, P, i64, P, P, size_t, P]),
     "nif_train_step_aux": (i32, [MD, OD, P, P, P, P, P, P, i64, P, P, size_t, P]),
     "nif_primary_resolve": (i32, [MD, P, i64, P, P, P, i64, P, P, P, P, P, P]),
     "nif_frontend_rest_nearer": (i32, [MD, P, P, i64, P, P, P, i64, P, P, P, P, size_t, P]),

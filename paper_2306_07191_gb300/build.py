@@ -22,6 +22,7 @@ UNITS = {
     "bvh.cu": ["-fmad=false"],
     "nif_simt.cu": [],
     "nif_tc.cu": [],
+    "nif_train_tc.cu": [],
     "api.cu": [],
     "noalloc.cu": [],
     "det.cu": [],

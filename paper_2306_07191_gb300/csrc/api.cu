@@ -607,11 +607,12 @@ nif_status nif_train_step(nif_model_desc* m, nif_optim_desc* o, const nif_ray* d
                             d_ws, ws_bytes, stream);
 }
 
-nif_status nif_train_step_aux(nif_model_desc* m, nif_optim_desc* o, const nif_ray* d_rays,
-                              const uint32_t* d_ray_id, const uint32_t* d_qobj,
-                              const int64_t* d_group_off, const uint8_t* d_label, const float* d_aux,
-                              int64_t nq, float* d_loss, void* d_ws, size_t ws_bytes, void* stream) {
-  CallRange nvtx_range("nif_train_step_aux");
+// Forward, loss and backward of a training step into o's gradients (no
+// update); *wv receives the workspace view for the caller.
+static nif_status train_grads(const nif_model_desc* m, const nif_optim_desc* o, const nif_ray* d_rays,
+                              const uint32_t* d_ray_id, const uint32_t* d_qobj, const int64_t* d_group_off,
+                              const uint8_t* d_label, const float* d_aux, int64_t nq, float* d_loss,
+                              void* d_ws, size_t ws_bytes, cudaStream_t st, TrainWs* wv) {
   NifParams p;
   nif_status s = make_params(m, &p);
   if (s != NIF_OK) return s;
@@ -622,8 +623,36 @@ nif_status nif_train_step_aux(nif_model_desc* m, nif_optim_desc* o, const nif_ra
   NIF_CHECK_ARG(nq >= 1, "nif_train_step: empty batch");
   NIF_CHECK_ARG(d_rays && d_ray_id && d_qobj && d_group_off && d_label && d_ws, "nif_train_step: null pointer");
   NIF_CHECK_ARG(o->loss_scale > 0.f, "nif_train_step: loss_scale must be positive");
+  NIF_CHECK_ARG((o->d_loss_scale == nullptr) == (o->d_scale_state == nullptr),
+                "nif_train_step: d_loss_scale and d_scale_state go together");
+  NIF_CHECK_ARG(!o->d_loss_scale || (o->half_precision && o->scale_window >= 1),
+                "nif_train_step: dynamic loss scaling needs half_precision and scale_window >= 1");
   TrainWs w = train_layout(p, d_ws, nq);
   if (w.bytes > ws_bytes) return fail(NIF_ERR_WORKSPACE, "nif_train_step: workspace too small (%zu < %zu)", ws_bytes, w.bytes);
+  *wv = w;
+  if (o->half_precision) {
+    NIF_CHECK_ARG(!o->deterministic, "nif_train_step: half precision is not combined with deterministic gradients");
+    NIF_CHECK_ARG(!d_aux && p.O == 1, "nif_train_step: half precision trains one-output networks");
+    s = check_bwd_tc_shape(p);
+    if (s != NIF_OK) return s;
+    // the model's own 16-bit copies (refreshed by Adam from the masters)
+    NifParams ph = p;
+    ph.err = w.err;
+    ph.saved16 = reinterpret_cast<uint32_t*>(w.saved);
+    ph.ld_saved = nq;
+    s = launch_fwd_tc_save(ph, d_rays, d_ray_id, d_qobj, d_group_off, nq, w.z, w.err, st);
+    if (s != NIF_OK) return s;
+    s = launch_loss(w.z, d_label, nq, o->loss_scale, w.dz, d_loss, st, o->d_loss_scale);
+    if (s != NIF_OK) return s;
+    int32_t* ovf = o->d_scale_state ? o->d_scale_state : overflow_word(w.err);
+    s = launch_bwd_tc(ph, d_group_off, nq, ph.saved16, w.dz, o->d_w_grad, w.dx, ovf, w.err, st);
+    if (s != NIF_OK) return s;
+    s = launch_grid_bwd(ph, d_rays, d_ray_id, d_qobj, nq, w.dx, nq, o->d_g_grad, st);
+    if (s != NIF_OK) return s;
+    // with a fixed scale an overflow is an error of the call
+    if (!o->d_scale_state) return launch_overflow_to_error(ovf, w.err, st);
+    return NIF_OK;
+  }
   // FP32 master view of the model: forward and backward run on the masters.
   NifParams pm = p;
   pm.err = w.err;
@@ -632,7 +661,6 @@ nif_status nif_train_step_aux(nif_model_desc* m, nif_optim_desc* o, const nif_ra
   pm.weights = o->d_w_master;
   pm.mlp_dtype = NIF_F32;
   pm.scales = nullptr;
-  cudaStream_t st = as_stream(stream);
   s = launch_fwd_f32(pm, d_rays, d_ray_id, d_qobj, d_group_off, nq, nullptr, w.z, w.saved, nq, st);
   if (s != NIF_OK) return s;
   s = p.O == 1 ? launch_loss(w.z, d_label, nq, o->loss_scale, w.dz, d_loss, st)
@@ -653,26 +681,55 @@ nif_status nif_train_step_aux(nif_model_desc* m, nif_optim_desc* o, const nif_ra
     if (s != NIF_OK) return s;
     s = launch_grid_bwd(pm, d_rays, d_ray_id, d_qobj, nq, w.dx, nq, o->d_g_grad, st, dw.rkey, dw.rval);
     if (s != NIF_OK) return s;
-    s = launch_sum_records(dw.rkey, dw.rval, nq * grid_taps_per_pair(p), o->d_g_grad, dw.sort, dw.sort_bytes,
-                           st);
-    if (s != NIF_OK) return s;
-  } else {
-    s = launch_bwd_f32(pm, d_group_off, nq, w.saved, w.dz, o->d_w_grad, w.dx, st);
-    if (s != NIF_OK) return s;
-    s = launch_grid_bwd(pm, d_rays, d_ray_id, d_qobj, nq, w.dx, nq, o->d_g_grad, st);
-    if (s != NIF_OK) return s;
+    return launch_sum_records(dw.rkey, dw.rval, nq * grid_taps_per_pair(p), o->d_g_grad, dw.sort, dw.sort_bytes,
+                              st);
   }
+  s = launch_bwd_f32(pm, d_group_off, nq, w.saved, w.dz, o->d_w_grad, w.dx, st);
+  if (s != NIF_OK) return s;
+  return launch_grid_bwd(pm, d_rays, d_ray_id, d_qobj, nq, w.dx, nq, o->d_g_grad, st);
+}
+
+nif_status nif_train_grads(const nif_model_desc* m, const nif_optim_desc* o, const nif_ray* d_rays,
+                           const uint32_t* d_ray_id, const uint32_t* d_qobj, const int64_t* d_group_off,
+                           const uint8_t* d_label, int64_t nq, float* d_loss, void* d_ws, size_t ws_bytes,
+                           void* stream) {
+  CallRange nvtx_range("nif_train_grads");
+  TrainWs w;
+  return train_grads(m, o, d_rays, d_ray_id, d_qobj, d_group_off, d_label, nullptr, nq, d_loss, d_ws, ws_bytes,
+                     as_stream(stream), &w);
+}
+
+nif_status nif_train_step_aux(nif_model_desc* m, nif_optim_desc* o, const nif_ray* d_rays,
+                              const uint32_t* d_ray_id, const uint32_t* d_qobj,
+                              const int64_t* d_group_off, const uint8_t* d_label, const float* d_aux,
+                              int64_t nq, float* d_loss, void* d_ws, size_t ws_bytes, void* stream) {
+  CallRange nvtx_range("nif_train_step_aux");
+  cudaStream_t st = as_stream(stream);
+  TrainWs w;
+  nif_status s = train_grads(m, o, d_rays, d_ray_id, d_qobj, d_group_off, d_label, d_aux, nq, d_loss, d_ws,
+                             ws_bytes, st, &w);
+  if (s != NIF_OK) return s;
+  NifParams p;
+  s = make_params(m, &p);
+  if (s != NIF_OK) return s;
   const int step = o->step + 1;
   const int64_t nw = (int64_t)p.n_nets * p.P;
   const int64_t ng = (int64_t)p.n_obj * p.obj_elems;
+  // dynamic loss scaling: the step is skipped when its gradients overflowed
+  const float* dsc = o->d_loss_scale;
+  const int32_t* skip = o->d_scale_state;
   void* wcopy = m->mlp_dtype == NIF_E4M3 ? nullptr : const_cast<void*>(m->d_weights);
   s = launch_adam(o->d_w_master, o->d_w_grad, o->d_w_m, o->d_w_v, nw, o->lr, o->beta1, o->beta2, o->eps,
-                  o->loss_scale, step, wcopy == o->d_w_master ? nullptr : wcopy, m->mlp_dtype, st, w.err);
+                  o->loss_scale, step, wcopy == o->d_w_master ? nullptr : wcopy, m->mlp_dtype, st, w.err, dsc, skip);
   if (s != NIF_OK) return s;
   void* gcopy = const_cast<void*>(m->d_grids);
   s = launch_adam(o->d_g_master, o->d_g_grad, o->d_g_m, o->d_g_v, ng, o->lr, o->beta1, o->beta2, o->eps,
-                  o->loss_scale, step, gcopy == o->d_g_master ? nullptr : gcopy, m->grid_dtype, st, w.err);
+                  o->loss_scale, step, gcopy == o->d_g_master ? nullptr : gcopy, m->grid_dtype, st, w.err, dsc, skip);
   if (s != NIF_OK) return s;
+  if (o->d_loss_scale) {
+    s = launch_loss_scale_update(o->d_loss_scale, o->d_scale_state, o->scale_window, st);
+    if (s != NIF_OK) return s;
+  }
   o->step = step;
   return NIF_OK;
 }

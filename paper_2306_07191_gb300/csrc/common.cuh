@@ -52,6 +52,12 @@ constexpr size_t kTileCtrOffset = 64;
 inline uint32_t* tile_counter(DevError* e) {
   return e ? reinterpret_cast<uint32_t*>(reinterpret_cast<char*>(e) + kTileCtrOffset) : nullptr;
 }
+// Byte 96 of the head: overflow flag of a half-precision training step
+// without dynamic loss scaling (turned into an error by the step).
+constexpr size_t kOverflowOffset = 96;
+inline int32_t* overflow_word(DevError* e) {
+  return reinterpret_cast<int32_t*>(reinterpret_cast<char*>(e) + kOverflowOffset);
+}
 
 __device__ __forceinline__ void raise_error(DevError* e, int32_t code, int64_t detail) {
   if (e && atomicCAS(&e->code, 0, code) == 0) e->detail = detail;

@@ -52,10 +52,27 @@ nif_status launch_fwd_tc(const NifParams& p, const nif_ray* rays, const uint32_t
                          uint32_t* occ, float* logits, int tile_m, int ctas_per_sm,
                          DevError* err, cudaStream_t st);
 nif_status check_tc_shape(const NifParams& p);
+// Training forward on the tensor cores: logits and p.saved16 (16-bit
+// activations x, h_1 .. h_H, [K/2 + H*W/2][p.ld_saved] words of two).
+nif_status launch_fwd_tc_save(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
+                              const uint32_t* qobj, const int64_t* goff, int64_t nq, float* logits,
+                              DevError* err, cudaStream_t st);
+// Tensor-core MLP backward from the saved 16-bit activations (nif_train_tc.cu):
+// wgrad += dW (scaled like dz), dx = dL/dx (FP32, [K][ld]); overflow is set to
+// 1 when a scaled gradient does not fit the operand type.
+nif_status check_bwd_tc_shape(const NifParams& p);
+nif_status launch_bwd_tc(const NifParams& p, const int64_t* goff, int64_t ld, const uint32_t* saved,
+                         const float* dz, float* wgrad, float* dx, int32_t* overflow, DevError* err,
+                         cudaStream_t st);
+// A set overflow flag becomes NIF_ERR_NUMERIC (detail -1) in err; the flag is cleared.
+nif_status launch_overflow_to_error(int32_t* flag, DevError* err, cudaStream_t st);
+// Dynamic loss scale after a step (state = {overflow flag, steps without overflow}).
+nif_status launch_loss_scale_update(float* scale, int32_t* state, int window, cudaStream_t st);
 nif_status launch_wait_selftest(DevError* err, long long limit_cycles, cudaStream_t st);
 
+// d_scale (nullable): a device loss scale used instead of `scale`.
 nif_status launch_loss(const float* z, const uint8_t* label, int64_t nq, float scale, float* dz,
-                       float* loss, cudaStream_t st);
+                       float* loss, cudaStream_t st, const float* d_scale = nullptr);
 nif_status launch_loss_aux(const float* z, const uint8_t* label, const float* aux, int64_t nq, int n_out,
                            float scale, float* dz, float* loss, cudaStream_t st);
 // Closest NIF hit per ray from O-output pairs (z_0 < 0: a hit at
@@ -88,9 +105,12 @@ nif_status launch_sum_records(uint32_t* rkey, float* rval, int64_t n_records, fl
 // dst[i] = src[i] converted to dtype (NIF_F32, NIF_F16 or NIF_BF16).
 nif_status launch_cast(const float* src, int64_t n, void* dst, int dtype, cudaStream_t st);
 // err (nullable): a non-finite updated parameter is recorded as
-// NIF_ERR_NUMERIC with its index as the detail.
+// NIF_ERR_NUMERIC with its index as the detail.  d_scale (nullable): a device
+// loss scale the gradients are divided by instead of grad_scale; skip
+// (nullable): when *skip is set the step only zeroes the gradients.
 nif_status launch_adam(float* th, float* gr, float* m1, float* m2, int64_t n, float lr, float b1,
                        float b2, float eps, float grad_scale, int step, void* copy, int copy_dtype,
-                       cudaStream_t st, DevError* err = nullptr);
+                       cudaStream_t st, DevError* err = nullptr, const float* d_scale = nullptr,
+                       const int32_t* skip = nullptr);
 
 }  // namespace nif

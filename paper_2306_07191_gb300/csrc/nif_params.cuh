@@ -37,6 +37,10 @@ struct NifParams {
   int64_t obj_elems;  // spherical: elements of one object's grid block
   int64_t n_rays;     // rays the query lists index (0: not known to the call)
   DevError* err;      // device error word of the call's workspace (nullable)
+  // training forward on the tensor cores (nullable): the 16-bit activations
+  // x, h_1 .. h_H of every query as [K/2 + H*width/2][ld_saved] words of two
+  uint32_t* saved16;
+  int64_t ld_saved;
 };
 
 // A query's inputs are in range: its object below n_objects and, when the

@@ -578,7 +578,8 @@ __global__ void __launch_bounds__(kFThreads) k_mlp_fwd_f32(NifParams p, const ni
 
 // ------------------------------------------------------------------- loss
 __global__ void k_loss(const float* z, const uint8_t* label, int64_t nq, float scale, float* dz,
-                       float* loss) {
+                       float* loss, const float* d_scale) {
+  if (d_scale) scale = *d_scale;
   float part = 0.f;
   const float invB = 1.0f / static_cast<float>(nq);
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
@@ -894,7 +895,14 @@ __global__ void __launch_bounds__(256) k_adam(float* __restrict__ th, float* __r
                                               int64_t n, float lr, float b1, float b2, float eps,
                                               float inv_scale, float c1, float c2,
                                               TC* __restrict__ copy, DevError* err,
-                                              int64_t i0) {
+                                              int64_t i0, const float* d_scale, const int32_t* skip) {
+  if (skip && *skip) {  // the step's scaled gradients overflowed: no update
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+      gr[i] = 0.f;
+    return;
+  }
+  if (d_scale) inv_scale = 1.0f / *d_scale;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     float g = gr[i] * inv_scale;
@@ -936,7 +944,15 @@ __global__ void __launch_bounds__(256) k_adam4(float4* __restrict__ th, float4* 
                                                float4* __restrict__ m1, float4* __restrict__ m2,
                                                int64_t n4, float lr, float b1, float b2, float eps,
                                                float inv_scale, float c1, float c2,
-                                               TC* __restrict__ copy, DevError* err) {
+                                               TC* __restrict__ copy, DevError* err,
+                                               const float* d_scale, const int32_t* skip) {
+  if (skip && *skip) {  // the step's scaled gradients overflowed: no update
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
+         i += (int64_t)gridDim.x * blockDim.x)
+      gr[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  if (d_scale) inv_scale = 1.0f / *d_scale;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
        i += (int64_t)gridDim.x * blockDim.x) {
     float4 t = th[i], g = gr[i], m = m1[i], v = m2[i];
@@ -1178,11 +1194,11 @@ nif_status launch_fwd_f32(const NifParams& p, const nif_ray* rays, const uint32_
 }
 
 nif_status launch_loss(const float* z, const uint8_t* label, int64_t nq, float scale, float* dz,
-                       float* loss, cudaStream_t st) {
+                       float* loss, cudaStream_t st, const float* d_scale) {
   if (loss) NIF_CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(float), st));
   if (nq == 0) return NIF_OK;
   int blocks = static_cast<int>(std::min<int64_t>(ceil_div(nq, 256), sm_count() * 4));
-  k_loss<<<blocks, 256, 0, st>>>(z, label, nq, scale, dz, loss);
+  k_loss<<<blocks, 256, 0, st>>>(z, label, nq, scale, dz, loss, d_scale);
   NIF_LAUNCH_CHECK();
   return NIF_OK;
 }
@@ -1352,7 +1368,7 @@ nif_status launch_cast(const float* src, int64_t n, void* dst, int dtype, cudaSt
 
 nif_status launch_adam(float* th, float* gr, float* m1, float* m2, int64_t n, float lr, float b1,
                        float b2, float eps, float grad_scale, int step, void* copy, int copy_dtype,
-                       cudaStream_t st, DevError* err) {
+                       cudaStream_t st, DevError* err, const float* d_scale, const int32_t* skip) {
   if (n == 0) return NIF_OK;
   double c1 = 1.0 / (1.0 - std::pow(static_cast<double>(b1), step));
   double c2 = 1.0 / (1.0 - std::pow(static_cast<double>(b2), step));
@@ -1368,13 +1384,13 @@ nif_status launch_adam(float* th, float* gr, float* m1, float* m2, int64_t n, fl
     auto v4 = [](float* q) { return reinterpret_cast<float4*>(q); };
     if (copy == nullptr || copy_dtype == NIF_F32)
       k_adam4<float><<<b4, 256, 0, st>>>(v4(th), v4(gr), v4(m1), v4(m2), n4, lr, b1, b2, eps, inv, (float)c1,
-                                         (float)c2, (float*)copy, err);
+                                         (float)c2, (float*)copy, err, d_scale, skip);
     else if (copy_dtype == NIF_F16)
       k_adam4<__half><<<b4, 256, 0, st>>>(v4(th), v4(gr), v4(m1), v4(m2), n4, lr, b1, b2, eps, inv, (float)c1,
-                                          (float)c2, (__half*)copy, err);
+                                          (float)c2, (__half*)copy, err, d_scale, skip);
     else if (copy_dtype == NIF_BF16)
       k_adam4<__nv_bfloat16><<<b4, 256, 0, st>>>(v4(th), v4(gr), v4(m1), v4(m2), n4, lr, b1, b2, eps, inv,
-                                                 (float)c1, (float)c2, (__nv_bfloat16*)copy, err);
+                                                 (float)c1, (float)c2, (__nv_bfloat16*)copy, err, d_scale, skip);
     else
       return fail(NIF_ERR_UNSUPPORTED, "adam: unsupported copy dtype %d", copy_dtype);
     NIF_LAUNCH_CHECK();
@@ -1390,11 +1406,11 @@ nif_status launch_adam(float* th, float* gr, float* m1, float* m2, int64_t n, fl
     blocks = 1;
   }
   if (copy == nullptr || copy_dtype == NIF_F32)
-    k_adam<float><<<blocks, 256, 0, st>>>(th, gr, m1, m2, n, lr, b1, b2, eps, inv, (float)c1, (float)c2, (float*)copy, err, i0);
+    k_adam<float><<<blocks, 256, 0, st>>>(th, gr, m1, m2, n, lr, b1, b2, eps, inv, (float)c1, (float)c2, (float*)copy, err, i0, d_scale, skip);
   else if (copy_dtype == NIF_F16)
-    k_adam<__half><<<blocks, 256, 0, st>>>(th, gr, m1, m2, n, lr, b1, b2, eps, inv, (float)c1, (float)c2, (__half*)copy, err, i0);
+    k_adam<__half><<<blocks, 256, 0, st>>>(th, gr, m1, m2, n, lr, b1, b2, eps, inv, (float)c1, (float)c2, (__half*)copy, err, i0, d_scale, skip);
   else if (copy_dtype == NIF_BF16)
-    k_adam<__nv_bfloat16><<<blocks, 256, 0, st>>>(th, gr, m1, m2, n, lr, b1, b2, eps, inv, (float)c1, (float)c2, (__nv_bfloat16*)copy, err, i0);
+    k_adam<__nv_bfloat16><<<blocks, 256, 0, st>>>(th, gr, m1, m2, n, lr, b1, b2, eps, inv, (float)c1, (float)c2, (__nv_bfloat16*)copy, err, i0, d_scale, skip);
   else
     return fail(NIF_ERR_UNSUPPORTED, "adam: unsupported copy dtype %d", copy_dtype);
   NIF_LAUNCH_CHECK();

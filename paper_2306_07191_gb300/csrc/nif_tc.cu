@@ -34,46 +34,10 @@
 
 #include "nif_params.cuh"
 #include "nif_kernels.cuh"
+#include "tc_ptx.cuh"
 
 namespace nif {
 namespace tc {
-
-constexpr int kM = 128;
-constexpr int kThreads = 256;
-constexpr int kSphMaxK = 32;  // widest spherical input the TMEM kernel builds per thread
-constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
-
-// ------------------------------------------------------------ PTX wrappers
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait: gives up after `limit` SM cycles (~2 s by default) and
-// records NIF_ERR_TIMEOUT with `site` as the detail.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, DevError* err,
-                                          long long limit = kWaitCycles, int64_t site = 1) {
-  long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > limit) {
-      raise_error(err, NIF_ERR_TIMEOUT, site);
-      return false;
-    }
-  }
-  return true;
-}
 
 // Self-test of the bounded wait: waits on an mbarrier that nothing arrives
 // on, so the wait must give up after `limit` cycles and record the timeout;
@@ -88,171 +52,6 @@ __global__ void k_wait_selftest(DevError* err, long long limit) {
   if (threadIdx.x == 0) mbar_wait(smem_u32(&bar), 0, err, limit, 42);
   __syncthreads();
 }
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
-               "r"(ncols)
-               : "memory");
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
-               : "memory");
-}
-template <int kKind>  // 0: kind::f16 (f16/bf16), 1: kind::f8f6f4 (e4m3)
-__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                    uint32_t accumulate) {
-  if constexpr (kKind == 0) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-  } else {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-  }
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-      : "memory");
-}
-// 32 lanes x 16 columns of FP32 from TMEM (this warp's lane quarter).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float v[16]) {
-  uint32_t r[16];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// Stores of 32-bit words into this warp's TMEM lane quarter (one lane per
-// thread, consecutive columns from taddr), and the wait for their completion.
-__device__ __forceinline__ void tmem_st1(uint32_t taddr, uint32_t v) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(v) : "memory");
-}
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t v[8]) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
-      : "memory");
-}
-__device__ __forceinline__ void tmem_st4(uint32_t taddr, const uint32_t v[4]) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "r"(v[0]),
-               "r"(v[1]), "r"(v[2]), "r"(v[3])
-               : "memory");
-}
-__device__ __forceinline__ void tmem_wait_st() {
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
-// MMA whose A operand is read from tensor memory (rows = lanes, two 16-bit
-// elements per 32-bit column, K-major), B from shared memory.
-__device__ __forceinline__ void mma_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
-                                       uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "setp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
-      "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-// TMA: one tiled tensor copy global -> shared, completing on an mbarrier.
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map, int c0, int c1,
-                                            int c2, int c3, int c4, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
-      : "memory");
-}
-
-// Tensor maps of the hidden layers' weights (all networks), one per layer:
-// dimensions (k within a 16-byte row, row within 8, 16-byte column block,
-// 8-row group, network), so that one box of a network lands in shared memory
-// exactly in the K-major core-matrix layout the MMA reads.
-struct WeightMaps {
-  CUtensorMap m[8];
-};
-
-// Shared-memory matrix descriptor: K-major, no swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
-  d |= static_cast<uint64_t>((lbo & 0x3FFFFu) >> 4) << 16;
-  d |= static_cast<uint64_t>((sbo & 0x3FFFFu) >> 4) << 32;
-  d |= static_cast<uint64_t>(1) << 46;  // descriptor version for tcgen05
-  return d;                             // base offset 0, no swizzle
-}
-
-// Instruction descriptor: FP32 accumulator, A and B of format `fmt`
-// (kind::f16: 0 = f16, 1 = bf16; kind::f8f6f4: 0 = e4m3), both K-major.
-__host__ __device__ constexpr uint32_t instr_desc(int m, int n, uint32_t fmt) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | (static_cast<uint32_t>(n >> 3) << 17) |
-         (static_cast<uint32_t>(m >> 4) << 24);
-}
-
-// Byte offset of element (row, k) of a K-major tile with kdim columns.
-__device__ __forceinline__ uint32_t tile_off(int row, int k, int kdim, int esz) {
-  const int cb = 16 / esz;  // elements per 16-byte core row
-  return static_cast<uint32_t>(((row >> 3) * (kdim / cb) + k / cb) * 128 + (row & 7) * 16 +
-                               (k % cb) * esz);
-}
-
-template <int DT>
-struct Op;
-template <>
-struct Op<NIF_F16> {
-  using T = __half;
-  static constexpr int esz = 2, kind = 0, fmt = 0;
-  __device__ static T cvt(float v) { return __float2half_rn(v); }
-  __device__ static float load(const void* p, int64_t i) {
-    return __half2float(static_cast<const __half*>(p)[i]);
-  }
-};
-template <>
-struct Op<NIF_BF16> {
-  using T = __nv_bfloat16;
-  static constexpr int esz = 2, kind = 0, fmt = 1;
-  __device__ static T cvt(float v) { return __float2bfloat16_rn(v); }
-  __device__ static float load(const void* p, int64_t i) {
-    return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]);
-  }
-};
-template <>
-struct Op<NIF_E4M3> {
-  using T = __nv_fp8_e4m3;
-  static constexpr int esz = 1, kind = 1, fmt = 0;
-  __device__ static T cvt(float v) { return __nv_fp8_e4m3(v); }
-  __device__ static float load(const void* p, int64_t i) {
-    return static_cast<float>(static_cast<const __nv_fp8_e4m3*>(p)[i]);
-  }
-};
 
 // Interpolation of FP16 grids in packed half2 arithmetic (trilerp_h2) unless
 // built with -DNIF_FP16_LERP=0, which interpolates in FP32 from 8 weights.
@@ -281,17 +80,6 @@ __device__ __forceinline__ void store_elem(uint8_t* tile, int row, int k, int kd
   using O = Op<DT>;
   typename O::T t = O::cvt(v);
   *reinterpret_cast<typename O::T*>(tile + tile_off(row, k, kdim, O::esz)) = t;
-}
-
-// Tile claiming of the persistent kernels.  With a counter (zeroed before
-// the launch) each CTA claims its next tile when it is ready for one, so the
-// CTAs an SM's warp scheduler favours take more tiles and all of them finish
-// together; without one, tiles go round-robin by block index.
-__device__ __forceinline__ int64_t first_tile(uint32_t* ctr) {
-  return ctr ? static_cast<int64_t>(atomicAdd(ctr, 1u)) : static_cast<int64_t>(blockIdx.x);
-}
-__device__ __forceinline__ int64_t next_tile(uint32_t* ctr, int64_t t) {
-  return ctr ? static_cast<int64_t>(atomicAdd(ctr, 1u)) : t + gridDim.x;
 }
 
 struct Layout {
@@ -621,10 +409,12 @@ __host__ __device__ inline uint32_t tm_cols(int Kp, int W) {
 }
 
 // kMulti: an output layer of p.O <= kMaxOut rows (the primary-ray outputs)
-// instead of the single occupancy logit.
+// instead of the single occupancy logit.  kSave: the training forward, which
+// also writes every query's 16-bit network input and hidden activations to
+// p.saved16 (the operands of the tensor-core backward).
 constexpr int kMaxOut = 8;
 
-template <int F, typename TG, int DT, int kOcc, bool kMulti = false>
+template <int F, typename TG, int DT, int kOcc, bool kMulti = false, bool kSave = false>
 __global__ void __launch_bounds__(kThreads, kOcc)
     k_fused_tm(const __grid_constant__ NifParams p, const nif_ray* __restrict__ rays,
                const uint32_t* __restrict__ ray_id, const uint32_t* __restrict__ qobj,
@@ -820,8 +610,11 @@ __global__ void __launch_bounds__(kThreads, kOcc)
               }
             }
 #pragma unroll
-            for (int u = 0; u < kJB; ++u)
+            for (int u = 0; u < kJB; ++u) {
               tmem_st1(lane_base + act_col + static_cast<uint32_t>((jb + u) * p.L + l), word[u]);
+              if constexpr (kSave)
+                if (q < qend) p.saved16[static_cast<int64_t>((jb + u) * p.L + l) * p.ld_saved + q] = word[u];
+            }
           }
         } else {
 #pragma unroll
@@ -876,6 +669,17 @@ __global__ void __launch_bounds__(kThreads, kOcc)
         for (int i = 0; i < 16; ++i) {
           const float a = v[i];
           v[i] = a > 0.f ? a : (p.act == NIF_ACT_LEAKY ? p.slope * a : 0.f);
+        }
+        if constexpr (kSave) {
+          // h_{l+1} of this row in the operand type, as the backward reads it
+          uint32_t pk[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) pk[i] = pack2(v[2 * i], v[2 * i + 1]);
+          const int64_t qs = q0 + qi;
+          if (qs < qend)
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+              p.saved16[static_cast<int64_t>(K / 2 + l * (W / 2) + (ecol0 + c0) / 2 + i) * p.ld_saved + qs] = pk[i];
         }
         if (l + 1 < H) {
           uint32_t pk[8];
@@ -1482,6 +1286,46 @@ nif_status launch_fwd_tc(const NifParams& p, const nif_ray* rays, const uint32_t
   if (p.mlp_dtype == NIF_BF16) return launch_dt<NIF_BF16>(p, rays, ray_id, qobj, goff, blocks, per_sm, occ, logits, err, ctr, st);
   if (p.mlp_dtype == NIF_E4M3) return launch_dt<NIF_E4M3>(p, rays, ray_id, qobj, goff, blocks, per_sm, occ, logits, err, ctr, st);
   return fail(NIF_ERR_UNSUPPORTED, "tensor-core path: mlp dtype %d", p.mlp_dtype);
+}
+
+// Training forward on the tensor cores: logits and the 16-bit activations
+// of every query (p.saved16, [K/2 + H*W/2][p.ld_saved] words), the serial
+// schedule at 4 CTAs per SM.  Multi-resolution grids with two features, one
+// output, FP16 or BF16 operands.
+nif_status launch_fwd_tc_save(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
+                              const uint32_t* qobj, const int64_t* goff, int64_t nq, float* logits,
+                              DevError* err, cudaStream_t st) {
+  nif_status s = check_tc_shape(p);
+  if (s != NIF_OK) return s;
+  if (p.enc != NIF_ENC_MULTIRES || p.F != 2 || p.O != 1 || !p.saved16 || p.ld_saved < nq ||
+      (p.mlp_dtype != NIF_F16 && p.mlp_dtype != NIF_BF16) || !tc_activations_in_tmem())
+    return fail(NIF_ERR_UNSUPPORTED, "tensor-core training forward: two-feature multi-resolution grids, "
+                                     "one output, FP16 or BF16 operands");
+  const int Kp = (p.K + 15) / 16 * 16;
+  tc::LayoutTm L = tc::make_layout_tm(Kp, p.width, p.n_hidden, p.n_nets, 1);
+  const size_t sh = L.total + 1024;
+  tc::WeightMaps wm;
+  const int use_tma = make_weight_maps(p, 2, Kp, &wm) && tc_weights_by_tma() ? 1 : 0;
+  const int per_sm = std::min(4, 512 / static_cast<int>(tc::tm_cols(Kp, p.width)));
+  const int blocks = static_cast<int>(std::max<int64_t>(
+      1, std::min<int64_t>(sm_count() * per_sm, ceil_div(nq, tc::kM) + p.n_nets)));
+  uint32_t* ctr = tile_counter(err);
+  if (ctr) NIF_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t), st));
+  auto go = [&](auto kern) -> nif_status {
+    NIF_CUDA_TRY(ensure_smem(kern, sh));
+    kern<<<blocks, tc::kThreads, sh, st>>>(p, rays, ray_id, qobj, goff, nullptr, logits, err, Kp, wm, use_tma,
+                                           ctr);
+    return NIF_OK;
+  };
+  if (p.grid_dtype == NIF_F16)
+    s = p.mlp_dtype == NIF_F16 ? go(tc::k_fused_tm<2, __half, NIF_F16, 4, false, true>)
+                               : go(tc::k_fused_tm<2, __half, NIF_BF16, 4, false, true>);
+  else
+    s = p.mlp_dtype == NIF_F16 ? go(tc::k_fused_tm<2, float, NIF_F16, 4, false, true>)
+                               : go(tc::k_fused_tm<2, float, NIF_BF16, 4, false, true>);
+  if (s != NIF_OK) return s;
+  NIF_LAUNCH_CHECK();
+  return NIF_OK;
 }
 
 nif_status launch_wait_selftest(DevError* err, long long limit_cycles, cudaStream_t st) {

@@ -336,11 +336,18 @@ class NifModel:
 
 class Trainer:
     """Adam state for a NifModel (Sec. 5 'Training'): FP32 masters, FP32
-    gradients and moments; nif_train_step refreshes the model's copies."""
+    gradients and moments; nif_train_step refreshes the model's copies.
+
+    half_precision: forward and MLP backward on the tensor cores with the
+    model's 16-bit copies (FP32 accumulation, masters and moments FP32).
+    dynamic_scale: the loss scale lives on the device, starts at loss_scale,
+    halves after a step whose scaled gradients overflow the 16-bit type (the
+    step is skipped) and doubles after scale_window clean steps."""
 
     def __init__(self, model: NifModel, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-15,
                  loss_scale=1.0, w_master: torch.Tensor | None = None,
-                 g_master: torch.Tensor | None = None, deterministic: bool = False):
+                 g_master: torch.Tensor | None = None, deterministic: bool = False,
+                 half_precision: bool = False, dynamic_scale: bool = False, scale_window: int = 2000):
         self.model = model
         dev = model.obj_aabb.device
         self.w_master = (w_master if w_master is not None else model.weights.float()).clone().contiguous()
@@ -361,6 +368,14 @@ class Trainer:
             setattr(self.o, "d_" + name, getattr(self, name).data_ptr())
         self.loss = torch.zeros(1, dtype=torch.float32, device=dev)
         self._ws = None
+        self.o.half_precision = int(half_precision)
+        self.scale = self.scale_state = None
+        if dynamic_scale:
+            self.scale = torch.full((1,), float(loss_scale), dtype=torch.float32, device=dev)
+            self.scale_state = torch.zeros(2, dtype=torch.int32, device=dev)
+            self.o.d_loss_scale = self.scale.data_ptr()
+            self.o.d_scale_state = self.scale_state.data_ptr()
+            self.o.scale_window = int(scale_window)
 
     def state_bytes(self, stream=None) -> np.ndarray:
         """The optimiser state (nif_state_save): FP32 masters, Adam moments and
@@ -388,13 +403,26 @@ class Trainer:
     def load(self, path: str):
         self.load_state_bytes(np.fromfile(path, dtype=np.uint8))
 
+    def _workspace(self, d, nq: int, device):
+        need = L.lib.nif_train_workspace_size(ctypes.byref(d), nq)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = torch.zeros(need, dtype=torch.uint8, device=device)
+        return self._ws
+
+    def grads(self, rays, ray_id, qobj, goff, label, nq: int, stream=None):
+        """nif_train_grads: the step's forward, loss and backward into
+        w_grad / g_grad (gradients of the scaled loss), without the update."""
+        d = self.model.desc()
+        ws = self._workspace(d, nq, rays.device)
+        L.call("nif_train_grads", ctypes.byref(d), ctypes.byref(self.o), _ptr(rays), _ptr(ray_id), _ptr(qobj),
+               _ptr(goff), _ptr(label), nq, _ptr(self.loss), _ptr(ws), ws.numel(), _stream(stream))
+        return self.loss
+
     def step(self, rays, ray_id, qobj, goff, label, nq: int, stream=None, aux=None):
         """One nif_train_step (or nif_train_step_aux with the targets aux
         [nq, O-1] of an O-output network)."""
         d = self.model.desc()
-        need = L.lib.nif_train_workspace_size(ctypes.byref(d), nq)
-        if self._ws is None or self._ws.numel() < need:
-            self._ws = torch.zeros(need, dtype=torch.uint8, device=rays.device)
+        self._workspace(d, nq, rays.device)
         if self.o.deterministic:
             dn = L.lib.nif_deterministic_workspace_size(ctypes.byref(d), nq)
             if self._det_ws is None or self._det_ws.numel() < dn:

@@ -74,6 +74,11 @@ class RoomConfig:
     samples: int = 1            # shadow rays per pixel (area-light samples)
     max_pairs_per_ray: int = 6  # capacity of the front end's pair lists
     pairs_per_spp: int = 0      # training pairs kept per jittered sample (0 = all)
+    # training precision: FP32 on the CUDA cores over the FP32 masters, or
+    # the model's 16-bit copies on the tensor cores with a dynamic loss scale
+    half_precision_train: bool = False
+    loss_scale: float = 65536.0
+    scale_window: int = 2000
 
 
 def small_object_precision_config() -> RoomConfig:
@@ -276,7 +281,10 @@ class RoomPipeline:
         aux = pairs[5] if len(pairs) > 5 else None  # regression targets (several outputs)
         self.pairs = pairs
         npool = int(rid.shape[0])
-        self.trainer = nif.Trainer(self.model, lr=c.lr, w_master=self.w_master, g_master=self.g_master)
+        hp = bool(c.half_precision_train)
+        self.trainer = nif.Trainer(self.model, lr=c.lr, w_master=self.w_master, g_master=self.g_master,
+                                   half_precision=hp, dynamic_scale=hp,
+                                   loss_scale=c.loss_scale if hp else 1.0, scale_window=c.scale_window)
         draw = BatchDraw(npool, seed)
         losses = []
         step_ev = []

@@ -1,0 +1,75 @@
+"""The precision pattern on the precision workload at full size: the small
+object in the room under 4 point lights (8,294,400 shadow rays), its network
+trained in FP32 on the GPU, then inferred with FP32, BF16, FP16 and
+FP8-E4M3 operands (FP32 accumulation).  On the oracle's own pairs of 1,500
+sampled pixels, each precision's logits are compared with the FP64 oracle's
+logits of the trained FP32 network; the errors are printed per precision and
+held to the bars of each operand type."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import oracle  # noqa: E402
+from oracle import frames  # noqa: E402
+from oracle import nif as onif  # noqa: E402
+from paper_2306_07191_gb300 import _lib as L  # noqa: E402
+from paper_2306_07191_gb300 import pipeline, synth  # noqa: E402
+
+# |z_gpu - z_fp64| <= bar * max(1, |z_fp64|): the unit-scale logit bars of the
+# operand types, scaled by the logit's magnitude for the trained network
+BARS = {"f32": 1e-4, "bf16": 6e-2, "f16": 2e-2, "e4m3": 0.25}
+
+
+def test_trained_logits_per_precision_vs_fp64():
+    cfg = pipeline.small_object_precision_config()
+    p = pipeline.RoomPipeline(cfg, log=lambda *a: None)
+    p.train()
+    q8, sc8 = p.calibrate_e4m3(p.pairs)
+    g32 = p.trainer.g_master.detach().cpu().numpy().astype(np.float64)
+    w32 = p.trainer.w_master.detach().clone()
+    ws = p.ws
+    npix = ws.camera.shape[0]
+    spp = cfg.n_lights
+    pix = np.sort(np.random.default_rng(11).choice(npix, 1500, replace=False))
+    lp = np.tile(ws.light.astype(np.float32).reshape(1, spp, 3), (len(pix), 1, 1)).reshape(-1, 3)
+    ors = frames.frame_rays(oracle.OracleBVH(ws.scene.verts, ws.scene.tris), ws.camera[pix], lp, cfg.tmin, spp)
+    gids = (pix[:, None] * spp + np.arange(spp)[None, :]).reshape(-1)
+    assert np.array_equal(ors.view(np.uint32), p.rays[torch.from_numpy(gids).cuda()].cpu().numpy().view(np.uint32))
+    r, ob, inn = onif.queries(ors, ws.scene.obj_aabb)
+    order = np.argsort(inn, kind="stable")
+    r, ob, inn = r[order], ob[order], inn[order]
+    nq = len(r)
+    assert nq > 500
+    K = 3 * len(cfg.res) * cfg.n_features
+    wflat = w32.cpu().numpy().astype(np.float64)
+    P = wflat.size // 2
+    nets = [synth.unflatten_mlp(wflat[g * P:(g + 1) * P], K, cfg.width_mlp, cfg.n_hidden) for g in range(2)]
+    om = onif.Model(res=list(cfg.res), F=cfg.n_features, log2_table=cfg.log2_table, obj_aabb=ws.scene.obj_aabb,
+                    grids=g32.reshape(1, 2, -1), nets=nets, net_mode="class")
+    zo = onif.forward(om, ors, r, ob, inn)
+    assert np.abs(zo).max() > 1.0 and (zo < 0).any() and (zo > 0).any()
+    ray_id = torch.from_numpy(gids[r].astype(np.int32)).cuda()
+    qobj = torch.from_numpy((ob.astype(np.uint32) | (inn.astype(np.uint32) << 31)).view(np.int32)).cuda()
+    goff = torch.tensor([0, int((~inn).sum()), nq], dtype=torch.int64, device="cuda")
+    model = p.model
+    scale = np.maximum(1.0, np.abs(zo))
+    report = {}
+    for name, dt, w, sc in (("f32", L.NIF_F32, w32, None), ("bf16", L.NIF_BF16, w32.bfloat16(), None),
+                            ("f16", L.NIF_F16, w32.half(), None), ("e4m3", L.NIF_E4M3, q8, sc8)):
+        model.cfg.mlp_dtype, model.weights, model.scales = dt, w.contiguous(), sc
+        z = model.infer_queries(p.rays, ray_id, qobj, goff, nq)[:nq].cpu().numpy().astype(np.float64)
+        model.check()
+        err = np.abs(z - zo)
+        report[name] = (float(err.max()), float(err.mean()), float((err / scale).max()))
+        sure = np.abs(zo) > BARS[name] * scale
+        assert np.array_equal(z[sure] < 0, zo[sure] < 0), name
+        assert report[name][2] <= BARS[name], (name, report[name])
+    print("\nlogit error vs FP64 (max abs, mean abs, max relative to max(1,|z|)); "
+          f"{nq} pairs, |z| up to {np.abs(zo).max():.2f}:")
+    for name, (mx, mean, rel) in report.items():
+        print(f"  {name}: {mx:.3e} {mean:.3e} {rel:.3e}")

@@ -392,3 +392,129 @@ def test_deterministic_steps_repeat_and_resume_bit_for_bit():
         a, b = getattr(ta, k), getattr(tb, k)
         assert float((a - b).abs().max()) <= 1e-6 * max(1e-12, float(b.abs().max())) + 1e-12, k
     assert float(ta.g_m.abs().max()) > 0 and float(ta.w_m.abs().max()) > 0
+
+
+def _room_subset(p, cfg, seed=9, n_pix=1000):
+    """The oracle's own shadow rays and pairs of n_pix sampled pixels of the
+    room frame (bit-equal to the GPU's rays)."""
+    import oracle
+    from oracle import frames
+    ws = p.ws
+    pix = np.sort(np.random.default_rng(seed).choice(ws.camera.shape[0], n_pix, replace=False))
+    ors = frames.frame_rays(oracle.OracleBVH(ws.scene.verts, ws.scene.tris), ws.camera[pix], ws.light, cfg.tmin)
+    assert np.array_equal(ors.view(np.uint32), p.rays[torch.from_numpy(pix).cuda()].cpu().numpy().view(np.uint32))
+    r, ob, inn = onif.queries(ors, ws.scene.obj_aabb)
+    return ors, r, ob, inn
+
+
+def test_half_precision_gradients_room_subset():
+    """The half-precision training path (nif_train_grads with
+    half_precision: the forward on the tensor cores saving FP16
+    activations, the MLP backward on the tensor cores, FP32 accumulation, a
+    fixed loss scale of 1024) on the room workload after online training:
+    on the oracle's pairs of 1,000 sampled pixels, away from activation
+    kinks, its gradients of the FP16 network (the model's FP16 weights and
+    latents) agree with the FP64 oracle's within relative L2 2e-2; untouched
+    latents stay exactly zero."""
+    from paper_2306_07191_gb300 import pipeline
+    cfg = pipeline.RoomConfig()
+    p = pipeline.RoomPipeline(cfg, log=lambda *a: None)
+    p.train()
+    ors, r, ob, inn = _room_subset(p, cfg)
+    GF = p.V * cfg.n_features
+    K = 3 * len(cfg.res) * cfg.n_features
+    g16, w16 = p.model.grids, p.model.weights
+    wflat = w16.float().cpu().numpy().astype(np.float64)
+    P = wflat.size // 2
+    nets = [synth.unflatten_mlp(wflat[g * P:(g + 1) * P], K, cfg.width_mlp, cfg.n_hidden) for g in range(2)]
+    asked = []
+    rec = onif.Model(res=list(cfg.res), F=cfg.n_features, log2_table=cfg.log2_table, obj_aabb=p.ws.scene.obj_aabb,
+                     grids=_Grids(GF, lambda base: _Recorder(asked, base)), nets=nets, net_mode="class")
+    onif.encode(rec, ors, r, ob)
+    keys = np.unique(np.concatenate(asked))
+    vals = g16[torch.from_numpy(keys).cuda()].float().cpu().numpy().astype(np.float64)
+    om = onif.Model(res=list(cfg.res), F=cfg.n_features, log2_table=cfg.log2_table, obj_aabb=p.ws.scene.obj_aabb,
+                    grids=_Grids(GF, lambda base: _Sparse(keys, vals, base)), nets=nets, net_mode="class")
+    keep = _away_from_kinks(om, ors, r, ob, inn)
+    assert keep.mean() > 0.97
+    r, ob, inn = r[keep], ob[keep], inn[keep]
+    order = np.argsort(inn, kind="stable")
+    r, ob, inn = r[order], ob[order], inn[order]
+    nq = len(r)
+    y = _labels_for(r, ob)
+    Lo, dnets, (gk, gv) = onif.loss_and_grads(om, ors, r, ob, inn, y.astype(np.float64), sparse_grids=True)
+    tr = nif.Trainer(p.model, half_precision=True, loss_scale=1024.0)
+    rays_t = torch.from_numpy(ors).cuda()
+    ray_id = torch.from_numpy(r.astype(np.int32)).cuda()
+    qobj = torch.from_numpy((ob.astype(np.uint32) | (inn.astype(np.uint32) << 31)).view(np.int32)).cuda()
+    goff = torch.tensor([0, int((~inn).sum()), nq], dtype=torch.int64, device="cuda")
+    loss = tr.grads(rays_t, ray_id, qobj, goff, torch.from_numpy(y).cuda(), nq)
+    torch.cuda.synchronize()
+    p.model.check(tr._ws)
+    assert abs(float(loss.item()) - Lo) <= 2e-2 * max(Lo, 1e-6) + 1e-6
+    gw = tr.w_grad.cpu().numpy() / 1024.0
+    want_w = np.concatenate([np.concatenate([m.reshape(-1) for m in net]) for net in dnets])
+    assert _rel_l2(gw, want_w) <= 2e-2, _rel_l2(gw, want_w)
+    gk_t = torch.from_numpy(gk).cuda()
+    gg = tr.g_grad[gk_t].cpu().numpy() / 1024.0
+    assert np.abs(gv).max() > 0 and _rel_l2(gg, gv) <= 2e-2, _rel_l2(gg, gv)
+    rest = tr.g_grad.detach()
+    rest[torch.from_numpy(_tapped(om, ors, r, ob)).cuda()] = 0
+    assert int(torch.count_nonzero(rest).item()) == 0
+
+
+def test_dynamic_loss_scale_skips_overflowing_steps():
+    """Dynamic loss scaling on the half-precision path: a step whose scaled
+    gradients overflow FP16 (a 64-pair batch under a scale of 2^28) leaves
+    the masters and moments unchanged, zeroes the gradients and halves the
+    scale; a step under a scale that fits updates the masters; after
+    scale_window clean steps the scale doubles.  No host synchronisation is
+    needed inside a step: the scale and its state live on the device."""
+    model, om, rays, flat, grid = _setup(n_rays=8000, seed=21, res=(4, 5, 8, 13, 19, 28, 43, 64))
+    cfg16 = nif.NifConfig(**{**model.cfg.__dict__, "mlp_dtype": L.NIF_F16})
+    m16 = nif.NifModel(cfg16, model.obj_aabb, model.grids.clone(), model.weights.half())
+    rays_t = torch.from_numpy(rays).cuda()
+    ray_id, qobj, goff, nq, r, ob, inn = _frontend(m16, rays_t)
+    sel = torch.arange(64, device="cuda")
+    n_out = int((~torch.from_numpy(inn[:64])).sum())
+    g64 = torch.tensor([0, n_out, 64], dtype=torch.int64, device="cuda")
+    order = torch.from_numpy(np.argsort(inn[:64], kind="stable")).cuda()
+    rid64, q64 = ray_id[sel][order].contiguous(), qobj[sel][order].contiguous()
+    lab = torch.from_numpy(_labels_for(r[:64], ob[:64])[np.argsort(inn[:64], kind="stable")]).cuda()
+    tr = nif.Trainer(m16, half_precision=True, dynamic_scale=True, loss_scale=float(1 << 28), scale_window=3)
+    w0, g0 = tr.w_master.clone(), tr.g_master.clone()
+    tr.step(rays_t, rid64, q64, g64, lab, 64)
+    torch.cuda.synchronize()
+    assert float(tr.scale.item()) == float(1 << 27)
+    assert torch.equal(tr.w_master, w0) and torch.equal(tr.g_master, g0)
+    assert float(tr.w_grad.abs().max()) == 0.0 and float(tr.w_m.abs().max()) == 0.0
+    # halve until it fits, then updates happen and clean steps count
+    for _ in range(12):
+        tr.step(rays_t, rid64, q64, g64, lab, 64)
+    torch.cuda.synchronize()
+    assert not torch.equal(tr.w_master, w0)
+    s = float(tr.scale.item())
+    assert 1.0 <= s < float(1 << 27)
+    st = tr.scale_state.cpu().tolist()
+    assert st[0] == 0 and 0 <= st[1] < 3
+    m16.check(tr._ws)
+
+
+def test_half_precision_training_learns_like_fp32():
+    """Online training of the room pipeline at a reduced size with the
+    half-precision path (FP16 operands on the tensor cores, dynamic loss
+    scale) reaches a loss and a visibility disagreement with the BVH close
+    to the FP32 path's on the same batches."""
+    from paper_2306_07191_gb300 import pipeline
+    res = {}
+    for hp in (False, True):
+        cfg = pipeline.RoomConfig(half_precision_train=hp)
+        cfg.width, cfg.height, cfg.n_obj = 640, 360, 12
+        cfg.train_steps, cfg.batch, cfg.train_spp = 32, 32768, 1
+        p = pipeline.RoomPipeline(cfg, log=lambda *a: None)
+        p.train()
+        res[hp] = (p.losses[-1], p.disagreement()["all"])
+        p.check()
+    (l32, d32), (l16, d16) = res[False], res[True]
+    assert l16 <= 1.25 * l32 + 2e-3, res
+    assert d16 <= 1.25 * d32 + 2e-3, res
