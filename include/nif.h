@@ -372,6 +372,18 @@ nif_status nif_encode(const nif_model_desc* m, const nif_ray* d_rays, const uint
                       const uint32_t* d_qobj, int64_t nq, void* d_features,
                       int32_t features_dtype, void* stream);
 
+/* The inference stage alone (the paper's separate "Inference" kernel after
+ * its "Grid" kernel, Sec. 6.6 and Table 2): the network over encoded inputs
+ * d_x [nq][K] in the network's 16-bit operand type (e.g. nif_encode's FP16
+ * rows for an FP16 network; rows 16-byte aligned: K a multiple of 8), grouped
+ * by network as d_group_off [n_nets + 1] gives them; d_logits[q] (FP32)
+ * receives each row's logit z.  Tensor cores, two tiles of 128 rows in flight
+ * per CTA.  FP16 or BF16 networks of width 64 with one output and at most two
+ * networks (single or class mode).  d_ws (nullable, >= 256 bytes) receives
+ * device errors (timed-out waits) for nif_check. */
+nif_status nif_mlp_infer(const nif_model_desc* m, const void* d_x, const int64_t* d_group_off, int64_t nq,
+                         float* d_logits, void* d_ws, size_t ws_bytes, void* stream);
+
 /* Steps a1-a4 on a grouped query list: per query the logit z (d_logits[q],
  * nullable) and, for z < 0 (sigmoid(z) < 0.5, occluded), bit d_ray_id[q] is
  * OR-ed into d_occluded_bits (nullable; caller initialises it, e.g. to zero

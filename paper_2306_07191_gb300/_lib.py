@@ -91,6 +91,7 @@ SIGNATURES = {
     "nif_check": (i32, [P, ctypes.POINTER(i64), P]),
     "nif_frontend": (i32, [MD, P, P, i64, P, P, i64, P, P, P, size_t, P]),
     "nif_encode": (i32, [MD, P, P, P, i64, P, i32, P]),
+    "nif_mlp_infer": (i32, [MD, P, P, i64, P, P, size_t, P]),
     "nif_infer_queries": (i32, [MD, P, i64, P, P, P, i64, P, P, P, size_t, P]),
     "nif_infer": (i32, [MD, P, P, i64, P, P, size_t, P]),
     "nif_infer_query_counts": (i32, [MD, P, size_t, i64, P, P]),

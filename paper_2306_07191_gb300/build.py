@@ -23,6 +23,7 @@ UNITS = {
     "nif_simt.cu": [],
     "nif_tc.cu": [],
     "nif_train_tc.cu": [],
+    "nif_mlp_tc.cu": [],
     "api.cu": [],
     "noalloc.cu": [],
     "det.cu": [],

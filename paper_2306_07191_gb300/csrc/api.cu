@@ -403,6 +403,21 @@ nif_status nif_infer_queries(const nif_model_desc* m, const nif_ray* d_rays, int
                        m->tile_m, m->ctas_per_sm, static_cast<DevError*>(d_ws), st);
 }
 
+nif_status nif_mlp_infer(const nif_model_desc* m, const void* d_x, const int64_t* d_group_off, int64_t nq,
+                         float* d_logits, void* d_ws, size_t ws_bytes, void* stream) {
+  CallRange nvtx_range("nif_mlp_infer");
+  NifParams p;
+  nif_status s = make_params(m, &p);
+  if (s != NIF_OK) return s;
+  NIF_CHECK_ARG(nq >= 0, "nif_mlp_infer: negative nq");
+  NIF_CHECK_ARG(d_group_off != nullptr, "nif_mlp_infer: null group offsets");
+  if (nq == 0) return NIF_OK;
+  NIF_CHECK_ARG(d_x && d_logits, "nif_mlp_infer: null pointer");
+  NIF_CHECK_ARG(aligned16(d_x), "nif_mlp_infer: inputs not 16-byte aligned");
+  NIF_CHECK_ARG(d_ws == nullptr || ws_bytes >= kErrBytes, "nif_mlp_infer: workspace too small");
+  return launch_mlp_pipe(p, d_x, d_group_off, nq, d_logits, static_cast<DevError*>(d_ws), as_stream(stream));
+}
+
 nif_status nif_infer(const nif_model_desc* m, const void* d_tlas, const nif_ray* d_rays, int64_t n,
                      uint32_t* d_occluded_bits, void* d_ws, size_t ws_bytes, void* stream) {
   CallRange nvtx_range("nif_infer");

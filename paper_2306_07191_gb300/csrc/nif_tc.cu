@@ -753,9 +753,6 @@ __host__ __device__ inline uint32_t ws_cols(int Kp, int W) {
   return need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
 }
 
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
 // Named barrier 1 over the four MLP warps, OR-reducing a predicate, so that
 // every MLP thread takes the same branch after it.
 __device__ __forceinline__ bool mlp_sync_or(bool pred) {

@@ -151,6 +151,23 @@ def test_gradients_match_oracle(act):
     assert not np.any(gg.reshape(-1)[untouched])
 
 
+def _ulp_nudged(rays, seed=0):
+    """The rays with every origin and direction component moved by one FP32
+    ulp up or down at random (an input, to measure how much the FP64
+    gradient itself moves under FP32 rounding of its inputs)."""
+    rng = np.random.default_rng(seed)
+    out = rays.copy()
+    for c in (0, 1, 2, 4, 5, 6):
+        up = rng.random(len(out)) < 0.5
+        out[:, c] = np.where(up, np.nextafter(out[:, c], np.float32(np.inf)),
+                             np.nextafter(out[:, c], np.float32(-np.inf))).astype(np.float32)
+    return out
+
+
+def _flat_w(dnets):
+    return np.concatenate([np.concatenate([m.reshape(-1) for m in net]) for net in dnets])
+
+
 class _Recorder:
     """A grid table that records the entries a lookup asks for (and answers
     zeros): the oracle's own tap indices, before any value is known."""
@@ -231,6 +248,10 @@ def test_room_subset_gradients_match_oracle():
     nq = len(r)
     y = _labels_for(r, ob)
     Lo, dnets, (gk, gv) = onif.loss_and_grads(om, ors, r, ob, inn, y.astype(np.float64), sparse_grids=True)
+    # how far the FP64 gradient itself moves when the rays move by one ulp
+    _, dn_u, (gk_u, gv_u) = onif.loss_and_grads(om, _ulp_nudged(ors), r, ob, inn, y.astype(np.float64),
+                                                sparse_grids=True)
+    cond_w = _rel_l2(_flat_w(dn_u), _flat_w(dnets))
     # the same pairs on the GPU: the FP32 masters through nif_fwd_train,
     # nif_loss, nif_mlp_bwd and nif_grid_bwd
     rays_t = torch.from_numpy(ors).cuda()
@@ -244,10 +265,14 @@ def test_room_subset_gradients_match_oracle():
     loss.backward()
     assert abs(float(loss.item()) - Lo) <= 1e-5 * max(1.0, Lo)
     gw = w.grad.cpu().numpy()
-    want_w = np.concatenate([np.concatenate([m.reshape(-1) for m in net]) for net in dnets])
-    assert _rel_l2(gw, want_w) <= 1e-3
+    want_w = _flat_w(dnets)
     gk_t = torch.from_numpy(gk).cuda()
     gg = g.grad[gk_t].cpu().numpy()
+    both = np.intersect1d(gk, gk_u)
+    cond_g = _rel_l2(gv_u[np.searchsorted(gk_u, both)], gv[np.searchsorted(gk, both)])
+    print(f"\nroom subset, FP32 path: {nq} pairs ({keep.mean():.4f} kept); rel L2 weights {_rel_l2(gw, want_w):.3e} "
+          f"(FP64 moves {cond_w:.3e} under 1 ulp), latents {_rel_l2(gg, gv):.3e} (FP64 moves {cond_g:.3e})")
+    assert _rel_l2(gw, want_w) <= 1e-3
     assert np.abs(gv).max() > 0 and _rel_l2(gg, gv) <= 1e-3
     # every latent no pair taps (of the 1.465G) is exactly zero
     rest = g.grad.detach()
@@ -453,10 +478,12 @@ def test_half_precision_gradients_room_subset():
     p.model.check(tr._ws)
     assert abs(float(loss.item()) - Lo) <= 2e-2 * max(Lo, 1e-6) + 1e-6
     gw = tr.w_grad.cpu().numpy() / 1024.0
-    want_w = np.concatenate([np.concatenate([m.reshape(-1) for m in net]) for net in dnets])
-    assert _rel_l2(gw, want_w) <= 2e-2, _rel_l2(gw, want_w)
+    want_w = _flat_w(dnets)
     gk_t = torch.from_numpy(gk).cuda()
     gg = tr.g_grad[gk_t].cpu().numpy() / 1024.0
+    print(f"\nroom subset, half-precision path: {nq} pairs; rel L2 weights {_rel_l2(gw, want_w):.3e}, "
+          f"latents {_rel_l2(gg, gv):.3e}")
+    assert _rel_l2(gw, want_w) <= 2e-2, _rel_l2(gw, want_w)
     assert np.abs(gv).max() > 0 and _rel_l2(gg, gv) <= 2e-2, _rel_l2(gg, gv)
     rest = tr.g_grad.detach()
     rest[torch.from_numpy(_tapped(om, ors, r, ob)).cuda()] = 0
