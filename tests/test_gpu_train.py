@@ -235,7 +235,9 @@ def test_room_subset_gradients_match_oracle():
                                         cfg.width_mlp, cfg.n_hidden))
     rec = onif.Model(res=list(cfg.res), F=cfg.n_features, log2_table=cfg.log2_table, obj_aabb=ws.scene.obj_aabb,
                      grids=_Grids(GF, lambda base: _Recorder(asked, base)), nets=nets, net_mode="class")
+    nudged = _ulp_nudged(ors)
     onif.encode(rec, ors, r, ob)
+    onif.encode(rec, nudged, r, ob)
     keys = np.unique(np.concatenate(asked))
     vals = gm[torch.from_numpy(keys).cuda()].cpu().numpy().astype(np.float64)
     om = onif.Model(res=list(cfg.res), F=cfg.n_features, log2_table=cfg.log2_table, obj_aabb=ws.scene.obj_aabb,
@@ -249,7 +251,7 @@ def test_room_subset_gradients_match_oracle():
     y = _labels_for(r, ob)
     Lo, dnets, (gk, gv) = onif.loss_and_grads(om, ors, r, ob, inn, y.astype(np.float64), sparse_grids=True)
     # how far the FP64 gradient itself moves when the rays move by one ulp
-    _, dn_u, (gk_u, gv_u) = onif.loss_and_grads(om, _ulp_nudged(ors), r, ob, inn, y.astype(np.float64),
+    _, dn_u, (gk_u, gv_u) = onif.loss_and_grads(om, nudged, r, ob, inn, y.astype(np.float64),
                                                 sparse_grids=True)
     cond_w = _rel_l2(_flat_w(dn_u), _flat_w(dnets))
     # the same pairs on the GPU: the FP32 masters through nif_fwd_train,
