@@ -667,7 +667,8 @@ def run_ours(args):
                    "exact_cast": cfg.exact_cast, "cuda_graph": bool(graphs),
                    "round1": round1, "round1_pairs": round1_pairs,
                    "fused_schedule": SCHED_NAME[pipe.forward_models()[0][0].cfg.schedule],
-                   "fused_ctas_per_sm": pipe.forward_models()[0][0].cfg.ctas_per_sm, "autotune_ms": tune_ms,
+                   "fused_ctas_per_sm": pipe.forward_models()[0][0].cfg.ctas_per_sm,
+                   "fused_tile_m": pipe.forward_models()[0][0].cfg.tile_m or 128, "autotune_ms": tune_ms,
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "ms_per_step_eager": ms_eager,
         "bvh_rays_per_s": world * n / (bms * 1e-3), "bvh_ms_per_step": bms,
@@ -807,6 +808,7 @@ def run_grouped(args):
             "config": {"workload": WORKLOADS["grouped"], "rays": n, "objects": n_obj,
                        "triangles": int(sc.tris.shape[0]), "pairs_per_object": gw.counts.tolist(),
                        "fused_schedule": SCHED_NAME[sched], "fused_ctas_per_sm": best,
+                       "fused_tile_m": model.cfg.tile_m or 128,
                        "autotune_ms": sweep, "cuda_graph": True},
             "bvh_rays_per_s": n / (bvh_ms * 1e-3), "bvh_ms_per_step": bvh_ms, "speedup_vs_bvh": bvh_ms / nif_ms,
             "roofline": {"kernel": "nif fused encode+MLP (tcgen05), grouped", "bound": "hbm",

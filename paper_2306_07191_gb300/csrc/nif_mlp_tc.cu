@@ -7,8 +7,9 @@
 // k_mlp_pipe is persistent and warp-specialised, with two tiles of 128 rows
 // in flight per CTA (slots 0 and 1), so that one tile's MMAs run while the
 // other tile's epilogue runs:
-//   warps 0-1   load a tile's inputs into the slot's shared-memory A tile
-//               (16-byte copies into the K-major core-matrix layout);
+//   warps 0, 1, 3 load a tile's inputs into the slot's shared-memory A tile
+//               (16-byte copies, eight in flight per thread, into the
+//               K-major core-matrix layout);
 //   warp 2      one thread issues the MMAs: per layer, slot 0 then slot 1
 //               (layer 1 reads A from shared memory, later layers from TMEM);
 //   warps 4-7   epilogue of slot 0, warps 8-11 epilogue of slot 1: each
@@ -28,7 +29,8 @@ namespace tc {
 
 constexpr int kPipeWarps = 12;
 constexpr int kPipeThreads = 32 * kPipeWarps;
-constexpr int kPipeLoaders = 64;  // threads of warps 0-1
+constexpr int kPipeLoaders = 96;  // threads of warps 0, 1 and 3
+constexpr int kPipeBatch = 8;     // 16-byte loads in flight per loader thread
 constexpr int kPipeMaxNets = 2;
 
 struct PipeLayout {
@@ -111,9 +113,9 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
   auto tile_of = [&](int k) { return static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(k) * gridDim.x; };
   const uint32_t idesc = instr_desc(kM, W, O::fmt);
 
-  if (warp < 2) {
+  if (warp < 2 || warp == 3) {
     // ---------------------------------------------------------- loaders
-    const int lt = tid;
+    const int lt = warp == 3 ? 64 + lane : tid;
     const int cpr = Kp / 8;  // 16-byte chunks per row
     for (int k = 0;; ++k) {
       const int64_t t = tile_of(k);
@@ -126,12 +128,20 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
       const int g = find_group(s_pre, p.n_nets, t);
       const int64_t q0 = goff[g] + (t - s_pre[g]) * kM, qend = goff[g + 1];
       uint8_t* xs = smem + L.x_off[s];
-      for (int c = lt; c < 128 * cpr; c += kPipeLoaders) {
-        const int r = c / cpr, kb = c % cpr;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (q0 + r < qend && kb * 8 < K)
-          v = __ldg(reinterpret_cast<const uint4*>(x + (q0 + r) * static_cast<int64_t>(K) + kb * 8));
-        *reinterpret_cast<uint4*>(xs + tile_off(r, kb * 8, Kp, 2)) = v;
+      for (int c0 = lt; c0 < 128 * cpr; c0 += kPipeLoaders * kPipeBatch) {
+        uint4 v[kPipeBatch];
+#pragma unroll
+        for (int i = 0; i < kPipeBatch; ++i) {
+          const int c = c0 + i * kPipeLoaders, r = c / cpr, kb = c % cpr;
+          v[i] = make_uint4(0u, 0u, 0u, 0u);
+          if (c < 128 * cpr && q0 + r < qend && kb * 8 < K)
+            v[i] = __ldg(reinterpret_cast<const uint4*>(x + (q0 + r) * static_cast<int64_t>(K) + kb * 8));
+        }
+#pragma unroll
+        for (int i = 0; i < kPipeBatch; ++i) {
+          const int c = c0 + i * kPipeLoaders, r = c / cpr, kb = c % cpr;
+          if (c < 128 * cpr) *reinterpret_cast<uint4*>(xs + tile_off(r, kb * 8, Kp, 2)) = v[i];
+        }
       }
       fence_proxy_async();
       mbar_arrive(smem_u32(&s_xfull[s]));
@@ -201,12 +211,19 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
         if (!ok) break;
         tc_fence_after();
         float z = 0.f;
-        for (int c0 = 0; c0 < W; c0 += 16) {
+        // the row's W = 64 accumulator columns: four loads in flight, one wait
+        uint32_t raw[4][16];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tmem_ld16_nowait(lane_base + static_cast<uint32_t>(16 * c), raw[c]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) tmem_ld_wait16(raw[c]);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const int c0 = 16 * c;
           float v[16];
-          tmem_ld16(lane_base + static_cast<uint32_t>(c0), v);
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
-            const float a = v[i];
+            const float a = __uint_as_float(raw[c][i]);
             v[i] = a > 0.f ? a : (p.act == NIF_ACT_LEAKY ? p.slope * a : 0.f);
           }
           if (l + 1 < H) {

@@ -385,7 +385,7 @@ struct LayoutTm {
   }
 };
 
-__host__ __device__ inline LayoutTm make_layout_tm(int Kp, int W, int H, int n_nets, int n_out = 1) {
+__host__ __device__ inline LayoutTm make_layout_tm(int Kp, int W, int H, int n_nets, int n_out = 1, int rb = 1) {
   LayoutTm L{};
   L.w0_off = 0;
   L.w1_bytes = W * Kp * 2;
@@ -395,16 +395,17 @@ __host__ __device__ inline LayoutTm make_layout_tm(int Kp, int W, int H, int n_n
   L.wout_off = o;
   o += n_out * W * 4;
   L.zpart_off = o;
-  o += 2 * n_out * kM * 4;
+  o += 2 * n_out * kM * rb * 4;
   L.pre_off = o;
   o += (n_nets + 1) * 8;
   L.total = o;
   return L;
 }
 
-// TMEM columns: accumulator [0, W), activations [W, W + max(Kp, W)/2).
-__host__ __device__ inline uint32_t tm_cols(int Kp, int W) {
-  const int need = W + (Kp > W ? Kp : W) / 2;
+// TMEM columns per row block: accumulator [0, W), activations
+// [W, W + max(Kp, W)/2); rb row blocks of 128 queries side by side.
+__host__ __device__ inline uint32_t tm_cols(int Kp, int W, int rb = 1) {
+  const int need = rb * (W + (Kp > W ? Kp : W) / 2);
   return need <= 32 ? 32 : need <= 64 ? 64 : need <= 128 ? 128 : need <= 256 ? 256 : 512;
 }
 
@@ -414,8 +415,8 @@ __host__ __device__ inline uint32_t tm_cols(int Kp, int W) {
 // p.saved16 (the operands of the tensor-core backward).
 constexpr int kMaxOut = 8;
 
-template <int F, typename TG, int DT, int kOcc, bool kMulti = false, bool kSave = false>
-__global__ void __launch_bounds__(kThreads, kOcc)
+template <int F, typename TG, int DT, int kOcc, bool kMulti = false, bool kSave = false, int kRB = 1>
+__global__ void __launch_bounds__(kThreads * kRB, kOcc)
     k_fused_tm(const __grid_constant__ NifParams p, const nif_ray* __restrict__ rays,
                const uint32_t* __restrict__ ray_id, const uint32_t* __restrict__ qobj,
                const int64_t* __restrict__ goff, uint32_t* __restrict__ occ,
@@ -434,12 +435,13 @@ __global__ void __launch_bounds__(kThreads, kOcc)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int W = p.width, H = p.n_hidden, K = p.K;
   const int nout = kMulti ? p.O : 1;
-  const LayoutTm L = make_layout_tm(Kp, W, H, p.n_nets, nout);
+  const LayoutTm L = make_layout_tm(Kp, W, H, p.n_nets, nout, kRB);
+  constexpr int kTM = kM * kRB;  // queries per tile
   float* wout = reinterpret_cast<float*>(smem + L.wout_off);
   float* zpart = reinterpret_cast<float*>(smem + L.zpart_off);
   int64_t* s_pre = reinterpret_cast<int64_t*>(smem + L.pre_off);
   const uint32_t bar = smem_u32(&s_bar);
-  const uint32_t ncols = tm_cols(Kp, W);
+  const uint32_t ncols = tm_cols(Kp, W, kRB);
 
   if (warp == 0) tmem_alloc(smem_u32(&s_tmem), ncols);
   const uint32_t wbar = smem_u32(&s_wbar);
@@ -454,18 +456,21 @@ __global__ void __launch_bounds__(kThreads, kOcc)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = s_tmem;
-  const uint32_t act_col = static_cast<uint32_t>(W);  // activation columns start here
-
-  const int64_t n_tiles = build_tile_prefix(goff, p.n_nets, kM, s_pre);
+  const int64_t n_tiles = build_tile_prefix(goff, p.n_nets, kTM, s_pre);
   const uint32_t idesc = instr_desc(kM, W, O::fmt);
   uint32_t phase = 0;
   int cur_g = -1;
 
-  const int qi = tid & (kM - 1);  // query row == TMEM lane
-  const int half = tid >> 7;       // level parity handled by this thread
+  const int qi = tid & (kM - 1);                   // query row == TMEM lane
+  const int blk = kRB > 1 ? (tid >> 7) & (kRB - 1) : 0;  // row block of this thread's query
+  const int half = tid >> (kRB > 1 ? 8 : 7);        // level parity handled by this thread
+  const int rq = blk * kM + qi;                     // query row within the tile
   const int ecol0 = half * (W / 2);
-  // this warp's lane quarter: rows 32*(warp&3) .. +31
-  const uint32_t lane_base = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16);
+  // row block b's columns: accumulator [b*cb, b*cb + W), activations after it
+  const uint32_t cb = static_cast<uint32_t>(W + (Kp > W ? Kp : W) / 2);
+  // this warp's lane quarter: rows 32*(warp&3) .. +31, in its row block's columns
+  const uint32_t lane_base = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + static_cast<uint32_t>(blk) * cb;
+  const uint32_t act_rel = static_cast<uint32_t>(W);  // activations, relative to lane_base
 
   auto pack2 = [](float a, float b) {
     typename O::T x = O::cvt(a), y = O::cvt(b);
@@ -477,7 +482,7 @@ __global__ void __launch_bounds__(kThreads, kOcc)
   __syncthreads();
   for (int64_t t = s_next; t < n_tiles; t = s_next) {
     const int g = find_group(s_pre, p.n_nets, t);
-    const int64_t q0 = goff[g] + (t - s_pre[g]) * kM;
+    const int64_t q0 = goff[g] + (t - s_pre[g]) * kTM;
     const int64_t qend = goff[g + 1];
 
     // ---- weights of network g into shared memory (B operands, K-major):
@@ -498,7 +503,7 @@ __global__ void __launch_bounds__(kThreads, kOcc)
           const int fin = l == 0 ? K : W;
           const int fpad = l == 0 ? Kp : W;
           uint8_t* wt = smem + L.w_off(l);
-          for (int e = tid; e < W * fpad; e += kThreads) {
+          for (int e = tid; e < W * fpad; e += kThreads * kRB) {
             const int n = e / fpad, k = e % fpad;
             const float v = k < fin ? O::load(p.weights, wbase + off + static_cast<int64_t>(n) * fin + k) : 0.f;
             store_elem<DT>(wt, n, k, fpad, v);
@@ -507,7 +512,7 @@ __global__ void __launch_bounds__(kThreads, kOcc)
         }
         fence_proxy_async();
       }
-      for (int e = tid; e < W * nout; e += kThreads) wout[e] = O::load(p.weights, wbase + off_out + e);
+      for (int e = tid; e < W * nout; e += kThreads * kRB) wout[e] = O::load(p.weights, wbase + off_out + e);
       cur_g = g;
     }
 
@@ -516,7 +521,7 @@ __global__ void __launch_bounds__(kThreads, kOcc)
       // the paper's encoding: a few taps per query, so the first four warps
       // (one per lane quarter) build whole rows and store them packed
       if (half == 0) {
-        const int64_t q = q0 + qi;
+        const int64_t q = q0 + rq;
         float x[kSphMaxK];
 #pragma unroll
         for (int k = 0; k < kSphMaxK; ++k) x[k] = 0.f;
@@ -530,11 +535,11 @@ __global__ void __launch_bounds__(kThreads, kOcc)
           uint32_t pk[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) pk[i] = pack2(x[2 * (c + i)], x[2 * (c + i) + 1]);
-          tmem_st8(lane_base + act_col + static_cast<uint32_t>(c), pk);
+          tmem_st8(lane_base + act_rel + static_cast<uint32_t>(c), pk);
         }
       }
     } else {
-      const int64_t q = q0 + qi;
+      const int64_t q = q0 + rq;
       const bool live = q < qend && check_query(p, ray_id, qobj, q);
       QueryPoints pts;
       const TG* tpos = nullptr;
@@ -611,7 +616,7 @@ __global__ void __launch_bounds__(kThreads, kOcc)
             }
 #pragma unroll
             for (int u = 0; u < kJB; ++u) {
-              tmem_st1(lane_base + act_col + static_cast<uint32_t>((jb + u) * p.L + l), word[u]);
+              tmem_st1(lane_base + act_rel + static_cast<uint32_t>((jb + u) * p.L + l), word[u]);
               if constexpr (kSave)
                 if (q < qend) p.saved16[static_cast<int64_t>((jb + u) * p.L + l) * p.ld_saved + q] = word[u];
             }
@@ -630,13 +635,13 @@ __global__ void __launch_bounds__(kThreads, kOcc)
             }
 #pragma unroll
             for (int f2 = 0; f2 < FP; ++f2)
-              tmem_st1(lane_base + act_col + static_cast<uint32_t>((j * p.L + l) * FP + f2),
+              tmem_st1(lane_base + act_rel + static_cast<uint32_t>((j * p.L + l) * FP + f2),
                        pack2(v[2 * f2], v[2 * f2 + 1]));
           }
         }
       }
       if (half == 0)
-        for (int k2 = K / 2; k2 < Kp / 2; ++k2) tmem_st1(lane_base + act_col + k2, 0u);
+        for (int k2 = K / 2; k2 < Kp / 2; ++k2) tmem_st1(lane_base + act_rel + k2, 0u);
     }
     tmem_wait_st();
     tc_fence_before();
@@ -654,7 +659,9 @@ __global__ void __launch_bounds__(kThreads, kOcc)
         const uint32_t sbo = (kdim / 8) * 128;
         for (int kk = 0; kk < kdim / 16; ++kk) {
           const uint64_t bd = smem_desc(b0 + kk * 256, 128, sbo);
-          mma_ta(tmem, tmem + act_col + static_cast<uint32_t>(kk * 8), bd, idesc, kk > 0 ? 1u : 0u);
+#pragma unroll
+          for (int b = 0; b < kRB; ++b)
+            mma_ta(tmem + b * cb, tmem + b * cb + static_cast<uint32_t>(W + kk * 8), bd, idesc, kk > 0 ? 1u : 0u);
         }
         mma_commit(bar);
       }
@@ -675,7 +682,7 @@ __global__ void __launch_bounds__(kThreads, kOcc)
           uint32_t pk[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) pk[i] = pack2(v[2 * i], v[2 * i + 1]);
-          const int64_t qs = q0 + qi;
+          const int64_t qs = q0 + rq;
           if (qs < qend)
 #pragma unroll
             for (int i = 0; i < 8; ++i)
@@ -685,7 +692,7 @@ __global__ void __launch_bounds__(kThreads, kOcc)
           uint32_t pk[8];
 #pragma unroll
           for (int i = 0; i < 8; ++i) pk[i] = pack2(v[2 * i], v[2 * i + 1]);
-          tmem_st8(lane_base + act_col + static_cast<uint32_t>((ecol0 + c0) / 2), pk);
+          tmem_st8(lane_base + act_rel + static_cast<uint32_t>((ecol0 + c0) / 2), pk);
         } else if constexpr (kMulti) {
 #pragma unroll
           for (int o = 0; o < kMaxOut; ++o)
@@ -707,18 +714,18 @@ __global__ void __launch_bounds__(kThreads, kOcc)
     // ---- step a4: logit (and the other outputs) and visibility
 #pragma unroll
     for (int o = 0; o < (kMulti ? kMaxOut : 1); ++o)
-      if (o < nout) zpart[(half * nout + o) * kM + qi] = zacc[o];
+      if (o < nout) zpart[(half * nout + o) * kTM + rq] = zacc[o];
     __syncthreads();
-    if (tid < kM) {
+    if (tid < kTM) {
       const int64_t q = q0 + tid;
       if (q < qend) {
         // a rejected query's outputs are 0 and its ray's bit is left alone
         const bool ok = query_ok(p, ray_id[q], qobj[q]);
-        const float z = ok ? zpart[tid] + zpart[nout * kM + tid] : 0.f;
+        const float z = ok ? zpart[tid] + zpart[nout * kTM + tid] : 0.f;
         if constexpr (kMulti) {
           if (logits)
             for (int o = 0; o < nout; ++o)
-              logits[q * nout + o] = ok ? zpart[o * kM + tid] + zpart[(nout + o) * kM + tid] : 0.f;
+              logits[q * nout + o] = ok ? zpart[o * kTM + tid] + zpart[(nout + o) * kTM + tid] : 0.f;
         } else {
           if (logits) logits[q] = z;
         }
@@ -1121,22 +1128,30 @@ template <int DT>
 static nif_status launch_tm(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,
                             const uint32_t* qobj, const int64_t* goff, int blocks, int per_sm,
                             uint32_t* occ, float* logits, DevError* err, uint32_t* ctr,
-                            cudaStream_t st) {
+                            cudaStream_t st, int tile_m = 128) {
   const int Kp = (p.K + 15) / 16 * 16;
-  tc::LayoutTm L = tc::make_layout_tm(Kp, p.width, p.n_hidden, p.n_nets, p.O);
+  const int rb = tile_m == 256 ? 2 : 1;
+  tc::LayoutTm L = tc::make_layout_tm(Kp, p.width, p.n_hidden, p.n_nets, p.O, rb);
   size_t sh = L.total + 1024;
   tc::WeightMaps wm;
   const int use_tma = make_weight_maps(p, 2, Kp, &wm) && tc_weights_by_tma() ? 1 : 0;
   auto go = [&](auto kern) -> nif_status {
     NIF_CUDA_TRY(ensure_smem(kern, sh));
-    kern<<<blocks, tc::kThreads, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, err, Kp, wm,
-                                           use_tma, ctr);
+    kern<<<blocks, tc::kThreads * rb, sh, st>>>(p, rays, ray_id, qobj, goff, occ, logits, err, Kp, wm,
+                                                use_tma, ctr);
     return NIF_OK;
   };
   nif_status s;
   // the spherical encodings do not use F at compile time: take the F = 2 forms
   const int fsel = p.enc != NIF_ENC_MULTIRES ? 2 : p.F;
-  if (p.O > 1) {
+  if (rb == 2) {
+    // tiles of 256 queries: two 128-row blocks side by side in TMEM, one
+    // query per thread pair of each block, 2 CTAs of 512 threads per SM
+    if (p.O > 1 || fsel != 2)
+      return fail(NIF_ERR_UNSUPPORTED, "tile_m 256: one output and two features per level");
+    s = p.grid_dtype == NIF_F16 ? go(tc::k_fused_tm<2, __half, DT, 2, false, false, 2>)
+                                : go(tc::k_fused_tm<2, float, DT, 2, false, false, 2>);
+  } else if (p.O > 1) {
     // several outputs (primary rays): FP16 grids, an even F of 2
     if (p.grid_dtype != NIF_F16 || fsel != 2)
       return fail(NIF_ERR_UNSUPPORTED, "tensor-core path with %d outputs: FP16 grids and 2 features", p.O);
@@ -1250,13 +1265,28 @@ nif_status launch_fwd_tc(const NifParams& p, const nif_ray* rays, const uint32_t
   if (s != NIF_OK) return s;
   if (p.enc != NIF_ENC_MULTIRES && p.net_mode == NIF_NETS_CLASS)
     return fail(NIF_ERR_ARG, "spherical encodings: one class per model (net_mode single or object)");
-  if (tile_m != 0 && tile_m != 128)
-    return fail(NIF_ERR_UNSUPPORTED, "tensor-core path: tile_m %d (128 supported)", tile_m);
+  if (tile_m != 0 && tile_m != 128 && tile_m != 256)
+    return fail(NIF_ERR_UNSUPPORTED, "tensor-core path: tile_m %d (128 or 256 supported)", tile_m);
+  if (tile_m == 256 && (p.mlp_dtype == NIF_E4M3 || !tm_supported(p) || p.O > 1 ||
+                        p.schedule == NIF_SCHED_PIPELINED))
+    return fail(NIF_ERR_UNSUPPORTED, "tile_m 256: 16-bit operands, one output, the serial schedule");
   if (p.O > 1 && (p.mlp_dtype == NIF_E4M3 || !tm_supported(p) || p.schedule == NIF_SCHED_PIPELINED))
     return fail(NIF_ERR_UNSUPPORTED,
                 "tensor-core path with %d outputs: 16-bit operands and the serial schedule", p.O);
   uint32_t* ctr = tile_counter(err);
   if (ctr) NIF_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(uint32_t), st));
+  if (tile_m == 256) {
+    // two 128-row blocks per tile: each CTA holds tm_cols(.., 2) TMEM columns
+    const int Kp16 = (p.K + 15) / 16 * 16;
+    const int cap = 512 / static_cast<int>(tc::tm_cols(Kp16, p.width, 2));
+    const int per_sm = std::max(1, std::min(std::min(ctas_per_sm > 0 ? ctas_per_sm : 2, cap), 2));
+    int blocks = sm_count() * per_sm;
+    if (nq_hint >= 0)
+      blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(blocks, ceil_div(nq_hint, 256) + p.n_nets)));
+    if (p.mlp_dtype == NIF_F16)
+      return launch_tm<NIF_F16>(p, rays, ray_id, qobj, goff, blocks, per_sm, occ, logits, err, ctr, st, 256);
+    return launch_tm<NIF_BF16>(p, rays, ray_id, qobj, goff, blocks, per_sm, occ, logits, err, ctr, st, 256);
+  }
   if (ws_supported(p) && p.O == 1) {
     const int Kp16 = (p.K + 15) / 16 * 16;
     const bool pick = p.schedule == NIF_SCHED_PIPELINED ||

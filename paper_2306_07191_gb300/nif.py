@@ -555,27 +555,30 @@ def quantize_e4m3(weights_f32: torch.Tensor, cfg: NifConfig, n_nets: int, act_am
 # replaces the choice only when it is faster by more than TUNE_MARGIN, so that
 # timing noise between near-equal candidates does not flip the choice.
 SCHEDULE_CANDIDATES = ((L.NIF_SCHED_SERIAL, 4), (L.NIF_SCHED_PIPELINED, 0), (L.NIF_SCHED_SERIAL, 3),
-                       (L.NIF_SCHED_SERIAL, 2))
+                       (L.NIF_SCHED_SERIAL, 2), (L.NIF_SCHED_SERIAL, 2, 256))
 TUNE_MARGIN = 0.02
 
 
 def autotune(model: NifModel, run, key_extra=(), candidates=SCHEDULE_CANDIDATES, reps: int = 5,
              cache_path: str | None = None, also=()):
-    """Pick the tensor-core forward's (schedule, CTAs per SM) by timing
-    `run()` (the caller's own query, e.g. nif_infer on its rays): the median
-    of `reps` runs per candidate, each after an L2 flush.  The choice is
-    written into model.cfg (and the cfg of every model in `also`, other
-    networks the same run() queries) and cached per (model shape, key_extra,
-    GPU) in a JSON file.  Returns (schedule, ctas_per_sm, {candidate: ms})."""
+    """Pick the tensor-core forward's (schedule, CTAs per SM, tile M) by
+    timing `run()` (the caller's own query, e.g. nif_infer on its rays): the
+    median of `reps` runs per candidate, each after an L2 flush.  A candidate
+    is (schedule, ctas) or (schedule, ctas, tile_m) (tile_m 128 when left
+    out; 256 runs tiles of two 128-row blocks); one the library refuses for
+    this model is skipped.  The choice is written into model.cfg (and the cfg
+    of every model in `also`, other networks the same run() queries) and
+    cached per (model shape, key_extra, GPU) in a JSON file.  Returns
+    (schedule, ctas_per_sm, {candidate: ms})."""
     import hashlib
     import json
     import os
     c = model.cfg
     cfgs = [c] + [m.cfg for m in also]
 
-    def apply(sched, ctas):
+    def apply(sched, ctas, tile_m=128):
         for cf in cfgs:
-            cf.schedule, cf.ctas_per_sm = int(sched), int(ctas)
+            cf.schedule, cf.ctas_per_sm, cf.tile_m = int(sched), int(ctas), int(tile_m)
 
     cands = [tuple(x) for x in candidates]
     key = hashlib.sha1(json.dumps([list(c.res), c.n_features, c.log2_table, c.grid_dtype, c.n_hidden,
@@ -594,9 +597,12 @@ def autotune(model: NifModel, run, key_extra=(), candidates=SCHEDULE_CANDIDATES,
     label = {L.NIF_SCHED_SERIAL: "serial", L.NIF_SCHED_PIPELINED: "pipelined", L.NIF_SCHED_AUTO: "auto"}
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=model.obj_aabb.device)  # > L2
     timings = {}
-    for sched, ctas in cands:
-        apply(sched, ctas)
-        run()
+    for cand in cands:
+        apply(*cand)
+        try:
+            run()
+        except L.NifError:
+            continue  # not offered for this model
         torch.cuda.synchronize()
         got = []
         for _ in range(reps):
@@ -607,14 +613,15 @@ def autotune(model: NifModel, run, key_extra=(), candidates=SCHEDULE_CANDIDATES,
             e1.record()
             torch.cuda.synchronize()
             got.append(e0.elapsed_time(e1))
-        timings[(sched, ctas)] = sorted(got)[len(got) // 2]
+        timings[cand] = sorted(got)[len(got) // 2]
     del flush
-    choice = cands[0]
-    for k in cands[1:]:
+    tried = [k for k in cands if k in timings]
+    choice = tried[0]
+    for k in tried[1:]:
         if timings[k] < timings[choice] * (1.0 - TUNE_MARGIN):
             choice = k
     apply(*choice)
-    ms = {f"{label[k[0]]}/{k[1]}": v for k, v in timings.items()}
+    ms = {f"{label[k[0]]}/{k[1]}" + (f"/m{k[2]}" if len(k) > 2 else ""): v for k, v in timings.items()}
     cache[key] = {"choice": list(choice), "ms": ms}
     try:
         with open(cache_path, "w") as f:

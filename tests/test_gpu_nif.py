@@ -272,11 +272,13 @@ def test_frontend_many_pairs_per_ray(use_tlas):
     assert sorted(zip(r.tolist(), ob.tolist(), inn.tolist())) == sorted(zip(rr.tolist(), oo.tolist(), ii.tolist()))
 
 
+@pytest.mark.parametrize("tile_m", [128, 256])
 @pytest.mark.parametrize("mlp_dt,tol", [("f16", 2e-2), ("bf16", 6e-2)])
-def test_per_object_networks_grouped_launch(mlp_dt, tol):
+def test_per_object_networks_grouped_launch(mlp_dt, tol, tile_m):
     """One network per object (Sec. 6.3) in one persistent grouped launch:
     uneven group sizes, each group's weights loaded when the tile's group
-    changes; logits against the oracle with every object's own network."""
+    changes; logits against the oracle with every object's own network, for
+    tiles of 128 and of 256 queries (two 128-row blocks in TMEM)."""
     gw = workloads.grouped_objects(n_obj=6, total_rays=20000, tri_min=500, tri_max=5000, seed=3)
     rng = np.random.default_rng(9)
     res = [4, 8, 16, 32]
@@ -284,7 +286,8 @@ def test_per_object_networks_grouped_launch(mlp_dt, tol):
     grid = rng.uniform(-1, 1, size=(6, 2, int(cfg_v) * 2)).astype(np.float32)
     mats = [synth.mlp_init(rng, 24, 64, 3) for _ in range(6)]
     model, om = _build(res, 2, 19, gw.scene.obj_aabb, grid, mats, grid_dt="f16", mlp_dt=mlp_dt,
-                       net_mode=L.NIF_NETS_OBJECT)
+                       net_mode=L.NIF_NETS_OBJECT, schedule=SER)
+    model.cfg.tile_m = tile_m
     n = len(gw.rays)
     obj = np.repeat(np.arange(6), gw.counts)
     rays_t = torch.from_numpy(gw.rays).cuda()
@@ -301,11 +304,11 @@ def test_per_object_networks_grouped_launch(mlp_dt, tol):
     assert hit.all()
     zo = onif.forward(om, gw.rays, np.arange(n), obj, np.zeros(n, bool))
     err = np.abs(z.cpu().numpy()[:n] - zo)
-    assert (gw.counts % 128 != 0).any() and gw.counts.max() > 128  # ragged, multi-tile groups
+    assert (gw.counts % tile_m != 0).any() and gw.counts.max() > tile_m  # ragged, multi-tile groups
     assert err.max() <= tol, err.max()
 
 
-@pytest.mark.parametrize("sched", [SER, PIPE])
+@pytest.mark.parametrize("sched", [SER, PIPE, "serial/256"])
 @pytest.mark.parametrize("mlp_dt,tol", [("f16", 2e-2), ("bf16", 6e-2)])
 def test_sixteen_level_input_both_schedules(sched, mlp_dt, tol):
     """K = 96 (16 levels x 2 features x 3 points), hashed fine levels and two
@@ -321,7 +324,9 @@ def test_sixteen_level_input_both_schedules(sched, mlp_dt, tol):
     grid = rng.uniform(-1, 1, size=(3, 2, V * 2)).astype(np.float32)
     mats = [synth.mlp_init(rng, 96, 64, 3), synth.mlp_init(rng, 96, 64, 3)]
     model, om = _build(res, 2, log2, boxes, grid, mats, grid_dt="f16", mlp_dt=mlp_dt,
-                       net_mode=L.NIF_NETS_CLASS, schedule=sched)
+                       net_mode=L.NIF_NETS_CLASS, schedule=SER if sched == "serial/256" else sched)
+    if sched == "serial/256":  # tiles of 256 queries
+        model.cfg.tile_m = 256
     # rays aimed at a uniform point of a random box, from inside and outside
     n = 7000
     o = rng.uniform(-3, 3, size=(n, 3))
