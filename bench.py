@@ -469,6 +469,8 @@ def run_ours(args):
         cfg.schedule = {"serial": L.NIF_SCHED_SERIAL, "pipelined": L.NIF_SCHED_PIPELINED}[args.schedule]
     if args.exact_cast:
         cfg.exact_cast = args.exact_cast
+    if args.train_precision == "f16" and hasattr(cfg, "half_precision_train"):
+        cfg.half_precision_train = True
     pipe = pipe_cls(cfg, log=log)
     train_s = pipe.train()
     n_par = pipe.param_count()
@@ -481,6 +483,7 @@ def run_ours(args):
         "adam_bytes_per_step": 34 * n_par,
         "adam_floor_ms": 34 * n_par / (_peaks()[0] * 1e9) * 1e3,
         "wall_includes": "host-side batch draw (numpy) and copies",
+        "precision": args.train_precision,
         # batch loss every 8 steps and at the last one
         "loss_curve": [round(v, 6) for v in pipe.losses[::8] + pipe.losses[-1:]]}
     dis = pipe.disagreement()
@@ -571,28 +574,46 @@ def run_ours(args):
     # launch overhead between its kernels (the stage split comes from an
     # eager run with events between the calls)
     graphs = {}
-    if not args.no_graph:
-        def capture(fn):
-            g = torch.cuda.CUDAGraph()
-            gs = torch.cuda.Stream()
-            gs.wait_stream(stream)
-            with torch.cuda.stream(gs):
-                fn()
-                torch.cuda.synchronize()
-                with torch.cuda.graph(g, stream=gs):
-                    fn()
-            stream.wait_stream(gs)
+
+    def capture(fn):
+        g = torch.cuda.CUDAGraph()
+        gs = torch.cuda.Stream()
+        gs.wait_stream(stream)
+        with torch.cuda.stream(gs):
+            fn()
             torch.cuda.synchronize()
-            return g
+            with torch.cuda.graph(g, stream=gs):
+                fn()
+        stream.wait_stream(gs)
+        torch.cuda.synchronize()
+        return g
+
+    # the comparison trees over every triangle: the LBVH the pipeline built
+    # and a PLOC tree (locally-ordered clustering, lower surface-area cost),
+    # built untimed; the NIF step is compared with the faster cast
+    trees = {"lbvh": pipe.bvh, "ploc": nif.BVH(pipe.verts, pipe.tris, pipe.tags, builder="ploc")}
+    if not args.no_graph:
         graphs["nif"] = capture(nif_step)
-        graphs["bvh"] = capture(lambda: pipe.bvh.cast_shadow(rays, out=bits))
+        for name, tree in trees.items():
+            graphs[name] = capture(lambda t=tree: t.cast_shadow(rays, out=bits))
     with ClockSampler(local) as clk:
         torch.cuda.profiler.start()
         eager_ms, subs = timed(nif_step, args.steps, args.warmup, sub=True)
         nif_ms = timed(graphs["nif"].replay, args.steps, args.warmup)[0] if graphs else eager_ms
-        bvh_ms, _ = timed(graphs["bvh"].replay if graphs else (lambda: pipe.bvh.cast_shadow(rays, out=bits)),
-                          args.steps, args.warmup)
+        tree_ms = {name: timed(graphs[name].replay if graphs else (lambda t=tree: t.cast_shadow(rays, out=bits)),
+                               args.steps, args.warmup)[0] for name, tree in trees.items()}
         torch.cuda.profiler.stop()
+    tree_med = {name: statistics.median(v) for name, v in tree_ms.items()}
+    best_tree = min(tree_med, key=tree_med.get)
+    bvh_ms = tree_ms[best_tree]
+    tree_stats = {}
+    for name, tree in trees.items():
+        st_ = tree.stats(rays)
+        st_["ms_per_step"] = reduce_max(tree_med[name], world, dev)
+        st_["rays_per_s"] = world * n / (st_["ms_per_step"] * 1e-3)
+        tree_stats[name] = st_
+        tree.check()
+    log(f"comparison trees: {tree_stats}")
     clocks = clk.summary()
     nq1, nq = pipe.last_query_counts()
     pipe.check()
@@ -672,7 +693,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "ms_per_step_eager": ms_eager,
         "bvh_rays_per_s": world * n / (bms * 1e-3), "bvh_ms_per_step": bms,
-        "speedup_vs_bvh": bms / ms,
+        "speedup_vs_bvh": bms / ms, "bvh_compared": best_tree, "bvh_trees": tree_stats,
         "visibility_disagreement": dis, "ablations": abl, "train_s": train_s,
         "train": train_stats,
         "stages_ms": subs,
@@ -1091,6 +1112,9 @@ def main():
     ap.add_argument("--workload", default="full", choices=sorted(WORKLOADS))
     ap.add_argument("--primary-two-rounds", action="store_true",
                     help="primary workload: nearest pair first, then only pairs entered before the nearest hit")
+    ap.add_argument("--train-precision", choices=("f32", "f16"), default="f32",
+                    help="online training: FP32 on the CUDA cores, or FP16 operands on the tensor cores with a "
+                         "dynamic loss scale")
     ap.add_argument("--no-graph", action="store_true",
                     help="time the step's calls one by one instead of replaying a CUDA graph of them")
     ap.add_argument("--exact-cast", choices=("first", "after", "overlap"), default=None,

@@ -224,10 +224,36 @@ nif_status bvh_build(const float* d_verts, int64_t n_verts, const int32_t* d_tri
 nif_status bvh_build_boxes(const float* d_boxes, int64_t n, void* d_bvh, size_t bvh_bytes,
                            void* d_ws, size_t ws_bytes, void* stream);
 
+/* The same tree contract built by parallel locally-ordered clustering
+ * (PLOC; Meister & Bittner 2018) instead of the Morton-code split: the
+ * Morton-ordered primitives are clusters; every round each cluster finds the
+ * cluster within 16 positions of it whose union box has the least surface
+ * area, mutual nearest neighbours merge, until one cluster is left.  A tree
+ * of lower surface-area cost than bvh_build's, for the comparison of Sec. 6.6
+ * (the paper's baseline is an SAH builder).  Same output buffer and the same
+ * leaf collapse, node layout and exact casts; a larger workspace
+ * (bvh_build_ploc_workspace_size bytes).  Synchronises the stream once per
+ * clustering round (a few tens of rounds), so it is a set-up call, not one
+ * to capture in a graph. */
+size_t bvh_build_ploc_workspace_size(int64_t n_tris);
+nif_status bvh_build_ploc(const float* d_verts, int64_t n_verts, const int32_t* d_tris,
+                          int64_t n_tris, const int32_t* d_tri_tag, void* d_bvh, size_t bvh_bytes,
+                          void* d_ws, size_t ws_bytes, void* stream);
+
 /* Host copy of the build statistics (synchronises the stream): node count,
  * primitive count, tree depth.  Returns NIF_OK or an error. */
 nif_status bvh_info(const void* d_bvh, int64_t* n_nodes, int64_t* n_prims, int32_t* depth,
                     void* stream);
+
+/* Quality figures of a tree (synchronises the stream): *sah_cost, the
+ * surface-area cost of the tree as built (MacDonald & Booth 1990: the
+ * expected cost of a ray through the root's box, 1.2 per traversal step and
+ * 1 per triangle test, with the leaf collapse applied), and, over the n rays
+ * d_rays cast any-hit, the mean number of nodes visited and of triangles
+ * tested per ray (*nodes_per_ray, *tris_per_ray; 0 when n = 0).  d_sums is
+ * 16 bytes of device scratch.  Any output pointer may be NULL. */
+nif_status bvh_stats(const void* d_bvh, const nif_ray* d_rays, int64_t n, double* sah_cost,
+                     double* nodes_per_ray, double* tris_per_ray, void* d_sums, void* stream);
 
 /* Status of a BVH buffer (synchronises the stream).  The build and every
  * traversal through the buffer (the casts below, and the NIF front ends'

@@ -73,7 +73,11 @@ SIGNATURES = {
     "bvh_build_workspace_size": (size_t, [i64]),
     "bvh_build": (i32, [P, i64, P, i64, P, P, size_t, P, size_t, P]),
     "bvh_build_boxes": (i32, [P, i64, P, size_t, P, size_t, P]),
+    "bvh_build_ploc_workspace_size": (size_t, [i64]),
+    "bvh_build_ploc": (i32, [P, i64, P, i64, P, P, size_t, P, size_t, P]),
     "bvh_info": (i32, [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32), P]),
+    "bvh_stats": (i32, [P, P, i64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                        ctypes.POINTER(ctypes.c_double), P, P]),
     "bvh_check": (i32, [P, P]),
     "bvh_cast_shadow": (i32, [P, P, i64, P, P]),
     "bvh_cast_shadow_or": (i32, [P, P, i64, P, P]),

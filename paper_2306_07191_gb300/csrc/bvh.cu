@@ -20,6 +20,7 @@
 // widened by a few ulps) on boxes padded outward at build time, so it never
 // rejects a node holding a triangle whose FP32 test reports a hit.
 #include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
 
 #include "bvh_layout.cuh"
 
@@ -403,7 +404,8 @@ __global__ void k_emit_prims(const float* verts, const int32_t* tris, const floa
 }
 
 __global__ void k_header(Header* h, int kind, int64_t n, const uint32_t* cb, const uint8_t* collapse,
-                         int has_tags, int64_t off_nodes, int64_t off_prims, int64_t off_ids) {
+                         int has_tags, int64_t off_nodes, int64_t off_prims, int64_t off_ids,
+                         const float4* node_lo = nullptr) {
   Header H{};
   H.magic = kMagic;
   H.kind = kind;
@@ -421,6 +423,8 @@ __global__ void k_header(Header* h, int kind, int64_t n, const uint32_t* cb, con
     H.scene_hi[k] = n ? ord2f(cb[3 + k]) : 0.f;
   }
   H.has_tags = has_tags;
+  // surface-area cost of the tree (the bottom-up pass's cost of the root)
+  H.sah_cost = n > 1 && node_lo ? node_lo[0].w : (n > 0 ? kCostIntersect * static_cast<float>(n) : 0.f);
   if (H.depth > kStack) {
     H.status.code = NIF_ERR_UNSUPPORTED;
     H.status.detail = H.depth;
@@ -428,9 +432,280 @@ __global__ void k_header(Header* h, int kind, int64_t n, const uint32_t* cb, con
   *h = H;
 }
 
+// ------------------------------------------------------------- PLOC
+// The stronger comparison tree: parallel locally-ordered clustering (Meister
+// & Bittner 2018, "Parallel Locally-Ordered Clustering for Bounding Volume
+// Hierarchy Construction").  Clusters start as the Morton-ordered
+// primitives; every round each cluster finds, among the kPlocRadius clusters
+// on either side of it in that order, the one whose union box has the least
+// surface area, mutual nearest neighbours merge into a new node, and the
+// surviving clusters are compacted in order, until one cluster is left.  The
+// tree then gets the same leaf order, surface-area leaf collapse and node
+// layout as the LBVH.
+constexpr int kPlocRadius = 16;
+
+struct PlocWs {
+  int32_t* ref[2];   // cluster -> node reference (>= 0 inner, < 0 ~Morton position)
+  float4* lo[2];
+  float4* hi[2];
+  int32_t* nn;
+  int32_t* valid;
+  int32_t* pos;
+  int32_t* cnt;      // leaves under each inner node
+  int32_t* leafpos;  // Morton position -> position in the final leaf order
+  uint32_t* order2;  // final leaf order -> primitive
+  int32_t* lp2;      // leaf_parent in the final leaf order
+  int32_t* counters; // [0] next inner node id, [1] clusters left
+  void* scan_tmp;
+  size_t scan_bytes;
+};
+
+size_t ploc_scan_bytes(int64_t n) {
+  size_t bytes = 0;
+  if (cub::DeviceScan::ExclusiveSum(nullptr, bytes, (int32_t*)nullptr, (int32_t*)nullptr, (int)n) != cudaSuccess)
+    bytes = static_cast<size_t>(n) * 8 + (16u << 20);
+  return bytes;
+}
+
+size_t ploc_extra_bytes(int64_t n) {
+  if (n <= 0) return 0;
+  size_t s = 0;
+  auto add = [&](size_t b) { s += align_up(b, 256); };
+  for (int k = 0; k < 2; ++k) {
+    add(n * 4);
+    add(n * 16);
+    add(n * 16);
+  }
+  for (int k = 0; k < 7; ++k) add(n * 4);
+  add(64);
+  add(ploc_scan_bytes(n));
+  return s;
+}
+
+PlocWs ploc_carve(void* base, int64_t n) {
+  PlocWs w{};
+  char* p = static_cast<char*>(base);
+  auto take = [&](size_t b) {
+    char* r = p;
+    p += align_up(b, 256);
+    return r;
+  };
+  for (int k = 0; k < 2; ++k) {
+    w.ref[k] = (int32_t*)take(n * 4);
+    w.lo[k] = (float4*)take(n * 16);
+    w.hi[k] = (float4*)take(n * 16);
+  }
+  w.nn = (int32_t*)take(n * 4);
+  w.valid = (int32_t*)take(n * 4);
+  w.pos = (int32_t*)take(n * 4);
+  w.cnt = (int32_t*)take(n * 4);
+  w.leafpos = (int32_t*)take(n * 4);
+  w.order2 = (uint32_t*)take(n * 4);
+  w.lp2 = (int32_t*)take(n * 4);
+  w.counters = (int32_t*)take(64);
+  w.scan_bytes = ploc_scan_bytes(n);
+  w.scan_tmp = take(w.scan_bytes);
+  return w;
+}
+
+__device__ __forceinline__ float union_area(float4 alo, float4 ahi, float4 blo, float4 bhi) {
+  const float x = fmaxf(ahi.x, bhi.x) - fminf(alo.x, blo.x);
+  const float y = fmaxf(ahi.y, bhi.y) - fminf(alo.y, blo.y);
+  const float z = fmaxf(ahi.z, bhi.z) - fminf(alo.z, blo.z);
+  return x * y + y * z + z * x;
+}
+
+__global__ void k_ploc_init(const uint32_t* order, const float4* plo, const float4* phi, int64_t n,
+                            int32_t* ref, float4* lo, float4* hi, int32_t* counters) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i == 0) {
+    counters[0] = static_cast<int32_t>(n - 2);
+    counters[1] = static_cast<int32_t>(n);
+  }
+  if (i >= n) return;
+  const uint32_t p = order[i];
+  ref[i] = ~static_cast<int32_t>(i);
+  lo[i] = plo[p];
+  hi[i] = phi[p];
+}
+
+// Nearest neighbour of every cluster within the radius (least union area;
+// ties to the lower index, so that the relation is symmetric).
+__global__ void k_ploc_nn(int m, const float4* lo, const float4* hi, int32_t* nn) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const float4 a = lo[i], b = hi[i];
+  float best = INFINITY;
+  int bj = -1;
+  const int j0 = max(0, i - kPlocRadius), j1 = min(m - 1, i + kPlocRadius);
+  for (int j = j0; j <= j1; ++j) {
+    if (j == i) continue;
+    const float sa = union_area(a, b, lo[j], hi[j]);
+    if (sa < best) {
+      best = sa;
+      bj = j;
+    }
+  }
+  nn[i] = bj;
+}
+
+// Mutual nearest neighbours (i < j) merge into a new inner node written at
+// cluster i; cluster j drops out.  Every other cluster is kept as it is.
+__global__ void k_ploc_merge(int m, const int32_t* nn, const int32_t* ref, const float4* lo, const float4* hi,
+                             int32_t* ref_out, float4* lo_out, float4* hi_out, int32_t* valid, BuildWs w,
+                             int32_t* counters) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  const int j = nn[i];
+  const bool mutual = j >= 0 && nn[j] == i;
+  if (mutual && j < i) {
+    valid[i] = 0;
+    return;
+  }
+  valid[i] = 1;
+  if (!mutual) {
+    ref_out[i] = ref[i];
+    lo_out[i] = lo[i];
+    hi_out[i] = hi[i];
+    return;
+  }
+  const int32_t id = atomicSub(&counters[0], 1);
+  const int32_t a = ref[i], b = ref[j];
+  w.left[id] = a;
+  w.right[id] = b;
+  if (a >= 0) w.parent[a] = id;
+  else w.leaf_parent[~a] = id;
+  if (b >= 0) w.parent[b] = id;
+  else w.leaf_parent[~b] = id;
+  const float4 la = lo[i], ha = hi[i], lb = lo[j], hb = hi[j];
+  ref_out[i] = id;
+  lo_out[i] = make_float4(fminf(la.x, lb.x), fminf(la.y, lb.y), fminf(la.z, lb.z), 0.f);
+  hi_out[i] = make_float4(fmaxf(ha.x, hb.x), fmaxf(ha.y, hb.y), fmaxf(ha.z, hb.z), 0.f);
+}
+
+__global__ void k_ploc_compact(int m, const int32_t* valid, const int32_t* pos, const int32_t* ref_in,
+                               const float4* lo_in, const float4* hi_in, int32_t* ref, float4* lo, float4* hi,
+                               int32_t* counters) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m) return;
+  if (i == m - 1) counters[1] = pos[i] + valid[i];
+  if (!valid[i]) return;
+  const int k = pos[i];
+  ref[k] = ref_in[i];
+  lo[k] = lo_in[i];
+  hi[k] = hi_in[i];
+}
+
+// Leaves under every inner node (bottom-up; the second child to arrive
+// processes the parent).
+__global__ void k_ploc_counts(BuildWs w, int32_t* cnt, int64_t n) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int32_t node = w.leaf_parent[k];
+  for (int guard = 0; node >= 0 && guard < kMaxWalk; ++guard) {
+    __threadfence();
+    if (atomicAdd(&w.flags[node], 1) == 0) return;
+    __threadfence();
+    const int32_t a = w.left[node], b = w.right[node];
+    cnt[node] = (a < 0 ? 1 : __ldcg(&cnt[a])) + (b < 0 ? 1 : __ldcg(&cnt[b]));
+    node = w.parent[node];
+  }
+}
+
+// Position of every leaf in the tree's left-to-right order: the leaves of
+// the left siblings along its path to the root come before it.
+__global__ void k_ploc_leafpos(BuildWs w, const int32_t* cnt, const uint32_t* order, int64_t n,
+                               int32_t* leafpos, uint32_t* order2, int32_t* lp2) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int32_t child = ~static_cast<int32_t>(k), a = w.leaf_parent[k];
+  int32_t pos = 0;
+  for (int guard = 0; a >= 0 && guard < kMaxWalk; ++guard) {
+    if (w.right[a] == child) {
+      const int32_t l = w.left[a];
+      pos += l < 0 ? 1 : cnt[l];
+    }
+    child = a;
+    a = w.parent[a];
+  }
+  leafpos[k] = pos;
+  order2[pos] = order[k];
+  lp2[pos] = w.leaf_parent[k];
+}
+
+__global__ void k_ploc_relabel(BuildWs w, const int32_t* leafpos, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n - 1) return;
+  const int32_t a = w.left[i], b = w.right[i];
+  if (a < 0) w.left[i] = ~leafpos[~a];
+  if (b < 0) w.right[i] = ~leafpos[~b];
+}
+
+// Leaf range [first, last] of every inner node in the final order.
+__global__ void k_ploc_ranges(BuildWs w, int64_t n) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  int32_t node = w.leaf_parent[k];
+  for (int guard = 0; node >= 0 && guard < kMaxWalk; ++guard) {
+    __threadfence();
+    if (atomicAdd(&w.flags[node], 1) == 0) return;
+    __threadfence();
+    const int32_t a = w.left[node], b = w.right[node];
+    const int32_t fa = a < 0 ? ~a : __ldcg(&w.first[a]), la = a < 0 ? ~a : __ldcg(&w.last[a]);
+    const int32_t fb = b < 0 ? ~b : __ldcg(&w.first[b]), lb = b < 0 ? ~b : __ldcg(&w.last[b]);
+    w.first[node] = min(fa, fb);
+    w.last[node] = max(la, lb);
+    node = w.parent[node];
+  }
+}
+
+__global__ void k_set_root_parent(int32_t* parent) { parent[0] = -1; }
+
+// The PLOC tree over the Morton-ordered primitives, in the LBVH's form:
+// w.left/right/parent/first/last, w.leaf_parent and the leaf order *order_out.
+// Synchronises the stream once per clustering round (the build is not timed).
+nif_status ploc_tree(BuildWs w, PlocWs pw, const uint32_t* order, int64_t n, const uint32_t** order_out,
+                     cudaStream_t st) {
+  const int T = 256;
+  k_ploc_init<<<ceil_div(n, T), T, 0, st>>>(order, w.prim_lo, w.prim_hi, n, pw.ref[0], pw.lo[0], pw.hi[0],
+                                           pw.counters);
+  k_set_root_parent<<<1, 1, 0, st>>>(w.parent);
+  NIF_LAUNCH_CHECK();
+  int m = static_cast<int>(n);
+  for (int round = 0; m > 1; ++round) {
+    if (round > 4096) return fail(NIF_ERR_TIMEOUT, "bvh_build_ploc: clustering did not converge");
+    const int b = static_cast<int>(ceil_div(m, T));
+    k_ploc_nn<<<b, T, 0, st>>>(m, pw.lo[0], pw.hi[0], pw.nn);
+    k_ploc_merge<<<b, T, 0, st>>>(m, pw.nn, pw.ref[0], pw.lo[0], pw.hi[0], pw.ref[1], pw.lo[1], pw.hi[1], pw.valid,
+                                  w, pw.counters);
+    size_t sb = pw.scan_bytes;
+    NIF_CUDA_TRY(cub::DeviceScan::ExclusiveSum(pw.scan_tmp, sb, pw.valid, pw.pos, m, st));
+    k_ploc_compact<<<b, T, 0, st>>>(m, pw.valid, pw.pos, pw.ref[1], pw.lo[1], pw.hi[1], pw.ref[0], pw.lo[0],
+                                    pw.hi[0], pw.counters);
+    NIF_LAUNCH_CHECK();
+    int32_t left = 0;
+    NIF_CUDA_TRY(cudaMemcpyAsync(&left, pw.counters + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    NIF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (left >= m) return fail(NIF_ERR_NUMERIC, "bvh_build_ploc: a clustering round merged nothing");
+    m = left;
+  }
+  const int64_t blocks = ceil_div(n, T);
+  NIF_CUDA_TRY(cudaMemsetAsync(w.flags, 0, n * 4, st));
+  k_ploc_counts<<<blocks, T, 0, st>>>(w, pw.cnt, n);
+  k_ploc_leafpos<<<blocks, T, 0, st>>>(w, pw.cnt, order, n, pw.leafpos, pw.order2, pw.lp2);
+  k_ploc_relabel<<<ceil_div(n - 1, T), T, 0, st>>>(w, pw.leafpos, n);
+  NIF_LAUNCH_CHECK();
+  NIF_CUDA_TRY(cudaMemcpyAsync(w.leaf_parent, pw.lp2, n * 4, cudaMemcpyDeviceToDevice, st));
+  NIF_CUDA_TRY(cudaMemsetAsync(w.flags, 0, n * 4, st));
+  k_ploc_ranges<<<blocks, T, 0, st>>>(w, n);
+  NIF_LAUNCH_CHECK();
+  *order_out = pw.order2;
+  return NIF_OK;
+}
+
 nif_status build(int kind, const float* verts, const int32_t* tris, const float* boxes,
                  const int32_t* tags, int64_t n, void* out, size_t out_bytes, void* ws,
-                 size_t ws_bytes, cudaStream_t st) {
+                 size_t ws_bytes, cudaStream_t st, bool ploc) {
   if (out_bytes < output_size(n))
     return fail(NIF_ERR_WORKSPACE, "bvh buffer too small: %zu < %zu", out_bytes, output_size(n));
   if (n >= (int64_t(1) << 28)) return fail(NIF_ERR_UNSUPPORTED, "bvh: too many primitives");
@@ -443,7 +718,7 @@ nif_status build(int kind, const float* verts, const int32_t* tris, const float*
     NIF_LAUNCH_CHECK();
     return NIF_OK;
   }
-  size_t need = workspace_size(n);
+  size_t need = workspace_size(n) + (ploc ? ploc_extra_bytes(n) : 0);
   if (ws_bytes < need)
     return fail(NIF_ERR_WORKSPACE, "bvh workspace too small: %zu < %zu", ws_bytes, need);
   BuildWs w = carve(ws, n);
@@ -465,10 +740,17 @@ nif_status build(int kind, const float* verts, const int32_t* tris, const float*
   const uint64_t* sorted_keys = dk.Current();
   const uint32_t* order = dv.Current();
   if (n > 1) {
-    NIF_CUDA_TRY(cudaMemsetAsync(w.flags, 0, n * 4, st));
     NIF_CUDA_TRY(cudaMemsetAsync(w.collapse, 0, n, st));
-    k_karras<<<ceil_div(n - 1, T), T, 0, st>>>(sorted_keys, n, w.left, w.right, w.parent,
-                                               w.leaf_parent, w.first, w.last);
+    if (ploc) {
+      PlocWs pw = ploc_carve(static_cast<char*>(ws) + workspace_size(n), n);
+      nif_status s = ploc_tree(w, pw, order, n, &order, st);
+      if (s != NIF_OK) return s;
+      NIF_CUDA_TRY(cudaMemsetAsync(w.flags, 0, n * 4, st));
+    } else {
+      NIF_CUDA_TRY(cudaMemsetAsync(w.flags, 0, n * 4, st));
+      k_karras<<<ceil_div(n - 1, T), T, 0, st>>>(sorted_keys, n, w.left, w.right, w.parent,
+                                                 w.leaf_parent, w.first, w.last);
+    }
     NIF_LAUNCH_CHECK();
     // box hierarchies (the NIF top level) keep leaves of at most 2 boxes: a
     // failed leaf test costs about as much as a node test there
@@ -487,7 +769,7 @@ nif_status build(int kind, const float* verts, const int32_t* tris, const float*
                                           (float4*)(base + off_prims), (int32_t*)(base + off_ids));
   NIF_LAUNCH_CHECK();
   k_header<<<1, 1, 0, st>>>((Header*)base, kind, n, w.cbounds, w.collapse, tags != nullptr,
-                            off_nodes, off_prims, off_ids);
+                            off_nodes, off_prims, off_ids, n > 1 ? w.node_lo : nullptr);
   NIF_LAUNCH_CHECK();
   return NIF_OK;
 }
@@ -535,10 +817,11 @@ enum Mode { kAny = 0, kClosest = 1, kPairs = 2, kPairsClosest = 3 };
 // Returns true on a hit; for kClosest also the nearest t and prim id.
 // Errors (a stack that would overflow, the visit bound reached) are recorded
 // in the buffer's status word with the index `who` of the ray or query.
-template <int kMode>
+// kCount: also count the nodes visited and the triangles tested into *nv, *nt.
+template <int kMode, bool kCount = false>
 __device__ __forceinline__ bool traverse(const char* bvh, const Header& H, const RayF& r,
                                          int32_t want_tag, float& best_t, int32_t& best_id,
-                                         int64_t who) {
+                                         int64_t who, uint32_t* nv = nullptr, uint32_t* nt = nullptr) {
   DevError* status = &reinterpret_cast<Header*>(const_cast<char*>(bvh))->status;
   const Node* nodes = reinterpret_cast<const Node*>(bvh + H.off_nodes);
   const float4* prims = reinterpret_cast<const float4*>(bvh + H.off_prims);
@@ -552,6 +835,7 @@ __device__ __forceinline__ bool traverse(const char* bvh, const Header& H, const
   if (ref == kEmptyRoot) return false;
   for (int guard = 0; guard < kMaxVisits; ++guard) {
     if (ref >= 0) {
+      if constexpr (kCount) ++*nv;
       const float4* np = reinterpret_cast<const float4*>(nodes + ref);
       float4 a = __ldg(np), b = __ldg(np + 1), c = __ldg(np + 2);
       int4 d = __ldg(reinterpret_cast<const int4*>(np + 3));
@@ -583,6 +867,7 @@ __device__ __forceinline__ bool traverse(const char* bvh, const Header& H, const
         constexpr bool kTagged = kMode == kPairs || kMode == kPairsClosest;
         constexpr bool kNearest = kMode == kClosest || kMode == kPairsClosest;
         if (kTagged && __float_as_int(p2.z) != want_tag) continue;
+        if constexpr (kCount) ++*nt;
         float t;
         if (mt(r, p0, p1, p2, tmax, t)) {
           hit = true;
@@ -602,6 +887,32 @@ __device__ __forceinline__ bool traverse(const char* bvh, const Header& H, const
   }
   raise_error(status, NIF_ERR_TIMEOUT, who);
   return hit;
+}
+
+// The any-hit cast counting its work: sums of nodes visited and triangles
+// tested over all rays into sums[0], sums[1].
+__global__ void __launch_bounds__(128) k_cast_shadow_count(const char* bvh, const nif_ray* rays, int64_t n,
+                                                           unsigned long long* sums) {
+  __shared__ Header H;
+  if (threadIdx.x == 0) H = *reinterpret_cast<const Header*>(bvh);
+  __syncthreads();
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  uint32_t nv = 0, nt = 0;
+  if (i < n) {
+    RayF r = load_ray(rays, i);
+    float t;
+    int32_t id;
+    traverse<kAny, true>(bvh, H, r, 0, t, id, i, &nv, &nt);
+  }
+  unsigned long long a = nv, b = nt;
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&sums[0], a);
+    atomicAdd(&sums[1], b);
+  }
 }
 
 template <bool kOr>
@@ -832,7 +1143,24 @@ nif_status bvh_build(const float* d_verts, int64_t n_verts, const int32_t* d_tri
   NIF_CHECK_ARG((reinterpret_cast<uintptr_t>(d_bvh) & 255) == 0, "bvh_build: output not 256-byte aligned");
   NIF_CHECK_ARG((reinterpret_cast<uintptr_t>(d_ws) & 255) == 0, "bvh_build: workspace not 256-byte aligned");
   return bvh::build(0, d_verts, d_tris, nullptr, d_tri_tag, n_tris, d_bvh, bvh_bytes, d_ws, ws_bytes,
-                    as_stream(stream));
+                    as_stream(stream), false);
+}
+
+size_t bvh_build_ploc_workspace_size(int64_t n_tris) {
+  return n_tris < 0 ? 0 : bvh::workspace_size(n_tris) + bvh::ploc_extra_bytes(n_tris);
+}
+
+nif_status bvh_build_ploc(const float* d_verts, int64_t n_verts, const int32_t* d_tris, int64_t n_tris,
+                          const int32_t* d_tri_tag, void* d_bvh, size_t bvh_bytes, void* d_ws,
+                          size_t ws_bytes, void* stream) {
+  CallRange nvtx_range("bvh_build_ploc");
+  NIF_CHECK_ARG(n_tris >= 0 && n_verts >= 0, "bvh_build_ploc: negative size");
+  NIF_CHECK_ARG(d_bvh != nullptr, "bvh_build_ploc: null output");
+  NIF_CHECK_ARG(n_tris == 0 || (d_verts && d_tris && d_ws), "bvh_build_ploc: null input");
+  NIF_CHECK_ARG((reinterpret_cast<uintptr_t>(d_bvh) & 255) == 0, "bvh_build_ploc: output not 256-byte aligned");
+  NIF_CHECK_ARG((reinterpret_cast<uintptr_t>(d_ws) & 255) == 0, "bvh_build_ploc: workspace not 256-byte aligned");
+  return bvh::build(0, d_verts, d_tris, nullptr, d_tri_tag, n_tris, d_bvh, bvh_bytes, d_ws, ws_bytes,
+                    as_stream(stream), true);
 }
 
 nif_status bvh_build_boxes(const float* d_boxes, int64_t n, void* d_bvh, size_t bvh_bytes, void* d_ws,
@@ -844,7 +1172,7 @@ nif_status bvh_build_boxes(const float* d_boxes, int64_t n, void* d_bvh, size_t 
   NIF_CHECK_ARG((reinterpret_cast<uintptr_t>(d_bvh) & 255) == 0, "bvh_build_boxes: output not 256-byte aligned");
   NIF_CHECK_ARG((reinterpret_cast<uintptr_t>(d_ws) & 255) == 0, "bvh_build_boxes: workspace not 256-byte aligned");
   return bvh::build(1, nullptr, nullptr, d_boxes, nullptr, n, d_bvh, bvh_bytes, d_ws, ws_bytes,
-                    as_stream(stream));
+                    as_stream(stream), false);
 }
 
 nif_status bvh_info(const void* d_bvh, int64_t* n_nodes, int64_t* n_prims, int32_t* depth,
@@ -858,6 +1186,30 @@ nif_status bvh_info(const void* d_bvh, int64_t* n_nodes, int64_t* n_prims, int32
   if (n_prims) *n_prims = h.n_prims;
   if (depth) *depth = h.depth;
   if (h.depth > bvh::kStack) return fail(NIF_ERR_UNSUPPORTED, "bvh depth %d exceeds stack", h.depth);
+  return NIF_OK;
+}
+
+nif_status bvh_stats(const void* d_bvh, const nif_ray* d_rays, int64_t n, double* sah_cost,
+                     double* nodes_per_ray, double* tris_per_ray, void* d_sums, void* stream) {
+  CallRange nvtx_range("bvh_stats");
+  NIF_CHECK_ARG(d_bvh != nullptr && n >= 0, "bvh_stats: bad argument");
+  NIF_CHECK_ARG(n == 0 || (d_rays && d_sums), "bvh_stats: null rays or sums");
+  cudaStream_t st = as_stream(stream);
+  bvh::Header h;
+  NIF_CUDA_TRY(cudaMemcpyAsync(&h, d_bvh, sizeof(h), cudaMemcpyDeviceToHost, st));
+  unsigned long long sums[2] = {0ull, 0ull};
+  if (n > 0) {
+    NIF_CUDA_TRY(cudaMemsetAsync(d_sums, 0, 2 * sizeof(unsigned long long), st));
+    bvh::k_cast_shadow_count<<<ceil_div(n, 128), 128, 0, st>>>(static_cast<const char*>(d_bvh), d_rays, n,
+                                                                static_cast<unsigned long long*>(d_sums));
+    NIF_LAUNCH_CHECK();
+    NIF_CUDA_TRY(cudaMemcpyAsync(sums, d_sums, sizeof(sums), cudaMemcpyDeviceToHost, st));
+  }
+  NIF_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h.magic != bvh::kMagic) return fail(NIF_ERR_ARG, "bvh_stats: not a bvh buffer");
+  if (sah_cost) *sah_cost = h.sah_cost;
+  if (nodes_per_ray) *nodes_per_ray = n ? static_cast<double>(sums[0]) / n : 0.0;
+  if (tris_per_ray) *tris_per_ray = n ? static_cast<double>(sums[1]) / n : 0.0;
   return NIF_OK;
 }
 

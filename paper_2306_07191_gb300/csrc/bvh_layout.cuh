@@ -40,7 +40,8 @@ struct Header {
   // query index) when a traversal hits the node-visit bound.  Read by
   // bvh_check.
   DevError status;
-  int32_t pad[38];
+  float sah_cost;  // surface-area cost of the tree (1.2 per step, 1 per triangle)
+  int32_t pad[37];
 };
 static_assert(sizeof(Header) == 256, "header size");
 

@@ -81,10 +81,15 @@ class BVH:
     """Exact shadow-ray visibility over a triangle soup (or object boxes)."""
 
     def __init__(self, verts: torch.Tensor, tris: torch.Tensor, tags: torch.Tensor | None = None,
-                 boxes: bool = False, stream=None):
+                 boxes: bool = False, stream=None, builder: str = "lbvh"):
+        """builder: "lbvh" (bvh_build, Morton-code splits) or "ploc"
+        (bvh_build_ploc, locally-ordered clustering: a lower surface-area
+        cost)."""
         self.n = int(tris.shape[0])
+        self.builder = builder
         nb = L.lib.bvh_build_size(self.n)
-        nw = L.lib.bvh_build_workspace_size(self.n)
+        nw = (L.lib.bvh_build_ploc_workspace_size(self.n) if builder == "ploc"
+              else L.lib.bvh_build_workspace_size(self.n))
         dev = verts.device
         self.buf = torch.empty(nb, dtype=torch.uint8, device=dev)
         ws = torch.empty(max(nw, 256), dtype=torch.uint8, device=dev)
@@ -93,12 +98,22 @@ class BVH:
                    _stream(stream))
         else:
             self._inputs = (verts, tris, tags)
-            L.call("bvh_build", _ptr(verts), int(verts.shape[0]), _ptr(tris), self.n, _ptr(tags),
-                   _ptr(self.buf), nb, _ptr(ws), ws.numel(), _stream(stream))
+            L.call("bvh_build_ploc" if builder == "ploc" else "bvh_build", _ptr(verts), int(verts.shape[0]),
+                   _ptr(tris), self.n, _ptr(tags), _ptr(self.buf), nb, _ptr(ws), ws.numel(), _stream(stream))
         torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
         del ws
         self._inputs = None
         self.check(stream)
+
+    def stats(self, rays: torch.Tensor | None = None, stream=None):
+        """bvh_stats: the tree's surface-area cost and, over `rays` cast
+        any-hit, the mean nodes visited and triangles tested per ray."""
+        n = int(rays.shape[0]) if rays is not None else 0
+        sums = torch.zeros(2, dtype=torch.int64, device=self.buf.device)
+        sah, nv, nt = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        L.call("bvh_stats", _ptr(self.buf), _ptr(rays) if n else None, n, ctypes.byref(sah), ctypes.byref(nv),
+               ctypes.byref(nt), _ptr(sums), _stream(stream))
+        return {"sah_cost": sah.value, "nodes_per_ray": nv.value, "tris_per_ray": nt.value}
 
     def check(self, stream=None):
         """Raise NifError if the build or any traversal through this buffer

@@ -162,3 +162,59 @@ def test_degenerate_triangle_sets_build_shallow_exact_trees():
         assert np.array_equal(occ.astype(np.uint8), occ_ref)
         assert np.array_equal(tt.view(np.uint32), t_ref.view(np.uint32))
         assert np.array_equal(pp, p_ref)
+
+
+@pytest.mark.parametrize("case", ["tiny", "spun", "tags"])
+def test_ploc_tree_casts_equal_brute_force(case):
+    """bvh_build_ploc (locally-ordered clustering, Meister & Bittner 2018):
+    any-hit, closest-hit and per-pair casts through its tree equal brute
+    force bit for bit, like the LBVH's; its surface-area cost is below the
+    LBVH's, and bvh_stats reports the work per ray of both."""
+    rng = np.random.default_rng(21)
+    tags = None
+    if case == "tiny":
+        w = workloads.tiny_object()
+        v, t = w.verts, w.tris
+        rays = np.concatenate([w.rays[:20000], synth.aimed_rays(rng, 12000, w.aabb[0], 1.5)])
+    elif case == "spun":
+        base = np.array([[1.0, 0.0, 0.0], [-0.5, 0.8660254, 0.0], [-0.5, -0.8660254, 0.0]])
+        tri3 = []
+        for a, th in zip(synth.unit_vectors(rng, 3000), rng.uniform(0, 2 * np.pi, 3000)):
+            K = np.array([[0, -a[2], a[1]], [a[2], 0, -a[0]], [-a[1], a[0], 0]])
+            tri3.append(base @ (np.eye(3) + np.sin(th) * K + (1 - np.cos(th)) * K @ K).T)
+        v = np.concatenate(tri3).astype(np.float32)
+        t = np.arange(len(v), dtype=np.int32).reshape(-1, 3)
+        rays = synth.shell_rays(rng, 4097, radius=2.0)
+    else:
+        sc = workloads.room_scene(6, 10, 64, 48, seed=3).scene
+        v, t, tags = sc.verts, sc.tris, sc.tri_obj
+        rays = synth.shell_rays(rng, 6000, radius=12.0)
+        rays[:, 0:3] *= 0.5
+    occ_ref, t_ref, p_ref = oracle.brute_cast(v, t, rays)
+    vt, tt = _cuda(v), _cuda(t)
+    ploc = nif.BVH(vt, tt, _cuda(tags) if tags is not None else None, builder="ploc")
+    lbvh = nif.BVH(vt, tt, _cuda(tags) if tags is not None else None)
+    r = _cuda(rays)
+    bits = ploc.cast_shadow(r)
+    th, pr = ploc.cast_closest(r)
+    torch.cuda.synchronize()
+    ploc.check()
+    assert np.array_equal(nif.bits_to_bool(bits, len(rays)).cpu().numpy().astype(np.uint8), occ_ref)
+    assert np.array_equal(th.cpu().numpy().view(np.uint32), t_ref.view(np.uint32))
+    assert np.array_equal(pr.cpu().numpy(), p_ref)
+    assert 0 < ploc.info()["depth"] <= 96 and ploc.info()["prims"] == len(t)
+    if tags is not None:
+        # per-pair labels through the clustered tree
+        obj = rng.integers(0, 6, size=len(rays)).astype(np.int32)
+        hit = ploc.cast_pairs(r, torch.arange(len(rays), dtype=torch.int32, device="cuda"), _cuda(obj))
+        first = np.array([np.nonzero(tags == k)[0][0] for k in range(6)])
+        count = np.array([np.count_nonzero(tags == k) for k in range(6)])
+        ref = oracle.brute_pairs(v, t, first, count, rays, np.arange(len(rays)), obj)
+        assert np.array_equal(hit.cpu().numpy(), ref)
+    sp, sl = ploc.stats(r), lbvh.stats(r)
+    print(f"\n{case}: SAH cost PLOC {sp['sah_cost']:.2f} LBVH {sl['sah_cost']:.2f}; nodes/ray "
+          f"{sp['nodes_per_ray']:.1f} vs {sl['nodes_per_ray']:.1f}; triangles/ray {sp['tris_per_ray']:.1f} vs "
+          f"{sl['tris_per_ray']:.1f}")
+    assert sp["nodes_per_ray"] > 0 and sp["sah_cost"] > 0
+    if case == "tiny":
+        assert sp["sah_cost"] < sl["sah_cost"]

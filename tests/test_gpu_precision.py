@@ -20,16 +20,16 @@ from oracle import nif as onif  # noqa: E402
 from paper_2306_07191_gb300 import _lib as L  # noqa: E402
 from paper_2306_07191_gb300 import pipeline, synth  # noqa: E402
 
-# |z_gpu - z_fp64| <= bar * max(1, |z_fp64|): the unit-scale logit bars of the
-# operand types, scaled by the logit's magnitude for the trained network.
-# The trained logits reach |z| ~ 160, and FP32 accumulation over the input
-# and three 64-wide layers then rounds to about 1e-4 relative (measured
-# 1.05e-4): the FP32 bar is 1e-3 relative here, against 1e-4 absolute on the
-# unit-scale untrained networks of the parity tests.
+# |z_gpu - z_fp64| <= bar * max(1, S), S = sum_j |w_out_j h_j| the magnitude
+# of the output layer's terms: the unit-scale logit bars of the operand types
+# (FP32 1e-4, BF16 6e-2, FP16 2e-2), scaled by the size of the computation
+# whose rounding they bound.  The trained network's terms reach S ~ 10^2 and
+# its logits can cancel well below S, so scaling by |z| would not bound the
+# rounding of the terms.
 # FP8-E4M3 (3 mantissa bits) has a target, not a gate: its 0.25 is
 # reported, and its gate is the visibility decision, which must agree with
 # the FP64 decision on at least 99% of the pairs.
-BARS = {"f32": 1e-3, "bf16": 6e-2, "f16": 2e-2, "e4m3": 0.25}
+BARS = {"f32": 1e-4, "bf16": 6e-2, "f16": 2e-2, "e4m3": 0.25}
 
 
 def test_trained_logits_per_precision_vs_fp64():
@@ -59,12 +59,21 @@ def test_trained_logits_per_precision_vs_fp64():
     om = onif.Model(res=list(cfg.res), F=cfg.n_features, log2_table=cfg.log2_table, obj_aabb=ws.scene.obj_aabb,
                     grids=g32.reshape(1, 2, -1), nets=nets, net_mode="class")
     zo = onif.forward(om, ors, r, ob, inn)
+    # S per pair: the FP64 output layer's sum of absolute terms
+    x = onif.encode(om, ors, r, ob)
+    net = om.net_of(ob, inn)
+    S = np.zeros(nq)
+    for g in (0, 1):
+        sel = net == g
+        if sel.any():
+            _, _, post = onif.mlp_forward(x[sel], om.nets[g], om.act, om.slope)
+            S[sel] = np.abs(post[-1]) @ np.abs(np.asarray(om.nets[g][-1], np.float64)[0])
     assert np.abs(zo).max() > 1.0 and (zo < 0).any() and (zo > 0).any()
     ray_id = torch.from_numpy(gids[r].astype(np.int32)).cuda()
     qobj = torch.from_numpy((ob.astype(np.uint32) | (inn.astype(np.uint32) << 31)).view(np.int32)).cuda()
     goff = torch.tensor([0, int((~inn).sum()), nq], dtype=torch.int64, device="cuda")
     model = p.model
-    scale = np.maximum(1.0, np.abs(zo))
+    scale = np.maximum(1.0, S)
     report, sure, zs = {}, {}, {}
     for name, dt, w, sc in (("f32", L.NIF_F32, w32, None), ("bf16", L.NIF_BF16, w32.bfloat16(), None),
                             ("f16", L.NIF_F16, w32.half(), None), ("e4m3", L.NIF_E4M3, q8, sc8)):
@@ -76,8 +85,8 @@ def test_trained_logits_per_precision_vs_fp64():
                         float(np.mean((z < 0) != (zo < 0))))
         sure[name] = np.abs(zo) > BARS[name] * scale
         zs[name] = z
-    print("\nlogit error vs FP64 (max abs, mean abs, max relative to max(1,|z|), decisions differing); "
-          f"{nq} pairs, |z| up to {np.abs(zo).max():.2f}:")
+    print("\nlogit error vs FP64 (max abs, mean abs, max relative to max(1, S), decisions differing); "
+          f"{nq} pairs, |z| up to {np.abs(zo).max():.2f}, S up to {S.max():.1f}:")
     for name, (mx, mean, rel, dis) in report.items():
         print(f"  {name}: {mx:.3e} {mean:.3e} {rel:.3e} {dis:.2e}")
     for name in report:
