@@ -5,7 +5,9 @@ triangles (30.1M) on a jittered lattice in a 12-triangle room, 1920x1080
 pixel-centre primary hits, a 4 x 4 ceiling area light sampled 4 times per
 pixel -> 8,294,400 shadow rays; dense 8-level x 2-feature FP16 grids (R 4..64)
 per object, shared outer/inner 3x64 networks in FP16 on the tensor cores,
-trained online on 64 shadow samples per pixel before timing.  --workload room
+trained online on 64 shadow samples per pixel before timing (FP16 forward and
+backward on the tensor cores with FP32 masters and a dynamic loss scale;
+--train-precision f32 trains in FP32 on the CUDA cores).  --workload room
 is the 1.0M-triangle scene with hashed 16-level grids and one point light
 (2,073,600 shadow rays); the other workloads are listed in WORKLOADS.
 
@@ -77,14 +79,6 @@ WORKLOADS = {
 # SM, round-1 rule) of the kernel as it stands; a configuration without an
 # entry reports null.
 FUSED_TRAFFIC_BYTES = {
-    # profiles/fused_tm_room.md: rounds 1 + 2 of one step
-    ("room", "serial", 4, "outer"): 1092881000 + 3713536 + 625983000 + 3601408,
-    # profiles/fused_ws_full.md: rounds 1 + 2 of one step
-    ("full", "pipelined", 0, "nearest"): 492514560 + 6791168 + 260741888 + 2782464,
-    # profiles/fused_tm_paper_mixed_dram.md: outer and inner networks, rounds 1 + 2
-    ("paper", "serial", 4, "outer"): 31652352 + 29184 + 10637568 + 5376 + 7505152 + 5888 + 8780544 + 4608,
-    # profiles/fused_tm_paper_mixed_dram.md: rounds 1 + 2 of one step
-    ("mixed", "serial", 4, "outer"): 249415424 + 3222528 + 55454976 + 3072,
 }
 
 
@@ -1112,7 +1106,7 @@ def main():
     ap.add_argument("--workload", default="full", choices=sorted(WORKLOADS))
     ap.add_argument("--primary-two-rounds", action="store_true",
                     help="primary workload: nearest pair first, then only pairs entered before the nearest hit")
-    ap.add_argument("--train-precision", choices=("f32", "f16"), default="f32",
+    ap.add_argument("--train-precision", choices=("f32", "f16"), default="f16",
                     help="online training: FP32 on the CUDA cores, or FP16 operands on the tensor cores with a "
                          "dynamic loss scale")
     ap.add_argument("--no-graph", action="store_true",
