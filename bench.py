@@ -814,7 +814,13 @@ def run_grouped(args):
     nif_ms = time_fn(g.replay, args.steps, args.warmup)
     model.check(ws)
     bvh_bits = nif.empty_bits(n, dev)
-    bvh_ms = time_fn(lambda: bvh.cast_shadow(rays, out=bvh_bits), args.steps, args.warmup)
+    # the comparison: the faster of the LBVH and PLOC casts of the same rays
+    trees = {"lbvh": bvh, "ploc": nif.BVH(verts, tris, builder="ploc")}
+    tree_ms = {name: time_fn(lambda t=t: t.cast_shadow(rays, out=bvh_bits), args.steps, args.warmup)
+               for name, t in trees.items()}
+    best_tree = min(tree_ms, key=tree_ms.get)
+    bvh_ms = tree_ms[best_tree]
+    tree_stats = {name: {**t.stats(rays), "ms_per_step": tree_ms[name]} for name, t in trees.items()}
     alg_bytes, flops_q = 3 * 8 * 8 * 2 * 2, 2 * (48 * 64 + 2 * 64 * 64 + 64)
     hbm, tflops, src = _peaks()
     line = {"metric": METRIC, "value": n / (nif_ms * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -826,6 +832,7 @@ def run_grouped(args):
                        "fused_tile_m": model.cfg.tile_m or 128,
                        "autotune_ms": sweep, "cuda_graph": True},
             "bvh_rays_per_s": n / (bvh_ms * 1e-3), "bvh_ms_per_step": bvh_ms, "speedup_vs_bvh": bvh_ms / nif_ms,
+            "bvh_compared": best_tree, "bvh_trees": tree_stats,
             "roofline": {"kernel": "nif fused encode+MLP (tcgen05), grouped", "bound": "hbm",
                          "achieved": n * alg_bytes / (nif_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
                          "frac": n * alg_bytes / (nif_ms * 1e-3) / 1e9 / hbm, "traffic": None,

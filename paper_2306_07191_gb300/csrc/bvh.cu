@@ -28,6 +28,13 @@ namespace nif {
 namespace bvh {
 
 constexpr int kLeafMax = 8;
+// Leaf size bound of box hierarchies (the NIF top level): a failed leaf test
+// costs about as much as a node test there.
+#ifndef NIF_TLAS_LEAF_MAX
+#define NIF_TLAS_LEAF_MAX 2
+#endif
+constexpr int kBoxLeafMax = NIF_TLAS_LEAF_MAX;
+static_assert(kBoxLeafMax >= 1 && kBoxLeafMax <= 8, "leaf size");
 constexpr int kMaxWalk = 4096;  // bound on parent walks (a valid tree is far shallower)
 constexpr float kCostTraverse = 1.2f;
 constexpr float kCostIntersect = 1.0f;
@@ -752,9 +759,9 @@ nif_status build(int kind, const float* verts, const int32_t* tris, const float*
                                                  w.leaf_parent, w.first, w.last);
     }
     NIF_LAUNCH_CHECK();
-    // box hierarchies (the NIF top level) keep leaves of at most 2 boxes: a
-    // failed leaf test costs about as much as a node test there
-    k_bottom_up<<<blocks, T, 0, st>>>(w, order, n, kind == 0 ? kLeafMax : 2);
+    // box hierarchies (the NIF top level) keep leaves of at most
+    // kBoxLeafMax boxes
+    k_bottom_up<<<blocks, T, 0, st>>>(w, order, n, kind == 0 ? kLeafMax : kBoxLeafMax);
     NIF_LAUNCH_CHECK();
     k_emit_nodes<<<ceil_div(n - 1, T), T, 0, st>>>(w, order, n, (Node*)(base + off_nodes));
     NIF_LAUNCH_CHECK();

@@ -138,8 +138,19 @@ __device__ __forceinline__ void tmem_ld_wait16(uint32_t r[16]) {
 
 // Stores of 32-bit words into this warp's TMEM lane quarter (one lane per
 // thread, consecutive columns from taddr), and the wait for their completion.
+// tmem_st1 carries no memory clobber: it writes tensor memory only, so the
+// compiler may issue the global loads of a following lookup before it (its
+// order against the other tcgen05 instructions, all volatile, is kept).
+// Building with -DNIF_TMEM_ST_CLOBBER=1 restores the clobber.
+#ifndef NIF_TMEM_ST_CLOBBER
+#define NIF_TMEM_ST_CLOBBER 0
+#endif
 __device__ __forceinline__ void tmem_st1(uint32_t taddr, uint32_t v) {
+#if NIF_TMEM_ST_CLOBBER
   asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(v) : "memory");
+#else
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(v));
+#endif
 }
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t v[8]) {
   asm volatile(
