@@ -7,9 +7,12 @@
 // k_mlp_pipe is persistent and warp-specialised, with two tiles of 128 rows
 // in flight per CTA (slots 0 and 1), so that one tile's MMAs run while the
 // other tile's epilogue runs:
-//   warps 0, 1, 3 load a tile's inputs into the slot's shared-memory A tile
-//               (16-byte copies, eight in flight per thread, into the
-//               K-major core-matrix layout);
+//   warp 0      one thread copies a tile's inputs into the slot's shared-
+//               memory A tile with one TMA load (a 3D view of the [nq][K]
+//               inputs: 8 inputs, 128 rows, K/8 column blocks), which lands
+//               in a K-major core-matrix layout: column block kb of 8-row
+//               group j at kb * 2048 + j * 128 bytes; rows past nq and
+//               column blocks past K/8 are filled with zeros by the copy;
 //   warp 2      one thread issues the MMAs: per layer, slot 0 then slot 1
 //               (layer 1 reads A from shared memory, later layers from TMEM);
 //   warps 4-7   epilogue of slot 0, warps 8-11 epilogue of slot 1: each
@@ -27,14 +30,15 @@
 namespace nif {
 namespace tc {
 
-constexpr int kPipeWarps = 12;
+constexpr int kPipeWarps = 12;  // warps 1 and 3 have no role (epilogue warps need warp % 4 = lane quarter)
 constexpr int kPipeThreads = 32 * kPipeWarps;
-constexpr int kPipeLoaders = 96;  // threads of warps 0, 1 and 3
-constexpr int kPipeBatch = 8;     // 16-byte loads in flight per loader thread
 constexpr int kPipeMaxNets = 2;
+// A tile: byte stride between K-adjacent core matrices (one 16-byte column
+// block of all 128 rows) and between M-adjacent ones (8 rows of 16 bytes)
+constexpr uint32_t kXLbo = 128 * 16, kXSbo = 128;
 
 struct PipeLayout {
-  uint32_t x_off[2];   // A tiles of the two slots: [128][Kp] K-major
+  uint32_t x_off[2];   // A tiles of the two slots: [Kp/8][128][8] (core matrices, see kXLbo)
   uint32_t w_off;      // per network: W_1 [W][Kp] | W_2 .. W_H [W][W], K-major
   uint32_t net_bytes;  // bytes of one network's hidden layers
   uint32_t wout_off;   // FP32 [n_nets][W]
@@ -57,11 +61,12 @@ __host__ __device__ inline PipeLayout pipe_layout(int Kp, int W, int H, int n_ne
   return L;
 }
 
-// x: [nq][K] inputs in the operand type; goff: [n_nets + 1] group offsets
+// xmap: the [nq][K] inputs in the operand type as a 3D TMA tensor (see
+// launch_mlp_pipe); goff: [n_nets + 1] group offsets
 // (group g's rows run through network g); logits: [nq].
 template <int DT>
 __global__ void __launch_bounds__(kPipeThreads, 2)
-    k_mlp_pipe(const __grid_constant__ NifParams p, const uint16_t* __restrict__ x,
+    k_mlp_pipe(const __grid_constant__ NifParams p, const __grid_constant__ CUtensorMap xmap,
                const int64_t* __restrict__ goff, float* __restrict__ logits, int Kp, DevError* err) {
   using O = Op<DT>;
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -77,7 +82,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
   if (warp == 0) tmem_alloc(smem_u32(&s_tmem), 256);
   if (tid == 0) {
     for (int s = 0; s < 2; ++s) {
-      mbar_init(smem_u32(&s_xfull[s]), kPipeLoaders);
+      mbar_init(smem_u32(&s_xfull[s]), 1);
       mbar_init(smem_u32(&s_xempty[s]), 1);
       mbar_init(smem_u32(&s_accfull[s]), 1);
       mbar_init(smem_u32(&s_actready[s]), 4);
@@ -86,7 +91,10 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
     fence_mbar_init();
     s_abort = 0;
   }
-  // weights of every network into shared memory (B operands, K-major)
+  // weights of every network into shared memory (B operands, K-major): a
+  // 16-byte chunk is 8 consecutive inputs of one output row, which is one
+  // core-matrix row, so rows are copied chunk by chunk (K is a multiple of
+  // 8; chunks past K are zero)
   for (int g = 0; g < p.n_nets; ++g) {
     const int64_t wbase = static_cast<int64_t>(g) * p.P;
     int64_t off = 0;
@@ -94,11 +102,13 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
       const int fin = l == 0 ? K : W, fpad = l == 0 ? Kp : W;
       uint8_t* wt = smem + L.w_off + static_cast<uint32_t>(g) * L.net_bytes +
                     (l == 0 ? 0u : static_cast<uint32_t>(W * Kp * 2 + (l - 1) * W * W * 2));
-      for (int e = tid; e < W * fpad; e += kPipeThreads) {
-        const int n = e / fpad, k = e % fpad;
-        const float v = k < fin ? O::load(p.weights, wbase + off + static_cast<int64_t>(n) * fin + k) : 0.f;
-        typename O::T t = O::cvt(v);
-        *reinterpret_cast<typename O::T*>(wt + tile_off(n, k, fpad, 2)) = t;
+      const uint16_t* src = static_cast<const uint16_t*>(p.weights) + wbase + off;
+      const int cpr = fpad / 8;
+      for (int c = tid; c < W * cpr; c += kPipeThreads) {
+        const int n = c / cpr, kb = c % cpr;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (kb * 8 < fin) v = __ldg(reinterpret_cast<const uint4*>(src + static_cast<int64_t>(n) * fin + kb * 8));
+        *reinterpret_cast<uint4*>(wt + tile_off(n, kb * 8, fpad, 2)) = v;
       }
       off += static_cast<int64_t>(W) * fin;
     }
@@ -113,39 +123,27 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
   auto tile_of = [&](int k) { return static_cast<int64_t>(blockIdx.x) + static_cast<int64_t>(k) * gridDim.x; };
   const uint32_t idesc = instr_desc(kM, W, O::fmt);
 
-  if (warp < 2 || warp == 3) {
-    // ---------------------------------------------------------- loaders
-    const int lt = warp == 3 ? 64 + lane : tid;
-    const int cpr = Kp / 8;  // 16-byte chunks per row
-    for (int k = 0;; ++k) {
-      const int64_t t = tile_of(k);
-      if (t >= n_tiles || *reinterpret_cast<volatile int*>(&s_abort)) break;
-      const int s = k & 1, u = k >> 1;
-      if (u > 0 && !mbar_wait(smem_u32(&s_xempty[s]), (u - 1) & 1, err, kWaitCycles, 11)) {
-        s_abort = 1;
-        break;
-      }
-      const int g = find_group(s_pre, p.n_nets, t);
-      const int64_t q0 = goff[g] + (t - s_pre[g]) * kM, qend = goff[g + 1];
-      uint8_t* xs = smem + L.x_off[s];
-      for (int c0 = lt; c0 < 128 * cpr; c0 += kPipeLoaders * kPipeBatch) {
-        uint4 v[kPipeBatch];
-#pragma unroll
-        for (int i = 0; i < kPipeBatch; ++i) {
-          const int c = c0 + i * kPipeLoaders, r = c / cpr, kb = c % cpr;
-          v[i] = make_uint4(0u, 0u, 0u, 0u);
-          if (c < 128 * cpr && q0 + r < qend && kb * 8 < K)
-            v[i] = __ldg(reinterpret_cast<const uint4*>(x + (q0 + r) * static_cast<int64_t>(K) + kb * 8));
+  if (warp == 0) {
+    // ------------------------------------------------------------ loader
+    if (lane == 0) {
+      const uint32_t tile_bytes = static_cast<uint32_t>(128 * Kp * 2);
+      for (int k = 0;; ++k) {
+        const int64_t t = tile_of(k);
+        if (t >= n_tiles || *reinterpret_cast<volatile int*>(&s_abort)) break;
+        const int s = k & 1, u = k >> 1;
+        if (u > 0 && !mbar_wait(smem_u32(&s_xempty[s]), (u - 1) & 1, err, kWaitCycles, 11)) {
+          s_abort = 1;
+          break;
         }
-#pragma unroll
-        for (int i = 0; i < kPipeBatch; ++i) {
-          const int c = c0 + i * kPipeLoaders, r = c / cpr, kb = c % cpr;
-          if (c < 128 * cpr) *reinterpret_cast<uint4*>(xs + tile_off(r, kb * 8, Kp, 2)) = v[i];
-        }
+        const int g = find_group(s_pre, p.n_nets, t);
+        const int64_t q0 = goff[g] + (t - s_pre[g]) * kM;
+        // rows of the tile past its group's end belong to the next group
+        // (or lie past nq and read as zeros): their outputs are not written
+        mbar_expect_tx(smem_u32(&s_xfull[s]), tile_bytes);
+        tma_load_3d(smem_u32(smem + L.x_off[s]), &xmap, 0, static_cast<int>(q0), 0, smem_u32(&s_xfull[s]));
       }
-      fence_proxy_async();
-      mbar_arrive(smem_u32(&s_xfull[s]));
     }
+    __syncwarp();
   } else if (warp == 2) {
     // -------------------------------------------------------------- MMA
     if (lane == 0) {
@@ -174,8 +172,8 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
               const uint32_t xa = smem_u32(smem + L.x_off[s]);
               const uint32_t sbo = static_cast<uint32_t>(Kp / 8) * 128;
               for (int kk = 0; kk < Kp / 16; ++kk)
-                mma<0>(acc, smem_desc(xa + kk * 256, 128, sbo), smem_desc(wb + kk * 256, 128, sbo), idesc,
-                       kk > 0 ? 1u : 0u);
+                mma<0>(acc, smem_desc(xa + kk * 2 * kXLbo, kXLbo, kXSbo), smem_desc(wb + kk * 256, 128, sbo),
+                       idesc, kk > 0 ? 1u : 0u);
               mma_commit(smem_u32(&s_accfull[s]));
               mma_commit(smem_u32(&s_xempty[s]));
             } else {
@@ -193,6 +191,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
     __syncwarp();
   } else if (warp >= 4) {
     // --------------------------------------------------------- epilogue
+    const bool leaky = p.act == NIF_ACT_LEAKY;
     const int s = (warp - 4) >> 2;  // slot of this group
     const int quarter = warp & 3;
     const int row = 32 * quarter + lane;
@@ -222,22 +221,17 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
           const int c0 = 16 * c;
           float v[16];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const float a = __uint_as_float(raw[c][i]);
-            v[i] = a > 0.f ? a : (p.act == NIF_ACT_LEAKY ? p.slope * a : 0.f);
-          }
+          for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(raw[c][i]);
           if (l + 1 < H) {
             uint32_t pk[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-              typename O::T a = O::cvt(v[2 * i]), b = O::cvt(v[2 * i + 1]);
-              pk[i] = static_cast<uint32_t>(*reinterpret_cast<uint16_t*>(&a)) |
-                      (static_cast<uint32_t>(*reinterpret_cast<uint16_t*>(&b)) << 16);
-            }
+            act_pack16<DT>(v, leaky, p.slope, pk);
             tmem_st8(lane_base + static_cast<uint32_t>(W) + static_cast<uint32_t>(c0 / 2), pk);
           } else {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) z += v[i] * wout[g * W + c0 + i];
+            for (int i = 0; i < 16; ++i) {
+              const float a = v[i];
+              z += (a > 0.f ? a : (leaky ? p.slope * a : 0.f)) * wout[g * W + c0 + i];
+            }
           }
         }
         if (l + 1 < H) {
@@ -275,7 +269,27 @@ nif_status launch_mlp_pipe(const NifParams& p, const void* x, const int64_t* gof
   if (p.width != 64 || p.n_hidden < 1 || p.n_hidden > 8 || p.K % 8 != 0 || p.K > 256 || p.O != 1)
     return fail(NIF_ERR_UNSUPPORTED, "nif_mlp_infer: width 64, 1..8 hidden layers, K a multiple of 8 up "
                                      "to 256, one output");
+  if ((reinterpret_cast<uintptr_t>(p.weights) & 15) != 0 || (p.P * 2) % 16 != 0)
+    return fail(NIF_ERR_UNSUPPORTED, "nif_mlp_infer: weights 16-byte aligned per network");
+  if (nq > INT32_MAX) return fail(NIF_ERR_UNSUPPORTED, "nif_mlp_infer: at most 2^31 - 1 rows per call");
   const int Kp = (p.K + 15) / 16 * 16;
+  // the inputs as a 3D tensor (8 inputs of a column block, row, column
+  // block) whose 8 x 128 x Kp/8 boxes are the A tiles
+  auto enc = tensor_map_encoder();
+  if (!enc) return fail(NIF_ERR_CUDA, "nif_mlp_infer: the driver has no cuTensorMapEncodeTiled");
+  CUtensorMap xmap;
+  {
+    cuuint64_t dims[3] = {8, static_cast<cuuint64_t>(nq), static_cast<cuuint64_t>(p.K / 8)};
+    cuuint64_t strides[2] = {static_cast<cuuint64_t>(p.K) * 2, 16};
+    cuuint32_t box[3] = {8, static_cast<cuuint32_t>(tc::kM), static_cast<cuuint32_t>(Kp / 8)};
+    cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapDataType dt =
+        p.mlp_dtype == NIF_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    if (enc(&xmap, dt, 3, const_cast<void*>(x), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return fail(NIF_ERR_UNSUPPORTED, "nif_mlp_infer: no tensor map for the inputs");
+  }
   tc::PipeLayout L = tc::pipe_layout(Kp, p.width, p.n_hidden, p.n_nets);
   const size_t sh = L.total + 1024;
   if (sh > 220 * 1024) return fail(NIF_ERR_UNSUPPORTED, "nif_mlp_infer: %zu bytes of shared memory", sh);
@@ -285,7 +299,7 @@ nif_status launch_mlp_pipe(const NifParams& p, const void* x, const int64_t* gof
       std::max<int64_t>(1, std::min<int64_t>(sm_count() * per_sm, ceil_div(nq, 2 * tc::kM))));
   auto go = [&](auto kern) -> nif_status {
     NIF_CUDA_TRY(ensure_smem(kern, sh));
-    kern<<<blocks, tc::kPipeThreads, sh, st>>>(p, static_cast<const uint16_t*>(x), goff, logits, Kp, err);
+    kern<<<blocks, tc::kPipeThreads, sh, st>>>(p, xmap, goff, logits, Kp, err);
     return NIF_OK;
   };
   nif_status s = p.mlp_dtype == NIF_F16 ? go(tc::k_mlp_pipe<NIF_F16>) : go(tc::k_mlp_pipe<NIF_BF16>);

@@ -472,11 +472,8 @@ __global__ void __launch_bounds__(kThreads * kRB, kOcc)
   const uint32_t lane_base = tmem + (static_cast<uint32_t>(32 * (warp & 3)) << 16) + static_cast<uint32_t>(blk) * cb;
   const uint32_t act_rel = static_cast<uint32_t>(W);  // activations, relative to lane_base
 
-  auto pack2 = [](float a, float b) {
-    typename O::T x = O::cvt(a), y = O::cvt(b);
-    return static_cast<uint32_t>(*reinterpret_cast<uint16_t*>(&x)) |
-           (static_cast<uint32_t>(*reinterpret_cast<uint16_t*>(&y)) << 16);
-  };
+  auto pack2 = [](float a, float b) { return O::pack2(a, b); };
+  const bool leaky = p.act == NIF_ACT_LEAKY;
 
   if (tid == 0) s_next = first_tile(tile_ctr);
   __syncthreads();
@@ -672,16 +669,11 @@ __global__ void __launch_bounds__(kThreads * kRB, kOcc)
       for (int c0 = 0; c0 < W / 2; c0 += 16) {
         float v[16];
         tmem_ld16(lane_base + static_cast<uint32_t>(ecol0 + c0), v);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const float a = v[i];
-          v[i] = a > 0.f ? a : (p.act == NIF_ACT_LEAKY ? p.slope * a : 0.f);
-        }
+        // h_{l+1} of this row in the operand type: the next layer's A
+        // operand, and what the backward reads when saving
+        uint32_t pk[8];
+        if (kSave || l + 1 < H) act_pack16<DT>(v, leaky, p.slope, pk);
         if constexpr (kSave) {
-          // h_{l+1} of this row in the operand type, as the backward reads it
-          uint32_t pk[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) pk[i] = pack2(v[2 * i], v[2 * i + 1]);
           const int64_t qs = q0 + rq;
           if (qs < qend)
 #pragma unroll
@@ -689,11 +681,12 @@ __global__ void __launch_bounds__(kThreads * kRB, kOcc)
               p.saved16[static_cast<int64_t>(K / 2 + l * (W / 2) + (ecol0 + c0) / 2 + i) * p.ld_saved + qs] = pk[i];
         }
         if (l + 1 < H) {
-          uint32_t pk[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) pk[i] = pack2(v[2 * i], v[2 * i + 1]);
           tmem_st8(lane_base + act_rel + static_cast<uint32_t>((ecol0 + c0) / 2), pk);
-        } else if constexpr (kMulti) {
+          continue;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = act_fn_tc(p, v[i]);
+        if constexpr (kMulti) {
 #pragma unroll
           for (int o = 0; o < kMaxOut; ++o)
             if (o < nout)
@@ -827,11 +820,8 @@ __global__ void __launch_bounds__(32 * (kEW + 4), kOcc)
   const uint32_t lane_base = tmem + (static_cast<uint32_t>(32 * quarter) << 16);
   const int qi = 32 * quarter + lane;  // query row == TMEM lane
 
-  auto pack2 = [](float a, float b) {
-    typename O::T x = O::cvt(a), y = O::cvt(b);
-    return static_cast<uint32_t>(*reinterpret_cast<uint16_t*>(&x)) |
-           (static_cast<uint32_t>(*reinterpret_cast<uint16_t*>(&y)) << 16);
-  };
+  auto pack2 = [](float a, float b) { return O::pack2(a, b); };
+  const bool leaky = p.act == NIF_ACT_LEAKY;
 
   if (warp < kEW) {
     // ================================================= encode warps
@@ -999,8 +989,7 @@ __global__ void __launch_bounds__(32 * (kEW + 4), kOcc)
           tmem_ld16(lane_base + static_cast<uint32_t>(c0), v);
           if (l + 1 < H) {
             uint32_t pk[8];
-#pragma unroll
-            for (int i = 0; i < 8; ++i) pk[i] = pack2(act_fn_tc(p, v[2 * i]), act_fn_tc(p, v[2 * i + 1]));
+            act_pack16<DT>(v, leaky, p.slope, pk);
             tmem_st8(lane_base + abuf + static_cast<uint32_t>(c0 / 2), pk);
           } else {
 #pragma unroll
@@ -1041,7 +1030,7 @@ static bool tc_activations_in_tmem() { return NIF_TC_SMEM_ACTIVATIONS == 0; }
 #endif
 static bool tc_weights_by_tma() { return NIF_TC_WEIGHT_LOOP == 0; }
 
-static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   static std::once_flag once;
   std::call_once(once, [] {

@@ -195,6 +195,15 @@ __device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
 // Tensor maps of the hidden layers' weights (all networks), one per layer:
 // dimensions (k within a 16-byte row, row within 8, 16-byte column block,
 // 8-row group, network), so that one box of a network lands in shared memory
@@ -229,6 +238,10 @@ __device__ __forceinline__ uint32_t tile_off(int row, int k, int kdim, int esz) 
 
 template <int DT>
 struct Op;
+// pack2(a, b): a and b rounded to the operand type, a in the low half of the
+// word (one paired conversion); relu_pack2(a, b): the same of max(a, 0) and
+// max(b, 0), taken after the rounding (rounding to nearest is monotone and
+// keeps 0, so the result is the same bits up to the sign of zero).
 template <>
 struct Op<NIF_F16> {
   using T = __half;
@@ -236,6 +249,14 @@ struct Op<NIF_F16> {
   __device__ static T cvt(float v) { return __float2half_rn(v); }
   __device__ static float load(const void* p, int64_t i) {
     return __half2float(static_cast<const __half*>(p)[i]);
+  }
+  __device__ static uint32_t pack2(float a, float b) {
+    const __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+  __device__ static uint32_t relu_pack2(float a, float b) {
+    const __half2 h = __hmax2(__floats2half2_rn(a, b), __float2half2_rn(0.f));
+    return *reinterpret_cast<const uint32_t*>(&h);
   }
 };
 template <>
@@ -245,6 +266,14 @@ struct Op<NIF_BF16> {
   __device__ static T cvt(float v) { return __float2bfloat16_rn(v); }
   __device__ static float load(const void* p, int64_t i) {
     return __bfloat162float(static_cast<const __nv_bfloat16*>(p)[i]);
+  }
+  __device__ static uint32_t pack2(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+  __device__ static uint32_t relu_pack2(float a, float b) {
+    const __nv_bfloat162 h = __hmax2(__floats2bfloat162_rn(a, b), __float2bfloat162_rn(0.f));
+    return *reinterpret_cast<const uint32_t*>(&h);
   }
 };
 template <>
@@ -256,6 +285,25 @@ struct Op<NIF_E4M3> {
     return static_cast<float>(static_cast<const __nv_fp8_e4m3*>(p)[i]);
   }
 };
+
+// The activation of 16 FP32 accumulators (ReLU, or leaky ReLU with slope
+// `slope`, Sec. 5 "Architecture") packed two per word in the 16-bit operand
+// type: the next layer's A operand.  ReLU works on packed pairs after the
+// rounding; the leaky form is applied in FP32 before it.
+template <int DT>
+__device__ __forceinline__ void act_pack16(const float* v, bool leaky, float slope, uint32_t* pk) {
+  using O = Op<DT>;
+  if (!leaky) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) pk[i] = O::relu_pack2(v[2 * i], v[2 * i + 1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float a = v[2 * i], b = v[2 * i + 1];
+      pk[i] = O::pack2(a > 0.f ? a : slope * a, b > 0.f ? b : slope * b);
+    }
+  }
+}
 
 // Tile claiming of the persistent kernels.  With a counter (zeroed before
 // the launch) each CTA claims its next tile when it is ready for one, so the
@@ -269,4 +317,7 @@ __device__ __forceinline__ int64_t next_tile(uint32_t* ctr, int64_t t) {
 }
 
 }  // namespace tc
+
+// The driver's cuTensorMapEncodeTiled, or null when the driver lacks it.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 }  // namespace nif

@@ -104,11 +104,14 @@ def full_scale_config() -> RoomConfig:
     """480 displaced icospheres of 62,720 triangles (30.1M) on a jittered
     lattice in the room, a 4 x 4 area light, 4 samples per pixel -> 8,294,400
     shadow rays; dense 8-level FP16 grids per object, FP16 networks, trained on
-    16 jittered samples x 4 light samples = 64 shadow samples per pixel."""
+    16 jittered samples x 4 light samples = 64 shadow samples per pixel.  The
+    exact cast of the 12 room triangles follows the NIF query and skips the
+    rays it occluded (3.045 ms per step against 3.079 ms with the cast first
+    on one GB300)."""
     return RoomConfig(layout=_FULL.layout, n_obj=_FULL.n_obj, n=_FULL.n, res=_FULL.res,
                       log2_table=_FULL.log2_table, grid_dtype=L.NIF_F16, mlp_dtype=L.NIF_F16,
                       area_light=_FULL.area_light, samples=_FULL.samples, train_spp=16,
-                      pairs_per_spp=1 << 20, max_pairs_per_ray=8)
+                      pairs_per_spp=1 << 20, max_pairs_per_ray=8, exact_cast="after")
 
 
 class RoomPipeline:
@@ -386,10 +389,10 @@ class RoomPipeline:
 
     def query_step(self, bits: torch.Tensor, rays: torch.Tensor | None = None, ev=None):
         """The calls of one two-round visibility query, with optional CUDA
-        events ev[0..3] recorded between them: the non-NIF cast (or its
-        start, see _exact_begin), then nif_frontend_nearest, the forward of
-        round 1, nif_frontend_rest and the forward of round 2 (what nif_infer
-        does for one model)."""
+        events ev[0..3] (and ev[4]) recorded between them: the non-NIF cast
+        (or its start, see _exact_begin), then nif_frontend_nearest, the
+        forward of round 1, nif_frontend_rest, the forward of round 2 and the
+        end of the non-NIF cast (what nif_infer does for one model)."""
         rays = self.rays if rays is None else rays
         b = self._query_buffers()
         vp, sp, n = ctypes.c_void_p, nif._stream(), int(rays.shape[0])
@@ -421,6 +424,8 @@ class RoomPipeline:
         if ev is not None:
             ev[3].record(stream)
         forward(b["goff2"])
+        if ev is not None and len(ev) > 4:
+            ev[4].record(stream)
         self._exact_end(join, bits, rays, stream)
         return bits
 
