@@ -806,9 +806,10 @@ def run_ours(args):
                 "h2d_bytes_per_step": n * 32, "d2h_bytes_per_step": bits.numel() * 4,
                 "frames_in_flight": 2, "l2": "flushed before every frame's query, inside the timed span",
                 "latency_ms_per_frame": reduce_max(statistics.median(lat_ms), world, dev)},
-        # per step: the exact cast, 3 + 3 front-end kernels, one fused
-        # forward per network model and round
-        "gpu_launches": (7 + 2 * len(pipe.forward_models())) * args.steps,
+        # per step: the exact cast (and the mask clear when it does not come
+        # first), 3 + 3 front-end kernels, one fused forward per network
+        # model and round
+        "gpu_launches": (7 + (cfg.exact_cast != "first") + 2 * len(pipe.forward_models())) * args.steps,
         "clocks": clocks,
     }
     if mlp_alone is not None:
