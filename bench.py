@@ -557,7 +557,11 @@ def run_ours(args):
         cfg.schedule = {"serial": L.NIF_SCHED_SERIAL, "pipelined": L.NIF_SCHED_PIPELINED}[args.schedule]
     if args.exact_cast:
         cfg.exact_cast = args.exact_cast
-    if args.train_precision == "f16" and hasattr(cfg, "half_precision_train"):
+    # half-precision training needs a 16-bit network over the multi-resolution
+    # encoding (the precision sweep trains its FP32 network in FP32 and
+    # quantises it afterwards; the paper's spherical encoding trains in FP32)
+    if (args.train_precision == "f16" and pipe_cls is RoomPipeline
+            and cfg.mlp_dtype in (L.NIF_F16, L.NIF_BF16)):
         cfg.half_precision_train = True
     pipe = pipe_cls(cfg, log=log)
     train_s = pipe.train()
@@ -571,7 +575,7 @@ def run_ours(args):
         "adam_bytes_per_step": 34 * n_par,
         "adam_floor_ms": 34 * n_par / (_peaks()[0] * 1e9) * 1e3,
         "wall_includes": "host-side batch draw (numpy) and copies",
-        "precision": args.train_precision,
+        "precision": "f16" if getattr(cfg, "half_precision_train", False) else "f32",
         # batch loss every 8 steps and at the last one
         "loss_curve": [round(v, 6) for v in pipe.losses[::8] + pipe.losses[-1:]]}
     dis = pipe.disagreement()
