@@ -282,6 +282,18 @@ def sigmoid(z):
     return 1.0 / (1.0 + np.exp(-z))
 
 
+def l2_sigmoid_terms(z, y):
+    """e = sigmoid(z) - y and sigmoid'(z) = sigmoid(z) (1 - sigmoid(z)) of the
+    L2 loss on the sigmoid, with 1 - sigmoid(z) taken as sigmoid(-z) (the
+    same number, without the cancellation that loses it for large z); for a
+    label y = 1, e = -sigmoid(-z) likewise."""
+    z = np.asarray(z, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    sp, sm = sigmoid(z), sigmoid(-z)
+    e = np.where(y == 1.0, -sm, sp - y)
+    return e, sp * sm
+
+
 def ray_occlusion(n_rays: int, ray_id, z) -> np.ndarray:
     """Ray occluded (1) when any of its pairs has sigmoid(z) < 0.5 <=> z < 0."""
     occ = np.zeros(n_rays, dtype=bool)
@@ -290,14 +302,19 @@ def ray_occlusion(n_rays: int, ray_id, z) -> np.ndarray:
 
 
 # ---------------------------------------------------------------- step 5
-def loss_and_grads(m: Model, rays, ray_id, obj, inner, label, sparse_grids: bool = False):
+def loss_and_grads(m: Model, rays, ray_id, obj, inner, label, sparse_grids: bool = False, z_at=None):
     """L = (1/B) sum (sigmoid(z) - y)^2 with y = 1 for visible pairs, and its
     gradients w.r.t. every network weight and every grid latent.
     Returns (L, dnets (same structure as m.nets), dgrids (same shape as m.grids)).
     With sparse_grids the grid gradient is returned as (flat index, value)
     over the latents the pairs tap (flat index ((obj * 2 + grid) * V + vertex)
     * F + feature), for grids too large to hold densely; the arithmetic is
-    the same sum of weight x dL/dx per tap."""
+    the same sum of weight x dL/dx per tap.
+    z_at (one logit per pair, optional): dL/dz is taken at these logits
+    instead of the forward's own, and carried back through the network and
+    the grids at the FP64 activations (the chain rule's J^T dL/dz with dL/dz
+    from elsewhere); L stays the forward's own.  It checks a backward pass
+    apart from the forward whose logits it was given."""
     B = len(ray_id)
     y = np.asarray(label, dtype=np.float64)
     x, tap_idx, tap_w = encode(m, rays, ray_id, obj, want_taps=True)
@@ -309,9 +326,11 @@ def loss_and_grads(m: Model, rays, ray_id, obj, inner, label, sparse_grids: bool
         sel = np.nonzero(net == g)[0]
         mats = m.nets[g]
         z, pre, post = mlp_forward(x[sel], mats, m.act, m.slope)
-        s = sigmoid(z)
-        L += float(np.sum((s - y[sel]) ** 2)) / B
-        dz = (2.0 / B) * (s - y[sel]) * s * (1.0 - s)
+        e, ds = l2_sigmoid_terms(z, y[sel])
+        L += float(np.sum(e ** 2)) / B
+        if z_at is not None:
+            e, ds = l2_sigmoid_terms(np.asarray(z_at, dtype=np.float64)[sel], y[sel])
+        dz = (2.0 / B) * e * ds
         dnets[g][-1] += (dz[:, None] * post[-1]).sum(axis=0)[None, :]
         dh = dz[:, None] * np.asarray(mats[-1], dtype=np.float64)
         for li in range(len(mats) - 2, -1, -1):

@@ -80,12 +80,12 @@ def loss_and_grads(m: onif.Model, rays, ray_id, obj, inner, label, aux):
         sel = np.nonzero(net == g)[0]
         mats = m.nets[g]
         Z, pre, post = mlp_outputs(x[sel], mats, m.act, m.slope)
-        s = onif.sigmoid(Z[:, 0])
+        e, ds = onif.l2_sigmoid_terms(Z[:, 0], y[sel])
         hit = 1.0 - y[sel]
         r = Z[:, 1:] - a[sel]
-        L += float(np.sum((s - y[sel]) ** 2) + np.sum(hit[:, None] * r * r)) / B
+        L += float(np.sum(e ** 2) + np.sum(hit[:, None] * r * r)) / B
         dZ = np.zeros_like(Z)
-        dZ[:, 0] = (2.0 / B) * (s - y[sel]) * s * (1.0 - s)
+        dZ[:, 0] = (2.0 / B) * e * ds
         dZ[:, 1:] = (2.0 / B) * hit[:, None] * r
         dnets[g][-1] += dZ.T @ post[-1]
         dh = dZ @ np.asarray(mats[-1], dtype=np.float64)

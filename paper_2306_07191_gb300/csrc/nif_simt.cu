@@ -577,6 +577,15 @@ __global__ void __launch_bounds__(kFThreads) k_mlp_fwd_f32(NifParams p, const ni
 }
 
 // ------------------------------------------------------------------- loss
+// sigmoid(z) and sigmoid(-z) = 1 - sigmoid(z), each from its own
+// exponential: 1 - sigmoid(z) formed by subtraction rounds to 0 in FP32 once
+// z > 17, which would drop the (tiny, nonzero) L2-loss gradient of a
+// confident pair; the product sigmoid(z) sigmoid(-z) keeps it.
+__device__ __forceinline__ void sigmoid_pair(float z, float& sp, float& sm) {
+  sp = 1.0f / (1.0f + expf(-z));
+  sm = 1.0f / (1.0f + expf(z));
+}
+
 __global__ void k_loss(const float* z, const uint8_t* label, int64_t nq, float scale, float* dz,
                        float* loss, const float* d_scale) {
   if (d_scale) scale = *d_scale;
@@ -584,11 +593,11 @@ __global__ void k_loss(const float* z, const uint8_t* label, int64_t nq, float s
   const float invB = 1.0f / static_cast<float>(nq);
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nq;
        q += (int64_t)gridDim.x * blockDim.x) {
-    float s = 1.0f / (1.0f + expf(-z[q]));
-    float y = label[q] ? 1.0f : 0.0f;
-    float e = s - y;
+    float sp, sm;
+    sigmoid_pair(z[q], sp, sm);
+    const float e = label[q] ? -sm : sp;  // sigmoid(z) - y
     part += e * e;
-    dz[q] = scale * 2.0f * invB * e * s * (1.0f - s);
+    dz[q] = scale * 2.0f * invB * e * (sp * sm);
   }
   for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
   if (loss && (threadIdx.x & 31) == 0) atomicAdd(loss, part * invB);
@@ -604,11 +613,12 @@ __global__ void k_loss_aux(const float* z, const uint8_t* label, const float* au
        q += (int64_t)gridDim.x * blockDim.x) {
     const float* zq = z + q * O;
     float* dq = dz + q * O;
-    const float s = 1.0f / (1.0f + expf(-zq[0]));
+    float sp, sm;
+    sigmoid_pair(zq[0], sp, sm);
     const float y = label[q] ? 1.0f : 0.0f;
-    const float e = s - y;
+    const float e = label[q] ? -sm : sp;  // sigmoid(z) - y
     part += e * e;
-    dq[0] = scale * 2.0f * invB * e * s * (1.0f - s);
+    dq[0] = scale * 2.0f * invB * e * (sp * sm);
     const float hit = 1.0f - y;
     for (int k = 1; k < O; ++k) {
       const float r = hit > 0.f ? zq[k] - aux[q * (O - 1) + (k - 1)] : 0.f;

@@ -384,6 +384,83 @@ def test_single_layer_gradient_closed_form():
     np.testing.assert_allclose(dnets[0][0][0], want, rtol=1e-12)
 
 
+def test_sigmoid_loss_terms_against_50_digit_arithmetic():
+    """sigmoid(z) - y and sigmoid(z)(1 - sigmoid(z)) of the L2 loss keep full
+    relative precision for confident logits (|z| up to 40, where forming
+    1 - sigmoid(z) by subtraction loses every digit), checked against the
+    same formulas in 50-digit arithmetic; a single-layer weight gradient at
+    such logits likewise."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    zs = np.array([-40.0, -25.0, -5.0, -0.5, 0.0, 0.5, 5.0, 25.0, 40.0])
+    for y in (0.0, 1.0):
+        e, ds = onif.l2_sigmoid_terms(zs, np.full(zs.shape, y))
+        for k, z in enumerate(zs):
+            s = 1 / (1 + mp.exp(-mp.mpf(z)))
+            e_want, ds_want = s - y, s * (1 - s)
+            assert abs(e[k] - float(e_want)) <= 1e-14 * abs(float(e_want)) + 1e-300, (z, y)
+            assert abs(ds[k] - float(ds_want)) <= 1e-14 * float(ds_want), (z, y)
+    rng = np.random.default_rng(31)
+    m = _model([3], 2, 19, n_hidden=0, seed=9)
+    m.nets[0][0] = rng.normal(size=(1, m.K)) * 60
+    rays = synth.aimed_rays(rng, 12, BOX, 6.0)
+    rid, obj, inner = np.arange(12), np.zeros(12, np.int64), np.zeros(12, bool)
+    y = np.ones(12)
+    _, dnets, _ = onif.loss_and_grads(m, rays, rid, obj, inner, y)
+    x = onif.encode(m, rays, rid, obj)
+    z = x @ m.nets[0][0][0]
+    assert np.abs(z).max() > 20
+    dz = [2 / mp.mpf(12) * (1 / (1 + mp.exp(-mp.mpf(v))) - 1) * (1 / (1 + mp.exp(-mp.mpf(v))))
+          * (1 - 1 / (1 + mp.exp(-mp.mpf(v)))) for v in z]
+    want = np.array([float(sum(dz[q] * mp.mpf(x[q, k]) for q in range(12))) for k in range(m.K)])
+    np.testing.assert_allclose(dnets[0][0][0], want, rtol=1e-12, atol=1e-300)
+
+
+def test_gradient_at_given_logits_closed_form_and_linearity():
+    """dL/dz taken at given logits z_at: with no hidden layer the weight
+    gradient is (2/B) sum (s(z_at) - y) s(z_at) (1 - s(z_at)) x, written out
+    here; with hidden layers each pair's contribution scales with its dL/dz
+    (the backward is linear in it), so one pair's gradient at z_at is its
+    gradient at its own logit times dL/dz(z_at) / dL/dz(z); L stays the
+    forward's own."""
+    rng = np.random.default_rng(21)
+    m = _model([3], 2, 19, n_hidden=0, seed=9)
+    m.nets[0][0] = rng.normal(size=(1, m.K)) * 5
+    rays = synth.aimed_rays(rng, 30, BOX, 6.0)
+    rid = np.arange(30)
+    obj = np.zeros(30, np.int64)
+    inner = np.zeros(30, bool)
+    y = rng.integers(0, 2, size=30).astype(float)
+    x = onif.encode(m, rays, rid, obj)
+    z = x @ m.nets[0][0][0]
+    za = z + rng.normal(scale=0.3, size=30)
+    L, dnets, _ = onif.loss_and_grads(m, rays, rid, obj, inner, y, z_at=za)
+    s0 = 1 / (1 + np.exp(-z))
+    assert abs(L - np.mean((s0 - y) ** 2)) < 1e-14
+    s = 1 / (1 + np.exp(-za))
+    np.testing.assert_allclose(dnets[0][0][0], (2 / 30) * ((s - y) * s * (1 - s)) @ x, rtol=1e-12)
+    # hidden layers: one pair, the gradient scales with dL/dz
+    m2 = _model([2, 4], 2, 19, n_hidden=2, width=6, seed=3)
+    for W in m2.nets[0]:
+        W *= 3.0
+    m2.grids *= 2.0
+    r1 = synth.aimed_rays(rng, 1, BOX, 6.0)
+    one = (np.arange(1), np.zeros(1, np.int64), np.zeros(1, bool), np.ones(1))
+    _, dn, dg = onif.loss_and_grads(m2, r1, *one)
+    z1 = onif.mlp_forward(onif.encode(m2, r1, one[0], one[1]), m2.nets[0], m2.act, m2.slope)[0]
+    za1 = z1 - 0.7
+
+    def dz(v):
+        sv = 1 / (1 + np.exp(-v))
+        return 2 * (sv - 1) * sv * (1 - sv)
+    ratio = float(dz(za1)[0] / dz(z1)[0])
+    _, dn_a, dg_a = onif.loss_and_grads(m2, r1, *one, z_at=za1)
+    for a, b in zip(dn_a[0], dn[0]):
+        np.testing.assert_allclose(a, ratio * b, rtol=1e-12, atol=1e-300)
+    np.testing.assert_allclose(dg_a, ratio * dg, rtol=1e-12, atol=1e-300)
+    assert np.abs(dg).max() > 0 and abs(ratio - 1) > 0.1
+
+
 # ------------------------------------------------------------ Adam
 def test_adam_first_step_closed_form():
     """Step 1: m_hat = g, v_hat = g^2, so the update is -lr g / (|g| + eps)."""
