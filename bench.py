@@ -557,6 +557,8 @@ def run_ours(args):
         cfg.schedule = {"serial": L.NIF_SCHED_SERIAL, "pipelined": L.NIF_SCHED_PIPELINED}[args.schedule]
     if args.exact_cast:
         cfg.exact_cast = args.exact_cast
+    if args.tlas:
+        cfg.tlas_builder = args.tlas
     # half-precision training needs a 16-bit network over the multi-resolution
     # encoding (the precision sweep trains its FP32 network in FP32 and
     # quantises it afterwards; the paper's spherical encoding trains in FP32)
@@ -783,7 +785,7 @@ def run_ours(args):
                    "queries_round1": nq1, "queries_all_pairs": nq_all, "triangles": pipe.n_tris,
                    "objects": cfg.n_obj, "nif_objects": pipe.n_obj, "triangles_nif": pipe.n_tris_nif,
                    "l2": "flushed (256 MB write) before every timed step",
-                   "exact_cast": cfg.exact_cast, "cuda_graph": bool(graphs),
+                   "exact_cast": cfg.exact_cast, "tlas": cfg.tlas_builder, "cuda_graph": bool(graphs),
                    "round1": round1, "round1_pairs": round1_pairs,
                    "fused_schedule": SCHED_NAME[pipe.forward_models()[0][0].cfg.schedule],
                    "fused_ctas_per_sm": pipe.forward_models()[0][0].cfg.ctas_per_sm,
@@ -1226,6 +1228,8 @@ def main():
     ap.add_argument("--exact-cast", choices=("first", "after", "overlap"), default=None,
                     help="when the non-NIF geometry is cast: before the NIF query (default), after it, "
                          "or beside it on a second stream")
+    ap.add_argument("--tlas", choices=("lbvh", "ploc"), default=None,
+                    help="builder of the top level over the object boxes (default: the workload's)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -240,6 +240,15 @@ nif_status bvh_build_ploc(const float* d_verts, int64_t n_verts, const int32_t* 
                           int64_t n_tris, const int32_t* d_tri_tag, void* d_bvh, size_t bvh_bytes,
                           void* d_ws, size_t ws_bytes, void* stream);
 
+/* bvh_build_boxes_ploc: the top level over object boxes (d_boxes [n][6],
+ * min xyz, max xyz) built by the same clustering as bvh_build_ploc, with
+ * bvh_build_boxes' leaves and layout; scratch of
+ * bvh_build_ploc_workspace_size(n) bytes.  Either top level serves
+ * nif_frontend, nif_infer and the other front-end calls, which find the same
+ * pairs through both. */
+nif_status bvh_build_boxes_ploc(const float* d_boxes, int64_t n, void* d_bvh, size_t bvh_bytes,
+                                void* d_ws, size_t ws_bytes, void* stream);
+
 /* Host copy of the build statistics (synchronises the stream): node count,
  * primitive count, tree depth.  Returns NIF_OK or an error. */
 nif_status bvh_info(const void* d_bvh, int64_t* n_nodes, int64_t* n_prims, int32_t* depth,

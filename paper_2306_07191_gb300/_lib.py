@@ -73,6 +73,7 @@ SIGNATURES = {
     "bvh_build_workspace_size": (size_t, [i64]),
     "bvh_build": (i32, [P, i64, P, i64, P, P, size_t, P, size_t, P]),
     "bvh_build_boxes": (i32, [P, i64, P, size_t, P, size_t, P]),
+    "bvh_build_boxes_ploc": (i32, [P, i64, P, size_t, P, size_t, P]),
     "bvh_build_ploc_workspace_size": (size_t, [i64]),
     "bvh_build_ploc": (i32, [P, i64, P, i64, P, P, size_t, P, size_t, P]),
     "bvh_info": (i32, [P, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i32), P]),

@@ -1182,6 +1182,20 @@ nif_status bvh_build_boxes(const float* d_boxes, int64_t n, void* d_bvh, size_t 
                     as_stream(stream), false);
 }
 
+nif_status bvh_build_boxes_ploc(const float* d_boxes, int64_t n, void* d_bvh, size_t bvh_bytes, void* d_ws,
+                                size_t ws_bytes, void* stream) {
+  CallRange nvtx_range("bvh_build_boxes_ploc");
+  NIF_CHECK_ARG(n >= 0, "bvh_build_boxes_ploc: negative size");
+  NIF_CHECK_ARG(d_bvh != nullptr, "bvh_build_boxes_ploc: null output");
+  NIF_CHECK_ARG(n == 0 || (d_boxes && d_ws), "bvh_build_boxes_ploc: null input");
+  NIF_CHECK_ARG((reinterpret_cast<uintptr_t>(d_bvh) & 255) == 0,
+                "bvh_build_boxes_ploc: output not 256-byte aligned");
+  NIF_CHECK_ARG((reinterpret_cast<uintptr_t>(d_ws) & 255) == 0,
+                "bvh_build_boxes_ploc: workspace not 256-byte aligned");
+  return bvh::build(1, nullptr, nullptr, d_boxes, nullptr, n, d_bvh, bvh_bytes, d_ws, ws_bytes,
+                    as_stream(stream), true);
+}
+
 nif_status bvh_info(const void* d_bvh, int64_t* n_nodes, int64_t* n_prims, int32_t* depth,
                     void* stream) {
   NIF_CHECK_ARG(d_bvh != nullptr, "bvh_info: null bvh");

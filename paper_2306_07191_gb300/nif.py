@@ -94,8 +94,8 @@ class BVH:
         self.buf = torch.empty(nb, dtype=torch.uint8, device=dev)
         ws = torch.empty(max(nw, 256), dtype=torch.uint8, device=dev)
         if boxes:
-            L.call("bvh_build_boxes", _ptr(verts), self.n, _ptr(self.buf), nb, _ptr(ws), ws.numel(),
-                   _stream(stream))
+            L.call("bvh_build_boxes_ploc" if builder == "ploc" else "bvh_build_boxes", _ptr(verts), self.n,
+                   _ptr(self.buf), nb, _ptr(ws), ws.numel(), _stream(stream))
         else:
             self._inputs = (verts, tris, tags)
             L.call("bvh_build_ploc" if builder == "ploc" else "bvh_build", _ptr(verts), int(verts.shape[0]),
@@ -122,8 +122,10 @@ class BVH:
         L.call("bvh_check", _ptr(self.buf), _stream(stream))
 
     @classmethod
-    def from_boxes(cls, boxes: torch.Tensor, stream=None) -> "BVH":
-        return cls(boxes.contiguous(), boxes, boxes=True, stream=stream)
+    def from_boxes(cls, boxes: torch.Tensor, stream=None, builder: str = "lbvh") -> "BVH":
+        """The top level over object boxes [n][6] (bvh_build_boxes, or
+        bvh_build_boxes_ploc with builder="ploc")."""
+        return cls(boxes.contiguous(), boxes, boxes=True, stream=stream, builder=builder)
 
     def info(self):
         nn, npr, dep = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int32()

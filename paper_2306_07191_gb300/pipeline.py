@@ -69,6 +69,7 @@ class RoomConfig:
     # end skip rays), "after" (skipping rays NIF occluded) or "overlap" (on a
     # second stream beside the NIF query)
     exact_cast: str = "first"
+    tlas_builder: str = "lbvh"  # top level over the object boxes: "lbvh" or "ploc"
     n_lights: int = 1           # point lights (one shadow ray per light per pixel)
     area_light: bool = False    # 4 x 4 ceiling quad light instead of point lights
     samples: int = 1            # shadow rays per pixel (area-light samples)
@@ -150,7 +151,7 @@ class RoomPipeline:
         self.bvh = nif.BVH(self.verts, self.tris, self.tags)
         room = tri_obj < 0
         self.room_bvh = nif.BVH(self.verts, torch.from_numpy(sc.tris[room]).to(dev))
-        self.tlas = nif.BVH.from_boxes(self.obj_aabb)
+        self.tlas = nif.BVH.from_boxes(self.obj_aabb, builder=cfg.tlas_builder)
         self.light = torch.from_numpy(ws.light.astype(np.float32).reshape(-1)).to(dev)
         # evaluation frame: pixel-centre camera rays -> primary hits -> shadow rays
         self.rays = self._eval_rays(torch.from_numpy(ws.camera).to(dev))

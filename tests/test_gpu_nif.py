@@ -58,7 +58,7 @@ def _query_arrays(ray_id, qobj, nq):
     return r, (q & 0x7FFFFFFF).astype(np.int64), (q >> 31).astype(bool)
 
 
-@pytest.mark.parametrize("use_tlas", [False, True])
+@pytest.mark.parametrize("use_tlas", [False, True, "ploc"])
 def test_frontend_query_set_bit_exact(use_tlas):
     rng = np.random.default_rng(21)
     boxes = random_boxes_scene(rng, n_obj=9)
@@ -71,7 +71,8 @@ def test_frontend_query_set_bit_exact(use_tlas):
         cfg = nif.NifConfig(res=[2], n_features=1, net_mode=mode)
         model = nif.NifModel(cfg, torch.from_numpy(boxes).cuda(), torch.zeros(9 * 2 * 27).cuda(),
                              torch.zeros(nn * nif.NifModel.weight_count(cfg)).cuda())
-        tlas = nif.BVH.from_boxes(torch.from_numpy(boxes).cuda()) if use_tlas else None
+        tlas = (nif.BVH.from_boxes(torch.from_numpy(boxes).cuda(), builder="ploc" if use_tlas == "ploc" else "lbvh")
+                if use_tlas else None)
         ray_id, qobj, goff, nq = _gpu_queries(model, torch.from_numpy(rays).cuda(), tlas)
         r, ob, inn = _query_arrays(ray_id, qobj, nq)
         rr, oo, ii = onif.queries(rays, boxes)
@@ -247,7 +248,7 @@ def test_fp8_e4m3_logits_within_reported_bound():
     assert err.mean() <= 0.05, err.mean()
 
 
-@pytest.mark.parametrize("use_tlas", [False, True])
+@pytest.mark.parametrize("use_tlas", [False, True, "ploc"])
 def test_frontend_many_pairs_per_ray(use_tlas):
     """Rays crossing 16 boxes in a row: more pairs per ray than the front end
     keeps per ray in its single-traversal slots."""
@@ -262,7 +263,8 @@ def test_frontend_many_pairs_per_ray(use_tlas):
     cfg = nif.NifConfig(res=[2], n_features=1, net_mode=L.NIF_NETS_CLASS)
     model = nif.NifModel(cfg, torch.from_numpy(boxes).cuda(), torch.zeros(16 * 2 * 27).cuda(),
                          torch.zeros(2 * nif.NifModel.weight_count(cfg)).cuda())
-    tlas = nif.BVH.from_boxes(torch.from_numpy(boxes).cuda()) if use_tlas else None
+    tlas = (nif.BVH.from_boxes(torch.from_numpy(boxes).cuda(), builder="ploc" if use_tlas == "ploc" else "lbvh")
+            if use_tlas else None)
     ray_id, qobj, goff, count = model.frontend(torch.from_numpy(rays).cuda(), tlas=tlas, max_q=20 * n)
     model.check()
     nq = int(count.item())
