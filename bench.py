@@ -72,6 +72,10 @@ WORKLOADS = {
             "rows of synthetic FP16 inputs, U(-1, 1), in two groups (2/3 outer, 1/3 inner), class networks "
             "3x64 FP16 with Xavier weights; shapes K = 96 (the room's hashed 16x2 encoding) and K = 48 "
             "(the full-scale 8x2 encoding); L2 flushed before every launch"),
+    "mma": ("the tensor-core instruction rate (nif_tc_mma_rate): SM cycles per tcgen05.mma (kind::f16, "
+            "K = 16, one CTA per SM on every SM, zero operands) at the shapes the MLP kernels issue "
+            "(M = 128 x N = 64, M = 64 x N = 256) and at the widest (M = 128 x N = 256); 64 back-to-back "
+            "MMAs per commit, and 4 per commit as in a hidden layer"),
     "precision": ("precision sweep: small-configuration object (20,480 tris) in the room, 4 point "
                   "lights -> 8,294,400 shadow rays; dense 8x2 FP32 grids (R 4..64), MLP 3x64 trained "
                   "in FP32, inferred in FP32 / BF16 / FP16 / FP8-E4M3"),
@@ -360,25 +364,33 @@ def mlp_alone_stats(pipe, bits, steps: int, warmup: int, flush):
         L.call("nif_mlp_infer", ctypes.byref(d), vp(x.data_ptr()), vp(goff.data_ptr()), nq, vp(z.data_ptr()),
                vp(ws.data_ptr()), ws.numel(), nif._stream())
 
-    out = {"rows": nq, "K": c.K, "input_bytes": nq * c.K * 2}
+    out = {"rows": nq, "K": c.K, "input_bytes": nq * c.K * 2, "per_tile_m": {}}
     _, bf16_peak, src = _peaks()
     flops = nq * 2 * (c.K * 64 + (c.n_hidden - 1) * 64 * 64 + 64)
-    for mode in ("hbm", "l2"):
-        ts = []
-        for i in range(warmup + steps):
-            if mode == "hbm":
-                flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            run()
-            e1.record()
-            torch.cuda.synchronize()
-            if i >= warmup:
-                ts.append(e0.elapsed_time(e1))
-        ms = statistics.median(ts)
-        tf = flops / (ms * 1e-3) / 1e12
-        out[mode] = {"ms": ms, "tensor_tflops": tf, "tensor_frac": tf / bf16_peak,
-                     "input_gbs": nq * c.K * 2 / (ms * 1e-3) / 1e9}
+    # both tile shapes of nif_mlp_infer: 256 rows as the MMA's N, 128 rows as its M
+    for tile_m in (256, 128):
+        d.tile_m = tile_m
+        res = {}
+        for mode in ("hbm", "l2"):
+            ts = []
+            for i in range(warmup + steps):
+                if mode == "hbm":
+                    flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                run()
+                e1.record()
+                torch.cuda.synchronize()
+                if i >= warmup:
+                    ts.append(e0.elapsed_time(e1))
+            ms = statistics.median(ts)
+            tf = flops / (ms * 1e-3) / 1e12
+            res[mode] = {"ms": ms, "tensor_tflops": tf, "tensor_frac": tf / bf16_peak,
+                         "input_gbs": nq * c.K * 2 / (ms * 1e-3) / 1e9}
+        out["per_tile_m"][tile_m] = res
+    best = min(out["per_tile_m"], key=lambda m: out["per_tile_m"][m]["hbm"]["ms"])
+    out["tile_m"] = best
+    out["hbm"], out["l2"] = out["per_tile_m"][best]["hbm"], out["per_tile_m"][best]["l2"]
     out["tensor_peak_tflops"] = bf16_peak
     out["peak_source"] = src
     model.check(ws)
@@ -420,39 +432,55 @@ def run_mlp(args):
                                  torch.from_numpy(flat).half().to(dev))
             x = torch.from_numpy(rng.uniform(-1, 1, size=(rows, K)).astype(np.float16)).to(dev)
             goff = torch.tensor([0, 2 * rows // 3, rows], dtype=torch.int64, device=dev)
-            z = torch.empty(rows, dtype=torch.float32, device=dev)
             ws = torch.zeros(256, dtype=torch.uint8, device=dev)
-            d = model.desc()
             st = nif._stream()
             stream = torch.cuda.current_stream(dev)
-
-            def run():
-                L.call("nif_mlp_infer", ctypes.byref(d), vp(x.data_ptr()), vp(goff.data_ptr()), rows,
-                       vp(z.data_ptr()), vp(ws.data_ptr()), ws.numel(), st)
-
-            for _ in range(args.warmup):
-                flush.zero_()
-                run()
-            torch.cuda.synchronize()
-            ts = []
-            torch.cuda.profiler.start()
-            for _ in range(args.steps):
-                flush.zero_()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                run()
-                e1.record(stream)
-                ts.append((e0, e1))
-            torch.cuda.profiler.stop()
-            torch.cuda.synchronize()
-            model.check(ws)
-            assert torch.isfinite(z).all()
-            ms = statistics.median(a.elapsed_time(b) for a, b in ts)
             flops = rows * 2 * (K * 64 + 2 * 64 * 64 + 64)
+            per_tile = {}
+            outs = {}
+            # both tile shapes: 128 rows as the MMA's M, 256 rows as its N
+            for tile_m in (256, 128):
+                model.cfg.tile_m = tile_m
+                d = model.desc()
+                z = torch.empty(rows, dtype=torch.float32, device=dev)
+
+                def run():
+                    L.call("nif_mlp_infer", ctypes.byref(d), vp(x.data_ptr()), vp(goff.data_ptr()), rows,
+                           vp(z.data_ptr()), vp(ws.data_ptr()), ws.numel(), st)
+
+                for _ in range(args.warmup):
+                    flush.zero_()
+                    run()
+                torch.cuda.synchronize()
+                ts = []
+                torch.cuda.profiler.start()
+                for _ in range(args.steps):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    run()
+                    e1.record(stream)
+                    ts.append((e0, e1))
+                torch.cuda.profiler.stop()
+                torch.cuda.synchronize()
+                model.check(ws)
+                assert torch.isfinite(z).all()
+                ms = statistics.median(a.elapsed_time(b) for a, b in ts)
+                tf = flops / (ms * 1e-3) / 1e12
+                per_tile[tile_m] = {"ms": ms, "rows_per_s": rows / (ms * 1e-3), "tensor_tflops": tf,
+                                    "tensor_frac": tf / bf16_peak}
+                outs[tile_m] = z
+            # the two tile shapes round the last hidden layer differently
+            # (FP32 dot, or FP16 operands of one more MMA): logits agree to
+            # the FP16 rounding of that layer
+            diff = float((outs[128] - outs[256]).abs().max())
+            best = min(per_tile, key=lambda m: per_tile[m]["ms"])
+            ms = per_tile[best]["ms"]
             tf = flops / (ms * 1e-3) / 1e12
             shapes[name] = {"K": K, "ms": ms, "rows_per_s": rows / (ms * 1e-3), "tensor_tflops": tf,
                             "tensor_frac": tf / bf16_peak, "input_gbs": rows * K * 2 / (ms * 1e-3) / 1e9,
-                            "flops_per_row": flops // rows}
+                            "flops_per_row": flops // rows, "tile_m": best, "per_tile_m": per_tile,
+                            "max_logit_diff_between_tiles": diff}
     clocks = clk.summary()
     head = shapes["room K=96"]
     line = {
@@ -462,12 +490,73 @@ def run_mlp(args):
         "config": {"workload": WORKLOADS["mlp"], "rows": rows, "l2": "flushed (256 MB write) before every launch",
                    "parallelism": "single GPU"},
         "shapes": shapes,
-        "roofline": {"kernel": "k_mlp_pipe (room K=96)", "bound": "tensor", "achieved": head["tensor_tflops"],
+        "roofline": {"kernel": ("k_mlp_rows" if head["tile_m"] == 256 else "k_mlp_pipe") + " (room K=96)", "bound": "tensor", "achieved": head["tensor_tflops"],
                      "peak": bf16_peak, "unit": "TFLOP/s", "frac": head["tensor_frac"], "traffic": None,
                      "peak_source": src},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 4 * args.steps,
         "clocks": clocks,
         "cpu_baseline": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_mma(args):
+    """SM cycles per tcgen05.mma at the MLP kernels' shapes (nif_tc_mma_rate)
+    and the tensor-pipe rate each implies at the sampled SM clock against the
+    measured bf16 peak: the ceiling of an MLP kernel that issues MMAs of that
+    shape back to back."""
+    import ctypes
+
+    import torch
+
+    from paper_2306_07191_gb300 import _lib as L
+    from paper_2306_07191_gb300 import nif
+    world, rank, local = dist_env()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    _, bf16_peak, src = _peaks()
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    cyc = torch.zeros(n_sm, dtype=torch.int64, device=dev)
+    ws = torch.zeros(256, dtype=torch.uint8, device=dev)
+    vp = ctypes.c_void_p
+    shapes = [(128, 64, 0), (128, 64, 1), (64, 256, 0), (128, 128, 0), (128, 256, 0), (128, 256, 1)]
+    rows = []
+    with ClockSampler(local) as clk:
+        for _ in range(max(1, args.steps // 5)):
+            for m, n, a_tmem in shapes:
+                for chain, reps in ((64, 40), (4, 400)):
+                    L.call("nif_tc_mma_rate", m, n, a_tmem, chain, reps, n_sm, vp(cyc.data_ptr()), vp(ws.data_ptr()),
+                           ws.numel(), nif._stream())
+                    torch.cuda.synchronize()
+                    c = cyc.double()
+                    assert bool((c > 0).all()), "an MMA wait timed out"
+                    rows.append((m, n, a_tmem, chain, float(c.mean()) / (reps * chain)))
+    clocks = clk.summary()
+    det = ctypes.c_int64()
+    L.call("nif_check", vp(ws.data_ptr()), ctypes.byref(det), nif._stream())
+    mhz = clocks.get("sm_mhz") or 2070.0
+    out = {}
+    for m, n, a_tmem, chain, per in rows:
+        key = f"M{m}xN{n}" + ("_A_tmem" if a_tmem else "") + f"_chain{chain}"
+        out.setdefault(key, []).append(per)
+    table = {}
+    for key, v in out.items():
+        per = statistics.median(v)
+        m = int(key.split("x")[0][1:])
+        n = int(key.split("N")[1].split("_")[0])
+        fma_clk = m * n * 16 / per
+        tf = 2 * fma_clk * n_sm * mhz * 1e6 / 1e12
+        table[key] = {"cycles_per_mma": per, "fma_per_clk_per_sm": fma_clk, "tflops_at_clock": tf,
+                      "frac_of_bf16_peak": tf / bf16_peak}
+    head = table["M128xN64_chain64"]
+    line = {
+        "metric": "SM cycles per tcgen05.mma (kind::f16) at the MLP's shape", "value": head["cycles_per_mma"],
+        "unit": "cycles", "n_gpus": 1, "steps": args.steps, "warmup": 0, "ms_per_step": None,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f16", "data": "synthetic",
+        "config": {"workload": WORKLOADS["mma"], "ctas": n_sm, "sm_mhz_for_rates": mhz, "parallelism": "single GPU"},
+        "shapes": table, "tensor_peak_tflops": bf16_peak, "peak_source": src,
+        "gpu_launches": len(rows), "clocks": clocks, "cpu_baseline": None,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -1237,6 +1326,8 @@ def main():
         run_grouped(args)
     elif args.workload == "mlp":
         run_mlp(args)
+    elif args.workload == "mma":
+        run_mma(args)
     elif args.workload == "primary":
         run_primary(args)
     elif args.workload == "render":

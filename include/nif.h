@@ -412,8 +412,13 @@ nif_status nif_encode(const nif_model_desc* m, const nif_ray* d_rays, const uint
  * d_x [nq][K] in the network's 16-bit operand type (e.g. nif_encode's FP16
  * rows for an FP16 network; rows 16-byte aligned: K a multiple of 8), grouped
  * by network as d_group_off [n_nets + 1] gives them; d_logits[q] (FP32)
- * receives each row's logit z.  Tensor cores, two tiles of 128 rows in flight
- * per CTA.  FP16 or BF16 networks of width 64 with one output and at most two
+ * receives each row's logit z.  Tensor cores.  m->tile_m picks the tile:
+ * 0 or 128 for tiles of 128 rows (rows as the MMA's M, features as its N;
+ * two tiles in flight per CTA, two CTAs per SM), 256 for tiles of 256 rows
+ * (rows as N, features as M: half as many MMAs per row; two tiles in flight
+ * per SM; NIF_ERR_UNSUPPORTED when its buffers do not fit in shared memory).
+ * The two differ in rounding only by the order of the output layer's FP32
+ * sums.  FP16 or BF16 networks of width 64 with one output and at most two
  * networks (single or class mode).  d_ws (nullable, >= 256 bytes) receives
  * device errors (timed-out waits) for nif_check. */
 nif_status nif_mlp_infer(const nif_model_desc* m, const void* d_x, const int64_t* d_group_off, int64_t nq,
@@ -507,6 +512,19 @@ nif_status nif_infer_query_counts(const nif_model_desc* m, const void* d_ws, siz
  *   - Calls no cudaMalloc / cudaFree and no allocating library routine. */
 nif_status nif_infer_noalloc(const nif_model_desc* m, const void* d_tlas, const nif_ray* d_rays,
                              int64_t n, uint32_t* d_occluded_bits, void* stream);
+
+/* Tensor-core instruction rate (a measurement of the hardware; the paper has
+ * no counterpart): SM cycles taken by tcgen05.mma (kind::f16, one CTA, K = 16
+ * per instruction) at M = m (64 or 128) x N = n (a multiple of 16 up to 256),
+ * A from shared memory or (a_tmem, m = 128) from tensor memory.  Each of
+ * n_ctas CTAs (at most the SM count) issues `chain` MMAs from one thread,
+ * commits them and waits, `reps` times after two untimed rounds, and writes
+ * the SM cycles of the timed rounds to d_cycles[cta] (device int64, -1 when a
+ * wait timed out; the timeout is also recorded in d_ws, >= 256 bytes, for
+ * nif_check).  Cycles per MMA = d_cycles / (reps * chain).  Operands are
+ * zeros; asynchronous on `stream`. */
+nif_status nif_tc_mma_rate(int32_t m, int32_t n, int32_t a_tmem, int32_t chain, int32_t reps,
+                           int32_t n_ctas, int64_t* d_cycles, void* d_ws, size_t ws_bytes, void* stream);
 
 /* ------------------------------------------------------------ training --
  * Optimiser state (Sec. 5 "Training": Adam, beta1 0.9, beta2 0.999,

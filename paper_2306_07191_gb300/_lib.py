@@ -97,6 +97,7 @@ SIGNATURES = {
     "nif_frontend": (i32, [MD, P, P, i64, P, P, i64, P, P, P, size_t, P]),
     "nif_encode": (i32, [MD, P, P, P, i64, P, i32, P]),
     "nif_mlp_infer": (i32, [MD, P, P, i64, P, P, size_t, P]),
+    "nif_tc_mma_rate": (i32, [i32, i32, i32, i32, i32, i32, P, P, size_t, P]),
     "nif_infer_queries": (i32, [MD, P, i64, P, P, P, i64, P, P, P, size_t, P]),
     "nif_infer": (i32, [MD, P, P, i64, P, P, size_t, P]),
     "nif_infer_query_counts": (i32, [MD, P, size_t, i64, P, P]),

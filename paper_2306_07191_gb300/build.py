@@ -27,6 +27,7 @@ UNITS = {
     "api.cu": [],
     "noalloc.cu": [],
     "det.cu": [],
+    "tc_rate.cu": [],
 }
 
 

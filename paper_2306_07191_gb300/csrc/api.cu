@@ -415,7 +415,8 @@ nif_status nif_mlp_infer(const nif_model_desc* m, const void* d_x, const int64_t
   NIF_CHECK_ARG(d_x && d_logits, "nif_mlp_infer: null pointer");
   NIF_CHECK_ARG(aligned16(d_x), "nif_mlp_infer: inputs not 16-byte aligned");
   NIF_CHECK_ARG(d_ws == nullptr || ws_bytes >= kErrBytes, "nif_mlp_infer: workspace too small");
-  return launch_mlp_pipe(p, d_x, d_group_off, nq, d_logits, static_cast<DevError*>(d_ws), as_stream(stream));
+  return launch_mlp_pipe(p, d_x, d_group_off, nq, d_logits, static_cast<DevError*>(d_ws), as_stream(stream),
+                         m->tile_m);
 }
 
 nif_status nif_infer(const nif_model_desc* m, const void* d_tlas, const nif_ray* d_rays, int64_t n,

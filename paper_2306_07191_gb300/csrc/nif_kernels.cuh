@@ -55,7 +55,7 @@ nif_status check_tc_shape(const NifParams& p);
 // The inference stage alone over encoded inputs x [nq][K] (16-bit) on the
 // tensor cores, two tiles in flight per CTA (nif_mlp_tc.cu).
 nif_status launch_mlp_pipe(const NifParams& p, const void* x, const int64_t* goff, int64_t nq, float* logits,
-                           DevError* err, cudaStream_t st);
+                           DevError* err, cudaStream_t st, int tile_m = 0);
 // Training forward on the tensor cores: logits and p.saved16 (16-bit
 // activations x, h_1 .. h_H, [K/2 + H*W/2][p.ld_saved] words of two).
 nif_status launch_fwd_tc_save(const NifParams& p, const nif_ray* rays, const uint32_t* ray_id,

@@ -293,13 +293,11 @@ __global__ void __launch_bounds__(kThreads, kOcc)
       const int kdim = l == 0 ? Kp : W;
       if (tid == 0) {
         tc_fence_after();
-        const uint32_t a0 = smem_u32(tileA), b0 = smem_u32(smem + L.w_off(l));
         const uint32_t sbo = (kdim / (16 / esz)) * 128;
-        for (int kk = 0; kk < kdim / kstep; ++kk) {
-          const uint64_t ad = smem_desc(a0 + kk * 256, 128, sbo);
-          const uint64_t bd = smem_desc(b0 + kk * 256, 128, sbo);
-          mma<O::kind>(tmem, ad, bd, idesc, kk > 0 ? 1u : 0u);
-        }
+        const uint64_t ad = smem_desc(smem_u32(tileA), 128, sbo);
+        const uint64_t bd = smem_desc(smem_u32(smem + L.w_off(l)), 128, sbo);
+        for (int kk = 0; kk < kdim / kstep; ++kk)
+          mma<O::kind>(tmem, desc_advance(ad, kk * 256), desc_advance(bd, kk * 256), idesc, kk > 0 ? 1u : 0u);
         mma_commit(bar);
       }
       bool ok = mbar_wait(bar, phase, err);
@@ -652,10 +650,9 @@ __global__ void __launch_bounds__(kThreads * kRB, kOcc)
       const int kdim = l == 0 ? Kp : W;
       if (tid == 0) {
         tc_fence_after();
-        const uint32_t b0 = smem_u32(smem + L.w_off(l));
-        const uint32_t sbo = (kdim / 8) * 128;
+        const uint64_t bd0 = smem_desc(smem_u32(smem + L.w_off(l)), 128, (kdim / 8) * 128);
         for (int kk = 0; kk < kdim / 16; ++kk) {
-          const uint64_t bd = smem_desc(b0 + kk * 256, 128, sbo);
+          const uint64_t bd = desc_advance(bd0, kk * 256);
 #pragma unroll
           for (int b = 0; b < kRB; ++b)
             mma_ta(tmem + b * cb, tmem + b * cb + static_cast<uint32_t>(W + kk * 8), bd, idesc, kk > 0 ? 1u : 0u);
@@ -970,12 +967,10 @@ __global__ void __launch_bounds__(32 * (kEW + 4), kOcc)
         tc_fence_after();
         const int kdim = l == 0 ? Kp : W;
         if (leader) {
-          const uint32_t b0 = smem_u32(smem + L.w_off(l));
-          const uint32_t sbo = (kdim / 8) * 128;
-          for (int kk = 0; kk < kdim / 16; ++kk) {
-            const uint64_t bd = smem_desc(b0 + kk * 256, 128, sbo);
-            mma_ta(tmem, tmem + abuf + static_cast<uint32_t>(kk * 8), bd, idesc, kk > 0 ? 1u : 0u);
-          }
+          const uint64_t bd = smem_desc(smem_u32(smem + L.w_off(l)), 128, (kdim / 8) * 128);
+          for (int kk = 0; kk < kdim / 16; ++kk)
+            mma_ta(tmem, tmem + abuf + static_cast<uint32_t>(kk * 8), desc_advance(bd, kk * 256), idesc,
+                   kk > 0 ? 1u : 0u);
           mma_commit(mbar);
         }
         const bool ok = mbar_wait(mbar, mphase, err);

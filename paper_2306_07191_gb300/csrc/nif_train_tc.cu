@@ -223,18 +223,18 @@ __global__ void __launch_bounds__(kBwdThreads, 1)
       if (tid == 0) {
         tc_fence_after();
         // dW_l^T += H_{l-1}^T dA_l: K = 128 pairs
-        const uint32_t a0 = smem_u32(ht(l - 1)), b0 = smem_u32(l == H + 1 ? dzt : dat);
+        const uint64_t a0 = smem_desc(smem_u32(ht(l - 1)), 128, 2048);
+        const uint64_t b0 = smem_desc(smem_u32(l == H + 1 ? dzt : dat), 128, 2048);
         const uint32_t idw = instr_desc(128, no, fmt);
         for (int kk = 0; kk < 128 / 16; ++kk)
-          mma<0>(tmem + dw_col(l), smem_desc(a0 + kk * 256, 128, 2048), smem_desc(b0 + kk * 256, 128, 2048), idw,
+          mma<0>(tmem + dw_col(l), desc_advance(a0, kk * 256), desc_advance(b0, kk * 256), idw,
                  (kk > 0 || !fresh[l - 1]) ? 1u : 0u);
         // dH_{l-1} = dA_l W_l: K = the layer's outputs
-        const uint32_t a1 = smem_u32(da), b1 = smem_u32(smem + L.wt_off[l - 1]);
-        const uint32_t idh = instr_desc(128, fi, fmt);
         const uint32_t sbo = static_cast<uint32_t>(no / 8) * 128;
+        const uint64_t a1 = smem_desc(smem_u32(da), 128, sbo), b1 = smem_desc(smem_u32(smem + L.wt_off[l - 1]), 128, sbo);
+        const uint32_t idh = instr_desc(128, fi, fmt);
         for (int kk = 0; kk < no / 16; ++kk)
-          mma<0>(tmem + kDhCol, smem_desc(a1 + kk * 256, 128, sbo), smem_desc(b1 + kk * 256, 128, sbo), idh,
-                 kk > 0 ? 1u : 0u);
+          mma<0>(tmem + kDhCol, desc_advance(a1, kk * 256), desc_advance(b1, kk * 256), idh, kk > 0 ? 1u : 0u);
         mma_commit(bar);
       }
       fresh[l - 1] = false;

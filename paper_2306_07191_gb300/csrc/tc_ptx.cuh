@@ -222,6 +222,13 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   return d;                             // base offset 0, no swizzle
 }
 
+// A descriptor moved `bytes` (a multiple of 16) further along shared memory:
+// the start-address field holds the address in 16-byte units in its low 14
+// bits, and shared-memory addresses stay below 256 KB, so no carry leaves it.
+__device__ __forceinline__ uint64_t desc_advance(uint64_t d, uint32_t bytes) {
+  return d + static_cast<uint64_t>(bytes >> 4);
+}
+
 // Instruction descriptor: FP32 accumulator, A and B of format `fmt`
 // (kind::f16: 0 = f16, 1 = bf16; kind::f8f6f4: 0 = e4m3), both K-major.
 __host__ __device__ constexpr uint32_t instr_desc(int m, int n, uint32_t fmt) {

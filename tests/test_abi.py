@@ -216,3 +216,12 @@ def test_argument_errors_of_the_widened_calls(L):
     taps = 3 * 16 * 8 * 2
     assert L.lib.nif_deterministic_workspace_size(ctypes.byref(d1), 1000) >= 1000 * taps * 8
     assert L.lib.nif_deterministic_workspace_size(ctypes.byref(d1), -1) == 0
+
+
+def test_argument_errors_of_the_rate_measurement(L):
+    """nif_tc_mma_rate refuses shapes the tensor cores do not take and bad
+    counts before touching the device."""
+    P = ctypes.c_void_p
+    for m, n, a_tmem, chain, reps in ((96, 64, 0, 4, 4), (128, 8, 0, 4, 4), (128, 272, 0, 4, 4),
+                                      (64, 256, 1, 4, 4), (128, 64, 0, 0, 4), (128, 64, 0, 4, 0)):
+        assert L.lib.nif_tc_mma_rate(m, n, a_tmem, chain, reps, 1, P(256), P(256), 256, None) == L.NIF_ERR_ARG
