@@ -419,6 +419,7 @@ def run_mlp(args):
     _, bf16_peak, src = _peaks()
     vp = ctypes.c_void_p
     shapes = {}
+    gpu_warm(flush)
     with ClockSampler(local) as clk:
         for name, res in (("room K=96", workloads.ROOM_RES), ("full K=48", workloads.TINY_RES)):
             rng = np.random.default_rng(len(res))
@@ -501,6 +502,20 @@ def run_mlp(args):
         print(json.dumps(line), flush=True)
 
 
+def gpu_warm(buf, seconds: float = 0.5):
+    """Keep the GPU busy for a moment before a short timed run, so that its
+    memory and SM clocks have left their idle states (the MLP and rate
+    workloads time a few milliseconds in all)."""
+    import time
+
+    import torch
+    t0 = time.time()
+    while time.time() - t0 < seconds:
+        for _ in range(20):
+            buf.zero_()
+        torch.cuda.synchronize()
+
+
 def run_mma(args):
     """SM cycles per tcgen05.mma at the MLP kernels' shapes (nif_tc_mma_rate)
     and the tensor-pipe rate each implies at the sampled SM clock against the
@@ -520,6 +535,7 @@ def run_mma(args):
     cyc = torch.zeros(n_sm, dtype=torch.int64, device=dev)
     ws = torch.zeros(256, dtype=torch.uint8, device=dev)
     vp = ctypes.c_void_p
+    gpu_warm(torch.empty(256 << 20, dtype=torch.uint8, device=dev))
     shapes = [(128, 64, 0), (128, 64, 1), (64, 256, 0), (128, 128, 0), (128, 256, 0), (128, 256, 1)]
     rows = []
     with ClockSampler(local) as clk:
