@@ -532,29 +532,34 @@ def run_mma(args):
     torch.cuda.set_device(dev)
     _, bf16_peak, src = _peaks()
     n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    cyc = torch.zeros(n_sm, dtype=torch.int64, device=dev)
     ws = torch.zeros(256, dtype=torch.uint8, device=dev)
     vp = ctypes.c_void_p
     gpu_warm(torch.empty(256 << 20, dtype=torch.uint8, device=dev))
-    shapes = [(128, 64, 0), (128, 64, 1), (64, 256, 0), (128, 128, 0), (128, 256, 0), (128, 256, 1)]
+    # (M, N, A in TMEM, CTAs per SM)
+    shapes = [(128, 64, 0, 1), (128, 64, 1, 1), (64, 256, 0, 1), (128, 128, 0, 1), (128, 256, 0, 1),
+              (128, 256, 1, 1), (128, 64, 0, 2), (128, 64, 1, 2), (128, 128, 0, 2)]
+    cyc = torch.zeros(2 * n_sm, dtype=torch.int64, device=dev)
     rows = []
     with ClockSampler(local) as clk:
         for _ in range(max(1, args.steps // 5)):
-            for m, n, a_tmem in shapes:
+            for m, n, a_tmem, per_sm in shapes:
                 for chain, reps in ((64, 40), (4, 400)):
-                    L.call("nif_tc_mma_rate", m, n, a_tmem, chain, reps, n_sm, vp(cyc.data_ptr()), vp(ws.data_ptr()),
+                    nc = per_sm * n_sm
+                    L.call("nif_tc_mma_rate", m, n, a_tmem, chain, reps, nc, vp(cyc.data_ptr()), vp(ws.data_ptr()),
                            ws.numel(), nif._stream())
                     torch.cuda.synchronize()
-                    c = cyc.double()
+                    c = cyc[:nc].double()
                     assert bool((c > 0).all()), "an MMA wait timed out"
-                    rows.append((m, n, a_tmem, chain, float(c.mean()) / (reps * chain)))
+                    # cycles per MMA of one SM: each CTA's own rate divided by the CTAs sharing the SM
+                    rows.append((m, n, a_tmem, per_sm, chain, float(c.mean()) / (reps * chain) / per_sm))
     clocks = clk.summary()
     det = ctypes.c_int64()
     L.call("nif_check", vp(ws.data_ptr()), ctypes.byref(det), nif._stream())
     mhz = clocks.get("sm_mhz") or 2070.0
     out = {}
-    for m, n, a_tmem, chain, per in rows:
-        key = f"M{m}xN{n}" + ("_A_tmem" if a_tmem else "") + f"_chain{chain}"
+    for m, n, a_tmem, per_sm, chain, per in rows:
+        key = f"M{m}xN{n}" + ("_A_tmem" if a_tmem else "") + (f"_{per_sm}cta_per_sm" if per_sm > 1 else "") + \
+            f"_chain{chain}"
         out.setdefault(key, []).append(per)
     table = {}
     for key, v in out.items():

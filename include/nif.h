@@ -517,7 +517,8 @@ nif_status nif_infer_noalloc(const nif_model_desc* m, const void* d_tlas, const 
  * no counterpart): SM cycles taken by tcgen05.mma (kind::f16, one CTA, K = 16
  * per instruction) at M = m (64 or 128) x N = n (a multiple of 16 up to 256),
  * A from shared memory or (a_tmem, m = 128) from tensor memory.  Each of
- * n_ctas CTAs (at most the SM count) issues `chain` MMAs from one thread,
+ * n_ctas CTAs (at most twice the SM count; above the SM count two CTAs share
+ * an SM and n is at most 128) issues `chain` MMAs from one thread,
  * commits them and waits, `reps` times after two untimed rounds, and writes
  * the SM cycles of the timed rounds to d_cycles[cta] (device int64, -1 when a
  * wait timed out; the timeout is also recorded in d_ws, >= 256 bytes, for

@@ -13,8 +13,9 @@
 //               in a K-major core-matrix layout: column block kb of 8-row
 //               group j at kb * 2048 + j * 128 bytes; rows past nq and
 //               column blocks past K/8 are filled with zeros by the copy;
-//   warp 2      one thread issues the MMAs: per layer, slot 0 then slot 1
-//               (layer 1 reads A from shared memory, later layers from TMEM);
+//   warps 1, 2  one thread each issues the MMAs of slot 0 (warp 1) or slot
+//               1 (warp 2), layer by layer (layer 1 reads A from shared
+//               memory, later layers from TMEM);
 //   warps 4-7   epilogue of slot 0, warps 8-11 epilogue of slot 1: each
 //               thread owns one row (its TMEM lane), reads the FP32
 //               accumulator, applies the activation and writes the next
@@ -30,7 +31,7 @@
 namespace nif {
 namespace tc {
 
-constexpr int kPipeWarps = 12;  // warps 1 and 3 have no role (epilogue warps need warp % 4 = lane quarter)
+constexpr int kPipeWarps = 12;  // warp 3 has no role (epilogue warps need warp % 4 = lane quarter)
 constexpr int kPipeThreads = 32 * kPipeWarps;
 constexpr int kPipeMaxNets = 2;
 // A tile: byte stride between K-adjacent core matrices (one 16-byte column
@@ -144,50 +145,50 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
       }
     }
     __syncwarp();
-  } else if (warp == 2) {
-    // -------------------------------------------------------------- MMA
+  } else if (warp == 1 || warp == 2) {
+    // ------------------------------------------------- MMA, one per slot
+    // warp 1 issues slot 0's MMAs, warp 2 slot 1's: two issuing threads
+    // keep more small MMAs in the tensor pipe than one issuing both slots
     if (lane == 0) {
-      uint32_t ph_act[2] = {0u, 0u};
+      const int s = warp - 1;
+      uint32_t ph_act = 0u;
       bool ok = true;
-      for (int k = 0; ok && tile_of(k) < n_tiles; k += 2) {
+      for (int k = s; ok && tile_of(k) < n_tiles; k += 2) {
+        const int64_t t = tile_of(k);
+        const int u = k >> 1;
+        const int g = find_group(s_pre, p.n_nets, t);
+        const uint32_t acc = tmem + 128u * static_cast<uint32_t>(s);
         for (int l = 0; ok && l < H; ++l) {
-          for (int s = 0; s < 2; ++s) {
-            const int64_t t = tile_of(k + s);
-            if (t >= n_tiles) continue;
-            const int u = (k + s) >> 1;
-            if (l == 0) {
-              ok = mbar_wait(smem_u32(&s_xfull[s]), u & 1, err, kWaitCycles, 12) &&
-                   (u == 0 || mbar_wait(smem_u32(&s_accfree[s]), (u - 1) & 1, err, kWaitCycles, 13));
-            } else {
-              ok = mbar_wait(smem_u32(&s_actready[s]), ph_act[s], err, kWaitCycles, 14);
-              ph_act[s] ^= 1u;
-            }
-            if (!ok) break;
-            tc_fence_after();
-            const int g = find_group(s_pre, p.n_nets, t);
-            const uint32_t wb = smem_u32(smem + L.w_off + static_cast<uint32_t>(g) * L.net_bytes +
-                                         (l == 0 ? 0u : static_cast<uint32_t>(W * Kp * 2 + (l - 1) * W * W * 2)));
-            const uint32_t acc = tmem + 128u * static_cast<uint32_t>(s);
-            // descriptors formed once per layer, then advanced by their
-            // start-address field (16-byte units) per K step, so that the
-            // issuing thread spends few cycles between MMAs
-            if (l == 0) {
-              const uint64_t ad = smem_desc(smem_u32(smem + L.x_off[s]), kXLbo, kXSbo);
-              const uint64_t bd = smem_desc(wb, 128, static_cast<uint32_t>(Kp / 8) * 128);
-              mma<0>(acc, ad, bd, idesc, 0u);
-              for (int kk = 1; kk < Kp / 16; ++kk)
-                mma<0>(acc, desc_advance(ad, kk * 2 * kXLbo), desc_advance(bd, kk * 256), idesc, 1u);
-              mma_commit(smem_u32(&s_accfull[s]));
-              mma_commit(smem_u32(&s_xempty[s]));
-            } else {
-              // W = 64: four K steps of 16, A from the activation columns
-              const uint64_t bd = smem_desc(wb, 128, 1024);
+          if (l == 0) {
+            ok = mbar_wait(smem_u32(&s_xfull[s]), u & 1, err, kWaitCycles, 12) &&
+                 (u == 0 || mbar_wait(smem_u32(&s_accfree[s]), (u - 1) & 1, err, kWaitCycles, 13));
+          } else {
+            ok = mbar_wait(smem_u32(&s_actready[s]), ph_act, err, kWaitCycles, 14);
+            ph_act ^= 1u;
+          }
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t wb = smem_u32(smem + L.w_off + static_cast<uint32_t>(g) * L.net_bytes +
+                                       (l == 0 ? 0u : static_cast<uint32_t>(W * Kp * 2 + (l - 1) * W * W * 2)));
+          // descriptors formed once per layer, then advanced by their
+          // start-address field (16-byte units) per K step, so that the
+          // issuing thread spends few cycles between MMAs
+          if (l == 0) {
+            const uint64_t ad = smem_desc(smem_u32(smem + L.x_off[s]), kXLbo, kXSbo);
+            const uint64_t bd = smem_desc(wb, 128, static_cast<uint32_t>(Kp / 8) * 128);
+            mma<0>(acc, ad, bd, idesc, 0u);
+            for (int kk = 1; kk < Kp / 16; ++kk)
+              mma<0>(acc, desc_advance(ad, kk * 2 * kXLbo), desc_advance(bd, kk * 256), idesc, 1u);
+            mma_commit(smem_u32(&s_accfull[s]));
+            mma_commit(smem_u32(&s_xempty[s]));
+          } else {
+            // W = 64: four K steps of 16, A from the activation columns
+            const uint64_t bd = smem_desc(wb, 128, 1024);
 #pragma unroll
-              for (int kk = 0; kk < 4; ++kk)
-                mma_ta(acc, acc + 64u + static_cast<uint32_t>(kk * 8), desc_advance(bd, kk * 256), idesc,
-                       kk > 0 ? 1u : 0u);
-              mma_commit(smem_u32(&s_accfull[s]));
-            }
+            for (int kk = 0; kk < 4; ++kk)
+              mma_ta(acc, acc + 64u + static_cast<uint32_t>(kk * 8), desc_advance(bd, kk * 256), idesc,
+                     kk > 0 ? 1u : 0u);
+            mma_commit(smem_u32(&s_accfull[s]));
           }
         }
       }
@@ -289,10 +290,10 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
 //            (each step halves the rows a lane keeps), the four warps'
 //            partial sums meet in shared memory and are added in a fixed
 //            order, one row per thread.
-// Roles: warp 0 copies (one thread), warp 1 issues the MMAs (one thread),
-// warps 4-11 run slot 0's epilogue and warps 12-19 slot 1's (warp w reads
-// TMEM lane quarter w % 4; warps w and w + 4 take the two 128-row halves of
-// the tile).  Tiles alternate between the two TMEM slots of 256 columns;
+// Roles: warp 0 copies (one thread), warps 1 and 2 issue the MMAs of slot 0
+// and slot 1 (one thread each), warps 4-11 run slot 0's epilogue and warps
+// 12-19 slot 1's (warp w reads TMEM lane quarter w % 4; warps w and w + 4
+// take the two 128-row halves of the tile).  Tiles alternate between the two TMEM slots of 256 columns;
 // their inputs cycle through n_buf shared-memory buffers, so that the copy of
 // the next tile overlaps the two tiles in flight.
 constexpr int kRowsTile = 256;
@@ -419,50 +420,47 @@ __global__ void __launch_bounds__(kRowsThreads, 1)
       }
     }
     __syncwarp();
-  } else if (warp == 1) {
-    // -------------------------------------------------------------- MMA
+  } else if (warp == 1 || warp == 2) {
+    // ------------------------------------------------- MMA, one per slot
     if (lane == 0) {
+      const int s = warp - 1;
       const uint32_t id_k = instr_desc(64, kRowsTile, O::fmt);  // B K-major (the inputs)
       const uint32_t id_mn = id_k | (1u << 16);                  // B MN-major (the activations)
-      uint32_t ph_act[2] = {0u, 0u};
+      uint32_t ph_act = 0u;
       bool ok = true;
-      for (int k = 0; ok && tile_of(k) < n_tiles; k += 2) {
+      for (int kt = s; ok && tile_of(kt) < n_tiles; kt += 2) {
+        const int64_t t = tile_of(kt);
+        const int b = kt % n_buf, u = kt >> 1;
+        const int g = find_group(s_pre, p.n_nets, t);
+        const uint32_t net = smem_u32(smem + L.w_off + static_cast<uint32_t>(g) * L.net_bytes);
+        const uint32_t xb = smem_u32(smem + L.buf_off + static_cast<uint32_t>(b) * L.buf_bytes);
+        const uint32_t acc = tmem + 256u * static_cast<uint32_t>(s);
+        const uint64_t bd = smem_desc(xb, kRowsKStride, 128);
         for (int l = 0; ok && l < H; ++l) {
-          for (int s = 0; s < 2; ++s) {
-            const int kt = k + s;
-            const int64_t t = tile_of(kt);
-            if (t >= n_tiles) continue;
-            const int b = kt % n_buf, u = kt >> 1;
-            if (l == 0) {
-              ok = mbar_wait(smem_u32(&s_full[b]), (kt / n_buf) & 1, err, kWaitCycles, 22) &&
-                   (u == 0 || mbar_wait(smem_u32(&s_accfree[s]), (u - 1) & 1, err, kWaitCycles, 23));
-            } else {
-              ok = mbar_wait(smem_u32(&s_actready[s]), ph_act[s], err, kWaitCycles, 24);
-              ph_act[s] ^= 1u;
-            }
-            if (!ok) break;
-            tc_fence_after();
-            const int g = find_group(s_pre, p.n_nets, t);
-            const uint32_t net = smem_u32(smem + L.w_off + static_cast<uint32_t>(g) * L.net_bytes);
-            const uint32_t xb = smem_u32(smem + L.buf_off + static_cast<uint32_t>(b) * L.buf_bytes);
-            const uint32_t acc = tmem + 256u * static_cast<uint32_t>(s);
-            const uint64_t bd = smem_desc(xb, kRowsKStride, 128);
-            if (l == 0) {
-              const uint64_t ad = smem_desc(net, 128, static_cast<uint32_t>(Kp / 8) * 128);
-              mma<0>(acc, ad, bd, id_k, 0u);
-              for (int kk = 1; kk < Kp / 16; ++kk)
-                mma<0>(acc, desc_advance(ad, kk * 256), desc_advance(bd, kk * 2 * kRowsKStride), id_k, 1u);
-            } else {
-              const uint64_t ad =
-                  smem_desc(net + static_cast<uint32_t>(64 * Kp * 2 + (l - 1) * 64 * 64 * 2), 128, 1024);
-#pragma unroll
-              for (int kk = 0; kk < 4; ++kk)
-                mma<0>(acc, desc_advance(ad, kk * 256), desc_advance(bd, kk * 2 * kRowsKStride), id_mn,
-                       kk > 0 ? 1u : 0u);
-            }
-            mma_commit(smem_u32(&s_accfull[s]));
-            if (l == H - 1) mma_commit(smem_u32(&s_empty[b]));  // the tile's last read of its buffer
+          if (l == 0) {
+            ok = mbar_wait(smem_u32(&s_full[b]), (kt / n_buf) & 1, err, kWaitCycles, 22) &&
+                 (u == 0 || mbar_wait(smem_u32(&s_accfree[s]), (u - 1) & 1, err, kWaitCycles, 23));
+          } else {
+            ok = mbar_wait(smem_u32(&s_actready[s]), ph_act, err, kWaitCycles, 24);
+            ph_act ^= 1u;
           }
+          if (!ok) break;
+          tc_fence_after();
+          if (l == 0) {
+            const uint64_t ad = smem_desc(net, 128, static_cast<uint32_t>(Kp / 8) * 128);
+            mma<0>(acc, ad, bd, id_k, 0u);
+            for (int kk = 1; kk < Kp / 16; ++kk)
+              mma<0>(acc, desc_advance(ad, kk * 256), desc_advance(bd, kk * 2 * kRowsKStride), id_k, 1u);
+          } else {
+            const uint64_t ad =
+                smem_desc(net + static_cast<uint32_t>(64 * Kp * 2 + (l - 1) * 64 * 64 * 2), 128, 1024);
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+              mma<0>(acc, desc_advance(ad, kk * 256), desc_advance(bd, kk * 2 * kRowsKStride), id_mn,
+                     kk > 0 ? 1u : 0u);
+          }
+          mma_commit(smem_u32(&s_accfull[s]));
+          if (l == H - 1) mma_commit(smem_u32(&s_empty[b]));  // the tile's last read of its buffer
         }
       }
       if (!ok) s_abort = 1;

@@ -129,18 +129,21 @@ def test_mlp_infer_leaky_depths(n_hidden, tile_m):
 
 def test_tc_mma_rate_measures_every_shape():
     """nif_tc_mma_rate (the tensor-core instruction-rate measurement behind
-    the MLP kernels' tile shapes) runs on every SM at the shapes the kernels
-    issue and reports a plausible number of cycles per MMA: at least the
-    cycles a 128 x 256 x 16 product needs at the nominal 4,096 FP16 FMAs per
-    cycle per SM, and no wait timed out."""
+    the MLP kernels' tile shapes) runs on every SM, with one or two CTAs per
+    SM, at the shapes the kernels issue and reports a plausible number of
+    cycles per MMA: at least the cycles the product needs at the nominal
+    4,096 FP16 FMAs per cycle per SM, and no wait timed out; a shape too wide
+    for two CTAs per SM is refused."""
     n_sm = torch.cuda.get_device_properties(0).multi_processor_count
-    cyc = torch.zeros(n_sm, dtype=torch.int64, device="cuda")
+    cyc = torch.zeros(2 * n_sm, dtype=torch.int64, device="cuda")
     ws = torch.zeros(256, dtype=torch.uint8, device="cuda")
-    for m, n, a_tmem in ((128, 64, 0), (128, 64, 1), (64, 256, 0), (128, 256, 0)):
-        L.call("nif_tc_mma_rate", m, n, a_tmem, 16, 8, n_sm, ctypes.c_void_p(cyc.data_ptr()),
+    for m, n, a_tmem, per_sm in ((128, 64, 0, 1), (128, 64, 1, 1), (64, 256, 0, 1), (128, 256, 0, 1),
+                                 (128, 64, 1, 2)):
+        nc = per_sm * n_sm
+        L.call("nif_tc_mma_rate", m, n, a_tmem, 16, 8, nc, ctypes.c_void_p(cyc.data_ptr()),
                ctypes.c_void_p(ws.data_ptr()), ws.numel(), nif._stream())
         torch.cuda.synchronize()
-        per = cyc.double().cpu().numpy() / (16 * 8)
+        per = cyc[:nc].double().cpu().numpy() / (16 * 8)
         assert (per > 0).all()
         assert per.min() >= m * n * 16 / 4096 * 0.9, per.min()
         assert np.median(per) < 10000
@@ -148,4 +151,7 @@ def test_tc_mma_rate_measures_every_shape():
     L.call("nif_check", ctypes.c_void_p(ws.data_ptr()), ctypes.byref(det), nif._stream())
     with pytest.raises(L.NifError):
         L.call("nif_tc_mma_rate", 96, 64, 0, 16, 8, 1, ctypes.c_void_p(cyc.data_ptr()),
+               ctypes.c_void_p(ws.data_ptr()), ws.numel(), nif._stream())
+    with pytest.raises(L.NifError):
+        L.call("nif_tc_mma_rate", 128, 256, 0, 16, 8, 2 * n_sm, ctypes.c_void_p(cyc.data_ptr()),
                ctypes.c_void_p(ws.data_ptr()), ws.numel(), nif._stream())
