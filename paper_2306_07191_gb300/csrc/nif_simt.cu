@@ -143,6 +143,16 @@ __device__ __forceinline__ const bvh::Header* tlas_header(const char* tlas) {
 #define NIF_FRONT_SLOTS 8
 #endif
 constexpr int kSlots = NIF_FRONT_SLOTS;
+// Resident blocks of 128 threads per SM the round-1 count and the round-2
+// passes are compiled for: 10 caps them at 48 registers (40 warps per SM; a
+// few bytes spill, in the rarely taken walk of rays with more pairs than
+// slots); 8 leaves them 57-64 (32 warps), 12 spills in the walk itself
+#ifndef NIF_FRONT_FIRST_BLOCKS
+#define NIF_FRONT_FIRST_BLOCKS 10
+#endif
+#ifndef NIF_FRONT_REST_BLOCKS
+#define NIF_FRONT_REST_BLOCKS 10
+#endif
 static_assert(kSlots >= 1 && kSlots <= 64, "slots per ray");
 
 template <bool kTlas, bool kKeep>
@@ -304,7 +314,7 @@ __device__ __forceinline__ int ray_pairs_traverse(const NifParams& p, const char
 // keeps the first kSlots pairs in slots with the index of the pair round 1
 // queries, and counts those pairs per bucket.
 template <bool kTlas>
-__global__ void __launch_bounds__(128) k_front_count_first(NifParams p, const char* tlas,
+__global__ void __launch_bounds__(128, NIF_FRONT_FIRST_BLOCKS) k_front_count_first(NifParams p, const char* tlas,
                                                            const nif_ray* rays, int64_t n,
                                                            const uint32_t* bits, uint32_t* g_count,
                                                            uint32_t* slots, uint8_t* nhits,
@@ -366,7 +376,7 @@ __global__ void __launch_bounds__(128) k_front_scatter_first(NifParams p, const 
 // Round 2: the other pairs of the rays round 1 left unoccluded, counted
 // (kScatter false) or written after round 1's pairs (kScatter true).
 template <bool kTlas, bool kScatter>
-__global__ void __launch_bounds__(128) k_front_rest(NifParams p, const char* tlas,
+__global__ void __launch_bounds__(128, NIF_FRONT_REST_BLOCKS) k_front_rest(NifParams p, const char* tlas,
                                                     const nif_ray* rays, int64_t n,
                                                     const uint32_t* bits, uint32_t* g_counter,
                                                     int64_t max_q, const uint32_t* slots,
